@@ -1,0 +1,155 @@
+"""Seeded synthetic workloads: parameter dictionaries only.
+
+This module is the one place that both the CUDA path and the CPU oracle take their
+inputs from.  It holds no arithmetic of the method: it only states material constants,
+grid sizes, projectile placement and the counter-based random draws of the batched
+impact distribution.  Each builder returns a plain dictionary
+    {"grid": {...}, "materials": [...], "layers": [...], "projectile": {...} | None}
+with SI units throughout (m, kg/m^3, Pa, J/kg, m/s).
+"""
+from __future__ import annotations
+
+import math
+
+# --- materials -----------------------------------------------------------------------
+
+def basalt(strength: bool = False, cohesion: float = 10e6, friction: float = 0.6,
+           limit: float = 2.5e9) -> dict:
+    """Basalt-like Tillotson material (the constants the impact configurations name).
+    The shear modulus follows from Poisson's ratio 0.25 with bulk modulus K = A, G = 0.6 A.
+    With strength: Collins-type yield, cohesion -> Y_i0, friction -> mu_i = mu_d,
+    limiting strength -> Y_im = Y_dm, damaged cohesion Y_d0 = 0.01 MPa (Table 1 of the
+    paper lists 0.01 MPa for every rock); tensile limit -Y_i0."""
+    m = dict(eos="tillotson", rho0=2700.0, A=26.7e9, B=26.7e9, E0=487e6, a=0.5, b=1.5,
+             alpha=5.0, beta=5.0, Eiv=4.72e6, Ecv=18.2e6, gamma=0.0, strength="none",
+             p_t=0.0)
+    if strength:
+        m.update(strength="collins", Yi0=cohesion, mui=friction, Yim=limit, Yd0=0.01e6,
+                 mud=friction, Ydm=limit, G=0.6 * m["A"], eps_fb=1e-4, B_dam=1e-11, p_bd=3e8,
+                 p_t=-cohesion)
+    return m
+
+
+def iron() -> dict:
+    """Iron-like Tillotson projectile, rho0 = 7800 kg/m^3 as the configuration states.
+    The remaining constants are the commonly tabulated Tillotson iron set (Tillotson 1962,
+    as reprinted by Melosh 1989): A = 128 GPa, B = 105 GPa, E0 = 9.5 MJ/kg, a = 0.5,
+    b = 1.5, alpha = beta = 5, E_iv = 2.4 MJ/kg, E_cv = 8.67 MJ/kg.  Hydrodynamic."""
+    return dict(eos="tillotson", rho0=7800.0, A=128e9, B=105e9, E0=9.5e6, a=0.5, b=1.5,
+                alpha=5.0, beta=5.0, Eiv=2.4e6, Ecv=8.67e6, gamma=0.0, strength="none", p_t=0.0)
+
+
+def ideal_gas(gamma: float = 1.4, rho0: float = 1.0) -> dict:
+    return dict(eos="ideal_gas", rho0=rho0, gamma=gamma, A=0.0, B=0.0, E0=1.0, a=0.0, b=0.0,
+                alpha=0.0, beta=0.0, Eiv=0.0, Ecv=1.0, strength="none", p_t=0.0)
+
+
+# --- grid ----------------------------------------------------------------------------
+
+def grid(nr: int, nz: int, dx: float, **kw) -> dict:
+    g = dict(nr=int(nr), nz=int(nz), dx=float(dx), pml_r=0, pml_b=0, pml_R=0.01, pml_c=0.0,
+             gravity=0.0, cfl=0.4, dt_init=1e30, dt_max=1e30, dt_growth=1.2, dt_min=0.0,
+             av_cq=1.0, av_cl=0.25, f_min=1e-6, bc_top="outflow", bc_bottom="noslip")
+    g.update(kw)
+    return g
+
+
+def impact(nr: int, nz: int, dx: float, target: dict, projectile_mat: dict | None,
+           radius_cells: float, v_imp: float, surface_row: int, pml: int, gravity: float = 0.0,
+           **gkw) -> dict:
+    """Half-space target with its surface at row `surface_row`; a sphere of radius
+    `radius_cells` cells on the axis, tangent to the surface, moving down at `v_imp`."""
+    mats = [target] if projectile_mat is None else [target, projectile_mat]
+    pmat = 0 if projectile_mat is None else 1
+    zs = surface_row * dx
+    R = radius_cells * dx
+    return {
+        "grid": grid(nr, nz, dx, pml_r=pml, pml_b=pml, gravity=gravity, **gkw),
+        "materials": mats,
+        "layers": [dict(mat=0, zlo=0.0, zhi=zs, rho=0.0, I0=0.0, vz=0.0)],
+        "projectile": dict(mat=pmat, radius=R, zc=zs + R, vz=-abs(v_imp), rho=0.0, I0=0.0),
+        "z_surface": zs,
+    }
+
+
+# --- the five configurations -------------------------------------------------------------
+
+def plain_fp64_100() -> dict:
+    """100 x 100 cells of 10 m, basalt half-space (surface at row 70), hydrodynamic,
+    projectile radius 5 cells at 10 km/s, PML 16 on the right and bottom, no gravity,
+    CFL 0.4; 200 steps."""
+    w = impact(100, 100, 10.0, basalt(), None, 5, 10e3, 70, 16)
+    w["name"] = "plain_fp64_100x100"
+    w["steps"] = 200
+    return w
+
+
+def full_fp64_800() -> dict:
+    """800 x 800 cells of 25 m, iron projectile (radius 20 cells, 15 km/s) into basalt
+    with Collins strength and damage, gravity 1.62 m/s^2, PML 40; run to 20 s."""
+    w = impact(800, 800, 25.0, basalt(strength=True), iron(), 20, 15e3, 560, 40, gravity=1.62)
+    w["name"] = "full_fp64_800x800"
+    w["t_end"] = 20.0
+    return w
+
+
+def large_4000() -> dict:
+    """4000 x 4000 cells, the 100x100 configuration's physics (10 m cells, basalt,
+    hydrodynamic, PML 16, surface at 70 % of the height), projectile radius 100 cells;
+    2000 steps."""
+    w = impact(4000, 4000, 10.0, basalt(), None, 100, 10e3, 2800, 16)
+    w["name"] = "large_4000x4000"
+    w["steps"] = 2000
+    return w
+
+
+def scaled_plain(n: int, radius_cells: float = None) -> dict:
+    """The 100x100 configuration's physics on an n x n grid (surface at 70 %)."""
+    rc = radius_cells if radius_cells is not None else max(2.0, n / 40.0)
+    w = impact(n, n, 10.0, basalt(), None, rc, 10e3, int(round(0.7 * n)), 16)
+    w["name"] = f"plain_{n}x{n}"
+    return w
+
+
+# --- counter-based draws for the batched distribution (SplitMix64) -------------------------
+
+_MASK = (1 << 64) - 1
+
+
+def splitmix64(x: int) -> int:
+    """SplitMix64 finaliser (Steele, Lea & Flood 2014) of a 64-bit counter."""
+    z = (x + 0x9E3779B97F4A7C15) & _MASK
+    z = ((z ^ (z >> 30)) * 0xBF58476D1CE4E5B9) & _MASK
+    z = ((z ^ (z >> 27)) * 0x94D049BB133111EB) & _MASK
+    return z ^ (z >> 31)
+
+
+def uniform01(seed: int, field: int) -> float:
+    """53-bit uniform draw in [0, 1) for (seed, field)."""
+    return (splitmix64((seed << 8) | field) >> 11) * (1.0 / (1 << 53))
+
+
+def batched_draw(seed: int) -> dict:
+    """One impact of the batched distribution: square grid U{200..800} cells, projectile
+    radius U{8..32} cells, velocity U(6, 20) km/s, cohesion log-uniform on 1..100 MPa,
+    friction U(0.4, 0.8), projectile basalt or iron with probability 1/2.  Cells of 25 m,
+    PML 40, gravity 1.62, surface at 70 % of the height."""
+    n = 200 + int(uniform01(seed, 0) * 601)
+    rad = 8 + int(uniform01(seed, 1) * 25)
+    v = 6e3 + 14e3 * uniform01(seed, 2)
+    coh = math.exp(math.log(1e6) + (math.log(100e6) - math.log(1e6)) * uniform01(seed, 3))
+    fr = 0.4 + 0.4 * uniform01(seed, 4)
+    dense = uniform01(seed, 5) < 0.5
+    return dict(seed=seed, n=n, radius_cells=rad, v_imp=v, cohesion=coh, friction=fr,
+                projectile="iron" if dense else "basalt")
+
+
+def batched_run(draw: dict, n_override: int | None = None) -> dict:
+    n = n_override or draw["n"]
+    tgt = basalt(strength=True, cohesion=draw["cohesion"], friction=draw["friction"])
+    proj = iron() if draw["projectile"] == "iron" else basalt()
+    w = impact(n, n, 25.0, tgt, proj, draw["radius_cells"], draw["v_imp"], int(round(0.7 * n)),
+               40, gravity=1.62)
+    w["name"] = f"batched_seed{draw['seed']}"
+    w["t_end"] = 20.0
+    return w

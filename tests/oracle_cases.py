@@ -1,0 +1,79 @@
+"""Small synthetic set-ups shared by the oracle pins and the GPU parity tests (parameter
+dictionaries only; no arithmetic of the method)."""
+from __future__ import annotations
+
+import numpy as np
+
+from paper_2403_04267_gb300 import workloads as W
+
+
+def sod_spec(nz: int, nr: int = 3) -> dict:
+    dx = 1.0 / nz
+    g = W.grid(nr, nz, dx, bc_top="wall")
+    gas = W.ideal_gas(1.4)
+    return {"grid": g, "materials": [gas], "projectile": None, "layers": [
+        dict(mat=0, zlo=0.0, zhi=0.5, rho=1.0, I0=1.0 / (0.4 * 1.0), vz=0.0),
+        dict(mat=0, zlo=0.5, zhi=1.0, rho=0.125, I0=0.1 / (0.4 * 0.125), vz=0.0)]}
+
+
+def rh_spec(nz: int, up: float = 2000.0, length: float = 400.0) -> dict:
+    bas = dict(W.basalt(), p_t=-1e12)
+    g = W.grid(3, nz, length / nz, bc_top="outflow")
+    return {"grid": g, "materials": [bas], "projectile": None,
+            "layers": [dict(mat=0, zlo=0.0, zhi=length, rho=2700.0, I0=0.0, vz=-up)]}
+
+
+def gas_box_spec(nr: int, nz: int, p: float = 1e5) -> dict:
+    gas = W.ideal_gas(1.4, rho0=1.2)
+    g = W.grid(nr, nz, 1.0, bc_top="wall")
+    return {"grid": g, "materials": [gas], "projectile": None,
+            "layers": [dict(mat=0, zlo=0.0, zhi=float(nz), rho=1.2, I0=p / (0.4 * 1.2), vz=0.0)]}
+
+
+def hydrostatic_spec(nr: int, nz: int, dx: float = 25.0, g: float = 1.62) -> dict:
+    bas = W.basalt(strength=True)
+    gr = W.grid(nr, nz, dx, gravity=g, bc_top="outflow")
+    return {"grid": gr, "materials": [bas], "projectile": None,
+            "layers": [dict(mat=0, zlo=0.0, zhi=0.75 * nz * dx, rho=0.0, I0=0.0, vz=0.0)]}
+
+
+def plane_wave_spec(nz: int, pml_b: int, av: bool = False, dx: float = 10.0) -> dict:
+    bas = dict(W.basalt(), p_t=-1e12)
+    kw = {} if av else dict(av_cq=0.0, av_cl=0.0)
+    g = W.grid(2, nz, dx, bc_top="wall", pml_b=pml_b, pml_R=0.01, **kw)
+    return {"grid": g, "materials": [bas], "projectile": None,
+            "layers": [dict(mat=0, zlo=0.0, zhi=nz * dx, rho=2700.0, I0=0.0, vz=0.0)]}
+
+
+def plane_wave_fields(nz: int, dx: float = 10.0, U: float = 1.0, width: float = 20.0,
+                      centre: float = 0.6):
+    """Density and vertex z-velocity of a Gaussian pulse travelling down (linear acoustics
+    of basalt: rho' = rho0 U g / c, v_z = -U g)."""
+    bas = W.basalt()
+    c = np.sqrt(bas["A"] / bas["rho0"])
+    zc = centre * nz * dx
+    zcell = (np.arange(nz) + 0.5) * dx
+    zv = np.arange(nz + 1) * dx
+    gc = np.exp(-((zcell - zc) / (width * dx / 2)) ** 2)
+    gv = np.exp(-((zv - zc) / (width * dx / 2)) ** 2)
+    rho = bas["rho0"] * (1 + U * gc / c)
+    vz = -U * gv
+    vz[0] = 0.0
+    vz[-1] = 0.0
+    return rho, vz, c
+
+
+def random_impact_spec(seed: int, nr: int, nz: int, nmat: int = 2, strength: bool = True,
+                       pml: int = 4, gravity: float = 1.62) -> dict:
+    """Small impact with ragged sizes used as a brute-force edge case."""
+    rng = np.random.default_rng(seed)
+    tgt = W.basalt(strength=strength, cohesion=float(rng.uniform(1e6, 1e8)),
+                   friction=float(rng.uniform(0.4, 0.8)))
+    proj = W.iron() if nmat == 2 else None
+    surface = max(2, int(0.6 * nz))
+    rad = float(rng.uniform(1.5, max(1.6, min(nr, nz) / 5)))
+    v = float(rng.uniform(3e3, 15e3))
+    w = W.impact(nr, nz, 20.0, tgt, proj, rad, v, surface, pml, gravity=gravity)
+    w["grid"]["pml_r"] = min(pml, nr - 1)
+    w["grid"]["pml_b"] = min(pml, nz - 1)
+    return w

@@ -1,0 +1,123 @@
+"""Pins of the PML (Sect. 3): the attenuation profile gives the stated theoretical
+reflection, and a plane pulse entering the bottom strip at normal incidence returns
+with an amplitude near R = 0.01 (delta = 30 cells), while the same column without the
+strip reflects it almost fully."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle_cases as OC
+from oracle import oracle as O
+
+
+def _golden():
+    vals = {}
+    with open(__file__.replace("test_oracle_pml.py", "golden/pml_reflection.txt")) as fh:
+        for line in fh:
+            if line.strip() and not line.startswith("#"):
+                k, v = line.split()
+                vals[k] = float(v)
+    return vals
+
+
+def test_profile_round_trip_attenuation_is_R():
+    g = _golden()
+    c, dx, width, R = 3144.6, 10.0, g["width_cells"], g["R"]
+    n = 20000
+    y = (np.arange(n) + 0.5) / n * width
+    integral = sum(O.pml_profile(c, width, dx, yy, R) for yy in y) * (width * dx / n)
+    assert math.isclose(math.exp(-2 * integral / c), R, rel_tol=1e-6)
+    assert O.pml_profile(c, width, dx, 0.0, R) == 0.0
+    assert math.isclose(O.pml_profile(c, width, dx, width, R), 1.5 * c / (width * dx) * math.log(1 / R), rel_tol=1e-14)
+
+
+def _reflection(pml_b, av=False, nz=300):
+    s = O.OracleSim(OC.plane_wave_spec(nz, pml_b, av=av))
+    rho, vz, c = OC.plane_wave_fields(nz)
+    s.set("rho0", np.repeat(rho[:, None], 2, axis=1))
+    s.set("vz", np.repeat(vz[:, None], 3, axis=1))
+    probe = int(0.45 * nz)
+    dx = 10.0
+    t_inc = 2.5 * (0.6 - 0.45) * nz * dx / c
+    t_ret = 0.9 * (0.45 + 0.45) * nz * dx / c + 0.5 * (0.6 - 0.45) * nz * dx / c
+    T = 2.0 * 0.6 * nz * dx / c
+    inc = ret = 0.0
+    while s.scalars()["t"] < T:
+        s.step(1)
+        t = s.scalars()["t"]
+        v = abs(s.get("vz")[probe, 1])
+        if t < t_inc:
+            inc = max(inc, v)
+        if t > t_ret:
+            ret = max(ret, v)
+    return ret / inc
+
+
+def test_plane_wave_reflection():
+    R = _golden()["R"]
+    wall = _reflection(0)
+    pml = _reflection(30)
+    assert wall > 0.95
+    assert 0.5 * R < pml < 2.0 * R
+    # with the artificial viscosity on the strip still absorbs to well below 5 %
+    assert _reflection(30, av=True) < 0.05
+
+
+# --- tangential transparency ----------------------------------------------------------
+# Multiplying the stretched equations by s = 1 + i d / omega (Sect. 3) leaves the
+# tangential derivatives unstretched: a wave travelling parallel to a strip inside it
+# obeys the unstretched equations exactly, provided every auxiliary starts at
+# -d (q - q_ref) for its conserved quantity q (true automatically for waves that enter
+# from outside).  The explicit scheme reproduces this at first order in dt.
+
+def _tangential(strip, pml, cfl, dx=10.0, T=0.2):
+    from paper_2403_04267_gb300 import workloads as W
+    bas = dict(W.basalt(), p_t=-1e12)
+    c = math.sqrt(bas["A"] / bas["rho0"])
+    nr, nz = (24, 160) if strip == "right" else (160, 24)
+    g = W.grid(nr, nz, dx, bc_top="wall", bc_bottom="freeslip", av_cq=0.0, av_cl=0.0, cfl=cfl,
+               dt_max=cfl * dx / c, pml_R=0.01, pml_r=pml if strip == "right" else 0,
+               pml_b=pml if strip == "bottom" else 0)
+    s = O.OracleSim({"grid": g, "materials": [bas], "projectile": None,
+                     "layers": [dict(mat=0, zlo=0.0, zhi=nz * dx, rho=2700.0)]})
+    V = (np.arange(nr) + 0.5) * dx ** 3
+    if strip == "right":
+        zc, zv = (np.arange(nz) + 0.5) * dx, np.arange(nz + 1) * dx
+        z0, w = 0.7 * nz * dx, 10 * dx
+        rho = np.repeat((2700 * (1 + np.exp(-((zc - z0) / w) ** 2) / c))[:, None], nr, 1)
+        vz = np.repeat((-np.exp(-((zv - z0) / w) ** 2))[:, None], nr + 1, 1)
+        vz[0] = vz[-1] = 0.0
+        s.set("rho0", rho)
+        s.set("vz", vz)
+    else:
+        rc = (np.arange(nr) + 0.5) * dx
+        r0, w = 0.4 * nr * dx, 10 * dx
+        rho = np.repeat((2700 * (1 + np.exp(-((rc - r0) / w) ** 2) / c))[None, :], nz, 0)
+        s.set("rho0", rho)
+    if pml:
+        M = rho * V[None, :]
+        if strip == "right":
+            dc = np.array([O.pml_profile(c, pml, dx, i + 0.5 - (nr - pml), 0.01) if i >= nr - pml else 0.0 for i in range(nr)])
+            dv = np.array([O.pml_profile(c, pml, dx, i - (nr - pml), 0.01) if i > nr - pml else 0.0 for i in range(nr + 1)])
+            mv = np.zeros((nz + 1, nr + 1))
+            for a, b in ((0, 0), (0, 1), (1, 0), (1, 1)):
+                mv[a:a + nz, b:b + nr] += 0.25 * M
+            s.set("phi1_r", -dc[None, :] * (M - 2700.0 * V[None, :]))
+            s.set("psi1z_r", -dv[None, :] * mv * vz)
+        else:
+            dc = np.array([O.pml_profile(c, pml, dx, pml - j - 0.5, 0.01) if j < pml else 0.0 for j in range(nz)])
+            s.set("phi1_b", -dc[:, None] * (M - 2700.0 * V[None, :]))
+    s.step(int(round(T * c / (cfl * dx))))
+    return s.get("vz" if strip == "right" else "vr")
+
+
+@pytest.mark.parametrize("strip", ["right", "bottom"])
+def test_tangential_wave_inside_strip_is_not_attenuated(strip):
+    devs = []
+    for cfl in (0.4, 0.2, 0.1):
+        ref = _tangential(strip, 0, cfl)
+        got = _tangential(strip, 24, cfl)
+        devs.append(np.abs(got - ref).max() / np.abs(ref).max())
+    assert 0.4 < devs[1] / devs[0] < 0.6 and 0.4 < devs[2] / devs[1] < 0.6   # first order in dt
+    assert devs[2] < 0.08
