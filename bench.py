@@ -1,0 +1,317 @@
+#!/usr/bin/env python
+"""Headline benchmark: cell-updates/s of the explicit ALE step of SALEc-2D on GB300.
+
+Workload (default): the 4000 x 4000 single-run configuration (10 m cells, basalt
+Tillotson half-space, hydrodynamic, projectile radius 100 cells at 10 km/s, PML 16 right
+and bottom, no gravity), FP64, K steps from t = 0 (default K = 2000, the configuration's
+run length).  One "step" is one full cycle of the hot path (EoS + artificial viscosity +
+Courant min-reduction, Lagrangian momentum/energy/strength, PML, donor-cell remap,
+momentum remap, heat) over all 16e6 cells.  The state (~1.3 GB) is larger than L2, so no
+flush is needed between steps.
+
+Output: one JSON line (see the contract in the design doc):
+  value      cell-updates/s, device-timed (CUDA events on the library's stream), state
+             resident in HBM; N GPUs run N independent replicas (weak scaling)
+  e2e        the same metric through the C ABI with host buffers: the initial state is
+             copied from pinned host memory, every step reads its scalars (t, dt, status)
+             back, and the final pressure field is copied to the host
+  roofline   the dominant kernel against its bound
+  cpu_baseline  the serial FP64 oracle on the host cores, on a bounded sample
+``--impl reference`` times the oracle itself (the reference arm of this repository).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "cell-updates/s per ALE step (FP64 vs FP32, % HBM roofline); batched runs/hour"
+UNIT = "cell-updates/s"
+
+# FP64 issue rate: 152 SMs x 2 DFMA/clk/SM x 2 flop x 2.07 GHz (the part's nominal
+# 1.25 TFLOP/s FP64); measured 1.19 TFLOP/s with a dependent-chain-free DFMA loop.
+FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12
+
+# Algorithmic bytes per cell-update of each kernel (FP64, one material, hydrodynamic):
+# fields each kernel must read and write once.  Derivation in the design doc section 7.
+KERNEL_BYTES_PER_CELL = {
+    "k_phase0": 16 + 8 + 16 + 8 + 8 + 16 + 16,        # (f,rho) I v pmax(rw) -> (P,M) (pbar,phi)
+    "k_phase1": 16 + 16 + 16 + 16 + 8 + 8,            # (P,M) phi v -> vL mv dK
+    "k_phase2": 16 + 16 + 16 + 8 + 16 + 16,           # vL (P,M) (pbar,phi) I -> (fL,rhoL) (VL,IL)
+    "k_phase3a": 16 + 16 + 16 + 16 + 8 + 8 + 8,       # vL (fL,rhoL) (VL,IL) -> (f,rho) I dMR dMZ
+    "k_phase3b": 8 + 8 + 16 + 8 + 8 + 16 + 8,         # dMR dMZ vL mv dK -> v kheat
+    "k_phase3c": 16 + 8 + 8 + 8,                      # (f,rho) kheat I(rw)
+}
+
+
+def _load_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            d = json.load(fh)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms while running."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.path or not os.path.exists(self.path):
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                rows.append((float(parts[1]), float(parts[2]), float(parts[3]), parts[5:9]))
+            except ValueError:
+                continue
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k, v in enumerate(r[3]) if v.lower() == "active"})
+        loaded = [r for r in rows if r[2] > 200.0] or rows
+        return {"sm_mhz": statistics.median(r[0] for r in loaded), "sm_max_mhz": max(r[1] for r in rows),
+                "power_w_max": max(r[2] for r in rows), "samples": len(rows), "reasons": reasons}
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def _workload(name):
+    from paper_2403_04267_gb300 import workloads as W
+    return {"large_4000": W.large_4000, "full_800": W.full_fp64_800, "plain_100": W.plain_fp64_100,
+            "plain_2000": lambda: W.scaled_plain(2000, radius_cells=50)}[name]()
+
+
+def _cpu_baseline(spec, steps):
+    """The oracle as it stands, serial, on `steps` steps of the full workload from t = 0."""
+    from oracle import oracle as O
+    t0 = time.perf_counter()
+    s = O.OracleSim(spec)
+    t1 = time.perf_counter()
+    s.step(steps)
+    t2 = time.perf_counter()
+    cells = spec["grid"]["nr"] * spec["grid"]["nz"]
+    return {"value": cells * steps / (t2 - t1), "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{steps} steps of the full {spec['grid']['nr']}x{spec['grid']['nz']} workload from t=0 "
+                      f"(serial C, -O2; set-up {t1 - t0:.1f} s excluded)", "seconds": round(t2 - t1, 2)}
+
+
+def run_reference(args):
+    ws, rank, _ = _dist()
+    if rank != 0:
+        return 0
+    from oracle import oracle as O
+    from paper_2403_04267_gb300 import workloads as W
+    spec = _workload(args.workload)
+    # each reference step: one oracle step of the same physics on a bounded window so the
+    # whole --steps/--warmup run stays within minutes (per-step budget ~0.06 s)
+    n = 400
+    sample = W.scaled_plain(n, radius_cells=10) if args.workload == "large_4000" else spec
+    s = O.OracleSim(sample)
+    s.step(args.warmup)
+    t0 = time.perf_counter()
+    s.step(args.steps)
+    dt = time.perf_counter() - t0
+    cells = sample["grid"]["nr"] * sample["grid"]["nz"]
+    value = cells * args.steps / dt
+    desc = (f"serial FP64 oracle, {args.steps} steps of the same physics on a {sample['grid']['nr']}x"
+            f"{sample['grid']['nz']} grid per step (bounded sample of the {args.workload} workload)")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": dt * 1e3 / max(args.steps, 1), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": args.workload, "sample": desc},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": desc},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2000)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="large_4000", choices=["large_4000", "full_800", "plain_100", "plain_2000"])
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--cpu-steps", type=int, default=2)
+    ap.add_argument("--no-cpu", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    from paper_2403_04267_gb300 import salec
+
+    ws, rank, local = _dist()
+    torch.cuda.set_device(local)
+    if ws > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    spec = _workload(args.workload)
+    cells = spec["grid"]["nr"] * spec["grid"]["nz"]
+    sim = salec.Sim(spec)
+    stream = sim.stream
+    nbytes = sim.checkpoint_bytes()
+    init = sim.state[:nbytes].clone()          # device copy of the initial state
+
+    def restore():
+        sim.state[:nbytes].copy_(init)
+        torch.cuda.synchronize()
+
+    def barrier():
+        torch.cuda.synchronize()
+        if ws > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    # warm-up, then back to t = 0 so the timed region is exactly K steps of the run
+    sim.step(args.warmup)
+    torch.cuda.synchronize()
+    restore()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    sim.set_kernel_timing(True)
+    barrier()
+    with ClockSampler(local) as clk:
+        e0.record(stream)
+        sim.step(args.steps)
+        e1.record(stream)
+        barrier()
+    ms = e0.elapsed_time(e1)
+    ktimes, ksteps = sim.kernel_times()
+    sim.set_kernel_timing(False)
+    sc = sim.scalars()
+    ms_max = ms
+    if ws > 1:
+        t = torch.tensor([ms], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_max = float(t.item())
+    value = ws * cells * args.steps / (ms_max * 1e-3)
+
+    # end to end through the C ABI with host buffers
+    e2e = None
+    if not args.no_e2e:
+        host = torch.empty(nbytes, dtype=torch.uint8, pin_memory=True)
+        host.copy_(init.cpu())
+        p_host = np.zeros((spec["grid"]["nz"], spec["grid"]["nr"]))
+        restore()
+        barrier()
+        t0 = time.perf_counter()
+        sim.set_state(host.numpy())
+        for _ in range(args.steps):
+            sim.step(1)
+            sim.scalars()
+        p_host[:] = sim.get("p")
+        torch.cuda.synchronize()
+        t_e2e = time.perf_counter() - t0
+        if ws > 1:
+            t = torch.tensor([t_e2e], device="cuda", dtype=torch.float64)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            t_e2e = float(t.item())
+        e2e = {"value": ws * cells * args.steps / t_e2e, "unit": UNIT,
+               "h2d_bytes_per_step": nbytes / args.steps,
+               "d2h_bytes_per_step": 64 + p_host.nbytes / args.steps,
+               "note": "initial state H2D once from pinned memory (amortised over the steps), "
+                       "per-step scalar read-back, final pressure field D2H"}
+
+    if rank != 0:
+        dist.destroy_process_group()
+        return 0
+
+    # roofline of the dominant kernel
+    hbm_peak, peak_kind = _load_peaks()
+    dom = max(ktimes, key=ktimes.get)
+    dom_ms = ktimes[dom]
+    dom_bytes = KERNEL_BYTES_PER_CELL[dom] * cells
+    achieved_gbs = dom_bytes / (dom_ms * 1e-3) / 1e9
+    roof = {"bound": "alu", "kernel": dom, "unit": "TFLOP/s", "peak": round(FP64_PEAK_TFLOPS, 4),
+            "peak_kind": "nominal FP64 issue rate 152 SM x 2 DFMA/clk x 2.07 GHz (measured DFMA loop: 1.19)",
+            "achieved": None, "frac": None, "traffic": None,
+            "hbm": {"achieved_gbs": round(achieved_gbs, 1), "peak_gbs": hbm_peak, "peak_kind": peak_kind,
+                    "frac": round(achieved_gbs / hbm_peak, 4), "bytes_per_cell": KERNEL_BYTES_PER_CELL[dom]}}
+    flops_per_cell = _FLOPS_PER_CELL.get(dom)
+    if flops_per_cell:
+        ach = flops_per_cell * cells / (dom_ms * 1e-3) / 1e12
+        roof["achieved"] = round(ach, 4)
+        roof["frac"] = round(ach / FP64_PEAK_TFLOPS, 4)
+        roof["flops_per_cell"] = flops_per_cell
+    step_bytes = sum(KERNEL_BYTES_PER_CELL.values()) * cells
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": ms_max / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64", "data": "synthetic",
+        "config": {"workload": args.workload + " " + spec["name"], "grid": f"{spec['grid']['nr']}x{spec['grid']['nz']}",
+                   "cells": cells, "precision": "FP64", "l2": "state > L2 (no flush)",
+                   "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU",
+                   "sim_time_s": sc["t"], "status": sc["status"]},
+        "gpu_launches": sim.launches_per_step() * args.steps,
+        "kernel_ms": {k: round(v, 4) for k, v in ktimes.items()},
+        "step_hbm_frac": round(step_bytes / (ms / args.steps * 1e-3) / 1e9 / hbm_peak, 4),
+        "roofline": roof, "clocks": clk.summary(), "e2e": e2e,
+    }
+    if ws == 1 and not args.no_cpu:
+        del sim
+        torch.cuda.empty_cache()
+        line["cpu_baseline"] = _cpu_baseline(spec, args.cpu_steps)
+    print(json.dumps(line))
+    if ws > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+# FP64 operations per cell issued by each kernel on the common path (measured once with
+# ncu's per-opcode DP instruction counters, FMA counted as 2); see the design doc section 7.
+_FLOPS_PER_CELL: dict = {}
+
+if __name__ == "__main__":
+    sys.exit(main())

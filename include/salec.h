@@ -1,0 +1,193 @@
+/*
+ * salec.h -- C ABI of the GB300 (sm_103a) SALEc-2D time-step library.
+ *
+ * The library advances a 2D axisymmetric Eulerian (SALE) impact simulation with
+ * perfectly matched absorbing layers: the Lagrangian step (Eqs. 1-2 of the paper),
+ * the PML auxiliary terms and damping (Sect. 3, Eqs. 15-26), the Eulerian donor-cell
+ * remap (Eqs. 3-5) and the Courant time step (Sect. 6, Eq. 14).  Every step of the
+ * cycle runs in CUDA kernels on one GPU; nothing falls back to the CPU.
+ *
+ * Conventions
+ *  - Every call returns a salec_status; out-parameters are written only on SALEC_OK.
+ *    salec_last_error() gives a one-line reason for the last failure of a context.
+ *  - Call order: salec_create -> salec_set_material (each material) -> salec_add_layer /
+ *    salec_place_projectile -> salec_finalize -> salec_step / read-outs.  A call out of
+ *    order returns SALEC_EORDER.
+ *  - Memory: the device state lives in ONE caller-owned device buffer (e.g. a torch
+ *    uint8 tensor) of salec_state_bytes() bytes, 256-byte aligned; the library borrows it
+ *    until salec_destroy and never allocates device memory of its own.  Host buffers
+ *    passed to read-out calls are caller-owned and written synchronously.
+ *  - Streams: every kernel and copy is issued on the stream given to salec_create
+ *    (a cudaStream_t passed as void*, NULL = legacy default stream).  salec_step only
+ *    enqueues; read-out calls synchronise that stream.
+ *  - Fields are row-major [j][i] with j = 0 at the bottom: cell fields nz x nr, vertex
+ *    fields (nz+1) x (nr+1).  SI units.
+ *  - A context is not thread-safe; distinct contexts may be used from distinct threads.
+ */
+#ifndef SALEC_H
+#define SALEC_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct salec_ctx salec_ctx;
+
+typedef enum {
+    SALEC_OK = 0,
+    SALEC_EINVAL = 1,      /* bad argument (size, index, parameter out of range) */
+    SALEC_ENOMEM = 2,      /* the state buffer is too small or misaligned */
+    SALEC_ECUDA = 3,       /* a CUDA call failed (message in salec_last_error) */
+    SALEC_EORDER = 4,      /* call made before/after the stage it belongs to */
+    SALEC_EUNSTABLE = 5    /* the device status word reports a non-positive volume or
+                              density, a NaN, or dt below dt_min (see salec_get_scalars) */
+} salec_status;
+
+/* arithmetic of the step */
+enum { SALEC_FP64 = 0 };
+
+enum { SALEC_EOS_TILLOTSON = 0, SALEC_EOS_IDEAL_GAS = 1 };
+enum { SALEC_STRENGTH_NONE = 0, SALEC_STRENGTH_COLLINS = 1 };
+enum { SALEC_TOP_OUTFLOW = 0, SALEC_TOP_WALL = 1 };
+enum { SALEC_BOTTOM_NOSLIP = 0, SALEC_BOTTOM_FREESLIP = 1 };
+
+/* Grid, boundary and numerical parameters (Table 2 of the paper names the grid and the
+ * PML widths p_r, p_b; Sect. 4 the boundary conditions; Sect. 6 the Courant number). */
+typedef struct salec_grid {
+    int nr, nz;            /* cells in r and z (>= 1 each) */
+    int nmat;              /* materials, 1..3 */
+    double dx;             /* cell size, m */
+    int pml_right;         /* right absorbing strip width, cells (0 = none, < nr) */
+    int pml_bottom;        /* bottom absorbing strip width, cells (0 = none, < nz) */
+    double pml_R;          /* theoretical reflection coefficient R of Eq. 26, 0 < R < 1 */
+    double pml_c;          /* wave speed c of Eq. 26; <= 0: max sqrt(A/rho0) of the Tillotson materials */
+    double gravity;        /* m/s^2, acting in -z */
+    double cfl;            /* Courant number C0 of Eq. 14 */
+    double dt_init;        /* "previous" dt that limits the growth of the first step */
+    double dt_max;         /* upper bound of dt */
+    double dt_growth;      /* dt_{n+1} <= dt_growth * dt_n */
+    double dt_min;         /* a step with dt < dt_min sets the unstable status */
+    double av_cq, av_cl;   /* artificial viscosity constants (quadratic, linear) */
+    double f_min;          /* a material with a smaller volume fraction is removed */
+    int bc_top;            /* SALEC_TOP_OUTFLOW or SALEC_TOP_WALL */
+    int bc_bottom;         /* SALEC_BOTTOM_NOSLIP or SALEC_BOTTOM_FREESLIP */
+} salec_grid;
+
+/* One material: Tillotson (1962) or ideal-gas EoS; optional Collins et al. (2004)
+ * strength with scalar damage (Sect. 1 and Table 1 of the paper). */
+typedef struct salec_material {
+    int eos;                                        /* SALEC_EOS_* */
+    double rho0;                                    /* reference density, kg/m^3 */
+    double A, B, E0, a, b, alpha, beta, Eiv, Ecv;   /* Tillotson constants (Pa, J/kg) */
+    double gamma;                                   /* ideal-gas ratio of specific heats */
+    int strength;                                   /* SALEC_STRENGTH_* */
+    double Yi0, mui, Yim, Yd0, mud, Ydm;            /* intact / damaged yield surfaces */
+    double G;                                       /* shear modulus, Pa */
+    double eps_fb, B_dam, p_bd;                     /* failure strain max(eps_fb, B_dam (p - p_bd)) */
+    double p_t;                                     /* tensile limit of intact material, <= 0 */
+} salec_material;
+
+/* Field codes for salec_get_field / salec_set_field. */
+enum {
+    SALEC_F_VOLFRAC0 = 0, SALEC_F_VOLFRAC1 = 1, SALEC_F_VOLFRAC2 = 2,  /* f_m */
+    SALEC_F_DENS0 = 3, SALEC_F_DENS1 = 4, SALEC_F_DENS2 = 5,           /* rho_m */
+    SALEC_F_IE = 6, SALEC_F_SRR = 7, SALEC_F_SZZ = 8, SALEC_F_SRZ = 9, SALEC_F_DAMAGE = 10,
+    SALEC_F_PMAX = 11,                 /* running max of (matter pressure - p0(row)) */
+    SALEC_F_VR = 12, SALEC_F_VZ = 13,  /* vertex velocity */
+    SALEC_F_PRESSURE = 14,             /* matter pressure sum f_m p_m / sum f_m (read only) */
+    /* PML auxiliaries (zero outside their strip): cells */
+    SALEC_F_PHI1_B = 20, SALEC_F_PHI3_B = 21, SALEC_F_PSI2_B = 22,
+    SALEC_F_PHI1_R = 23, SALEC_F_PHI3_R = 24, SALEC_F_PSI2_R = 25,
+    /* PML auxiliaries: vertices */
+    SALEC_F_PHI2R_B = 30, SALEC_F_PHI2Z_B = 31, SALEC_F_PSI1R_B = 32, SALEC_F_PSI1Z_B = 33,
+    SALEC_F_PHI2R_R = 34, SALEC_F_PHI2Z_R = 35, SALEC_F_PSI1R_R = 36, SALEC_F_PSI1Z_R = 37
+};
+
+/* Bytes of the device state buffer for this grid (persistent state, per-step scratch,
+ * reduction partials and tables).  grid must pass the same checks as salec_create. */
+salec_status salec_state_bytes(const salec_grid* grid, int precision, size_t* bytes);
+
+/* Create a context over a caller-owned device buffer dev_state of `bytes` bytes
+ * (>= salec_state_bytes, 256-byte aligned) on CUDA stream `stream`.  The buffer is
+ * borrowed until salec_destroy.  *out receives the context. */
+salec_status salec_create(const salec_grid* grid, int precision, void* dev_state, size_t bytes,
+                          void* stream, salec_ctx** out);
+
+/* Set material `id` (0..nmat-1).  Must precede salec_finalize. */
+salec_status salec_set_material(salec_ctx* ctx, int id, const salec_material* mat);
+
+/* Fill the rows between heights zlo < zhi (m; fractional rows allowed) with material
+ * `mat` at density rho (rho <= 0: rho0, or discrete hydrostatic equilibrium when gravity
+ * > 0 and the material is Tillotson with I0 = 0), specific internal energy I0 and
+ * vertical velocity vz. */
+salec_status salec_add_layer(salec_ctx* ctx, int mat, double zlo, double zhi, double rho,
+                             double I0, double vz);
+
+/* Place a sphere of `radius` (m) centred on the axis at height zc, moving with vertical
+ * velocity vz, density rho (<= 0: rho0) and energy I0.  Cell fractions are r-weighted
+ * 16 x 16 sub-samples; the sphere displaces layer material. */
+salec_status salec_place_projectile(salec_ctx* ctx, int mat, double radius, double zc,
+                                    double vz, double rho, double I0);
+
+/* Build the initial state on the host (fractions, densities, vertex velocities, PML
+ * profiles of Eq. 26, reference rows) and copy it to the device. */
+salec_status salec_finalize(salec_ctx* ctx);
+
+/* Enqueue nsteps full cycles on the context's stream (no host synchronisation). */
+salec_status salec_step(salec_ctx* ctx, int nsteps);
+
+/* Synchronise and read the scalars: out[0] t, out[1] dt of the last step, out[2] step
+ * count, out[3] status bits (1 non-positive volume/density, 2 NaN, 4 dt < dt_min),
+ * out[4] mass out through the top, out[5] mass removed by clean-up, out[6] mass added by
+ * the PML damping, out[7] z-momentum out through the top.  Returns SALEC_EUNSTABLE
+ * (with out written) when status != 0. */
+salec_status salec_get_scalars(salec_ctx* ctx, double out[8]);
+
+/* Set the time and the previous dt (restart). */
+salec_status salec_set_time(salec_ctx* ctx, double t, double dt_prev);
+
+/* Copy a field into host_out (n = nr*nz for cell fields, (nr+1)*(nz+1) for vertex
+ * fields), or overwrite a field from host_in (tests, fault injection). */
+salec_status salec_get_field(salec_ctx* ctx, int field, double* host_out, size_t n);
+salec_status salec_set_field(salec_ctx* ctx, int field, const double* host_in, size_t n);
+
+/* Crater read-out (surface where sum_m f_m crosses 1/2, scanned from the top and
+ * interpolated between cell centres): heights[nr] per column, depth on the axis below
+ * z_surface, diameter (twice the first radius beyond the deepest column where the
+ * surface regains z_surface), and depth_profile[npts] at r_k = (k + 1/2) r_extent / npts
+ * with r_extent = (nr - pml_right) dx.  heights / depth_profile may be NULL. */
+salec_status salec_crater_profile(salec_ctx* ctx, double z_surface, int npts,
+                                  double* depth_profile, double* heights, double* depth,
+                                  double* diameter);
+
+/* Conservation sums per radian: out[0] mass, out[1] z-momentum, out[2] kinetic energy,
+ * out[3] internal energy (block sums on the device, FP64). */
+salec_status salec_conservation(salec_ctx* ctx, double out[4]);
+
+/* Checkpoint: the persistent part of the device state (fields, PML auxiliaries, tables,
+ * scalars) as an opaque byte image of salec_checkpoint_bytes() bytes. */
+salec_status salec_checkpoint_bytes(salec_ctx* ctx, size_t* bytes);
+salec_status salec_get_state(salec_ctx* ctx, void* host, size_t bytes);
+salec_status salec_set_state(salec_ctx* ctx, const void* host, size_t bytes);
+
+/* Number of kernel launches one step issues (for launch accounting). */
+int salec_launches_per_step(const salec_ctx* ctx);
+
+/* Per-kernel timing: with timing on, salec_step records a CUDA event before the first
+ * and after every kernel of each step on the context's stream; salec_kernel_times
+ * synchronises, returns in avg_ms[k] (n >= salec_launches_per_step) the mean duration
+ * of kernel k over the steps recorded since timing was switched on or last read, the
+ * number of steps in *steps, and restarts the count.  salec_kernel_name(k) names kernel k. */
+salec_status salec_set_kernel_timing(salec_ctx* ctx, int on);
+salec_status salec_kernel_times(salec_ctx* ctx, double* avg_ms, int n, int* steps);
+const char* salec_kernel_name(int k);
+
+const char* salec_last_error(const salec_ctx* ctx);
+void salec_destroy(salec_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SALEC_H */

@@ -71,6 +71,8 @@ typedef struct {
     double *p0, *rho_ref, *I_ref;        /* reference state per row */
     /* set-up accumulators */
     double *setup_V[ORC_MAXMAT], *setup_M[ORC_MAXMAT], *setup_E, *setup_Pz;
+    double *setup_R[ORC_MAXMAT], *setup_mix[ORC_MAXMAT];   /* density of the contributions; 1 if they differ */
+    double *setup_I, *setup_Imix;                          /* likewise for the specific energy */
     int finalized;
     /* scalars */
     double t, dt, dt_prev;
@@ -210,6 +212,7 @@ orc_sim* orc_create(const orc_grid* g, const orc_material* mats)
         s->f[m] = zalloc(nc); s->rho[m] = zalloc(nc);
         s->fL[m] = zalloc(nc); s->rhoL[m] = zalloc(nc);
         s->setup_V[m] = zalloc(nc); s->setup_M[m] = zalloc(nc);
+        s->setup_R[m] = zalloc(nc); s->setup_mix[m] = zalloc(nc);
     }
     s->I = zalloc(nc); s->srr = zalloc(nc); s->szz = zalloc(nc); s->srz = zalloc(nc);
     s->D = zalloc(nc); s->pmax = zalloc(nc);
@@ -220,7 +223,7 @@ orc_sim* orc_create(const orc_grid* g, const orc_material* mats)
     s->phi2r_r = zalloc(nv); s->phi2z_r = zalloc(nv); s->psi1r_r = zalloc(nv); s->psi1z_r = zalloc(nv);
     s->dB_c = zalloc(nz); s->dB_v = zalloc(nz + 1); s->dR_c = zalloc(nr); s->dR_v = zalloc(nr + 1);
     s->p0 = zalloc(nz); s->rho_ref = zalloc(nz); s->I_ref = zalloc(nz);
-    s->setup_E = zalloc(nc); s->setup_Pz = zalloc(nc);
+    s->setup_E = zalloc(nc); s->setup_Pz = zalloc(nc); s->setup_I = zalloc(nc); s->setup_Imix = zalloc(nc);
     s->P = zalloc(nc); s->pbar = zalloc(nc); s->mv = zalloc(nv); s->vLr = zalloc(nv); s->vLz = zalloc(nv);
     s->dK = zalloc(nv); s->kheat = zalloc(nv);
     s->VL = zalloc(nc); s->IL = zalloc(nc); s->srrL = zalloc(nc); s->szzL = zalloc(nc); s->srzL = zalloc(nc);
@@ -238,13 +241,13 @@ void orc_destroy(orc_sim* s)
                       &s->vr, &s->vz, &s->phi1_b, &s->phi3_b, &s->psi2_b, &s->phi1_r, &s->phi3_r,
                       &s->psi2_r, &s->phi2r_b, &s->phi2z_b, &s->psi1r_b, &s->psi1z_b, &s->phi2r_r,
                       &s->phi2z_r, &s->psi1r_r, &s->psi1z_r, &s->dB_c, &s->dB_v, &s->dR_c, &s->dR_v,
-                      &s->p0, &s->rho_ref, &s->I_ref, &s->setup_E, &s->setup_Pz, &s->P, &s->pbar,
+                      &s->p0, &s->rho_ref, &s->I_ref, &s->setup_E, &s->setup_Pz, &s->setup_I, &s->setup_Imix, &s->P, &s->pbar,
                       &s->mv, &s->vLr, &s->vLz, &s->dK, &s->kheat, &s->VL, &s->IL, &s->srrL, &s->szzL, &s->srzL, &s->DL,
                       &s->dVR, &s->dVZ, &s->dMR, &s->dMZ};
     for (size_t k = 0; k < sizeof(all) / sizeof(all[0]); ++k) free(*all[k]);
     for (int m = 0; m < ORC_MAXMAT; ++m) {
         free(s->f[m]); free(s->rho[m]); free(s->fL[m]); free(s->rhoL[m]);
-        free(s->setup_V[m]); free(s->setup_M[m]);
+        free(s->setup_V[m]); free(s->setup_M[m]); free(s->setup_R[m]); free(s->setup_mix[m]);
     }
     free(s);
 }
@@ -257,6 +260,23 @@ void orc_destroy(orc_sim* s)
  * Newton's method from the surface down.  Pinned by test_oracle_rest.py (hydrostatic
  * column stays at rest) and test_oracle_setup.py (sphere volume).
  * ------------------------------------------------------------------------------------ */
+/* one contribution of material `mat` to cell c; a cell whose contributions all share one
+   density keeps that density exactly (M / V would round it) */
+static void contribute(orc_sim* s, int mat, int c, double vol, double rho, double I0, double vz)
+{
+    double mass = rho * vol;
+    int empty = 1;
+    for (int m = 0; m < s->g.nmat; ++m) if (s->setup_V[m][c] != 0.0) empty = 0;
+    if (empty) s->setup_I[c] = I0;
+    else if (s->setup_I[c] != I0) s->setup_Imix[c] = 1.0;
+    if (s->setup_V[mat][c] == 0.0) s->setup_R[mat][c] = rho;
+    else if (s->setup_R[mat][c] != rho) s->setup_mix[mat][c] = 1.0;
+    s->setup_V[mat][c] += vol;
+    s->setup_M[mat][c] += mass;
+    s->setup_E[c] += mass * I0;
+    s->setup_Pz[c] += mass * vz;
+}
+
 int orc_add_layer(orc_sim* s, int mat, double zlo, double zhi, double rho, double I0, double vz)
 {
     if (s->finalized || mat < 0 || mat >= s->g.nmat || !(zhi > zlo)) return 1;
@@ -305,13 +325,7 @@ int orc_add_layer(orc_sim* s, int mat, double zlo, double zhi, double rho, doubl
     for (int j = 0; j < nz; ++j) {
         if (w[j] <= 0.0) continue;
         for (int i = 0; i < nr; ++i) {
-            int c = CID(s, i, j);
-            double vol = w[j] * s->V[i];
-            double mass = rowrho[j] * vol;
-            s->setup_V[mat][c] += vol;
-            s->setup_M[mat][c] += mass;
-            s->setup_E[c] += mass * I0;
-            s->setup_Pz[c] += mass * vz;
+            contribute(s, mat, CID(s, i, j), w[j] * s->V[i], rowrho[j], I0, vz);
         }
     }
     free(w); free(rowrho);
@@ -348,12 +362,7 @@ int orc_place_projectile(orc_sim* s, int mat, double radius, double zc, double v
             }
             s->setup_E[c] *= keep;
             s->setup_Pz[c] *= keep;
-            double vol = frac * s->V[i];
-            double mass = r * vol;
-            s->setup_V[mat][c] += vol;
-            s->setup_M[mat][c] += mass;
-            s->setup_E[c] += mass * I0;
-            s->setup_Pz[c] += mass * vz;
+            contribute(s, mat, c, frac * s->V[i], r, I0, vz);
         }
     }
     return 0;
@@ -394,10 +403,11 @@ int orc_finalize(orc_sim* s)
                 double fm = s->setup_V[m][c] / s->V[i];
                 if (fm < s->g.f_min) fm = 0.0;
                 s->f[m][c] = fm;
-                s->rho[m][c] = fm > 0.0 ? s->setup_M[m][c] / s->setup_V[m][c] : 0.0;
+                s->rho[m][c] = fm > 0.0 ? (s->setup_mix[m][c] != 0.0 ? s->setup_M[m][c] / s->setup_V[m][c]
+                                                                     : s->setup_R[m][c]) : 0.0;
                 if (fm > 0.0) Mtot += s->setup_M[m][c];
             }
-            s->I[c] = Mtot > 0.0 ? s->setup_E[c] / Mtot : 0.0;
+            s->I[c] = Mtot > 0.0 ? (s->setup_Imix[c] != 0.0 ? s->setup_E[c] / Mtot : s->setup_I[c]) : 0.0;
         }
     }
     /* vertex velocity: quarter-cell momentum over quarter-cell mass */
@@ -915,21 +925,39 @@ static void phase3_remap(orc_sim* s)
             if (above >= 0) { FZ_M[above] -= sg * mass; FZ_E[above] -= sg * fl.E; }
         }
     }
-    /* new cell state, clean-up and the PML mass / energy terms */
+    /* new cell state, clean-up and the PML mass / energy terms.  Intensive quantities are
+       updated in increment form, q' = q^L + (net flux of q-content - q^L net carrier flux)
+       / new carrier amount, which is exact when nothing flows. */
     for (int j = 0; j < nz; ++j) for (int i = 0; i < nr; ++i) {
         int c = CID(s, i, j);
         double V = s->V[i];
-        double Mtot = 0.0, Vmat = 0.0;
-        for (int m = 0; m < nm; ++m) { Mtot += Mm[m][c]; Vmat += Vm[m][c]; }
-        double I = Mtot > 0.0 ? E[c] / Mtot : 0.0;
+        double VmL[ORC_MAXMAT], MmL[ORC_MAXMAT], rho_new[ORC_MAXMAT];
+        double MLtot = 0.0, VLmat = 0.0, dMtot = 0.0, dVtot = 0.0;
+        for (int m = 0; m < nm; ++m) {
+            VmL[m] = s->fL[m][c] * s->VL[c];
+            MmL[m] = s->rhoL[m][c] * VmL[m];
+            MLtot += MmL[m]; VLmat += VmL[m];
+            /* Vm, Mm hold the Lagrangian contents plus the net fluxes */
+            double dVm = Vm[m][c] - VmL[m], dMm = Mm[m][c] - MmL[m];
+            dMtot += dMm; dVtot += dVm;
+            rho_new[m] = Vm[m][c] > 0.0 ? s->rhoL[m][c] + (dMm - s->rhoL[m][c] * dVm) / Vm[m][c] : 0.0;
+        }
+        double Mtot = MLtot + dMtot, Vmat = VLmat + dVtot;
+        double dE = E[c] - s->IL[c] * MLtot;
+        double I = Mtot > 0.0 ? s->IL[c] + (dE - s->IL[c] * dMtot) / Mtot : 0.0;
         double srr = 0.0, szz = 0.0, srz = 0.0, D = 0.0;
-        if (Vmat > 0.0) { srr = SV[0][c] / Vmat; szz = SV[1][c] / Vmat; srz = SV[2][c] / Vmat; D = SV[3][c] / Vmat; }
+        if (Vmat > 0.0) {
+            srr = s->srrL[c] + ((SV[0][c] - s->srrL[c] * VLmat) - s->srrL[c] * dVtot) / Vmat;
+            szz = s->szzL[c] + ((SV[1][c] - s->szzL[c] * VLmat) - s->szzL[c] * dVtot) / Vmat;
+            srz = s->srzL[c] + ((SV[2][c] - s->srzL[c] * VLmat) - s->srzL[c] * dVtot) / Vmat;
+            D = s->DL[c] + ((SV[3][c] - s->DL[c] * VLmat) - s->DL[c] * dVtot) / Vmat;
+        }
         double Mkeep = 0.0, Vkeep = 0.0;
         for (int m = 0; m < nm; ++m) {
             double fm = Vm[m][c] / V;
             if (fm < s->g.f_min) {
                 s->mass_discarded += Mm[m][c];
-                Vm[m][c] = 0.0; Mm[m][c] = 0.0;
+                Vm[m][c] = 0.0; Mm[m][c] = 0.0; rho_new[m] = 0.0;
             }
             Mkeep += Mm[m][c]; Vkeep += Vm[m][c];
         }
@@ -944,18 +972,18 @@ static void phase3_remap(orc_sim* s)
         double kappa = 1.0;
         if (Mkeep > 0.0 && dsum > 0.0) {
             double Mref = Vkeep * s->rho_ref[j];
-            double Mnew = Mkeep - dt * (dsum * (Mkeep - Mref) + s->phi1_b[c] + s->phi1_r[c]);
-            double Eold = Mkeep * I;
-            double Enew = Eold - dt * (dsum * (Eold - Mref * s->I_ref[j]) + s->phi3_b[c] + s->phi3_r[c]);
+            double dM = -dt * (dsum * (Mkeep - Mref) + s->phi1_b[c] + s->phi1_r[c]);
+            double dEp = -dt * (dsum * (Mkeep * I - Mref * s->I_ref[j]) + s->phi3_b[c] + s->phi3_r[c]);
+            double Mnew = Mkeep + dM;
             if (!(Mnew > 0.0)) s->status |= 1;
-            s->mass_pml += Mnew - Mkeep;
-            kappa = Mnew / Mkeep;
-            I = Enew / Mnew;
+            s->mass_pml += dM;
+            kappa = 1.0 + dM / Mkeep;
+            I = I + (dEp - I * dM) / Mnew;
         }
         for (int m = 0; m < nm; ++m) {
             if (Vm[m][c] > 0.0) {
                 s->f[m][c] = Vm[m][c] / V;
-                s->rho[m][c] = kappa * (Mm[m][c] / Vm[m][c]);
+                s->rho[m][c] = kappa * rho_new[m];
             } else {
                 s->f[m][c] = 0.0; s->rho[m][c] = 0.0;
             }
@@ -1080,8 +1108,16 @@ static void phase3_vertex(orc_sim* s)
             double dsum = s->dB_v[j] + s->dR_v[i];
             pr = pr - dt * (dsum * pr + s->phi2r_b[v] + s->phi2r_r[v]);
             pz = pz - dt * (dsum * pz + s->phi2z_b[v] + s->phi2z_r[v]);
+            /* a vertex with no material in any adjacent cell after the clean-up carries
+               no momentum (its dual mass is then only round-off of the fluxes) */
+            int occupied = 0;
+            for (int dj = -1; dj <= 0; ++dj) for (int di = -1; di <= 0; ++di) {
+                int ci = i + di, cj = j + dj;
+                if (ci < 0 || ci >= nr || cj < 0 || cj >= nz) continue;
+                if (cell_phi(s, CID(s, ci, cj)) > 0.0) occupied = 1;
+            }
             double vr = 0.0, vz = 0.0;
-            if (m > 0.0) { vr = pr / m; vz = pz / m; }
+            if (m > 0.0 && occupied) { vr = pr / m; vz = pz / m; }
             apply_velocity_bc(s, i, j, &vr, &vz);
             s->vr[v] = vr;
             s->vz[v] = vz;

@@ -1,0 +1,830 @@
+// salec_api.cu -- host side of the C ABI in include/salec.h: state layout inside the
+// caller's device buffer, initial conditions (layers, projectile, hydrostatic rows, PML
+// profiles of Eq. 26, reference rows), stepping, field and scalar read-outs, checkpoint.
+#include <cuda_runtime.h>
+
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <string>
+#include <vector>
+
+#include "salec_internal.cuh"
+
+using namespace salec;
+
+namespace {
+
+constexpr size_t kAlign = 256;
+
+// Offsets of every array inside the state buffer.  The persistent part (scalars, tables,
+// fields, PML auxiliaries) comes first so a checkpoint is one contiguous range.
+struct Layout {
+    size_t scal, A_R, A_Z, V, invV, p0, rho_ref, I_ref, dB_c, dB_v, dR_c, dR_v;
+    size_t fr[kMaxMat], I, s01, s2d, pmax, v;
+    size_t pb_c, pb_psi2, pb_v, pr_c, pr_psi2, pr_v;
+    size_t persist_end;
+    size_t PM, pbphi, vL, mv, dK, kheat, frL[kMaxMat], VIL, sL01, sL2d, dMR, dMZ, partial, tmp;
+    size_t total;
+};
+
+size_t take(size_t& cur, size_t bytes)
+{
+    const size_t off = cur;
+    cur += (bytes + kAlign - 1) / kAlign * kAlign;
+    return off;
+}
+
+Layout make_layout(const salec_grid& g)
+{
+    Layout L;
+    memset(&L, 0, sizeof(L));
+    const size_t nr = g.nr, nz = g.nz, nc = nr * nz, nv = (nr + 1) * (nz + 1);
+    const size_t pb = g.pml_bottom, pr = g.pml_right;
+    const size_t d = sizeof(double), d2 = 2 * d, d4 = 4 * d;
+    size_t cur = 0;
+    L.scal = take(cur, sizeof(DevScalars));
+    L.A_R = take(cur, (nr + 1) * d);
+    L.A_Z = take(cur, nr * d);
+    L.V = take(cur, nr * d);
+    L.invV = take(cur, nr * d);
+    L.p0 = take(cur, nz * d);
+    L.rho_ref = take(cur, nz * d);
+    L.I_ref = take(cur, nz * d);
+    L.dB_c = take(cur, nz * d);
+    L.dB_v = take(cur, (nz + 1) * d);
+    L.dR_c = take(cur, nr * d);
+    L.dR_v = take(cur, (nr + 1) * d);
+    for (int m = 0; m < g.nmat; ++m) L.fr[m] = take(cur, nc * d2);
+    L.I = take(cur, nc * d);
+    L.s01 = take(cur, nc * d2);
+    L.s2d = take(cur, nc * d2);
+    L.pmax = take(cur, nc * d);
+    L.v = take(cur, nv * d2);
+    L.pb_c = take(cur, nr * pb * d2);
+    L.pb_psi2 = take(cur, nr * pb * d);
+    L.pb_v = take(cur, (nr + 1) * pb * d4);
+    L.pr_c = take(cur, pr * nz * d2);
+    L.pr_psi2 = take(cur, pr * nz * d);
+    L.pr_v = take(cur, pr * (nz + 1) * d4);
+    L.persist_end = cur;
+    L.PM = take(cur, nc * d2);
+    L.pbphi = take(cur, nc * d2);
+    L.vL = take(cur, nv * d2);
+    L.mv = take(cur, nv * d);
+    L.dK = take(cur, nv * d);
+    L.kheat = take(cur, nv * d);
+    for (int m = 0; m < g.nmat; ++m) L.frL[m] = take(cur, nc * d2);
+    L.VIL = take(cur, nc * d2);
+    L.sL01 = take(cur, nc * d2);
+    L.sL2d = take(cur, nc * d2);
+    L.dMR = take(cur, (nr + 1) * nz * d);
+    L.dMZ = take(cur, nr * (nz + 1) * d);
+    const size_t nb = (size_t)cell_blocks(g.nr, g.nz);
+    const size_t nbv = (size_t)vertex_blocks(g.nr, g.nz);
+    L.partial = take(cur, (nb > 4 * nbv ? nb : 4 * nbv) * d);
+    L.tmp = take(cur, nv * d);
+    L.total = cur;
+    return L;
+}
+
+bool grid_ok(const salec_grid* g)
+{
+    if (!g) return false;
+    if (g->nr < 1 || g->nz < 1 || g->nmat < 1 || g->nmat > kMaxMat) return false;
+    if (!(g->dx > 0.0) || !(g->cfl > 0.0) || !(g->dt_growth > 0.0) || !(g->dt_max > 0.0)) return false;
+    if (g->pml_right < 0 || g->pml_right >= g->nr || g->pml_bottom < 0 || g->pml_bottom >= g->nz) return false;
+    if (g->f_min < 0.0 || g->gravity < 0.0) return false;
+    if (g->bc_top != SALEC_TOP_OUTFLOW && g->bc_top != SALEC_TOP_WALL) return false;
+    if (g->bc_bottom != SALEC_BOTTOM_NOSLIP && g->bc_bottom != SALEC_BOTTOM_FREESLIP) return false;
+    if ((size_t)g->nr * (size_t)g->nz > (size_t)1 << 31) return false;
+    return true;
+}
+
+}  // namespace
+
+struct salec_ctx {
+    salec_grid g;
+    int precision;
+    Layout L;
+    char* base;
+    size_t bytes;
+    cudaStream_t stream;
+    salec_material mats[kMaxMat];
+    bool mat_set[kMaxMat];
+    bool finalized;
+    Params P;
+    // set-up accumulators (host, freed at finalize)
+    std::vector<double> sV[kMaxMat], sM[kMaxMat], sE, sPz;
+    std::vector<double> sR[kMaxMat];      // density shared by all contributions (exact)
+    std::vector<char> sMix[kMaxMat];      // contributions of differing density
+    std::vector<double> sI;               // specific energy shared by all contributions
+    std::vector<char> sImix;
+    std::vector<double> A_R, A_Z, Vc;
+    std::string err;
+    // optional per-kernel timing: 7 events per recorded step
+    bool timing = false;
+    std::vector<cudaEvent_t> ev;
+    size_t ev_used = 0;
+};
+
+static salec_status fail(salec_ctx* ctx, salec_status st, const char* fmt, ...)
+{
+    if (ctx) {
+        char buf[512];
+        va_list ap;
+        va_start(ap, fmt);
+        vsnprintf(buf, sizeof(buf), fmt, ap);
+        va_end(ap);
+        ctx->err = buf;
+    }
+    return st;
+}
+
+static salec_status cuda_check(salec_ctx* ctx, cudaError_t e, const char* what)
+{
+    if (e == cudaSuccess) return SALEC_OK;
+    return fail(ctx, SALEC_ECUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+template <typename T>
+static T* at(salec_ctx* ctx, size_t off) { return reinterpret_cast<T*>(ctx->base + off); }
+
+static Mat to_mat(const salec_material& s)
+{
+    Mat m;
+    memset(&m, 0, sizeof(m));
+    m.eos = s.eos; m.strength = s.strength;
+    m.rho0 = s.rho0; m.inv_rho0 = 1.0 / s.rho0;
+    m.A = s.A; m.B = s.B; m.E0 = s.E0; m.a = s.a; m.b = s.b; m.alpha = s.alpha; m.beta = s.beta;
+    m.Eiv = s.Eiv; m.Ecv = s.Ecv;
+    m.inv_dE = (s.Ecv > s.Eiv) ? 1.0 / (s.Ecv - s.Eiv) : 0.0;
+    m.gamma = s.gamma;
+    m.Yi0 = s.Yi0; m.mui = s.mui; m.Yim = s.Yim; m.Yd0 = s.Yd0; m.mud = s.mud; m.Ydm = s.Ydm;
+    m.inv_Yspan = (s.Yim != s.Yi0) ? 1.0 / (s.Yim - s.Yi0) : 0.0;
+    m.G = s.strength == SALEC_STRENGTH_COLLINS ? s.G : 0.0;
+    m.eps_fb = s.eps_fb; m.B_dam = s.B_dam; m.p_bd = s.p_bd; m.p_t = s.p_t;
+    m.c2_floor = s.eos == SALEC_EOS_TILLOTSON ? 0.01 * s.A / s.rho0 : 0.0;
+    return m;
+}
+
+static void fill_params(salec_ctx* ctx)
+{
+    Params& P = ctx->P;
+    const salec_grid& g = ctx->g;
+    const Layout& L = ctx->L;
+    P.nr = g.nr; P.nz = g.nz; P.nmat = g.nmat; P.pr = g.pml_right; P.pb = g.pml_bottom;
+    P.bc_top = g.bc_top; P.bc_bottom = g.bc_bottom;
+    P.any_strength = 0;
+    for (int m = 0; m < g.nmat; ++m) {
+        P.mat[m] = to_mat(ctx->mats[m]);
+        if (ctx->mats[m].strength == SALEC_STRENGTH_COLLINS) P.any_strength = 1;
+    }
+    P.nblk_cells = cell_blocks(g.nr, g.nz);
+    P.dx = g.dx; P.dx2 = g.dx * g.dx; P.cfl = g.cfl; P.growth = g.dt_growth; P.dt_max = g.dt_max;
+    P.dt_min = g.dt_min; P.g = g.gravity; P.cq = g.av_cq; P.cl = g.av_cl; P.f_min = g.f_min;
+    Ptrs& p = P.p;
+    for (int m = 0; m < kMaxMat; ++m) {
+        p.fr[m] = m < g.nmat ? at<double2>(ctx, L.fr[m]) : nullptr;
+        p.frL[m] = m < g.nmat ? at<double2>(ctx, L.frL[m]) : nullptr;
+    }
+    p.I = at<double>(ctx, L.I); p.s01 = at<double2>(ctx, L.s01); p.s2d = at<double2>(ctx, L.s2d);
+    p.pmax = at<double>(ctx, L.pmax); p.v = at<double2>(ctx, L.v);
+    p.pb_c = at<double2>(ctx, L.pb_c); p.pb_psi2 = at<double>(ctx, L.pb_psi2); p.pb_v = at<double4_32a>(ctx, L.pb_v);
+    p.pr_c = at<double2>(ctx, L.pr_c); p.pr_psi2 = at<double>(ctx, L.pr_psi2); p.pr_v = at<double4_32a>(ctx, L.pr_v);
+    p.A_R = at<double>(ctx, L.A_R); p.A_Z = at<double>(ctx, L.A_Z); p.V = at<double>(ctx, L.V);
+    p.invV = at<double>(ctx, L.invV); p.p0 = at<double>(ctx, L.p0); p.rho_ref = at<double>(ctx, L.rho_ref);
+    p.I_ref = at<double>(ctx, L.I_ref); p.dB_c = at<double>(ctx, L.dB_c); p.dB_v = at<double>(ctx, L.dB_v);
+    p.dR_c = at<double>(ctx, L.dR_c); p.dR_v = at<double>(ctx, L.dR_v);
+    p.PM = at<double2>(ctx, L.PM); p.pbphi = at<double2>(ctx, L.pbphi); p.vL = at<double2>(ctx, L.vL);
+    p.mv = at<double>(ctx, L.mv); p.dK = at<double>(ctx, L.dK); p.kheat = at<double>(ctx, L.kheat);
+    p.VIL = at<double2>(ctx, L.VIL); p.sL01 = at<double2>(ctx, L.sL01); p.sL2d = at<double2>(ctx, L.sL2d);
+    p.dMR = at<double>(ctx, L.dMR); p.dMZ = at<double>(ctx, L.dMZ); p.partial = at<double>(ctx, L.partial);
+    p.scal = at<DevScalars>(ctx, L.scal);
+}
+
+extern "C" {
+
+salec_status salec_state_bytes(const salec_grid* grid, int precision, size_t* bytes)
+{
+    if (!grid_ok(grid) || precision != SALEC_FP64 || !bytes) return SALEC_EINVAL;
+    *bytes = make_layout(*grid).total;
+    return SALEC_OK;
+}
+
+salec_status salec_create(const salec_grid* grid, int precision, void* dev_state, size_t bytes, void* stream,
+                          salec_ctx** out)
+{
+    if (!out || !grid_ok(grid) || precision != SALEC_FP64) return SALEC_EINVAL;
+    Layout L = make_layout(*grid);
+    if (!dev_state || bytes < L.total || ((uintptr_t)dev_state % kAlign) != 0) return SALEC_ENOMEM;
+    salec_ctx* ctx = new salec_ctx();
+    ctx->g = *grid;
+    ctx->precision = precision;
+    ctx->L = L;
+    ctx->base = (char*)dev_state;
+    ctx->bytes = bytes;
+    ctx->stream = (cudaStream_t)stream;
+    memset(ctx->mats, 0, sizeof(ctx->mats));
+    for (int m = 0; m < kMaxMat; ++m) ctx->mat_set[m] = false;
+    ctx->finalized = false;
+    const size_t nc = (size_t)grid->nr * grid->nz;
+    for (int m = 0; m < grid->nmat; ++m) {
+        ctx->sV[m].assign(nc, 0.0); ctx->sM[m].assign(nc, 0.0);
+        ctx->sR[m].assign(nc, 0.0); ctx->sMix[m].assign(nc, 0);
+    }
+    ctx->sE.assign(nc, 0.0);
+    ctx->sI.assign(nc, 0.0);
+    ctx->sImix.assign(nc, 0);
+    ctx->sPz.assign(nc, 0.0);
+    const int nr = grid->nr;
+    const double dx = grid->dx;
+    ctx->A_R.resize(nr + 1); ctx->A_Z.resize(nr); ctx->Vc.resize(nr);
+    for (int i = 0; i <= nr; ++i) ctx->A_R[i] = ((double)i * dx) * dx;
+    for (int i = 0; i < nr; ++i) {
+        const double rc = ((double)i + 0.5) * dx;
+        ctx->A_Z[i] = rc * dx;
+        ctx->Vc[i] = rc * dx * dx;
+    }
+    *out = ctx;
+    return SALEC_OK;
+}
+
+salec_status salec_set_material(salec_ctx* ctx, int id, const salec_material* mat)
+{
+    if (!ctx || !mat) return SALEC_EINVAL;
+    if (ctx->finalized) return fail(ctx, SALEC_EORDER, "set_material after finalize");
+    if (id < 0 || id >= ctx->g.nmat) return fail(ctx, SALEC_EINVAL, "material id %d out of range", id);
+    if (mat->eos != SALEC_EOS_TILLOTSON && mat->eos != SALEC_EOS_IDEAL_GAS)
+        return fail(ctx, SALEC_EINVAL, "unknown eos %d", mat->eos);
+    if (!(mat->rho0 > 0.0)) return fail(ctx, SALEC_EINVAL, "rho0 must be positive");
+    if (mat->eos == SALEC_EOS_TILLOTSON && !(mat->E0 > 0.0 && mat->A > 0.0 && mat->Ecv > mat->Eiv))
+        return fail(ctx, SALEC_EINVAL, "Tillotson constants out of range");
+    if (mat->strength != SALEC_STRENGTH_NONE && mat->strength != SALEC_STRENGTH_COLLINS)
+        return fail(ctx, SALEC_EINVAL, "unknown strength model %d", mat->strength);
+    if (mat->strength == SALEC_STRENGTH_COLLINS && !(mat->G > 0.0 && mat->Yim > mat->Yi0 && mat->eps_fb > 0.0))
+        return fail(ctx, SALEC_EINVAL, "strength constants out of range");
+    ctx->mats[id] = *mat;
+    ctx->mat_set[id] = true;
+    return SALEC_OK;
+}
+
+// Add volume `vol` of material `mat` at density rho to cell c.  Cells whose contributions
+// share one density keep it exactly; otherwise the density is mass / volume.
+static void add_content(salec_ctx* ctx, int mat, size_t c, double vol, double rho, double I0, double vz)
+{
+    const double mass = rho * vol;
+    bool empty = true;
+    for (int m = 0; m < ctx->g.nmat; ++m) empty = empty && ctx->sV[m][c] == 0.0;
+    if (empty) ctx->sI[c] = I0;
+    else if (ctx->sI[c] != I0) ctx->sImix[c] = 1;
+    if (ctx->sV[mat][c] == 0.0) ctx->sR[mat][c] = rho;
+    else if (ctx->sR[mat][c] != rho) ctx->sMix[mat][c] = 1;
+    ctx->sV[mat][c] += vol;
+    ctx->sM[mat][c] += mass;
+    ctx->sE[c] += mass * I0;
+    ctx->sPz[c] += mass * vz;
+}
+
+salec_status salec_add_layer(salec_ctx* ctx, int mat, double zlo, double zhi, double rho, double I0, double vz)
+{
+    if (!ctx) return SALEC_EINVAL;
+    if (ctx->finalized) return fail(ctx, SALEC_EORDER, "add_layer after finalize");
+    if (mat < 0 || mat >= ctx->g.nmat || !ctx->mat_set[mat]) return fail(ctx, SALEC_EORDER, "material %d not set", mat);
+    if (!(zhi > zlo)) return fail(ctx, SALEC_EINVAL, "layer needs zlo < zhi");
+    const salec_material& M = ctx->mats[mat];
+    const int nr = ctx->g.nr, nz = ctx->g.nz;
+    const double dx = ctx->g.dx, g = ctx->g.gravity;
+    const bool hydro = rho <= 0.0 && g > 0.0 && M.eos == SALEC_EOS_TILLOTSON;
+    if (hydro && I0 != 0.0) return fail(ctx, SALEC_EINVAL, "hydrostatic layer must be cold (I0 = 0)");
+    std::vector<double> w(nz), rrow(nz, rho > 0.0 ? rho : M.rho0);
+    for (int j = 0; j < nz; ++j) {
+        const double z0 = (double)j * dx, z1 = ((double)j + 1.0) * dx;
+        const double lo = zlo > z0 ? zlo : z0, hi = zhi < z1 ? zhi : z1;
+        w[j] = hi > lo ? (hi - lo) / dx : 0.0;
+    }
+    if (hydro) {
+        // discrete hydrostatic balance at the vertex between rows j (below) and j+1:
+        // P_j - P_{j+1} = (rho_j + rho_{j+1}) g dx / 2 with the cold curve P = A mu + B mu^2;
+        // per row a quadratic in mu, solved in the cancellation-free form of its root.
+        for (int j = 0; j < nz; ++j)
+            if (w[j] > 0.0 && w[j] < 1.0) return fail(ctx, SALEC_EINVAL, "hydrostatic layer must fill whole rows");
+        const double k = 0.5 * dx * g;
+        double Pup = 0.0, rup = 0.0;
+        int j = nz - 1;
+        while (j >= 0 && !(w[j] > 0.0)) --j;
+        for (; j >= 0 && w[j] > 0.0; --j) {
+            const double rhs = Pup + k * rup;
+            const double lin = M.A - k * M.rho0, cst = k * M.rho0 + rhs;
+            double mu;
+            if (M.B != 0.0) mu = 2.0 * cst / (lin + sqrt(lin * lin + 4.0 * M.B * cst));
+            else mu = cst / lin;
+            rrow[j] = M.rho0 * (1.0 + mu);
+            Pup = M.A * mu + M.B * mu * mu;
+            rup = rrow[j];
+        }
+    }
+    for (int j = 0; j < nz; ++j) {
+        if (!(w[j] > 0.0)) continue;
+        for (int i = 0; i < nr; ++i) {
+            add_content(ctx, mat, (size_t)j * nr + i, w[j] * ctx->Vc[i], rrow[j], I0, vz);
+        }
+    }
+    return SALEC_OK;
+}
+
+salec_status salec_place_projectile(salec_ctx* ctx, int mat, double radius, double zc, double vz, double rho, double I0)
+{
+    if (!ctx) return SALEC_EINVAL;
+    if (ctx->finalized) return fail(ctx, SALEC_EORDER, "place_projectile after finalize");
+    if (mat < 0 || mat >= ctx->g.nmat || !ctx->mat_set[mat]) return fail(ctx, SALEC_EORDER, "material %d not set", mat);
+    if (!(radius > 0.0)) return fail(ctx, SALEC_EINVAL, "radius must be positive");
+    const double r0 = rho > 0.0 ? rho : ctx->mats[mat].rho0;
+    const int nr = ctx->g.nr, nz = ctx->g.nz;
+    const double dx = ctx->g.dx, R2 = radius * radius;
+    // only rows and columns that can touch the sphere
+    const int jlo = (int)floor((zc - radius) / dx) - 1, jhi = (int)ceil((zc + radius) / dx) + 1;
+    const int ihi = (int)ceil(radius / dx) + 1;
+    for (int j = jlo < 0 ? 0 : jlo; j < nz && j <= jhi; ++j) {
+        for (int i = 0; i < nr && i <= ihi; ++i) {
+            double wi = 0.0, wt = 0.0;
+            for (int b = 0; b < 16; ++b) {
+                const double zs = dx * ((double)j + ((double)b + 0.5) / 16.0);
+                const double dz = zs - zc;
+                for (int a = 0; a < 16; ++a) {
+                    const double rs = dx * ((double)i + ((double)a + 0.5) / 16.0);
+                    wt += rs;
+                    if (rs * rs + dz * dz < R2) wi += rs;
+                }
+            }
+            const double frac = wi / wt;
+            if (!(frac > 0.0)) continue;
+            const size_t c = (size_t)j * nr + i;
+            const double keep = 1.0 - frac;
+            for (int k = 0; k < ctx->g.nmat; ++k) { ctx->sV[k][c] *= keep; ctx->sM[k][c] *= keep; }
+            ctx->sE[c] *= keep;
+            ctx->sPz[c] *= keep;
+            add_content(ctx, mat, c, frac * ctx->Vc[i], r0, I0, vz);
+        }
+    }
+    return SALEC_OK;
+}
+
+static double profile(double c, int width, double dx, double y, double R)
+{
+    if (width <= 0 || y <= 0.0) return 0.0;
+    const double s = y / (double)width;
+    return 1.5 * c / ((double)width * dx) * s * s * log(1.0 / R);
+}
+
+salec_status salec_finalize(salec_ctx* ctx)
+{
+    if (!ctx) return SALEC_EINVAL;
+    if (ctx->finalized) return fail(ctx, SALEC_EORDER, "finalize called twice");
+    const salec_grid& g = ctx->g;
+    for (int m = 0; m < g.nmat; ++m)
+        if (!ctx->mat_set[m]) return fail(ctx, SALEC_EORDER, "material %d not set", m);
+    const int nr = g.nr, nz = g.nz, pr = g.pml_right, pb = g.pml_bottom;
+    const size_t nc = (size_t)nr * nz, nv = (size_t)(nr + 1) * (nz + 1);
+    fill_params(ctx);
+    const Params& P = ctx->P;
+    // PML wave speed
+    double c = g.pml_c;
+    if (!(c > 0.0)) {
+        c = 0.0;
+        for (int m = 0; m < g.nmat; ++m)
+            if (ctx->mats[m].eos == SALEC_EOS_TILLOTSON) {
+                const double cm = sqrt(ctx->mats[m].A / ctx->mats[m].rho0);
+                c = cm > c ? cm : c;
+            }
+    }
+    if ((pr > 0 || pb > 0) && !(c > 0.0 && g.pml_R > 0.0 && g.pml_R < 1.0))
+        return fail(ctx, SALEC_EINVAL, "PML needs a wave speed and 0 < R < 1");
+    // cells
+    std::vector<double2> fr[kMaxMat];
+    for (int m = 0; m < g.nmat; ++m) fr[m].assign(nc, make_double2(0.0, 0.0));
+    std::vector<double> I(nc, 0.0), Mkept(nc, 0.0), Mall(nc, 0.0);
+    for (size_t cc = 0; cc < nc; ++cc) {
+        const int i = (int)(cc % nr);
+        double mk = 0.0, ma = 0.0;
+        for (int m = 0; m < g.nmat; ++m) {
+            double f = ctx->sV[m][cc] / ctx->Vc[i];
+            if (f < g.f_min) f = 0.0;
+            ma += ctx->sM[m][cc];
+            if (f > 0.0) {
+                fr[m][cc] = make_double2(f, ctx->sMix[m][cc] ? ctx->sM[m][cc] / ctx->sV[m][cc] : ctx->sR[m][cc]);
+                mk += ctx->sM[m][cc];
+            }
+        }
+        Mkept[cc] = mk;
+        Mall[cc] = ma;
+        I[cc] = mk > 0.0 ? (ctx->sImix[cc] ? ctx->sE[cc] / mk : ctx->sI[cc]) : 0.0;
+    }
+    // vertices: quarter-cell momentum / quarter-cell mass
+    std::vector<double2> v(nv, make_double2(0.0, 0.0));
+    for (int j = 0; j <= nz; ++j)
+        for (int i = 0; i <= nr; ++i) {
+            double mom = 0.0, mass = 0.0;
+            for (int dj = -1; dj <= 0; ++dj)
+                for (int di = -1; di <= 0; ++di) {
+                    const int ci = i + di, cj = j + dj;
+                    if (ci < 0 || ci >= nr || cj < 0 || cj >= nz) continue;
+                    const size_t cc = (size_t)cj * nr + ci;
+                    if (Mall[cc] > 0.0) mom += 0.25 * ctx->sPz[cc] * (Mkept[cc] / Mall[cc]);
+                    mass += 0.25 * Mkept[cc];
+                }
+            double vz = mass > 0.0 ? mom / mass : 0.0;
+            if (j == 0 || (j == nz && g.bc_top == SALEC_TOP_WALL)) vz = 0.0;
+            v[(size_t)j * (nr + 1) + i] = make_double2(0.0, vz);
+        }
+    // reference rows from the outermost column
+    std::vector<double> p0(nz, 0.0), rref(nz, 0.0), Iref(nz, 0.0);
+    for (int j = 0; j < nz; ++j) {
+        const size_t cc = (size_t)j * nr + (nr - 1);
+        double phat = 0.0, phi = 0.0, mass = 0.0;
+        for (int m = 0; m < g.nmat; ++m) {
+            const double2 f = fr[m][cc];
+            if (!(f.x > 0.0)) continue;
+            double pm, c2;
+            eos_eval(P.mat[m], f.y, I[cc], pm, c2);
+            const double pmin = P.mat[m].p_t;
+            pm = pm < pmin ? pmin : pm;
+            phat += f.x * pm; phi += f.x; mass += f.x * f.y;
+        }
+        if (phi > 0.0) { p0[j] = phat / phi; rref[j] = mass / phi; Iref[j] = I[cc]; }
+    }
+    // PML profiles (Eq. 26)
+    std::vector<double> dBc(nz, 0.0), dBv(nz + 1, 0.0), dRc(nr, 0.0), dRv(nr + 1, 0.0);
+    for (int j = 0; j < pb; ++j) {
+        dBc[j] = profile(c, pb, g.dx, (double)pb - (double)j - 0.5, g.pml_R);
+        dBv[j] = profile(c, pb, g.dx, (double)(pb - j), g.pml_R);
+    }
+    for (int i = nr - pr; i < nr; ++i) dRc[i] = profile(c, pr, g.dx, (double)i + 0.5 - (double)(nr - pr), g.pml_R);
+    for (int i = nr - pr + 1; i <= nr; ++i) dRv[i] = profile(c, pr, g.dx, (double)(i - (nr - pr)), g.pml_R);
+    std::vector<double> invV(nr);
+    for (int i = 0; i < nr; ++i) invV[i] = 1.0 / ctx->Vc[i];
+    // scalars
+    DevScalars s;
+    memset(&s, 0, sizeof(s));
+    s.dt_prev = g.dt_init;
+    const Layout& L = ctx->L;
+    cudaStream_t st = ctx->stream;
+    cudaError_t e = cudaMemsetAsync(ctx->base, 0, L.persist_end, st);
+    auto up = [&](size_t off, const void* src, size_t n) {
+        if (e == cudaSuccess && n) e = cudaMemcpyAsync(ctx->base + off, src, n, cudaMemcpyHostToDevice, st);
+    };
+    up(L.scal, &s, sizeof(s));
+    up(L.A_R, ctx->A_R.data(), (nr + 1) * sizeof(double));
+    up(L.A_Z, ctx->A_Z.data(), nr * sizeof(double));
+    up(L.V, ctx->Vc.data(), nr * sizeof(double));
+    up(L.invV, invV.data(), nr * sizeof(double));
+    up(L.p0, p0.data(), nz * sizeof(double));
+    up(L.rho_ref, rref.data(), nz * sizeof(double));
+    up(L.I_ref, Iref.data(), nz * sizeof(double));
+    up(L.dB_c, dBc.data(), nz * sizeof(double));
+    up(L.dB_v, dBv.data(), (nz + 1) * sizeof(double));
+    up(L.dR_c, dRc.data(), nr * sizeof(double));
+    up(L.dR_v, dRv.data(), (nr + 1) * sizeof(double));
+    for (int m = 0; m < g.nmat; ++m) up(L.fr[m], fr[m].data(), nc * sizeof(double2));
+    up(L.I, I.data(), nc * sizeof(double));
+    up(L.v, v.data(), nv * sizeof(double2));
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_check(ctx, e, "finalize upload");
+    for (int m = 0; m < kMaxMat; ++m) {
+        ctx->sV[m].clear(); ctx->sV[m].shrink_to_fit(); ctx->sM[m].clear(); ctx->sM[m].shrink_to_fit();
+        ctx->sR[m].clear(); ctx->sR[m].shrink_to_fit(); ctx->sMix[m].clear(); ctx->sMix[m].shrink_to_fit();
+    }
+    ctx->sE.clear(); ctx->sE.shrink_to_fit(); ctx->sPz.clear(); ctx->sPz.shrink_to_fit();
+    ctx->sI.clear(); ctx->sI.shrink_to_fit(); ctx->sImix.clear(); ctx->sImix.shrink_to_fit();
+    ctx->finalized = true;
+    return SALEC_OK;
+}
+
+salec_status salec_step(salec_ctx* ctx, int nsteps)
+{
+    if (!ctx || nsteps < 0) return SALEC_EINVAL;
+    if (!ctx->finalized) return fail(ctx, SALEC_EORDER, "step before finalize");
+    const int K = launches_per_step() + 1;
+    for (int n = 0; n < nsteps; ++n) {
+        cudaEvent_t* evp = nullptr;
+        if (ctx->timing) {
+            while (ctx->ev_used + K > ctx->ev.size()) {
+                cudaEvent_t e0;
+                cudaError_t ce = cudaEventCreate(&e0);
+                if (ce != cudaSuccess) return cuda_check(ctx, ce, "event create");
+                ctx->ev.push_back(e0);
+            }
+            evp = ctx->ev.data() + ctx->ev_used;
+            ctx->ev_used += K;
+        }
+        cudaError_t e = launch_step(ctx->P, ctx->stream, evp);
+        if (e != cudaSuccess) return cuda_check(ctx, e, "step launch");
+    }
+    return SALEC_OK;
+}
+
+salec_status salec_set_kernel_timing(salec_ctx* ctx, int on)
+{
+    if (!ctx) return SALEC_EINVAL;
+    ctx->timing = on != 0;
+    ctx->ev_used = 0;
+    return SALEC_OK;
+}
+
+salec_status salec_kernel_times(salec_ctx* ctx, double* avg_ms, int n, int* steps)
+{
+    const int K = launches_per_step();
+    if (!ctx || !avg_ms || !steps || n < K) return SALEC_EINVAL;
+    cudaError_t e = cudaStreamSynchronize(ctx->stream);
+    if (e != cudaSuccess) return cuda_check(ctx, e, "kernel times");
+    const size_t ns = ctx->ev_used / (K + 1);
+    for (int k = 0; k < K; ++k) avg_ms[k] = 0.0;
+    for (size_t s = 0; s < ns; ++s)
+        for (int k = 0; k < K; ++k) {
+            float ms = 0.0f;
+            e = cudaEventElapsedTime(&ms, ctx->ev[s * (K + 1) + k], ctx->ev[s * (K + 1) + k + 1]);
+            if (e != cudaSuccess) return cuda_check(ctx, e, "event elapsed");
+            avg_ms[k] += ms;
+        }
+    for (int k = 0; k < K; ++k) avg_ms[k] = ns ? avg_ms[k] / (double)ns : 0.0;
+    *steps = (int)ns;
+    ctx->ev_used = 0;
+    return SALEC_OK;
+}
+
+const char* salec_kernel_name(int k)
+{
+    return kernel_name(k);
+}
+
+salec_status salec_get_scalars(salec_ctx* ctx, double out[8])
+{
+    if (!ctx || !out) return SALEC_EINVAL;
+    if (!ctx->finalized) return fail(ctx, SALEC_EORDER, "scalars before finalize");
+    DevScalars s;
+    cudaError_t e = cudaMemcpyAsync(&s, ctx->base + ctx->L.scal, sizeof(s), cudaMemcpyDeviceToHost, ctx->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+    if (e != cudaSuccess) return cuda_check(ctx, e, "read scalars");
+    out[0] = s.t; out[1] = s.dt; out[2] = (double)s.nstep; out[3] = (double)s.status;
+    out[4] = s.mass_out; out[5] = s.mass_discarded; out[6] = s.mass_pml; out[7] = s.zmom_out;
+    if (s.status != 0) return fail(ctx, SALEC_EUNSTABLE, "device status %d", s.status);
+    return SALEC_OK;
+}
+
+salec_status salec_set_time(salec_ctx* ctx, double t, double dt_prev)
+{
+    if (!ctx) return SALEC_EINVAL;
+    if (!ctx->finalized) return fail(ctx, SALEC_EORDER, "set_time before finalize");
+    DevScalars s;
+    cudaError_t e = cudaMemcpyAsync(&s, ctx->base + ctx->L.scal, sizeof(s), cudaMemcpyDeviceToHost, ctx->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+    s.t = t;
+    s.dt_prev = dt_prev;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(ctx->base + ctx->L.scal, &s, sizeof(s), cudaMemcpyHostToDevice, ctx->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+    return cuda_check(ctx, e, "set_time");
+}
+
+// Where a field lives: a device array of `stride` doubles per element, component `comp`,
+// over the whole grid (strip == 0) or over a PML strip (1 bottom cells, 2 right cells,
+// 3 bottom vertices, 4 right vertices).
+struct FieldLoc { size_t off; int stride, comp, strip; bool vertex; };
+
+static bool locate(const salec_ctx* ctx, int field, FieldLoc& F)
+{
+    const Layout& L = ctx->L;
+    F.strip = 0; F.vertex = false; F.stride = 1; F.comp = 0;
+    if (field >= SALEC_F_VOLFRAC0 && field <= SALEC_F_VOLFRAC2) {
+        if (field - SALEC_F_VOLFRAC0 >= ctx->g.nmat) return false;
+        F.off = L.fr[field - SALEC_F_VOLFRAC0]; F.stride = 2; F.comp = 0; return true;
+    }
+    if (field >= SALEC_F_DENS0 && field <= SALEC_F_DENS2) {
+        if (field - SALEC_F_DENS0 >= ctx->g.nmat) return false;
+        F.off = L.fr[field - SALEC_F_DENS0]; F.stride = 2; F.comp = 1; return true;
+    }
+    switch (field) {
+    case SALEC_F_IE: F.off = L.I; return true;
+    case SALEC_F_SRR: F.off = L.s01; F.stride = 2; F.comp = 0; return true;
+    case SALEC_F_SZZ: F.off = L.s01; F.stride = 2; F.comp = 1; return true;
+    case SALEC_F_SRZ: F.off = L.s2d; F.stride = 2; F.comp = 0; return true;
+    case SALEC_F_DAMAGE: F.off = L.s2d; F.stride = 2; F.comp = 1; return true;
+    case SALEC_F_PMAX: F.off = L.pmax; return true;
+    case SALEC_F_VR: F.off = L.v; F.stride = 2; F.comp = 0; F.vertex = true; return true;
+    case SALEC_F_VZ: F.off = L.v; F.stride = 2; F.comp = 1; F.vertex = true; return true;
+    case SALEC_F_PHI1_B: F.off = L.pb_c; F.stride = 2; F.comp = 0; F.strip = 1; return true;
+    case SALEC_F_PHI3_B: F.off = L.pb_c; F.stride = 2; F.comp = 1; F.strip = 1; return true;
+    case SALEC_F_PSI2_B: F.off = L.pb_psi2; F.strip = 1; return true;
+    case SALEC_F_PHI1_R: F.off = L.pr_c; F.stride = 2; F.comp = 0; F.strip = 2; return true;
+    case SALEC_F_PHI3_R: F.off = L.pr_c; F.stride = 2; F.comp = 1; F.strip = 2; return true;
+    case SALEC_F_PSI2_R: F.off = L.pr_psi2; F.strip = 2; return true;
+    default: break;
+    }
+    if (field >= SALEC_F_PHI2R_B && field <= SALEC_F_PSI1Z_R) {
+        const int k = field - SALEC_F_PHI2R_B;
+        F.vertex = true; F.stride = 4; F.comp = k % 4;
+        F.strip = k < 4 ? 3 : 4;
+        F.off = k < 4 ? L.pb_v : L.pr_v;
+        return true;
+    }
+    return false;
+}
+
+// number of elements of the device array behind a location, and the map from a
+// full-grid index to it (-1 outside the strip)
+static size_t loc_count(const salec_ctx* ctx, const FieldLoc& F)
+{
+    const size_t nr = ctx->g.nr, nz = ctx->g.nz, pr = ctx->g.pml_right, pb = ctx->g.pml_bottom;
+    switch (F.strip) {
+    case 1: return nr * pb;
+    case 2: return pr * nz;
+    case 3: return (nr + 1) * pb;
+    case 4: return pr * (nz + 1);
+    default: return F.vertex ? (nr + 1) * (nz + 1) : nr * nz;
+    }
+}
+static long strip_index(const salec_ctx* ctx, const FieldLoc& F, int i, int j)
+{
+    const int nr = ctx->g.nr, pr = ctx->g.pml_right, pb = ctx->g.pml_bottom;
+    switch (F.strip) {
+    case 1: return j < pb ? (long)j * nr + i : -1;
+    case 2: return i >= nr - pr ? (long)j * pr + (i - (nr - pr)) : -1;
+    case 3: return j < pb ? (long)j * (nr + 1) + i : -1;
+    case 4: return i > nr - pr ? (long)j * pr + (i - (nr - pr + 1)) : -1;
+    default: return F.vertex ? (long)j * (nr + 1) + i : (long)j * nr + i;
+    }
+}
+
+salec_status salec_get_field(salec_ctx* ctx, int field, double* host_out, size_t n)
+{
+    if (!ctx || !host_out) return SALEC_EINVAL;
+    if (!ctx->finalized) return fail(ctx, SALEC_EORDER, "get_field before finalize");
+    const int nr = ctx->g.nr, nz = ctx->g.nz;
+    const size_t nc = (size_t)nr * nz;
+    if (field == SALEC_F_PRESSURE) {
+        if (n != nc) return fail(ctx, SALEC_EINVAL, "pressure needs n = nr*nz");
+        double* tmp = at<double>(ctx, ctx->L.tmp);
+        cudaError_t e = launch_pressure(ctx->P, tmp, ctx->stream);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(host_out, tmp, nc * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+        return cuda_check(ctx, e, "get pressure");
+    }
+    FieldLoc F;
+    if (!locate(ctx, field, F)) return fail(ctx, SALEC_EINVAL, "unknown field %d", field);
+    const size_t want = F.vertex ? (size_t)(nr + 1) * (nz + 1) : nc;
+    if (n != want) return fail(ctx, SALEC_EINVAL, "field %d needs n = %zu", field, want);
+    const size_t cnt = loc_count(ctx, F);
+    std::vector<double> buf(cnt * F.stride + 1);
+    cudaError_t e = cudaSuccess;
+    if (cnt) e = cudaMemcpyAsync(buf.data(), ctx->base + F.off, cnt * F.stride * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+    if (e != cudaSuccess) return cuda_check(ctx, e, "get field");
+    const int ni = F.vertex ? nr + 1 : nr, nj = F.vertex ? nz + 1 : nz;
+    for (int j = 0; j < nj; ++j)
+        for (int i = 0; i < ni; ++i) {
+            const long k = strip_index(ctx, F, i, j);
+            host_out[(size_t)j * ni + i] = k < 0 ? 0.0 : buf[(size_t)k * F.stride + F.comp];
+        }
+    return SALEC_OK;
+}
+
+salec_status salec_set_field(salec_ctx* ctx, int field, const double* host_in, size_t n)
+{
+    if (!ctx || !host_in) return SALEC_EINVAL;
+    if (!ctx->finalized) return fail(ctx, SALEC_EORDER, "set_field before finalize");
+    if (field == SALEC_F_PRESSURE) return fail(ctx, SALEC_EINVAL, "pressure is read-only");
+    const int nr = ctx->g.nr, nz = ctx->g.nz;
+    FieldLoc F;
+    if (!locate(ctx, field, F)) return fail(ctx, SALEC_EINVAL, "unknown field %d", field);
+    const size_t want = F.vertex ? (size_t)(nr + 1) * (nz + 1) : (size_t)nr * nz;
+    if (n != want) return fail(ctx, SALEC_EINVAL, "field %d needs n = %zu", field, want);
+    const size_t cnt = loc_count(ctx, F);
+    if (!cnt) return SALEC_OK;
+    std::vector<double> buf(cnt * F.stride);
+    cudaError_t e = cudaMemcpyAsync(buf.data(), ctx->base + F.off, cnt * F.stride * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+    if (e != cudaSuccess) return cuda_check(ctx, e, "set field (read)");
+    const int ni = F.vertex ? nr + 1 : nr, nj = F.vertex ? nz + 1 : nz;
+    for (int j = 0; j < nj; ++j)
+        for (int i = 0; i < ni; ++i) {
+            const long k = strip_index(ctx, F, i, j);
+            if (k >= 0) buf[(size_t)k * F.stride + F.comp] = host_in[(size_t)j * ni + i];
+        }
+    e = cudaMemcpyAsync(ctx->base + F.off, buf.data(), cnt * F.stride * sizeof(double), cudaMemcpyHostToDevice, ctx->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+    return cuda_check(ctx, e, "set field (write)");
+}
+
+salec_status salec_crater_profile(salec_ctx* ctx, double z_surface, int npts, double* depth_profile, double* heights,
+                                  double* depth, double* diameter)
+{
+    if (!ctx || !depth || !diameter || npts < 0 || (npts > 0 && !depth_profile)) return SALEC_EINVAL;
+    if (!ctx->finalized) return fail(ctx, SALEC_EORDER, "crater_profile before finalize");
+    const int nr = ctx->g.nr;
+    const double dx = ctx->g.dx;
+    std::vector<double> h(nr);
+    double* tmp = at<double>(ctx, ctx->L.tmp);
+    cudaError_t e = launch_column_heights(ctx->P, tmp, ctx->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(h.data(), tmp, nr * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+    if (e != cudaSuccess) return cuda_check(ctx, e, "crater profile");
+    // depth on the axis; deepest column; first up-crossing of z_surface beyond it
+    int kmin = 0;
+    for (int i = 1; i < nr; ++i) if (z_surface - h[i] > z_surface - h[kmin]) kmin = i;
+    double D = 0.0;
+    if (z_surface - h[kmin] > 0.0) {
+        D = 2.0 * ((double)nr - 0.5) * dx;
+        for (int i = kmin; i + 1 < nr; ++i)
+            if (h[i] < z_surface && z_surface <= h[i + 1]) {
+                D = 2.0 * (((double)i + 0.5) * dx + (z_surface - h[i]) / (h[i + 1] - h[i]) * dx);
+                break;
+            }
+    }
+    if (npts > 0) {
+        const double rext = (double)(nr - ctx->g.pml_right) * dx;
+        for (int k = 0; k < npts; ++k) {
+            const double r = ((double)k + 0.5) * rext / npts;
+            double x = r / dx - 0.5;     // fractional column-centre index
+            double val;
+            if (x <= 0.0) val = z_surface - h[0];
+            else if (x >= nr - 1) val = z_surface - h[nr - 1];
+            else {
+                const int i0 = (int)floor(x);
+                const double w = x - i0;
+                val = (1.0 - w) * (z_surface - h[i0]) + w * (z_surface - h[i0 + 1]);
+            }
+            depth_profile[k] = val;
+        }
+    }
+    if (heights) memcpy(heights, h.data(), nr * sizeof(double));
+    *depth = z_surface - h[0];
+    *diameter = D;
+    return SALEC_OK;
+}
+
+salec_status salec_conservation(salec_ctx* ctx, double out[4])
+{
+    if (!ctx || !out) return SALEC_EINVAL;
+    if (!ctx->finalized) return fail(ctx, SALEC_EORDER, "conservation before finalize");
+    double* part = at<double>(ctx, ctx->L.partial);
+    int nb = 0;
+    cudaError_t e = launch_conservation(ctx->P, part, &nb, ctx->stream);
+    std::vector<double> h((size_t)4 * nb);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(h.data(), part, h.size() * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+    if (e != cudaSuccess) return cuda_check(ctx, e, "conservation");
+    double s[4] = {0, 0, 0, 0};
+    for (int b = 0; b < nb; ++b)
+        for (int k = 0; k < 4; ++k) s[k] += h[(size_t)4 * b + k];
+    for (int k = 0; k < 4; ++k) out[k] = s[k];
+    return SALEC_OK;
+}
+
+salec_status salec_checkpoint_bytes(salec_ctx* ctx, size_t* bytes)
+{
+    if (!ctx || !bytes) return SALEC_EINVAL;
+    *bytes = ctx->L.persist_end;
+    return SALEC_OK;
+}
+
+salec_status salec_get_state(salec_ctx* ctx, void* host, size_t bytes)
+{
+    if (!ctx || !host) return SALEC_EINVAL;
+    if (!ctx->finalized) return fail(ctx, SALEC_EORDER, "get_state before finalize");
+    if (bytes != ctx->L.persist_end) return fail(ctx, SALEC_EINVAL, "checkpoint needs %zu bytes", ctx->L.persist_end);
+    cudaError_t e = cudaMemcpyAsync(host, ctx->base, bytes, cudaMemcpyDeviceToHost, ctx->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+    return cuda_check(ctx, e, "get_state");
+}
+
+salec_status salec_set_state(salec_ctx* ctx, const void* host, size_t bytes)
+{
+    if (!ctx || !host) return SALEC_EINVAL;
+    if (!ctx->finalized) return fail(ctx, SALEC_EORDER, "set_state before finalize");
+    if (bytes != ctx->L.persist_end) return fail(ctx, SALEC_EINVAL, "checkpoint needs %zu bytes", ctx->L.persist_end);
+    cudaError_t e = cudaMemcpyAsync(ctx->base, host, bytes, cudaMemcpyHostToDevice, ctx->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+    return cuda_check(ctx, e, "set_state");
+}
+
+int salec_launches_per_step(const salec_ctx* ctx)
+{
+    (void)ctx;
+    return launches_per_step();
+}
+
+const char* salec_last_error(const salec_ctx* ctx)
+{
+    return ctx ? ctx->err.c_str() : "null context";
+}
+
+void salec_destroy(salec_ctx* ctx)
+{
+    if (!ctx) return;
+    for (cudaEvent_t e : ctx->ev) cudaEventDestroy(e);
+    delete ctx;
+}
+
+}  // extern "C"

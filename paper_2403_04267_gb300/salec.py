@@ -1,0 +1,261 @@
+"""Python binding of the C ABI in include/salec.h (ctypes; argument marshalling only).
+
+Every step of the time step runs in the CUDA library ``_build/libsalec.so``; this module
+only converts arguments.  PyTorch provides the device buffer and the stream.  If the
+library cannot be loaded the calls raise: there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+from . import build as _build
+
+SALEC_OK, SALEC_EINVAL, SALEC_ENOMEM, SALEC_ECUDA, SALEC_EORDER, SALEC_EUNSTABLE = range(6)
+SALEC_FP64 = 0
+_STATUS = {0: "SALEC_OK", 1: "SALEC_EINVAL", 2: "SALEC_ENOMEM", 3: "SALEC_ECUDA", 4: "SALEC_EORDER",
+           5: "SALEC_EUNSTABLE"}
+
+FIELDS = {
+    "f0": 0, "f1": 1, "f2": 2, "rho0": 3, "rho1": 4, "rho2": 5, "I": 6, "srr": 7, "szz": 8,
+    "srz": 9, "D": 10, "pmax": 11, "vr": 12, "vz": 13, "p": 14,
+    "phi1_b": 20, "phi3_b": 21, "psi2_b": 22, "phi1_r": 23, "phi3_r": 24, "psi2_r": 25,
+    "phi2r_b": 30, "phi2z_b": 31, "psi1r_b": 32, "psi1z_b": 33,
+    "phi2r_r": 34, "phi2z_r": 35, "psi1r_r": 36, "psi1z_r": 37,
+}
+VERTEX_FIELDS = {"vr", "vz", "phi2r_b", "phi2z_b", "psi1r_b", "psi1z_b",
+                 "phi2r_r", "phi2z_r", "psi1r_r", "psi1z_r"}
+
+
+class salec_grid(C.Structure):
+    _fields_ = [
+        ("nr", C.c_int), ("nz", C.c_int), ("nmat", C.c_int), ("dx", C.c_double),
+        ("pml_right", C.c_int), ("pml_bottom", C.c_int), ("pml_R", C.c_double), ("pml_c", C.c_double),
+        ("gravity", C.c_double), ("cfl", C.c_double), ("dt_init", C.c_double), ("dt_max", C.c_double),
+        ("dt_growth", C.c_double), ("dt_min", C.c_double), ("av_cq", C.c_double), ("av_cl", C.c_double),
+        ("f_min", C.c_double), ("bc_top", C.c_int), ("bc_bottom", C.c_int),
+    ]
+
+
+class salec_material(C.Structure):
+    _fields_ = [
+        ("eos", C.c_int), ("rho0", C.c_double),
+        ("A", C.c_double), ("B", C.c_double), ("E0", C.c_double), ("a", C.c_double), ("b", C.c_double),
+        ("alpha", C.c_double), ("beta", C.c_double), ("Eiv", C.c_double), ("Ecv", C.c_double),
+        ("gamma", C.c_double), ("strength", C.c_int),
+        ("Yi0", C.c_double), ("mui", C.c_double), ("Yim", C.c_double), ("Yd0", C.c_double),
+        ("mud", C.c_double), ("Ydm", C.c_double), ("G", C.c_double),
+        ("eps_fb", C.c_double), ("B_dam", C.c_double), ("p_bd", C.c_double), ("p_t", C.c_double),
+    ]
+
+
+_lib = None
+EXPORTS = ["salec_state_bytes", "salec_create", "salec_set_material", "salec_add_layer",
+           "salec_place_projectile", "salec_finalize", "salec_step", "salec_get_scalars",
+           "salec_set_time", "salec_get_field", "salec_set_field", "salec_crater_profile",
+           "salec_conservation", "salec_checkpoint_bytes", "salec_get_state", "salec_set_state",
+           "salec_launches_per_step", "salec_set_kernel_timing", "salec_kernel_times",
+           "salec_kernel_name", "salec_last_error", "salec_destroy"]
+
+
+def load(build: bool = True):
+    """Load (building first if needed) the CUDA library and declare its signatures."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = _build.build() if build else _build.LIB
+    if not os.path.exists(path):
+        raise RuntimeError(f"CUDA library missing: {path}")
+    L = C.CDLL(path)
+    P, D, Z, I = C.c_void_p, C.c_double, C.c_size_t, C.c_int
+    PD = C.POINTER(C.c_double)
+    sig = {
+        "salec_state_bytes": (I, [C.POINTER(salec_grid), I, C.POINTER(C.c_size_t)]),
+        "salec_create": (I, [C.POINTER(salec_grid), I, P, Z, P, C.POINTER(P)]),
+        "salec_set_material": (I, [P, I, C.POINTER(salec_material)]),
+        "salec_add_layer": (I, [P, I, D, D, D, D, D]),
+        "salec_place_projectile": (I, [P, I, D, D, D, D, D]),
+        "salec_finalize": (I, [P]),
+        "salec_step": (I, [P, I]),
+        "salec_get_scalars": (I, [P, PD]),
+        "salec_set_time": (I, [P, D, D]),
+        "salec_get_field": (I, [P, I, PD, Z]),
+        "salec_set_field": (I, [P, I, PD, Z]),
+        "salec_crater_profile": (I, [P, D, I, PD, PD, PD, PD]),
+        "salec_conservation": (I, [P, PD]),
+        "salec_checkpoint_bytes": (I, [P, C.POINTER(C.c_size_t)]),
+        "salec_get_state": (I, [P, P, Z]),
+        "salec_set_state": (I, [P, P, Z]),
+        "salec_launches_per_step": (I, [P]),
+        "salec_set_kernel_timing": (I, [P, I]),
+        "salec_kernel_times": (I, [P, PD, I, C.POINTER(C.c_int)]),
+        "salec_kernel_name": (C.c_char_p, [I]),
+        "salec_last_error": (C.c_char_p, [P]),
+        "salec_destroy": (None, [P]),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(L, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = L
+    return L
+
+
+class SalecError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{_STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+_EOS = {"tillotson": 0, "ideal_gas": 1}
+_STR = {"none": 0, "collins": 1}
+_TOP = {"outflow": 0, "wall": 1}
+_BOTTOM = {"noslip": 0, "freeslip": 1}
+
+
+def make_grid(d: dict, nmat: int) -> salec_grid:
+    g = salec_grid()
+    g.nr, g.nz, g.nmat, g.dx = int(d["nr"]), int(d["nz"]), int(nmat), float(d["dx"])
+    g.pml_right, g.pml_bottom = int(d.get("pml_r", 0)), int(d.get("pml_b", 0))
+    for k in ("pml_R", "pml_c", "gravity", "cfl", "dt_init", "dt_max", "dt_growth", "dt_min",
+              "av_cq", "av_cl", "f_min"):
+        setattr(g, k, float(d.get(k, 0.0)))
+    g.bc_top = _TOP[d.get("bc_top", "outflow")]
+    g.bc_bottom = _BOTTOM[d.get("bc_bottom", "noslip")]
+    return g
+
+
+def make_material(d: dict) -> salec_material:
+    m = salec_material()
+    for name, _ in salec_material._fields_:
+        if name == "eos":
+            m.eos = _EOS[d.get("eos", "tillotson")]
+        elif name == "strength":
+            m.strength = _STR[d.get("strength", "none")]
+        else:
+            setattr(m, name, float(d.get(name, 0.0)))
+    return m
+
+
+class Sim:
+    """One simulation on the current CUDA device.  ``spec`` is a workload dictionary
+    (see workloads.py).  The device state is one torch uint8 tensor owned here."""
+
+    def __init__(self, spec: dict, device=None, stream=None):
+        import torch
+        L = load()
+        self.spec = spec
+        self.nmat = len(spec["materials"])
+        self.grid = make_grid(spec["grid"], self.nmat)
+        self.nr, self.nz = self.grid.nr, self.grid.nz
+        nb = C.c_size_t()
+        self._check(L.salec_state_bytes(C.byref(self.grid), SALEC_FP64, C.byref(nb)), None)
+        self.device = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
+        self.state = torch.empty(nb.value, dtype=torch.uint8, device=self.device)
+        self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        h = C.c_void_p()
+        self._check(L.salec_create(C.byref(self.grid), SALEC_FP64, C.c_void_p(self.state.data_ptr()), nb.value,
+                                   C.c_void_p(self.stream.cuda_stream), C.byref(h)), None)
+        self._h = h
+        for k, m in enumerate(spec["materials"]):
+            mm = make_material(m)
+            self._check(L.salec_set_material(h, k, C.byref(mm)))
+        for lay in spec.get("layers", []):
+            self._check(L.salec_add_layer(h, int(lay["mat"]), float(lay["zlo"]), float(lay["zhi"]),
+                                          float(lay.get("rho", 0.0)), float(lay.get("I0", 0.0)),
+                                          float(lay.get("vz", 0.0))))
+        pj = spec.get("projectile")
+        if pj:
+            self._check(L.salec_place_projectile(h, int(pj["mat"]), float(pj["radius"]), float(pj["zc"]),
+                                                 float(pj["vz"]), float(pj.get("rho", 0.0)),
+                                                 float(pj.get("I0", 0.0))))
+        self._check(L.salec_finalize(h))
+
+    def _check(self, st, h="self"):
+        if st != SALEC_OK:
+            hh = self._h if h == "self" else None
+            msg = load().salec_last_error(hh).decode() if hh else ""
+            raise SalecError(st, msg)
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h:
+            load().salec_destroy(h)
+            self._h = None
+
+    @property
+    def handle(self):
+        return self._h
+
+    def step(self, n: int) -> None:
+        self._check(load().salec_step(self._h, int(n)))
+
+    def scalars(self, check: bool = False) -> dict:
+        out = np.zeros(8)
+        st = load().salec_get_scalars(self._h, out.ctypes.data_as(C.POINTER(C.c_double)))
+        if st not in (SALEC_OK, SALEC_EUNSTABLE) or (check and st != SALEC_OK):
+            self._check(st)
+        return {"t": out[0], "dt": out[1], "nstep": int(out[2]), "status": int(out[3]),
+                "mass_out": out[4], "mass_discarded": out[5], "mass_pml": out[6], "zmom_out": out[7]}
+
+    def set_time(self, t: float, dt_prev: float) -> None:
+        self._check(load().salec_set_time(self._h, float(t), float(dt_prev)))
+
+    def _shape(self, name):
+        return (self.nz + 1, self.nr + 1) if name in VERTEX_FIELDS else (self.nz, self.nr)
+
+    def get(self, name: str) -> np.ndarray:
+        out = np.zeros(self._shape(name))
+        self._check(load().salec_get_field(self._h, FIELDS[name], out.ctypes.data_as(C.POINTER(C.c_double)), out.size))
+        return out
+
+    def set(self, name: str, values) -> None:
+        arr = np.ascontiguousarray(values, dtype=np.float64).reshape(self._shape(name))
+        self._check(load().salec_set_field(self._h, FIELDS[name], arr.ctypes.data_as(C.POINTER(C.c_double)), arr.size))
+
+    def conservation(self) -> dict:
+        out = np.zeros(4)
+        self._check(load().salec_conservation(self._h, out.ctypes.data_as(C.POINTER(C.c_double))))
+        return {"mass": out[0], "zmom": out[1], "ke": out[2], "ie": out[3]}
+
+    def crater(self, z_surface: float, npts: int = 64):
+        prof = np.zeros(max(npts, 1))
+        h = np.zeros(self.nr)
+        d, D = C.c_double(), C.c_double()
+        self._check(load().salec_crater_profile(self._h, float(z_surface), int(npts),
+                                                prof.ctypes.data_as(C.POINTER(C.c_double)),
+                                                h.ctypes.data_as(C.POINTER(C.c_double)), C.byref(d), C.byref(D)))
+        return {"depth": d.value, "diameter": D.value, "profile": prof[:npts], "heights": h}
+
+    def surface_heights(self) -> np.ndarray:
+        return self.crater(0.0, 0)["heights"]
+
+    def checkpoint_bytes(self) -> int:
+        n = C.c_size_t()
+        self._check(load().salec_checkpoint_bytes(self._h, C.byref(n)))
+        return n.value
+
+    def get_state(self) -> np.ndarray:
+        buf = np.zeros(self.checkpoint_bytes(), dtype=np.uint8)
+        self._check(load().salec_get_state(self._h, C.c_void_p(buf.ctypes.data), buf.size))
+        return buf
+
+    def set_state(self, buf) -> None:
+        b = np.ascontiguousarray(buf, dtype=np.uint8)
+        self._check(load().salec_set_state(self._h, C.c_void_p(b.ctypes.data), b.size))
+
+    def launches_per_step(self) -> int:
+        return load().salec_launches_per_step(self._h)
+
+    def set_kernel_timing(self, on: bool) -> None:
+        self._check(load().salec_set_kernel_timing(self._h, 1 if on else 0))
+
+    def kernel_times(self) -> tuple[dict, int]:
+        """Mean per-kernel duration (ms) over the steps recorded since the last read."""
+        n = self.launches_per_step()
+        out = np.zeros(n)
+        steps = C.c_int()
+        self._check(load().salec_kernel_times(self._h, out.ctypes.data_as(C.POINTER(C.c_double)), n, C.byref(steps)))
+        return {load().salec_kernel_name(k).decode(): float(out[k]) for k in range(n)}, steps.value

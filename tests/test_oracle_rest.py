@@ -9,7 +9,7 @@ from oracle import oracle as O
 
 
 def test_uniform_gas_box_is_bitwise_at_rest():
-    s = O.OracleSim(OC.gas_box_spec(7, 9))
+    s = O.OracleSim(OC.gas_box_spec(37, 29))
     rho0, I0 = s.get("rho0").copy(), s.get("I").copy()
     s.step(200)
     assert np.all(s.get("vr") == 0.0) and np.all(s.get("vz") == 0.0)
