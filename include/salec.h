@@ -184,6 +184,7 @@ salec_status salec_set_kernel_timing(salec_ctx* ctx, int on);
 salec_status salec_kernel_times(salec_ctx* ctx, double* avg_ms, int n, int* steps);
 const char* salec_kernel_name(int k);
 
+
 const char* salec_last_error(const salec_ctx* ctx);
 void salec_destroy(salec_ctx* ctx);
 

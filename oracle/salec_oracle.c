@@ -776,7 +776,7 @@ static void phase2_cell(orc_sim* s)
                 double Vm = fm * V;
                 double VmL = Vm + (fm / phi) * dVmat;
                 if (!(VmL > 0.0)) s->status |= 1;
-                s->rhoL[m][c] = s->rho[m][c] * Vm / VmL;
+                s->rhoL[m][c] = s->rho[m][c] * (Vm / VmL);
                 s->fL[m][c] = VmL / VL;
             }
             /* strength and damage */

@@ -23,7 +23,7 @@ constexpr size_t kAlign = 256;
 // Offsets of every array inside the state buffer.  The persistent part (scalars, tables,
 // fields, PML auxiliaries) comes first so a checkpoint is one contiguous range.
 struct Layout {
-    size_t scal, A_R, A_Z, V, invV, p0, rho_ref, I_ref, dB_c, dB_v, dR_c, dR_v;
+    size_t scal, A_R, A_Z, V, invV, inv2rc, p0, rho_ref, I_ref, dB_c, dB_v, dR_c, dR_v;
     size_t fr[kMaxMat], I, s01, s2d, pmax, v;
     size_t pb_c, pb_psi2, pb_v, pr_c, pr_psi2, pr_v;
     size_t persist_end;
@@ -51,6 +51,7 @@ Layout make_layout(const salec_grid& g)
     L.A_Z = take(cur, nr * d);
     L.V = take(cur, nr * d);
     L.invV = take(cur, nr * d);
+    L.inv2rc = take(cur, nr * d);
     L.p0 = take(cur, nz * d);
     L.rho_ref = take(cur, nz * d);
     L.I_ref = take(cur, nz * d);
@@ -159,6 +160,7 @@ static Mat to_mat(const salec_material& s)
     memset(&m, 0, sizeof(m));
     m.eos = s.eos; m.strength = s.strength;
     m.rho0 = s.rho0; m.inv_rho0 = 1.0 / s.rho0;
+    m.rho0sq_E0 = s.eos == SALEC_EOS_TILLOTSON ? s.rho0 * s.rho0 / s.E0 : 0.0;
     m.A = s.A; m.B = s.B; m.E0 = s.E0; m.a = s.a; m.b = s.b; m.alpha = s.alpha; m.beta = s.beta;
     m.Eiv = s.Eiv; m.Ecv = s.Ecv;
     m.inv_dE = (s.Ecv > s.Eiv) ? 1.0 / (s.Ecv - s.Eiv) : 0.0;
@@ -196,7 +198,7 @@ static void fill_params(salec_ctx* ctx)
     p.pb_c = at<double2>(ctx, L.pb_c); p.pb_psi2 = at<double>(ctx, L.pb_psi2); p.pb_v = at<double4_32a>(ctx, L.pb_v);
     p.pr_c = at<double2>(ctx, L.pr_c); p.pr_psi2 = at<double>(ctx, L.pr_psi2); p.pr_v = at<double4_32a>(ctx, L.pr_v);
     p.A_R = at<double>(ctx, L.A_R); p.A_Z = at<double>(ctx, L.A_Z); p.V = at<double>(ctx, L.V);
-    p.invV = at<double>(ctx, L.invV); p.p0 = at<double>(ctx, L.p0); p.rho_ref = at<double>(ctx, L.rho_ref);
+    p.invV = at<double>(ctx, L.invV); p.inv2rc = at<double>(ctx, L.inv2rc); p.p0 = at<double>(ctx, L.p0); p.rho_ref = at<double>(ctx, L.rho_ref);
     p.I_ref = at<double>(ctx, L.I_ref); p.dB_c = at<double>(ctx, L.dB_c); p.dB_v = at<double>(ctx, L.dB_v);
     p.dR_c = at<double>(ctx, L.dR_c); p.dR_v = at<double>(ctx, L.dR_v);
     p.PM = at<double2>(ctx, L.PM); p.pbphi = at<double2>(ctx, L.pbphi); p.vL = at<double2>(ctx, L.vL);
@@ -464,8 +466,11 @@ salec_status salec_finalize(salec_ctx* ctx)
     }
     for (int i = nr - pr; i < nr; ++i) dRc[i] = profile(c, pr, g.dx, (double)i + 0.5 - (double)(nr - pr), g.pml_R);
     for (int i = nr - pr + 1; i <= nr; ++i) dRv[i] = profile(c, pr, g.dx, (double)(i - (nr - pr)), g.pml_R);
-    std::vector<double> invV(nr);
-    for (int i = 0; i < nr; ++i) invV[i] = 1.0 / ctx->Vc[i];
+    std::vector<double> invV(nr), inv2rc(nr);
+    for (int i = 0; i < nr; ++i) {
+        invV[i] = 1.0 / ctx->Vc[i];
+        inv2rc[i] = 1.0 / (2.0 * (((double)i + 0.5) * g.dx));
+    }
     // scalars
     DevScalars s;
     memset(&s, 0, sizeof(s));
@@ -481,6 +486,7 @@ salec_status salec_finalize(salec_ctx* ctx)
     up(L.A_Z, ctx->A_Z.data(), nr * sizeof(double));
     up(L.V, ctx->Vc.data(), nr * sizeof(double));
     up(L.invV, invV.data(), nr * sizeof(double));
+    up(L.inv2rc, inv2rc.data(), nr * sizeof(double));
     up(L.p0, p0.data(), nz * sizeof(double));
     up(L.rho_ref, rref.data(), nz * sizeof(double));
     up(L.I_ref, Iref.data(), nz * sizeof(double));

@@ -18,7 +18,7 @@ constexpr int kThreads = kBlockX * kBlockY;
 // Material constants with the derived quantities the kernels use.
 struct Mat {
     int eos, strength;
-    double rho0, inv_rho0, A, B, E0, a, b, alpha, beta, Eiv, Ecv, inv_dE, gamma;
+    double rho0, inv_rho0, rho0sq_E0, A, B, E0, a, b, alpha, beta, Eiv, Ecv, inv_dE, gamma;
     double Yi0, mui, Yim, Yd0, mud, Ydm, inv_Yspan, G, eps_fb, B_dam, p_bd, p_t, c2_floor;
 };
 
@@ -52,6 +52,7 @@ struct Ptrs {
     const double* A_Z;      // nr vertical face areas
     const double* V;        // nr cell volumes
     const double* invV;     // nr
+    const double* inv2rc;   // nr  1 / (2 r_c)
     const double* p0;       // nz reference pressure per row
     const double* rho_ref;  // nz
     const double* I_ref;    // nz
@@ -98,13 +99,14 @@ __host__ __device__ inline void eos_eval(const Mat& m, double rho, double I_in, 
         c2_out = m.gamma * gm1 * I;
         return;
     }
-    const double eta = rho * m.inv_rho0;
-    const double mu = eta - 1.0;
-    const double eta2E0 = m.E0 * eta * eta;
-    const double w0 = I / eta2E0 + 1.0;
+    // two divisions: 1/rho and 1/w0 (1/(E0 eta^2) = (rho0^2/E0) / rho^2)
+    const double irho = 1.0 / rho;
+    const double mu = (rho - m.rho0) * m.inv_rho0;
+    const double ie = m.rho0sq_E0 * irho * irho;        // 1 / (E0 eta^2)
+    const double w0 = I * ie + 1.0;
     const double iw = 1.0 / w0;
     const double bw = m.b * iw;                         // b / w0
-    const double dw = m.b * I * iw * iw / eta2E0;       // b I / (w0^2 E0 eta^2)
+    const double dw = bw * iw * I * ie;                 // b I / (w0^2 E0 eta^2)
     // compressed branch and its partial derivatives
     const double pc = (m.a + bw) * rho * I + mu * (m.A + m.B * mu);
     const double pc_r = (m.a + bw) * I + 2.0 * dw * I + (m.A + 2.0 * m.B * mu) * m.inv_rho0;
@@ -113,7 +115,6 @@ __host__ __device__ inline void eos_eval(const Mat& m, double rho, double I_in, 
     if (rho >= m.rho0 || I <= m.Eiv) {
         p = pc; p_r = pc_r; p_I = pc_I;
     } else {
-        const double irho = 1.0 / rho;
         const double x = m.rho0 * irho - 1.0;            // rho0/rho - 1
         const double x_r = -m.rho0 * irho * irho;        // dx/drho
         const double ea = exp(-m.alpha * x * x);
@@ -135,7 +136,7 @@ __host__ __device__ inline void eos_eval(const Mat& m, double rho, double I_in, 
             p_I = we * pe_I + wc * pc_I + (pe - pc) * m.inv_dE;
         }
     }
-    double c2 = p_r + p / (rho * rho) * p_I;
+    double c2 = p_r + p * irho * irho * p_I;
     if (!(c2 > m.c2_floor)) c2 = m.c2_floor;
     p_out = p;
     c2_out = c2;
@@ -162,4 +163,21 @@ int launches_per_step();
 int cell_blocks(int nr, int nz);
 int vertex_blocks(int nr, int nz);
 
+}  // namespace salec
+
+namespace salec {
+// Sign tests on the bit pattern: integer instructions instead of FP64 compares (which
+// issue on the FP64 pipe, the bottleneck of the FP64 form).  pos(x): x > 0 (or +NaN);
+// neg(x): x < 0 or x == -0.0 (callers treat -0.0 like 0 by moving zero volume).
+__device__ __forceinline__ bool pos(double x) { return __double_as_longlong(x) > 0; }
+__device__ __forceinline__ bool neg(double x) { return __double_as_longlong(x) < 0; }
+__device__ __forceinline__ bool is_nan(double x)
+{
+    return (__double_as_longlong(x) & 0x7fffffffffffffffLL) > 0x7ff0000000000000LL;
+}
+// max of two non-negative doubles by their bit patterns
+__device__ __forceinline__ double max_nonneg(double a, double b)
+{
+    return __longlong_as_double(max(__double_as_longlong(a), __double_as_longlong(b)));
+}
 }  // namespace salec

@@ -54,16 +54,18 @@ __global__ void __launch_bounds__(kThreads) k_phase0(Params P)
     const int j = blockIdx.y * kBlockY + threadIdx.y;
     const int nr = P.nr;
     const Ptrs& p = P.p;
-    double cand = INFINITY;
+    // largest |v| + c of the block; min over cells of dx / (|v| + c) = dx / max(|v| + c)
+    // exactly (correctly rounded division is monotonic), so one division per step suffices
+    double speed = 0.0;
     if (i < nr && j < P.nz) {
         const int c = j * nr + i;
-        double phat = 0.0, phi = 0.0, mass = 0.0, c2m = 0.0;
+        double phat = 0.0, phi = 0.0, mass = 0.0, c2m = 0.0, p1 = 0.0, r1 = 0.0;
         const double Ic = p.I[c];
         const double D = STR ? p.s2d[c].y : 0.0;
 #pragma unroll
         for (int m = 0; m < NM; ++m) {
             const double2 fr = p.fr[m][c];
-            if (fr.x > 0.0) {
+            if (pos(fr.x)) {
                 double pm, c2;
                 eos_eval(P.mat[m], fr.y, Ic, pm, c2);
                 const double pmin = (1.0 - D) * P.mat[m].p_t;
@@ -71,11 +73,13 @@ __global__ void __launch_bounds__(kThreads) k_phase0(Params P)
                 phat += fr.x * pm;
                 phi += fr.x;
                 mass += fr.x * fr.y;
-                c2m = c2 > c2m ? c2 : c2m;
+                c2m = max_nonneg(c2m, c2);
+                p1 = pm;
+                r1 = fr.y;
             }
         }
         double Pc = 0.0, pbar = 0.0;
-        if (phi > 0.0) {
+        if (pos(phi)) {
             const int nv = nr + 1;
             const double2 va = p.v[j * nv + i], vb = p.v[j * nv + i + 1];
             const double2 vc = p.v[(j + 1) * nv + i + 1], vd = p.v[(j + 1) * nv + i];
@@ -83,37 +87,42 @@ __global__ void __launch_bounds__(kThreads) k_phase0(Params P)
             const double uB = 0.5 * (va.y + vb.y), uT = 0.5 * (vd.y + vc.y);
             const double div = (p.A_R[i + 1] * uR - p.A_R[i] * uL + p.A_Z[i] * (uT - uB)) * p.invV[i];
             const double cs = sqrt(c2m);
+            // one material: p_bar = p and rho_bar = rho; otherwise divide by Phi once
+            const double iphi = NM == 1 ? 1.0 : 1.0 / phi;
+            pbar = NM == 1 ? p1 : phat * iphi;
             double q = 0.0;
-            if (div < 0.0) {
-                const double rb = mass / phi;
+            if (neg(div)) {
+                const double rb = NM == 1 ? r1 : mass * iphi;
                 q = rb * (P.cq * P.dx2 * div * div - P.cl * P.dx * cs * div);
             }
             Pc = phat + phi * q;
-            pbar = phat / phi;
             const double over = pbar - p.p0[j];
             if (over > p.pmax[c]) p.pmax[c] = over;
             double w = va.x * va.x + va.y * va.y;
-            w = fmax(w, vb.x * vb.x + vb.y * vb.y);
-            w = fmax(w, vc.x * vc.x + vc.y * vc.y);
-            w = fmax(w, vd.x * vd.x + vd.y * vd.y);
-            cand = P.dx / (sqrt(w) + cs);
-            if (cand != cand) atomicOr(&p.scal->status, 2);
+            w = max_nonneg(w, vb.x * vb.x + vb.y * vb.y);
+            w = max_nonneg(w, vc.x * vc.x + vc.y * vc.y);
+            w = max_nonneg(w, vd.x * vd.x + vd.y * vd.y);
+            speed = sqrt(w) + cs;
+            if (is_nan(speed)) atomicOr(&p.scal->status, 2);
         }
         p.PM[c] = make_double2(Pc, mass * p.V[i]);
         p.pbphi[c] = make_double2(pbar, phi);
     }
-    // block minimum, then the last block to finish reduces the minima
-    __shared__ double sh[kThreads / 32];
+    // block maximum (on the bit patterns of the non-negative speeds), then the last block
+    // to finish reduces the block maxima
+    __shared__ long long sh[kThreads / 32];
     __shared__ bool last;
     const int tid = threadIdx.y * kBlockX + threadIdx.x;
-    cand = warp_min(cand);
-    if ((tid & 31) == 0) sh[tid >> 5] = cand;
+    long long sb = __double_as_longlong(speed);
+    for (int o = 16; o > 0; o >>= 1) sb = max(sb, __shfl_down_sync(0xffffffffu, sb, o));
+    if ((tid & 31) == 0) sh[tid >> 5] = sb;
     __syncthreads();
     const int nblk = gridDim.x * gridDim.y;
+    long long* part = reinterpret_cast<long long*>(p.partial);
     if (tid == 0) {
-        double b = sh[0];
-        for (int w = 1; w < kThreads / 32; ++w) b = fmin(b, sh[w]);
-        p.partial[blockIdx.y * gridDim.x + blockIdx.x] = b;
+        long long b = sh[0];
+        for (int w = 1; w < kThreads / 32; ++w) b = max(b, sh[w]);
+        part[blockIdx.y * gridDim.x + blockIdx.x] = b;
         __threadfence();
         const unsigned prev = atomicAdd(&p.scal->counter, 1u);
         last = (prev == (unsigned)(nblk - 1));
@@ -121,17 +130,17 @@ __global__ void __launch_bounds__(kThreads) k_phase0(Params P)
     __syncthreads();
     if (!last) return;
     __threadfence();
-    double m = INFINITY;
-    for (int k = tid; k < nblk; k += kThreads) m = fmin(m, __ldcg(&p.partial[k]));
-    m = warp_min(m);
+    long long m = 0;
+    for (int k = tid; k < nblk; k += kThreads) m = max(m, __ldcg(&part[k]));
+    for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_down_sync(0xffffffffu, m, o));
     if ((tid & 31) == 0) sh[tid >> 5] = m;
     __syncthreads();
     if (tid == 0) {
-        double b = sh[0];
-        for (int w = 1; w < kThreads / 32; ++w) b = fmin(b, sh[w]);
+        long long b = sh[0];
+        for (int w = 1; w < kThreads / 32; ++w) b = max(b, sh[w]);
         DevScalars* s = p.scal;
         double dt = P.growth * s->dt_prev;
-        const double cdt = P.cfl * b;
+        const double cdt = P.cfl * (P.dx / __longlong_as_double(b));
         dt = cdt < dt ? cdt : dt;
         dt = P.dt_max < dt ? P.dt_max : dt;
         if (dt < P.dt_min) s->status |= 4;
@@ -213,7 +222,7 @@ __global__ void __launch_bounds__(kThreads) k_phase1(Params P)
     }
     const double2 vn = p.v[v];
     double vr = 0.0, vz = 0.0;
-    if (mass > 0.0) {
+    if (pos(mass)) {
         const double im = 1.0 / mass;
         vr = vn.x + dt * ((Fr - psr) * im);
         vz = vn.y + dt * ((Fz - psz) * im - P.g);
@@ -243,7 +252,7 @@ __global__ void __launch_bounds__(kThreads) k_phase2(Params P)
     const Ptrs& p = P.p;
     const int c = j * nr + i;
     const double phi = p.pbphi[c].y;
-    if (!(phi > 0.0)) {
+    if (!pos(phi)) {
 #pragma unroll
         for (int m = 0; m < NM; ++m) p.frL[m][c] = make_double2(0.0, 0.0);
         p.VIL[c] = make_double2(p.V[i], 0.0);
@@ -261,8 +270,7 @@ __global__ void __launch_bounds__(kThreads) k_phase2(Params P)
     const double err = (uR - uL) * idx;
     const double ezz = (uT - uB) * idx;
     const double V = p.V[i];
-    const double rc = (i + 0.5) * dx;
-    const double ett = (uR + uL) / (2.0 * rc);
+    const double ett = (uR + uL) * p.inv2rc[i];
     const double rad_flux = p.A_R[i + 1] * uR - p.A_R[i] * uL;
     const double ver_flux = p.A_Z[i] * (uT - uB);
     const double dV = dt * (rad_flux + ver_flux);
@@ -298,7 +306,7 @@ __global__ void __launch_bounds__(kThreads) k_phase2(Params P)
     }
     const double dE = -Pc * dV + work - dt * psi2;
     const double Ic = p.I[c];
-    const double IL = M > 0.0 ? Ic + dE / M : Ic;
+    const double IL = pos(M) ? Ic + dE / M : Ic;
     p.VIL[c] = make_double2(VL, IL);
     // volume partition: compression closes void first; expansion shared pro rata with void
     double Vvoid = (1.0 - phi) * V;
@@ -310,18 +318,17 @@ __global__ void __launch_bounds__(kThreads) k_phase2(Params P)
     } else {
         dVmat = phi * dV;
     }
-    const double iVL = 1.0 / VL;
-    const double iphi = 1.0 / phi;
     bool bad = false;
     double G = 0.0, Y = 0.0, iepsf = 0.0;
 #pragma unroll
     for (int m = 0; m < NM; ++m) {
         const double2 fr = p.fr[m][c];
-        if (fr.x > 0.0) {
+        if (pos(fr.x)) {
             const double Vm = fr.x * V;
-            const double VmL = Vm + fr.x * iphi * dVmat;
-            bad |= !(VmL > 0.0);
-            p.frL[m][c] = make_double2(VmL * iVL, fr.y * Vm / VmL);
+            // one material: f_m / Phi = 1; true divisions keep a resting cell exact
+            const double VmL = NM == 1 ? Vm + dVmat : Vm + fr.x / phi * dVmat;
+            bad |= !pos(VmL);
+            p.frL[m][c] = make_double2(VmL / VL, fr.y * (Vm / VmL));
             if (STR && P.mat[m].strength == SALEC_STRENGTH_COLLINS) {
                 const Mat& mm = P.mat[m];
                 const double pb = p.pbphi[c].x;
@@ -337,8 +344,9 @@ __global__ void __launch_bounds__(kThreads) k_phase2(Params P)
     }
     if (bad) atomicOr(&p.scal->status, 1);
     if (STR) {
+        const double iphi = 1.0 / phi;
         G *= iphi; Y *= iphi; iepsf *= iphi;
-        if (G > 0.0) {
+        if (pos(G)) {
             const double omega = 0.5 * (dvr_dz - dvz_dr);
             const double erz = 0.5 * (dvr_dz + dvz_dr);
             const double tr3 = (err + ezz + ett) * (1.0 / 3.0);
@@ -446,34 +454,34 @@ __global__ void __launch_bounds__(kThreads) k_phase3a(Params P)
         {
             const double dV = radial_dV(P, i, j, dt);
             double sm = 0.0;
-            if (dV > 0.0) { move<NM, STR>(P, c - 1, dV, 1.0, acc, fm, fe); sm = fm; FRm -= fm; FRe -= fe; }
-            else if (dV < 0.0) { move<NM, STR>(P, c, -dV, -1.0, acc, fm, fe); sm = -fm; FRm += fm; FRe += fe; }
+            if (pos(dV)) { move<NM, STR>(P, c - 1, dV, 1.0, acc, fm, fe); sm = fm; FRm -= fm; FRe -= fe; }
+            else if (neg(dV)) { move<NM, STR>(P, c, -dV, -1.0, acc, fm, fe); sm = -fm; FRm += fm; FRe += fe; }
             p.dMR[j * (nr + 1) + i] = sm;
         }
         // right face r_{i+1}
         {
             const double dV = radial_dV(P, i + 1, j, dt);
-            if (dV > 0.0) { move<NM, STR>(P, c, dV, -1.0, acc, fm, fe); FRm += fm; FRe += fe; }
-            else if (dV < 0.0) { move<NM, STR>(P, c + 1, -dV, 1.0, acc, fm, fe); FRm -= fm; FRe -= fe; }
+            if (pos(dV)) { move<NM, STR>(P, c, dV, -1.0, acc, fm, fe); FRm += fm; FRe += fe; }
+            else if (neg(dV)) { move<NM, STR>(P, c + 1, -dV, 1.0, acc, fm, fe); FRm -= fm; FRe -= fe; }
             if (i == nr - 1) p.dMR[j * (nr + 1) + nr] = 0.0;
         }
         // bottom face z_j
         {
             const double dV = vertical_dV(P, i, j, dt);
             double sm = 0.0;
-            if (dV > 0.0) { move<NM, STR>(P, c - nr, dV, 1.0, acc, fm, fe); sm = fm; FZm -= fm; FZe -= fe; }
-            else if (dV < 0.0) { move<NM, STR>(P, c, -dV, -1.0, acc, fm, fe); sm = -fm; FZm += fm; FZe += fe; }
+            if (pos(dV)) { move<NM, STR>(P, c - nr, dV, 1.0, acc, fm, fe); sm = fm; FZm -= fm; FZe -= fe; }
+            else if (neg(dV)) { move<NM, STR>(P, c, -dV, -1.0, acc, fm, fe); sm = -fm; FZm += fm; FZe += fe; }
             p.dMZ[j * nr + i] = sm;
         }
         // top face z_{j+1}: above the domain only outflow (inflow is void)
         {
             const double dV = vertical_dV(P, i, j + 1, dt);
             double sm = 0.0;
-            if (dV > 0.0) {
+            if (pos(dV)) {
                 move<NM, STR>(P, c, dV, -1.0, acc, fm, fe);
                 FZm += fm; FZe += fe; sm = fm;
                 if (j == nz - 1) t_out += fm;
-            } else if (dV < 0.0 && j + 1 < nz) {
+            } else if (neg(dV) && j + 1 < nz) {
                 move<NM, STR>(P, c + nr, -dV, 1.0, acc, fm, fe); FZm -= fm; FZe -= fe;
             }
             if (j == nz - 1) p.dMZ[nz * nr + i] = sm;
@@ -481,7 +489,6 @@ __global__ void __launch_bounds__(kThreads) k_phase3a(Params P)
         // new state in increment form: q' = q^L + (net q-content flux - q^L net carrier
         // flux) / new carrier amount (exact when nothing flows)
         const double V = p.V[i];
-        const double iV = p.invV[i];
         double Vm[NM], Mm[NM], rn[NM];
         double MLtot = 0.0, VLmat = 0.0, dMtot = 0.0, dVtot = 0.0;
 #pragma unroll
@@ -493,12 +500,12 @@ __global__ void __launch_bounds__(kThreads) k_phase3a(Params P)
             dMtot += acc.Mm[m]; dVtot += acc.Vm[m];
             Vm[m] = VmL + acc.Vm[m];
             Mm[m] = MmL + acc.Mm[m];
-            rn[m] = Vm[m] > 0.0 ? fl.y + (acc.Mm[m] - fl.y * acc.Vm[m]) / Vm[m] : 0.0;
+            rn[m] = pos(Vm[m]) ? fl.y + (acc.Mm[m] - fl.y * acc.Vm[m]) / Vm[m] : 0.0;
         }
         const double Mtot = MLtot + dMtot, Vtot = VLmat + dVtot;
-        double Ic = Mtot > 0.0 ? vil.y + (acc.E - vil.y * dMtot) / Mtot : 0.0;
+        double Ic = pos(Mtot) ? vil.y + (acc.E - vil.y * dMtot) / Mtot : 0.0;
         double s0 = 0.0, s1 = 0.0, s2 = 0.0, Dm = 0.0;
-        if (STR && Vtot > 0.0) {
+        if (STR && pos(Vtot)) {
             const double iv = 1.0 / Vtot;
             const double2 a = p.sL01[c], b = p.sL2d[c];
             s0 = a.x + (acc.S[0] - a.x * dVtot) * iv;
@@ -506,10 +513,11 @@ __global__ void __launch_bounds__(kThreads) k_phase3a(Params P)
             s2 = b.x + (acc.S[2] - b.x * dVtot) * iv;
             Dm = b.y + (acc.S[3] - b.y * dVtot) * iv;
         }
-        double Mkeep = 0.0, Vkeep = 0.0;
+        double Mkeep = 0.0, Vkeep = 0.0, fnew[NM];
 #pragma unroll
         for (int m = 0; m < NM; ++m) {
-            if (Vm[m] * iV < P.f_min) {
+            fnew[m] = Vm[m] / V;    // a true division: exact 1 for a full resting cell
+            if (fnew[m] < P.f_min) {
                 t_disc += Mm[m];
                 Vm[m] = 0.0;
                 Mm[m] = 0.0;
@@ -518,7 +526,7 @@ __global__ void __launch_bounds__(kThreads) k_phase3a(Params P)
             Mkeep += Mm[m];
             Vkeep += Vm[m];
         }
-        if (!(Mkeep > 0.0)) { Ic = 0.0; s0 = s1 = s2 = Dm = 0.0; }
+        if (!pos(Mkeep)) { Ic = 0.0; s0 = s1 = s2 = Dm = 0.0; }
         double kappa = 1.0;
         const bool inB = j < P.pb, inR = i >= nr - P.pr;
         if (inB || inR) {
@@ -540,7 +548,7 @@ __global__ void __launch_bounds__(kThreads) k_phase3a(Params P)
                 p.pr_c[k] = a;
                 dsum += d; phi1 += a.x; phi3 += a.y;
             }
-            if (Mkeep > 0.0 && dsum > 0.0) {
+            if (pos(Mkeep) && pos(dsum)) {
                 const double Mref = Vkeep * p.rho_ref[j];
                 const double dM = -dt * (dsum * (Mkeep - Mref) + phi1);
                 const double dEp = -dt * (dsum * (Mkeep * Ic - Mref * p.I_ref[j]) + phi3);
@@ -553,8 +561,8 @@ __global__ void __launch_bounds__(kThreads) k_phase3a(Params P)
         }
 #pragma unroll
         for (int m = 0; m < NM; ++m) {
-            if (Vm[m] > 0.0)
-                p.fr[m][c] = make_double2(Vm[m] * iV, kappa * rn[m]);
+            if (pos(Vm[m]))
+                p.fr[m][c] = make_double2(fnew[m], kappa * rn[m]);
             else
                 p.fr[m][c] = make_double2(0.0, 0.0);
         }
@@ -619,35 +627,36 @@ __global__ void __launch_bounds__(kThreads) k_phase3b(Params P)
         double outZr = 0.0, outZz = 0.0, inZr = 0.0, inZz = 0.0;
         if (i > 0) {   // face to (i-1, j)
             const double f = dual_R(P, i - 1, j);
-            const double2 w = f > 0.0 ? p.vL[v - 1] : vL;
+            const double2 w = pos(f) ? p.vL[v - 1] : vL;
             inRr = f * w.x; inRz = f * w.y;
             m += f; kin += 0.5 * f * (w.x * w.x + w.y * w.y);
         }
         if (i < nr) {  // face to (i+1, j)
             const double f = dual_R(P, i, j);
-            const double2 w = f > 0.0 ? vL : p.vL[v + 1];
+            const double2 w = pos(f) ? vL : p.vL[v + 1];
             outRr = f * w.x; outRz = f * w.y;
             m -= f; kin -= 0.5 * f * (w.x * w.x + w.y * w.y);
         }
         if (j > 0) {   // face to (i, j-1)
             const double f = dual_Z(P, i, j - 1);
-            const double2 w = f > 0.0 ? p.vL[v - nv] : vL;
+            const double2 w = pos(f) ? p.vL[v - nv] : vL;
             inZr = f * w.x; inZz = f * w.y;
             m += f; kin += 0.5 * f * (w.x * w.x + w.y * w.y);
         }
         {              // face to (i, j+1), or out through the top
             const double f = dual_Z(P, i, j);
-            const double2 w = (f > 0.0 || j == nz) ? vL : p.vL[v + nv];
+            const double2 w = (pos(f) || j == nz) ? vL : p.vL[v + nv];
             outZr = f * w.x; outZz = f * w.y;
             m -= f; kin -= 0.5 * f * (w.x * w.x + w.y * w.y);
             if (j == nz) t_zmom += outZz;
         }
         pr += (inRr - outRr) + (inZr - outZr);
         pz += (inRz - outRz) + (inZz - outZz);
-        double kheat = 0.0;
-        if (m > 0.0) {
-            const double dKr = kin - 0.5 * (pr * pr + pz * pz) / m;
-            kheat = (p.dK[v] + dKr) / m;
+        double kheat = 0.0, im = 0.0;
+        if (pos(m)) {
+            im = 1.0 / m;
+            const double dKr = kin - 0.5 * (pr * pr + pz * pz) * im;
+            kheat = (p.dK[v] + dKr) * im;
         }
         p.kheat[v] = kheat;
         double dsum = 0.0, a2r = 0.0, a2z = 0.0;
@@ -680,17 +689,17 @@ __global__ void __launch_bounds__(kThreads) k_phase3b(Params P)
             const int ci = (k == 0 || k == 3) ? i - 1 : i;
             const int cj = (k < 2) ? j - 1 : j;
             if (ci < 0 || ci >= nr || cj < 0 || cj >= nz) continue;
-            for (int mm = 0; mm < P.nmat; ++mm) occupied |= p.fr[mm][cj * nr + ci].x > 0.0;
+            for (int mm = 0; mm < P.nmat; ++mm) occupied |= pos(p.fr[mm][cj * nr + ci].x);
         }
         double vr = 0.0, vz = 0.0;
-        if (m > 0.0 && occupied) { vr = pr / m; vz = pz / m; }
+        if (pos(m) && occupied) { vr = pr * im; vz = pz * im; }
         if (i == 0 || i == nr) vr = 0.0;
         if (j == 0) {
             vz = 0.0;
             if (P.bc_bottom == SALEC_BOTTOM_NOSLIP) vr = 0.0;
         }
         if (j == nz && P.bc_top == SALEC_TOP_WALL) vz = 0.0;
-        if (vr != vr || vz != vz) atomicOr(&p.scal->status, 2);
+        if (is_nan(vr) || is_nan(vz)) atomicOr(&p.scal->status, 2);
         p.v[v] = make_double2(vr, vz);
     }
     __shared__ double sh[kThreads / 32];
@@ -716,7 +725,7 @@ __global__ void __launch_bounds__(kThreads) k_phase3c(Params P)
             const double2 fr = p.fr[m][c];
             M += fr.x * fr.y;
         }
-        if (M > 0.0) {
+        if (pos(M)) {
             const double add = 0.25 * (p.kheat[j * nv + i] + p.kheat[j * nv + i + 1] +
                                        p.kheat[(j + 1) * nv + i + 1] + p.kheat[(j + 1) * nv + i]);
             p.I[c] += add;

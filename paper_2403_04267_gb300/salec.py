@@ -259,3 +259,4 @@ class Sim:
         steps = C.c_int()
         self._check(load().salec_kernel_times(self._h, out.ctypes.data_as(C.POINTER(C.c_double)), n, C.byref(steps)))
         return {load().salec_kernel_name(k).decode(): float(out[k]) for k in range(n)}, steps.value
+
