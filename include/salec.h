@@ -184,7 +184,31 @@ salec_status salec_set_kernel_timing(salec_ctx* ctx, int on);
 salec_status salec_kernel_times(salec_ctx* ctx, double* avg_ms, int n, int* steps);
 const char* salec_kernel_name(int k);
 
+/* Courant time step without any allocation, for callers that cannot allocate or lend
+ * device memory (an external memory manager owns every allocation, a plug-in sees only
+ * another program's field pointers, the allocator is locked).  The paper has no
+ * counterpart; it is the step size salec_step's first kernel computes, evaluated on
+ * caller-owned device buffers:
+ *   grid    nr, nz, nmat, dx, cfl, dt_growth, dt_max are used
+ *   mats    nmat materials (host)
+ *   fr[m]   device pointer to nr*nz (f_m, rho_m) pairs of doubles, row-major [j][i]
+ *   I       device pointer to nr*nz specific internal energies
+ *   D       device pointer to nr*nz damage values, or NULL (not needed for dt)
+ *   v       device pointer to (nr+1)*(nz+1) (v_r, v_z) pairs
+ *   dt_prev the previous step (growth limit); *dt_out receives the step (host).
+ * The call enqueues a memset and one kernel on `stream` and synchronises it.  Its scratch
+ * is file-scope device memory of fixed size (65536 blocks of 32 x 8 cells, e.g. 4096 x
+ * 4096 cells; larger grids return SALEC_EINVAL) held by every device that loads the
+ * library until the process exits.  The first call on a device looks up that memory's
+ * address with the device current; make it before any stream capture.  All calls share
+ * the scratch: calls that overlap on the GPU (different streams or threads) race.
+ * Failures without a context are described by salec_last_error(NULL). */
+salec_status salec_courant_dt_noalloc(const salec_grid* grid, const salec_material* mats,
+                                      const double* const* fr, const double* I, const double* D,
+                                      const double* v, double dt_prev, double* dt_out, void* stream);
 
+/* Message of the last failure of `ctx`; with ctx == NULL, of the last failed call of this
+ * thread that has no context. */
 const char* salec_last_error(const salec_ctx* ctx);
 void salec_destroy(salec_ctx* ctx);
 

@@ -823,7 +823,7 @@ int salec_launches_per_step(const salec_ctx* ctx)
 
 const char* salec_last_error(const salec_ctx* ctx)
 {
-    return ctx ? ctx->err.c_str() : "null context";
+    return ctx ? ctx->err.c_str() : noalloc_last_error();
 }
 
 void salec_destroy(salec_ctx* ctx)

@@ -160,6 +160,7 @@ cudaError_t launch_pressure(const Params& P, double* out, cudaStream_t s);
 cudaError_t launch_column_heights(const Params& P, double* heights, cudaStream_t s);
 cudaError_t launch_conservation(const Params& P, double* partial4, int* nblocks, cudaStream_t s);
 int launches_per_step();
+const char* noalloc_last_error();
 int cell_blocks(int nr, int nz);
 int vertex_blocks(int nr, int nz);
 

@@ -57,7 +57,7 @@ EXPORTS = ["salec_state_bytes", "salec_create", "salec_set_material", "salec_add
            "salec_set_time", "salec_get_field", "salec_set_field", "salec_crater_profile",
            "salec_conservation", "salec_checkpoint_bytes", "salec_get_state", "salec_set_state",
            "salec_launches_per_step", "salec_set_kernel_timing", "salec_kernel_times",
-           "salec_kernel_name", "salec_last_error", "salec_destroy"]
+           "salec_kernel_name", "salec_courant_dt_noalloc", "salec_last_error", "salec_destroy"]
 
 
 def load(build: bool = True):
@@ -92,6 +92,8 @@ def load(build: bool = True):
         "salec_set_kernel_timing": (I, [P, I]),
         "salec_kernel_times": (I, [P, PD, I, C.POINTER(C.c_int)]),
         "salec_kernel_name": (C.c_char_p, [I]),
+        "salec_courant_dt_noalloc": (I, [C.POINTER(salec_grid), C.POINTER(salec_material), C.POINTER(C.c_void_p),
+                                         P, P, P, D, PD, P]),
         "salec_last_error": (C.c_char_p, [P]),
         "salec_destroy": (None, [P]),
     }
@@ -260,3 +262,20 @@ class Sim:
         self._check(load().salec_kernel_times(self._h, out.ctypes.data_as(C.POINTER(C.c_double)), n, C.byref(steps)))
         return {load().salec_kernel_name(k).decode(): float(out[k]) for k in range(n)}, steps.value
 
+
+def courant_dt_noalloc(spec: dict, fr_ptrs, I_ptr: int, v_ptr: int, dt_prev: float, stream_ptr: int,
+                       D_ptr: int | None = None) -> float:
+    """Courant time step of a state held in caller device buffers, with no allocation
+    (see salec_courant_dt_noalloc in include/salec.h).  Pointers are raw device addresses."""
+    L = load()
+    nm = len(spec["materials"])
+    g = make_grid(spec["grid"], nm)
+    mats = (salec_material * nm)(*[make_material(m) for m in spec["materials"]])
+    frs = (C.c_void_p * nm)(*[C.c_void_p(int(p)) for p in fr_ptrs])
+    out = C.c_double()
+    st = L.salec_courant_dt_noalloc(C.byref(g), mats, frs, C.c_void_p(int(I_ptr)),
+                                    C.c_void_p(int(D_ptr)) if D_ptr else None, C.c_void_p(int(v_ptr)),
+                                    float(dt_prev), C.byref(out), C.c_void_p(int(stream_ptr)))
+    if st != SALEC_OK:
+        raise SalecError(st, L.salec_last_error(None).decode())
+    return out.value
