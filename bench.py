@@ -41,16 +41,23 @@ UNIT = "cell-updates/s"
 # 1.25 TFLOP/s FP64); measured 1.19 TFLOP/s with a dependent-chain-free DFMA loop.
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12
 
-# Algorithmic bytes per cell-update of each kernel (FP64, one material, hydrodynamic):
-# fields each kernel must read and write once.  Derivation in the design doc section 7.
-KERNEL_BYTES_PER_CELL = {
-    "k_phase0": 16 + 8 + 16 + 8 + 8 + 16 + 16,        # (f,rho) I v pmax(rw) -> (P,M) (pbar,phi)
-    "k_phase1": 16 + 16 + 16 + 16 + 8 + 8,            # (P,M) phi v -> vL mv dK
-    "k_phase2": 16 + 16 + 16 + 8 + 16 + 16,           # vL (P,M) (pbar,phi) I -> (fL,rhoL) (VL,IL)
-    "k_phase3a": 16 + 16 + 16 + 16 + 8 + 8 + 8,       # vL (fL,rhoL) (VL,IL) -> (f,rho) I dMR dMZ
-    "k_phase3b": 8 + 8 + 16 + 8 + 8 + 16 + 8,         # dMR dMZ vL mv dK -> v kheat
-    "k_phase3c": 16 + 8 + 8 + 8,                      # (f,rho) kheat I(rw)
-}
+# Algorithmic bytes per cell-update of each kernel (one material, hydrodynamic): the fields
+# each kernel must read and write once, e = element bytes (8 FP64, 4 mixed), energies 8.
+def kernel_bytes_per_cell(e: int) -> dict:
+    return {
+        "k_phase0": 2 * e + 8 + 2 * e + 2 * e + 2 * e + 2 * e,    # (f,rho) I v pmax(rw) -> (P,M) (pbar,phi)
+        "k_phase1": 2 * e + 2 * e + 2 * e + 2 * e + e + e,        # (P,M) phi v -> vL mv dK
+        "k_phase2": 2 * e + 2 * e + 2 * e + 8 + 2 * e + e + 8,    # vL (P,M) (pbar,phi) I -> (fL,rhoL) VL IL
+        "k_phase3a": 2 * e + 2 * e + e + 8 + 2 * e + 8 + e + e,   # vL (fL,rhoL) VL IL -> (f,rho) I dMR dMZ
+        "k_phase3b": e + e + 2 * e + e + e + 2 * e + e,           # dMR dMZ vL mv dK -> v kheat
+        "k_phase3c": 2 * e + e + 8 + 8,                           # (f,rho) kheat I(rw)
+    }
+
+
+# persistent state read once and written once per step (one material, hydrodynamic):
+# (f, rho), I, pmax, v
+def step_bytes_per_cell(e: int) -> int:
+    return 2 * (2 * e + 8 + e + 2 * e)
 
 
 def _load_peaks():
@@ -182,6 +189,7 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--cpu-steps", type=int, default=2)
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--precision", default="both", choices=["both", "fp64", "fp32mix"])
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     if args.impl == "reference":
@@ -199,14 +207,6 @@ def main():
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     spec = _workload(args.workload)
     cells = spec["grid"]["nr"] * spec["grid"]["nz"]
-    sim = salec.Sim(spec)
-    stream = sim.stream
-    nbytes = sim.checkpoint_bytes()
-    init = sim.state[:nbytes].clone()          # device copy of the initial state
-
-    def restore():
-        sim.state[:nbytes].copy_(init)
-        torch.cuda.synchronize()
 
     def barrier():
         torch.cuda.synchronize()
@@ -214,94 +214,131 @@ def main():
             dist.barrier()
         torch.cuda.synchronize()
 
-    # warm-up, then back to t = 0 so the timed region is exactly K steps of the run
-    sim.step(args.warmup)
-    torch.cuda.synchronize()
-    restore()
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
-    sim.set_kernel_timing(True)
-    barrier()
-    with ClockSampler(local) as clk:
-        e0.record(stream)
-        sim.step(args.steps)
-        e1.record(stream)
-        barrier()
-    ms = e0.elapsed_time(e1)
-    ktimes, ksteps = sim.kernel_times()
-    sim.set_kernel_timing(False)
-    sc = sim.scalars()
-    ms_max = ms
-    if ws > 1:
-        t = torch.tensor([ms], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_max = float(t.item())
-    value = ws * cells * args.steps / (ms_max * 1e-3)
+    def measure(precision, with_e2e):
+        """Device-timed K steps from t = 0 (after W warm-up steps and a restore), with live
+        per-kernel events; then optionally the same K steps end to end through the C ABI."""
+        sim = salec.Sim(spec, precision=precision)
+        stream = sim.stream
+        nbytes = sim.checkpoint_bytes()
+        init = sim.state[:nbytes].clone()          # device copy of the initial state
 
-    # end to end through the C ABI with host buffers
-    e2e = None
-    if not args.no_e2e:
-        host = torch.empty(nbytes, dtype=torch.uint8, pin_memory=True)
-        host.copy_(init.cpu())
-        p_host = np.zeros((spec["grid"]["nz"], spec["grid"]["nr"]))
-        restore()
-        barrier()
-        t0 = time.perf_counter()
-        sim.set_state(host.numpy())
-        for _ in range(args.steps):
-            sim.step(1)
-            sim.scalars()
-        p_host[:] = sim.get("p")
+        def restore():
+            sim.state[:nbytes].copy_(init)
+            torch.cuda.synchronize()
+
+        sim.step(args.warmup)
         torch.cuda.synchronize()
-        t_e2e = time.perf_counter() - t0
+        restore()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        sim.set_kernel_timing(True)
+        barrier()
+        with ClockSampler(local) as clk:
+            e0.record(stream)
+            sim.step(args.steps)
+            e1.record(stream)
+            barrier()
+        ms = e0.elapsed_time(e1)
+        ktimes, _ = sim.kernel_times()
+        sim.set_kernel_timing(False)
+        sc = sim.scalars()
+        ms_max = ms
         if ws > 1:
-            t = torch.tensor([t_e2e], device="cuda", dtype=torch.float64)
+            t = torch.tensor([ms], device="cuda", dtype=torch.float64)
             dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            t_e2e = float(t.item())
-        e2e = {"value": ws * cells * args.steps / t_e2e, "unit": UNIT,
-               "h2d_bytes_per_step": nbytes / args.steps,
-               "d2h_bytes_per_step": 64 + p_host.nbytes / args.steps,
-               "note": "initial state H2D once from pinned memory (amortised over the steps), "
-                       "per-step scalar read-back, final pressure field D2H"}
+            ms_max = float(t.item())
+        out = {"value": ws * cells * args.steps / (ms_max * 1e-3), "ms": ms, "ms_max": ms_max, "ktimes": ktimes,
+               "scalars": sc, "clocks": clk.summary(), "launches": sim.launches_per_step() * args.steps,
+               "crater": sim.crater(spec["z_surface"], 64)}
+        if with_e2e:
+            host = torch.empty(nbytes, dtype=torch.uint8, pin_memory=True)
+            host.copy_(init.cpu())
+            p_host = np.zeros((spec["grid"]["nz"], spec["grid"]["nr"]))
+            restore()
+            barrier()
+            t0 = time.perf_counter()
+            sim.set_state(host.numpy())
+            for _ in range(args.steps):
+                sim.step(1)
+                sim.scalars()
+            p_host[:] = sim.get("p")
+            torch.cuda.synchronize()
+            t_e2e = time.perf_counter() - t0
+            if ws > 1:
+                t = torch.tensor([t_e2e], device="cuda", dtype=torch.float64)
+                dist.all_reduce(t, op=dist.ReduceOp.MAX)
+                t_e2e = float(t.item())
+            out["e2e"] = {"value": ws * cells * args.steps / t_e2e, "unit": UNIT,
+                          "h2d_bytes_per_step": nbytes / args.steps,
+                          "d2h_bytes_per_step": 64 + p_host.nbytes / args.steps,
+                          "note": "initial state H2D once from pinned memory (amortised over the steps), "
+                                  "per-step scalar read-back, final pressure field D2H"}
+        del sim, init
+        torch.cuda.empty_cache()
+        return out
 
+    hbm_peak, peak_kind = _load_peaks()
+
+    def roofline(res, e):
+        kt = res["ktimes"]
+        dom = max(kt, key=kt.get)
+        kb = kernel_bytes_per_cell(e)
+        gbs = kb[dom] * cells / (kt[dom] * 1e-3) / 1e9
+        roof = {"kernel": dom, "hbm": {"achieved_gbs": round(gbs, 1), "peak_gbs": hbm_peak, "peak_kind": peak_kind,
+                                       "frac": round(gbs / hbm_peak, 4), "bytes_per_cell": kb[dom]}}
+        return roof, dom
+
+    res64 = measure("fp64", not args.no_e2e) if args.precision in ("both", "fp64") else None
+    res32 = measure("fp32mix", not args.no_e2e and args.precision == "fp32mix") if args.precision in ("both", "fp32mix") else None
     if rank != 0:
         dist.destroy_process_group()
         return 0
 
-    # roofline of the dominant kernel
-    hbm_peak, peak_kind = _load_peaks()
-    dom = max(ktimes, key=ktimes.get)
-    dom_ms = ktimes[dom]
-    dom_bytes = KERNEL_BYTES_PER_CELL[dom] * cells
-    achieved_gbs = dom_bytes / (dom_ms * 1e-3) / 1e9
-    roof = {"bound": "alu", "kernel": dom, "unit": "TFLOP/s", "peak": round(FP64_PEAK_TFLOPS, 4),
-            "peak_kind": "nominal FP64 issue rate 152 SM x 2 DFMA/clk x 2.07 GHz (measured DFMA loop: 1.19)",
-            "achieved": None, "frac": None, "traffic": None,
-            "hbm": {"achieved_gbs": round(achieved_gbs, 1), "peak_gbs": hbm_peak, "peak_kind": peak_kind,
-                    "frac": round(achieved_gbs / hbm_peak, 4), "bytes_per_cell": KERNEL_BYTES_PER_CELL[dom]}}
-    flops_per_cell = _FLOPS_PER_CELL.get(dom)
-    if flops_per_cell:
-        ach = flops_per_cell * cells / (dom_ms * 1e-3) / 1e12
-        roof["achieved"] = round(ach, 4)
-        roof["frac"] = round(ach / FP64_PEAK_TFLOPS, 4)
-        roof["flops_per_cell"] = flops_per_cell
-    step_bytes = sum(KERNEL_BYTES_PER_CELL.values()) * cells
+    main_res = res64 if res64 is not None else res32
+    e_main = 8 if res64 is not None else 4
+    roof_hbm, dom = roofline(main_res, e_main)
+    if res64 is not None:
+        flops = _FLOPS_PER_CELL.get(dom)
+        ach = flops * cells / (main_res["ktimes"][dom] * 1e-3) / 1e12 if flops else None
+        roof = {"bound": "alu", "kernel": dom, "unit": "TFLOP/s", "peak": round(FP64_PEAK_TFLOPS, 4),
+                "peak_kind": "nominal FP64 issue rate 152 SM x 2 DFMA/clk x 2.07 GHz (measured DFMA loop: 1.19)",
+                "achieved": round(ach, 4) if ach else None, "frac": round(ach / FP64_PEAK_TFLOPS, 4) if ach else None,
+                "flops_per_cell": flops, "traffic": _TRAFFIC_PER_CELL.get(dom) and _TRAFFIC_PER_CELL[dom] * cells,
+                "hbm": roof_hbm["hbm"]}
+    else:
+        h = roof_hbm["hbm"]
+        roof = {"bound": "hbm", "kernel": dom, "unit": "GB/s", "achieved": h["achieved_gbs"], "peak": hbm_peak,
+                "frac": h["frac"], "traffic": None, "peak_kind": peak_kind}
+    ms = main_res["ms"]
+    sc = main_res["scalars"]
     line = {
-        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
-        "ms_per_step": ms_max / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "f64", "data": "synthetic",
+        "metric": METRIC, "value": main_res["value"], "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": main_res["ms_max"] / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64" if res64 is not None else "f32+f64",
+        "data": "synthetic",
         "config": {"workload": args.workload + " " + spec["name"], "grid": f"{spec['grid']['nr']}x{spec['grid']['nz']}",
-                   "cells": cells, "precision": "FP64", "l2": "state > L2 (no flush)",
-                   "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU",
+                   "cells": cells, "precision": "FP64" if res64 is not None else "FP32-mix",
+                   "l2": "state > L2 (no flush)", "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU",
                    "sim_time_s": sc["t"], "status": sc["status"]},
-        "gpu_launches": sim.launches_per_step() * args.steps,
-        "kernel_ms": {k: round(v, 4) for k, v in ktimes.items()},
-        "step_hbm_frac": round(step_bytes / (ms / args.steps * 1e-3) / 1e9 / hbm_peak, 4),
-        "roofline": roof, "clocks": clk.summary(), "e2e": e2e,
+        "gpu_launches": main_res["launches"],
+        "kernel_ms": {k: round(v, 4) for k, v in main_res["ktimes"].items()},
+        "step_hbm_frac": round(step_bytes_per_cell(e_main) * cells / (ms / args.steps * 1e-3) / 1e9 / hbm_peak, 4),
+        "roofline": roof, "clocks": main_res["clocks"], "e2e": main_res.get("e2e"),
     }
+    if res64 is not None and res32 is not None:
+        r32, d32 = roofline(res32, 4)
+        c64, c32 = res64["crater"], res32["crater"]
+        line["fp32_mix"] = {
+            "value": res32["value"], "unit": UNIT, "ms_per_step": res32["ms_max"] / args.steps,
+            "speedup_vs_fp64": res32["value"] / res64["value"],
+            "kernel_ms": {k: round(v, 4) for k, v in res32["ktimes"].items()},
+            "roofline": {"bound": "hbm", "kernel": d32, "unit": "GB/s", **r32["hbm"],
+                         "traffic": _TRAFFIC_PER_CELL_FP32MIX.get(d32) and _TRAFFIC_PER_CELL_FP32MIX[d32] * cells,
+                         "traffic_note": "DRAM read+write bytes per cell from ncu on 2000x2000, times the cells"},
+            "step_hbm_frac": round(step_bytes_per_cell(4) * cells / (res32["ms"] / args.steps * 1e-3) / 1e9 / hbm_peak, 4),
+            "crater_vs_fp64": {"depth": [c32["depth"], c64["depth"]], "diameter": [c32["diameter"], c64["diameter"]]},
+            "gpu_launches": res32["launches"], "clocks": res32["clocks"], "status": res32["scalars"]["status"]}
     if ws == 1 and not args.no_cpu:
-        del sim
-        torch.cuda.empty_cache()
         line["cpu_baseline"] = _cpu_baseline(spec, args.cpu_steps)
     print(json.dumps(line))
     if ws > 1:
@@ -309,9 +346,12 @@ def main():
     return 0
 
 
-# FP64 operations per cell issued by each kernel on the common path (measured once with
-# ncu's per-opcode DP instruction counters, FMA counted as 2); see the design doc section 7.
-_FLOPS_PER_CELL: dict = {}
+# FP64 operations per cell (2 DFMA + DADD + DMUL) issued by each FP64-form kernel on the
+# 4000 x 4000 physics, and DRAM bytes per cell, from ncu on the 2000 x 2000 case
+# (profiles/); refreshed whenever the kernels change.
+_FLOPS_PER_CELL: dict = {"k_phase0": 82.3, "k_phase1": 49.5, "k_phase2": 62.4, "k_phase3a": 96.0, "k_phase3b": 84.9, "k_phase3c": 5.5}
+_TRAFFIC_PER_CELL: dict = {"k_phase0": 58.0, "k_phase1": 72.1, "k_phase2": 75.6, "k_phase3a": 78.5, "k_phase3b": 80.4, "k_phase3c": 28.9}
+_TRAFFIC_PER_CELL_FP32MIX: dict = {"k_phase0": 28.1, "k_phase1": 31.5, "k_phase2": 40.0, "k_phase3a": 42.1, "k_phase3b": 37.8, "k_phase3c": 16.5}
 
 if __name__ == "__main__":
     sys.exit(main())

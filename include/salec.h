@@ -45,8 +45,11 @@ typedef enum {
                               density, a NaN, or dt below dt_min (see salec_get_scalars) */
 } salec_status;
 
-/* arithmetic of the step */
-enum { SALEC_FP64 = 0 };
+/* Arithmetic of the step.  SALEC_FP64: every field and operation in FP64.
+ * SALEC_FP32MIX: fields, stencils and material laws in FP32, while the specific internal
+ * energy and its updates, the Courant reduction and the conservation sums are FP64
+ * (SURVEY's mixed form; the state buffer is about half the size). */
+enum { SALEC_FP64 = 0, SALEC_FP32MIX = 1 };
 
 enum { SALEC_EOS_TILLOTSON = 0, SALEC_EOS_IDEAL_GAS = 1 };
 enum { SALEC_STRENGTH_NONE = 0, SALEC_STRENGTH_COLLINS = 1 };

@@ -23,11 +23,12 @@ constexpr size_t kAlign = 256;
 // Offsets of every array inside the state buffer.  The persistent part (scalars, tables,
 // fields, PML auxiliaries) comes first so a checkpoint is one contiguous range.
 struct Layout {
+    size_t es;   // bytes of one element of the form (8 FP64, 4 mixed); energies are always 8
     size_t scal, A_R, A_Z, V, invV, inv2rc, p0, rho_ref, I_ref, dB_c, dB_v, dR_c, dR_v;
     size_t fr[kMaxMat], I, s01, s2d, pmax, v;
     size_t pb_c, pb_psi2, pb_v, pr_c, pr_psi2, pr_v;
     size_t persist_end;
-    size_t PM, pbphi, vL, mv, dK, kheat, frL[kMaxMat], VIL, sL01, sL2d, dMR, dMZ, partial, tmp;
+    size_t PM, pbphi, vL, mv, dK, kheat, frL[kMaxMat], VL, IL, sL01, sL2d, dMR, dMZ, partial, tmp;
     size_t total;
 };
 
@@ -38,13 +39,14 @@ size_t take(size_t& cur, size_t bytes)
     return off;
 }
 
-Layout make_layout(const salec_grid& g)
+Layout make_layout(const salec_grid& g, int precision)
 {
     Layout L;
     memset(&L, 0, sizeof(L));
     const size_t nr = g.nr, nz = g.nz, nc = nr * nz, nv = (nr + 1) * (nz + 1);
     const size_t pb = g.pml_bottom, pr = g.pml_right;
-    const size_t d = sizeof(double), d2 = 2 * d, d4 = 4 * d;
+    L.es = precision == SALEC_FP32MIX ? sizeof(float) : sizeof(double);
+    const size_t d = L.es, d2 = 2 * d, d4 = 4 * d, e8 = sizeof(double);
     size_t cur = 0;
     L.scal = take(cur, sizeof(DevScalars));
     L.A_R = take(cur, (nr + 1) * d);
@@ -54,13 +56,13 @@ Layout make_layout(const salec_grid& g)
     L.inv2rc = take(cur, nr * d);
     L.p0 = take(cur, nz * d);
     L.rho_ref = take(cur, nz * d);
-    L.I_ref = take(cur, nz * d);
+    L.I_ref = take(cur, nz * e8);
     L.dB_c = take(cur, nz * d);
     L.dB_v = take(cur, (nz + 1) * d);
     L.dR_c = take(cur, nr * d);
     L.dR_v = take(cur, (nr + 1) * d);
     for (int m = 0; m < g.nmat; ++m) L.fr[m] = take(cur, nc * d2);
-    L.I = take(cur, nc * d);
+    L.I = take(cur, nc * e8);
     L.s01 = take(cur, nc * d2);
     L.s2d = take(cur, nc * d2);
     L.pmax = take(cur, nc * d);
@@ -79,15 +81,16 @@ Layout make_layout(const salec_grid& g)
     L.dK = take(cur, nv * d);
     L.kheat = take(cur, nv * d);
     for (int m = 0; m < g.nmat; ++m) L.frL[m] = take(cur, nc * d2);
-    L.VIL = take(cur, nc * d2);
+    L.VL = take(cur, nc * d);
+    L.IL = take(cur, nc * e8);
     L.sL01 = take(cur, nc * d2);
     L.sL2d = take(cur, nc * d2);
     L.dMR = take(cur, (nr + 1) * nz * d);
     L.dMZ = take(cur, nr * (nz + 1) * d);
     const size_t nb = (size_t)cell_blocks(g.nr, g.nz);
     const size_t nbv = (size_t)vertex_blocks(g.nr, g.nz);
-    L.partial = take(cur, (nb > 4 * nbv ? nb : 4 * nbv) * d);
-    L.tmp = take(cur, nv * d);
+    L.partial = take(cur, (nb > 4 * nbv ? nb : 4 * nbv) * e8);
+    L.tmp = take(cur, nv * e8);
     L.total = cur;
     return L;
 }
@@ -117,7 +120,8 @@ struct salec_ctx {
     salec_material mats[kMaxMat];
     bool mat_set[kMaxMat];
     bool finalized;
-    Params P;
+    ParamsT<double> Pd;     // FP64 form
+    ParamsT<float> Pf;      // mixed form
     // set-up accumulators (host, freed at finalize)
     std::vector<double> sV[kMaxMat], sM[kMaxMat], sE, sPz;
     std::vector<double> sR[kMaxMat];      // density shared by all contributions (exact)
@@ -154,74 +158,82 @@ static salec_status cuda_check(salec_ctx* ctx, cudaError_t e, const char* what)
 template <typename T>
 static T* at(salec_ctx* ctx, size_t off) { return reinterpret_cast<T*>(ctx->base + off); }
 
-static Mat to_mat(const salec_material& s)
+template <typename T>
+static MatT<T> to_mat(const salec_material& s)
 {
-    Mat m;
+    MatT<T> m;
     memset(&m, 0, sizeof(m));
     m.eos = s.eos; m.strength = s.strength;
-    m.rho0 = s.rho0; m.inv_rho0 = 1.0 / s.rho0;
-    m.rho0sq_E0 = s.eos == SALEC_EOS_TILLOTSON ? s.rho0 * s.rho0 / s.E0 : 0.0;
-    m.A = s.A; m.B = s.B; m.E0 = s.E0; m.a = s.a; m.b = s.b; m.alpha = s.alpha; m.beta = s.beta;
-    m.Eiv = s.Eiv; m.Ecv = s.Ecv;
-    m.inv_dE = (s.Ecv > s.Eiv) ? 1.0 / (s.Ecv - s.Eiv) : 0.0;
-    m.gamma = s.gamma;
-    m.Yi0 = s.Yi0; m.mui = s.mui; m.Yim = s.Yim; m.Yd0 = s.Yd0; m.mud = s.mud; m.Ydm = s.Ydm;
-    m.inv_Yspan = (s.Yim != s.Yi0) ? 1.0 / (s.Yim - s.Yi0) : 0.0;
-    m.G = s.strength == SALEC_STRENGTH_COLLINS ? s.G : 0.0;
-    m.eps_fb = s.eps_fb; m.B_dam = s.B_dam; m.p_bd = s.p_bd; m.p_t = s.p_t;
-    m.c2_floor = s.eos == SALEC_EOS_TILLOTSON ? 0.01 * s.A / s.rho0 : 0.0;
+    m.rho0 = T(s.rho0); m.inv_rho0 = T(1.0 / s.rho0);
+    m.rho0sq_E0 = T(s.eos == SALEC_EOS_TILLOTSON ? s.rho0 * s.rho0 / s.E0 : 0.0);
+    m.A = T(s.A); m.B = T(s.B); m.E0 = T(s.E0); m.a = T(s.a); m.b = T(s.b); m.alpha = T(s.alpha);
+    m.beta = T(s.beta); m.Eiv = T(s.Eiv); m.Ecv = T(s.Ecv);
+    m.inv_dE = T((s.Ecv > s.Eiv) ? 1.0 / (s.Ecv - s.Eiv) : 0.0);
+    m.gamma = T(s.gamma);
+    m.Yi0 = T(s.Yi0); m.mui = T(s.mui); m.Yim = T(s.Yim); m.Yd0 = T(s.Yd0); m.mud = T(s.mud); m.Ydm = T(s.Ydm);
+    m.inv_Yspan = T((s.Yim != s.Yi0) ? 1.0 / (s.Yim - s.Yi0) : 0.0);
+    m.G = T(s.strength == SALEC_STRENGTH_COLLINS ? s.G : 0.0);
+    m.eps_fb = T(s.eps_fb); m.B_dam = T(s.B_dam); m.p_bd = T(s.p_bd); m.p_t = T(s.p_t);
+    m.c2_floor = T(s.eos == SALEC_EOS_TILLOTSON ? 0.01 * s.A / s.rho0 : 0.0);
     return m;
 }
 
-static void fill_params(salec_ctx* ctx)
+template <typename T>
+static void fill_params(salec_ctx* ctx, ParamsT<T>& P)
 {
-    Params& P = ctx->P;
+    typedef typename VT<T>::T2 T2;
+    typedef typename VT<T>::T4 T4;
     const salec_grid& g = ctx->g;
     const Layout& L = ctx->L;
     P.nr = g.nr; P.nz = g.nz; P.nmat = g.nmat; P.pr = g.pml_right; P.pb = g.pml_bottom;
     P.bc_top = g.bc_top; P.bc_bottom = g.bc_bottom;
     P.any_strength = 0;
     for (int m = 0; m < g.nmat; ++m) {
-        P.mat[m] = to_mat(ctx->mats[m]);
+        P.mat[m] = to_mat<T>(ctx->mats[m]);
         if (ctx->mats[m].strength == SALEC_STRENGTH_COLLINS) P.any_strength = 1;
     }
     P.nblk_cells = cell_blocks(g.nr, g.nz);
-    P.dx = g.dx; P.dx2 = g.dx * g.dx; P.cfl = g.cfl; P.growth = g.dt_growth; P.dt_max = g.dt_max;
-    P.dt_min = g.dt_min; P.g = g.gravity; P.cq = g.av_cq; P.cl = g.av_cl; P.f_min = g.f_min;
-    Ptrs& p = P.p;
+    P.dx = T(g.dx); P.dx2 = T(g.dx * g.dx); P.cfl = T(g.cfl); P.g = T(g.gravity); P.cq = T(g.av_cq);
+    P.cl = T(g.av_cl); P.f_min = T(g.f_min);
+    P.dxd = g.dx; P.cfld = g.cfl; P.growth = g.dt_growth; P.dt_max = g.dt_max; P.dt_min = g.dt_min;
+    PtrsT<T>& p = P.p;
     for (int m = 0; m < kMaxMat; ++m) {
-        p.fr[m] = m < g.nmat ? at<double2>(ctx, L.fr[m]) : nullptr;
-        p.frL[m] = m < g.nmat ? at<double2>(ctx, L.frL[m]) : nullptr;
+        p.fr[m] = m < g.nmat ? at<T2>(ctx, L.fr[m]) : nullptr;
+        p.frL[m] = m < g.nmat ? at<T2>(ctx, L.frL[m]) : nullptr;
     }
-    p.I = at<double>(ctx, L.I); p.s01 = at<double2>(ctx, L.s01); p.s2d = at<double2>(ctx, L.s2d);
-    p.pmax = at<double>(ctx, L.pmax); p.v = at<double2>(ctx, L.v);
-    p.pb_c = at<double2>(ctx, L.pb_c); p.pb_psi2 = at<double>(ctx, L.pb_psi2); p.pb_v = at<double4_32a>(ctx, L.pb_v);
-    p.pr_c = at<double2>(ctx, L.pr_c); p.pr_psi2 = at<double>(ctx, L.pr_psi2); p.pr_v = at<double4_32a>(ctx, L.pr_v);
-    p.A_R = at<double>(ctx, L.A_R); p.A_Z = at<double>(ctx, L.A_Z); p.V = at<double>(ctx, L.V);
-    p.invV = at<double>(ctx, L.invV); p.inv2rc = at<double>(ctx, L.inv2rc); p.p0 = at<double>(ctx, L.p0); p.rho_ref = at<double>(ctx, L.rho_ref);
-    p.I_ref = at<double>(ctx, L.I_ref); p.dB_c = at<double>(ctx, L.dB_c); p.dB_v = at<double>(ctx, L.dB_v);
-    p.dR_c = at<double>(ctx, L.dR_c); p.dR_v = at<double>(ctx, L.dR_v);
-    p.PM = at<double2>(ctx, L.PM); p.pbphi = at<double2>(ctx, L.pbphi); p.vL = at<double2>(ctx, L.vL);
-    p.mv = at<double>(ctx, L.mv); p.dK = at<double>(ctx, L.dK); p.kheat = at<double>(ctx, L.kheat);
-    p.VIL = at<double2>(ctx, L.VIL); p.sL01 = at<double2>(ctx, L.sL01); p.sL2d = at<double2>(ctx, L.sL2d);
-    p.dMR = at<double>(ctx, L.dMR); p.dMZ = at<double>(ctx, L.dMZ); p.partial = at<double>(ctx, L.partial);
+    p.I = at<double>(ctx, L.I); p.s01 = at<T2>(ctx, L.s01); p.s2d = at<T2>(ctx, L.s2d);
+    p.pmax = at<T>(ctx, L.pmax); p.v = at<T2>(ctx, L.v);
+    p.pb_c = at<T2>(ctx, L.pb_c); p.pb_psi2 = at<T>(ctx, L.pb_psi2); p.pb_v = at<T4>(ctx, L.pb_v);
+    p.pr_c = at<T2>(ctx, L.pr_c); p.pr_psi2 = at<T>(ctx, L.pr_psi2); p.pr_v = at<T4>(ctx, L.pr_v);
+    p.A_R = at<T>(ctx, L.A_R); p.A_Z = at<T>(ctx, L.A_Z); p.V = at<T>(ctx, L.V);
+    p.invV = at<T>(ctx, L.invV); p.inv2rc = at<T>(ctx, L.inv2rc); p.p0 = at<T>(ctx, L.p0);
+    p.rho_ref = at<T>(ctx, L.rho_ref); p.I_ref = at<double>(ctx, L.I_ref); p.dB_c = at<T>(ctx, L.dB_c);
+    p.dB_v = at<T>(ctx, L.dB_v); p.dR_c = at<T>(ctx, L.dR_c); p.dR_v = at<T>(ctx, L.dR_v);
+    p.PM = at<T2>(ctx, L.PM); p.pbphi = at<T2>(ctx, L.pbphi); p.vL = at<T2>(ctx, L.vL);
+    p.mv = at<T>(ctx, L.mv); p.dK = at<T>(ctx, L.dK); p.kheat = at<T>(ctx, L.kheat);
+    p.VL = at<T>(ctx, L.VL); p.IL = at<double>(ctx, L.IL); p.sL01 = at<T2>(ctx, L.sL01);
+    p.sL2d = at<T2>(ctx, L.sL2d); p.dMR = at<T>(ctx, L.dMR); p.dMZ = at<T>(ctx, L.dMZ);
+    p.partial = at<double>(ctx, L.partial);
     p.scal = at<DevScalars>(ctx, L.scal);
 }
+
+static bool mixed(const salec_ctx* ctx) { return ctx->precision == SALEC_FP32MIX; }
 
 extern "C" {
 
 salec_status salec_state_bytes(const salec_grid* grid, int precision, size_t* bytes)
 {
-    if (!grid_ok(grid) || precision != SALEC_FP64 || !bytes) return SALEC_EINVAL;
-    *bytes = make_layout(*grid).total;
+    if (!grid_ok(grid) || (precision != SALEC_FP64 && precision != SALEC_FP32MIX) || !bytes) return SALEC_EINVAL;
+    *bytes = make_layout(*grid, precision).total;
     return SALEC_OK;
 }
 
 salec_status salec_create(const salec_grid* grid, int precision, void* dev_state, size_t bytes, void* stream,
                           salec_ctx** out)
 {
-    if (!out || !grid_ok(grid) || precision != SALEC_FP64) return SALEC_EINVAL;
-    Layout L = make_layout(*grid);
+    if (!out || !grid_ok(grid) || (precision != SALEC_FP64 && precision != SALEC_FP32MIX)) return SALEC_EINVAL;
+    if (precision == SALEC_FP32MIX && !(grid->f_min >= 1e-7)) return SALEC_EINVAL;   // FP32 fractions need a floor
+    Layout L = make_layout(*grid, precision);
     if (!dev_state || bytes < L.total || ((uintptr_t)dev_state % kAlign) != 0) return SALEC_ENOMEM;
     salec_ctx* ctx = new salec_ctx();
     ctx->g = *grid;
@@ -391,8 +403,9 @@ salec_status salec_finalize(salec_ctx* ctx)
         if (!ctx->mat_set[m]) return fail(ctx, SALEC_EORDER, "material %d not set", m);
     const int nr = g.nr, nz = g.nz, pr = g.pml_right, pb = g.pml_bottom;
     const size_t nc = (size_t)nr * nz, nv = (size_t)(nr + 1) * (nz + 1);
-    fill_params(ctx);
-    const Params& P = ctx->P;
+    fill_params<double>(ctx, ctx->Pd);
+    fill_params<float>(ctx, ctx->Pf);
+    const ParamsT<double>& P = ctx->Pd;
     // PML wave speed
     double c = g.pml_c;
     if (!(c > 0.0)) {
@@ -451,7 +464,7 @@ salec_status salec_finalize(salec_ctx* ctx)
             const double2 f = fr[m][cc];
             if (!(f.x > 0.0)) continue;
             double pm, c2;
-            eos_eval(P.mat[m], f.y, I[cc], pm, c2);
+            eos_eval<double>(P.mat[m], f.y, I[cc], pm, c2);
             const double pmin = P.mat[m].p_t;
             pm = pm < pmin ? pmin : pm;
             phat += f.x * pm; phi += f.x; mass += f.x * f.y;
@@ -480,23 +493,32 @@ salec_status salec_finalize(salec_ctx* ctx)
     cudaError_t e = cudaMemsetAsync(ctx->base, 0, L.persist_end, st);
     auto up = [&](size_t off, const void* src, size_t n) {
         if (e == cudaSuccess && n) e = cudaMemcpyAsync(ctx->base + off, src, n, cudaMemcpyHostToDevice, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);   // src may be a temporary
+    };
+    // arrays of the form's element type: converted from FP64 on the host when mixed
+    const bool mx = mixed(ctx);
+    auto upT = [&](size_t off, const double* src, size_t n) {
+        if (!mx) { up(off, src, n * sizeof(double)); return; }
+        std::vector<float> f(n);
+        for (size_t k = 0; k < n; ++k) f[k] = (float)src[k];
+        up(off, f.data(), n * sizeof(float));
     };
     up(L.scal, &s, sizeof(s));
-    up(L.A_R, ctx->A_R.data(), (nr + 1) * sizeof(double));
-    up(L.A_Z, ctx->A_Z.data(), nr * sizeof(double));
-    up(L.V, ctx->Vc.data(), nr * sizeof(double));
-    up(L.invV, invV.data(), nr * sizeof(double));
-    up(L.inv2rc, inv2rc.data(), nr * sizeof(double));
-    up(L.p0, p0.data(), nz * sizeof(double));
-    up(L.rho_ref, rref.data(), nz * sizeof(double));
+    upT(L.A_R, ctx->A_R.data(), nr + 1);
+    upT(L.A_Z, ctx->A_Z.data(), nr);
+    upT(L.V, ctx->Vc.data(), nr);
+    upT(L.invV, invV.data(), nr);
+    upT(L.inv2rc, inv2rc.data(), nr);
+    upT(L.p0, p0.data(), nz);
+    upT(L.rho_ref, rref.data(), nz);
     up(L.I_ref, Iref.data(), nz * sizeof(double));
-    up(L.dB_c, dBc.data(), nz * sizeof(double));
-    up(L.dB_v, dBv.data(), (nz + 1) * sizeof(double));
-    up(L.dR_c, dRc.data(), nr * sizeof(double));
-    up(L.dR_v, dRv.data(), (nr + 1) * sizeof(double));
-    for (int m = 0; m < g.nmat; ++m) up(L.fr[m], fr[m].data(), nc * sizeof(double2));
+    upT(L.dB_c, dBc.data(), nz);
+    upT(L.dB_v, dBv.data(), nz + 1);
+    upT(L.dR_c, dRc.data(), nr);
+    upT(L.dR_v, dRv.data(), nr + 1);
+    for (int m = 0; m < g.nmat; ++m) upT(L.fr[m], reinterpret_cast<const double*>(fr[m].data()), 2 * nc);
     up(L.I, I.data(), nc * sizeof(double));
-    up(L.v, v.data(), nv * sizeof(double2));
+    upT(L.v, reinterpret_cast<const double*>(v.data()), 2 * nv);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) return cuda_check(ctx, e, "finalize upload");
     for (int m = 0; m < kMaxMat; ++m) {
@@ -526,7 +548,8 @@ salec_status salec_step(salec_ctx* ctx, int nsteps)
             evp = ctx->ev.data() + ctx->ev_used;
             ctx->ev_used += K;
         }
-        cudaError_t e = launch_step(ctx->P, ctx->stream, evp);
+        cudaError_t e = mixed(ctx) ? launch_step<float>(ctx->Pf, ctx->stream, evp)
+                                   : launch_step<double>(ctx->Pd, ctx->stream, evp);
         if (e != cudaSuccess) return cuda_check(ctx, e, "step launch");
     }
     return SALEC_OK;
@@ -597,12 +620,12 @@ salec_status salec_set_time(salec_ctx* ctx, double t, double dt_prev)
 // Where a field lives: a device array of `stride` doubles per element, component `comp`,
 // over the whole grid (strip == 0) or over a PML strip (1 bottom cells, 2 right cells,
 // 3 bottom vertices, 4 right vertices).
-struct FieldLoc { size_t off; int stride, comp, strip; bool vertex; };
+struct FieldLoc { size_t off; int stride, comp, strip; bool vertex; size_t es; };
 
 static bool locate(const salec_ctx* ctx, int field, FieldLoc& F)
 {
     const Layout& L = ctx->L;
-    F.strip = 0; F.vertex = false; F.stride = 1; F.comp = 0;
+    F.strip = 0; F.vertex = false; F.stride = 1; F.comp = 0; F.es = L.es;
     if (field >= SALEC_F_VOLFRAC0 && field <= SALEC_F_VOLFRAC2) {
         if (field - SALEC_F_VOLFRAC0 >= ctx->g.nmat) return false;
         F.off = L.fr[field - SALEC_F_VOLFRAC0]; F.stride = 2; F.comp = 0; return true;
@@ -612,7 +635,7 @@ static bool locate(const salec_ctx* ctx, int field, FieldLoc& F)
         F.off = L.fr[field - SALEC_F_DENS0]; F.stride = 2; F.comp = 1; return true;
     }
     switch (field) {
-    case SALEC_F_IE: F.off = L.I; return true;
+    case SALEC_F_IE: F.off = L.I; F.es = sizeof(double); return true;
     case SALEC_F_SRR: F.off = L.s01; F.stride = 2; F.comp = 0; return true;
     case SALEC_F_SZZ: F.off = L.s01; F.stride = 2; F.comp = 1; return true;
     case SALEC_F_SRZ: F.off = L.s2d; F.stride = 2; F.comp = 0; return true;
@@ -672,7 +695,8 @@ salec_status salec_get_field(salec_ctx* ctx, int field, double* host_out, size_t
     if (field == SALEC_F_PRESSURE) {
         if (n != nc) return fail(ctx, SALEC_EINVAL, "pressure needs n = nr*nz");
         double* tmp = at<double>(ctx, ctx->L.tmp);
-        cudaError_t e = launch_pressure(ctx->P, tmp, ctx->stream);
+        cudaError_t e = mixed(ctx) ? launch_pressure<float>(ctx->Pf, tmp, ctx->stream)
+                                   : launch_pressure<double>(ctx->Pd, tmp, ctx->stream);
         if (e == cudaSuccess) e = cudaMemcpyAsync(host_out, tmp, nc * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream);
         if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
         return cuda_check(ctx, e, "get pressure");
@@ -683,10 +707,14 @@ salec_status salec_get_field(salec_ctx* ctx, int field, double* host_out, size_t
     if (n != want) return fail(ctx, SALEC_EINVAL, "field %d needs n = %zu", field, want);
     const size_t cnt = loc_count(ctx, F);
     std::vector<double> buf(cnt * F.stride + 1);
+    std::vector<float> fbuf(F.es == sizeof(float) ? cnt * F.stride + 1 : 0);
+    void* dst = F.es == sizeof(float) ? (void*)fbuf.data() : (void*)buf.data();
     cudaError_t e = cudaSuccess;
-    if (cnt) e = cudaMemcpyAsync(buf.data(), ctx->base + F.off, cnt * F.stride * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream);
+    if (cnt) e = cudaMemcpyAsync(dst, ctx->base + F.off, cnt * F.stride * F.es, cudaMemcpyDeviceToHost, ctx->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
     if (e != cudaSuccess) return cuda_check(ctx, e, "get field");
+    if (F.es == sizeof(float))
+        for (size_t k = 0; k < cnt * F.stride; ++k) buf[k] = (double)fbuf[k];
     const int ni = F.vertex ? nr + 1 : nr, nj = F.vertex ? nz + 1 : nz;
     for (int j = 0; j < nj; ++j)
         for (int i = 0; i < ni; ++i) {
@@ -709,16 +737,22 @@ salec_status salec_set_field(salec_ctx* ctx, int field, const double* host_in, s
     const size_t cnt = loc_count(ctx, F);
     if (!cnt) return SALEC_OK;
     std::vector<double> buf(cnt * F.stride);
-    cudaError_t e = cudaMemcpyAsync(buf.data(), ctx->base + F.off, cnt * F.stride * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream);
+    std::vector<float> fbuf(F.es == sizeof(float) ? cnt * F.stride : 0);
+    void* raw = F.es == sizeof(float) ? (void*)fbuf.data() : (void*)buf.data();
+    cudaError_t e = cudaMemcpyAsync(raw, ctx->base + F.off, cnt * F.stride * F.es, cudaMemcpyDeviceToHost, ctx->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
     if (e != cudaSuccess) return cuda_check(ctx, e, "set field (read)");
+    if (F.es == sizeof(float))
+        for (size_t k = 0; k < cnt * F.stride; ++k) buf[k] = (double)fbuf[k];
     const int ni = F.vertex ? nr + 1 : nr, nj = F.vertex ? nz + 1 : nz;
     for (int j = 0; j < nj; ++j)
         for (int i = 0; i < ni; ++i) {
             const long k = strip_index(ctx, F, i, j);
             if (k >= 0) buf[(size_t)k * F.stride + F.comp] = host_in[(size_t)j * ni + i];
         }
-    e = cudaMemcpyAsync(ctx->base + F.off, buf.data(), cnt * F.stride * sizeof(double), cudaMemcpyHostToDevice, ctx->stream);
+    if (F.es == sizeof(float))
+        for (size_t k = 0; k < cnt * F.stride; ++k) fbuf[k] = (float)buf[k];
+    e = cudaMemcpyAsync(ctx->base + F.off, raw, cnt * F.stride * F.es, cudaMemcpyHostToDevice, ctx->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
     return cuda_check(ctx, e, "set field (write)");
 }
@@ -732,7 +766,8 @@ salec_status salec_crater_profile(salec_ctx* ctx, double z_surface, int npts, do
     const double dx = ctx->g.dx;
     std::vector<double> h(nr);
     double* tmp = at<double>(ctx, ctx->L.tmp);
-    cudaError_t e = launch_column_heights(ctx->P, tmp, ctx->stream);
+    cudaError_t e = mixed(ctx) ? launch_column_heights<float>(ctx->Pf, tmp, ctx->stream)
+                               : launch_column_heights<double>(ctx->Pd, tmp, ctx->stream);
     if (e == cudaSuccess) e = cudaMemcpyAsync(h.data(), tmp, nr * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
     if (e != cudaSuccess) return cuda_check(ctx, e, "crater profile");
@@ -776,7 +811,8 @@ salec_status salec_conservation(salec_ctx* ctx, double out[4])
     if (!ctx->finalized) return fail(ctx, SALEC_EORDER, "conservation before finalize");
     double* part = at<double>(ctx, ctx->L.partial);
     int nb = 0;
-    cudaError_t e = launch_conservation(ctx->P, part, &nb, ctx->stream);
+    cudaError_t e = mixed(ctx) ? launch_conservation<float>(ctx->Pf, part, &nb, ctx->stream)
+                               : launch_conservation<double>(ctx->Pd, part, &nb, ctx->stream);
     std::vector<double> h((size_t)4 * nb);
     if (e == cudaSuccess) e = cudaMemcpyAsync(h.data(), part, h.size() * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);

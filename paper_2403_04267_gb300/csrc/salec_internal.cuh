@@ -1,6 +1,12 @@
 // salec_internal.cuh -- shared definitions of the CUDA library: parameter blocks passed
 // to the kernels by value, the device-state layout, and the material laws used on both
 // the host (set-up) and the device (time step).
+//
+// Two arithmetic forms share the kernels through the element type T:
+//   T = double  the FP64 form;
+//   T = float   the mixed form: fields, stencils and material laws in FP32, while the
+//               specific internal energy I, its updates, the Courant reduction and the
+//               conservation sums stay FP64.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -15,12 +21,27 @@ constexpr int kBlockX = 32;
 constexpr int kBlockY = 8;
 constexpr int kThreads = kBlockX * kBlockY;
 
-// Material constants with the derived quantities the kernels use.
-struct Mat {
-    int eos, strength;
-    double rho0, inv_rho0, rho0sq_E0, A, B, E0, a, b, alpha, beta, Eiv, Ecv, inv_dE, gamma;
-    double Yi0, mui, Yim, Yd0, mud, Ydm, inv_Yspan, G, eps_fb, B_dam, p_bd, p_t, c2_floor;
+// vector types of an element type
+template <typename T> struct VT;
+template <> struct VT<double> {
+    typedef double2 T2;
+    typedef double4_32a T4;
+    __host__ __device__ static double2 mk(double a, double b) { return make_double2(a, b); }
 };
+template <> struct VT<float> {
+    typedef float2 T2;
+    typedef float4 T4;
+    __host__ __device__ static float2 mk(float a, float b) { return make_float2(a, b); }
+};
+
+// Material constants with the derived quantities the kernels use.
+template <typename T>
+struct MatT {
+    int eos, strength;
+    T rho0, inv_rho0, rho0sq_E0, A, B, E0, a, b, alpha, beta, Eiv, Ecv, inv_dE, gamma;
+    T Yi0, mui, Yim, Yd0, mud, Ydm, inv_Yspan, G, eps_fb, B_dam, p_bd, p_t, c2_floor;
+};
+typedef MatT<double> Mat;
 
 // Scalars of a run, resident on the device.
 struct DevScalars {
@@ -32,57 +53,70 @@ struct DevScalars {
 };
 
 // Device pointers into the caller's state buffer.
-struct Ptrs {
+template <typename T>
+struct PtrsT {
+    typedef typename VT<T>::T2 T2;
+    typedef typename VT<T>::T4 T4;
     // persistent cell state
-    double2* fr[kMaxMat];   // (f_m, rho_m)
-    double* I;              // specific internal energy
-    double2* s01;           // (s_rr, s_zz)        [strength only]
-    double2* s2d;           // (s_rz, D)           [strength only]
-    double* pmax;           // running peak over-pressure
-    double2* v;             // vertex (v_r, v_z)
+    T2* fr[kMaxMat];        // (f_m, rho_m)
+    double* I;              // specific internal energy (FP64 in every form)
+    T2* s01;                // (s_rr, s_zz)        [strength only]
+    T2* s2d;                // (s_rz, D)           [strength only]
+    T* pmax;                // running peak over-pressure
+    T2* v;                  // vertex (v_r, v_z)
     // PML auxiliaries (compact strips)
-    double2* pb_c;          // bottom cells (phi1, phi3), index j*nr + i, j < pb
-    double* pb_psi2;        // bottom cells psi2
-    double4_32a* pb_v;      // bottom vertices (phi2r, phi2z, psi1r, psi1z), index j*(nr+1)+i, j < pb
-    double2* pr_c;          // right cells (phi1, phi3), index j*pr + (i - (nr - pr))
-    double* pr_psi2;
-    double4_32a* pr_v;      // right vertices, index j*pr + (i - (nr - pr + 1)), i > nr - pr
+    T2* pb_c;               // bottom cells (phi1, phi3), index j*nr + i, j < pb
+    T* pb_psi2;             // bottom cells psi2
+    T4* pb_v;               // bottom vertices (phi2r, phi2z, psi1r, psi1z), index j*(nr+1)+i, j < pb
+    T2* pr_c;               // right cells (phi1, phi3), index j*pr + (i - (nr - pr))
+    T* pr_psi2;
+    T4* pr_v;               // right vertices, index j*pr + (i - (nr - pr + 1)), i > nr - pr
     // tables
-    const double* A_R;      // nr+1 radial face areas
-    const double* A_Z;      // nr vertical face areas
-    const double* V;        // nr cell volumes
-    const double* invV;     // nr
-    const double* inv2rc;   // nr  1 / (2 r_c)
-    const double* p0;       // nz reference pressure per row
-    const double* rho_ref;  // nz
+    const T* A_R;           // nr+1 radial face areas
+    const T* A_Z;           // nr vertical face areas
+    const T* V;             // nr cell volumes
+    const T* invV;          // nr
+    const T* inv2rc;        // nr  1 / (2 r_c)
+    const T* p0;            // nz reference pressure per row
+    const T* rho_ref;       // nz
     const double* I_ref;    // nz
-    const double* dB_c;     // nz   bottom-strip profile at cell centres
-    const double* dB_v;     // nz+1 bottom-strip profile at vertices
-    const double* dR_c;     // nr
-    const double* dR_v;     // nr+1
+    const T* dB_c;          // nz   bottom-strip profile at cell centres
+    const T* dB_v;          // nz+1 bottom-strip profile at vertices
+    const T* dR_c;          // nr
+    const T* dR_v;          // nr+1
     // per-step scratch
-    double2* PM;            // (P, M) per cell
-    double2* pbphi;         // (p_bar, Phi) per cell
-    double2* vL;            // Lagrangian vertex velocity
-    double* mv;             // vertex mass
-    double* dK;             // Lagrangian kinetic-energy deficit per vertex
-    double* kheat;          // specific heat returned per vertex
-    double2* frL[kMaxMat];  // Lagrangian (f_m^L, rho_m^L)
-    double2* VIL;           // (V^L, I^L)
-    double2* sL01;          // Lagrangian (s_rr, s_zz)
-    double2* sL2d;          // Lagrangian (s_rz, D)
-    double* dMR;            // signed mass flux through radial faces, (nr+1) x nz
-    double* dMZ;            // signed mass flux through vertical faces, nr x (nz+1)
+    T2* PM;                 // (P, M) per cell
+    T2* pbphi;              // (p_bar, Phi) per cell
+    T2* vL;                 // Lagrangian vertex velocity
+    T* mv;                  // vertex mass
+    T* dK;                  // Lagrangian kinetic-energy deficit per vertex
+    T* kheat;               // specific heat returned per vertex
+    T2* frL[kMaxMat];       // Lagrangian (f_m^L, rho_m^L)
+    T* VL;                  // Lagrangian cell volume
+    double* IL;             // Lagrangian specific internal energy
+    T2* sL01;               // Lagrangian (s_rr, s_zz)
+    T2* sL2d;               // Lagrangian (s_rz, D)
+    T* dMR;                 // signed mass flux through radial faces, (nr+1) x nz
+    T* dMZ;                 // signed mass flux through vertical faces, nr x (nz+1)
     double* partial;        // per-block reduction partials
     DevScalars* scal;
 };
 
-struct Params {
+template <typename T>
+struct ParamsT {
     int nr, nz, nmat, pr, pb, bc_top, bc_bottom, any_strength, nblk_cells;
-    double dx, dx2, cfl, growth, dt_max, dt_min, g, cq, cl, f_min;
-    Mat mat[kMaxMat];
-    Ptrs p;
+    T dx, dx2, cfl, g, cq, cl, f_min;
+    double dxd, cfld, growth, dt_max, dt_min;
+    MatT<T> mat[kMaxMat];
+    PtrsT<T> p;
 };
+
+template <typename T> __host__ __device__ inline T t_exp(T x);
+template <> __host__ __device__ inline double t_exp<double>(double x) { return exp(x); }
+template <> __host__ __device__ inline float t_exp<float>(float x) { return expf(x); }
+template <typename T> __host__ __device__ inline T t_sqrt(T x);
+template <> __host__ __device__ inline double t_sqrt<double>(double x) { return sqrt(x); }
+template <> __host__ __device__ inline float t_sqrt<float>(float x) { return sqrtf(x); }
 
 // ---------------------------------------------------------------------------------
 // Tillotson (1962) equation of state as the paper's SALEc heritage uses it (Sect. 1,
@@ -90,95 +124,104 @@ struct Params {
 // exponential terms, linear blend in I between E_iv and E_cv.  Returns the pressure
 // before the tension cut-off and c^2 = dp/drho + p/rho^2 dp/dI (floored).
 // ---------------------------------------------------------------------------------
-__host__ __device__ inline void eos_eval(const Mat& m, double rho, double I_in, double& p_out, double& c2_out)
+template <typename T>
+__host__ __device__ inline void eos_eval(const MatT<T>& m, T rho, T I_in, T& p_out, T& c2_out)
 {
-    const double I = I_in > 0.0 ? I_in : 0.0;
+    const T zero = T(0), one = T(1), two = T(2);
+    const T I = I_in > zero ? I_in : zero;
     if (m.eos == SALEC_EOS_IDEAL_GAS) {
-        const double gm1 = m.gamma - 1.0;
+        const T gm1 = m.gamma - one;
         p_out = gm1 * rho * I;
         c2_out = m.gamma * gm1 * I;
         return;
     }
     // two divisions: 1/rho and 1/w0 (1/(E0 eta^2) = (rho0^2/E0) / rho^2)
-    const double irho = 1.0 / rho;
-    const double mu = (rho - m.rho0) * m.inv_rho0;
-    const double ie = m.rho0sq_E0 * irho * irho;        // 1 / (E0 eta^2)
-    const double w0 = I * ie + 1.0;
-    const double iw = 1.0 / w0;
-    const double bw = m.b * iw;                         // b / w0
-    const double dw = bw * iw * I * ie;                 // b I / (w0^2 E0 eta^2)
+    const T irho = one / rho;
+    const T mu = (rho - m.rho0) * m.inv_rho0;
+    const T ie = m.rho0sq_E0 * irho * irho;            // 1 / (E0 eta^2)
+    const T w0 = I * ie + one;
+    const T iw = one / w0;
+    const T bw = m.b * iw;                             // b / w0
+    const T dw = bw * iw * I * ie;                     // b I / (w0^2 E0 eta^2)
     // compressed branch and its partial derivatives
-    const double pc = (m.a + bw) * rho * I + mu * (m.A + m.B * mu);
-    const double pc_r = (m.a + bw) * I + 2.0 * dw * I + (m.A + 2.0 * m.B * mu) * m.inv_rho0;
-    const double pc_I = rho * (m.a + bw - dw);
-    double p, p_r, p_I;
+    const T pc = (m.a + bw) * rho * I + mu * (m.A + m.B * mu);
+    const T pc_r = (m.a + bw) * I + two * dw * I + (m.A + two * m.B * mu) * m.inv_rho0;
+    const T pc_I = rho * (m.a + bw - dw);
+    T p, p_r, p_I;
     if (rho >= m.rho0 || I <= m.Eiv) {
         p = pc; p_r = pc_r; p_I = pc_I;
     } else {
-        const double x = m.rho0 * irho - 1.0;            // rho0/rho - 1
-        const double x_r = -m.rho0 * irho * irho;        // dx/drho
-        const double ea = exp(-m.alpha * x * x);
-        const double eb = exp(-m.beta * x);
-        const double tb = bw * rho * I;                  // b rho I / w0
-        const double tb_r = bw * I + 2.0 * dw * I;
-        const double ta = m.A * mu * eb;
-        const double ta_r = m.A * m.inv_rho0 * eb - m.beta * x_r * ta;
-        const double tsum = tb + ta;
-        const double pe = m.a * rho * I + tsum * ea;
-        const double pe_r = m.a * I + (tb_r + ta_r) * ea - 2.0 * m.alpha * x * x_r * tsum * ea;
-        const double pe_I = m.a * rho + rho * (bw - dw) * ea;
+        const T x = m.rho0 * irho - one;               // rho0/rho - 1
+        const T x_r = -m.rho0 * irho * irho;           // dx/drho
+        const T ea = t_exp<T>(-m.alpha * x * x);
+        const T eb = t_exp<T>(-m.beta * x);
+        const T tb = bw * rho * I;                     // b rho I / w0
+        const T tb_r = bw * I + two * dw * I;
+        const T ta = m.A * mu * eb;
+        const T ta_r = m.A * m.inv_rho0 * eb - m.beta * x_r * ta;
+        const T tsum = tb + ta;
+        const T pe = m.a * rho * I + tsum * ea;
+        const T pe_r = m.a * I + (tb_r + ta_r) * ea - two * m.alpha * x * x_r * tsum * ea;
+        const T pe_I = m.a * rho + rho * (bw - dw) * ea;
         if (I >= m.Ecv) {
             p = pe; p_r = pe_r; p_I = pe_I;
         } else {
-            const double we = (I - m.Eiv) * m.inv_dE, wc = (m.Ecv - I) * m.inv_dE;
+            const T we = (I - m.Eiv) * m.inv_dE, wc = (m.Ecv - I) * m.inv_dE;
             p = we * pe + wc * pc;
             p_r = we * pe_r + wc * pc_r;
             p_I = we * pe_I + wc * pc_I + (pe - pc) * m.inv_dE;
         }
     }
-    double c2 = p_r + p * irho * irho * p_I;
+    T c2 = p_r + p * irho * irho * p_I;
     if (!(c2 > m.c2_floor)) c2 = m.c2_floor;
     p_out = p;
     c2_out = c2;
 }
 
 // Collins et al. (2004) yield strength blended by damage, at max(p, 0).
-__host__ __device__ inline double yield_eval(const Mat& m, double p_in, double D)
+template <typename T>
+__host__ __device__ inline T yield_eval(const MatT<T>& m, T p_in, T D)
 {
-    const double p = p_in > 0.0 ? p_in : 0.0;
-    const double Yi = m.Yi0 + m.mui * p / (1.0 + m.mui * p * m.inv_Yspan);
-    double Yd = m.Yd0 + m.mud * p;
+    const T zero = T(0), one = T(1);
+    const T p = p_in > zero ? p_in : zero;
+    const T Yi = m.Yi0 + m.mui * p / (one + m.mui * p * m.inv_Yspan);
+    T Yd = m.Yd0 + m.mud * p;
     Yd = Yd < m.Ydm ? Yd : m.Ydm;
-    const double Y = (1.0 - D) * Yi + D * Yd;
-    return Y > 0.0 ? Y : 0.0;
+    const T Y = (one - D) * Yi + D * Yd;
+    return Y > zero ? Y : zero;
 }
 
-// launchers (salec_kernels.cu)
-cudaError_t launch_step(const Params& P, cudaStream_t s, cudaEvent_t* ev);
+// Sign tests on the bit pattern: integer instructions instead of floating-point compares
+// (FP64 compares issue on the FP64 pipe, the bottleneck of the FP64 form).  pos(x): x > 0
+// (or +NaN); neg(x): x < 0 or x == -0 (callers then move zero volume).
+__device__ __forceinline__ bool pos(double x) { return __double_as_longlong(x) > 0; }
+__device__ __forceinline__ bool neg(double x) { return __double_as_longlong(x) < 0; }
+__device__ __forceinline__ bool pos(float x) { return __float_as_int(x) > 0; }
+__device__ __forceinline__ bool neg(float x) { return __float_as_int(x) < 0; }
+__device__ __forceinline__ bool is_nan(double x)
+{
+    return (__double_as_longlong(x) & 0x7fffffffffffffffLL) > 0x7ff0000000000000LL;
+}
+__device__ __forceinline__ bool is_nan(float x) { return (__float_as_int(x) & 0x7fffffff) > 0x7f800000; }
+// max of two non-negative numbers by their bit patterns
+__device__ __forceinline__ double max_nonneg(double a, double b)
+{
+    return __longlong_as_double(max(__double_as_longlong(a), __double_as_longlong(b)));
+}
+__device__ __forceinline__ float max_nonneg(float a, float b)
+{
+    return __int_as_float(max(__float_as_int(a), __float_as_int(b)));
+}
+
+// launchers (salec_kernels.cu), instantiated for T = double and T = float
+template <typename T> cudaError_t launch_step(const ParamsT<T>& P, cudaStream_t s, cudaEvent_t* ev);
+template <typename T> cudaError_t launch_pressure(const ParamsT<T>& P, double* out, cudaStream_t s);
+template <typename T> cudaError_t launch_column_heights(const ParamsT<T>& P, double* heights, cudaStream_t s);
+template <typename T> cudaError_t launch_conservation(const ParamsT<T>& P, double* partial4, int* nblocks, cudaStream_t s);
 const char* kernel_name(int k);
-cudaError_t launch_pressure(const Params& P, double* out, cudaStream_t s);
-cudaError_t launch_column_heights(const Params& P, double* heights, cudaStream_t s);
-cudaError_t launch_conservation(const Params& P, double* partial4, int* nblocks, cudaStream_t s);
 int launches_per_step();
 const char* noalloc_last_error();
 int cell_blocks(int nr, int nz);
 int vertex_blocks(int nr, int nz);
 
-}  // namespace salec
-
-namespace salec {
-// Sign tests on the bit pattern: integer instructions instead of FP64 compares (which
-// issue on the FP64 pipe, the bottleneck of the FP64 form).  pos(x): x > 0 (or +NaN);
-// neg(x): x < 0 or x == -0.0 (callers treat -0.0 like 0 by moving zero volume).
-__device__ __forceinline__ bool pos(double x) { return __double_as_longlong(x) > 0; }
-__device__ __forceinline__ bool neg(double x) { return __double_as_longlong(x) < 0; }
-__device__ __forceinline__ bool is_nan(double x)
-{
-    return (__double_as_longlong(x) & 0x7fffffffffffffffLL) > 0x7ff0000000000000LL;
-}
-// max of two non-negative doubles by their bit patterns
-__device__ __forceinline__ double max_nonneg(double a, double b)
-{
-    return __longlong_as_double(max(__double_as_longlong(a), __double_as_longlong(b)));
-}
 }  // namespace salec

@@ -15,6 +15,8 @@ from . import build as _build
 
 SALEC_OK, SALEC_EINVAL, SALEC_ENOMEM, SALEC_ECUDA, SALEC_EORDER, SALEC_EUNSTABLE = range(6)
 SALEC_FP64 = 0
+SALEC_FP32MIX = 1
+PRECISIONS = {"fp64": SALEC_FP64, "fp32mix": SALEC_FP32MIX}
 _STATUS = {0: "SALEC_OK", 1: "SALEC_EINVAL", 2: "SALEC_ENOMEM", 3: "SALEC_ECUDA", 4: "SALEC_EORDER",
            5: "SALEC_EUNSTABLE"}
 
@@ -143,22 +145,25 @@ def make_material(d: dict) -> salec_material:
 
 class Sim:
     """One simulation on the current CUDA device.  ``spec`` is a workload dictionary
-    (see workloads.py).  The device state is one torch uint8 tensor owned here."""
+    (see workloads.py); ``precision`` is "fp64" or "fp32mix" (FP32 fields and stencils,
+    FP64 specific internal energy, Courant reduction and sums).  The device state is one
+    torch uint8 tensor owned here."""
 
-    def __init__(self, spec: dict, device=None, stream=None):
+    def __init__(self, spec: dict, device=None, stream=None, precision: str = "fp64"):
         import torch
         L = load()
         self.spec = spec
+        self.precision = PRECISIONS[precision]
         self.nmat = len(spec["materials"])
         self.grid = make_grid(spec["grid"], self.nmat)
         self.nr, self.nz = self.grid.nr, self.grid.nz
         nb = C.c_size_t()
-        self._check(L.salec_state_bytes(C.byref(self.grid), SALEC_FP64, C.byref(nb)), None)
+        self._check(L.salec_state_bytes(C.byref(self.grid), self.precision, C.byref(nb)), None)
         self.device = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
         self.state = torch.empty(nb.value, dtype=torch.uint8, device=self.device)
         self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
         h = C.c_void_p()
-        self._check(L.salec_create(C.byref(self.grid), SALEC_FP64, C.c_void_p(self.state.data_ptr()), nb.value,
+        self._check(L.salec_create(C.byref(self.grid), self.precision, C.c_void_p(self.state.data_ptr()), nb.value,
                                    C.c_void_p(self.stream.cuda_stream), C.byref(h)), None)
         self._h = h
         for k, m in enumerate(spec["materials"]):
