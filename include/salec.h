@@ -187,6 +187,41 @@ salec_status salec_set_kernel_timing(salec_ctx* ctx, int on);
 salec_status salec_kernel_times(salec_ctx* ctx, double* avg_ms, int n, int* steps);
 const char* salec_kernel_name(int k);
 
+/* End time of a run (default: none).  salec_batch_run stops a run once t >= t_end; a
+ * run at or past its end time does nothing in a batched step. */
+salec_status salec_set_end_time(salec_ctx* ctx, double t_end);
+
+/* Block shapes (threads in r x threads in z) of the six kernels of a step, as 12 ints
+ * (x0, y0, ..., x5, y5).  x must be a multiple of 32, 128 <= x*y <= 512.  The shape changes
+ * no field, only speed. */
+salec_status salec_set_block_shapes(salec_ctx* ctx, const int* shapes);
+salec_status salec_get_block_shapes(const salec_ctx* ctx, int* shapes);
+
+/* Autotuner: runs trial_steps real steps (after one untimed step) with each candidate
+ * block shape for all kernels, timing every kernel with CUDA events, and keeps for each
+ * kernel its fastest shape (written to shapes_out, 12 ints, if not NULL).  The simulation
+ * advances by (candidates x (trial_steps + 1)) steps, seven candidates. */
+salec_status salec_autotune(salec_ctx* ctx, int trial_steps, int* shapes_out);
+
+/* Batches: many independent runs (each a finalized context with its own state buffer,
+ * all of one precision, material count and strength setting) advanced together: every
+ * step is six launches for the whole batch, one block per (run, tile) entry of a work list,
+ * each run with its own time step and its own end time.  The batch needs one caller-owned
+ * device buffer of salec_batch_bytes() bytes (run parameter blocks and work lists).
+ * salec_batch_run replays a CUDA graph of `chunk` steps until every run reaches its end
+ * time or max_steps steps; salec_batch_poll copies each run's (t, dt, steps, status, t_end)
+ * into out[5 r .. 5 r + 4].  Streams: all batch work goes on the stream given here. */
+typedef struct salec_batch salec_batch;
+salec_status salec_batch_bytes(salec_ctx* const* runs, int nruns, size_t* bytes);
+salec_status salec_batch_create(salec_ctx* const* runs, int nruns, void* dev_buf, size_t bytes, void* stream,
+                                salec_batch** out);
+salec_status salec_batch_step(salec_batch* batch, int nsteps);
+salec_status salec_batch_run(salec_batch* batch, int chunk, long max_steps, long* steps_done, int* runs_done);
+salec_status salec_batch_poll(salec_batch* batch, double* out);
+salec_status salec_batch_autotune(salec_batch* batch, int trial_steps, int* shapes_out);
+const char* salec_batch_last_error(const salec_batch* batch);
+void salec_batch_destroy(salec_batch* batch);
+
 /* Courant time step without any allocation, for callers that cannot allocate or lend
  * device memory (an external memory manager owns every allocation, a plug-in sees only
  * another program's field pointers, the allocator is locked).  The paper has no

@@ -20,6 +20,13 @@ namespace {
 
 constexpr size_t kAlign = 256;
 
+// Block shapes the autotuner tries (threads in x are consecutive cells of a row, so x stays a
+// multiple of the 32-thread warp); the smallest has 128 threads, which sizes the reduction
+// partials.
+const dim3 kShapes[] = {dim3(32, 4), dim3(32, 8), dim3(32, 16), dim3(64, 4), dim3(64, 8), dim3(128, 2), dim3(128, 4)};
+constexpr int kNumShapes = sizeof(kShapes) / sizeof(kShapes[0]);
+const dim3 kDefaultShape(32, 8);
+
 // Offsets of every array inside the state buffer.  The persistent part (scalars, tables,
 // fields, PML auxiliaries) comes first so a checkpoint is one contiguous range.
 struct Layout {
@@ -87,7 +94,11 @@ Layout make_layout(const salec_grid& g, int precision)
     L.sL2d = take(cur, nc * d2);
     L.dMR = take(cur, (nr + 1) * nz * d);
     L.dMZ = take(cur, nr * (nz + 1) * d);
-    const size_t nb = (size_t)cell_blocks(g.nr, g.nz);
+    size_t nb = 0;
+    for (int k = 0; k < kNumShapes; ++k) {
+        const size_t t = (size_t)tiles_of(g.nr, g.nz, 0, kShapes[k]);
+        nb = t > nb ? t : nb;
+    }
     const size_t nbv = (size_t)vertex_blocks(g.nr, g.nz);
     L.partial = take(cur, (nb > 4 * nbv ? nb : 4 * nbv) * e8);
     L.tmp = take(cur, nv * e8);
@@ -122,6 +133,7 @@ struct salec_ctx {
     bool finalized;
     ParamsT<double> Pd;     // FP64 form
     ParamsT<float> Pf;      // mixed form
+    dim3 shape[6];          // block shape of each kernel (salec_autotune picks them)
     // set-up accumulators (host, freed at finalize)
     std::vector<double> sV[kMaxMat], sM[kMaxMat], sE, sPz;
     std::vector<double> sR[kMaxMat];      // density shared by all contributions (exact)
@@ -245,6 +257,7 @@ salec_status salec_create(const salec_grid* grid, int precision, void* dev_state
     memset(ctx->mats, 0, sizeof(ctx->mats));
     for (int m = 0; m < kMaxMat; ++m) ctx->mat_set[m] = false;
     ctx->finalized = false;
+    for (int k = 0; k < 6; ++k) ctx->shape[k] = kDefaultShape;
     const size_t nc = (size_t)grid->nr * grid->nz;
     for (int m = 0; m < grid->nmat; ++m) {
         ctx->sV[m].assign(nc, 0.0); ctx->sM[m].assign(nc, 0.0);
@@ -488,6 +501,8 @@ salec_status salec_finalize(salec_ctx* ctx)
     DevScalars s;
     memset(&s, 0, sizeof(s));
     s.dt_prev = g.dt_init;
+    s.t_end = 1e300;
+    s.active = 1;
     const Layout& L = ctx->L;
     cudaStream_t st = ctx->stream;
     cudaError_t e = cudaMemsetAsync(ctx->base, 0, L.persist_end, st);
@@ -548,8 +563,8 @@ salec_status salec_step(salec_ctx* ctx, int nsteps)
             evp = ctx->ev.data() + ctx->ev_used;
             ctx->ev_used += K;
         }
-        cudaError_t e = mixed(ctx) ? launch_step<float>(ctx->Pf, ctx->stream, evp)
-                                   : launch_step<double>(ctx->Pd, ctx->stream, evp);
+        cudaError_t e = mixed(ctx) ? launch_step<float>(ctx->Pf, ctx->shape, ctx->stream, evp)
+                                   : launch_step<double>(ctx->Pd, ctx->shape, ctx->stream, evp);
         if (e != cudaSuccess) return cuda_check(ctx, e, "step launch");
     }
     return SALEC_OK;
@@ -849,6 +864,396 @@ salec_status salec_set_state(salec_ctx* ctx, const void* host, size_t bytes)
     cudaError_t e = cudaMemcpyAsync(ctx->base, host, bytes, cudaMemcpyHostToDevice, ctx->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
     return cuda_check(ctx, e, "set_state");
+}
+
+salec_status salec_set_end_time(salec_ctx* ctx, double t_end)
+{
+    if (!ctx) return SALEC_EINVAL;
+    if (!ctx->finalized) return fail(ctx, SALEC_EORDER, "set_end_time before finalize");
+    DevScalars* d = at<DevScalars>(ctx, ctx->L.scal);
+    cudaError_t e = cudaMemcpyAsync(&d->t_end, &t_end, sizeof(double), cudaMemcpyHostToDevice, ctx->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+    return cuda_check(ctx, e, "set_end_time");
+}
+
+static bool shape_ok(unsigned x, unsigned y)
+{
+    return x >= 32 && x % 32 == 0 && y >= 1 && x * y <= (unsigned)kMaxThreads && x * y >= 128;
+}
+
+salec_status salec_set_block_shapes(salec_ctx* ctx, const int* shapes)
+{
+    if (!ctx || !shapes) return SALEC_EINVAL;
+    for (int k = 0; k < 6; ++k)
+        if (!shape_ok((unsigned)shapes[2 * k], (unsigned)shapes[2 * k + 1]))
+            return fail(ctx, SALEC_EINVAL, "block shape %d x %d not allowed", shapes[2 * k], shapes[2 * k + 1]);
+    for (int k = 0; k < 6; ++k) ctx->shape[k] = dim3(shapes[2 * k], shapes[2 * k + 1]);
+    return SALEC_OK;
+}
+
+salec_status salec_get_block_shapes(const salec_ctx* ctx, int* shapes)
+{
+    if (!ctx || !shapes) return SALEC_EINVAL;
+    for (int k = 0; k < 6; ++k) { shapes[2 * k] = (int)ctx->shape[k].x; shapes[2 * k + 1] = (int)ctx->shape[k].y; }
+    return SALEC_OK;
+}
+
+// Autotuner: every candidate block shape runs `trial_steps` real steps of this simulation
+// (after one untimed step) with per-kernel events; each kernel keeps its fastest shape.
+// The state after the call is the state after all those steps: the block shape does not
+// change any field (only the summation order of the diagnostic tallies).
+salec_status salec_autotune(salec_ctx* ctx, int trial_steps, int* shapes_out)
+{
+    if (!ctx || trial_steps < 1) return SALEC_EINVAL;
+    if (!ctx->finalized) return fail(ctx, SALEC_EORDER, "autotune before finalize");
+    const int K = launches_per_step();
+    double best[6];
+    dim3 pick[6];
+    for (int k = 0; k < K; ++k) { best[k] = 1e300; pick[k] = ctx->shape[k]; }
+    const bool was_timing = ctx->timing;
+    for (int c = 0; c < kNumShapes; ++c) {
+        for (int k = 0; k < K; ++k) ctx->shape[k] = kShapes[c];
+        ctx->timing = false;
+        salec_status st = salec_step(ctx, 1);
+        if (st != SALEC_OK) return st;
+        salec_set_kernel_timing(ctx, 1);
+        st = salec_step(ctx, trial_steps);
+        if (st != SALEC_OK) return st;
+        double ms[8];
+        int ns = 0;
+        st = salec_kernel_times(ctx, ms, 8, &ns);
+        if (st != SALEC_OK) return st;
+        for (int k = 0; k < K; ++k)
+            if (ms[k] < best[k]) { best[k] = ms[k]; pick[k] = kShapes[c]; }
+    }
+    for (int k = 0; k < K; ++k) ctx->shape[k] = pick[k];
+    ctx->timing = was_timing;
+    ctx->ev_used = 0;
+    if (shapes_out) salec_get_block_shapes(ctx, shapes_out);
+    return SALEC_OK;
+}
+
+// ---------------------------------------------------------------------------------
+// Batches: many independent runs advanced by one set of launches per step.
+// ---------------------------------------------------------------------------------
+struct salec_batch {
+    std::vector<salec_ctx*> runs;
+    int precision = 0, nmat = 0;
+    bool strength = false;
+    cudaStream_t stream = nullptr;
+    char* dev = nullptr;
+    size_t bytes = 0;
+    size_t off_params = 0, off_poll = 0, off_work[6] = {0, 0, 0, 0, 0, 0};
+    int ntiles[6] = {0, 0, 0, 0, 0, 0};
+    std::vector<char> retired;      // runs left out of the work lists (reached their end time)
+    dim3 shape[6];
+    cudaGraphExec_t graph = nullptr;
+    int graph_steps = 0;
+    bool timing = false;
+    std::vector<cudaEvent_t> ev;
+    size_t ev_used = 0;
+    std::string err;
+};
+
+static salec_status bfail(salec_batch* b, salec_status st, const char* msg)
+{
+    if (b) b->err = msg;
+    return st;
+}
+
+// bytes of the batch buffer: run parameter blocks, a poll area, and for each kernel the
+// largest work list any allowed block shape needs
+static size_t batch_layout(salec_ctx* const* runs, int n, salec_batch* b)
+{
+    size_t cur = 0;
+    const size_t psize = runs[0]->precision == SALEC_FP32MIX ? sizeof(ParamsT<float>) : sizeof(ParamsT<double>);
+    const size_t op = take(cur, psize * (size_t)n);
+    const size_t opoll = take(cur, sizeof(double) * 5 * (size_t)n);
+    size_t ow[6];
+    for (int k = 0; k < 6; ++k) {
+        size_t cap = 0;
+        for (int r = 0; r < n; ++r) {
+            size_t mx = 0;
+            for (int c = 0; c < kNumShapes; ++c) {
+                const size_t t = (size_t)tiles_of(runs[r]->g.nr, runs[r]->g.nz, k, kShapes[c]);
+                mx = t > mx ? t : mx;
+            }
+            cap += mx;
+        }
+        ow[k] = take(cur, cap * sizeof(BatchTile));
+    }
+    if (b) {
+        b->off_params = op;
+        b->off_poll = opoll;
+        for (int k = 0; k < 6; ++k) b->off_work[k] = ow[k];
+    }
+    return cur;
+}
+
+static salec_status batch_check(salec_ctx* const* runs, int n)
+{
+    if (!runs || n < 1) return SALEC_EINVAL;
+    for (int r = 0; r < n; ++r) {
+        if (!runs[r] || !runs[r]->finalized) return SALEC_EORDER;
+        if (runs[r]->precision != runs[0]->precision || runs[r]->g.nmat != runs[0]->g.nmat) return SALEC_EINVAL;
+        const int s0 = runs[0]->Pd.any_strength, sr = runs[r]->Pd.any_strength;
+        if (s0 != sr) return SALEC_EINVAL;
+        if (runs[r]->g.nr + 1 > 0xffff * 32 || runs[r]->g.nz + 1 > 0xffff) return SALEC_EINVAL;
+    }
+    return SALEC_OK;
+}
+
+salec_status salec_batch_bytes(salec_ctx* const* runs, int nruns, size_t* bytes)
+{
+    const salec_status st = batch_check(runs, nruns);
+    if (st != SALEC_OK || !bytes) return st != SALEC_OK ? st : SALEC_EINVAL;
+    *bytes = batch_layout(runs, nruns, nullptr);
+    return SALEC_OK;
+}
+
+static salec_status batch_build_work(salec_batch* b)
+{
+    b->retired.resize(b->runs.size(), 0);
+    for (int k = 0; k < 6; ++k) {
+        std::vector<BatchTile> w;
+        for (int r = 0; r < (int)b->runs.size(); ++r) {
+            if (b->retired[r]) continue;
+            const salec_grid& g = b->runs[r]->g;
+            const int ni = kernel_on_vertices(k) ? g.nr + 1 : g.nr, nj = kernel_on_vertices(k) ? g.nz + 1 : g.nz;
+            const int gx = (ni + (int)b->shape[k].x - 1) / (int)b->shape[k].x;
+            const int gy = (nj + (int)b->shape[k].y - 1) / (int)b->shape[k].y;
+            for (int by = 0; by < gy; ++by)
+                for (int bx = 0; bx < gx; ++bx) w.push_back(BatchTile{r, bx, by, gx | (gy << 16)});
+        }
+        b->ntiles[k] = (int)w.size();
+        cudaError_t e = cudaMemcpyAsync(b->dev + b->off_work[k], w.data(), w.size() * sizeof(BatchTile),
+                                        cudaMemcpyHostToDevice, b->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+        if (e != cudaSuccess) return bfail(b, SALEC_ECUDA, cudaGetErrorString(e));
+    }
+    if (b->graph) { cudaGraphExecDestroy(b->graph); b->graph = nullptr; b->graph_steps = 0; }
+    return SALEC_OK;
+}
+
+salec_status salec_batch_create(salec_ctx* const* runs, int nruns, void* dev_buf, size_t bytes, void* stream,
+                                salec_batch** out)
+{
+    salec_status st = batch_check(runs, nruns);
+    if (st != SALEC_OK || !out) return st != SALEC_OK ? st : SALEC_EINVAL;
+    salec_batch* b = new salec_batch();
+    const size_t need = batch_layout(runs, nruns, b);
+    if (!dev_buf || bytes < need || ((uintptr_t)dev_buf % kAlign) != 0) { delete b; return SALEC_ENOMEM; }
+    b->runs.assign(runs, runs + nruns);
+    b->precision = runs[0]->precision;
+    b->nmat = runs[0]->g.nmat;
+    b->strength = runs[0]->Pd.any_strength != 0;
+    b->stream = (cudaStream_t)stream;
+    b->dev = (char*)dev_buf;
+    b->bytes = bytes;
+    for (int k = 0; k < 6; ++k) b->shape[k] = kDefaultShape;
+    // run parameter blocks
+    cudaError_t e = cudaSuccess;
+    if (b->precision == SALEC_FP32MIX) {
+        std::vector<ParamsT<float>> P(nruns);
+        for (int r = 0; r < nruns; ++r) P[r] = runs[r]->Pf;
+        e = cudaMemcpyAsync(b->dev + b->off_params, P.data(), P.size() * sizeof(P[0]), cudaMemcpyHostToDevice, b->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+    } else {
+        std::vector<ParamsT<double>> P(nruns);
+        for (int r = 0; r < nruns; ++r) P[r] = runs[r]->Pd;
+        e = cudaMemcpyAsync(b->dev + b->off_params, P.data(), P.size() * sizeof(P[0]), cudaMemcpyHostToDevice, b->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+    }
+    if (e != cudaSuccess) { delete b; return SALEC_ECUDA; }
+    st = batch_build_work(b);
+    if (st != SALEC_OK) { delete b; return st; }
+    *out = b;
+    return SALEC_OK;
+}
+
+static cudaError_t batch_launch(salec_batch* b, cudaEvent_t* ev)
+{
+    const BatchTile* work[6];
+    for (int k = 0; k < 6; ++k) work[k] = reinterpret_cast<const BatchTile*>(b->dev + b->off_work[k]);
+    if (b->precision == SALEC_FP32MIX)
+        return launch_batch_step<float>(reinterpret_cast<const ParamsT<float>*>(b->dev + b->off_params), b->nmat,
+                                        b->strength, work, b->ntiles, b->shape, b->stream, ev);
+    return launch_batch_step<double>(reinterpret_cast<const ParamsT<double>*>(b->dev + b->off_params), b->nmat,
+                                     b->strength, work, b->ntiles, b->shape, b->stream, ev);
+}
+
+static salec_status batch_restore_retired(salec_batch* b);
+
+salec_status salec_batch_step(salec_batch* b, int nsteps)
+{
+    if (!b || nsteps < 0) return SALEC_EINVAL;
+    const salec_status st0 = batch_restore_retired(b);
+    if (st0 != SALEC_OK) return st0;
+    const int K = launches_per_step() + 1;
+    for (int n = 0; n < nsteps; ++n) {
+        cudaEvent_t* evp = nullptr;
+        if (b->timing) {
+            while (b->ev_used + K > b->ev.size()) {
+                cudaEvent_t e0;
+                if (cudaEventCreate(&e0) != cudaSuccess) return bfail(b, SALEC_ECUDA, "event create");
+                b->ev.push_back(e0);
+            }
+            evp = b->ev.data() + b->ev_used;
+            b->ev_used += K;
+        }
+        const cudaError_t e = batch_launch(b, evp);
+        if (e != cudaSuccess) return bfail(b, SALEC_ECUDA, cudaGetErrorString(e));
+    }
+    return SALEC_OK;
+}
+
+// Scalars of every run: out[5 r + (0 t, 1 dt, 2 steps, 3 status, 4 t_end)] (synchronises).
+salec_status salec_batch_poll(salec_batch* b, double* out)
+{
+    if (!b || !out) return SALEC_EINVAL;
+    const int n = (int)b->runs.size();
+    double* d = reinterpret_cast<double*>(b->dev + b->off_poll);
+    cudaError_t e = b->precision == SALEC_FP32MIX
+                        ? launch_batch_poll<float>(reinterpret_cast<const ParamsT<float>*>(b->dev + b->off_params), n, d, b->stream)
+                        : launch_batch_poll<double>(reinterpret_cast<const ParamsT<double>*>(b->dev + b->off_params), n, d, b->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(out, d, sizeof(double) * 5 * n, cudaMemcpyDeviceToHost, b->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+    if (e != cudaSuccess) return bfail(b, SALEC_ECUDA, cudaGetErrorString(e));
+    return SALEC_OK;
+}
+
+// Capture `chunk` batched steps as a CUDA graph on the batch stream.
+static salec_status batch_capture(salec_batch* b, int chunk)
+{
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) {
+        (void)cudaGetLastError();   // do not leave the error for a later, unrelated check
+        return bfail(b, SALEC_ECUDA, cudaGetErrorString(e));
+    }
+    for (int k = 0; k < chunk && e == cudaSuccess; ++k) e = batch_launch(b, nullptr);
+    const cudaError_t e2 = cudaStreamEndCapture(b->stream, &g);
+    if (e != cudaSuccess || e2 != cudaSuccess) {
+        if (g) cudaGraphDestroy(g);
+        (void)cudaGetLastError();
+        return bfail(b, SALEC_ECUDA, cudaGetErrorString(e != cudaSuccess ? e : e2));
+    }
+    e = cudaGraphInstantiate(&b->graph, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) { b->graph = nullptr; return bfail(b, SALEC_ECUDA, cudaGetErrorString(e)); }
+    b->graph_steps = chunk;
+    return SALEC_OK;
+}
+
+// Runs left out of the work lists by an earlier salec_batch_run come back (their end time
+// may have changed since).
+static salec_status batch_restore_retired(salec_batch* b)
+{
+    bool any = false;
+    for (char& r : b->retired) { any = any || r; r = 0; }
+    return any ? batch_build_work(b) : SALEC_OK;
+}
+
+// Advance every run until it reaches its end time (salec_set_end_time), in CUDA-graph
+// replays of `chunk` steps (the graph is captured once per block-shape set, chunk size and
+// set of runs), polling completion after each replay; at most max_steps steps.  A run that
+// is done does nothing in later steps (its blocks return at once); once done runs hold an
+// eighth of the blocks they are left out of the work lists and the graph is captured again.
+salec_status salec_batch_run(salec_batch* b, int chunk, long max_steps, long* steps_done, int* runs_done)
+{
+    if (!b || chunk < 1 || max_steps < 0) return SALEC_EINVAL;
+    const int n = (int)b->runs.size();
+    if (b->stream == nullptr || b->stream == cudaStreamLegacy || b->stream == cudaStreamPerThread)
+        return bfail(b, SALEC_EINVAL, "batch_run captures a CUDA graph and needs a created stream, "
+                                      "not a default stream");
+    salec_status st0 = batch_restore_retired(b);
+    if (st0 != SALEC_OK) return st0;
+    if (b->graph && b->graph_steps != chunk) { cudaGraphExecDestroy(b->graph); b->graph = nullptr; }
+    std::vector<double> poll((size_t)5 * n);
+    long done_steps = 0;
+    int done = 0;
+    while (done_steps < max_steps) {
+        if (!b->graph) {
+            const salec_status st = batch_capture(b, chunk);
+            if (st != SALEC_OK) return st;
+        }
+        const cudaError_t e = cudaGraphLaunch(b->graph, b->stream);
+        if (e != cudaSuccess) return bfail(b, SALEC_ECUDA, cudaGetErrorString(e));
+        done_steps += chunk;
+        const salec_status st = salec_batch_poll(b, poll.data());
+        if (st != SALEC_OK) return st;
+        done = 0;
+        long tiles_done = 0, tiles_all = 0;
+        for (int r = 0; r < n; ++r) {
+            const bool d = poll[5 * r] >= poll[5 * r + 4];
+            done += d;
+            if (!b->retired[r]) {
+                const long t = tiles_of(b->runs[r]->g.nr, b->runs[r]->g.nz, 3, b->shape[3]);
+                tiles_all += t;
+                if (d) tiles_done += t;
+            }
+        }
+        if (done == n) break;
+        // once finished runs hold an eighth of the blocks, leave them out of the work lists
+        // (their blocks only return early) and capture the graph again
+        if (8 * tiles_done >= tiles_all && tiles_done > 0) {
+            for (int r = 0; r < n; ++r)
+                if (poll[5 * r] >= poll[5 * r + 4]) b->retired[r] = 1;
+            const salec_status st2 = batch_build_work(b);
+            if (st2 != SALEC_OK) return st2;
+        }
+    }
+    if (steps_done) *steps_done = done_steps;
+    if (runs_done) *runs_done = done;
+    return SALEC_OK;
+}
+
+salec_status salec_batch_autotune(salec_batch* b, int trial_steps, int* shapes_out)
+{
+    if (!b || trial_steps < 1) return SALEC_EINVAL;
+    const int K = launches_per_step();
+    double best[6];
+    dim3 pick[6];
+    for (int k = 0; k < K; ++k) { best[k] = 1e300; pick[k] = b->shape[k]; }
+    for (int c = 0; c < kNumShapes; ++c) {
+        for (int k = 0; k < K; ++k) b->shape[k] = kShapes[c];
+        salec_status st = batch_build_work(b);
+        if (st != SALEC_OK) return st;
+        b->timing = false;
+        st = salec_batch_step(b, 1);
+        if (st != SALEC_OK) return st;
+        b->timing = true;
+        b->ev_used = 0;
+        st = salec_batch_step(b, trial_steps);
+        if (st != SALEC_OK) return st;
+        if (cudaStreamSynchronize(b->stream) != cudaSuccess) return bfail(b, SALEC_ECUDA, "sync");
+        for (int k = 0; k < K; ++k) {
+            double tot = 0.0;
+            for (int s = 0; s < trial_steps; ++s) {
+                float ms = 0.0f;
+                cudaEventElapsedTime(&ms, b->ev[(size_t)s * (K + 1) + k], b->ev[(size_t)s * (K + 1) + k + 1]);
+                tot += ms;
+            }
+            if (tot < best[k]) { best[k] = tot; pick[k] = kShapes[c]; }
+        }
+        b->timing = false;
+        b->ev_used = 0;
+    }
+    for (int k = 0; k < K; ++k) b->shape[k] = pick[k];
+    const salec_status st = batch_build_work(b);
+    if (shapes_out)
+        for (int k = 0; k < K; ++k) { shapes_out[2 * k] = (int)pick[k].x; shapes_out[2 * k + 1] = (int)pick[k].y; }
+    return st;
+}
+
+const char* salec_batch_last_error(const salec_batch* b) { return b ? b->err.c_str() : "null batch"; }
+
+void salec_batch_destroy(salec_batch* b)
+{
+    if (!b) return;
+    if (b->graph) cudaGraphExecDestroy(b->graph);
+    for (cudaEvent_t e : b->ev) cudaEventDestroy(e);
+    delete b;
 }
 
 int salec_launches_per_step(const salec_ctx* ctx)

@@ -20,6 +20,11 @@ constexpr int kMaxMat = 3;
 constexpr int kBlockX = 32;
 constexpr int kBlockY = 8;
 constexpr int kThreads = kBlockX * kBlockY;
+constexpr int kMaxThreads = 512;      // largest block shape any kernel is launched with
+
+// one entry of a batched launch: block (bx, by) of run `run`, whose grid of blocks is
+// (g & 0xffff) x (g >> 16)
+struct BatchTile { int run, bx, by, g; };
 
 // vector types of an element type
 template <typename T> struct VT;
@@ -45,11 +50,13 @@ typedef MatT<double> Mat;
 
 // Scalars of a run, resident on the device.
 struct DevScalars {
-    double t, dt, dt_prev, pad0;
+    double t, dt, dt_prev, t_end;   // t_end: a batched run stops stepping once t >= t_end
     double mass_out, mass_discarded, mass_pml, zmom_out;
     unsigned long long nstep;
     unsigned int counter;   // last-block counter of the dt reduction
     int status;             // bit 1: non-positive volume or density, 2: NaN, 4: dt < dt_min
+    int active;             // the run stepped in the current batched step
+    int pad1;
 };
 
 // Device pointers into the caller's state buffer.
@@ -214,7 +221,13 @@ __device__ __forceinline__ float max_nonneg(float a, float b)
 }
 
 // launchers (salec_kernels.cu), instantiated for T = double and T = float
-template <typename T> cudaError_t launch_step(const ParamsT<T>& P, cudaStream_t s, cudaEvent_t* ev);
+template <typename T> cudaError_t launch_step(const ParamsT<T>& P, const dim3* blk, cudaStream_t s, cudaEvent_t* ev);
+template <typename T>
+cudaError_t launch_batch_step(const ParamsT<T>* runs_dev, int nmat, bool strength, const BatchTile* const* work,
+                              const int* ntiles, const dim3* blk, cudaStream_t s, cudaEvent_t* ev);
+template <typename T> cudaError_t launch_batch_poll(const ParamsT<T>* runs_dev, int n, double* out, cudaStream_t s);
+bool kernel_on_vertices(int k);
+int tiles_of(int nr, int nz, int k, dim3 blk);
 template <typename T> cudaError_t launch_pressure(const ParamsT<T>& P, double* out, cudaStream_t s);
 template <typename T> cudaError_t launch_column_heights(const ParamsT<T>& P, double* heights, cudaStream_t s);
 template <typename T> cudaError_t launch_conservation(const ParamsT<T>& P, double* partial4, int* nblocks, cudaStream_t s);

@@ -26,17 +26,18 @@ __device__ __forceinline__ double warp_sum(double v)
     return v;
 }
 
-// block-wide sum, result valid in thread 0
+// block-wide sum, result valid in thread 0 (blocks are whole warps, at most kMaxThreads)
 __device__ double block_sum(double v, double* sh)
 {
     const int tid = threadIdx.y * blockDim.x + threadIdx.x;
+    const int nw = (blockDim.x * blockDim.y) >> 5;
     v = warp_sum(v);
     __syncthreads();
     if ((tid & 31) == 0) sh[tid >> 5] = v;
     __syncthreads();
     double s = 0.0;
     if (tid == 0)
-        for (int w = 0; w < kThreads / 32; ++w) s += sh[w];
+        for (int w = 0; w < nw; ++w) s += sh[w];
     return s;
 }
 
@@ -44,12 +45,12 @@ __device__ double block_sum(double v, double* sh)
 // Phase 0: equation of state, artificial viscosity and the Courant time step.
 // ---------------------------------------------------------------------------------
 template <typename T, int NM, bool STR>
-__global__ void __launch_bounds__(kThreads) k_phase0(ParamsT<T> P)
+__device__ __forceinline__ void body_phase0(const ParamsT<T>& P, int bx, int by, int gx, int gy)
 {
     typedef VT<T> V;
     const T zero = T(0), one = T(1), half = T(0.5);
-    const int i = blockIdx.x * kBlockX + threadIdx.x;
-    const int j = blockIdx.y * kBlockY + threadIdx.y;
+    const int i = bx * blockDim.x + threadIdx.x;
+    const int j = by * blockDim.y + threadIdx.y;
     const int nr = P.nr;
     const PtrsT<T>& p = P.p;
     // largest |v| + c of the block; min over cells of dx / (|v| + c) equals dx / max(|v| + c)
@@ -109,18 +110,19 @@ __global__ void __launch_bounds__(kThreads) k_phase0(ParamsT<T> P)
     }
     // block maximum (on the bit patterns of the non-negative speeds), then the last block
     // to finish reduces the block maxima
-    __shared__ long long sh[kThreads / 32];
+    __shared__ long long sh[kMaxThreads / 32];
     __shared__ bool last;
-    const int tid = threadIdx.y * kBlockX + threadIdx.x;
+    const int tid = threadIdx.y * blockDim.x + threadIdx.x;
+    const int nw = (blockDim.x * blockDim.y) >> 5;
     for (int o = 16; o > 0; o >>= 1) speed = max_nonneg(speed, __shfl_down_sync(0xffffffffu, speed, o));
     if ((tid & 31) == 0) sh[tid >> 5] = __double_as_longlong(double(speed));
     __syncthreads();
-    const int nblk = gridDim.x * gridDim.y;
+    const int nblk = gx * gy;
     long long* part = reinterpret_cast<long long*>(p.partial);
     if (tid == 0) {
         long long b = sh[0];
-        for (int w = 1; w < kThreads / 32; ++w) b = max(b, sh[w]);
-        part[blockIdx.y * gridDim.x + blockIdx.x] = b;
+        for (int w = 1; w < nw; ++w) b = max(b, sh[w]);
+        part[by * gx + bx] = b;
         __threadfence();
         const unsigned prev = atomicAdd(&p.scal->counter, 1u);
         last = (prev == (unsigned)(nblk - 1));
@@ -129,13 +131,13 @@ __global__ void __launch_bounds__(kThreads) k_phase0(ParamsT<T> P)
     if (!last) return;
     __threadfence();
     long long m = 0;
-    for (int k = tid; k < nblk; k += kThreads) m = max(m, __ldcg(&part[k]));
+    for (int k = tid; k < nblk; k += nw * 32) m = max(m, __ldcg(&part[k]));
     for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_down_sync(0xffffffffu, m, o));
     if ((tid & 31) == 0) sh[tid >> 5] = m;
     __syncthreads();
     if (tid == 0) {
         long long b = sh[0];
-        for (int w = 1; w < kThreads / 32; ++w) b = max(b, sh[w]);
+        for (int w = 1; w < nw; ++w) b = max(b, sh[w]);
         DevScalars* s = p.scal;
         double dt = P.growth * s->dt_prev;
         const double cdt = P.cfld * (P.dxd / __longlong_as_double(b));
@@ -143,6 +145,7 @@ __global__ void __launch_bounds__(kThreads) k_phase0(ParamsT<T> P)
         dt = P.dt_max < dt ? P.dt_max : dt;
         if (dt < P.dt_min) s->status |= 4;
         s->dt = dt;
+        s->active = 1;
         s->counter = 0u;
     }
 }
@@ -153,12 +156,12 @@ __global__ void __launch_bounds__(kThreads) k_phase0(ParamsT<T> P)
 // 2 (i,j) corner a, 3 (i-1,j) corner b.
 // ---------------------------------------------------------------------------------
 template <typename T, bool STR>
-__global__ void __launch_bounds__(kThreads) k_phase1(ParamsT<T> P)
+__device__ __forceinline__ void body_phase1(const ParamsT<T>& P, int bx, int by, int gx, int gy)
 {
     typedef VT<T> V;
     const T zero = T(0), one = T(1), half = T(0.5);
-    const int i = blockIdx.x * kBlockX + threadIdx.x;
-    const int j = blockIdx.y * kBlockY + threadIdx.y;
+    const int i = bx * blockDim.x + threadIdx.x;
+    const int j = by * blockDim.y + threadIdx.y;
     const int nr = P.nr, nz = P.nz;
     if (i > nr || j > nz) return;
     const PtrsT<T>& p = P.p;
@@ -242,12 +245,12 @@ __global__ void __launch_bounds__(kThreads) k_phase1(ParamsT<T> P)
 // Phase 2: Lagrangian cell update from v^L.
 // ---------------------------------------------------------------------------------
 template <typename T, int NM, bool STR>
-__global__ void __launch_bounds__(kThreads) k_phase2(ParamsT<T> P)
+__device__ __forceinline__ void body_phase2(const ParamsT<T>& P, int bx, int by, int gx, int gy)
 {
     typedef VT<T> V;
     const T zero = T(0), one = T(1), half = T(0.5), two = T(2);
-    const int i = blockIdx.x * kBlockX + threadIdx.x;
-    const int j = blockIdx.y * kBlockY + threadIdx.y;
+    const int i = bx * blockDim.x + threadIdx.x;
+    const int j = by * blockDim.y + threadIdx.y;
     const int nr = P.nr;
     if (i >= nr || j >= P.nz) return;
     const PtrsT<T>& p = P.p;
@@ -438,12 +441,12 @@ __device__ __forceinline__ void move(const ParamsT<T>& P, int donor, T adV, T sg
 }
 
 template <typename T, int NM, bool STR>
-__global__ void __launch_bounds__(kThreads) k_phase3a(ParamsT<T> P)
+__device__ __forceinline__ void body_phase3a(const ParamsT<T>& P, int bx, int by, int gx, int gy)
 {
     typedef VT<T> V;
     const T zero = T(0), one = T(1);
-    const int i = blockIdx.x * kBlockX + threadIdx.x;
-    const int j = blockIdx.y * kBlockY + threadIdx.y;
+    const int i = bx * blockDim.x + threadIdx.x;
+    const int j = by * blockDim.y + threadIdx.y;
     const int nr = P.nr, nz = P.nz;
     const PtrsT<T>& p = P.p;
     double t_out = 0.0, t_disc = 0.0, t_pml = 0.0;
@@ -589,7 +592,7 @@ __global__ void __launch_bounds__(kThreads) k_phase3a(ParamsT<T> P)
     // tallies: block sums and one atomic per block, only in blocks where some thread has one
     // (most blocks touch neither the top boundary, the clean-up nor a strip)
     if (__syncthreads_or(t_out != 0.0 || t_disc != 0.0 || t_pml != 0.0)) {
-        __shared__ double sh[kThreads / 32];
+        __shared__ double sh[kMaxThreads / 32];
         const double b_out = block_sum(t_out, sh);
         const double b_disc = block_sum(t_disc, sh);
         const double b_pml = block_sum(t_pml, sh);
@@ -629,12 +632,12 @@ __device__ __forceinline__ T dual_Z(const ParamsT<T>& P, int i, int j)
 }
 
 template <typename T>
-__global__ void __launch_bounds__(kThreads) k_phase3b(ParamsT<T> P)
+__device__ __forceinline__ void body_phase3b(const ParamsT<T>& P, int bx, int by, int gx, int gy)
 {
     typedef VT<T> V;
     const T zero = T(0), one = T(1), half = T(0.5);
-    const int i = blockIdx.x * kBlockX + threadIdx.x;
-    const int j = blockIdx.y * kBlockY + threadIdx.y;
+    const int i = bx * blockDim.x + threadIdx.x;
+    const int j = by * blockDim.y + threadIdx.y;
     const int nr = P.nr, nz = P.nz, nv = nr + 1;
     const PtrsT<T>& p = P.p;
     double t_zmom = 0.0;
@@ -725,7 +728,7 @@ __global__ void __launch_bounds__(kThreads) k_phase3b(ParamsT<T> P)
         p.v[v] = V::mk(vr, vz);
     }
     if (__syncthreads_or(t_zmom != 0.0)) {
-        __shared__ double sh[kThreads / 32];
+        __shared__ double sh[kMaxThreads / 32];
         const double b = block_sum(t_zmom, sh);
         if (threadIdx.x == 0 && threadIdx.y == 0 && b != 0.0) atomicAdd(&p.scal->zmom_out, b);
     }
@@ -735,11 +738,11 @@ __global__ void __launch_bounds__(kThreads) k_phase3b(ParamsT<T> P)
 // Phase 3c: kinetic-energy deficit as heat; advance time.
 // ---------------------------------------------------------------------------------
 template <typename T, int NM>
-__global__ void __launch_bounds__(kThreads) k_phase3c(ParamsT<T> P)
+__device__ __forceinline__ void body_phase3c(const ParamsT<T>& P, int bx, int by, int gx, int gy)
 {
     typedef VT<T> V;
-    const int i = blockIdx.x * kBlockX + threadIdx.x;
-    const int j = blockIdx.y * kBlockY + threadIdx.y;
+    const int i = bx * blockDim.x + threadIdx.x;
+    const int j = by * blockDim.y + threadIdx.y;
     const int nr = P.nr, nv = nr + 1;
     const PtrsT<T>& p = P.p;
     if (i < nr && j < P.nz) {
@@ -756,7 +759,7 @@ __global__ void __launch_bounds__(kThreads) k_phase3c(ParamsT<T> P)
             p.I[c] += double(add);
         }
     }
-    if (blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0 && threadIdx.y == 0) {
+    if (bx == 0 && by == 0 && threadIdx.x == 0 && threadIdx.y == 0) {
         DevScalars* s = p.scal;
         s->t += s->dt;
         s->dt_prev = s->dt;
@@ -764,15 +767,71 @@ __global__ void __launch_bounds__(kThreads) k_phase3c(ParamsT<T> P)
     }
 }
 
+
+// ---------------------------------------------------------------------------------
+// Kernels: single run (one grid of blocks over the run) and batched (one block per entry of
+// a work list of (run, tile); a run's parameters are read from device memory; runs that
+// reached their end time are skipped; each run keeps its own dt reduction).
+// ---------------------------------------------------------------------------------
+
+template <typename T, int NM, bool STR>
+__global__ void __launch_bounds__(kMaxThreads) k_phase0(ParamsT<T> P) { body_phase0<T, NM, STR>(P, blockIdx.x, blockIdx.y, gridDim.x, gridDim.y); }
+template <typename T, bool STR>
+__global__ void __launch_bounds__(kMaxThreads) k_phase1(ParamsT<T> P) { body_phase1<T, STR>(P, blockIdx.x, blockIdx.y, gridDim.x, gridDim.y); }
+template <typename T, int NM, bool STR>
+__global__ void __launch_bounds__(kMaxThreads) k_phase2(ParamsT<T> P) { body_phase2<T, NM, STR>(P, blockIdx.x, blockIdx.y, gridDim.x, gridDim.y); }
+template <typename T, int NM, bool STR>
+__global__ void __launch_bounds__(kMaxThreads) k_phase3a(ParamsT<T> P) { body_phase3a<T, NM, STR>(P, blockIdx.x, blockIdx.y, gridDim.x, gridDim.y); }
+template <typename T>
+__global__ void __launch_bounds__(kMaxThreads) k_phase3b(ParamsT<T> P) { body_phase3b<T>(P, blockIdx.x, blockIdx.y, gridDim.x, gridDim.y); }
+template <typename T, int NM>
+__global__ void __launch_bounds__(kMaxThreads) k_phase3c(ParamsT<T> P) { body_phase3c<T, NM>(P, blockIdx.x, blockIdx.y, gridDim.x, gridDim.y); }
+
+// phase 0 decides for the whole step: a run at or past its end time does nothing
+template <typename T, int NM, bool STR>
+__global__ void __launch_bounds__(kMaxThreads) kb_phase0(const ParamsT<T>* __restrict__ runs, const BatchTile* __restrict__ work)
+{
+    const BatchTile w = work[blockIdx.x];
+    const ParamsT<T>& P = runs[w.run];
+    DevScalars* s = P.p.scal;
+    if (!(s->t < s->t_end)) {
+        if (w.bx == 0 && w.by == 0 && threadIdx.x == 0 && threadIdx.y == 0) s->active = 0;
+        return;
+    }
+    body_phase0<T, NM, STR>(P, w.bx, w.by, w.g & 0xffff, w.g >> 16);
+}
+#define SALEC_BATCHED(NAME, CALL)                                                          \
+    {                                                                                      \
+        const BatchTile w = work[blockIdx.x];                                              \
+        const ParamsT<T>& P = runs[w.run];                                                 \
+        if (P.p.scal->active == 0) return;                                                 \
+        CALL(P, w.bx, w.by, w.g & 0xffff, w.g >> 16);                                      \
+    }
+template <typename T, bool STR>
+__global__ void __launch_bounds__(kMaxThreads) kb_phase1(const ParamsT<T>* __restrict__ runs, const BatchTile* __restrict__ work)
+SALEC_BATCHED(phase1, (body_phase1<T, STR>))
+template <typename T, int NM, bool STR>
+__global__ void __launch_bounds__(kMaxThreads) kb_phase2(const ParamsT<T>* __restrict__ runs, const BatchTile* __restrict__ work)
+SALEC_BATCHED(phase2, (body_phase2<T, NM, STR>))
+template <typename T, int NM, bool STR>
+__global__ void __launch_bounds__(kMaxThreads) kb_phase3a(const ParamsT<T>* __restrict__ runs, const BatchTile* __restrict__ work)
+SALEC_BATCHED(phase3a, (body_phase3a<T, NM, STR>))
+template <typename T>
+__global__ void __launch_bounds__(kMaxThreads) kb_phase3b(const ParamsT<T>* __restrict__ runs, const BatchTile* __restrict__ work)
+SALEC_BATCHED(phase3b, (body_phase3b<T>))
+template <typename T, int NM>
+__global__ void __launch_bounds__(kMaxThreads) kb_phase3c(const ParamsT<T>* __restrict__ runs, const BatchTile* __restrict__ work)
+SALEC_BATCHED(phase3c, (body_phase3c<T, NM>))
+
 // ---------------------------------------------------------------------------------
 // Read-out kernels
 // ---------------------------------------------------------------------------------
 template <typename T, int NM>
-__global__ void __launch_bounds__(kThreads) k_pressure(ParamsT<T> P, double* out)
+__global__ void __launch_bounds__(kMaxThreads) k_pressure(ParamsT<T> P, double* out)
 {
     typedef VT<T> V;
-    const int i = blockIdx.x * kBlockX + threadIdx.x;
-    const int j = blockIdx.y * kBlockY + threadIdx.y;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int j = blockIdx.y * blockDim.y + threadIdx.y;
     if (i >= P.nr || j >= P.nz) return;
     const int c = j * P.nr + i;
     const PtrsT<T>& p = P.p;
@@ -823,11 +882,11 @@ __global__ void k_column_heights(ParamsT<T> P, double* h)
 
 // per-block FP64 sums of mass, z-momentum, kinetic and internal energy
 template <typename T, int NM>
-__global__ void __launch_bounds__(kThreads) k_conservation(ParamsT<T> P, double* partial4)
+__global__ void __launch_bounds__(kMaxThreads) k_conservation(ParamsT<T> P, double* partial4)
 {
     typedef VT<T> V;
-    const int i = blockIdx.x * kBlockX + threadIdx.x;
-    const int j = blockIdx.y * kBlockY + threadIdx.y;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int j = blockIdx.y * blockDim.y + threadIdx.y;
     const int nr = P.nr, nz = P.nz;
     const PtrsT<T>& p = P.p;
     auto cmass = [&](int ci, int cj) {
@@ -857,7 +916,7 @@ __global__ void __launch_bounds__(kThreads) k_conservation(ParamsT<T> P, double*
         pz = m * double(vv.y);
         ke = 0.5 * m * (double(vv.x) * double(vv.x) + double(vv.y) * double(vv.y));
     }
-    __shared__ double sh[kThreads / 32];
+    __shared__ double sh[kMaxThreads / 32];
     const double a = block_sum(mass, sh), b = block_sum(pz, sh), c = block_sum(ke, sh), d = block_sum(ie, sh);
     if (threadIdx.x == 0 && threadIdx.y == 0) {
         const int blk = blockIdx.y * gridDim.x + blockIdx.x;
@@ -871,12 +930,20 @@ __global__ void __launch_bounds__(kThreads) k_conservation(ParamsT<T> P, double*
 // ---------------------------------------------------------------------------------
 // Launchers
 // ---------------------------------------------------------------------------------
-static dim3 cell_grid(int nr, int nz) { return dim3((nr + kBlockX - 1) / kBlockX, (nz + kBlockY - 1) / kBlockY); }
-static dim3 vert_grid(int nr, int nz) { return dim3((nr + 1 + kBlockX - 1) / kBlockX, (nz + 1 + kBlockY - 1) / kBlockY); }
+static dim3 grid_of(int ni, int nj, dim3 blk) { return dim3((ni + blk.x - 1) / blk.x, (nj + blk.y - 1) / blk.y); }
+static dim3 cell_grid(int nr, int nz) { return grid_of(nr, nz, dim3(kBlockX, kBlockY)); }
+static dim3 vert_grid(int nr, int nz) { return grid_of(nr + 1, nz + 1, dim3(kBlockX, kBlockY)); }
 
 int cell_blocks(int nr, int nz) { dim3 g = cell_grid(nr, nz); return (int)(g.x * g.y); }
 int vertex_blocks(int nr, int nz) { dim3 g = vert_grid(nr, nz); return (int)(g.x * g.y); }
 int launches_per_step() { return 6; }
+// kernels 1 (forces) and 4 (momentum remap) run over vertices, the others over cells
+bool kernel_on_vertices(int k) { return k == 1 || k == 4; }
+int tiles_of(int nr, int nz, int k, dim3 blk)
+{
+    const dim3 g = kernel_on_vertices(k) ? grid_of(nr + 1, nz + 1, blk) : grid_of(nr, nz, blk);
+    return (int)(g.x * g.y);
+}
 
 const char* kernel_name(int k)
 {
@@ -884,37 +951,70 @@ const char* kernel_name(int k)
     return (k >= 0 && k < 6) ? names[k] : "";
 }
 
-// One cycle; with ev != nullptr an event is recorded before the first kernel and after
-// each kernel (7 events) so per-kernel durations can be read later on the same stream.
+// One cycle with per-kernel block shapes; with ev != nullptr an event is recorded before the
+// first kernel and after each kernel (7 events) for per-kernel durations.
 template <typename T, int NM, bool STR>
-static cudaError_t step_impl(const ParamsT<T>& P, cudaStream_t s, cudaEvent_t* ev)
+static cudaError_t step_impl(const ParamsT<T>& P, const dim3* blk, cudaStream_t s, cudaEvent_t* ev)
 {
-    const dim3 blk(kBlockX, kBlockY);
-    const dim3 gc = cell_grid(P.nr, P.nz), gv = vert_grid(P.nr, P.nz);
+    const int nr = P.nr, nz = P.nz;
     if (ev) cudaEventRecord(ev[0], s);
-    k_phase0<T, NM, STR><<<gc, blk, 0, s>>>(P);
+    k_phase0<T, NM, STR><<<grid_of(nr, nz, blk[0]), blk[0], 0, s>>>(P);
     if (ev) cudaEventRecord(ev[1], s);
-    k_phase1<T, STR><<<gv, blk, 0, s>>>(P);
+    k_phase1<T, STR><<<grid_of(nr + 1, nz + 1, blk[1]), blk[1], 0, s>>>(P);
     if (ev) cudaEventRecord(ev[2], s);
-    k_phase2<T, NM, STR><<<gc, blk, 0, s>>>(P);
+    k_phase2<T, NM, STR><<<grid_of(nr, nz, blk[2]), blk[2], 0, s>>>(P);
     if (ev) cudaEventRecord(ev[3], s);
-    k_phase3a<T, NM, STR><<<gc, blk, 0, s>>>(P);
+    k_phase3a<T, NM, STR><<<grid_of(nr, nz, blk[3]), blk[3], 0, s>>>(P);
     if (ev) cudaEventRecord(ev[4], s);
-    k_phase3b<T><<<gv, blk, 0, s>>>(P);
+    k_phase3b<T><<<grid_of(nr + 1, nz + 1, blk[4]), blk[4], 0, s>>>(P);
     if (ev) cudaEventRecord(ev[5], s);
-    k_phase3c<T, NM><<<gc, blk, 0, s>>>(P);
+    k_phase3c<T, NM><<<grid_of(nr, nz, blk[5]), blk[5], 0, s>>>(P);
     if (ev) cudaEventRecord(ev[6], s);
     return cudaGetLastError();
 }
 
 template <typename T>
-cudaError_t launch_step(const ParamsT<T>& P, cudaStream_t s, cudaEvent_t* ev)
+cudaError_t launch_step(const ParamsT<T>& P, const dim3* blk, cudaStream_t s, cudaEvent_t* ev)
 {
     const bool st = P.any_strength != 0;
     switch (P.nmat) {
-    case 1: return st ? step_impl<T, 1, true>(P, s, ev) : step_impl<T, 1, false>(P, s, ev);
-    case 2: return st ? step_impl<T, 2, true>(P, s, ev) : step_impl<T, 2, false>(P, s, ev);
-    case 3: return st ? step_impl<T, 3, true>(P, s, ev) : step_impl<T, 3, false>(P, s, ev);
+    case 1: return st ? step_impl<T, 1, true>(P, blk, s, ev) : step_impl<T, 1, false>(P, blk, s, ev);
+    case 2: return st ? step_impl<T, 2, true>(P, blk, s, ev) : step_impl<T, 2, false>(P, blk, s, ev);
+    case 3: return st ? step_impl<T, 3, true>(P, blk, s, ev) : step_impl<T, 3, false>(P, blk, s, ev);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+// One cycle of every run of a batch: work[k] lists the (run, tile) entries of kernel k
+// (ntiles[k] of them) for block shape blk[k].
+template <typename T, int NM, bool STR>
+static cudaError_t batch_impl(const ParamsT<T>* runs, const BatchTile* const* work, const int* ntiles,
+                              const dim3* blk, cudaStream_t s, cudaEvent_t* ev)
+{
+    if (ev) cudaEventRecord(ev[0], s);
+    kb_phase0<T, NM, STR><<<ntiles[0], blk[0], 0, s>>>(runs, work[0]);
+    if (ev) cudaEventRecord(ev[1], s);
+    kb_phase1<T, STR><<<ntiles[1], blk[1], 0, s>>>(runs, work[1]);
+    if (ev) cudaEventRecord(ev[2], s);
+    kb_phase2<T, NM, STR><<<ntiles[2], blk[2], 0, s>>>(runs, work[2]);
+    if (ev) cudaEventRecord(ev[3], s);
+    kb_phase3a<T, NM, STR><<<ntiles[3], blk[3], 0, s>>>(runs, work[3]);
+    if (ev) cudaEventRecord(ev[4], s);
+    kb_phase3b<T><<<ntiles[4], blk[4], 0, s>>>(runs, work[4]);
+    if (ev) cudaEventRecord(ev[5], s);
+    kb_phase3c<T, NM><<<ntiles[5], blk[5], 0, s>>>(runs, work[5]);
+    if (ev) cudaEventRecord(ev[6], s);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_batch_step(const ParamsT<T>* runs_dev, int nmat, bool strength, const BatchTile* const* work,
+                              const int* ntiles, const dim3* blk, cudaStream_t s, cudaEvent_t* ev)
+{
+    switch (nmat) {
+    case 1: return strength ? batch_impl<T, 1, true>(runs_dev, work, ntiles, blk, s, ev) : batch_impl<T, 1, false>(runs_dev, work, ntiles, blk, s, ev);
+    case 2: return strength ? batch_impl<T, 2, true>(runs_dev, work, ntiles, blk, s, ev) : batch_impl<T, 2, false>(runs_dev, work, ntiles, blk, s, ev);
+    case 3: return strength ? batch_impl<T, 3, true>(runs_dev, work, ntiles, blk, s, ev) : batch_impl<T, 3, false>(runs_dev, work, ntiles, blk, s, ev);
     default: return cudaErrorInvalidValue;
     }
 }
@@ -959,8 +1059,35 @@ cudaError_t launch_conservation(const ParamsT<T>& P, double* partial4, int* nblo
     return cudaGetLastError();
 }
 
-template cudaError_t launch_step<double>(const ParamsT<double>&, cudaStream_t, cudaEvent_t*);
-template cudaError_t launch_step<float>(const ParamsT<float>&, cudaStream_t, cudaEvent_t*);
+// Per-run scalars of a batch gathered into one array (t, dt, step count, status, t_end).
+template <typename T>
+__global__ void k_batch_poll(const ParamsT<T>* __restrict__ runs, int n, double* out)
+{
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= n) return;
+    const DevScalars* s = runs[r].p.scal;
+    out[5 * r + 0] = s->t;
+    out[5 * r + 1] = s->dt;
+    out[5 * r + 2] = (double)s->nstep;
+    out[5 * r + 3] = (double)s->status;
+    out[5 * r + 4] = s->t_end;
+}
+
+template <typename T>
+cudaError_t launch_batch_poll(const ParamsT<T>* runs_dev, int n, double* out, cudaStream_t s)
+{
+    k_batch_poll<T><<<(n + 127) / 128, 128, 0, s>>>(runs_dev, n, out);
+    return cudaGetLastError();
+}
+template cudaError_t launch_batch_poll<double>(const ParamsT<double>*, int, double*, cudaStream_t);
+template cudaError_t launch_batch_poll<float>(const ParamsT<float>*, int, double*, cudaStream_t);
+
+template cudaError_t launch_step<double>(const ParamsT<double>&, const dim3*, cudaStream_t, cudaEvent_t*);
+template cudaError_t launch_step<float>(const ParamsT<float>&, const dim3*, cudaStream_t, cudaEvent_t*);
+template cudaError_t launch_batch_step<double>(const ParamsT<double>*, int, bool, const BatchTile* const*, const int*,
+                                               const dim3*, cudaStream_t, cudaEvent_t*);
+template cudaError_t launch_batch_step<float>(const ParamsT<float>*, int, bool, const BatchTile* const*, const int*,
+                                              const dim3*, cudaStream_t, cudaEvent_t*);
 template cudaError_t launch_pressure<double>(const ParamsT<double>&, double*, cudaStream_t);
 template cudaError_t launch_pressure<float>(const ParamsT<float>&, double*, cudaStream_t);
 template cudaError_t launch_column_heights<double>(const ParamsT<double>&, double*, cudaStream_t);

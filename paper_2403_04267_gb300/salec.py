@@ -59,7 +59,13 @@ EXPORTS = ["salec_state_bytes", "salec_create", "salec_set_material", "salec_add
            "salec_set_time", "salec_get_field", "salec_set_field", "salec_crater_profile",
            "salec_conservation", "salec_checkpoint_bytes", "salec_get_state", "salec_set_state",
            "salec_launches_per_step", "salec_set_kernel_timing", "salec_kernel_times",
-           "salec_kernel_name", "salec_courant_dt_noalloc", "salec_last_error", "salec_destroy"]
+           "salec_kernel_name", "salec_courant_dt_noalloc", "salec_last_error", "salec_destroy",
+           "salec_set_end_time", "salec_set_block_shapes", "salec_get_block_shapes", "salec_autotune",
+           "salec_batch_bytes", "salec_batch_create", "salec_batch_step", "salec_batch_run", "salec_batch_poll",
+           "salec_batch_autotune", "salec_batch_last_error", "salec_batch_destroy",
+           "salec_mlp_n_params", "salec_mlp_bytes", "salec_mlp_create", "salec_mlp_set_params",
+           "salec_mlp_get_params", "salec_mlp_forward", "salec_mlp_gradient", "salec_mlp_train_step",
+           "salec_mlp_check", "salec_gemm_bf16", "salec_mlp_last_error", "salec_mlp_destroy"]
 
 
 def load(build: bool = True):
@@ -97,7 +103,31 @@ def load(build: bool = True):
         "salec_courant_dt_noalloc": (I, [C.POINTER(salec_grid), C.POINTER(salec_material), C.POINTER(C.c_void_p),
                                          P, P, P, D, PD, P]),
         "salec_last_error": (C.c_char_p, [P]),
+        "salec_set_end_time": (I, [P, D]),
+        "salec_set_block_shapes": (I, [P, C.POINTER(C.c_int)]),
+        "salec_get_block_shapes": (I, [P, C.POINTER(C.c_int)]),
+        "salec_autotune": (I, [P, I, C.POINTER(C.c_int)]),
+        "salec_batch_bytes": (I, [C.POINTER(P), I, C.POINTER(C.c_size_t)]),
+        "salec_batch_create": (I, [C.POINTER(P), I, P, Z, P, C.POINTER(P)]),
+        "salec_batch_step": (I, [P, I]),
+        "salec_batch_run": (I, [P, I, C.c_long, C.POINTER(C.c_long), C.POINTER(C.c_int)]),
+        "salec_batch_poll": (I, [P, PD]),
+        "salec_batch_autotune": (I, [P, I, C.POINTER(C.c_int)]),
+        "salec_batch_last_error": (C.c_char_p, [P]),
+        "salec_batch_destroy": (None, [P]),
         "salec_destroy": (None, [P]),
+        "salec_mlp_n_params": (I, []),
+        "salec_mlp_bytes": (I, [I, C.POINTER(C.c_size_t)]),
+        "salec_mlp_create": (I, [I, P, Z, P, C.POINTER(P)]),
+        "salec_mlp_set_params": (I, [P, P]),
+        "salec_mlp_get_params": (I, [P, P]),
+        "salec_mlp_forward": (I, [P, P, I, P]),
+        "salec_mlp_gradient": (I, [P, P, P, I, P, PD]),
+        "salec_mlp_train_step": (I, [P, P, P, I, C.c_float, C.c_float, C.c_float, C.c_float, P]),
+        "salec_mlp_check": (I, [P]),
+        "salec_gemm_bf16": (I, [I, I, I, P, C.c_long, C.c_long, P, C.c_long, C.c_long, P, C.c_long, P]),
+        "salec_mlp_last_error": (C.c_char_p, [P]),
+        "salec_mlp_destroy": (None, [P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)
@@ -256,6 +286,23 @@ class Sim:
     def launches_per_step(self) -> int:
         return load().salec_launches_per_step(self._h)
 
+    def set_end_time(self, t_end: float) -> None:
+        self._check(load().salec_set_end_time(self._h, float(t_end)))
+
+    def block_shapes(self) -> list:
+        a = (C.c_int * 12)()
+        self._check(load().salec_get_block_shapes(self._h, a))
+        return [(a[2 * k], a[2 * k + 1]) for k in range(6)]
+
+    def set_block_shapes(self, shapes) -> None:
+        a = (C.c_int * 12)(*[int(v) for xy in shapes for v in xy])
+        self._check(load().salec_set_block_shapes(self._h, a))
+
+    def autotune(self, trial_steps: int = 5) -> list:
+        a = (C.c_int * 12)()
+        self._check(load().salec_autotune(self._h, int(trial_steps), a))
+        return [(a[2 * k], a[2 * k + 1]) for k in range(6)]
+
     def set_kernel_timing(self, on: bool) -> None:
         self._check(load().salec_set_kernel_timing(self._h, 1 if on else 0))
 
@@ -284,3 +331,62 @@ def courant_dt_noalloc(spec: dict, fr_ptrs, I_ptr: int, v_ptr: int, dt_prev: flo
     if st != SALEC_OK:
         raise SalecError(st, L.salec_last_error(None).decode())
     return out.value
+
+
+class Batch:
+    """Independent runs advanced together (one set of launches per step, per-run dt and end
+    time, CUDA-graph-captured chunks).  ``sims`` are finalized Sim objects of one precision
+    and material class on the current device."""
+
+    def __init__(self, sims, stream=None):
+        import torch
+        L = load()
+        self.sims = list(sims)
+        n = len(self.sims)
+        self._arr = (C.c_void_p * n)(*[s.handle for s in self.sims])
+        nb = C.c_size_t()
+        st = L.salec_batch_bytes(self._arr, n, C.byref(nb))
+        if st != SALEC_OK:
+            raise SalecError(st, "runs cannot be batched together")
+        dev = self.sims[0].device
+        self.buf = torch.empty(nb.value, dtype=torch.uint8, device=dev)
+        # graph capture needs a created stream; the runs' own work must be finished first
+        self.stream = stream if stream is not None else torch.cuda.Stream(device=dev)
+        torch.cuda.synchronize(dev)
+        h = C.c_void_p()
+        st = L.salec_batch_create(self._arr, n, C.c_void_p(self.buf.data_ptr()), nb.value,
+                                  C.c_void_p(self.stream.cuda_stream), C.byref(h))
+        if st != SALEC_OK:
+            raise SalecError(st, "batch create failed")
+        self._h = h
+
+    def _check(self, st):
+        if st != SALEC_OK:
+            raise SalecError(st, load().salec_batch_last_error(self._h).decode())
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h:
+            load().salec_batch_destroy(h)
+            self._h = None
+
+    def step(self, n: int) -> None:
+        """n batched steps; returns after they finished (the runs' fields are then safe to
+        read on any stream)."""
+        self._check(load().salec_batch_step(self._h, int(n)))
+        self.stream.synchronize()
+
+    def run(self, chunk: int = 50, max_steps: int = 10 ** 9):
+        steps, done = C.c_long(), C.c_int()
+        self._check(load().salec_batch_run(self._h, int(chunk), int(max_steps), C.byref(steps), C.byref(done)))
+        return steps.value, done.value
+
+    def poll(self) -> np.ndarray:
+        out = np.zeros(5 * len(self.sims))
+        self._check(load().salec_batch_poll(self._h, out.ctypes.data_as(C.POINTER(C.c_double))))
+        return out.reshape(-1, 5)
+
+    def autotune(self, trial_steps: int = 3) -> list:
+        a = (C.c_int * 12)()
+        self._check(load().salec_batch_autotune(self._h, int(trial_steps), a))
+        return [(a[2 * k], a[2 * k + 1]) for k in range(6)]
