@@ -68,6 +68,7 @@ typedef struct {
     double *phi2r_b, *phi2z_b, *psi1r_b, *psi1z_b;                     /* vertices, bottom strip */
     double *phi2r_r, *phi2z_r, *psi1r_r, *psi1z_r;                     /* vertices, right strip */
     double *dB_c, *dB_v, *dR_c, *dR_v;   /* damping profiles: rows (cells, vertices), columns */
+    double *wR_c, *wR_v;                 /* 1 on rows whose reference state holds material (cells, vertices) */
     double *p0, *rho_ref, *I_ref;        /* reference state per row */
     /* set-up accumulators */
     double *setup_V[ORC_MAXMAT], *setup_M[ORC_MAXMAT], *setup_E, *setup_Pz;
@@ -222,6 +223,7 @@ orc_sim* orc_create(const orc_grid* g, const orc_material* mats)
     s->phi2r_b = zalloc(nv); s->phi2z_b = zalloc(nv); s->psi1r_b = zalloc(nv); s->psi1z_b = zalloc(nv);
     s->phi2r_r = zalloc(nv); s->phi2z_r = zalloc(nv); s->psi1r_r = zalloc(nv); s->psi1z_r = zalloc(nv);
     s->dB_c = zalloc(nz); s->dB_v = zalloc(nz + 1); s->dR_c = zalloc(nr); s->dR_v = zalloc(nr + 1);
+    s->wR_c = zalloc(nz); s->wR_v = zalloc(nz + 1);
     s->p0 = zalloc(nz); s->rho_ref = zalloc(nz); s->I_ref = zalloc(nz);
     s->setup_E = zalloc(nc); s->setup_Pz = zalloc(nc); s->setup_I = zalloc(nc); s->setup_Imix = zalloc(nc);
     s->P = zalloc(nc); s->pbar = zalloc(nc); s->mv = zalloc(nv); s->vLr = zalloc(nv); s->vLz = zalloc(nv);
@@ -240,7 +242,7 @@ void orc_destroy(orc_sim* s)
     double** all[] = {&s->A_R, &s->A_Z, &s->V, &s->I, &s->srr, &s->szz, &s->srz, &s->D, &s->pmax,
                       &s->vr, &s->vz, &s->phi1_b, &s->phi3_b, &s->psi2_b, &s->phi1_r, &s->phi3_r,
                       &s->psi2_r, &s->phi2r_b, &s->phi2z_b, &s->psi1r_b, &s->psi1z_b, &s->phi2r_r,
-                      &s->phi2z_r, &s->psi1r_r, &s->psi1z_r, &s->dB_c, &s->dB_v, &s->dR_c, &s->dR_v,
+                      &s->phi2z_r, &s->psi1r_r, &s->psi1z_r, &s->dB_c, &s->dB_v, &s->dR_c, &s->dR_v, &s->wR_c, &s->wR_v,
                       &s->p0, &s->rho_ref, &s->I_ref, &s->setup_E, &s->setup_Pz, &s->setup_I, &s->setup_Imix, &s->P, &s->pbar,
                       &s->mv, &s->vLr, &s->vLz, &s->dK, &s->kheat, &s->VL, &s->IL, &s->srrL, &s->szzL, &s->srzL, &s->DL,
                       &s->dVR, &s->dVZ, &s->dMR, &s->dMZ};
@@ -464,6 +466,12 @@ int orc_finalize(orc_sim* s)
         s->dR_c[i] = i >= nr - pr ? pml_profile(c, pr, s->g.dx, (double)i + 0.5 - (double)(nr - pr), s->g.pml_R) : 0.0;
     for (int i = 0; i <= nr; ++i)
         s->dR_v[i] = i > nr - pr ? pml_profile(c, pr, s->g.dx, (double)i - (double)(nr - pr), s->g.pml_R) : 0.0;
+    /* the right strip absorbs waves of the medium: it acts on the rows whose reference
+       (far-field) state holds material, not on the void above the target, where the
+       reference is empty and damping toward it would remove ejecta (reading of Sect. 3) */
+    for (int j = 0; j < nz; ++j) s->wR_c[j] = s->rho_ref[j] > 0.0 ? 1.0 : 0.0;
+    for (int j = 0; j <= nz; ++j)
+        s->wR_v[j] = ((j > 0 && s->rho_ref[j - 1] > 0.0) || (j < nz && s->rho_ref[j] > 0.0)) ? 1.0 : 0.0;
     s->finalized = 1;
     return 0;
 }
@@ -603,7 +611,8 @@ static void phase1_vertex(orc_sim* s)
             double Pc[4] = {0, 0, 0, 0}, Pp[4] = {0, 0, 0, 0};
             double devr = 0.0, devz = 0.0, mass = 0.0;
             double Tr_b = 0.0, Tz_b = 0.0, Tr_r = 0.0, Tz_r = 0.0;
-            int pml = s->dB_v[j] > 0.0 || s->dR_v[i] > 0.0;
+            const double dRv = s->dR_v[i] * s->wR_v[j];
+            int pml = s->dB_v[j] > 0.0 || dRv > 0.0;
             for (int k = 0; k < 4; ++k) {
                 int ci = ci_list[k], cj = cj_list[k];
                 if (ci < 0 || ci >= nr || cj < 0 || cj >= nz) continue;
@@ -634,8 +643,8 @@ static void phase1_vertex(orc_sim* s)
             }
             s->psi1r_b[v] -= dt * s->dB_v[j] * Tr_b;
             s->psi1z_b[v] -= dt * s->dB_v[j] * Tz_b;
-            s->psi1r_r[v] -= dt * s->dR_v[i] * Tr_r;
-            s->psi1z_r[v] -= dt * s->dR_v[i] * Tz_r;
+            s->psi1r_r[v] -= dt * dRv * Tr_r;
+            s->psi1z_r[v] -= dt * dRv * Tz_r;
             s->mv[v] = mass;
             double vr = 0.0, vz = 0.0;
             if (mass > 0.0) {
@@ -752,7 +761,7 @@ static void phase2_cell(orc_sim* s)
             double Pi_rad = -P * radial_flux + V * (Srr * err + Stt * ett + Srz * dvz_dr);
             double Pi_ver = -P * vertical_flux + V * (Szz * ezz + Srz * dvr_dz);
             s->psi2_b[c] -= dt * s->dB_c[j] * Pi_rad;
-            s->psi2_r[c] -= dt * s->dR_c[i] * Pi_ver;
+            s->psi2_r[c] -= dt * s->dR_c[i] * s->wR_c[j] * Pi_ver;
             double M = 0.0;
             for (int m = 0; m < nm; ++m) M += s->f[m][c] * s->rho[m][c] * V;
             double dE = -P * dV + dt * V * (Srr * err + Szz * ezz + Stt * ett + 2.0 * Srz * erz)
@@ -966,9 +975,10 @@ static void phase3_remap(orc_sim* s)
            strip, vertical in the right strip */
         s->phi1_b[c] += s->dB_c[j] * FR_M[c];
         s->phi3_b[c] += s->dB_c[j] * FR_E[c];
-        s->phi1_r[c] += s->dR_c[i] * FZ_M[c];
-        s->phi3_r[c] += s->dR_c[i] * FZ_E[c];
-        double dsum = s->dB_c[j] + s->dR_c[i];
+        const double dRc = s->dR_c[i] * s->wR_c[j];
+        s->phi1_r[c] += dRc * FZ_M[c];
+        s->phi3_r[c] += dRc * FZ_E[c];
+        double dsum = s->dB_c[j] + dRc;
         double kappa = 1.0;
         if (Mkeep > 0.0 && dsum > 0.0) {
             double Mref = Vkeep * s->rho_ref[j];
@@ -1103,9 +1113,10 @@ static void phase3_vertex(orc_sim* s)
             s->kheat[v] = m > 0.0 ? (s->dK[v] + dKr) / m : 0.0;
             s->phi2r_b[v] += s->dB_v[j] * (poutRr - pinRr);
             s->phi2z_b[v] += s->dB_v[j] * (poutRz - pinRz);
-            s->phi2r_r[v] += s->dR_v[i] * (poutZr - pinZr);
-            s->phi2z_r[v] += s->dR_v[i] * (poutZz - pinZz);
-            double dsum = s->dB_v[j] + s->dR_v[i];
+            const double dRv = s->dR_v[i] * s->wR_v[j];
+            s->phi2r_r[v] += dRv * (poutZr - pinZr);
+            s->phi2z_r[v] += dRv * (poutZz - pinZz);
+            double dsum = s->dB_v[j] + dRv;
             pr = pr - dt * (dsum * pr + s->phi2r_b[v] + s->phi2r_r[v]);
             pz = pz - dt * (dsum * pz + s->phi2z_b[v] + s->phi2z_r[v]);
             /* a vertex with no material in any adjacent cell after the clean-up carries
