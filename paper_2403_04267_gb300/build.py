@@ -15,7 +15,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libsalec.so")
-SOURCES = ["salec_kernels.cu", "salec_api.cu", "salec_noalloc.cu"]
+SOURCES = ["salec_kernels.cu", "salec_api.cu", "salec_noalloc.cu", "mlp_kernels.cu", "mlp_api.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
@@ -31,7 +31,7 @@ def _stale() -> bool:
         return True
     t = os.path.getmtime(LIB)
     deps = [os.path.join(CSRC, f) for f in os.listdir(CSRC)]
-    deps.append(os.path.join(HERE, "..", "include", "salec.h"))
+    deps += [os.path.join(HERE, "..", "include", h) for h in ("salec.h", "salec_mlp.h")]
     return any(os.path.getmtime(p) > t for p in deps if os.path.exists(p))
 
 

@@ -1,0 +1,350 @@
+// mlp_api.cu -- C ABI of the crater-surrogate MLP: parameters, forward pass, gradient and
+// Adam training step on one caller-owned device buffer, plus the bare BF16 GEMM.
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdint>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "../../include/salec_mlp.h"
+#include "mlp_internal.cuh"
+
+using namespace salec::mlp;
+
+namespace {
+
+constexpr int kLayers = 5;
+constexpr int kDims[kLayers + 1] = {SALEC_MLP_IN, 256, 256, 256, 256, SALEC_MLP_OUT};
+constexpr int kHid = 256;
+
+size_t align_up(size_t x) { return (x + 255) & ~size_t(255); }
+
+long n_params()
+{
+    long n = 0;
+    for (int l = 0; l < kLayers; ++l) n += (long)kDims[l + 1] * kDims[l] + kDims[l + 1];
+    return n;
+}
+
+long n_weights()
+{
+    long n = 0;
+    for (int l = 0; l < kLayers; ++l) n += (long)kDims[l + 1] * kDims[l];
+    return n;
+}
+
+struct Layout {
+    size_t theta, m1, m2, grad, wmap, wbf, X, Z[4], H[4], Y, G[2], loss, err, total;
+    Layout(int bmax)
+    {
+        const long P = n_params(), W = n_weights();
+        size_t o = 0;
+        auto take = [&](size_t bytes) { size_t r = o; o = align_up(o + bytes); return r; };
+        theta = take(P * 4); m1 = take(P * 4); m2 = take(P * 4); grad = take(P * 4);
+        wmap = take(P * 4);
+        wbf = take(W * 2);
+        X = take((size_t)bmax * SALEC_MLP_IN * 2);
+        for (int l = 0; l < 4; ++l) Z[l] = take((size_t)bmax * kHid * 4);
+        for (int l = 0; l < 4; ++l) H[l] = take((size_t)bmax * kHid * 2);
+        Y = take((size_t)bmax * SALEC_MLP_OUT * 4);
+        for (int l = 0; l < 2; ++l) G[l] = take((size_t)bmax * kHid * 2);
+        loss = take(8);
+        err = take(4);
+        total = o;
+    }
+};
+
+}  // namespace
+
+struct salec_mlp {
+    int bmax = 0;
+    cudaStream_t stream = nullptr;
+    std::string err;
+    float *theta = nullptr, *m1 = nullptr, *m2 = nullptr, *grad = nullptr;
+    int* wmap = nullptr;
+    __nv_bfloat16* wbf = nullptr;
+    __nv_bfloat16* X = nullptr;
+    float* Z[4] = {};
+    __nv_bfloat16* H[4] = {};
+    float* Y = nullptr;
+    __nv_bfloat16* G[2] = {};
+    double* loss = nullptr;
+    int* errflag = nullptr;
+    long steps = 0;                       // Adam steps taken
+    long woff[kLayers], boff[kLayers];    // offsets of W_l and b_l in theta
+    long wbf_off[kLayers];                // offset of W_l in the BF16 weight block
+};
+
+namespace {
+
+salec_status fail(salec_mlp* n, salec_status st, const std::string& msg)
+{
+    if (n) n->err = msg;
+    return st;
+}
+
+salec_status cuda_fail(salec_mlp* n, cudaError_t e, const char* where)
+{
+    return fail(n, SALEC_ECUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+#define MLP_CUDA(n, call, where)                                   \
+    do {                                                           \
+        cudaError_t e_ = (call);                                   \
+        if (e_ != cudaSuccess) return cuda_fail((n), e_, (where)); \
+    } while (0)
+
+GemmArgs gemm0(int M, int N, int K, int* err)
+{
+    GemmArgs g = {};
+    g.M = M; g.N = N; g.K = K;
+    g.err = err;
+    return g;
+}
+
+// forward pass on X (already BF16): Z_l, H_l for the hidden layers; the output layer with
+// the epilogue `out_epi` (plain store into y, or the fused loss gradient against t)
+salec_status forward_impl(salec_mlp* n, int B, float* y, long ldy, const float* t, bool with_loss)
+{
+    const __nv_bfloat16* Hin = n->X;
+    long ldin = SALEC_MLP_IN;
+    for (int l = 0; l < kLayers; ++l) {
+        const int ni = kDims[l], no = kDims[l + 1];
+        GemmArgs g = gemm0(B, no, ni, n->errflag);
+        g.A = Hin; g.a_sm = ldin; g.a_sk = 1;
+        g.B = n->wbf + n->wbf_off[l]; g.b_sn = ni; g.b_sk = 1;
+        g.bias = n->theta + n->boff[l];
+        if (l + 1 < kLayers) {
+            g.epi = kEpiBiasGelu;
+            g.C = n->Z[l]; g.ldc = kHid;
+            g.Hout = n->H[l]; g.ldh = kHid;
+        } else if (with_loss) {
+            g.epi = kEpiOutLoss;
+            g.C = y; g.ldc = ldy;
+            g.Tin = t; g.ldt = SALEC_MLP_OUT;
+            g.Hout = n->G[0]; g.ldh = kHid;
+            g.grad_scale = 2.0f / ((float)B * (float)SALEC_MLP_OUT);
+            g.loss = n->loss;
+        } else {
+            g.epi = kEpiStore;
+            g.C = y; g.ldc = ldy;
+        }
+        MLP_CUDA(n, launch_gemm(g, n->stream), "mlp forward gemm");
+        Hin = n->H[l < 4 ? l : 3];
+        ldin = kHid;
+    }
+    return SALEC_OK;
+}
+
+// backward pass from G[0] = dL/dY (BF16): weight and bias gradients into grad
+salec_status backward_impl(salec_mlp* n, int B, float* grad)
+{
+    int cur = 0;
+    for (int l = kLayers - 1; l >= 0; --l) {
+        const int ni = kDims[l], no = kDims[l + 1];
+        const __nv_bfloat16* G = n->G[cur];
+        const __nv_bfloat16* Hprev = l > 0 ? n->H[l - 1] : n->X;
+        const long ldprev = l > 0 ? kHid : SALEC_MLP_IN;
+        // dW_l[o][i] = sum_b G[b][o] Hprev[b][i]
+        GemmArgs gw = gemm0(no, ni, B, n->errflag);
+        gw.A = G; gw.a_sm = 1; gw.a_sk = kHid;
+        gw.B = Hprev; gw.b_sn = 1; gw.b_sk = ldprev;
+        gw.epi = kEpiStore;
+        gw.C = grad + n->woff[l]; gw.ldc = ni;
+        MLP_CUDA(n, launch_gemm(gw, n->stream), "mlp weight-gradient gemm");
+        MLP_CUDA(n, launch_colsum(G, B, no, kHid, grad + n->boff[l], n->stream), "mlp bias gradient");
+        if (l == 0) break;
+        // dL/dZ_{l-1}[b][i] = (sum_o G[b][o] W_l[o][i]) gelu'(Z_{l-1}[b][i])
+        GemmArgs gd = gemm0(B, ni, no, n->errflag);
+        gd.A = G; gd.a_sm = kHid; gd.a_sk = 1;
+        gd.B = n->wbf + n->wbf_off[l]; gd.b_sn = 1; gd.b_sk = ni;
+        gd.epi = kEpiGeluBwd;
+        gd.Zin = n->Z[l - 1]; gd.ldz = kHid;
+        gd.Hout = n->G[cur ^ 1]; gd.ldh = kHid;
+        MLP_CUDA(n, launch_gemm(gd, n->stream), "mlp activation-gradient gemm");
+        cur ^= 1;
+    }
+    return SALEC_OK;
+}
+
+salec_status check_batch(salec_mlp* n, int B)
+{
+    if (!n) return SALEC_EINVAL;
+    if (B < 1 || B > n->bmax) return fail(n, SALEC_EINVAL, "batch outside 1..batch_max");
+    return SALEC_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int salec_mlp_n_params(void) { return (int)n_params(); }
+
+salec_status salec_mlp_bytes(int batch_max, size_t* bytes)
+{
+    if (!bytes || batch_max < 1) return SALEC_EINVAL;
+    *bytes = Layout(batch_max).total;
+    return SALEC_OK;
+}
+
+salec_status salec_mlp_create(int batch_max, void* dev_buf, size_t bytes, void* stream, salec_mlp** out)
+{
+    if (!out || !dev_buf || batch_max < 1) return SALEC_EINVAL;
+    *out = nullptr;
+    Layout L(batch_max);
+    if (bytes < L.total) return SALEC_ENOMEM;
+    if (reinterpret_cast<uintptr_t>(dev_buf) & 255) return SALEC_EINVAL;
+    salec_mlp* n = new (std::nothrow) salec_mlp();
+    if (!n) return SALEC_ENOMEM;
+    unsigned char* b = static_cast<unsigned char*>(dev_buf);
+    n->bmax = batch_max;
+    n->stream = static_cast<cudaStream_t>(stream);
+    n->theta = reinterpret_cast<float*>(b + L.theta);
+    n->m1 = reinterpret_cast<float*>(b + L.m1);
+    n->m2 = reinterpret_cast<float*>(b + L.m2);
+    n->grad = reinterpret_cast<float*>(b + L.grad);
+    n->wmap = reinterpret_cast<int*>(b + L.wmap);
+    n->wbf = reinterpret_cast<__nv_bfloat16*>(b + L.wbf);
+    n->X = reinterpret_cast<__nv_bfloat16*>(b + L.X);
+    for (int l = 0; l < 4; ++l) {
+        n->Z[l] = reinterpret_cast<float*>(b + L.Z[l]);
+        n->H[l] = reinterpret_cast<__nv_bfloat16*>(b + L.H[l]);
+    }
+    n->Y = reinterpret_cast<float*>(b + L.Y);
+    for (int l = 0; l < 2; ++l) n->G[l] = reinterpret_cast<__nv_bfloat16*>(b + L.G[l]);
+    n->loss = reinterpret_cast<double*>(b + L.loss);
+    n->errflag = reinterpret_cast<int*>(b + L.err);
+    // parameter offsets and the weight -> BF16 block map
+    const long P = n_params();
+    std::vector<int> wmap(P, -1);
+    long o = 0, w = 0;
+    for (int l = 0; l < kLayers; ++l) {
+        const long cnt = (long)kDims[l + 1] * kDims[l];
+        n->woff[l] = o;
+        n->wbf_off[l] = w;
+        for (long i = 0; i < cnt; ++i) wmap[o + i] = (int)(w + i);
+        o += cnt;
+        w += cnt;
+        n->boff[l] = o;
+        o += kDims[l + 1];
+    }
+    cudaError_t e = cudaMemsetAsync(dev_buf, 0, L.total, n->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(n->wmap, wmap.data(), P * sizeof(int), cudaMemcpyHostToDevice, n->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(n->stream);
+    if (e != cudaSuccess) {
+        delete n;
+        return SALEC_ECUDA;
+    }
+    *out = n;
+    return SALEC_OK;
+}
+
+salec_status salec_mlp_set_params(salec_mlp* n, const float* theta_host)
+{
+    if (!n || !theta_host) return SALEC_EINVAL;
+    const long P = n_params();
+    MLP_CUDA(n, cudaMemcpyAsync(n->theta, theta_host, P * 4, cudaMemcpyHostToDevice, n->stream), "set_params copy");
+    MLP_CUDA(n, cudaMemsetAsync(n->m1, 0, P * 4, n->stream), "set_params reset");
+    MLP_CUDA(n, cudaMemsetAsync(n->m2, 0, P * 4, n->stream), "set_params reset");
+    MLP_CUDA(n, launch_refresh_bf16(n->theta, P, n->wmap, n->wbf, n->stream), "set_params bf16 copy");
+    MLP_CUDA(n, cudaStreamSynchronize(n->stream), "set_params sync");
+    n->steps = 0;
+    return SALEC_OK;
+}
+
+salec_status salec_mlp_get_params(salec_mlp* n, float* theta_host)
+{
+    if (!n || !theta_host) return SALEC_EINVAL;
+    MLP_CUDA(n, cudaMemcpyAsync(theta_host, n->theta, n_params() * 4, cudaMemcpyDeviceToHost, n->stream), "get_params");
+    MLP_CUDA(n, cudaStreamSynchronize(n->stream), "get_params sync");
+    return salec_mlp_check(n);
+}
+
+salec_status salec_mlp_forward(salec_mlp* n, const float* x_dev, int batch, float* y_dev)
+{
+    salec_status st = check_batch(n, batch);
+    if (st != SALEC_OK) return st;
+    if (!x_dev || !y_dev) return fail(n, SALEC_EINVAL, "null pointer");
+    MLP_CUDA(n, launch_to_bf16(x_dev, (long)batch * SALEC_MLP_IN, n->X, n->stream), "mlp input");
+    return forward_impl(n, batch, y_dev, SALEC_MLP_OUT, nullptr, false);
+}
+
+salec_status salec_mlp_gradient(salec_mlp* n, const float* x_dev, const float* t_dev, int batch, float* grad_dev,
+                                double* loss_host)
+{
+    salec_status st = check_batch(n, batch);
+    if (st != SALEC_OK) return st;
+    if (!x_dev || !t_dev) return fail(n, SALEC_EINVAL, "null pointer");
+    float* grad = grad_dev ? grad_dev : n->grad;
+    MLP_CUDA(n, cudaMemsetAsync(n->loss, 0, 8, n->stream), "mlp loss reset");
+    MLP_CUDA(n, launch_to_bf16(x_dev, (long)batch * SALEC_MLP_IN, n->X, n->stream), "mlp input");
+    st = forward_impl(n, batch, n->Y, SALEC_MLP_OUT, t_dev, true);
+    if (st != SALEC_OK) return st;
+    st = backward_impl(n, batch, grad);
+    if (st != SALEC_OK) return st;
+    if (loss_host) {
+        double s = 0.0;
+        MLP_CUDA(n, cudaMemcpyAsync(&s, n->loss, 8, cudaMemcpyDeviceToHost, n->stream), "mlp loss read");
+        MLP_CUDA(n, cudaStreamSynchronize(n->stream), "mlp loss sync");
+        *loss_host = s / ((double)batch * SALEC_MLP_OUT);
+        return salec_mlp_check(n);
+    }
+    return SALEC_OK;
+}
+
+salec_status salec_mlp_train_step(salec_mlp* n, const float* x_dev, const float* t_dev, int batch, float lr,
+                                  float beta1, float beta2, float eps, double* sse_dev)
+{
+    salec_status st = check_batch(n, batch);
+    if (st != SALEC_OK) return st;
+    if (!x_dev || !t_dev) return fail(n, SALEC_EINVAL, "null pointer");
+    if (!(lr >= 0.0f) || !(beta1 >= 0.0f && beta1 < 1.0f) || !(beta2 >= 0.0f && beta2 < 1.0f) || !(eps > 0.0f))
+        return fail(n, SALEC_EINVAL, "bad Adam hyper-parameters");
+    MLP_CUDA(n, cudaMemsetAsync(n->loss, 0, 8, n->stream), "mlp loss reset");
+    MLP_CUDA(n, launch_to_bf16(x_dev, (long)batch * SALEC_MLP_IN, n->X, n->stream), "mlp input");
+    st = forward_impl(n, batch, n->Y, SALEC_MLP_OUT, t_dev, true);
+    if (st != SALEC_OK) return st;
+    st = backward_impl(n, batch, n->grad);
+    if (st != SALEC_OK) return st;
+    n->steps += 1;
+    AdamArgs a;
+    a.lr = lr; a.beta1 = beta1; a.beta2 = beta2; a.eps = eps;
+    a.c1 = (float)(1.0 / (1.0 - std::pow((double)beta1, (double)n->steps)));
+    a.c2 = (float)(1.0 / (1.0 - std::pow((double)beta2, (double)n->steps)));
+    MLP_CUDA(n, launch_adam(n->theta, n->m1, n->m2, n->grad, n_params(), a, n->wmap, n->wbf, n->stream), "mlp adam");
+    if (sse_dev) MLP_CUDA(n, cudaMemcpyAsync(sse_dev, n->loss, 8, cudaMemcpyDeviceToDevice, n->stream), "mlp loss copy");
+    return SALEC_OK;
+}
+
+salec_status salec_mlp_check(salec_mlp* n)
+{
+    if (!n) return SALEC_EINVAL;
+    int f = 0;
+    MLP_CUDA(n, cudaMemcpyAsync(&f, n->errflag, 4, cudaMemcpyDeviceToHost, n->stream), "mlp flag read");
+    MLP_CUDA(n, cudaStreamSynchronize(n->stream), "mlp flag sync");
+    if (f) return fail(n, SALEC_ECUDA, "a tensor-core wait ran out of time");
+    return SALEC_OK;
+}
+
+salec_status salec_gemm_bf16(int M, int N, int K, const void* A, long a_sm, long a_sk, const void* B, long b_sn,
+                             long b_sk, float* C, long ldc, void* stream)
+{
+    if (M < 0 || N < 0 || K < 0) return SALEC_EINVAL;
+    if (M > 0 && N > 0 && (!C || (K > 0 && (!A || !B)))) return SALEC_EINVAL;   // K = 0: C = 0, A and B unused
+    GemmArgs g = gemm0(M, N, K, nullptr);
+    g.A = static_cast<const __nv_bfloat16*>(A); g.a_sm = a_sm; g.a_sk = a_sk;
+    g.B = static_cast<const __nv_bfloat16*>(B); g.b_sn = b_sn; g.b_sk = b_sk;
+    g.epi = kEpiStore;
+    g.C = C; g.ldc = ldc;
+    if (launch_gemm(g, static_cast<cudaStream_t>(stream)) != cudaSuccess) return SALEC_ECUDA;
+    return SALEC_OK;
+}
+
+const char* salec_mlp_last_error(const salec_mlp* n) { return n ? n->err.c_str() : ""; }
+
+void salec_mlp_destroy(salec_mlp* n) { delete n; }
+
+}  // extern "C"

@@ -1,0 +1,54 @@
+// mlp_internal.cuh -- argument blocks and launchers of the surrogate-MLP kernels.
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <stddef.h>
+
+namespace salec {
+namespace mlp {
+
+// fused epilogues of the GEMM
+enum Epi {
+    kEpiStore = 0,      // C = acc (+ bias[n] if bias)                               FP32
+    kEpiBiasGelu = 1,   // C = Z = acc + bias[n] (FP32), Hout = gelu(Z) (BF16)
+    kEpiGeluBwd = 2,    // Hout = acc * gelu'(Zin) (BF16): dL/dZ of a hidden layer
+    kEpiOutLoss = 3,    // C = Y = acc + bias[n]; Hout = grad_scale (Y - Tin) (BF16); loss += sum (Y - Tin)^2
+};
+
+struct GemmArgs {
+    int M, N, K;
+    const __nv_bfloat16* A;
+    long a_sm, a_sk;
+    const __nv_bfloat16* B;
+    long b_sn, b_sk;
+    int epi;
+    float* C;                 // FP32 output, row stride ldc
+    long ldc;
+    const float* bias;        // [N] or null
+    __nv_bfloat16* Hout;      // BF16 output, row stride ldh
+    long ldh;
+    const float* Zin;         // saved pre-activations, row stride ldz
+    long ldz;
+    const float* Tin;         // targets, row stride ldt
+    long ldt;
+    float grad_scale;         // 2 / (B n_out)
+    double* loss;             // sum of squared errors (atomic), or null
+    int* err;                 // error flag, or null
+    int nt, tmem_cols;        // set by the launcher
+};
+
+struct AdamArgs {
+    float lr, beta1, beta2, eps, c1, c2;   // c1 = 1 / (1 - beta1^t), c2 = 1 / (1 - beta2^t)
+};
+
+cudaError_t launch_gemm(const GemmArgs& g, cudaStream_t s);
+cudaError_t launch_colsum(const __nv_bfloat16* G, int M, int N, long ldg, float* out, cudaStream_t s);
+cudaError_t launch_to_bf16(const float* x, long n, __nv_bfloat16* y, cudaStream_t s);
+cudaError_t launch_adam(float* theta, float* m1, float* m2, const float* grad, long n, const AdamArgs& a,
+                        const int* wmap, __nv_bfloat16* wbf, cudaStream_t s);
+cudaError_t launch_refresh_bf16(const float* theta, long n, const int* wmap, __nv_bfloat16* wbf, cudaStream_t s);
+size_t gemm_smem_bytes(int nt);
+
+}  // namespace mlp
+}  // namespace salec

@@ -153,3 +153,19 @@ def batched_run(draw: dict, n_override: int | None = None) -> dict:
     w["name"] = f"batched_seed{draw['seed']}"
     w["t_end"] = 20.0
     return w
+
+
+# --- surrogate network initial parameters -------------------------------------------------
+
+def mlp_init(seed: int, dims=(5, 256, 256, 256, 256, 66), gain: float = 1.0):
+    """Flat parameter vector (per layer W row-major, then b), weights and biases uniform on
+    +-gain/sqrt(n_in), from a seeded generator."""
+    import numpy as np
+    rng = np.random.default_rng(seed)
+    parts = []
+    for l in range(len(dims) - 1):
+        ni, no = dims[l], dims[l + 1]
+        s = gain / math.sqrt(ni)
+        parts.append(rng.uniform(-s, s, no * ni))
+        parts.append(rng.uniform(-s, s, no))
+    return np.concatenate(parts)

@@ -1,0 +1,162 @@
+"""Tensor-core kernels of the crater-surrogate MLP against the FP64 oracle.
+
+The GEMM is compared with exact FP64 sums of the same BF16 products.  The network's
+forward pass, gradient and Adam step are compared with the oracle in its BF16 form, which
+rounds the same tensors to BF16 and does all arithmetic in FP64; the remaining differences
+come from FP32 accumulation and FP32 GELU, which move a BF16 rounding of an activation or a
+back-propagated gradient now and then by one unit (2^-8 relative) -- the tolerances below
+allow for a fraction of those."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from oracle import mlp_oracle as M
+from paper_2403_04267_gb300 import salec, surrogate as S, workloads as W
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    torch.cuda.set_device(0)
+    salec.load()
+
+
+def _bf16(a):
+    return torch.from_numpy(np.ascontiguousarray(a, dtype=np.float32)).to(torch.bfloat16).cuda()
+
+
+@pytest.mark.parametrize("M_,N_,K_,at,bt", [
+    (128, 256, 64, False, False),       # one full tile
+    (1, 16, 1, False, False),           # smallest
+    (300, 80, 200, False, False),       # ragged M tail, N not a multiple of 64, K tail
+    (257, 300, 129, True, False),       # two N tiles, transposed A
+    (130, 66, 520, False, True),        # transposed B
+    (66, 5, 4096, True, True),          # weight-gradient shape: long K, tiny N
+    (64, 256, 0, False, False),         # empty sum
+])
+def test_gemm_matches_exact_sums(M_, N_, K_, at, bt):
+    rng = np.random.default_rng(M_ * 7 + N_ * 13 + K_)
+    a = M.bf16_round(rng.standard_normal((M_, K_)))
+    b = M.bf16_round(rng.standard_normal((N_, K_)))
+    # stored transposed where asked: A(m, k) at k * M + m
+    A = _bf16(a.T.copy() if at else a)
+    B = _bf16(b.T.copy() if bt else b)
+    a_str = (1, M_) if at else (K_, 1)
+    b_str = (1, N_) if bt else (K_, 1)
+    ldc = N_ + 3
+    Cd = torch.full((max(M_, 1), ldc), float("nan"), dtype=torch.float32, device="cuda")
+    S.gemm_bf16(M_, N_, K_, A, a_str, B, b_str, Cd, ldc)
+    torch.cuda.synchronize()
+    got = Cd.cpu().numpy().astype(np.float64)
+    exact = a @ b.T
+    bound = np.abs(a) @ np.abs(b).T
+    err = np.abs(got[:M_, :N_] - exact)
+    # FP32 accumulation of K products: far below 2^-14 of the sum of magnitudes
+    assert np.all(err <= 2.0 ** -14 * bound + 1e-30), float(np.max(err / (bound + 1e-300)))
+    assert np.all(np.isnan(got[:M_, N_:]))       # columns past N untouched
+
+
+def _net(seed=11, gain=1.5):
+    return W.mlp_init(seed, gain=gain).astype(np.float32).astype(np.float64)
+
+
+def _data(B, seed=5):
+    rng = np.random.default_rng(seed)
+    X = rng.uniform(-1, 1, (B, 5)).astype(np.float32)
+    T = (0.5 * rng.standard_normal((B, 66))).astype(np.float32)
+    return X, T
+
+
+def test_forward_matches_oracle():
+    theta = _net()
+    X, _ = _data(300)
+    net = S.MLP(512)
+    net.set_params(theta)
+    y = net.forward(torch.from_numpy(X).cuda()).cpu().numpy().astype(np.float64)
+    ref, _ = M.forward(theta, X.astype(np.float64), bf16=True)
+    scale = np.max(np.abs(ref))
+    assert np.linalg.norm(y - ref) / np.linalg.norm(ref) < 1e-3
+    assert np.max(np.abs(y - ref)) < 1e-2 * scale
+
+
+def test_forward_single_chain():
+    """One chain of units (input 0 -> 3 -> 7 -> 1 -> 250 -> output 65) with unit weights:
+    output 65 is 2 gelu(gelu(gelu(gelu(x0)))) + 0.5 up to one BF16 rounding per layer and
+    every other output is exactly 0."""
+    theta = np.zeros(M.n_params())
+    L = M.unpack(theta)
+    L[0][0][3, 0] = 1.0
+    L[1][0][7, 3] = 1.0
+    L[2][0][1, 7] = 1.0
+    L[3][0][250, 1] = 1.0
+    L[4][0][65, 250] = 2.0
+    L[4][1][65] = 0.5
+    X = np.zeros((200, 5), dtype=np.float32)
+    X[:, 0] = np.linspace(-2, 2, 200, dtype=np.float32)
+    X[:, 3] = 9.0
+    net = S.MLP(256)
+    net.set_params(theta)
+    y = net.forward(torch.from_numpy(X).cuda()).cpu().numpy().astype(np.float64)
+    g = M.gelu
+    expect = 2.0 * g(g(g(g(M.bf16_round(X[:, 0].astype(np.float64)))))) + 0.5
+    assert np.max(np.abs(y[:, 65] - expect)) < 4 * 2.0 ** -8 * np.max(np.abs(expect))
+    y[:, 65] = 0.0
+    assert np.all(y == 0.0)
+
+
+def test_gradient_matches_oracle():
+    theta = _net(seed=12)
+    X, T = _data(260, seed=6)
+    net = S.MLP(512)
+    net.set_params(theta)
+    loss, g = net.gradient(torch.from_numpy(X).cuda(), torch.from_numpy(T).cuda())
+    g = g.cpu().numpy().astype(np.float64)
+    L_ref, g_ref = M.backward(theta, X.astype(np.float64), T.astype(np.float64), bf16=True)
+    assert abs(loss - L_ref) <= 1e-4 * L_ref
+    o = 0
+    for l, (ni, no) in enumerate(zip(M.DIMS[:-1], M.DIMS[1:])):
+        for name, cnt in (("W", ni * no), ("b", no)):
+            a, r = g[o:o + cnt], g_ref[o:o + cnt]
+            assert np.linalg.norm(a - r) <= 1e-2 * np.linalg.norm(r) + 1e-12, (l, name)
+            o += cnt
+    assert o == g.size
+
+
+def test_adam_step_matches_oracle():
+    theta = _net(seed=13)
+    X, T = _data(128, seed=7)
+    net = S.MLP(128)
+    net.set_params(theta)
+    lr = 1e-3
+    net.train_step(torch.from_numpy(X).cuda(), torch.from_numpy(T).cuda(), lr)
+    got = net.get_params().astype(np.float64)
+    _, g_ref = M.backward(theta, X.astype(np.float64), T.astype(np.float64), bf16=True)
+    ref = theta.copy()
+    M.adam(ref, g_ref, np.zeros_like(ref), np.zeros_like(ref), 1, lr)
+    step_ref = ref - theta
+    step = got - theta
+    # the first Adam step is lr * g / (|g| + eps): +-lr wherever |g| >> eps; parameters
+    # whose gradient sign is uncertain (|g| at rounding level) may move either way
+    big = np.abs(g_ref) > 1e-3 * np.max(np.abs(g_ref))
+    assert np.mean(np.abs(step[big] - step_ref[big]) < 1e-2 * lr) > 0.99
+    assert np.max(np.abs(step)) <= lr * (1 + 1e-3)
+
+
+def test_training_reduces_loss():
+    rng = np.random.default_rng(21)
+    X = rng.uniform(-1, 1, (1024, 5)).astype(np.float32)
+    # a smooth target: each output a fixed combination of sines of the inputs
+    Wt = rng.standard_normal((5, 66)) * 0.8
+    T = np.sin(X.astype(np.float64) @ Wt).astype(np.float32)
+    net = S.MLP(1024)
+    net.set_params(W.mlp_init(3).astype(np.float32))
+    Xd, Td = torch.from_numpy(X).cuda(), torch.from_numpy(T).cuda()
+    l0, _ = net.gradient(Xd, Td)
+    for _ in range(300):
+        net.train_step(Xd, Td, 2e-3)
+    l1, _ = net.gradient(Xd, Td)
+    net.check()
+    assert l1 < 0.1 * l0, (l0, l1)
