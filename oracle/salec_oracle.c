@@ -112,9 +112,10 @@ static void tillotson(const orc_material* m, double rho, double I_in, double* p_
     double dpc_drho = (m->a + m->b / w0) * I + 2.0 * m->b * I * I / (w0 * w0 * m->E0 * eta * eta)
                       + (m->A + 2.0 * m->B * mu) / m->rho0;
     double dpc_dI = rho * (m->a + m->b / w0 - m->b * I / (w0 * w0 * m->E0 * eta * eta));
-    double p, dp_drho, dp_dI;
+    double p, c2;
     if (rho >= m->rho0 || I <= m->Eiv) {
-        p = pc; dp_drho = dpc_drho; dp_dI = dpc_dI;
+        p = pc;
+        c2 = dpc_drho + pc / (rho * rho) * dpc_dI;
     } else {
         /* expanded branch p_e */
         double x = m->rho0 / rho - 1.0;
@@ -129,18 +130,22 @@ static void tillotson(const orc_material* m, double rho, double I_in, double* p_
         double dpe_drho = m->a * I + (dbterm_drho + daterm_drho) * Ea
                           + (bterm + aterm) * Ea * (-2.0 * m->alpha * x) * dx_drho;
         double dpe_dI = m->a * rho + (m->b * rho / w0 - m->b * rho * I / (w0 * w0 * m->E0 * eta * eta)) * Ea;
+        const double ce2 = dpe_drho + pe / (rho * rho) * dpe_dI;
         if (I >= m->Ecv) {
-            p = pe; dp_drho = dpe_drho; dp_dI = dpe_dI;
+            p = pe;
+            c2 = ce2;
         } else {
-            /* linear blend in I between the two branches */
+            /* linear blend in I between the two branches; the sound speed is the same blend
+               of the branches' own sound speeds (reading: the derivative of the blended
+               pressure adds (p_e - p_c)/(E_cv - E_iv) p/rho^2, which grows without bound
+               as rho -> 0 when A != B and is discontinuous at both blend ends) */
             double den = m->Ecv - m->Eiv;
             double we = I - m->Eiv, wc = m->Ecv - I;
             p = (we * pe + wc * pc) / den;
-            dp_drho = (we * dpe_drho + wc * dpc_drho) / den;
-            dp_dI = (we * dpe_dI + pe + wc * dpc_dI - pc) / den;
+            const double cc2 = dpc_drho + pc / (rho * rho) * dpc_dI;
+            c2 = (we * ce2 + wc * cc2) / den;
         }
     }
-    double c2 = dp_drho + p / (rho * rho) * dp_dI;
     double floor2 = 0.01 * m->A / m->rho0;
     if (!(c2 > floor2)) c2 = floor2;
     *p_out = p;

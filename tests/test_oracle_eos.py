@@ -88,3 +88,39 @@ def test_ideal_gas_textbook():
     p, c2 = O.eos(g, 2.0, 3.0)
     assert math.isclose(p, 0.4 * 2.0 * 3.0, rel_tol=1e-15)
     assert math.isclose(c2, 1.4 * p / 2.0, rel_tol=1e-15)
+
+
+def _branch_c2(m, rho, I, branch):
+    """c^2 of one Tillotson branch at (rho, I): the same material with the blend moved out
+    of the way (the branch formulas do not involve E_iv, E_cv), each branch pinned above by
+    central differences."""
+    mm = dict(m)
+    if branch == "compressed":
+        mm.update(Eiv=10.0 * I, Ecv=20.0 * I)     # I <= E_iv: compressed formula
+    else:
+        mm.update(Eiv=0.25 * I, Ecv=0.5 * I)      # I >= E_cv: expanded formula
+    return O.eos(mm, rho, I)[1]
+
+
+@pytest.mark.parametrize("m", [BAS, IRON])
+@pytest.mark.parametrize("eta", [0.9, 0.5, 1e-2, 1e-4])
+def test_blend_sound_speed_is_blend_of_branch_sound_speeds(m, eta):
+    """Reading of the hybrid region: c^2 = ((I - E_iv) c_e^2 + (E_cv - I) c_c^2) / (E_cv - E_iv),
+    floored like everywhere else; continuous at both blend ends, and bounded by the branch
+    values even far below rho0, where the derivative of the blended pressure is not (for
+    iron, A != B, it reaches c ~ 1e5 m/s at rho ~ 1e-4 rho0)."""
+    rho = eta * m["rho0"]
+    floor = 0.01 * m["A"] / m["rho0"]
+    for f in (0.1, 0.5, 0.9, 1 - 1e-6):
+        I = m["Eiv"] + f * (m["Ecv"] - m["Eiv"])
+        ce2, cc2 = _branch_c2(m, rho, I, "expanded"), _branch_c2(m, rho, I, "compressed")
+        _, c2 = O.eos(m, rho, I)
+        raw_e = ce2 if ce2 > floor else None
+        raw_c = cc2 if cc2 > floor else None
+        if raw_e is not None and raw_c is not None:
+            assert math.isclose(c2, max(f * ce2 + (1 - f) * cc2, floor), rel_tol=1e-9)
+        assert c2 <= max(ce2, cc2, floor) * (1 + 1e-12)
+    for Ie in (m["Eiv"], m["Ecv"]):
+        ca = O.eos(m, rho, Ie * (1 + 1e-10))[1]
+        cb = O.eos(m, rho, Ie * (1 - 1e-10))[1]
+        assert abs(ca - cb) <= 1e-6 * max(ca, cb)
