@@ -49,7 +49,7 @@ class Material(C.Structure):
 class Grid(C.Structure):
     _fields_ = [
         ("nr", C.c_int), ("nz", C.c_int), ("nmat", C.c_int), ("dx", C.c_double),
-        ("pml_r", C.c_int), ("pml_b", C.c_int), ("pml_R", C.c_double), ("pml_c", C.c_double),
+        ("pml_r", C.c_int), ("pml_b", C.c_int), ("pml_R", C.c_double), ("pml_c", C.c_double), ("pml_alpha", C.c_double),
         ("gravity", C.c_double), ("cfl", C.c_double), ("dt_init", C.c_double),
         ("dt_max", C.c_double), ("dt_growth", C.c_double), ("dt_min", C.c_double),
         ("av_cq", C.c_double), ("av_cl", C.c_double), ("f_min", C.c_double),
@@ -99,7 +99,7 @@ def lib():
         L.orc_surface_heights.argtypes = [P, D]
         L.orc_eos.argtypes = [C.POINTER(Material), C.c_double, C.c_double, D, D]
         L.orc_yield.restype = C.c_double
-        L.orc_yield.argtypes = [C.POINTER(Material), C.c_double, C.c_double]
+        L.orc_yield.argtypes = [C.POINTER(Material), C.c_double, C.c_double, C.c_double, C.c_double]
         L.orc_stress_update.argtypes = [D, D, C.c_double, C.c_double, C.c_double, C.c_double]
         L.orc_pml_profile.restype = C.c_double
         L.orc_pml_profile.argtypes = [C.c_double] * 5
@@ -141,9 +141,9 @@ def eos(material: dict, rho: float, I: float):
     return p.value, c2.value
 
 
-def yield_strength(material: dict, p: float, D: float) -> float:
+def yield_strength(material: dict, p: float, D: float, I: float = 0.0, rho: float | None = None) -> float:
     m = make_material(material)
-    return lib().orc_yield(C.byref(m), p, D)
+    return lib().orc_yield(C.byref(m), p, D, I, material["rho0"] if rho is None else rho)
 
 
 def stress_update(s4, rates5, G: float, Y: float, inv_epsf: float, dt: float):

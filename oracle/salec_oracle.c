@@ -47,7 +47,7 @@ typedef struct {
     int nr, nz, nmat;
     double dx;
     int pml_r, pml_b;
-    double pml_R, pml_c;
+    double pml_R, pml_c, pml_alpha;
     double gravity, cfl, dt_init, dt_max, dt_growth, dt_min;
     double av_cq, av_cl, f_min;
     int bc_top, bc_bottom;
@@ -69,6 +69,7 @@ typedef struct {
     double *phi2r_r, *phi2z_r, *psi1r_r, *psi1z_r;                     /* vertices, right strip */
     double *dB_c, *dB_v, *dR_c, *dR_v;   /* damping profiles: rows (cells, vertices), columns */
     double *wR_c, *wR_v;                 /* 1 on rows whose reference state holds material (cells, vertices) */
+    double alpha_b, alpha_r;             /* relaxation rates of the strips' auxiliaries */
     double *p0, *rho_ref, *I_ref;        /* reference state per row */
     /* set-up accumulators */
     double *setup_V[ORC_MAXMAT], *setup_M[ORC_MAXMAT], *setup_E, *setup_Pz;
@@ -167,19 +168,43 @@ static void material_eos(const orc_material* m, double rho, double I, double* p,
 }
 
 /* ------------------------------------------------------------------------------------
+ * Strength and tension of strongly expanded material.  Reading: rock expanded well below
+ * its reference density is fragmented; below rho0 / 2 it carries neither shear strength
+ * nor tension, and between rho0 / 2 and rho0 both are scaled by w = 2 rho / rho0 - 1.  In
+ * dilute ejecta (1e-7 of rho0 and less) a stress or tension of even the damaged cohesion
+ * times the strain of a step, per unit of so little mass, sends the specific energy to
+ * +-1e10 J/kg.  Pinned by test_oracle_strength.py.
+ * ------------------------------------------------------------------------------------ */
+static double expansion_weight(const orc_material* m, double rho)
+{
+    double w = 2.0 * rho / m->rho0 - 1.0;
+    return w < 0.0 ? 0.0 : (w > 1.0 ? 1.0 : w);
+}
+
+/* ------------------------------------------------------------------------------------
  * Collins et al. (2004) pressure-dependent yield strength (Sect. 1 cites it; Table 1
  * lists its constants), blended by the scalar damage D:
  *   Y_i = Y_i0 + mu_i p / (1 + mu_i p / (Y_im - Y_i0)),  Y_d = min(Y_d0 + mu_d p, Y_dm),
- *   Y = (1 - D) Y_i + D Y_d, evaluated at max(p, 0).
- * Pinned by test_oracle_strength.py (limits p -> 0, p -> infinity, D = 0 and D = 1).
+ *   Y = (1 - D) Y_i + D Y_d, evaluated at max(p, 0), times the thermal-softening factor
+ *   below (1 at I = 0) and the expansion weight above (1 at rho >= rho0).
+ * Pinned by test_oracle_strength.py (limits p -> 0, p -> infinity, D = 0 and D = 1;
+ * softening factor tanh(1.2) at I = E_iv / 2, zero from E_iv up).
  * ------------------------------------------------------------------------------------ */
-static double collins_yield(const orc_material* m, double p_in, double D)
+static double collins_yield(const orc_material* m, double p_in, double D, double I, double rho)
 {
     double p = p_in > 0.0 ? p_in : 0.0;
     double Yi = m->Yi0 + m->mui * p / (1.0 + m->mui * p / (m->Yim - m->Yi0));
     double Yd = m->Yd0 + m->mud * p;
     if (Yd > m->Ydm) Yd = m->Ydm;
     double Y = (1.0 - D) * Yi + D * Yd;
+    /* thermal softening (Collins et al. 2004): Y tanh(xi (T_m / T - 1)), xi = 1.2, zero at
+       and above melting.  The state carries no temperature; reading: T_m / T = E_iv / I with
+       the Tillotson incipient-vaporisation energy as the melt-energy scale */
+    if (I > 0.0) {
+        if (!(I < m->Eiv)) return 0.0;
+        Y *= tanh(1.2 * (m->Eiv / I - 1.0));
+    }
+    Y *= expansion_weight(m, rho);
     return Y > 0.0 ? Y : 0.0;
 }
 
@@ -385,7 +410,7 @@ static void cell_eos(const orc_sim* s, int c, double* phat, double* phi, double*
         if (!(fm > 0.0)) continue;
         double p, c2;
         material_eos(&s->mat[m], s->rho[m][c], s->I[c], &p, &c2);
-        double pmin = (1.0 - s->D[c]) * s->mat[m].p_t;
+        double pmin = (1.0 - s->D[c]) * s->mat[m].p_t * expansion_weight(&s->mat[m], s->rho[m][c]);
         if (p < pmin) p = pmin;
         ph += fm * p;
         fsum += fm;
@@ -463,6 +488,15 @@ int orc_finalize(orc_sim* s)
     }
     int pb = s->g.pml_b, pr = s->g.pml_r;
     if ((pb > 0 || pr > 0) && !(c > 0.0 && s->g.pml_R > 0.0 && s->g.pml_R < 1.0)) return 3;
+    /* relaxation of the auxiliaries (reading): each auxiliary decays at rate
+       alpha = pml_alpha c / delta of its strip, the complex-frequency-shifted stretch
+       s = 1 + d / (alpha + i omega) (Kuzuoglu & Mittra 1996) in place of 1 + d / (i omega).
+       Without it an auxiliary integrates a static tangential term -- the residual
+       deviatoric stress a shock leaves in a strong target -- without bound, and the
+       resulting force lifts the bottom strip until a cell empties (a batched impact at
+       t = 9 s).  Waves with omega >> alpha are absorbed and passed tangentially as before. */
+    s->alpha_b = pb > 0 ? s->g.pml_alpha * c / (pb * s->g.dx) : 0.0;
+    s->alpha_r = pr > 0 ? s->g.pml_alpha * c / (pr * s->g.dx) : 0.0;
     for (int j = 0; j < nz; ++j)
         s->dB_c[j] = j < pb ? pml_profile(c, pb, s->g.dx, (double)pb - (double)j - 0.5, s->g.pml_R) : 0.0;
     for (int j = 0; j <= nz; ++j)
@@ -483,7 +517,8 @@ int orc_finalize(orc_sim* s)
 
 /* ------------------------------------------------------------------------------------
  * Phase 0: EoS, artificial viscosity and the Courant time step.
- *   p_hat = sum_m f_m max(p_m, (1-D) p_t,m)   (void carries no pressure)
+ *   p_hat = sum_m f_m max(p_m, (1-D) p_t,m w_m)   (void carries no pressure; w_m the
+ *   expansion weight)
  *   q = rho_bar (c_Q dx^2 div^2 - c_L dx c div) when div v < 0            (Amsden 1980)
  *   P = p_hat + Phi q,   Phi = sum_m f_m
  *   dt = min(C0 min_cells dx / (max_vertex |v| + c), growth dt_prev, dt_max)   (Eq. 14)
@@ -646,10 +681,10 @@ static void phase1_vertex(orc_sim* s)
                 Tr_b += 0.5 * AR * (((Pp[0] + Pp[3]) - Pp[1]) - Pp[2]);
                 Tz_r += 0.5 * (AZl * (Pp[0] - Pp[3]) + AZr * (Pp[1] - Pp[2]));
             }
-            s->psi1r_b[v] -= dt * s->dB_v[j] * Tr_b;
-            s->psi1z_b[v] -= dt * s->dB_v[j] * Tz_b;
-            s->psi1r_r[v] -= dt * dRv * Tr_r;
-            s->psi1z_r[v] -= dt * dRv * Tz_r;
+            s->psi1r_b[v] = s->psi1r_b[v] * (1.0 - s->alpha_b * dt) - dt * s->dB_v[j] * Tr_b;
+            s->psi1z_b[v] = s->psi1z_b[v] * (1.0 - s->alpha_b * dt) - dt * s->dB_v[j] * Tz_b;
+            s->psi1r_r[v] = s->psi1r_r[v] * (1.0 - s->alpha_r * dt) - dt * dRv * Tr_r;
+            s->psi1z_r[v] = s->psi1z_r[v] * (1.0 - s->alpha_r * dt) - dt * dRv * Tz_r;
             s->mv[v] = mass;
             double vr = 0.0, vz = 0.0;
             if (mass > 0.0) {
@@ -716,9 +751,9 @@ void orc_stress_update(double sv[4], const double rates[5], double G, double Y, 
  * from the Lagrangian velocities v^L:
  *   dV = dt (A_R uR - A_L uL + A_Z (uT - uB)),  V^L = V + dV
  *   E^L = E - P dV + dt V (S:eps_dot) - dt psi2,   psi2 <- psi2 - dt d Pi_tangential
- *   volume change: in compression the void closes first; in expansion matter and void
- *   share dV in proportion to their fractions (consistent with the Phi-weighted pressure
- *   work); materials share the matter part pro rata;
+ *   volume change: matter and void share dV in proportion to their fractions in
+ *   compression and in expansion (equal strain: the material work sum_m -p_m dV_m is then
+ *   the -P dV charged to the energy); materials share the matter part pro rata;
  *   Jaumann elastic predictor, von Mises return to Y(p, D), damage += eps_p / eps_f.
  * Pinned by test_oracle_strength.py (pure-shear driver), test_oracle_conservation.py and
  * test_oracle_rh.py.
@@ -765,25 +800,15 @@ static void phase2_cell(orc_sim* s)
             double Stt = -(Srr + Szz);
             double Pi_rad = -P * radial_flux + V * (Srr * err + Stt * ett + Srz * dvz_dr);
             double Pi_ver = -P * vertical_flux + V * (Szz * ezz + Srz * dvr_dz);
-            s->psi2_b[c] -= dt * s->dB_c[j] * Pi_rad;
-            s->psi2_r[c] -= dt * s->dR_c[i] * s->wR_c[j] * Pi_ver;
+            s->psi2_b[c] = s->psi2_b[c] * (1.0 - s->alpha_b * dt) - dt * s->dB_c[j] * Pi_rad;
+            s->psi2_r[c] = s->psi2_r[c] * (1.0 - s->alpha_r * dt) - dt * s->dR_c[i] * s->wR_c[j] * Pi_ver;
             double M = 0.0;
             for (int m = 0; m < nm; ++m) M += s->f[m][c] * s->rho[m][c] * V;
             double dE = -P * dV + dt * V * (Srr * err + Szz * ezz + Stt * ett + 2.0 * Srz * erz)
                         - dt * (s->psi2_b[c] + s->psi2_r[c]);
             s->IL[c] = M > 0.0 ? s->I[c] + dE / M : s->I[c];
-            /* volume partition */
-            double Vvoid = (1.0 - phi) * V;
-            if (Vvoid < 0.0) Vvoid = 0.0;
-            double dVvoid, dVmat;
-            if (dV < 0.0) {
-                dVvoid = dV > -Vvoid ? dV : -Vvoid;
-                dVmat = dV - dVvoid;
-            } else {
-                dVmat = phi * dV;
-                dVvoid = dV - dVmat;
-            }
-            (void)dVvoid;
+            /* volume partition: matter and void share dV in proportion to their fractions */
+            double dVmat = phi * dV;
             for (int m = 0; m < nm; ++m) {
                 double fm = s->f[m][c];
                 if (!(fm > 0.0)) { s->fL[m][c] = 0.0; s->rhoL[m][c] = 0.0; continue; }
@@ -800,7 +825,7 @@ static void phase2_cell(orc_sim* s)
                 if (!(fm > 0.0) || s->mat[m].strength != ORC_STR_COLLINS) continue;
                 const orc_material* mm = &s->mat[m];
                 G += fm * mm->G;
-                Y += fm * collins_yield(mm, s->pbar[c], s->D[c]);
+                Y += fm * collins_yield(mm, s->pbar[c], s->D[c], s->I[c], s->rho[m][c]);
                 double ef = mm->B_dam * (s->pbar[c] - mm->p_bd);
                 if (ef < mm->eps_fb) ef = mm->eps_fb;
                 inv_epsf += fm / ef;
@@ -978,11 +1003,11 @@ static void phase3_remap(orc_sim* s)
         if (!(Mkeep > 0.0)) { I = 0.0; srr = 0.0; szz = 0.0; srz = 0.0; D = 0.0; }
         /* PML auxiliaries take d times the tangential divergence: radial in the bottom
            strip, vertical in the right strip */
-        s->phi1_b[c] += s->dB_c[j] * FR_M[c];
-        s->phi3_b[c] += s->dB_c[j] * FR_E[c];
+        s->phi1_b[c] = s->phi1_b[c] * (1.0 - s->alpha_b * dt) + s->dB_c[j] * FR_M[c];
+        s->phi3_b[c] = s->phi3_b[c] * (1.0 - s->alpha_b * dt) + s->dB_c[j] * FR_E[c];
         const double dRc = s->dR_c[i] * s->wR_c[j];
-        s->phi1_r[c] += dRc * FZ_M[c];
-        s->phi3_r[c] += dRc * FZ_E[c];
+        s->phi1_r[c] = s->phi1_r[c] * (1.0 - s->alpha_r * dt) + dRc * FZ_M[c];
+        s->phi3_r[c] = s->phi3_r[c] * (1.0 - s->alpha_r * dt) + dRc * FZ_E[c];
         double dsum = s->dB_c[j] + dRc;
         double kappa = 1.0;
         if (Mkeep > 0.0 && dsum > 0.0) {
@@ -1116,11 +1141,11 @@ static void phase3_vertex(orc_sim* s)
                          + KRin(s, KR, KZ, i, j) - KRout(s, KR, KZ, i, j);
             double dKr = m > 0.0 ? kin - 0.5 * (pr * pr + pz * pz) / m : 0.0;
             s->kheat[v] = m > 0.0 ? (s->dK[v] + dKr) / m : 0.0;
-            s->phi2r_b[v] += s->dB_v[j] * (poutRr - pinRr);
-            s->phi2z_b[v] += s->dB_v[j] * (poutRz - pinRz);
+            s->phi2r_b[v] = s->phi2r_b[v] * (1.0 - s->alpha_b * dt) + s->dB_v[j] * (poutRr - pinRr);
+            s->phi2z_b[v] = s->phi2z_b[v] * (1.0 - s->alpha_b * dt) + s->dB_v[j] * (poutRz - pinRz);
             const double dRv = s->dR_v[i] * s->wR_v[j];
-            s->phi2r_r[v] += dRv * (poutZr - pinZr);
-            s->phi2z_r[v] += dRv * (poutZz - pinZz);
+            s->phi2r_r[v] = s->phi2r_r[v] * (1.0 - s->alpha_r * dt) + dRv * (poutZr - pinZr);
+            s->phi2z_r[v] = s->phi2z_r[v] * (1.0 - s->alpha_r * dt) + dRv * (poutZz - pinZz);
             double dsum = s->dB_v[j] + dRv;
             pr = pr - dt * (dsum * pr + s->phi2r_b[v] + s->phi2r_r[v]);
             pz = pz - dt * (dsum * pz + s->phi2z_b[v] + s->phi2z_r[v]);
@@ -1299,7 +1324,7 @@ void orc_conservation(const orc_sim* s, double out[4])
 
 /* Point evaluations exported for the EoS / strength / profile pins. */
 void orc_eos(const orc_material* m, double rho, double I, double* p, double* c2) { material_eos(m, rho, I, p, c2); }
-double orc_yield(const orc_material* m, double p, double D) { return collins_yield(m, p, D); }
+double orc_yield(const orc_material* m, double p, double D, double I, double rho) { return collins_yield(m, p, D, I, rho); }
 double orc_pml_profile(double c, double width, double dx, double y, double R) { return pml_profile(c, width, dx, y, R); }
 
 /* ------------------------------------------------------------------------------------

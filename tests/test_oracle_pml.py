@@ -155,3 +155,30 @@ def test_right_strip_leaves_ejecta_in_void_rows_alone():
     assert sc["mass_out"] == 0.0
     assert sc["mass_discarded"] < 1e-6 * m0
     assert abs(m1 + sc["mass_discarded"] - m0) <= 1e-12 * m0
+
+
+@pytest.mark.parametrize("kappa", [0.0, 0.5])
+def test_auxiliary_relaxation_rate(kappa):
+    """Complex-frequency-shifted stretch 1 + d/(alpha + i omega) (Kuzuoglu & Mittra 1996):
+    each auxiliary decays at alpha = pml_alpha c / delta of its strip.  A basalt column at
+    rest with the bottom strip's phi2 auxiliary preset (a pure momentum source with nothing
+    else to drive it) keeps it at kappa = 0 and lets it decay as exp(-alpha t) otherwise;
+    the momentum it injects feeds back only at second order."""
+    from paper_2403_04267_gb300 import workloads as W
+    pb, dx, nz = 20, 10.0, 60
+    bas = W.basalt()
+    c = math.sqrt(bas["A"] / bas["rho0"])
+    spec = {"grid": W.grid(4, nz, dx, bc_top="wall", pml_b=pb, pml_alpha=kappa), "materials": [bas],
+            "projectile": None, "layers": [dict(mat=0, zlo=0.0, zhi=nz * dx, rho=0.0, I0=0.0, vz=0.0)]}
+    s = O.OracleSim(spec)
+    phi = s.get("phi2z_b")
+    phi0 = 1e-9
+    phi[5, 1] = phi0
+    s.set("phi2z_b", phi)
+    s.step(200)
+    t = s.scalars()["t"]
+    alpha = kappa * c / (pb * dx)
+    ratio = s.get("phi2z_b")[5, 1] / phi0
+    assert abs(ratio - math.exp(-alpha * t)) < 0.02 * max(math.exp(-alpha * t), 0.05)
+    if kappa > 0:
+        assert ratio < 0.9

@@ -76,3 +76,48 @@ def test_rotation_is_objective():
 def test_no_strength_zeroes_the_deviator():
     sv = O.stress_update([1.0, 2.0, 3.0, 0.4], [1, 1, 1, 1, 1], 0.0, 1e7, 1.0, 1e-3)
     assert list(sv) == [0.0, 0.0, 0.0, 0.4]
+
+
+def test_thermal_softening_factor():
+    """Collins et al. (2004) soften the yield strength by tanh(xi (T_m/T - 1)), xi = 1.2,
+    to zero at melting.  Reading: T_m/T = E_iv/I (no temperature in the state).  At
+    I = E_iv/2 the factor is tanh(1.2); it vanishes continuously at E_iv and stays zero above;
+    at I = 0 the strength is untouched."""
+    from paper_2403_04267_gb300 import workloads as W
+    m = W.basalt(strength=True)
+    for p, D in ((0.0, 0.0), (2e8, 0.3), (5e9, 1.0)):
+        Y0 = O.yield_strength(m, p, D)
+        assert O.yield_strength(m, p, D, 0.0) == Y0
+        assert math.isclose(O.yield_strength(m, p, D, 0.5 * m["Eiv"]), Y0 * math.tanh(1.2), rel_tol=1e-14)
+        assert O.yield_strength(m, p, D, m["Eiv"]) == 0.0
+        assert O.yield_strength(m, p, D, 10 * m["Eiv"]) == 0.0
+        assert O.yield_strength(m, p, D, m["Eiv"] * (1 - 1e-9)) < 1e-8 * Y0
+        assert O.yield_strength(m, p, D, 1e-6 * m["Eiv"]) == Y0 * math.tanh(1.2 * (1e6 - 1.0))
+
+
+def test_expansion_weakening_of_strength_and_tension():
+    """Reading: rock expanded below half its reference density is fragmented (no shear
+    strength, no tension); between rho0/2 and rho0 both scale with w = 2 rho/rho0 - 1."""
+    from paper_2403_04267_gb300 import workloads as W
+    coh = 5e6
+    m = W.basalt(strength=True, cohesion=coh)
+    rho0 = m["rho0"]
+    for p, D in ((0.0, 0.0), (1e8, 0.5)):
+        Y0 = O.yield_strength(m, p, D)
+        assert O.yield_strength(m, p, D, 0.0, 1.2 * rho0) == Y0
+        assert math.isclose(O.yield_strength(m, p, D, 0.0, 0.75 * rho0), 0.5 * Y0, rel_tol=1e-14)
+        assert O.yield_strength(m, p, D, 0.0, 0.5 * rho0) == 0.0
+        assert O.yield_strength(m, p, D, 0.0, 1e-7 * rho0) == 0.0
+    # tension cut-off in a cell: (1 - D) p_t w with p_t = -cohesion
+    spec = {"grid": W.grid(4, 4, 10.0), "materials": [m],
+            "layers": [dict(mat=0, zlo=0.0, zhi=40.0, rho=0.0, I0=0.0, vz=0.0)], "projectile": None}
+    s = O.OracleSim(spec)
+    rho = s.get("rho0")
+    rho[0, :] = 0.75 * rho0      # Tillotson p = A mu + B mu^2 = -5 GPa before the cut-off
+    rho[1, :] = 0.4 * rho0
+    rho[2, :] = 1.0 * rho0
+    s.set("rho0", rho)
+    p = s.get("p")
+    assert np.allclose(p[0], -0.5 * coh, rtol=1e-14)
+    assert np.all(p[1] == 0.0)
+    assert np.all(p[2] == 0.0)
