@@ -66,6 +66,7 @@ typedef struct salec_grid {
     int pml_bottom;        /* bottom absorbing strip width, cells (0 = none, < nz) */
     double pml_R;          /* theoretical reflection coefficient R of Eq. 26, 0 < R < 1 */
     double pml_c;          /* wave speed c of Eq. 26; <= 0: max sqrt(A/rho0) of the Tillotson materials */
+    double pml_alpha;      /* relaxation rate of the PML auxiliaries in units of c / (strip width); 0: none */
     double gravity;        /* m/s^2, acting in -z */
     double cfl;            /* Courant number C0 of Eq. 14 */
     double dt_init;        /* "previous" dt that limits the growth of the first step */
@@ -188,7 +189,8 @@ salec_status salec_kernel_times(salec_ctx* ctx, double* avg_ms, int n, int* step
 const char* salec_kernel_name(int k);
 
 /* End time of a run (default: none).  salec_batch_run stops a run once t >= t_end; a
- * run at or past its end time does nothing in a batched step. */
+ * run at or past its end time, or whose status is not 0 (see salec_get_scalars), does
+ * nothing in a batched step. */
 salec_status salec_set_end_time(salec_ctx* ctx, double t_end);
 
 /* Block shapes (threads in r x threads in z) of the six kernels of a step, as 12 ints
@@ -209,8 +211,8 @@ salec_status salec_autotune(salec_ctx* ctx, int trial_steps, int* shapes_out);
  * each run with its own time step and its own end time.  The batch needs one caller-owned
  * device buffer of salec_batch_bytes() bytes (run parameter blocks and work lists).
  * salec_batch_run replays a CUDA graph of `chunk` steps until every run reaches its end
- * time or max_steps steps; salec_batch_poll copies each run's (t, dt, steps, status, t_end)
- * into out[5 r .. 5 r + 4].  Streams: all batch work goes on the stream given here. */
+ * time or fails (status not 0), or max_steps steps; salec_batch_poll copies each run's
+ * (t, dt, steps, status, t_end) into out[5 r .. 5 r + 4].  Streams: all batch work goes on the stream given here. */
 typedef struct salec_batch salec_batch;
 salec_status salec_batch_bytes(salec_ctx* const* runs, int nruns, size_t* bytes);
 salec_status salec_batch_create(salec_ctx* const* runs, int nruns, void* dev_buf, size_t bytes, void* stream,

@@ -431,6 +431,13 @@ salec_status salec_finalize(salec_ctx* ctx)
     }
     if ((pr > 0 || pb > 0) && !(c > 0.0 && g.pml_R > 0.0 && g.pml_R < 1.0))
         return fail(ctx, SALEC_EINVAL, "PML needs a wave speed and 0 < R < 1");
+    if (!(g.pml_alpha >= 0.0)) return fail(ctx, SALEC_EINVAL, "pml_alpha must be >= 0");
+    // auxiliaries relax at alpha = pml_alpha c / delta of their strip (complex-frequency-
+    // shifted stretch 1 + d / (alpha + i omega)), so a static tangential term cannot grow them
+    // without bound
+    const double ab = pb > 0 ? g.pml_alpha * c / (pb * g.dx) : 0.0, ar = pr > 0 ? g.pml_alpha * c / (pr * g.dx) : 0.0;
+    ctx->Pd.alpha_b = ab; ctx->Pd.alpha_r = ar;
+    ctx->Pf.alpha_b = (float)ab; ctx->Pf.alpha_r = (float)ar;
     // cells
     std::vector<double2> fr[kMaxMat];
     for (int m = 0; m < g.nmat; ++m) fr[m].assign(nc, make_double2(0.0, 0.0));
@@ -478,7 +485,7 @@ salec_status salec_finalize(salec_ctx* ctx)
             if (!(f.x > 0.0)) continue;
             double pm, c2;
             eos_eval<double>(P.mat[m], f.y, I[cc], pm, c2);
-            const double pmin = P.mat[m].p_t;
+            const double pmin = P.mat[m].p_t * expansion_weight(P.mat[m], f.y);
             pm = pm < pmin ? pmin : pm;
             phat += f.x * pm; phi += f.x; mass += f.x * f.y;
         }
@@ -1154,7 +1161,8 @@ static salec_status batch_restore_retired(salec_batch* b)
     return any ? batch_build_work(b) : SALEC_OK;
 }
 
-// Advance every run until it reaches its end time (salec_set_end_time), in CUDA-graph
+// Advance every run until it reaches its end time (salec_set_end_time) or fails (status
+// not 0: it then stops where it failed), in CUDA-graph
 // replays of `chunk` steps (the graph is captured once per block-shape set, chunk size and
 // set of runs), polling completion after each replay; at most max_steps steps.  A run that
 // is done does nothing in later steps (its blocks return at once); once done runs hold an
@@ -1185,7 +1193,7 @@ salec_status salec_batch_run(salec_batch* b, int chunk, long max_steps, long* st
         done = 0;
         long tiles_done = 0, tiles_all = 0;
         for (int r = 0; r < n; ++r) {
-            const bool d = poll[5 * r] >= poll[5 * r + 4];
+            const bool d = (poll[5 * r] >= poll[5 * r + 4] || poll[5 * r + 3] != 0.0);
             done += d;
             if (!b->retired[r]) {
                 const long t = tiles_of(b->runs[r]->g.nr, b->runs[r]->g.nz, 3, b->shape[3]);
@@ -1198,7 +1206,7 @@ salec_status salec_batch_run(salec_batch* b, int chunk, long max_steps, long* st
         // (their blocks only return early) and capture the graph again
         if (8 * tiles_done >= tiles_all && tiles_done > 0) {
             for (int r = 0; r < n; ++r)
-                if (poll[5 * r] >= poll[5 * r + 4]) b->retired[r] = 1;
+                if ((poll[5 * r] >= poll[5 * r + 4] || poll[5 * r + 3] != 0.0)) b->retired[r] = 1;
             const salec_status st2 = batch_build_work(b);
             if (st2 != SALEC_OK) return st2;
         }

@@ -114,6 +114,7 @@ struct ParamsT {
     int nr, nz, nmat, pr, pb, bc_top, bc_bottom, any_strength, nblk_cells;
     T dx, dx2, cfl, g, cq, cl, f_min;
     double dxd, cfld, growth, dt_max, dt_min;
+    T alpha_b, alpha_r;     // relaxation rates of the bottom / right strips' auxiliaries (1/s)
     MatT<T> mat[kMaxMat];
     PtrsT<T> p;
 };
@@ -129,7 +130,8 @@ template <> __host__ __device__ inline float t_sqrt<float>(float x) { return sqr
 // Tillotson (1962) equation of state as the paper's SALEc heritage uses it (Sect. 1,
 // "various equations of state"): compressed branch, expanded branch with the two
 // exponential terms, linear blend in I between E_iv and E_cv.  Returns the pressure
-// before the tension cut-off and c^2 = dp/drho + p/rho^2 dp/dI (floored).
+// before the tension cut-off and c^2 = dp/drho + p/rho^2 dp/dI of the branch (in the
+// blend, the blend of the two branches' values), floored.
 // ---------------------------------------------------------------------------------
 template <typename T>
 __host__ __device__ inline void eos_eval(const MatT<T>& m, T rho, T I_in, T& p_out, T& c2_out)
@@ -154,9 +156,11 @@ __host__ __device__ inline void eos_eval(const MatT<T>& m, T rho, T I_in, T& p_o
     const T pc = (m.a + bw) * rho * I + mu * (m.A + m.B * mu);
     const T pc_r = (m.a + bw) * I + two * dw * I + (m.A + two * m.B * mu) * m.inv_rho0;
     const T pc_I = rho * (m.a + bw - dw);
-    T p, p_r, p_I;
+    const T irho2 = irho * irho;
+    T p, c2;
     if (rho >= m.rho0 || I <= m.Eiv) {
-        p = pc; p_r = pc_r; p_I = pc_I;
+        p = pc;
+        c2 = pc_r + pc * irho2 * pc_I;
     } else {
         const T x = m.rho0 * irho - one;               // rho0/rho - 1
         const T x_r = -m.rho0 * irho * irho;           // dx/drho
@@ -170,31 +174,59 @@ __host__ __device__ inline void eos_eval(const MatT<T>& m, T rho, T I_in, T& p_o
         const T pe = m.a * rho * I + tsum * ea;
         const T pe_r = m.a * I + (tb_r + ta_r) * ea - two * m.alpha * x * x_r * tsum * ea;
         const T pe_I = m.a * rho + rho * (bw - dw) * ea;
+        const T ce2 = pe_r + pe * irho2 * pe_I;
         if (I >= m.Ecv) {
-            p = pe; p_r = pe_r; p_I = pe_I;
+            p = pe;
+            c2 = ce2;
         } else {
+            // linear blend in I; the sound speed is the same blend of the two branches' own
+            // sound speeds (the derivative of the blended pressure would add
+            // (p_e - p_c)/(E_cv - E_iv) p/rho^2, unbounded as rho -> 0 when A != B)
             const T we = (I - m.Eiv) * m.inv_dE, wc = (m.Ecv - I) * m.inv_dE;
             p = we * pe + wc * pc;
-            p_r = we * pe_r + wc * pc_r;
-            p_I = we * pe_I + wc * pc_I + (pe - pc) * m.inv_dE;
+            c2 = we * ce2 + wc * (pc_r + pc * irho2 * pc_I);
         }
     }
-    T c2 = p_r + p * irho * irho * p_I;
     if (!(c2 > m.c2_floor)) c2 = m.c2_floor;
     p_out = p;
     c2_out = c2;
 }
 
-// Collins et al. (2004) yield strength blended by damage, at max(p, 0).
+template <typename T> __host__ __device__ inline T t_tanh(T x);
+template <> __host__ __device__ inline double t_tanh<double>(double x) { return tanh(x); }
+template <> __host__ __device__ inline float t_tanh<float>(float x) { return tanhf(x); }
+
+// Rock expanded well below its reference density is fragmented: below rho0 / 2 it carries
+// neither shear strength nor tension, between rho0 / 2 and rho0 both are scaled by
+// w = 2 rho / rho0 - 1 (in dilute ejecta a stress or tension times a step's strain, per unit
+// of so little mass, would send the specific energy to +-1e10 J/kg).
 template <typename T>
-__host__ __device__ inline T yield_eval(const MatT<T>& m, T p_in, T D)
+__host__ __device__ inline T expansion_weight(const MatT<T>& m, T rho)
+{
+    const T w = T(2) * rho * m.inv_rho0 - T(1);
+    return w < T(0) ? T(0) : (w > T(1) ? T(1) : w);
+}
+
+// Collins et al. (2004) yield strength blended by damage, at max(p, 0), with their thermal
+// softening Y tanh(xi (T_m / T - 1)), xi = 1.2, zero at and above melting, and the
+// expansion weight.  The state has no temperature: T_m / T is taken as E_iv / I, the
+// Tillotson incipient-vaporisation energy standing for the melt energy.  Without it a hot,
+// expanded mixture keeps a frictional strength mu p from its vapour pressure and heats
+// itself through its stress work.
+template <typename T>
+__host__ __device__ inline T yield_eval(const MatT<T>& m, T p_in, T D, T I, T rho)
 {
     const T zero = T(0), one = T(1);
     const T p = p_in > zero ? p_in : zero;
     const T Yi = m.Yi0 + m.mui * p / (one + m.mui * p * m.inv_Yspan);
     T Yd = m.Yd0 + m.mud * p;
     Yd = Yd < m.Ydm ? Yd : m.Ydm;
-    const T Y = (one - D) * Yi + D * Yd;
+    T Y = (one - D) * Yi + D * Yd;
+    if (I > zero) {
+        if (!(I < m.Eiv)) return zero;
+        Y *= t_tanh<T>(T(1.2) * (m.Eiv / I - one));
+    }
+    Y *= expansion_weight(m, rho);
     return Y > zero ? Y : zero;
 }
 

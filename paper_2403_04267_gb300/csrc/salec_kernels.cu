@@ -41,6 +41,18 @@ __device__ double block_sum(double v, double* sh)
     return s;
 }
 
+// The right absorbing strip acts on the rows whose reference (far-field) state holds
+// material: the medium whose waves it absorbs.  Above the target the reference is void and
+// damping toward it would remove ejecta, so there it does nothing (cells: row j; vertices:
+// either adjacent cell row).
+template <typename T>
+__device__ __forceinline__ bool strip_row_c(const PtrsT<T>& p, int j) { return pos(p.rho_ref[j]); }
+template <typename T>
+__device__ __forceinline__ bool strip_row_v(const PtrsT<T>& p, int j, int nz)
+{
+    return (j > 0 && pos(p.rho_ref[j - 1])) || (j < nz && pos(p.rho_ref[j]));
+}
+
 // ---------------------------------------------------------------------------------
 // Phase 0: equation of state, artificial viscosity and the Courant time step.
 // ---------------------------------------------------------------------------------
@@ -68,7 +80,7 @@ __device__ __forceinline__ void body_phase0(const ParamsT<T>& P, int bx, int by,
             if (pos(fr.x)) {
                 T pm, c2;
                 eos_eval<T>(P.mat[m], fr.y, Ic, pm, c2);
-                const T pmin = (one - D) * P.mat[m].p_t;
+                const T pmin = (one - D) * P.mat[m].p_t * expansion_weight(P.mat[m], fr.y);
                 pm = pm < pmin ? pmin : pm;
                 phat += fr.x * pm;
                 phi += fr.x;
@@ -207,18 +219,20 @@ __device__ __forceinline__ void body_phase1(const ParamsT<T>& P, int bx, int by,
         const T d = p.dB_v[j];
         typename V::T4 a = p.pb_v[v];
         const T Tr = half * AR * (((Pp[0] + Pp[3]) - Pp[1]) - Pp[2]) + devr_rad;
-        a.z -= dt * d * Tr;
-        a.w -= dt * d * devz_rad;
+        const T rl = one - P.alpha_b * dt;     // relaxation of the auxiliaries
+        a.z = a.z * rl - dt * d * Tr;
+        a.w = a.w * rl - dt * d * devz_rad;
         p.pb_v[v] = a;
         psr += a.z; psz += a.w;
     }
     if (i > nr - P.pr) {
         const int k = j * P.pr + (i - (nr - P.pr + 1));
-        const T d = p.dR_v[i];
+        const T d = strip_row_v(p, j, P.nz) ? p.dR_v[i] : zero;
         typename V::T4 a = p.pr_v[k];
         const T Tz = half * (AZl * (Pp[0] - Pp[3]) + AZr * (Pp[1] - Pp[2])) + devz_ver;
-        a.z -= dt * d * devr_ver;
-        a.w -= dt * d * Tz;
+        const T rl = one - P.alpha_r * dt;
+        a.z = a.z * rl - dt * d * devr_ver;
+        a.w = a.w * rl - dt * d * Tz;
         p.pr_v[k] = a;
         psr += a.z; psz += a.w;
     }
@@ -298,14 +312,14 @@ __device__ __forceinline__ void body_phase2(const ParamsT<T>& P, int bx, int by,
     T psi2 = zero;
     if (j < P.pb) {
         T a = p.pb_psi2[c];
-        a -= dt * p.dB_c[j] * Pi_rad;
+        a = a * (one - P.alpha_b * dt) - dt * p.dB_c[j] * Pi_rad;
         p.pb_psi2[c] = a;
         psi2 += a;
     }
     if (i >= nr - P.pr) {
         const int k = j * P.pr + (i - (nr - P.pr));
         T a = p.pr_psi2[k];
-        a -= dt * p.dR_c[i] * Pi_ver;
+        a = a * (one - P.alpha_r * dt) - dt * (strip_row_c(p, j) ? p.dR_c[i] : zero) * Pi_ver;
         p.pr_psi2[k] = a;
         psi2 += a;
     }
@@ -314,16 +328,10 @@ __device__ __forceinline__ void body_phase2(const ParamsT<T>& P, int bx, int by,
     // the specific internal energy is accumulated in FP64 in every form
     p.IL[c] = pos(M) ? Ic + double(dE / M) : Ic;
     p.VL[c] = VLc;
-    // volume partition: compression closes void first; expansion shared pro rata with void
-    T Vvoid = (one - phi) * Vc;
-    Vvoid = Vvoid < zero ? zero : Vvoid;
-    T dVmat;
-    if (dV < zero) {
-        const T dVvoid = dV > -Vvoid ? dV : -Vvoid;
-        dVmat = dV - dVvoid;
-    } else {
-        dVmat = phi * dV;
-    }
+    // volume partition: matter and void share every volume change in proportion to their
+    // fractions (equal strain), so each material's work -p_m dV_m adds up to the -P dV the
+    // energy update charges
+    const T dVmat = phi * dV;
     bool bad = false;
     T G = zero, Y = zero, iepsf = zero;
 #pragma unroll
@@ -339,7 +347,7 @@ __device__ __forceinline__ void body_phase2(const ParamsT<T>& P, int bx, int by,
                 const MatT<T>& mm = P.mat[m];
                 const T pb = p.pbphi[c].x;
                 G += fr.x * mm.G;
-                Y += fr.x * yield_eval<T>(mm, pb, D);
+                Y += fr.x * yield_eval<T>(mm, pb, D, T(Ic), fr.y);
                 T ef = mm.B_dam * (pb - mm.p_bd);
                 ef = ef < mm.eps_fb ? mm.eps_fb : ef;
                 iepsf += fr.x / ef;
@@ -550,17 +558,19 @@ __device__ __forceinline__ void body_phase3a(const ParamsT<T>& P, int bx, int by
             if (inB) {
                 const T d = p.dB_c[j];
                 typename V::T2 a = p.pb_c[c];
-                a.x += d * FRm;
-                a.y += d * FRe;
+                const T rl = one - P.alpha_b * dt;
+                a.x = a.x * rl + d * FRm;
+                a.y = a.y * rl + d * FRe;
                 p.pb_c[c] = a;
                 dsum += d; phi1 += a.x; phi3 += a.y;
             }
             if (inR) {
                 const int k = j * P.pr + (i - (nr - P.pr));
-                const T d = p.dR_c[i];
+                const T d = strip_row_c(p, j) ? p.dR_c[i] : zero;
                 typename V::T2 a = p.pr_c[k];
-                a.x += d * FZm;
-                a.y += d * FZe;
+                const T rl = one - P.alpha_r * dt;
+                a.x = a.x * rl + d * FZm;
+                a.y = a.y * rl + d * FZe;
                 p.pr_c[k] = a;
                 dsum += d; phi1 += a.x; phi3 += a.y;
             }
@@ -688,17 +698,19 @@ __device__ __forceinline__ void body_phase3b(const ParamsT<T>& P, int bx, int by
         if (j < P.pb) {
             const T d = p.dB_v[j];
             typename V::T4 a = p.pb_v[v];
-            a.x += d * (outRr - inRr);
-            a.y += d * (outRz - inRz);
+            const T rl = one - P.alpha_b * dt;
+            a.x = a.x * rl + d * (outRr - inRr);
+            a.y = a.y * rl + d * (outRz - inRz);
             p.pb_v[v] = a;
             dsum += d; a2r += a.x; a2z += a.y;
         }
         if (i > nr - P.pr) {
             const int k = j * P.pr + (i - (nr - P.pr + 1));
-            const T d = p.dR_v[i];
+            const T d = strip_row_v(p, j, P.nz) ? p.dR_v[i] : zero;
             typename V::T4 a = p.pr_v[k];
-            a.x += d * (outZr - inZr);
-            a.y += d * (outZz - inZz);
+            const T rl = one - P.alpha_r * dt;
+            a.x = a.x * rl + d * (outZr - inZr);
+            a.y = a.y * rl + d * (outZz - inZz);
             p.pr_v[k] = a;
             dsum += d; a2r += a.x; a2z += a.y;
         }
@@ -787,14 +799,15 @@ __global__ void __launch_bounds__(kMaxThreads) k_phase3b(ParamsT<T> P) { body_ph
 template <typename T, int NM>
 __global__ void __launch_bounds__(kMaxThreads) k_phase3c(ParamsT<T> P) { body_phase3c<T, NM>(P, blockIdx.x, blockIdx.y, gridDim.x, gridDim.y); }
 
-// phase 0 decides for the whole step: a run at or past its end time does nothing
+// phase 0 decides for the whole step: a run at or past its end time, or one whose status
+// reports a failure (non-positive volume or density, NaN, dt below dt_min), does nothing
 template <typename T, int NM, bool STR>
 __global__ void __launch_bounds__(kMaxThreads) kb_phase0(const ParamsT<T>* __restrict__ runs, const BatchTile* __restrict__ work)
 {
     const BatchTile w = work[blockIdx.x];
     const ParamsT<T>& P = runs[w.run];
     DevScalars* s = P.p.scal;
-    if (!(s->t < s->t_end)) {
+    if (!(s->t < s->t_end) || s->status != 0) {
         if (w.bx == 0 && w.by == 0 && threadIdx.x == 0 && threadIdx.y == 0) s->active = 0;
         return;
     }
@@ -843,7 +856,7 @@ __global__ void __launch_bounds__(kMaxThreads) k_pressure(ParamsT<T> P, double* 
         if (fr.x > T(0)) {
             T pm, c2;
             eos_eval<T>(P.mat[m], fr.y, T(p.I[c]), pm, c2);
-            const T pmin = (T(1) - D) * P.mat[m].p_t;
+            const T pmin = (T(1) - D) * P.mat[m].p_t * expansion_weight(P.mat[m], fr.y);
             pm = pm < pmin ? pmin : pm;
             phat += fr.x * pm;
             phi += fr.x;

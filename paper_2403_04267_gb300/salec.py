@@ -34,7 +34,7 @@ VERTEX_FIELDS = {"vr", "vz", "phi2r_b", "phi2z_b", "psi1r_b", "psi1z_b",
 class salec_grid(C.Structure):
     _fields_ = [
         ("nr", C.c_int), ("nz", C.c_int), ("nmat", C.c_int), ("dx", C.c_double),
-        ("pml_right", C.c_int), ("pml_bottom", C.c_int), ("pml_R", C.c_double), ("pml_c", C.c_double),
+        ("pml_right", C.c_int), ("pml_bottom", C.c_int), ("pml_R", C.c_double), ("pml_c", C.c_double), ("pml_alpha", C.c_double),
         ("gravity", C.c_double), ("cfl", C.c_double), ("dt_init", C.c_double), ("dt_max", C.c_double),
         ("dt_growth", C.c_double), ("dt_min", C.c_double), ("av_cq", C.c_double), ("av_cl", C.c_double),
         ("f_min", C.c_double), ("bc_top", C.c_int), ("bc_bottom", C.c_int),
@@ -153,7 +153,7 @@ def make_grid(d: dict, nmat: int) -> salec_grid:
     g = salec_grid()
     g.nr, g.nz, g.nmat, g.dx = int(d["nr"]), int(d["nz"]), int(nmat), float(d["dx"])
     g.pml_right, g.pml_bottom = int(d.get("pml_r", 0)), int(d.get("pml_b", 0))
-    for k in ("pml_R", "pml_c", "gravity", "cfl", "dt_init", "dt_max", "dt_growth", "dt_min",
+    for k in ("pml_R", "pml_c", "pml_alpha", "gravity", "cfl", "dt_init", "dt_max", "dt_growth", "dt_min",
               "av_cq", "av_cl", "f_min"):
         setattr(g, k, float(d.get(k, 0.0)))
     g.bc_top = _TOP[d.get("bc_top", "outflow")]

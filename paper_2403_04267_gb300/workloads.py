@@ -47,7 +47,7 @@ def ideal_gas(gamma: float = 1.4, rho0: float = 1.0) -> dict:
 # --- grid ----------------------------------------------------------------------------
 
 def grid(nr: int, nz: int, dx: float, **kw) -> dict:
-    g = dict(nr=int(nr), nz=int(nz), dx=float(dx), pml_r=0, pml_b=0, pml_R=0.01, pml_c=0.0,
+    g = dict(nr=int(nr), nz=int(nz), dx=float(dx), pml_r=0, pml_b=0, pml_R=0.01, pml_c=0.0, pml_alpha=0.0,
              gravity=0.0, cfl=0.4, dt_init=1e30, dt_max=1e30, dt_growth=1.2, dt_min=0.0,
              av_cq=1.0, av_cl=0.25, f_min=1e-6, bc_top="outflow", bc_bottom="noslip")
     g.update(kw)
@@ -58,7 +58,10 @@ def impact(nr: int, nz: int, dx: float, target: dict, projectile_mat: dict | Non
            radius_cells: float, v_imp: float, surface_row: int, pml: int, gravity: float = 0.0,
            **gkw) -> dict:
     """Half-space target with its surface at row `surface_row`; a sphere of radius
-    `radius_cells` cells on the axis, tangent to the surface, moving down at `v_imp`."""
+    `radius_cells` cells on the axis, tangent to the surface, moving down at `v_imp`.
+    The PML auxiliaries relax at 0.1 c / delta (complex-frequency-shifted stretch): runs to
+    tens of seconds in a strong target otherwise drift."""
+    gkw.setdefault("pml_alpha", 0.1)
     mats = [target] if projectile_mat is None else [target, projectile_mat]
     pmat = 0 if projectile_mat is None else 1
     zs = surface_row * dx
@@ -148,8 +151,10 @@ def batched_run(draw: dict, n_override: int | None = None) -> dict:
     n = n_override or draw["n"]
     tgt = basalt(strength=True, cohesion=draw["cohesion"], friction=draw["friction"])
     proj = iron() if draw["projectile"] == "iron" else basalt()
+    # dt_min: a healthy run of this family never steps below ~1e-4 s (25 m cells, speeds
+    # below 40 km/s); 1e-6 s flags a failed run so that a batch stops it
     w = impact(n, n, 25.0, tgt, proj, draw["radius_cells"], draw["v_imp"], int(round(0.7 * n)),
-               40, gravity=1.62)
+               40, gravity=1.62, dt_min=1e-6)
     w["name"] = f"batched_seed{draw['seed']}"
     w["t_end"] = 20.0
     return w
