@@ -1,0 +1,368 @@
+"""Python binding of the crater-surrogate MLP (include/salec_mlp.h) and its host-side
+preparation of inputs and targets.
+
+Every forward pass, gradient and Adam step runs in the CUDA library; this module converts
+arguments, owns the device buffer (PyTorch) and maps impact parameters and crater outputs to
+the network's normalised inputs and outputs.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import math
+
+import numpy as np
+
+from .salec import SALEC_OK, SalecError, load
+
+N_IN, N_OUT, N_PROFILE = 5, 66, 64
+DIMS = (N_IN, 256, 256, 256, 256, N_OUT)
+
+
+def n_params() -> int:
+    return int(load().salec_mlp_n_params())
+
+
+class MLP:
+    """5 -> 4 x 256 GELU -> 66 network with FP32 master parameters, BF16 tensor-core
+    operands and Adam state on one device buffer."""
+
+    def __init__(self, batch_max: int, device=None, stream=None):
+        import torch
+        L = load()
+        self.device = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
+        self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        nb = C.c_size_t()
+        if L.salec_mlp_bytes(int(batch_max), C.byref(nb)) != SALEC_OK:
+            raise SalecError(1, "bad batch_max")
+        self.buf = torch.empty(nb.value, dtype=torch.uint8, device=self.device)
+        h = C.c_void_p()
+        st = L.salec_mlp_create(int(batch_max), C.c_void_p(self.buf.data_ptr()), nb.value,
+                                C.c_void_p(self.stream.cuda_stream), C.byref(h))
+        if st != SALEC_OK:
+            raise SalecError(st, "salec_mlp_create failed")
+        self._h = h
+        self.batch_max = int(batch_max)
+        self.P = n_params()
+
+    def _check(self, st):
+        if st != SALEC_OK:
+            raise SalecError(st, load().salec_mlp_last_error(self._h).decode())
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h:
+            load().salec_mlp_destroy(h)
+            self._h = None
+
+    def set_params(self, theta) -> None:
+        a = np.ascontiguousarray(theta, dtype=np.float32)
+        assert a.size == self.P
+        self._check(load().salec_mlp_set_params(self._h, a.ctypes.data_as(C.c_void_p)))
+
+    def get_params(self) -> np.ndarray:
+        a = np.empty(self.P, dtype=np.float32)
+        self._check(load().salec_mlp_get_params(self._h, a.ctypes.data_as(C.c_void_p)))
+        return a
+
+    @staticmethod
+    def _dev(x, cols):
+        import torch
+        assert isinstance(x, torch.Tensor) and x.is_cuda and x.dtype == torch.float32 and x.is_contiguous()
+        assert x.dim() == 2 and x.shape[1] == cols
+        return x
+
+    def forward(self, x, out=None):
+        import torch
+        x = self._dev(x, N_IN)
+        y = out if out is not None else torch.empty((x.shape[0], N_OUT), dtype=torch.float32, device=x.device)
+        self._check(load().salec_mlp_forward(self._h, C.c_void_p(x.data_ptr()), int(x.shape[0]),
+                                             C.c_void_p(y.data_ptr())))
+        return y
+
+    def gradient(self, x, t):
+        """(loss, gradient) for inputs x and targets t (device tensors)."""
+        import torch
+        x, t = self._dev(x, N_IN), self._dev(t, N_OUT)
+        g = torch.empty(self.P, dtype=torch.float32, device=x.device)
+        loss = C.c_double()
+        self._check(load().salec_mlp_gradient(self._h, C.c_void_p(x.data_ptr()), C.c_void_p(t.data_ptr()),
+                                              int(x.shape[0]), C.c_void_p(g.data_ptr()), C.byref(loss)))
+        return loss.value, g
+
+    def train_step(self, x, t, lr: float, beta1: float = 0.9, beta2: float = 0.999, eps: float = 1e-8,
+                   sse=None) -> None:
+        ptr = C.c_void_p(sse.data_ptr()) if sse is not None else None
+        self._check(load().salec_mlp_train_step(self._h, C.c_void_p(x.data_ptr()), C.c_void_p(t.data_ptr()),
+                                                int(x.shape[0]), float(lr), float(beta1), float(beta2),
+                                                float(eps), ptr))
+
+    def check(self) -> None:
+        self._check(load().salec_mlp_check(self._h))
+
+
+def gemm_bf16(M, N, K, A, a_strides, B, b_strides, C_out, ldc, stream=None) -> None:
+    """C_out[m*ldc + n] = sum_k A[m*a_sm + k*a_sk] B[n*b_sn + k*b_sk] on the tensor cores
+    (A, B: BF16 device tensors; C_out: FP32 device tensor; strides in elements)."""
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    st = load().salec_gemm_bf16(int(M), int(N), int(K), C.c_void_p(A.data_ptr()), int(a_strides[0]),
+                                int(a_strides[1]), C.c_void_p(B.data_ptr()), int(b_strides[0]), int(b_strides[1]),
+                                C.c_void_p(C_out.data_ptr()), int(ldc), C.c_void_p(s.cuda_stream))
+    if st != SALEC_OK:
+        raise SalecError(st, "salec_gemm_bf16 failed")
+
+
+# --- inputs and outputs ----------------------------------------------------------------
+
+# impact-parameter ranges of the sampled distribution
+V_RANGE = (6e3, 20e3)
+RADIUS_RANGE = (8.0, 32.0)
+COHESION_RANGE = (1e6, 100e6)
+FRICTION_RANGE = (0.4, 0.8)
+DENSITIES = (2700.0, 7800.0)
+DEPTH_SCALE = 1000.0          # metres per unit of the network's outputs
+
+
+def _unit(x, lo, hi):
+    return 2.0 * (x - lo) / (hi - lo) - 1.0
+
+
+def features(draw: dict) -> np.ndarray:
+    """Normalised inputs in [-1, 1]: velocity, projectile radius (cells), projectile
+    density, log cohesion, friction coefficient."""
+    rho = DENSITIES[1] if draw["projectile"] == "iron" else DENSITIES[0]
+    return np.array([
+        _unit(draw["v_imp"], *V_RANGE),
+        _unit(draw["radius_cells"], *RADIUS_RANGE),
+        _unit(rho, *DENSITIES),
+        _unit(math.log(draw["cohesion"]), math.log(COHESION_RANGE[0]), math.log(COHESION_RANGE[1])),
+        _unit(draw["friction"], *FRICTION_RANGE),
+    ], dtype=np.float32)
+
+
+def targets(profile: np.ndarray, transient_depth: float, diameter: float) -> np.ndarray:
+    """66 outputs: the 64-point depth profile, the transient depth and the diameter, in
+    units of DEPTH_SCALE metres."""
+    out = np.empty(N_OUT, dtype=np.float32)
+    out[:N_PROFILE] = np.asarray(profile, dtype=np.float64) / DEPTH_SCALE
+    out[N_PROFILE] = transient_depth / DEPTH_SCALE
+    out[N_PROFILE + 1] = diameter / DEPTH_SCALE
+    return out
+
+
+def outputs_to_crater(y: np.ndarray) -> dict:
+    y = np.asarray(y, dtype=np.float64) * DEPTH_SCALE
+    return {"profile": y[..., :N_PROFILE], "transient_depth": y[..., N_PROFILE], "diameter": y[..., N_PROFILE + 1]}
+
+
+# --- training data from the batched solver ----------------------------------------------
+
+def simulate(draws, n: int = 400, t_end: float = 20.0, chunk: int = 100, precision: str = "fp32mix",
+             autotune: bool = True, log=None) -> dict:
+    """Runs the draws (impact parameters of the sampled distribution) on n x n grids as one
+    batch to t_end and returns their crater outputs: the 64-point depth profile and the
+    diameter at t_end, and the transient depth (largest depth on the axis over the run,
+    sampled after every `chunk` steps).  ``pml_reached`` flags runs whose crater rim reaches
+    the absorbing strip."""
+    import time
+    from . import salec, workloads as W
+    specs = [W.batched_run(d, n) for d in draws]
+    sims = [salec.Sim(sp, precision=precision) for sp in specs]
+    for s in sims:
+        s.set_end_time(t_end)
+    batch = salec.Batch(sims)
+    t0 = time.perf_counter()
+    if autotune:
+        batch.autotune(trial_steps=2)
+    R = len(sims)
+    transient = np.zeros(R)
+    total_steps = 0
+    while True:
+        steps, done = batch.run(chunk=chunk, max_steps=chunk)
+        total_steps += steps
+        for k, (s, sp) in enumerate(zip(sims, specs)):
+            c = s.crater(sp["z_surface"], 0)
+            transient[k] = max(transient[k], c["depth"])
+        if log:
+            log(f"  {total_steps} steps, {done}/{R} runs done, {time.perf_counter() - t0:.1f} s")
+        if done == R:
+            break
+    wall = time.perf_counter() - t0
+    prof = np.zeros((R, N_PROFILE))
+    diam = np.zeros(R)
+    reached = np.zeros(R, dtype=bool)
+    polled = batch.poll()
+    for k, (s, sp) in enumerate(zip(sims, specs)):
+        c = s.crater(sp["z_surface"], N_PROFILE)
+        prof[k] = c["profile"]
+        diam[k] = c["diameter"]
+        transient[k] = max(transient[k], c["depth"])
+        g = sp["grid"]
+        reached[k] = 0.5 * c["diameter"] >= (g["nr"] - g["pml_r"]) * g["dx"]
+    return {"X": np.stack([features(d) for d in draws]),
+            "T": np.stack([targets(prof[k], transient[k], diam[k]) for k in range(R)]),
+            "profile": prof, "transient_depth": transient, "diameter": diam, "pml_reached": reached,
+            "steps": polled[:, 2].copy(), "status": polled[:, 3].copy(), "wall_s": wall, "n": n,
+            "seeds": np.array([d["seed"] for d in draws])}
+
+
+def generate(seeds, n: int = 400, group: int = 1024, log=None, partial=None, **kw) -> dict:
+    """simulate() over seed groups of `group` runs, concatenated.  With `partial` (a path
+    prefix) each group is also saved as it completes."""
+    from . import workloads as W
+    parts = []
+    seeds = list(seeds)
+    for g0 in range(0, len(seeds), group):
+        draws = [W.batched_draw(s) for s in seeds[g0:g0 + group]]
+        if log:
+            log(f"group {g0 // group}: {len(draws)} runs at {n} x {n}")
+        parts.append(simulate(draws, n=n, log=log, **kw))
+        if partial:
+            np.savez_compressed(f"{partial}_{g0 // group}.npz", **{k: np.asarray(v) for k, v in parts[-1].items()})
+    out = {}
+    for key in parts[0]:
+        v = [p[key] for p in parts]
+        out[key] = np.concatenate(v) if isinstance(v[0], np.ndarray) else (sum(v) if key == "wall_s" else v[0])
+    return out
+
+
+def train(X, T, steps: int = 4000, lr: float = 2e-3, seed: int = 0, batch_max: int = 4096, log=None) -> "MLP":
+    """Full-batch Adam on (X, T) with a cosine learning-rate decay; returns the network."""
+    import torch
+    from . import workloads as W
+    net = MLP(max(batch_max, len(X)))
+    net.set_params(W.mlp_init(seed).astype(np.float32))
+    Xd = torch.from_numpy(np.ascontiguousarray(X, dtype=np.float32)).cuda()
+    Td = torch.from_numpy(np.ascontiguousarray(T, dtype=np.float32)).cuda()
+    for s in range(steps):
+        a = lr * 0.5 * (1.0 + math.cos(math.pi * s / steps))
+        net.train_step(Xd, Td, a)
+        if log and (s % 1000 == 0 or s == steps - 1):
+            loss, _ = net.gradient(Xd, Td)
+            log(f"  step {s}: loss {loss:.3e}")
+    net.check()
+    return net
+
+
+# weights of the outputs in the squared-error loss: transient depth and diameter, the two
+# numbers a cratering study reads, count 16x a profile point (targets scaled by 4)
+OUT_WEIGHT = np.ones(N_OUT, dtype=np.float32)
+OUT_WEIGHT[N_PROFILE:] = 4.0
+
+
+class Ensemble:
+    """Networks trained from different initial parameters on the same data.  Their mean is
+    the prediction; their spread in transient depth and diameter decides whether a
+    prediction is trusted or the draw goes to the solver."""
+
+    def __init__(self, X, T, members: int = 4, steps: int = 4000, lr: float = 2e-3, log=None):
+        Tw = np.asarray(T, dtype=np.float32) * OUT_WEIGHT
+        self.nets = [train(X, Tw, steps=steps, lr=lr, seed=1000 + k, log=log) for k in range(members)]
+
+    def predict(self, X):
+        """(mean outputs, relative spread of transient depth, of diameter) for inputs X."""
+        import torch
+        Xd = torch.from_numpy(np.ascontiguousarray(X, dtype=np.float32)).cuda()
+        outs = [net.forward(Xd) for net in self.nets]
+        for net in self.nets:
+            net.stream.synchronize()
+        ys = np.stack([y.cpu().numpy().astype(np.float64) / OUT_WEIGHT for y in outs])
+        mean = ys.mean(axis=0)
+        sd = np.max(np.abs(ys - mean), axis=0)
+        rel_d = sd[:, N_PROFILE] / np.maximum(np.abs(mean[:, N_PROFILE]), 1e-9)
+        rel_D = sd[:, N_PROFILE + 1] / np.maximum(np.abs(mean[:, N_PROFILE + 1]), 1e-9)
+        return mean, rel_d, rel_D
+
+
+def crater_errors(Y, T):
+    """Relative errors of transient depth and diameter (network outputs Y vs solver T)."""
+    Y, T = np.asarray(Y, dtype=np.float64), np.asarray(T, dtype=np.float64)
+    ed = np.abs(Y[:, N_PROFILE] - T[:, N_PROFILE]) / np.maximum(np.abs(T[:, N_PROFILE]), 1e-9)
+    eD = np.abs(Y[:, N_PROFILE + 1] - T[:, N_PROFILE + 1]) / np.maximum(np.abs(T[:, N_PROFILE + 1]), 1e-9)
+    return ed, eD
+
+
+def calibrate_gate(ens: "Ensemble", Xv, Tv, tol: float = 0.02, target: float = 0.95) -> float:
+    """Largest spread threshold tau such that, on validation draws whose ensemble spread in
+    transient depth and diameter is below tau, at least `target` of the predictions have
+    both errors within `tol` of the solver.  Returns 0 when no threshold qualifies."""
+    Y, sd, sD = ens.predict(Xv)
+    ed, eD = crater_errors(Y, Tv)
+    good = (ed <= tol) & (eD <= tol)
+    spread = np.maximum(sd, sD)
+    best = 0.0
+    for tau in np.sort(spread):
+        acc = spread <= tau
+        if acc.sum() >= 10 and good[acc].mean() >= target:
+            best = float(tau)
+    return best
+
+
+def gain_report(ens: "Ensemble", tau: float, Xh, Th, solver_s_per_run: float, tol: float = 0.02) -> dict:
+    """Surrogate with the solver as fallback on held-out draws: the ensemble answers the
+    draws whose spread is below tau, the solver the rest.  Returns the accepted fraction,
+    the accepted predictions' errors against the solver, and runs/hour with and without
+    the surrogate (the solver's cost per run measured by the caller)."""
+    import time
+    import torch
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    Y, sd, sD = ens.predict(Xh)
+    torch.cuda.synchronize()
+    t_inf = time.perf_counter() - t0
+    ed, eD = crater_errors(Y, Th)
+    acc = np.maximum(sd, sD) <= tau
+    n = len(Xh)
+    n_fallback = int((~acc).sum())
+    t_total = t_inf + n_fallback * solver_s_per_run
+    within = (ed <= tol) & (eD <= tol)
+    return {
+        "draws": n, "accepted": int(acc.sum()), "fallback": n_fallback, "gate_tau": tau,
+        "accepted_within_tol": float(within[acc].mean()) if acc.any() else None,
+        "accepted_depth_err_max": float(ed[acc].max()) if acc.any() else None,
+        "accepted_diameter_err_max": float(eD[acc].max()) if acc.any() else None,
+        "all_within_tol_fraction": float(within.mean()),
+        "depth_err_median_all": float(np.median(ed)), "diameter_err_median_all": float(np.median(eD)),
+        "inference_s": t_inf,
+        "runs_per_hour_solver": 3600.0 / solver_s_per_run,
+        "runs_per_hour_with_surrogate": n * 3600.0 / t_total,
+    }
+
+
+# --- command line: training data and training ---------------------------------------------
+
+TRAIN_SEEDS = range(100000, 104096)      # 4096 training draws
+HELDOUT_SEEDS = range(200000, 200256)    # 256 held-out draws (disjoint)
+
+
+def _main(argv=None):
+    import argparse
+    import sys
+    import time
+    ap = argparse.ArgumentParser(description="crater-surrogate training data and training")
+    sub = ap.add_subparsers(dest="cmd", required=True)
+    g = sub.add_parser("generate", help="run the batched solver on the training and held-out draws")
+    g.add_argument("--out", required=True)
+    g.add_argument("--n", type=int, default=400)
+    g.add_argument("--train", type=int, default=len(TRAIN_SEEDS))
+    g.add_argument("--heldout", type=int, default=len(HELDOUT_SEEDS))
+    g.add_argument("--group", type=int, default=1024)
+    g.add_argument("--t-end", type=float, default=20.0)
+    a = ap.parse_args(argv)
+
+    def log(msg):
+        print(msg, flush=True, file=sys.stderr)
+
+    if a.cmd == "generate":
+        t0 = time.perf_counter()
+        tr = generate(list(TRAIN_SEEDS)[:a.train], n=a.n, group=a.group, t_end=a.t_end, log=log,
+                      partial=a.out + ".train")
+        ho = generate(list(HELDOUT_SEEDS)[:a.heldout], n=a.n, group=a.group, t_end=a.t_end, log=log,
+                      partial=a.out + ".heldout")
+        np.savez_compressed(a.out, **{f"train_{k}": np.asarray(v) for k, v in tr.items()},
+                            **{f"heldout_{k}": np.asarray(v) for k, v in ho.items()})
+        log(f"done in {time.perf_counter() - t0:.1f} s")
+
+
+if __name__ == "__main__":
+    _main()

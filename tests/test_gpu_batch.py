@@ -113,3 +113,26 @@ def test_single_run_autotune_keeps_fields():
     assert len(shapes) == 6 and all(x % 32 == 0 for x, _ in shapes)
     b.step(21)
     _same(a, b, "fp64")
+
+
+def test_finished_runs_leave_and_rejoin_the_batch():
+    """After a run reaches its end time the batch drops it from its work lists; moving its
+    end time later brings it back on the next salec_batch_run, and it continues exactly as
+    the same run stepped alone."""
+    specs = _specs(3, seed0=300)
+    runs = [salec.Sim(s, precision="fp32mix") for s in specs]
+    probe = salec.Sim(specs[0], precision="fp32mix")
+    probe.step(12)
+    t12 = probe.scalars()["t"]
+    probe.step(10)
+    sc = probe.scalars()
+    runs[0].set_end_time(t12 - 1e-12)
+    for r in runs[1:]:
+        r.set_end_time(1e9)
+    b = salec.Batch(runs)
+    b.run(chunk=4, max_steps=40)
+    assert runs[0].scalars()["nstep"] == 12
+    runs[0].set_end_time(sc["t"] - 0.5 * sc["dt"])
+    steps, done = b.run(chunk=4, max_steps=40)
+    assert runs[0].scalars()["nstep"] == 22
+    _same(runs[0], probe, "fp32mix")
