@@ -102,9 +102,13 @@ static double* zalloc(size_t n) { return (double*)calloc(n ? n : 1, sizeof(doubl
  * limits a+b and a, ideal-gas limit at vanishing density, continuity at rho0 and at the
  * blend ends, derivatives against central differences).
  * ------------------------------------------------------------------------------------ */
-static void tillotson(const orc_material* m, double rho, double I_in, double* p_out, double* c2_out)
+static void tillotson(const orc_material* m, double rho_in, double I_in, double* p_out, double* c2_out)
 {
     double I = I_in > 0.0 ? I_in : 0.0;
+    /* evaluated at no less than 1e-12 rho0 (reading): below it the pressure is ~a rho I,
+       negligible, and c^2 no longer depends on rho; the floor keeps the rho^-2 terms finite
+       in FP32 as well */
+    double rho = rho_in > 1e-12 * m->rho0 ? rho_in : 1e-12 * m->rho0;
     double eta = rho / m->rho0;
     double mu = eta - 1.0;
     double w0 = I / (m->E0 * eta * eta) + 1.0;

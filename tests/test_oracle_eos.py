@@ -124,3 +124,15 @@ def test_blend_sound_speed_is_blend_of_branch_sound_speeds(m, eta):
         ca = O.eos(m, rho, Ie * (1 + 1e-10))[1]
         cb = O.eos(m, rho, Ie * (1 - 1e-10))[1]
         assert abs(ca - cb) <= 1e-6 * max(ca, cb)
+
+
+@pytest.mark.parametrize("m", [BAS, IRON])
+def test_density_floor(m):
+    """Reading: the Tillotson form is evaluated at no less than 1e-12 rho0; there p -> a rho I
+    and c^2 -> a (1 + a) I (pinned above), so the floor changes nothing but keeps the
+    rho^-2 terms finite."""
+    I = 2 * m["Ecv"]
+    lo = O.eos(m, 1e-12 * m["rho0"], I)
+    assert O.eos(m, 1e-20 * m["rho0"], I) == lo
+    assert O.eos(m, 0.0, I) == lo
+    assert math.isclose(lo[1], m["a"] * (1 + m["a"]) * I, rel_tol=1e-9)
