@@ -149,6 +149,205 @@ def _cpu_baseline(spec, steps):
                       f"(serial C, -O2; set-up {t1 - t0:.1f} s excluded)", "seconds": round(t2 - t1, 2)}
 
 
+def shard(n_units: int, rank: int, ws: int) -> list:
+    """The units (runs, seeds) rank `rank` of `ws` processes: r, r + ws, r + 2 ws, ...  No
+    unit is shared, none is left out, and no data-path exchange is needed."""
+    return list(range(rank, n_units, ws))
+
+
+def job_reduce(vals_max, vals_sum, device="cpu"):
+    """Whole-job figures over ranks: the max of times, the sum of counts (one all_reduce each;
+    a no-op in a single process)."""
+    import torch
+    import torch.distributed as dist
+    mx = torch.tensor(list(vals_max), dtype=torch.float64, device=device)
+    sm = torch.tensor(list(vals_sum), dtype=torch.float64, device=device)
+    if dist.is_available() and dist.is_initialized() and dist.get_world_size() > 1:
+        dist.all_reduce(mx, op=dist.ReduceOp.MAX)
+        dist.all_reduce(sm, op=dist.ReduceOp.SUM)
+    return mx.tolist(), sm.tolist()
+
+
+def _batched(args, rank, ws):
+    """Batched impacts of the seeded distribution (rank r takes seeds r, r + ws, ...), FP32-mix,
+    each to t_end: one batch, autotuned block shapes, CUDA-graph chunks.  A run whose status
+    reports a failure (a crater or projectile reaching an absorbing strip can drive a cell
+    to negative density) stops where it failed and counts as finished.  runs/hour over the
+    whole job; the plain FP64 solver, one run at a time, on the first few draws that finished
+    cleanly gives the reference runs/hour and the crater depth and diameter that the batch
+    is checked against (the FP64 GPU solver matches the FP64 oracle to 1e-9 and stands in
+    for it here)."""
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+    from paper_2403_04267_gb300 import salec, workloads as W
+    seeds = shard(args.batch_runs, rank, ws)
+    specs = [W.batched_run(W.batched_draw(sd)) for sd in seeds]
+    for sp in specs:
+        sp["t_end"] = args.batch_t_end
+    t0 = time.perf_counter()
+    sims = [salec.Sim(sp, precision="fp32mix") for sp in specs]
+    for sm in sims:
+        sm.set_end_time(args.batch_t_end)
+    batch = salec.Batch(sims)
+    setup_s = time.perf_counter() - t0
+    cells = sum(sp["grid"]["nr"] * sp["grid"]["nz"] for sp in specs)
+    torch.cuda.synchronize()
+    if ws > 1:
+        dist.barrier()
+    t0 = time.perf_counter()
+    shapes = batch.autotune(trial_steps=2)
+    steps, done = 0, 0
+    while done < len(sims) and time.perf_counter() - t0 < args.batch_max_s:
+        s1, done = batch.run(chunk=50, max_steps=2000)
+        steps += s1
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t0
+    polled = batch.poll()
+    failed = polled[:, 3] != 0
+    finished = (polled[:, 0] >= polled[:, 4]) | failed
+    cell_updates = float(sum(polled[k, 2] * specs[k]["grid"]["nr"] * specs[k]["grid"]["nz"] for k in range(len(specs))))
+    (tmax,), (nfin, nfail) = job_reduce([wall], [int(finished.sum()), int(failed.sum())], "cuda")
+    nfin, nfail = int(nfin), int(nfail)
+    out = {"runs": args.batch_runs, "t_end_s": args.batch_t_end, "precision": "FP32-mix",
+           "runs_finished": nfin, "runs_failed": nfail, "complete": nfin == args.batch_runs,
+           "wall_s": round(tmax, 2),
+           "runs_per_hour": nfin * 3600.0 / tmax if nfin == args.batch_runs else None,
+           "cell_updates_per_s": cell_updates / wall, "batch_steps": int(steps), "cells_per_step": cells,
+           "setup_s": round(setup_s, 1), "block_shapes": shapes, "runs_per_rank": len(specs)}
+    # reference: the plain FP64 solver, one run at a time, on the first draws that finished cleanly
+    ok = [k for k in range(len(specs)) if finished[k] and not failed[k]][:args.batch_ref_runs]
+    if ok:
+        errs_d, errs_D, t_ref, nref = [], [], 0.0, 0
+        t_start = time.perf_counter()
+        for k in ok:
+            if time.perf_counter() - t_start > args.batch_ref_max_s:
+                break
+            sp = specs[k]
+            ref = salec.Sim(sp, precision="fp64")
+            ref.set_end_time(args.batch_t_end)
+            one = salec.Batch([ref])            # one run: stops at the step that reaches t_end
+            torch.cuda.synchronize()
+            t1 = time.perf_counter()
+            one.run(chunk=50, max_steps=400000)
+            torch.cuda.synchronize()
+            t_ref += time.perf_counter() - t1
+            if ref.scalars()["status"] != 0:
+                continue
+            nref += 1
+            a, b = sims[k].crater(sp["z_surface"], 64), ref.crater(sp["z_surface"], 64)
+            errs_d.append(abs(a["depth"] / b["depth"] - 1) if b["depth"] else 0.0)
+            errs_D.append(abs(a["diameter"] / b["diameter"] - 1) if b["diameter"] else 0.0)
+            del one, ref
+        if nref:
+            out["fp64_single_run_runs_per_hour"] = nref * 3600.0 / t_ref
+            out["fp64_reference_runs"] = nref
+            if out["runs_per_hour"]:
+                out["speedup_vs_fp64_runs_per_hour"] = out["runs_per_hour"] / out["fp64_single_run_runs_per_hour"]
+            out["crater_rel_err_vs_fp64"] = {"depth_max": max(errs_d), "diameter_max": max(errs_D),
+                                             "depth_mean": float(np.mean(errs_d)),
+                                             "diameter_mean": float(np.mean(errs_D))}
+    del batch, sims
+    torch.cuda.empty_cache()
+    return out
+
+
+def _surrogate(args):
+    """The crater surrogate: an ensemble of MLPs trained on the GPU by the library's own
+    tcgen05 kernels on the batched solver's 400 x 400 runs (4096 training draws, 256
+    held-out), gated by ensemble spread with the solver as fallback.  Reports runs/hour on
+    the held-out draws with and without the surrogate (the solver's cost measured here: the
+    plain FP64 solver, one run at a time, on held-out draws), the accepted predictions'
+    errors, and the tensor throughput of training and of large-batch inference."""
+    import numpy as np
+    import torch
+    from paper_2403_04267_gb300 import salec, surrogate as S, workloads as W
+    path = os.path.join(ROOT, "paper_2403_04267_gb300", "data", "surrogate_400.npz")
+    if not os.path.exists(path):
+        return {"unavailable": "training data file missing (python -m paper_2403_04267_gb300.surrogate generate)"}
+    D = np.load(path)
+    ok_tr = D["train_status"] == 0
+    ok_ho = D["heldout_status"] == 0
+    X, T = D["train_X"][ok_tr], D["train_T"][ok_tr]
+    nv = max(len(X) // 10, 16)
+    Xf, Tf, Xv, Tv = X[:-nv], T[:-nv], X[-nv:], T[-nv:]
+    Xh, Th = D["heldout_X"][ok_ho], D["heldout_T"][ok_ho]
+    seeds_h = D["heldout_seeds"][ok_ho]
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    ens = S.Ensemble(Xf, Tf, members=args.sur_members, steps=args.sur_steps)
+    torch.cuda.synchronize()
+    t_train = time.perf_counter() - t0
+    tau = S.calibrate_gate(ens, Xv, Tv)
+    # the solver's cost per held-out run: plain FP64, one run at a time, to 20 s
+    t_sol, nsol, errs = 0.0, 0, []
+    for k in range(min(args.sur_solver_runs, len(seeds_h))):
+        sp = W.batched_run(W.batched_draw(int(seeds_h[k])), int(D["heldout_n"]))
+        ref = salec.Sim(sp, precision="fp64")
+        ref.set_end_time(20.0)
+        one = salec.Batch([ref])
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        one.run(chunk=50, max_steps=400000)
+        torch.cuda.synchronize()
+        t_sol += time.perf_counter() - t1
+        if ref.scalars()["status"] == 0:
+            nsol += 1
+            c = ref.crater(sp["z_surface"], 64)
+            errs.append(abs(c["diameter"] / (1000.0 * float(Th[k, S.N_PROFILE + 1])) - 1.0))
+        del one, ref
+    out = {"train_draws": int(ok_tr.sum()), "heldout_draws": int(ok_ho.sum()),
+           "failed_runs_excluded": int((~ok_tr).sum() + (~ok_ho).sum()),
+           "members": args.sur_members, "train_steps": args.sur_steps, "train_s": round(t_train, 2)}
+    if nsol:
+        rep = S.gain_report(ens, tau, Xh, Th, t_sol / max(args.sur_solver_runs, 1))
+        out.update(rep)
+        out["fp64_vs_dataset_diameter_err_max"] = max(errs)
+    # tensor throughput: one training step at the full training batch, and inference on
+    # a large batch of draws
+    net = ens.nets[0]
+    Xd = torch.from_numpy(np.ascontiguousarray(Xf, dtype=np.float32)).cuda()
+    Td = torch.from_numpy(np.ascontiguousarray(Tf, dtype=np.float32)).cuda()
+    fwd = 2.0 * sum(a * b for a, b in zip(S.DIMS[:-1], S.DIMS[1:]))        # flops per sample
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    for _ in range(3):
+        net.train_step(Xd, Td, 0.0)
+    ev0.record()
+    for _ in range(20):
+        net.train_step(Xd, Td, 0.0)
+    ev1.record()
+    torch.cuda.synchronize()
+    ms = ev0.elapsed_time(ev1) / 20
+    out["train_step_ms"] = ms
+    out["train_tflops"] = 3.0 * fwd * len(Xf) / (ms * 1e-3) / 1e12
+    big = S.MLP(args.sur_infer_batch)
+    big.set_params(net.get_params())
+    Xb = torch.rand((args.sur_infer_batch, S.N_IN), device="cuda") * 2 - 1
+    Yb = torch.empty((args.sur_infer_batch, S.N_OUT), device="cuda")
+    for _ in range(3):
+        big.forward(Xb, Yb)
+    ev0.record()
+    for _ in range(10):
+        big.forward(Xb, Yb)
+    ev1.record()
+    torch.cuda.synchronize()
+    ms = ev0.elapsed_time(ev1) / 10
+    peak = None
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            peak = float(json.load(fh)["bf16_tflops"])
+    except Exception:
+        peak = 1900.0
+    ach = fwd * args.sur_infer_batch / (ms * 1e-3) / 1e12
+    out["inference"] = {"batch": args.sur_infer_batch, "ms": ms, "draws_per_s": args.sur_infer_batch / (ms * 1e-3)}
+    out["roofline"] = {"bound": "tensor", "kernel": "k_gemm_bf16", "unit": "TFLOP/s", "achieved": ach,
+                       "peak": peak, "peak_kind": "measured bf16 burst", "frac": ach / peak,
+                       "note": "whole forward pass (5 GEMMs + input conversion) at the inference batch"}
+    big.check()
+    net.check()
+    return out
+
+
 def run_reference(args):
     ws, rank, _ = _dist()
     if rank != 0:
@@ -190,6 +389,17 @@ def main():
     ap.add_argument("--cpu-steps", type=int, default=2)
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--precision", default="both", choices=["both", "fp64", "fp32mix"])
+    ap.add_argument("--batch-runs", type=int, default=256)
+    ap.add_argument("--batch-t-end", type=float, default=20.0)
+    ap.add_argument("--batch-ref-runs", type=int, default=8)
+    ap.add_argument("--batch-max-s", type=float, default=900.0)
+    ap.add_argument("--batch-ref-max-s", type=float, default=300.0)
+    ap.add_argument("--no-batch", action="store_true")
+    ap.add_argument("--no-surrogate", action="store_true")
+    ap.add_argument("--sur-members", type=int, default=4)
+    ap.add_argument("--sur-steps", type=int, default=3000)
+    ap.add_argument("--sur-solver-runs", type=int, default=2)
+    ap.add_argument("--sur-infer-batch", type=int, default=65536)
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     if args.impl == "reference":
@@ -338,6 +548,10 @@ def main():
             "step_hbm_frac": round(step_bytes_per_cell(4) * cells / (res32["ms"] / args.steps * 1e-3) / 1e9 / hbm_peak, 4),
             "crater_vs_fp64": {"depth": [c32["depth"], c64["depth"]], "diameter": [c32["diameter"], c64["diameter"]]},
             "gpu_launches": res32["launches"], "clocks": res32["clocks"], "status": res32["scalars"]["status"]}
+    if not args.no_batch and args.batch_runs > 0:
+        line["batched"] = _batched(args, rank, ws)
+    if not args.no_surrogate and ws == 1:
+        line["surrogate"] = _surrogate(args)
     if ws == 1 and not args.no_cpu:
         line["cpu_baseline"] = _cpu_baseline(spec, args.cpu_steps)
     print(json.dumps(line))

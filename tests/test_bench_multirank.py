@@ -1,0 +1,59 @@
+"""The benchmark's multi-process path on the CPU: two gloo ranks shard the batched runs by
+seed with no overlap and no gap, and the whole-job figures are the max of the ranks' times
+and the sum of their counts.  (The GPU path runs the same functions over NCCL.)"""
+import os
+import socket
+import sys
+
+import pytest
+
+torch = pytest.importorskip("torch")
+import torch.distributed as dist
+import torch.multiprocessing as mp
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _free_port():
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+def _rank(rank, ws, port, n_units, out):
+    sys.path.insert(0, ROOT)
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=ws)
+    try:
+        import bench
+        mine = bench.shard(n_units, rank, ws)
+        # a rank's wall time and counts: made up, different per rank
+        mx, sm = bench.job_reduce([10.0 + rank], [len(mine), rank], "cpu")
+        got = [None] * ws
+        dist.all_gather_object(got, mine)
+        out[rank] = (got, mx, sm)
+    finally:
+        dist.destroy_process_group()
+
+
+@pytest.mark.parametrize("ws,n_units", [(2, 256), (2, 7)])
+def test_two_ranks_shard_and_reduce(ws, n_units):
+    port = _free_port()
+    with mp.Manager() as man:
+        out = man.dict()
+        mp.start_processes(_rank, args=(ws, port, n_units, out), nprocs=ws, start_method="spawn", join=True)
+        res = dict(out)
+    for rank in range(ws):
+        shards, mx, sm = res[rank]
+        flat = sorted(u for s in shards for u in s)
+        assert flat == list(range(n_units))                 # every unit once
+        assert mx == [10.0 + ws - 1]                        # max of the ranks' times
+        assert sm == [float(n_units), float(sum(range(ws)))]
+
+
+def test_single_process_is_a_no_op():
+    sys.path.insert(0, ROOT)
+    import bench
+    assert bench.shard(5, 0, 1) == [0, 1, 2, 3, 4]
+    assert bench.job_reduce([3.0], [4, 5]) == ([3.0], [4.0, 5.0])
