@@ -1152,13 +1152,24 @@ static salec_status batch_capture(salec_batch* b, int chunk)
     return SALEC_OK;
 }
 
-// Runs left out of the work lists by an earlier salec_batch_run come back (their end time
-// may have changed since).
+// A run left out of the work lists by an earlier salec_batch_run comes back if it is no
+// longer finished (its end time was moved since); one poll decides.
 static salec_status batch_restore_retired(salec_batch* b)
 {
     bool any = false;
-    for (char& r : b->retired) { any = any || r; r = 0; }
-    return any ? batch_build_work(b) : SALEC_OK;
+    for (char r : b->retired) any = any || r;
+    if (!any) return SALEC_OK;
+    const int n = (int)b->runs.size();
+    std::vector<double> poll((size_t)5 * n);
+    const salec_status st = salec_batch_poll(b, poll.data());
+    if (st != SALEC_OK) return st;
+    bool back = false;
+    for (int r = 0; r < n; ++r)
+        if (b->retired[r] && poll[5 * r] < poll[5 * r + 4] && poll[5 * r + 3] == 0.0) {
+            b->retired[r] = 0;
+            back = true;
+        }
+    return back ? batch_build_work(b) : SALEC_OK;
 }
 
 // Advance every run until it reaches its end time (salec_set_end_time) or fails (status

@@ -56,7 +56,7 @@ struct DevScalars {
     unsigned int counter;   // last-block counter of the dt reduction
     int status;             // bit 1: non-positive volume or density, 2: NaN, 4: dt < dt_min
     int active;             // the run stepped in the current batched step
-    int pad1;
+    float dtf;              // dt rounded to FP32 (the mixed form's kernels read it without a conversion)
 };
 
 // Device pointers into the caller's state buffer.
@@ -134,16 +134,20 @@ template <> __host__ __device__ inline float t_sqrt<float>(float x) { return sqr
 // blend, the blend of the two branches' values), floored.
 // ---------------------------------------------------------------------------------
 template <typename T>
-__host__ __device__ inline void eos_eval(const MatT<T>& m, T rho, T I_in, T& p_out, T& c2_out)
+__host__ __device__ inline void eos_eval(const MatT<T>& m, T rho_in, T I_in, T& p_out, T& c2_out)
 {
     const T zero = T(0), one = T(1), two = T(2);
     const T I = I_in > zero ? I_in : zero;
     if (m.eos == SALEC_EOS_IDEAL_GAS) {
         const T gm1 = m.gamma - one;
-        p_out = gm1 * rho * I;
+        p_out = gm1 * rho_in * I;
         c2_out = m.gamma * gm1 * I;
         return;
     }
+    // evaluated at no less than 1e-12 rho0: below it p ~ a rho I is negligible and c^2 no
+    // longer depends on rho, and the rho^-2 terms below stay finite in FP32
+    const T rho_floor = T(1e-12) * m.rho0;
+    const T rho = rho_in > rho_floor ? rho_in : rho_floor;
     // two divisions: 1/rho and 1/w0 (1/(E0 eta^2) = (rho0^2/E0) / rho^2)
     const T irho = one / rho;
     const T mu = (rho - m.rho0) * m.inv_rho0;
@@ -242,6 +246,13 @@ __device__ __forceinline__ bool is_nan(double x)
     return (__double_as_longlong(x) & 0x7fffffffffffffffLL) > 0x7ff0000000000000LL;
 }
 __device__ __forceinline__ bool is_nan(float x) { return (__float_as_int(x) & 0x7fffffff) > 0x7f800000; }
+// x != 0 (either sign of zero counts as zero) on the bit pattern
+__device__ __forceinline__ bool nonzero(double x) { return (__double_as_longlong(x) << 1) != 0; }
+__device__ __forceinline__ bool nonzero(float x) { return (__float_as_int(x) << 1) != 0; }
+// the step's dt in the element type: the FP32 copy needs no FP64 conversion
+template <typename T> __device__ __forceinline__ T step_dt(const DevScalars* s);
+template <> __device__ __forceinline__ double step_dt<double>(const DevScalars* s) { return s->dt; }
+template <> __device__ __forceinline__ float step_dt<float>(const DevScalars* s) { return s->dtf; }
 // max of two non-negative numbers by their bit patterns
 __device__ __forceinline__ double max_nonneg(double a, double b)
 {

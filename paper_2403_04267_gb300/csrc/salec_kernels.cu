@@ -157,6 +157,7 @@ __device__ __forceinline__ void body_phase0(const ParamsT<T>& P, int bx, int by,
         dt = P.dt_max < dt ? P.dt_max : dt;
         if (dt < P.dt_min) s->status |= 4;
         s->dt = dt;
+        s->dtf = float(dt);
         s->active = 1;
         s->counter = 0u;
     }
@@ -177,7 +178,7 @@ __device__ __forceinline__ void body_phase1(const ParamsT<T>& P, int bx, int by,
     const int nr = P.nr, nz = P.nz;
     if (i > nr || j > nz) return;
     const PtrsT<T>& p = P.p;
-    const T dt = T(p.scal->dt);
+    const T dt = step_dt<T>(p.scal);
     const int v = j * (nr + 1) + i;
     const T hoop = T(0.25) * P.dx2;
     T Pc[4] = {zero, zero, zero, zero}, Pp[4] = {zero, zero, zero, zero};
@@ -278,7 +279,7 @@ __device__ __forceinline__ void body_phase2(const ParamsT<T>& P, int bx, int by,
         if (STR) { p.sL01[c] = V::mk(zero, zero); p.sL2d[c] = V::mk(zero, zero); }
         return;
     }
-    const T dt = T(p.scal->dt);
+    const T dt = step_dt<T>(p.scal);
     const T dx = P.dx;
     const int nv = nr + 1;
     const typename V::T2 va = p.vL[j * nv + i], vb = p.vL[j * nv + i + 1];
@@ -326,7 +327,8 @@ __device__ __forceinline__ void body_phase2(const ParamsT<T>& P, int bx, int by,
     const T dE = -Pc * dV + work - dt * psi2;
     const double Ic = p.I[c];
     // the specific internal energy is accumulated in FP64 in every form
-    p.IL[c] = pos(M) ? Ic + double(dE / M) : Ic;
+    // no energy change: no FP64 instruction (the sum would return Ic unchanged)
+    p.IL[c] = (pos(M) && nonzero(dE)) ? Ic + double(dE / M) : Ic;
     p.VL[c] = VLc;
     // volume partition: matter and void share every volume change in proportion to their
     // fractions (equal strain), so each material's work -p_m dV_m adds up to the -P dV the
@@ -460,7 +462,7 @@ __device__ __forceinline__ void body_phase3a(const ParamsT<T>& P, int bx, int by
     double t_out = 0.0, t_disc = 0.0, t_pml = 0.0;
     if (i < nr && j < nz) {
         const int c = j * nr + i;
-        const T dt = T(p.scal->dt);
+        const T dt = step_dt<T>(p.scal);
         // acc collects the net fluxes; the Lagrangian contents are added back below
         Acc<T, NM> acc;
         const T VLc = p.VL[c];
@@ -527,7 +529,7 @@ __device__ __forceinline__ void body_phase3a(const ParamsT<T>& P, int bx, int by
             rn[m] = pos(Vm[m]) ? fl.y + (acc.Mm[m] - fl.y * acc.Vm[m]) / Vm[m] : zero;
         }
         const T Mtot = MLtot + dMtot, Vtot = VLmat + dVtot;
-        double Ic = pos(Mtot) ? ILc + double(acc.dI / Mtot) : 0.0;
+        double Ic = pos(Mtot) ? (nonzero(acc.dI) ? ILc + double(acc.dI / Mtot) : ILc) : 0.0;
         T s0 = zero, s1 = zero, s2 = zero, Dm = zero;
         if (STR && pos(Vtot)) {
             const T iv = one / Vtot;
@@ -601,7 +603,7 @@ __device__ __forceinline__ void body_phase3a(const ParamsT<T>& P, int bx, int by
     }
     // tallies: block sums and one atomic per block, only in blocks where some thread has one
     // (most blocks touch neither the top boundary, the clean-up nor a strip)
-    if (__syncthreads_or(t_out != 0.0 || t_disc != 0.0 || t_pml != 0.0)) {
+    if (__syncthreads_or(nonzero(t_out) || nonzero(t_disc) || nonzero(t_pml))) {
         __shared__ double sh[kMaxThreads / 32];
         const double b_out = block_sum(t_out, sh);
         const double b_disc = block_sum(t_disc, sh);
@@ -653,7 +655,7 @@ __device__ __forceinline__ void body_phase3b(const ParamsT<T>& P, int bx, int by
     double t_zmom = 0.0;
     if (i <= nr && j <= nz) {
         const int v = j * nv + i;
-        const T dt = T(p.scal->dt);
+        const T dt = step_dt<T>(p.scal);
         const typename V::T2 vL = p.vL[v];
         const T m0 = p.mv[v];
         T m = m0, pr = m0 * vL.x, pz = m0 * vL.y;
@@ -739,7 +741,7 @@ __device__ __forceinline__ void body_phase3b(const ParamsT<T>& P, int bx, int by
         if (is_nan(vr) || is_nan(vz)) atomicOr(&p.scal->status, 2);
         p.v[v] = V::mk(vr, vz);
     }
-    if (__syncthreads_or(t_zmom != 0.0)) {
+    if (__syncthreads_or(nonzero(t_zmom))) {
         __shared__ double sh[kMaxThreads / 32];
         const double b = block_sum(t_zmom, sh);
         if (threadIdx.x == 0 && threadIdx.y == 0 && b != 0.0) atomicAdd(&p.scal->zmom_out, b);
@@ -768,7 +770,7 @@ __device__ __forceinline__ void body_phase3c(const ParamsT<T>& P, int bx, int by
         if (pos(M)) {
             const T add = T(0.25) * (p.kheat[j * nv + i] + p.kheat[j * nv + i + 1] +
                                      p.kheat[(j + 1) * nv + i + 1] + p.kheat[(j + 1) * nv + i]);
-            p.I[c] += double(add);
+            if (nonzero(add)) p.I[c] += double(add);
         }
     }
     if (bx == 0 && by == 0 && threadIdx.x == 0 && threadIdx.y == 0) {
