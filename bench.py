@@ -278,7 +278,7 @@ def _surrogate(args):
     ens = S.Ensemble(Xf, Tf, members=args.sur_members, steps=args.sur_steps)
     torch.cuda.synchronize()
     t_train = time.perf_counter() - t0
-    tau = S.calibrate_gate(ens, Xv, Tv)
+    tau = S.calibrate_gate(ens, Xv, Tv, target=args.sur_gate_target)
     # the solver's cost per held-out run: plain FP64, one run at a time, to 20 s
     t_sol, nsol, errs = 0.0, 0, []
     for k in range(min(args.sur_solver_runs, len(seeds_h))):
@@ -302,6 +302,22 @@ def _surrogate(args):
     if nsol:
         rep = S.gain_report(ens, tau, Xh, Th, t_sol / max(args.sur_solver_runs, 1))
         out.update(rep)
+        # the same with the batched FP32-mix solver as the fallback, at the cost per run it
+        # had when it generated the training data (batches of 1024 runs of 400 x 400 to 20 s)
+        s_batch = float(D["train_wall_s"]) / len(D["train_status"])
+        rb = S.gain_report(ens, tau, Xh, Th, s_batch)
+        out["batched_fallback"] = {"solver_s_per_run": s_batch, "runs_per_hour_solver": rb["runs_per_hour_solver"],
+                                   "runs_per_hour_with_surrogate": rb["runs_per_hour_with_surrogate"]}
+        # the gate's trade-off: stricter validation targets accept fewer draws, more accurately
+        sweep = []
+        for target in (0.9, 0.95, 0.97, 0.99):
+            tt = S.calibrate_gate(ens, Xv, Tv, target=target)
+            r1 = S.gain_report(ens, tt, Xh, Th, t_sol / max(args.sur_solver_runs, 1))
+            r2 = S.gain_report(ens, tt, Xh, Th, s_batch)
+            sweep.append({"target": target, "accepted": r1["accepted"], "accepted_within_tol": r1["accepted_within_tol"],
+                          "runs_per_hour_fp64_fallback": r1["runs_per_hour_with_surrogate"],
+                          "runs_per_hour_batched_fallback": r2["runs_per_hour_with_surrogate"]})
+        out["gate_sweep"] = sweep
         out["fp64_vs_dataset_diameter_err_max"] = max(errs)
     # tensor throughput: one training step at the full training batch, and inference on
     # a large batch of draws
@@ -400,6 +416,7 @@ def main():
     ap.add_argument("--sur-steps", type=int, default=3000)
     ap.add_argument("--sur-solver-runs", type=int, default=2)
     ap.add_argument("--sur-infer-batch", type=int, default=65536)
+    ap.add_argument("--sur-gate-target", type=float, default=0.95)
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     if args.impl == "reference":

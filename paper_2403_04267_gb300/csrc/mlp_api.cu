@@ -19,6 +19,12 @@ namespace {
 constexpr int kLayers = 5;
 constexpr int kDims[kLayers + 1] = {SALEC_MLP_IN, 256, 256, 256, 256, SALEC_MLP_OUT};
 constexpr int kHid = 256;
+// BF16 row stride of the inputs and of W_1: 5 columns padded to 8 (16-byte rows, which the
+// TMA-fed GEMM needs); the padding stays zero
+constexpr int kInLd = 8;
+
+// BF16 row stride of W_l
+int w_ld(int l) { return l == 0 ? kInLd : kDims[l]; }
 
 size_t align_up(size_t x) { return (x + 255) & ~size_t(255); }
 
@@ -29,10 +35,10 @@ long n_params()
     return n;
 }
 
-long n_weights()
+long n_weights_bf16()
 {
     long n = 0;
-    for (int l = 0; l < kLayers; ++l) n += (long)kDims[l + 1] * kDims[l];
+    for (int l = 0; l < kLayers; ++l) n += (long)kDims[l + 1] * w_ld(l);
     return n;
 }
 
@@ -40,13 +46,13 @@ struct Layout {
     size_t theta, m1, m2, grad, wmap, wbf, X, Z[4], H[4], Y, G[2], loss, err, total;
     Layout(int bmax)
     {
-        const long P = n_params(), W = n_weights();
+        const long P = n_params(), W = n_weights_bf16();
         size_t o = 0;
         auto take = [&](size_t bytes) { size_t r = o; o = align_up(o + bytes); return r; };
         theta = take(P * 4); m1 = take(P * 4); m2 = take(P * 4); grad = take(P * 4);
         wmap = take(P * 4);
         wbf = take(W * 2);
-        X = take((size_t)bmax * SALEC_MLP_IN * 2);
+        X = take((size_t)bmax * kInLd * 2);
         for (int l = 0; l < 4; ++l) Z[l] = take((size_t)bmax * kHid * 4);
         for (int l = 0; l < 4; ++l) H[l] = take((size_t)bmax * kHid * 2);
         Y = take((size_t)bmax * SALEC_MLP_OUT * 4);
@@ -109,17 +115,19 @@ GemmArgs gemm0(int M, int N, int K, int* err)
 // the epilogue `out_epi` (plain store into y, or the fused loss gradient against t)
 salec_status forward_impl(salec_mlp* n, int B, float* y, long ldy, const float* t, bool with_loss)
 {
+    // the pre-activations Z are kept only for a backward pass
+    const bool keep_z = with_loss;
     const __nv_bfloat16* Hin = n->X;
-    long ldin = SALEC_MLP_IN;
+    long ldin = kInLd;
     for (int l = 0; l < kLayers; ++l) {
         const int ni = kDims[l], no = kDims[l + 1];
         GemmArgs g = gemm0(B, no, ni, n->errflag);
         g.A = Hin; g.a_sm = ldin; g.a_sk = 1;
-        g.B = n->wbf + n->wbf_off[l]; g.b_sn = ni; g.b_sk = 1;
+        g.B = n->wbf + n->wbf_off[l]; g.b_sn = w_ld(l); g.b_sk = 1;
         g.bias = n->theta + n->boff[l];
         if (l + 1 < kLayers) {
             g.epi = kEpiBiasGelu;
-            g.C = n->Z[l]; g.ldc = kHid;
+            g.C = keep_z ? n->Z[l] : nullptr; g.ldc = kHid;
             g.Hout = n->H[l]; g.ldh = kHid;
         } else if (with_loss) {
             g.epi = kEpiOutLoss;
@@ -147,7 +155,7 @@ salec_status backward_impl(salec_mlp* n, int B, float* grad)
         const int ni = kDims[l], no = kDims[l + 1];
         const __nv_bfloat16* G = n->G[cur];
         const __nv_bfloat16* Hprev = l > 0 ? n->H[l - 1] : n->X;
-        const long ldprev = l > 0 ? kHid : SALEC_MLP_IN;
+        const long ldprev = l > 0 ? kHid : kInLd;
         // dW_l[o][i] = sum_b G[b][o] Hprev[b][i]
         GemmArgs gw = gemm0(no, ni, B, n->errflag);
         gw.A = G; gw.a_sm = 1; gw.a_sk = kHid;
@@ -160,7 +168,7 @@ salec_status backward_impl(salec_mlp* n, int B, float* grad)
         // dL/dZ_{l-1}[b][i] = (sum_o G[b][o] W_l[o][i]) gelu'(Z_{l-1}[b][i])
         GemmArgs gd = gemm0(B, ni, no, n->errflag);
         gd.A = G; gd.a_sm = kHid; gd.a_sk = 1;
-        gd.B = n->wbf + n->wbf_off[l]; gd.b_sn = 1; gd.b_sk = ni;
+        gd.B = n->wbf + n->wbf_off[l]; gd.b_sn = 1; gd.b_sk = w_ld(l);
         gd.epi = kEpiGeluBwd;
         gd.Zin = n->Z[l - 1]; gd.ldz = kHid;
         gd.Hout = n->G[cur ^ 1]; gd.ldh = kHid;
@@ -222,14 +230,15 @@ salec_status salec_mlp_create(int batch_max, void* dev_buf, size_t bytes, void* 
     std::vector<int> wmap(P, -1);
     long o = 0, w = 0;
     for (int l = 0; l < kLayers; ++l) {
-        const long cnt = (long)kDims[l + 1] * kDims[l];
+        const int ni = kDims[l], no = kDims[l + 1], ld = w_ld(l);
         n->woff[l] = o;
         n->wbf_off[l] = w;
-        for (long i = 0; i < cnt; ++i) wmap[o + i] = (int)(w + i);
-        o += cnt;
-        w += cnt;
+        for (int r = 0; r < no; ++r)
+            for (int c = 0; c < ni; ++c) wmap[o + (long)r * ni + c] = (int)(w + (long)r * ld + c);
+        o += (long)no * ni;
+        w += (long)no * ld;
         n->boff[l] = o;
-        o += kDims[l + 1];
+        o += no;
     }
     cudaError_t e = cudaMemsetAsync(dev_buf, 0, L.total, n->stream);
     if (e == cudaSuccess) e = cudaMemcpyAsync(n->wmap, wmap.data(), P * sizeof(int), cudaMemcpyHostToDevice, n->stream);
@@ -268,7 +277,7 @@ salec_status salec_mlp_forward(salec_mlp* n, const float* x_dev, int batch, floa
     salec_status st = check_batch(n, batch);
     if (st != SALEC_OK) return st;
     if (!x_dev || !y_dev) return fail(n, SALEC_EINVAL, "null pointer");
-    MLP_CUDA(n, launch_to_bf16(x_dev, (long)batch * SALEC_MLP_IN, n->X, n->stream), "mlp input");
+    MLP_CUDA(n, launch_inputs_bf16(x_dev, batch, SALEC_MLP_IN, kInLd, n->X, n->stream), "mlp input");
     return forward_impl(n, batch, y_dev, SALEC_MLP_OUT, nullptr, false);
 }
 
@@ -280,7 +289,7 @@ salec_status salec_mlp_gradient(salec_mlp* n, const float* x_dev, const float* t
     if (!x_dev || !t_dev) return fail(n, SALEC_EINVAL, "null pointer");
     float* grad = grad_dev ? grad_dev : n->grad;
     MLP_CUDA(n, cudaMemsetAsync(n->loss, 0, 8, n->stream), "mlp loss reset");
-    MLP_CUDA(n, launch_to_bf16(x_dev, (long)batch * SALEC_MLP_IN, n->X, n->stream), "mlp input");
+    MLP_CUDA(n, launch_inputs_bf16(x_dev, batch, SALEC_MLP_IN, kInLd, n->X, n->stream), "mlp input");
     st = forward_impl(n, batch, n->Y, SALEC_MLP_OUT, t_dev, true);
     if (st != SALEC_OK) return st;
     st = backward_impl(n, batch, grad);
@@ -304,7 +313,7 @@ salec_status salec_mlp_train_step(salec_mlp* n, const float* x_dev, const float*
     if (!(lr >= 0.0f) || !(beta1 >= 0.0f && beta1 < 1.0f) || !(beta2 >= 0.0f && beta2 < 1.0f) || !(eps > 0.0f))
         return fail(n, SALEC_EINVAL, "bad Adam hyper-parameters");
     MLP_CUDA(n, cudaMemsetAsync(n->loss, 0, 8, n->stream), "mlp loss reset");
-    MLP_CUDA(n, launch_to_bf16(x_dev, (long)batch * SALEC_MLP_IN, n->X, n->stream), "mlp input");
+    MLP_CUDA(n, launch_inputs_bf16(x_dev, batch, SALEC_MLP_IN, kInLd, n->X, n->stream), "mlp input");
     st = forward_impl(n, batch, n->Y, SALEC_MLP_OUT, t_dev, true);
     if (st != SALEC_OK) return st;
     st = backward_impl(n, batch, n->grad);

@@ -11,7 +11,7 @@ namespace mlp {
 // fused epilogues of the GEMM
 enum Epi {
     kEpiStore = 0,      // C = acc (+ bias[n] if bias)                               FP32
-    kEpiBiasGelu = 1,   // C = Z = acc + bias[n] (FP32), Hout = gelu(Z) (BF16)
+    kEpiBiasGelu = 1,   // C = Z = acc + bias[n] (FP32; skipped when C is null), Hout = gelu(Z) (BF16)
     kEpiGeluBwd = 2,    // Hout = acc * gelu'(Zin) (BF16): dL/dZ of a hidden layer
     kEpiOutLoss = 3,    // C = Y = acc + bias[n]; Hout = grad_scale (Y - Tin) (BF16); loss += sum (Y - Tin)^2
 };
@@ -44,7 +44,7 @@ struct AdamArgs {
 
 cudaError_t launch_gemm(const GemmArgs& g, cudaStream_t s);
 cudaError_t launch_colsum(const __nv_bfloat16* G, int M, int N, long ldg, float* out, cudaStream_t s);
-cudaError_t launch_to_bf16(const float* x, long n, __nv_bfloat16* y, cudaStream_t s);
+cudaError_t launch_inputs_bf16(const float* x, int rows, int cols, int ld, __nv_bfloat16* y, cudaStream_t s);
 cudaError_t launch_adam(float* theta, float* m1, float* m2, const float* grad, long n, const AdamArgs& a,
                         const int* wmap, __nv_bfloat16* wbf, cudaStream_t s);
 cudaError_t launch_refresh_bf16(const float* theta, long n, const int* wmap, __nv_bfloat16* wbf, cudaStream_t s);

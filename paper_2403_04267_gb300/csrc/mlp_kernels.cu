@@ -15,8 +15,12 @@
 // owns TMEM lanes 32w..32w+31, i.e. rows 32w..32w+31 of the tile) and applies one of the
 // fused operations below.
 //
+// Operands that are K-major rows of 16-byte multiples (the forward pass) take a second
+// kernel, k_gemm_bf16_tma, fed by TMA (below).
+//
 // Every wait on an mbarrier is bounded; on expiry the kernel records an error code, waits
 // (bounded again) for its own MMAs, frees its tensor memory and returns.
+#include <cuda.h>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -145,6 +149,80 @@ __device__ __forceinline__ uint4 gather8(const __nv_bfloat16* __restrict__ P, lo
     return w.u;
 }
 
+// Epilogue: warp w reads TMEM lanes 32w..32w+31 (rows m0 + 32w + lane of the tile), 16
+// columns at a time, and applies the fused operation of g.epi.  In kEpiBiasGelu a null C
+// skips the pre-activation store (inference).  A row's 16 columns go out as 16-byte stores
+// when they lie inside N and the rows are 16-byte aligned (each thread writes its own row:
+// whole sectors, merged in L2); otherwise element by element.
+__device__ __forceinline__ void epilogue(const GemmArgs& g, uint32_t tmem, int m0, int n0, int NT, bool any_k)
+{
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int m = m0 + warp * 32 + lane;
+    const uint32_t trow = tmem + ((uint32_t)(warp * 32) << 16);
+    double lsum = 0.0;
+    const bool vec_c = ((g.ldc * 4) & 15) == 0 && ((reinterpret_cast<uintptr_t>(g.C) & 15) == 0);
+    const bool vec_h = ((g.ldh * 2) & 15) == 0 && ((reinterpret_cast<uintptr_t>(g.Hout) & 15) == 0);
+    const bool has_c = g.epi != kEpiGeluBwd && g.C != nullptr;
+    const bool has_h = g.epi != kEpiStore;
+    for (int c0 = 0; c0 < NT; c0 += 16) {
+        float v[16];
+        tmem_ld16(trow + (uint32_t)c0, v);
+        if (m >= g.M) continue;
+        const int nb = n0 + c0;
+        const bool full = nb + 16 <= g.N;
+        float x[16], h[16];
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+            const int n = nb + j;
+            const bool in = full || n < g.N;
+            float y = any_k ? v[j] : 0.0f;    // K = 0: empty sum
+            h[j] = 0.0f;
+            switch (g.epi) {
+            case kEpiStore:
+                if (g.bias && in) y += g.bias[n];
+                break;
+            case kEpiBiasGelu:
+                if (in) y += g.bias[n];
+                h[j] = gelu_f(y);
+                break;
+            case kEpiGeluBwd:
+                h[j] = in ? y * gelu_grad_f(g.Zin[(long)m * g.ldz + n]) : 0.0f;
+                break;
+            case kEpiOutLoss:
+                if (in) {
+                    y += g.bias[n];
+                    const float d = y - g.Tin[(long)m * g.ldt + n];
+                    lsum += (double)d * (double)d;
+                    h[j] = d * g.grad_scale;
+                }
+                break;
+            }
+            x[j] = y;
+        }
+        if (full && has_c && vec_c) {
+            float4* dst = reinterpret_cast<float4*>(g.C + (long)m * g.ldc + nb);
+#pragma unroll
+            for (int q = 0; q < 4; ++q) dst[q] = make_float4(x[4 * q], x[4 * q + 1], x[4 * q + 2], x[4 * q + 3]);
+        } else if (has_c) {
+            for (int j = 0; j < 16 && nb + j < g.N; ++j) g.C[(long)m * g.ldc + nb + j] = x[j];
+        }
+        if (full && has_h && vec_h) {
+            union { uint4 u[2]; __nv_bfloat16 b[16]; } pk;
+#pragma unroll
+            for (int j = 0; j < 16; ++j) pk.b[j] = __float2bfloat16_rn(h[j]);
+            uint4* dst = reinterpret_cast<uint4*>(g.Hout + (long)m * g.ldh + nb);
+            dst[0] = pk.u[0];
+            dst[1] = pk.u[1];
+        } else if (has_h) {
+            for (int j = 0; j < 16 && nb + j < g.N; ++j) g.Hout[(long)m * g.ldh + nb + j] = __float2bfloat16_rn(h[j]);
+        }
+    }
+    if (g.epi == kEpiOutLoss && g.loss) {
+        for (int o = 16; o > 0; o >>= 1) lsum += __shfl_down_sync(0xffffffffu, lsum, o);
+        if (lane == 0 && lsum != 0.0) atomicAdd(g.loss, lsum);
+    }
+}
+
 __global__ void __launch_bounds__(kGemmThreads) k_gemm_bf16(GemmArgs g)
 {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
@@ -153,7 +231,7 @@ __global__ void __launch_bounds__(kGemmThreads) k_gemm_bf16(GemmArgs g)
     __shared__ uint64_t bars[2];
     __shared__ uint32_t tmem_holder;
 
-    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int tid = threadIdx.x, warp = tid >> 5;
     const int m0 = blockIdx.x * kBM, n0 = blockIdx.y * g.nt;
     const int NT = g.nt;
     const uint32_t a_bytes = kBM * kBK * 2, b_bytes = (uint32_t)NT * kBK * 2;
@@ -229,51 +307,127 @@ __global__ void __launch_bounds__(kGemmThreads) k_gemm_bf16(GemmArgs g)
     }
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
 
-    if (ok) {
-        const int m = m0 + warp * 32 + lane;
-        const uint32_t trow = tmem + ((uint32_t)(warp * 32) << 16);
-        double lsum = 0.0;
-        for (int c0 = 0; c0 < NT; c0 += 16) {
-            float v[16];
-            tmem_ld16(trow + (uint32_t)c0, v);
-            if (m >= g.M) continue;
+    if (ok) epilogue(g, tmem, m0, n0, NT, nk > 0);
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 0) {
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(tmem_cols) : "memory");
+    }
+}
+
+// ---------------------------------------------------------------------------------------
+// The same contraction when both operands are K-major rows (A[m][k], B[n][k], rows of
+// 16-byte multiples): the forward pass.  One thread streams K slices into a ring of
+// kStages shared-memory stages with TMA (cp.async.bulk.tensor, 2-D maps, boxes of 8
+// elements x rows: one box is one column of core matrices, 16 bytes x rows, exactly the
+// canonical no-swizzle K-major layout), each stage's mbarrier completing on the bytes
+// delivered; the same thread issues the MMAs of a slice as soon as it lands and refills
+// the stage once tcgen05.commit reports those MMAs done.  The tile is 128 x NT with NT up
+// to 256 (a whole hidden layer, so the activations are read once).
+// ---------------------------------------------------------------------------------------
+constexpr int kStages = 4;
+constexpr int kMaxNT_TMA = 256;
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map, int x, int y, uint64_t* bar)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(dst),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(smem_u32(bar))
+        : "memory");
+}
+
+__global__ void __launch_bounds__(kGemmThreads) k_gemm_bf16_tma(const __grid_constant__ CUtensorMap mapA,
+                                                                const __grid_constant__ CUtensorMap mapB, GemmArgs g)
+{
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    unsigned char* smem = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    __shared__ uint64_t full[kStages], empty[kStages];
+    __shared__ uint32_t tmem_holder;
+    __shared__ int ok_flag;
+
+    const int tid = threadIdx.x, warp = tid >> 5;
+    const int m0 = blockIdx.x * kBM, n0 = blockIdx.y * g.nt;
+    const int NT = g.nt;
+    const uint32_t a_bytes = kBM * kBK * 2, b_bytes = (uint32_t)NT * kBK * 2;
+    const uint32_t stage_bytes = a_bytes + b_bytes;
+    const uint32_t tmem_cols = g.tmem_cols;
+    const int nk = (g.K + kBK - 1) / kBK;
+
+    if (tid == 0) {
+        for (int i = 0; i < kStages; ++i) { mbar_init(&full[i], 1); mbar_init(&empty[i], 1); }
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&mapA)) : "memory");
+        asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&mapB)) : "memory");
+        ok_flag = 1;
+    }
+    __syncwarp();
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_holder)),
+                     "r"(tmem_cols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = tmem_holder;
+
+    if (tid == 0) {
+        const uint32_t idesc = idesc_bf16(kBM, NT);
+        const uint32_t base = smem_u32(smem);
+        auto load_slice = [&](int kt) {
+            const int st = kt % kStages;
+            const uint32_t sa = base + st * stage_bytes, sb = sa + a_bytes;
+            mbar_expect_tx(&full[st], stage_bytes);
+            const int k0 = kt * kBK;
 #pragma unroll
-            for (int j = 0; j < 16; ++j) {
-                const int n = n0 + c0 + j;
-                if (n >= g.N) break;
-                float x = nk > 0 ? v[j] : 0.0f;    // K = 0: empty sum
-                switch (g.epi) {
-                case kEpiStore:
-                    if (g.bias) x += g.bias[n];
-                    g.C[(long)m * g.ldc + n] = x;
-                    break;
-                case kEpiBiasGelu: {
-                    x += g.bias[n];
-                    g.C[(long)m * g.ldc + n] = x;                                   // Z
-                    g.Hout[(long)m * g.ldh + n] = __float2bfloat16_rn(gelu_f(x));   // gelu(Z)
-                    break;
-                }
-                case kEpiGeluBwd: {
-                    const float z = g.Zin[(long)m * g.ldz + n];
-                    g.Hout[(long)m * g.ldh + n] = __float2bfloat16_rn(x * gelu_grad_f(z));
-                    break;
-                }
-                case kEpiOutLoss: {
-                    x += g.bias[n];
-                    g.C[(long)m * g.ldc + n] = x;                                   // Y
-                    const float d = x - g.Tin[(long)m * g.ldt + n];
-                    lsum += (double)d * (double)d;
-                    g.Hout[(long)m * g.ldh + n] = __float2bfloat16_rn(d * g.grad_scale);
-                    break;
-                }
-                }
+            for (int kg = 0; kg < kBK / 8; ++kg) {
+                tma_load_2d(sa + kg * (kBM * 16), &mapA, k0 + 8 * kg, m0, &full[st]);
+                tma_load_2d(sb + kg * (NT * 16), &mapB, k0 + 8 * kg, n0, &full[st]);
+            }
+        };
+        bool good = true;
+        int committed = 0;              // slices whose MMAs were committed
+        const int pre = nk < kStages ? nk : kStages;
+        for (int kt = 0; kt < pre; ++kt) load_slice(kt);
+        for (int kt = 0; kt < nk && good; ++kt) {
+            const int st = kt % kStages;
+            const uint32_t par = (uint32_t)(kt / kStages) & 1u;
+            if (!mbar_wait(&full[st], par)) { good = false; break; }
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const uint32_t a0 = base + st * stage_bytes, b0 = a0 + a_bytes;
+#pragma unroll
+            for (int kk = 0; kk < kBK / 16; ++kk) {
+                const uint64_t ad = sdesc(a0 + kk * 2 * (kBM * 16), kBM * 16, 128);
+                const uint64_t bd = sdesc(b0 + kk * 2 * (NT * 16), NT * 16, 128);
+                mma_bf16(tmem, ad, bd, idesc, (kt > 0 || kk > 0) ? 1u : 0u);
+            }
+            mma_commit(&empty[st]);
+            committed = kt + 1;
+            if (kt + kStages < nk) {
+                // the stage is refilled once its MMAs have read it
+                if (!mbar_wait(&empty[st], par)) { good = false; break; }
+                load_slice(kt + kStages);
             }
         }
-        if (g.epi == kEpiOutLoss && g.loss) {
-            for (int o = 16; o > 0; o >>= 1) lsum += __shfl_down_sync(0xffffffffu, lsum, o);
-            if (lane == 0 && lsum != 0.0) atomicAdd(g.loss, lsum);
+        // the last commit covers every MMA; wait for it (bounded)
+        if (good && committed > 0)
+            good = mbar_wait(&empty[(committed - 1) % kStages], (uint32_t)((committed - 1) / kStages) & 1u);
+        if (!good) {
+            if (g.err) atomicOr(g.err, 2);
+            // bounded chance for copies and MMAs still in flight to finish
+            for (int i = 0; i < kStages; ++i) (void)mbar_wait(&empty[i], 0);
+            ok_flag = 0;
         }
     }
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    if (ok_flag) epilogue(g, tmem, m0, n0, NT, nk > 0);
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
     if (warp == 0) {
@@ -291,11 +445,15 @@ __global__ void k_colsum(const __nv_bfloat16* __restrict__ G, int M, int N, long
     out[n] = s;
 }
 
-// FP32 -> BF16 (inputs of the first layer).
-__global__ void k_to_bf16(const float* __restrict__ x, long n, __nv_bfloat16* __restrict__ y)
+// FP32 -> BF16 inputs of the first layer: rows of `cols` values into rows of `ld`, the
+// padding zero.
+__global__ void k_inputs_bf16(const float* __restrict__ x, int rows, int cols, int ld, __nv_bfloat16* __restrict__ y)
 {
     const long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < n) y[i] = __float2bfloat16_rn(x[i]);
+    if (i >= (long)rows * ld) return;
+    const long r = i / ld;
+    const int c = (int)(i - r * ld);
+    y[i] = __float2bfloat16_rn(c < cols ? x[r * cols + c] : 0.0f);
 }
 
 // Adam on the FP32 master parameters; refreshes the BF16 copy of every weight.  wmap[i] is
@@ -329,10 +487,78 @@ __global__ void k_refresh_bf16(const float* __restrict__ theta, long n, const in
 
 size_t gemm_smem_bytes(int nt) { return 2 * (size_t)(kBM * kBK * 2 + nt * kBK * 2) + 1024; }
 
+namespace {
+
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+// cuTensorMapEncodeTiled from the driver, looked up once
+EncodeTiledFn encode_tiled()
+{
+    static EncodeTiledFn fn = nullptr;
+    static bool tried = false;
+    if (!tried) {
+        tried = true;
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<EncodeTiledFn>(p);
+        else
+            (void)cudaGetLastError();
+    }
+    return fn;
+}
+
+// 2-D map of a row-major BF16 matrix [rows][K] with row stride ld elements; boxes of 8
+// elements (16 bytes) x box_rows rows.  False when TMA cannot address it (alignment).
+bool make_map(CUtensorMap* map, const void* base, long rows, long K, long ld, int box_rows)
+{
+    EncodeTiledFn fn = encode_tiled();
+    if (!fn || rows < 1 || K < 1 || (reinterpret_cast<uintptr_t>(base) & 15) || ((ld * 2) & 15)) return false;
+    const cuuint64_t dims[2] = {(cuuint64_t)K, (cuuint64_t)rows};
+    const cuuint64_t strides[1] = {(cuuint64_t)(ld * 2)};
+    const cuuint32_t box[2] = {8u, (cuuint32_t)box_rows};
+    const cuuint32_t estr[2] = {1u, 1u};
+    return fn(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), dims, strides, box, estr,
+              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+size_t tma_smem_bytes(int nt) { return (size_t)kStages * (kBM * kBK * 2 + nt * kBK * 2) + 1024; }
+
+}  // namespace
+
 cudaError_t launch_gemm(const GemmArgs& g0, cudaStream_t s)
 {
     GemmArgs g = g0;
     if (g.M <= 0 || g.N <= 0) return cudaSuccess;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+    // both operands K-major with 16-byte rows: the TMA-fed kernel
+    if (g.K > 0 && g.a_sk == 1 && g.b_sk == 1) {
+        const int nt = ((g.N < kMaxNT_TMA ? g.N : kMaxNT_TMA) + 15) / 16 * 16;
+        CUtensorMap ma, mb;
+        if (make_map(&ma, g.A, g.M, g.K, g.a_sm, kBM) && make_map(&mb, g.B, g.N, g.K, g.b_sn, nt)) {
+            static bool attr_tma[64] = {};
+            if (!attr_tma[dev]) {
+                e = cudaFuncSetAttribute(k_gemm_bf16_tma, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)tma_smem_bytes(kMaxNT_TMA));
+                if (e != cudaSuccess) return e;
+                attr_tma[dev] = true;
+            }
+            g.nt = nt;
+            int cols = 32;
+            while (cols < nt) cols <<= 1;
+            g.tmem_cols = cols;
+            dim3 grid((unsigned)((g.M + kBM - 1) / kBM), (unsigned)((g.N + nt - 1) / nt));
+            k_gemm_bf16_tma<<<grid, kGemmThreads, tma_smem_bytes(nt), s>>>(ma, mb, g);
+            return cudaGetLastError();
+        }
+    }
     const int nt = ((g.N < kMaxNT ? g.N : kMaxNT) + 15) / 16 * 16;
     g.nt = nt;
     int cols = 32;
@@ -341,10 +567,6 @@ cudaError_t launch_gemm(const GemmArgs& g0, cudaStream_t s)
     const size_t smem = gemm_smem_bytes(nt);
     // the attribute is per device
     static bool attr_set[64] = {};
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e != cudaSuccess) return e;
-    if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
     if (!attr_set[dev]) {
         e = cudaFuncSetAttribute(k_gemm_bf16, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gemm_smem_bytes(kMaxNT));
         if (e != cudaSuccess) return e;
@@ -361,10 +583,11 @@ cudaError_t launch_colsum(const __nv_bfloat16* G, int M, int N, long ldg, float*
     return cudaGetLastError();
 }
 
-cudaError_t launch_to_bf16(const float* x, long n, __nv_bfloat16* y, cudaStream_t s)
+cudaError_t launch_inputs_bf16(const float* x, int rows, int cols, int ld, __nv_bfloat16* y, cudaStream_t s)
 {
+    const long n = (long)rows * ld;
     if (n <= 0) return cudaSuccess;
-    k_to_bf16<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(x, n, y);
+    k_inputs_bf16<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(x, rows, cols, ld, y);
     return cudaGetLastError();
 }
 

@@ -236,11 +236,20 @@ __host__ __device__ inline T yield_eval(const MatT<T>& m, T p_in, T D, T I, T rh
 
 // Sign tests on the bit pattern: integer instructions instead of floating-point compares
 // (FP64 compares issue on the FP64 pipe, the bottleneck of the FP64 form).  pos(x): x > 0
-// (or +NaN); neg(x): x < 0 or x == -0 (callers then move zero volume).
+// (or +NaN); neg(x): x < 0 (or -NaN), -0 excluded: a resting face (velocity -0)
+// moves nothing and costs nothing.
 __device__ __forceinline__ bool pos(double x) { return __double_as_longlong(x) > 0; }
-__device__ __forceinline__ bool neg(double x) { return __double_as_longlong(x) < 0; }
+__device__ __forceinline__ bool neg(double x)
+{
+    const long long b = __double_as_longlong(x);
+    return b < 0 && (b << 1) != 0;
+}
 __device__ __forceinline__ bool pos(float x) { return __float_as_int(x) > 0; }
-__device__ __forceinline__ bool neg(float x) { return __float_as_int(x) < 0; }
+__device__ __forceinline__ bool neg(float x)
+{
+    const int b = __float_as_int(x);
+    return b < 0 && (b << 1) != 0;
+}
 __device__ __forceinline__ bool is_nan(double x)
 {
     return (__double_as_longlong(x) & 0x7fffffffffffffffLL) > 0x7ff0000000000000LL;

@@ -1,6 +1,8 @@
 """Tensor-core kernels of the crater-surrogate MLP against the FP64 oracle.
 
-The GEMM is compared with exact FP64 sums of the same BF16 products.  The network's
+The GEMM is compared with exact FP64 sums of the same BF16 products, on both of its
+paths: operands gathered by threads (any strides) and operands streamed by TMA (K-major
+rows of 16-byte multiples).  The network's
 forward pass, gradient and Adam step are compared with the oracle in its BF16 form, which
 rounds the same tensors to BF16 and does all arithmetic in FP64; the remaining differences
 come from FP32 accumulation and FP32 GELU, which move a BF16 rounding of an activation or a
@@ -36,6 +38,9 @@ def _bf16(a):
     (130, 66, 520, False, True),        # transposed B
     (66, 5, 4096, True, True),          # weight-gradient shape: long K, tiny N
     (64, 256, 0, False, False),         # empty sum
+    (257, 300, 256, False, False),      # K-major, 16-byte rows: TMA path, NT = 256 and a 44-row tail
+    (512, 128, 1024, False, False),     # TMA path, 16 K slices through the 4-stage ring
+    (4100, 66, 256, False, False),      # TMA path, many M tiles, N not a multiple of 16
 ])
 def test_gemm_matches_exact_sums(M_, N_, K_, at, bt):
     rng = np.random.default_rng(M_ * 7 + N_ * 13 + K_)

@@ -206,3 +206,32 @@ def test_crater_readout_matches_oracle():
     assert np.allclose(cg["heights"], h, rtol=0, atol=1e-6)
     assert abs(cg["depth"] - d) < 1e-6 and abs(cg["diameter"] - D) < 1e-6
     assert np.allclose(cg["profile"], prof, rtol=0, atol=1e-6)
+
+
+@pytest.mark.slow
+def test_large_4000x4000_full_size_three_steps():
+    """The workload the benchmark times, at its full size (1.6e7 cells) and in its launch
+    configuration (default block shapes): three steps on the GPU and in the oracle
+    (about 20 s of serial CPU), every gated quantity within the FP64 bar."""
+    spec = W.large_4000()
+    g, r = _pair(spec, 3)
+    _assert_parity(g, r, spec)
+
+
+def test_batched_impact_draw_against_oracle():
+    """One draw of the batched impact distribution (strength, two materials, gravity,
+    PML 40 with relaxed auxiliaries) on a reduced grid, stepped through the batched
+    kernels, against the oracle: the batch runs the single-run code."""
+    d = W.batched_draw(9)           # iron, radius 12 cells, 16 km/s
+    spec = W.batched_run(d, 120)
+    g = salec.Sim(spec)
+    b = salec.Batch([g])
+    r = O.OracleSim(spec)
+    b.step(40)
+    r.step(40)
+    r2 = U.perturbed(O.OracleSim(spec))
+    r2.step(40)
+    sens = U.gated(U.parity(r2, r, spec))
+    s2, s1 = r2.scalars(), r.scalars()
+    sens.update({k: abs(s2[k] - s1[k]) / s1[k] for k in ("t", "dt")})
+    _assert_parity(g, r, spec, sensitivity=sens)
