@@ -258,6 +258,11 @@ __device__ __forceinline__ bool is_nan(float x) { return (__float_as_int(x) & 0x
 // x != 0 (either sign of zero counts as zero) on the bit pattern
 __device__ __forceinline__ bool nonzero(double x) { return (__double_as_longlong(x) << 1) != 0; }
 __device__ __forceinline__ bool nonzero(float x) { return (__float_as_int(x) << 1) != 0; }
+// Any active lane of the warp: a warp-uniform branch condition.  Guarding FP64 work with it
+// keeps the compiler from turning a rarely taken branch into predicated instructions that
+// every warp would issue (FP64 instructions occupy the FP64 pipe even when predicated off);
+// warps of resting cells then skip them entirely.
+__device__ __forceinline__ bool warp_any(bool p) { return __any_sync(__activemask(), p); }
 // the step's dt in the element type: the FP32 copy needs no FP64 conversion
 template <typename T> __device__ __forceinline__ T step_dt(const DevScalars* s);
 template <> __device__ __forceinline__ double step_dt<double>(const DevScalars* s) { return s->dt; }

@@ -328,7 +328,10 @@ __device__ __forceinline__ void body_phase2(const ParamsT<T>& P, int bx, int by,
     const double Ic = p.I[c];
     // the specific internal energy is accumulated in FP64 in every form
     // no energy change: no FP64 instruction (the sum would return Ic unchanged)
-    p.IL[c] = (pos(M) && nonzero(dE)) ? Ic + double(dE / M) : Ic;
+    const bool add_dE = pos(M) && nonzero(dE);
+    double ILnew = Ic;
+    if (warp_any(add_dE) && add_dE) ILnew = Ic + double(dE / M);
+    p.IL[c] = ILnew;
     p.VL[c] = VLc;
     // volume partition: matter and void share every volume change in proportion to their
     // fractions (equal strain), so each material's work -p_m dV_m adds up to the -P dV the
@@ -479,14 +482,16 @@ __device__ __forceinline__ void body_phase3a(const ParamsT<T>& P, int bx, int by
         {
             const T dV = radial_dV<T>(P, i, j, dt);
             T sm = zero;
-            if (pos(dV)) { move<T, NM, STR>(P, c - 1, dV, one, ILc, strip, acc, fm, fe); sm = fm; FRm -= fm; FRe -= fe; }
+            if (!warp_any(nonzero(dV))) {
+            } else if (pos(dV)) { move<T, NM, STR>(P, c - 1, dV, one, ILc, strip, acc, fm, fe); sm = fm; FRm -= fm; FRe -= fe; }
             else if (neg(dV)) { move<T, NM, STR>(P, c, -dV, -one, ILc, strip, acc, fm, fe); sm = -fm; FRm += fm; FRe += fe; }
             p.dMR[j * (nr + 1) + i] = sm;
         }
         // right face r_{i+1}
         {
             const T dV = radial_dV<T>(P, i + 1, j, dt);
-            if (pos(dV)) { move<T, NM, STR>(P, c, dV, -one, ILc, strip, acc, fm, fe); FRm += fm; FRe += fe; }
+            if (!warp_any(nonzero(dV))) {
+            } else if (pos(dV)) { move<T, NM, STR>(P, c, dV, -one, ILc, strip, acc, fm, fe); FRm += fm; FRe += fe; }
             else if (neg(dV)) { move<T, NM, STR>(P, c + 1, -dV, one, ILc, strip, acc, fm, fe); FRm -= fm; FRe -= fe; }
             if (i == nr - 1) p.dMR[j * (nr + 1) + nr] = zero;
         }
@@ -494,7 +499,8 @@ __device__ __forceinline__ void body_phase3a(const ParamsT<T>& P, int bx, int by
         {
             const T dV = vertical_dV<T>(P, i, j, dt);
             T sm = zero;
-            if (pos(dV)) { move<T, NM, STR>(P, c - nr, dV, one, ILc, strip, acc, fm, fe); sm = fm; FZm -= fm; FZe -= fe; }
+            if (!warp_any(nonzero(dV))) {
+            } else if (pos(dV)) { move<T, NM, STR>(P, c - nr, dV, one, ILc, strip, acc, fm, fe); sm = fm; FZm -= fm; FZe -= fe; }
             else if (neg(dV)) { move<T, NM, STR>(P, c, -dV, -one, ILc, strip, acc, fm, fe); sm = -fm; FZm += fm; FZe += fe; }
             p.dMZ[j * nr + i] = sm;
         }
@@ -502,7 +508,8 @@ __device__ __forceinline__ void body_phase3a(const ParamsT<T>& P, int bx, int by
         {
             const T dV = vertical_dV<T>(P, i, j + 1, dt);
             T sm = zero;
-            if (pos(dV)) {
+            if (!warp_any(nonzero(dV))) {
+            } else if (pos(dV)) {
                 move<T, NM, STR>(P, c, dV, -one, ILc, strip, acc, fm, fe);
                 FZm += fm; FZe += fe; sm = fm;
                 if (j == nz - 1) t_out += double(fm);
@@ -529,7 +536,9 @@ __device__ __forceinline__ void body_phase3a(const ParamsT<T>& P, int bx, int by
             rn[m] = pos(Vm[m]) ? fl.y + (acc.Mm[m] - fl.y * acc.Vm[m]) / Vm[m] : zero;
         }
         const T Mtot = MLtot + dMtot, Vtot = VLmat + dVtot;
-        double Ic = pos(Mtot) ? (nonzero(acc.dI) ? ILc + double(acc.dI / Mtot) : ILc) : 0.0;
+        double Ic = pos(Mtot) ? ILc : 0.0;
+        const bool add_dI = pos(Mtot) && nonzero(acc.dI);
+        if (warp_any(add_dI) && add_dI) Ic = ILc + double(acc.dI / Mtot);
         T s0 = zero, s1 = zero, s2 = zero, Dm = zero;
         if (STR && pos(Vtot)) {
             const T iv = one / Vtot;
@@ -544,7 +553,7 @@ __device__ __forceinline__ void body_phase3a(const ParamsT<T>& P, int bx, int by
         for (int m = 0; m < NM; ++m) {
             fnew[m] = Vm[m] / Vc;    // a true division: exact 1 for a full resting cell
             if (fnew[m] < P.f_min) {
-                t_disc += double(Mm[m]);
+                if (warp_any(nonzero(Mm[m])) && nonzero(Mm[m])) t_disc += double(Mm[m]);
                 Vm[m] = zero;
                 Mm[m] = zero;
                 rn[m] = zero;
@@ -685,7 +694,7 @@ __device__ __forceinline__ void body_phase3b(const ParamsT<T>& P, int bx, int by
             const typename V::T2 w = (pos(f) || j == nz) ? vL : p.vL[v + nv];
             outZr = f * w.x; outZz = f * w.y;
             m -= f; kin -= half * f * (w.x * w.x + w.y * w.y);
-            if (j == nz) t_zmom += double(outZz);
+            if (warp_any(j == nz) && j == nz) t_zmom += double(outZz);
         }
         pr += (inRr - outRr) + (inZr - outZr);
         pz += (inRz - outRz) + (inZz - outZz);
@@ -770,7 +779,7 @@ __device__ __forceinline__ void body_phase3c(const ParamsT<T>& P, int bx, int by
         if (pos(M)) {
             const T add = T(0.25) * (p.kheat[j * nv + i] + p.kheat[j * nv + i + 1] +
                                      p.kheat[(j + 1) * nv + i + 1] + p.kheat[(j + 1) * nv + i]);
-            if (nonzero(add)) p.I[c] += double(add);
+            if (warp_any(nonzero(add)) && nonzero(add)) p.I[c] += double(add);
         }
     }
     if (bx == 0 && by == 0 && threadIdx.x == 0 && threadIdx.y == 0) {
