@@ -580,9 +580,9 @@ def main():
 # FP64 operations per cell (2 DFMA + DADD + DMUL) issued by each FP64-form kernel on the
 # 4000 x 4000 physics, and DRAM bytes per cell, from ncu on the 2000 x 2000 case
 # (profiles/); refreshed whenever the kernels change.
-_FLOPS_PER_CELL: dict = {"k_phase0": 85.8, "k_phase1": 49.6, "k_phase2": 38.7, "k_phase3a": 75.9, "k_phase3b": 85.0, "k_phase3c": 4.8}
-_TRAFFIC_PER_CELL: dict = {"k_phase0": 58.0, "k_phase1": 72.2, "k_phase2": 75.6, "k_phase3a": 78.4, "k_phase3b": 80.5, "k_phase3c": 22.2}
-_TRAFFIC_PER_CELL_FP32MIX: dict = {"k_phase0": 28.2, "k_phase1": 31.5, "k_phase2": 40.0, "k_phase3a": 41.7, "k_phase3b": 37.9, "k_phase3c": 10.8}
+_FLOPS_PER_CELL: dict = {"k_phase0": 85.8, "k_phase1": 49.6, "k_phase2": 38.7, "k_phase3a": 75.9, "k_phase3b": 70.4, "k_phase3c": 4.8}
+_TRAFFIC_PER_CELL: dict = {"k_phase0": 58.0, "k_phase1": 72.2, "k_phase2": 75.6, "k_phase3a": 78.4, "k_phase3b": 63.4, "k_phase3c": 22.2}
+_TRAFFIC_PER_CELL_FP32MIX: dict = {"k_phase0": 28.2, "k_phase1": 31.5, "k_phase2": 40.0, "k_phase3a": 41.7, "k_phase3b": 30.0, "k_phase3c": 10.8}
 
 if __name__ == "__main__":
     sys.exit(main())

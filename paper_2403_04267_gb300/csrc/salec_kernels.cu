@@ -698,11 +698,18 @@ __device__ __forceinline__ void body_phase3b(const ParamsT<T>& P, int bx, int by
         }
         pr += (inRr - outRr) + (inZr - outZr);
         pz += (inRz - outRz) + (inZz - outZz);
+        // a resting vertex (no momentum, no kinetic energy, no flux, no deficit) gets no heat
+        // and, unless a strip's damping gives it momentum below, no velocity: its warp skips
+        // the reciprocal and the rest (the results are the same zeros)
+        const T dKv = p.dK[v];
+        const bool quiet = !nonzero(pr) && !nonzero(pz) && !nonzero(kin) && !nonzero(dKv);
         T kheat = zero, im = zero;
-        if (pos(m)) {
+        bool have_im = false;
+        if (pos(m) && warp_any(!quiet) && !quiet) {
             im = one / m;
+            have_im = true;
             const T dKr = kin - half * (pr * pr + pz * pz) * im;
-            kheat = (p.dK[v] + dKr) * im;
+            kheat = (dKv + dKr) * im;
         }
         p.kheat[v] = kheat;
         T dsum = zero, a2r = zero, a2z = zero;
@@ -729,18 +736,25 @@ __device__ __forceinline__ void body_phase3b(const ParamsT<T>& P, int bx, int by
             pr = pr - dt * (dsum * pr + a2r);
             pz = pz - dt * (dsum * pz + a2z);
         }
-        // no material in any adjacent cell after the clean-up: no momentum (the dual mass
-        // is then only round-off of the fluxes)
-        bool occupied = false;
-#pragma unroll
-        for (int k = 0; k < 4; ++k) {
-            const int ci = (k == 0 || k == 3) ? i - 1 : i;
-            const int cj = (k < 2) ? j - 1 : j;
-            if (ci < 0 || ci >= nr || cj < 0 || cj >= nz) continue;
-            for (int mm = 0; mm < P.nmat; ++mm) occupied |= pos(p.fr[mm][cj * nr + ci].x);
-        }
         T vr = zero, vz = zero;
-        if (pos(m) && occupied) { vr = pr * im; vz = pz * im; }
+        const bool moving = nonzero(pr) || nonzero(pz);
+        if (pos(m) && warp_any(moving) && moving) {
+            // no material in any adjacent cell after the clean-up: no momentum (the dual
+            // mass is then only round-off of the fluxes)
+            bool occupied = false;
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const int ci = (k == 0 || k == 3) ? i - 1 : i;
+                const int cj = (k < 2) ? j - 1 : j;
+                if (ci < 0 || ci >= nr || cj < 0 || cj >= nz) continue;
+                for (int mm = 0; mm < P.nmat; ++mm) occupied |= pos(p.fr[mm][cj * nr + ci].x);
+            }
+            if (occupied) {
+                if (!have_im) im = one / m;
+                vr = pr * im;
+                vz = pz * im;
+            }
+        }
         if (i == 0 || i == nr) vr = zero;
         if (j == 0) {
             vz = zero;
