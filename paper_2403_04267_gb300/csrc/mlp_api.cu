@@ -278,6 +278,14 @@ salec_status salec_mlp_forward(salec_mlp* n, const float* x_dev, int batch, floa
     if (st != SALEC_OK) return st;
     if (!x_dev || !y_dev) return fail(n, SALEC_EINVAL, "null pointer");
     MLP_CUDA(n, launch_inputs_bf16(x_dev, batch, SALEC_MLP_IN, kInLd, n->X, n->stream), "mlp input");
+    // all five layers in one kernel, activations on chip; the layer-by-layer GEMMs when
+    // the weights cannot be addressed by TMA
+    FusedLaunch f;
+    f.B = batch; f.X = n->X; f.ld_x = kInLd; f.Y = y_dev; f.err = n->errflag;
+    for (int l = 0; l < kLayers; ++l) { f.W[l] = n->wbf + n->wbf_off[l]; f.bias[l] = n->theta + n->boff[l]; }
+    const cudaError_t e = launch_mlp_forward_fused(f, n->stream);
+    if (e == cudaSuccess) return SALEC_OK;
+    if (e != cudaErrorNotSupported) return cuda_fail(n, e, "mlp fused forward");
     return forward_impl(n, batch, y_dev, SALEC_MLP_OUT, nullptr, false);
 }
 

@@ -38,11 +38,25 @@ struct GemmArgs {
     int nt, tmem_cols;        // set by the launcher
 };
 
+constexpr int SALEC_MLP_OUT_N = 66;
+
+// the fused inference pass: inputs, weights (BF16, W_1 rows padded like X), biases, outputs
+struct FusedLaunch {
+    int B;
+    const __nv_bfloat16* X;
+    int ld_x;
+    const __nv_bfloat16* W[5];
+    const float* bias[5];
+    float* Y;
+    int* err;
+};
+
 struct AdamArgs {
     float lr, beta1, beta2, eps, c1, c2;   // c1 = 1 / (1 - beta1^t), c2 = 1 / (1 - beta2^t)
 };
 
 cudaError_t launch_gemm(const GemmArgs& g, cudaStream_t s);
+cudaError_t launch_mlp_forward_fused(const FusedLaunch& f, cudaStream_t s);
 cudaError_t launch_colsum(const __nv_bfloat16* G, int M, int N, long ldg, float* out, cudaStream_t s);
 cudaError_t launch_inputs_bf16(const float* x, int rows, int cols, int ld, __nv_bfloat16* y, cudaStream_t s);
 cudaError_t launch_adam(float* theta, float* m1, float* m2, const float* grad, long n, const AdamArgs& a,

@@ -435,6 +435,156 @@ __global__ void __launch_bounds__(kGemmThreads) k_gemm_bf16_tma(const __grid_con
     }
 }
 
+// ---------------------------------------------------------------------------------------
+// The whole network's forward pass in one kernel (inference).  A CTA takes 128 samples;
+// their activations never leave the SM: each layer's epilogue writes gelu(Z) as BF16
+// straight into shared memory in the canonical K-major layout, where it is the next
+// layer's A operand.  The accumulator (128 x 256 FP32) lives in tensor memory.  Weights
+// stream from L2 with TMA, one 64-wide K slice (256 rows x 128 bytes) at a time, while
+// the other CTA on the SM computes.  Shared memory: activations 64 KB + one weight
+// stage 32 KB, so two CTAs fit on an SM (and 2 x 256 of its 512 TMEM columns).
+// ---------------------------------------------------------------------------------------
+constexpr int kFusedHid = 256;
+constexpr int kFusedOutPad = 80;      // 66 outputs padded to a multiple of 16
+constexpr uint32_t kHBytes = kBM * kFusedHid * 2;          // 65536
+constexpr uint32_t kWStageBytes = kFusedHid * kBK * 2;     // 32768
+
+size_t fused_smem_bytes() { return (size_t)kHBytes + kWStageBytes + 1024; }
+
+struct FusedArgs {
+    int B;                                   // samples
+    const __nv_bfloat16* X;                  // [B][ld_x] BF16 inputs, columns >= 5 zero
+    int ld_x;
+    const __nv_bfloat16* W1;                 // [256][ld_x] BF16, columns >= 5 zero
+    const float* bias[5];
+    float* Y;                                // [B][66]
+    int* err;
+};
+
+// core-matrix offset of (row r, 8-column group kg) in a K-major tile of `rows` rows
+__device__ __forceinline__ uint32_t cm_off(int r, int kg, int rows) { return kg * (rows * 16) + (r >> 3) * 128 + (r & 7) * 16; }
+
+__global__ void __launch_bounds__(kGemmThreads) k_mlp_forward_fused(const __grid_constant__ CUtensorMap mW2,
+                                                                    const __grid_constant__ CUtensorMap mW3,
+                                                                    const __grid_constant__ CUtensorMap mW4,
+                                                                    const __grid_constant__ CUtensorMap mW5,
+                                                                    FusedArgs a)
+{
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    unsigned char* smem = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    unsigned char* H = smem;                    // activations, 32 column groups of 2048 B
+    unsigned char* Ws = smem + kHBytes;         // one weight stage
+    __shared__ uint64_t wbar, mbar;
+    __shared__ uint32_t tmem_holder;
+    __shared__ int ok_flag;
+
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int m0 = blockIdx.x * kBM;
+    const int r = warp * 32 + lane;             // this thread's row of the tile (TMEM lane)
+    const int m = m0 + r;
+    const uint32_t tmem_cols = kFusedHid;
+
+    if (tid == 0) {
+        mbar_init(&wbar, 1);
+        mbar_init(&mbar, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        ok_flag = 1;
+    }
+    __syncwarp();
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_holder)),
+                     "r"(tmem_cols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    // layer 1 operands by the threads: X rows (8 BF16 = one core-matrix row) and W1 rows,
+    // K padded to 16 with a zero column group
+    {
+        uint4 xv = make_uint4(0u, 0u, 0u, 0u);
+        if (m < a.B) xv = *reinterpret_cast<const uint4*>(a.X + (long)m * a.ld_x);
+        *reinterpret_cast<uint4*>(H + cm_off(r, 0, kBM)) = xv;
+        *reinterpret_cast<uint4*>(H + cm_off(r, 1, kBM)) = make_uint4(0u, 0u, 0u, 0u);
+        for (int n = tid; n < kFusedHid; n += kGemmThreads) {
+            *reinterpret_cast<uint4*>(Ws + cm_off(n, 0, kFusedHid)) = *reinterpret_cast<const uint4*>(a.W1 + (long)n * a.ld_x);
+            *reinterpret_cast<uint4*>(Ws + cm_off(n, 1, kFusedHid)) = make_uint4(0u, 0u, 0u, 0u);
+        }
+    }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = tmem_holder;
+    const uint32_t trow = tmem + ((uint32_t)(warp * 32) << 16);
+    const uint32_t hbase = smem_u32(H), wbase = smem_u32(Ws);
+    uint32_t wphase = 0, mphase = 0;     // completed phases of the two barriers (same in every thread)
+    bool good = true;
+
+    for (int layer = 0; layer < 5; ++layer) {
+        const int N = layer == 4 ? kFusedOutPad : kFusedHid;
+        const uint32_t idesc = idesc_bf16(kBM, N);
+        const CUtensorMap* map = layer == 1 ? &mW2 : layer == 2 ? &mW3 : layer == 3 ? &mW4 : &mW5;
+        const int nslices = layer == 0 ? 1 : kFusedHid / kBK;
+        for (int kt = 0; kt < nslices; ++kt) {
+            if (tid == 0 && good) {
+                if (layer > 0) {
+                    // the stage is free: the previous slice's MMAs were waited for below
+                    mbar_expect_tx(&wbar, (uint32_t)N * kBK * 2);
+#pragma unroll
+                    for (int kg = 0; kg < kBK / 8; ++kg) tma_load_2d(wbase + kg * (N * 16), map, kt * kBK + 8 * kg, 0, &wbar);
+                    good = mbar_wait(&wbar, wphase & 1u);
+                }
+                if (good) {
+                    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                    const int kks = layer == 0 ? 1 : kBK / 16;
+                    for (int kk = 0; kk < kks; ++kk) {
+                        const uint64_t ad = sdesc(hbase + (kt * (kBK / 8) + 2 * kk) * (kBM * 16), kBM * 16, 128);
+                        const uint64_t bd = sdesc(wbase + 2 * kk * (N * 16), N * 16, 128);
+                        mma_bf16(tmem, ad, bd, idesc, (kt > 0 || kk > 0) ? 1u : 0u);
+                    }
+                    mma_commit(&mbar);
+                    good = mbar_wait(&mbar, mphase & 1u);
+                }
+                if (!good) ok_flag = 0;
+            }
+            if (layer > 0) ++wphase;
+            ++mphase;
+        }
+        __syncthreads();                 // every MMA of the layer is done (or the CTA gave up)
+        if (!ok_flag) break;
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const float* bias = a.bias[layer];
+        if (layer < 4) {
+            // gelu(Z) as BF16 into the activations, in the layout the next layer reads
+            for (int c0 = 0; c0 < kFusedHid; c0 += 16) {
+                float v[16];
+                tmem_ld16(trow + (uint32_t)c0, v);
+                union { uint4 u[2]; __nv_bfloat16 b[16]; } pk;
+#pragma unroll
+                for (int j = 0; j < 16; ++j) pk.b[j] = __float2bfloat16_rn(m < a.B ? gelu_f(v[j] + bias[c0 + j]) : 0.0f);
+                *reinterpret_cast<uint4*>(H + cm_off(r, (c0 >> 3), kBM)) = pk.u[0];
+                *reinterpret_cast<uint4*>(H + cm_off(r, (c0 >> 3) + 1, kBM)) = pk.u[1];
+            }
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        } else {
+            for (int c0 = 0; c0 < kFusedOutPad; c0 += 16) {
+                float v[16];
+                tmem_ld16(trow + (uint32_t)c0, v);
+                if (m < a.B)
+                    for (int j = 0; j < 16 && c0 + j < SALEC_MLP_OUT_N; ++j)
+                        a.Y[(long)m * SALEC_MLP_OUT_N + c0 + j] = v[j] + bias[c0 + j];
+            }
+        }
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        __syncthreads();
+    }
+    if (!ok_flag && tid == 0 && a.err) atomicOr(a.err, 4);
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 0) {
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(tmem_cols) : "memory");
+    }
+}
+
 // Column sums of a BF16 matrix (bias gradients): out[n] = sum_m G[m][n].
 __global__ void k_colsum(const __nv_bfloat16* __restrict__ G, int M, int N, long ldg, float* __restrict__ out)
 {
@@ -574,6 +724,33 @@ cudaError_t launch_gemm(const GemmArgs& g0, cudaStream_t s)
     }
     dim3 grid((unsigned)((g.M + kBM - 1) / kBM), (unsigned)((g.N + nt - 1) / nt));
     k_gemm_bf16<<<grid, kGemmThreads, smem, s>>>(g);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_mlp_forward_fused(const FusedLaunch& f, cudaStream_t s)
+{
+    if (f.B <= 0) return cudaSuccess;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+    CUtensorMap m2, m3, m4, m5;
+    if (!make_map(&m2, f.W[1], kFusedHid, kFusedHid, kFusedHid, kFusedHid) ||
+        !make_map(&m3, f.W[2], kFusedHid, kFusedHid, kFusedHid, kFusedHid) ||
+        !make_map(&m4, f.W[3], kFusedHid, kFusedHid, kFusedHid, kFusedHid) ||
+        !make_map(&m5, f.W[4], SALEC_MLP_OUT_N, kFusedHid, kFusedHid, kFusedOutPad))
+        return cudaErrorNotSupported;
+    static bool attr[64] = {};
+    if (!attr[dev]) {
+        e = cudaFuncSetAttribute(k_mlp_forward_fused, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fused_smem_bytes());
+        if (e != cudaSuccess) return e;
+        attr[dev] = true;
+    }
+    FusedArgs a;
+    a.B = f.B; a.X = f.X; a.ld_x = f.ld_x; a.W1 = f.W[0];
+    for (int l = 0; l < 5; ++l) a.bias[l] = f.bias[l];
+    a.Y = f.Y; a.err = f.err;
+    k_mlp_forward_fused<<<(unsigned)((f.B + kBM - 1) / kBM), kGemmThreads, fused_smem_bytes(), s>>>(m2, m3, m4, m5, a);
     return cudaGetLastError();
 }
 

@@ -75,10 +75,13 @@ def _data(B, seed=5):
     return X, T
 
 
-def test_forward_matches_oracle():
+@pytest.mark.parametrize("B", [300, 1000, 1])
+def test_forward_matches_oracle(B):
+    """The inference pass (one fused kernel: five layers per 128-sample tile, activations
+    kept on chip) against the oracle's BF16 form; ragged last tiles and a single sample."""
     theta = _net()
-    X, _ = _data(300)
-    net = S.MLP(512)
+    X, _ = _data(B)
+    net = S.MLP(1024)
     net.set_params(theta)
     y = net.forward(torch.from_numpy(X).cuda()).cpu().numpy().astype(np.float64)
     ref, _ = M.forward(theta, X.astype(np.float64), bf16=True)
