@@ -126,10 +126,38 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v)
     for (int j = 0; j < 16; ++j) v[j] = __uint_as_float(r[j]);
 }
 
-__device__ __forceinline__ float gelu_f(float z) { return 0.5f * z * (1.0f + erff(z * 0.70710678118654752f)); }
+// The normal CDF Phi(z) = (1 + erf(z / sqrt 2)) / 2, with the complementary error function
+// of Abramowitz & Stegun, Handbook of Mathematical Functions, formula 7.1.26: for x >= 0,
+// erfc(x) = t (a1 + t (a2 + t (a3 + t (a4 + t a5)))) exp(-x^2) + e(x), t = 1 / (1 + p x),
+// |e(x)| <= 1.5e-7.  Phi(z) is 1 - erfc(x) / 2 for z >= 0 and erfc(x) / 2 for z < 0
+// (x = |z| / sqrt 2), so the left tail is formed without cancellation.  Also returns
+// exp(-z^2 / 2) (the same exponential), which the GELU derivative needs.  The error is far
+// below the BF16 rounding (2^-9 relative) that every activation goes through.
+__device__ __forceinline__ float normal_cdf(float z, float* gauss)
+{
+    const float x = fabsf(z) * 0.70710678118654752f;
+    const float t = __fdividef(1.0f, fmaf(0.3275911f, x, 1.0f));
+    float pol = fmaf(t, 1.061405429f, -1.453152027f);
+    pol = fmaf(t, pol, 1.421413741f);
+    pol = fmaf(t, pol, -0.284496736f);
+    pol = fmaf(t, pol, 0.254829592f);
+    const float e = __expf(-x * x);
+    *gauss = e;
+    const float half_erfc = 0.5f * (pol * t) * e;
+    return z >= 0.0f ? 1.0f - half_erfc : half_erfc;
+}
+
+// GELU in its erf form, z Phi(z), and its derivative Phi(z) + z phi(z)
+__device__ __forceinline__ float gelu_f(float z)
+{
+    float e;
+    return z * normal_cdf(z, &e);
+}
 __device__ __forceinline__ float gelu_grad_f(float z)
 {
-    return 0.5f * (1.0f + erff(z * 0.70710678118654752f)) + z * expf(-0.5f * z * z) * 0.39894228040143268f;
+    float e;
+    const float P = normal_cdf(z, &e);
+    return fmaf(z * 0.39894228040143268f, e, P);
 }
 
 // Gather 8 consecutive-in-k elements of row r into one 16-byte core-matrix row.
@@ -440,12 +468,17 @@ __global__ void __launch_bounds__(kGemmThreads) k_gemm_bf16_tma(const __grid_con
 // their activations never leave the SM: each layer's epilogue writes gelu(Z) as BF16
 // straight into shared memory in the canonical K-major layout, where it is the next
 // layer's A operand.  The accumulator (128 x 256 FP32) lives in tensor memory.  Weights
-// stream from L2 with TMA, one 64-wide K slice (256 rows x 128 bytes) at a time, while
-// the other CTA on the SM computes.  Shared memory: activations 64 KB + one weight
-// stage 32 KB, so two CTAs fit on an SM (and 2 x 256 of its 512 TMEM columns).
+// stream from L2 with TMA, one 64-wide K slice (256 rows x 128 bytes) at a time; the first
+// slice of the next layer is issued as soon as a layer's last MMAs are done, so it lands
+// while the epilogue runs.  Shared memory: activations 64 KB + one weight stage 32 KB, so
+// two CTAs fit on an SM (and 2 x 256 of its 512 TMEM columns), each overlapping its MMA
+// chain with the other's epilogue.  The epilogue is the bulk of the instructions (an erf
+// per element), so it is spread over 16 warps: warp w reads TMEM lanes 32 (w mod 4) ..
+// + 31 (its rows) and column quarter w / 4 (64 columns).
 // ---------------------------------------------------------------------------------------
 constexpr int kFusedHid = 256;
 constexpr int kFusedOutPad = 80;      // 66 outputs padded to a multiple of 16
+constexpr int kFusedThreads = 512;
 constexpr uint32_t kHBytes = kBM * kFusedHid * 2;          // 65536
 constexpr uint32_t kWStageBytes = kFusedHid * kBK * 2;     // 32768
 
@@ -464,23 +497,26 @@ struct FusedArgs {
 // core-matrix offset of (row r, 8-column group kg) in a K-major tile of `rows` rows
 __device__ __forceinline__ uint32_t cm_off(int r, int kg, int rows) { return kg * (rows * 16) + (r >> 3) * 128 + (r & 7) * 16; }
 
-__global__ void __launch_bounds__(kGemmThreads) k_mlp_forward_fused(const __grid_constant__ CUtensorMap mW2,
-                                                                    const __grid_constant__ CUtensorMap mW3,
-                                                                    const __grid_constant__ CUtensorMap mW4,
-                                                                    const __grid_constant__ CUtensorMap mW5,
-                                                                    FusedArgs a)
+__global__ void __launch_bounds__(kFusedThreads, 2) k_mlp_forward_fused(const __grid_constant__ CUtensorMap mW2,
+                                                                        const __grid_constant__ CUtensorMap mW3,
+                                                                        const __grid_constant__ CUtensorMap mW4,
+                                                                        const __grid_constant__ CUtensorMap mW5,
+                                                                        FusedArgs a)
 {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     unsigned char* smem = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
     unsigned char* H = smem;                    // activations, 32 column groups of 2048 B
     unsigned char* Ws = smem + kHBytes;         // one weight stage
+    __shared__ __align__(16) float sbias[4 * kFusedHid + kFusedOutPad];
     __shared__ uint64_t wbar, mbar;
     __shared__ uint32_t tmem_holder;
     __shared__ int ok_flag;
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int m0 = blockIdx.x * kBM;
-    const int r = warp * 32 + lane;             // this thread's row of the tile (TMEM lane)
+    const int quarter = warp & 3;               // TMEM lanes 32 quarter .. + 31 (rows of the tile)
+    const int cq = warp >> 2;                   // column quarter of the epilogue
+    const int r = quarter * 32 + lane;          // this thread's row of the tile
     const int m = m0 + r;
     const uint32_t tmem_cols = kFusedHid;
 
@@ -497,87 +533,129 @@ __global__ void __launch_bounds__(kGemmThreads) k_mlp_forward_fused(const __grid
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
+    // biases of all layers (zero in the output layer's padding)
+    for (int k = tid; k < 4 * kFusedHid + kFusedOutPad; k += kFusedThreads) {
+        const int l = k / kFusedHid, n = k - l * kFusedHid;
+        sbias[k] = l < 4 ? a.bias[l][n] : (n < SALEC_MLP_OUT_N ? a.bias[4][n] : 0.0f);
+    }
     // layer 1 operands by the threads: X rows (8 BF16 = one core-matrix row) and W1 rows,
     // K padded to 16 with a zero column group
-    {
+    if (tid < kBM) {
         uint4 xv = make_uint4(0u, 0u, 0u, 0u);
-        if (m < a.B) xv = *reinterpret_cast<const uint4*>(a.X + (long)m * a.ld_x);
-        *reinterpret_cast<uint4*>(H + cm_off(r, 0, kBM)) = xv;
-        *reinterpret_cast<uint4*>(H + cm_off(r, 1, kBM)) = make_uint4(0u, 0u, 0u, 0u);
-        for (int n = tid; n < kFusedHid; n += kGemmThreads) {
-            *reinterpret_cast<uint4*>(Ws + cm_off(n, 0, kFusedHid)) = *reinterpret_cast<const uint4*>(a.W1 + (long)n * a.ld_x);
-            *reinterpret_cast<uint4*>(Ws + cm_off(n, 1, kFusedHid)) = make_uint4(0u, 0u, 0u, 0u);
-        }
+        if (m0 + tid < a.B) xv = *reinterpret_cast<const uint4*>(a.X + (long)(m0 + tid) * a.ld_x);
+        *reinterpret_cast<uint4*>(H + cm_off(tid, 0, kBM)) = xv;
+        *reinterpret_cast<uint4*>(H + cm_off(tid, 1, kBM)) = make_uint4(0u, 0u, 0u, 0u);
+    } else if (tid < kBM + kFusedHid) {
+        const int n = tid - kBM;
+        *reinterpret_cast<uint4*>(Ws + cm_off(n, 0, kFusedHid)) = *reinterpret_cast<const uint4*>(a.W1 + (long)n * a.ld_x);
+        *reinterpret_cast<uint4*>(Ws + cm_off(n, 1, kFusedHid)) = make_uint4(0u, 0u, 0u, 0u);
     }
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const uint32_t tmem = tmem_holder;
-    const uint32_t trow = tmem + ((uint32_t)(warp * 32) << 16);
+    const uint32_t trow = tmem + ((uint32_t)(quarter * 32) << 16);
     const uint32_t hbase = smem_u32(H), wbase = smem_u32(Ws);
-    uint32_t wphase = 0, mphase = 0;     // completed phases of the two barriers (same in every thread)
+    uint32_t wphase = 0, mphase = 0;     // completed phases of the two barriers (thread 0's view)
     bool good = true;
+    bool in_flight = false, mma_pending = false;  // thread 0: a weight load / MMAs not yet waited for
+
+    // thread 0: TMA of K slice kt of layer l's weights into the stage
+    auto load_slice = [&](int l, int kt) {
+        const int N = l == 4 ? kFusedOutPad : kFusedHid;
+        const CUtensorMap* map = l == 1 ? &mW2 : l == 2 ? &mW3 : l == 3 ? &mW4 : &mW5;
+        mbar_expect_tx(&wbar, (uint32_t)N * kBK * 2);
+#pragma unroll
+        for (int kg = 0; kg < kBK / 8; ++kg) tma_load_2d(wbase + kg * (N * 16), map, kt * kBK + 8 * kg, 0, &wbar);
+        in_flight = true;
+    };
 
     for (int layer = 0; layer < 5; ++layer) {
         const int N = layer == 4 ? kFusedOutPad : kFusedHid;
         const uint32_t idesc = idesc_bf16(kBM, N);
-        const CUtensorMap* map = layer == 1 ? &mW2 : layer == 2 ? &mW3 : layer == 3 ? &mW4 : &mW5;
         const int nslices = layer == 0 ? 1 : kFusedHid / kBK;
-        for (int kt = 0; kt < nslices; ++kt) {
-            if (tid == 0 && good) {
+        if (tid == 0) {
+            for (int kt = 0; kt < nslices && good; ++kt) {
                 if (layer > 0) {
-                    // the stage is free: the previous slice's MMAs were waited for below
-                    mbar_expect_tx(&wbar, (uint32_t)N * kBK * 2);
-#pragma unroll
-                    for (int kg = 0; kg < kBK / 8; ++kg) tma_load_2d(wbase + kg * (N * 16), map, kt * kBK + 8 * kg, 0, &wbar);
+                    // slice 0 was issued at the end of the previous layer; the stage is free
+                    // for the others because the previous slice's MMAs were waited for
+                    if (kt > 0) load_slice(layer, kt);
                     good = mbar_wait(&wbar, wphase & 1u);
+                    if (!good) break;
+                    in_flight = false;
+                    ++wphase;
                 }
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                const int kks = layer == 0 ? 1 : kBK / 16;
+                for (int kk = 0; kk < kks; ++kk) {
+                    const uint64_t ad = sdesc(hbase + (kt * (kBK / 8) + 2 * kk) * (kBM * 16), kBM * 16, 128);
+                    const uint64_t bd = sdesc(wbase + 2 * kk * (N * 16), N * 16, 128);
+                    mma_bf16(tmem, ad, bd, idesc, (kt > 0 || kk > 0) ? 1u : 0u);
+                }
+                mma_commit(&mbar);
+                mma_pending = true;
+                good = mbar_wait(&mbar, mphase & 1u);
                 if (good) {
-                    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-                    const int kks = layer == 0 ? 1 : kBK / 16;
-                    for (int kk = 0; kk < kks; ++kk) {
-                        const uint64_t ad = sdesc(hbase + (kt * (kBK / 8) + 2 * kk) * (kBM * 16), kBM * 16, 128);
-                        const uint64_t bd = sdesc(wbase + 2 * kk * (N * 16), N * 16, 128);
-                        mma_bf16(tmem, ad, bd, idesc, (kt > 0 || kk > 0) ? 1u : 0u);
-                    }
-                    mma_commit(&mbar);
-                    good = mbar_wait(&mbar, mphase & 1u);
+                    mma_pending = false;
+                    ++mphase;
                 }
-                if (!good) ok_flag = 0;
             }
-            if (layer > 0) ++wphase;
-            ++mphase;
+            // every MMA of the layer is done: the next layer's first slice can land while
+            // the epilogue below runs
+            if (good && layer < 4) load_slice(layer + 1, 0);
+            if (!good) ok_flag = 0;
         }
         __syncthreads();                 // every MMA of the layer is done (or the CTA gave up)
         if (!ok_flag) break;
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        const float* bias = a.bias[layer];
+        const float* bias = sbias + layer * kFusedHid;
         if (layer < 4) {
             // gelu(Z) as BF16 into the activations, in the layout the next layer reads
-            for (int c0 = 0; c0 < kFusedHid; c0 += 16) {
+            const bool live = m < a.B;
+#pragma unroll 1
+            for (int c0 = cq * 64; c0 < cq * 64 + 64; c0 += 16) {
                 float v[16];
                 tmem_ld16(trow + (uint32_t)c0, v);
-                union { uint4 u[2]; __nv_bfloat16 b[16]; } pk;
+                uint32_t w[8] = {0u, 0u, 0u, 0u, 0u, 0u, 0u, 0u};
+                if (live) {
+                    const float4* b4 = reinterpret_cast<const float4*>(bias + c0);
 #pragma unroll
-                for (int j = 0; j < 16; ++j) pk.b[j] = __float2bfloat16_rn(m < a.B ? gelu_f(v[j] + bias[c0 + j]) : 0.0f);
-                *reinterpret_cast<uint4*>(H + cm_off(r, (c0 >> 3), kBM)) = pk.u[0];
-                *reinterpret_cast<uint4*>(H + cm_off(r, (c0 >> 3) + 1, kBM)) = pk.u[1];
+                    for (int q = 0; q < 4; ++q) {
+                        const float4 b = b4[q];
+                        const __nv_bfloat162 lo = __floats2bfloat162_rn(gelu_f(v[4 * q] + b.x), gelu_f(v[4 * q + 1] + b.y));
+                        const __nv_bfloat162 hi = __floats2bfloat162_rn(gelu_f(v[4 * q + 2] + b.z), gelu_f(v[4 * q + 3] + b.w));
+                        w[2 * q] = *reinterpret_cast<const uint32_t*>(&lo);
+                        w[2 * q + 1] = *reinterpret_cast<const uint32_t*>(&hi);
+                    }
+                }
+                *reinterpret_cast<uint4*>(H + cm_off(r, (c0 >> 3), kBM)) = make_uint4(w[0], w[1], w[2], w[3]);
+                *reinterpret_cast<uint4*>(H + cm_off(r, (c0 >> 3) + 1, kBM)) = make_uint4(w[4], w[5], w[6], w[7]);
             }
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         } else {
-            for (int c0 = 0; c0 < kFusedOutPad; c0 += 16) {
+            // 80 padded columns in chunks of 16: chunk cq, and chunk 4 by the first quarter
+            for (int c0 = cq * 16; c0 < kFusedOutPad; c0 += 64) {
                 float v[16];
                 tmem_ld16(trow + (uint32_t)c0, v);
-                if (m < a.B)
-                    for (int j = 0; j < 16 && c0 + j < SALEC_MLP_OUT_N; ++j)
-                        a.Y[(long)m * SALEC_MLP_OUT_N + c0 + j] = v[j] + bias[c0 + j];
+                if (m < a.B) {
+                    float* y = a.Y + (long)m * SALEC_MLP_OUT_N + c0;
+#pragma unroll
+                    for (int j = 0; j < 16; ++j)
+                        if (c0 + j < SALEC_MLP_OUT_N) y[j] = v[j] + bias[c0 + j];
+                }
             }
         }
         asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
         __syncthreads();
     }
-    if (!ok_flag && tid == 0 && a.err) atomicOr(a.err, 4);
+    if (!ok_flag && tid == 0) {
+        if (a.err) atomicOr(a.err, 4);
+        // a weight load or MMAs still in flight get a bounded chance to finish before the
+        // CTA's memory goes away
+        if (in_flight) (void)mbar_wait(&wbar, wphase & 1u);
+        if (mma_pending) (void)mbar_wait(&mbar, mphase & 1u);
+    }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
     if (warp == 0) {
@@ -750,7 +828,7 @@ cudaError_t launch_mlp_forward_fused(const FusedLaunch& f, cudaStream_t s)
     a.B = f.B; a.X = f.X; a.ld_x = f.ld_x; a.W1 = f.W[0];
     for (int l = 0; l < 5; ++l) a.bias[l] = f.bias[l];
     a.Y = f.Y; a.err = f.err;
-    k_mlp_forward_fused<<<(unsigned)((f.B + kBM - 1) / kBM), kGemmThreads, fused_smem_bytes(), s>>>(m2, m3, m4, m5, a);
+    k_mlp_forward_fused<<<(unsigned)((f.B + kBM - 1) / kBM), kFusedThreads, fused_smem_bytes(), s>>>(m2, m3, m4, m5, a);
     return cudaGetLastError();
 }
 

@@ -90,6 +90,24 @@ def test_forward_matches_oracle(B):
     assert np.max(np.abs(y - ref)) < 1e-2 * scale
 
 
+def test_forward_inference_batch_sampled_rows():
+    """The inference batch the benchmark times (65 536 draws), here with a ragged tail of 77
+    more.  Rows are independent, so sampled rows (the first tile, the last two tiles and a
+    random spread) are checked against the oracle one by one; every output is finite."""
+    B = 65536 + 77
+    theta = _net(seed=17)
+    X, _ = _data(B, seed=9)
+    net = S.MLP(B)
+    net.set_params(theta)
+    y = net.forward(torch.from_numpy(X).cuda()).cpu().numpy().astype(np.float64)
+    assert np.all(np.isfinite(y))
+    rng = np.random.default_rng(4)
+    rows = np.unique(np.concatenate([np.arange(128), np.arange(B - 205, B), rng.choice(B, 1500, replace=False)]))
+    ref, _ = M.forward(theta, X[rows].astype(np.float64), bf16=True)
+    assert np.linalg.norm(y[rows] - ref) / np.linalg.norm(ref) < 1e-3
+    assert np.max(np.abs(y[rows] - ref)) < 1e-2 * np.max(np.abs(ref))
+
+
 def test_forward_single_chain():
     """One chain of units (input 0 -> 3 -> 7 -> 1 -> 250 -> output 65) with unit weights:
     output 65 is 2 gelu(gelu(gelu(gelu(x0)))) + 0.5 up to one BF16 rounding per layer and
