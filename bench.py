@@ -364,6 +364,37 @@ def _surrogate(args):
     return out
 
 
+def _layered(args):
+    """The paper's layered verification geometry (Sect. 4, Tables 1-2) at its own 400 m
+    resolution: 462 x 462 cells, sediment / crust / mantle in hydrostatic equilibrium
+    under Earth gravity with Table 1 strength, a 14.4 km dunite projectile, PML 30.
+    Device-timed steps from the start of the impact in both precisions (the state fits in
+    L2 at this size)."""
+    import torch
+    from paper_2403_04267_gb300 import salec, workloads as W
+    spec = W.chicxulub_like(462)
+    cells = spec["grid"]["nr"] * spec["grid"]["nz"]
+    out = {"workload": spec["name"], "cells": cells, "steps": args.layered_steps, "l2": "state fits in L2"}
+    for prec in ("fp64", "fp32mix"):
+        sim = salec.Sim(spec, precision=prec)
+        sim.step(args.warmup)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(sim.stream)
+        sim.step(args.layered_steps)
+        e1.record(sim.stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        sc = sim.scalars()
+        cr = sim.crater(spec["z_surface"], 64)
+        out[prec] = {"value": cells * args.layered_steps / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms / args.layered_steps,
+                     "sim_time_s": sc["t"], "status": sc["status"], "crater_depth_m": cr["depth"],
+                     "crater_diameter_m": cr["diameter"], "gpu_launches": sim.launches_per_step() * args.layered_steps}
+        del sim
+        torch.cuda.empty_cache()
+    return out
+
+
 def run_reference(args):
     ws, rank, _ = _dist()
     if rank != 0:
@@ -412,6 +443,8 @@ def main():
     ap.add_argument("--batch-ref-max-s", type=float, default=300.0)
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--no-surrogate", action="store_true")
+    ap.add_argument("--no-layered", action="store_true")
+    ap.add_argument("--layered-steps", type=int, default=1000)
     ap.add_argument("--sur-members", type=int, default=4)
     ap.add_argument("--sur-steps", type=int, default=3000)
     ap.add_argument("--sur-solver-runs", type=int, default=2)
@@ -565,6 +598,8 @@ def main():
             "step_hbm_frac": round(step_bytes_per_cell(4) * cells / (res32["ms"] / args.steps * 1e-3) / 1e9 / hbm_peak, 4),
             "crater_vs_fp64": {"depth": [c32["depth"], c64["depth"]], "diameter": [c32["diameter"], c64["diameter"]]},
             "gpu_launches": res32["launches"], "clocks": res32["clocks"], "status": res32["scalars"]["status"]}
+    if not args.no_layered and ws == 1:
+        line["layered"] = _layered(args)
     if not args.no_batch and args.batch_runs > 0:
         line["batched"] = _batched(args, rank, ws)
     if not args.no_surrogate and ws == 1:

@@ -125,7 +125,11 @@ salec_status salec_set_material(salec_ctx* ctx, int id, const salec_material* ma
 /* Fill the rows between heights zlo < zhi (m; fractional rows allowed) with material
  * `mat` at density rho (rho <= 0: rho0, or discrete hydrostatic equilibrium when gravity
  * > 0 and the material is Tillotson with I0 = 0), specific internal energy I0 and
- * vertical velocity vz. */
+ * vertical velocity vz.  A hydrostatic layer fills whole rows (SALEC_EINVAL otherwise).
+ * Hydrostatic layers stack: one whose top row lies right below a row filled by an earlier
+ * hydrostatic layer starts from that row's pressure and density (its overburden), so a
+ * layered target (sediment over crust over mantle, Sect. 4 of the paper) is added from
+ * the top down. */
 salec_status salec_add_layer(salec_ctx* ctx, int mat, double zlo, double zhi, double rho,
                              double I0, double vz);
 

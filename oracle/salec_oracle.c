@@ -75,6 +75,7 @@ typedef struct {
     double *setup_V[ORC_MAXMAT], *setup_M[ORC_MAXMAT], *setup_E, *setup_Pz;
     double *setup_R[ORC_MAXMAT], *setup_mix[ORC_MAXMAT];   /* density of the contributions; 1 if they differ */
     double *setup_I, *setup_Imix;                          /* likewise for the specific energy */
+    double *hyd_P, *hyd_R;               /* rows set by a hydrostatic layer: their pressure and density */
     int finalized;
     /* scalars */
     double t, dt, dt_prev;
@@ -260,6 +261,7 @@ orc_sim* orc_create(const orc_grid* g, const orc_material* mats)
     s->wR_c = zalloc(nz); s->wR_v = zalloc(nz + 1);
     s->p0 = zalloc(nz); s->rho_ref = zalloc(nz); s->I_ref = zalloc(nz);
     s->setup_E = zalloc(nc); s->setup_Pz = zalloc(nc); s->setup_I = zalloc(nc); s->setup_Imix = zalloc(nc);
+    s->hyd_P = zalloc(nz); s->hyd_R = zalloc(nz);
     s->P = zalloc(nc); s->pbar = zalloc(nc); s->mv = zalloc(nv); s->vLr = zalloc(nv); s->vLz = zalloc(nv);
     s->dK = zalloc(nv); s->kheat = zalloc(nv);
     s->VL = zalloc(nc); s->IL = zalloc(nc); s->srrL = zalloc(nc); s->szzL = zalloc(nc); s->srzL = zalloc(nc);
@@ -277,7 +279,7 @@ void orc_destroy(orc_sim* s)
                       &s->vr, &s->vz, &s->phi1_b, &s->phi3_b, &s->psi2_b, &s->phi1_r, &s->phi3_r,
                       &s->psi2_r, &s->phi2r_b, &s->phi2z_b, &s->psi1r_b, &s->psi1z_b, &s->phi2r_r,
                       &s->phi2z_r, &s->psi1r_r, &s->psi1z_r, &s->dB_c, &s->dB_v, &s->dR_c, &s->dR_v, &s->wR_c, &s->wR_v,
-                      &s->p0, &s->rho_ref, &s->I_ref, &s->setup_E, &s->setup_Pz, &s->setup_I, &s->setup_Imix, &s->P, &s->pbar,
+                      &s->p0, &s->rho_ref, &s->I_ref, &s->setup_E, &s->setup_Pz, &s->setup_I, &s->setup_Imix, &s->hyd_P, &s->hyd_R, &s->P, &s->pbar,
                       &s->mv, &s->vLr, &s->vLz, &s->dK, &s->kheat, &s->VL, &s->IL, &s->srrL, &s->szzL, &s->srzL, &s->DL,
                       &s->dVR, &s->dVZ, &s->dMR, &s->dMZ};
     for (size_t k = 0; k < sizeof(all) / sizeof(all[0]); ++k) free(*all[k]);
@@ -293,8 +295,12 @@ void orc_destroy(orc_sim* s)
  * on the symmetry axis whose cell fractions are r-weighted 16x16 sub-samples.  With
  * gravity a cold Tillotson layer (rho <= 0 requested) is put in discrete hydrostatic
  * equilibrium, -grad p0 + rho g = 0 (Sect. 3, the constraint on p0), solved per row by
- * Newton's method from the surface down.  Pinned by test_oracle_rest.py (hydrostatic
- * column stays at rest) and test_oracle_setup.py (sphere volume).
+ * Newton's method from the surface down.  Layers stack: a hydrostatic layer whose top row
+ * lies right below a row of an earlier hydrostatic layer starts from that row's pressure
+ * and density (its overburden), so a layered target (the paper's sediment / crust / mantle
+ * column, Sect. 4) is built from the top down.  Pinned by test_oracle_rest.py (hydrostatic
+ * columns, single and stacked, stay at rest; the stacked column's pressure matches the
+ * overburden) and test_oracle_setup.py (sphere volume).
  * ------------------------------------------------------------------------------------ */
 /* one contribution of material `mat` to cell c; a cell whose contributions all share one
    density keeps that density exactly (M / V would round it) */
@@ -341,6 +347,11 @@ int orc_add_layer(orc_sim* s, int mat, double zlo, double zhi, double rho, doubl
         for (int j = nz - 1; j >= 0; --j) if (w[j] > 0.0) { top = j; break; }
         for (int j = 0; j < nz; ++j)
             if (w[j] > 0.0 && w[j] < 1.0) { free(w); free(rowrho); return 2; }
+        /* overburden: the row right above, if an earlier hydrostatic layer filled it */
+        if (top >= 0 && top + 1 < nz && s->hyd_R[top + 1] > 0.0) {
+            Pabove = s->hyd_P[top + 1];
+            rhoabove = s->hyd_R[top + 1];
+        }
         for (int j = top; j >= 0 && w[j] > 0.0; --j) {
             double k = 0.5 * dx * s->g.gravity;
             double rhs = Pabove + k * rhoabove;
@@ -356,6 +367,8 @@ int orc_add_layer(orc_sim* s, int mat, double zlo, double zhi, double rho, doubl
             rowrho[j] = m->rho0 * (1.0 + mu);
             Pabove = m->A * mu + m->B * mu * mu;
             rhoabove = rowrho[j];
+            s->hyd_P[j] = Pabove;
+            s->hyd_R[j] = rowrho[j];
         }
     }
     for (int j = 0; j < nz; ++j) {

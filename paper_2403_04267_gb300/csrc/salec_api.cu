@@ -140,6 +140,7 @@ struct salec_ctx {
     std::vector<char> sMix[kMaxMat];      // contributions of differing density
     std::vector<double> sI;               // specific energy shared by all contributions
     std::vector<char> sImix;
+    std::vector<double> hydP, hydR;       // rows filled by a hydrostatic layer: pressure, density
     std::vector<double> A_R, A_Z, Vc;
     std::string err;
     // optional per-kernel timing: 7 events per recorded step
@@ -267,6 +268,8 @@ salec_status salec_create(const salec_grid* grid, int precision, void* dev_state
     ctx->sI.assign(nc, 0.0);
     ctx->sImix.assign(nc, 0);
     ctx->sPz.assign(nc, 0.0);
+    ctx->hydP.assign(grid->nz, 0.0);
+    ctx->hydR.assign(grid->nz, 0.0);
     const int nr = grid->nr;
     const double dx = grid->dx;
     ctx->A_R.resize(nr + 1); ctx->A_Z.resize(nr); ctx->Vc.resize(nr);
@@ -337,12 +340,18 @@ salec_status salec_add_layer(salec_ctx* ctx, int mat, double zlo, double zhi, do
         // discrete hydrostatic balance at the vertex between rows j (below) and j+1:
         // P_j - P_{j+1} = (rho_j + rho_{j+1}) g dx / 2 with the cold curve P = A mu + B mu^2;
         // per row a quadratic in mu, solved in the cancellation-free form of its root.
+        // A layer right below the rows of an earlier hydrostatic layer carries their
+        // weight: it starts from the pressure and density of the row above it.
         for (int j = 0; j < nz; ++j)
             if (w[j] > 0.0 && w[j] < 1.0) return fail(ctx, SALEC_EINVAL, "hydrostatic layer must fill whole rows");
         const double k = 0.5 * dx * g;
         double Pup = 0.0, rup = 0.0;
         int j = nz - 1;
         while (j >= 0 && !(w[j] > 0.0)) --j;
+        if (j >= 0 && j + 1 < nz && ctx->hydR[j + 1] > 0.0) {
+            Pup = ctx->hydP[j + 1];
+            rup = ctx->hydR[j + 1];
+        }
         for (; j >= 0 && w[j] > 0.0; --j) {
             const double rhs = Pup + k * rup;
             const double lin = M.A - k * M.rho0, cst = k * M.rho0 + rhs;
@@ -352,6 +361,8 @@ salec_status salec_add_layer(salec_ctx* ctx, int mat, double zlo, double zhi, do
             rrow[j] = M.rho0 * (1.0 + mu);
             Pup = M.A * mu + M.B * mu * mu;
             rup = rrow[j];
+            ctx->hydP[j] = Pup;
+            ctx->hydR[j] = rup;
         }
     }
     for (int j = 0; j < nz; ++j) {
@@ -549,6 +560,7 @@ salec_status salec_finalize(salec_ctx* ctx)
     }
     ctx->sE.clear(); ctx->sE.shrink_to_fit(); ctx->sPz.clear(); ctx->sPz.shrink_to_fit();
     ctx->sI.clear(); ctx->sI.shrink_to_fit(); ctx->sImix.clear(); ctx->sImix.shrink_to_fit();
+    ctx->hydP.clear(); ctx->hydP.shrink_to_fit(); ctx->hydR.clear(); ctx->hydR.shrink_to_fit();
     ctx->finalized = true;
     return SALEC_OK;
 }

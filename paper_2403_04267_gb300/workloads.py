@@ -39,6 +39,39 @@ def iron() -> dict:
                 alpha=5.0, beta=5.0, Eiv=2.4e6, Ecv=8.67e6, gamma=0.0, strength="none", p_t=0.0)
 
 
+def _layer_rock(rho0: float, A: float, strength: bool, Yi0: float, mui: float, Yim: float,
+                mud: float, **eos) -> dict:
+    """A rock of the layered target.  Strength: Table 1 of the paper (cohesion, friction and
+    limiting strength, intact and damaged; damaged cohesion 0.01 MPa).  Equation of state:
+    the paper gives none for these rocks, so the Tillotson constants are synthetic stand-ins:
+    the rock's density, A = B set per rock, the other constants basalt's unless given.
+    Shear modulus 0.6 A (Poisson's ratio 0.25)."""
+    m = dict(basalt(), rho0=rho0, A=A, B=A)
+    m.update(eos)
+    if strength:
+        m.update(strength="collins", Yi0=Yi0, mui=mui, Yim=Yim, Yd0=0.01e6, mud=mud, Ydm=Yim,
+                 G=0.6 * A, eps_fb=1e-4, B_dam=1e-11, p_bd=3e8, p_t=-Yi0)
+    return m
+
+
+def calcite(strength: bool = True) -> dict:
+    """Sediment layer: 2710 kg/m^3, A = B = 20 GPa; Table 1: 5 MPa, 1.0 / 0.4, 0.5 GPa."""
+    return _layer_rock(2710.0, 20e9, strength, 5e6, 1.0, 0.5e9, 0.4)
+
+
+def granite(strength: bool = True) -> dict:
+    """Crust layer: the commonly tabulated Tillotson granite (2680 kg/m^3, A = B = 18 GPa,
+    E0 = 16 MJ/kg, b = 1.3, E_iv = 3.5 MJ/kg, E_cv = 18 MJ/kg); Table 1: 10 MPa,
+    2.0 / 0.6, 2.5 GPa."""
+    return _layer_rock(2680.0, 18e9, strength, 10e6, 2.0, 2.5e9, 0.6, E0=16e6, b=1.3, Eiv=3.5e6, Ecv=18e6)
+
+
+def dunite(strength: bool = True) -> dict:
+    """Mantle layer (and projectile): 3320 kg/m^3, A = B = 130 GPa; Table 1: 10 MPa,
+    1.2 / 0.6, 3.5 GPa."""
+    return _layer_rock(3320.0, 130e9, strength, 10e6, 1.2, 3.5e9, 0.6)
+
+
 def ideal_gas(gamma: float = 1.4, rho0: float = 1.0) -> dict:
     return dict(eos="ideal_gas", rho0=rho0, gamma=gamma, A=0.0, B=0.0, E0=1.0, a=0.0, b=0.0,
                 alpha=0.0, beta=0.0, Eiv=0.0, Ecv=1.0, strength="none", p_t=0.0)
@@ -73,6 +106,41 @@ def impact(nr: int, nz: int, dx: float, target: dict, projectile_mat: dict | Non
         "projectile": dict(mat=pmat, radius=R, zc=zs + R, vz=-abs(v_imp), rho=0.0, I0=0.0),
         "z_surface": zs,
     }
+
+
+def layered_impact(nr: int, nz: int, dx: float, surface_row: int, sediment_rows: int,
+                   crust_rows: int, radius_cells: float, v_imp: float, pml: int,
+                   gravity: float = 9.81, strength: bool = True, **gkw) -> dict:
+    """The paper's three-layer target (Sect. 4): sediment (calcite) over crust (granite)
+    over mantle (dunite), each in hydrostatic equilibrium under its overburden, hit
+    vertically by a dunite sphere on the axis (materials 0, 1, 2; the projectile shares
+    the mantle's material).  Layer boundaries lie on row boundaries."""
+    gkw.setdefault("pml_alpha", 0.1)
+    z_s = surface_row * dx
+    z_c = (surface_row - sediment_rows) * dx
+    z_m = (surface_row - sediment_rows - crust_rows) * dx
+    R = radius_cells * dx
+    layers = [dict(mat=0, zlo=z_c, zhi=z_s, rho=0.0, I0=0.0, vz=0.0),
+              dict(mat=1, zlo=max(z_m, 0.0), zhi=z_c, rho=0.0, I0=0.0, vz=0.0)]
+    if z_m > 0.0:
+        layers.append(dict(mat=2, zlo=0.0, zhi=z_m, rho=0.0, I0=0.0, vz=0.0))
+    return {
+        "grid": grid(nr, nz, dx, pml_r=pml, pml_b=pml, gravity=gravity, **gkw),
+        "materials": [calcite(strength), granite(strength), dunite(strength)],
+        "layers": layers,
+        "projectile": dict(mat=2, radius=R, zc=z_s + R, vz=-abs(v_imp), rho=0.0, I0=0.0),
+        "z_surface": z_s,
+    }
+
+
+def chicxulub_like(n: int = 462) -> dict:
+    """The paper's verification geometry at its 400 m resolution (Sect. 4, Tables 1-2):
+    2.8 km of sediment (7 rows), 30 km of crust (75 rows), mantle below; a 14.4 km dunite
+    projectile (radius 18 cells); PML 30 on the right and bottom; n x n cells with the
+    surface 30 rows below the top.  The impact speed (12 km/s) is not given by the paper."""
+    w = layered_impact(n, n, 400.0, n - 30, 7, 75, 18, 12e3, 30)
+    w["name"] = f"chicxulub_like_{n}x{n}"
+    return w
 
 
 # --- the five configurations -------------------------------------------------------------

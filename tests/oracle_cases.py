@@ -77,3 +77,27 @@ def random_impact_spec(seed: int, nr: int, nz: int, nmat: int = 2, strength: boo
     w["grid"]["pml_r"] = min(pml, nr - 1)
     w["grid"]["pml_b"] = min(pml, nz - 1)
     return w
+
+
+def axis_focus_spec(n: int, pml: int) -> dict:
+    """The 100 x 100 impact's physics (10 m cells, basalt half-space with its surface at
+    70 % of the height, a 10 km/s projectile of radius n/20 cells) on an n x n grid with
+    reflecting walls (free-slip right, no-slip bottom), with or without PML strips of
+    `pml` cells: the setting of the paper's reflected-wave anomaly (Sect. 5)."""
+    return W.impact(n, n, 10.0, W.basalt(), None, 5 * n / 100, 10e3, int(0.7 * n), pml)
+
+
+def axis_anomaly_history(sim, n: int, t_end: float, every: int = 10):
+    """(t, axis, band) every `every` steps up to t_end: the largest |p - p(0)| in the
+    cells within 0.08 n of the axis, and in the band of columns 0.40 n .. 0.55 n, both
+    between 0.15 n and 0.55 n above the bottom (below the crater, above the strip)."""
+    p0 = sim.get("p").copy()
+    j0, j1 = int(0.15 * n), int(0.55 * n)
+    out = []
+    while sim.scalars()["t"] < t_end:
+        sim.step(every)
+        sc = sim.scalars()
+        assert sc["status"] == 0, sc
+        dp = np.abs(sim.get("p") - p0)[j0:j1]
+        out.append((sc["t"], dp[:, :int(0.08 * n)].max(), dp[:, int(0.40 * n):int(0.55 * n)].max()))
+    return np.array(out)

@@ -1,0 +1,123 @@
+"""Adjacent physics of the paper on the GPU: the layered target of its verification run
+(Sect. 4: sediment over crust over mantle, each in hydrostatic equilibrium under the
+layers above, Table 1 strength) against the oracle, and the reflected-wave anomaly on the
+symmetry axis (Sect. 5) with and without absorbing layers, in both precisions."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+import gpu_util as U
+import oracle_cases as OC
+from oracle import oracle as O
+from paper_2403_04267_gb300 import salec, workloads as W
+
+TOL = 1e-9
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    torch.cuda.set_device(0)
+    salec.load()
+
+
+def _check(g, r, spec, tol=TOL, sensitivity=None):
+    rep = U.parity(g, r, spec)
+    print({k: f"{v:.1e}" for k, v in rep.items()})
+    for k, e in U.gated(rep).items():
+        bound = tol if sensitivity is None else max(tol, 100.0 * sensitivity.get(k, 0.0))
+        assert e <= bound, f"{k}: {e:.3e} > {bound:.1e}"
+    sg, so = g.scalars(), r.scalars()
+    assert sg["nstep"] == so["nstep"] and sg["status"] == so["status"] == 0
+    for k in ("t", "dt"):
+        bound = tol if sensitivity is None else max(tol, 100.0 * sensitivity.get(k, 0.0))
+        assert abs(sg[k] - so[k]) <= bound * so[k], k
+
+
+def test_layered_column_matches_oracle_and_stays_at_rest():
+    """The stacked hydrostatic column (7 sediment, 20 crust, 23 mantle rows of 400 m under
+    Earth gravity): the GPU set-up carries each layer's overburden like the oracle's, and
+    the column stays at rest for 200 steps."""
+    spec = W.layered_impact(6, 60, 400.0, 50, 7, 20, 3, 12e3, 0)
+    spec["projectile"] = None
+    g, r = salec.Sim(spec), O.OracleSim(spec)
+    _check(g, r, spec)
+    # the same densities; the EoS evaluations differ only in rounding
+    assert np.allclose(g.get("p"), r.get("p"), rtol=1e-12, atol=0.0)
+    g.step(200)
+    r.step(200)
+    _check(g, r, spec)
+    v = np.hypot(g.get("vr"), g.get("vz")).max()
+    assert v / np.sqrt(130e9 / 3320.0) <= 1e-12
+
+
+def test_layered_impact_against_oracle():
+    """A dunite sphere (radius 4 cells, 12 km/s) into the three-layer target with Table 1
+    strength, damage, gravity and PML 10: every field after 1 step within the FP64 bar,
+    and after 60 steps within it or 100 x the oracle's own response to a 1e-15 input
+    perturbation (yielding cells are ill-conditioned)."""
+    spec = W.layered_impact(60, 80, 400.0, 70, 5, 30, 4, 12e3, 10)
+    g, r = salec.Sim(spec), O.OracleSim(spec)
+    g.step(1)
+    r.step(1)
+    _check(g, r, spec)
+    r2 = U.perturbed(O.OracleSim(spec))
+    r2.step(1)
+    for s in (g, r, r2):
+        s.step(59)
+    sens = U.gated(U.parity(r2, r, spec))
+    s2, s1 = r2.scalars(), r.scalars()
+    sens.update({k: abs(s2[k] - s1[k]) / s1[k] for k in ("t", "dt")})
+    _check(g, r, spec, sensitivity=sens)
+
+
+def _window(h, t0, t1, col):
+    sel = (h[:, 0] >= t0) & (h[:, 0] <= t1)
+    assert sel.sum() >= 3
+    return h[sel, col].max()
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32mix"])
+def test_axis_focusing_and_its_suppression(precision):
+    """The reflected-wave anomaly on the axis (Sect. 5) at 400 x 400 cells: four times the
+    100 x 100 case the oracle pins, so every arrival time is four times later (the
+    hydrodynamic impact is self-similar in r / t).  Without PML the bottom's reflection
+    reaches the axis region and the right wall's reflection converges on the axis well
+    above the amplitude it carried inward; the 16-cell strips remove both."""
+    n, s = 400, 4.0
+    h = {}
+    for pml in (0, 16):
+        sim = salec.Sim(OC.axis_focus_spec(n, pml), precision=precision)
+        h[pml] = OC.axis_anomaly_history(sim, n, 0.72 * s)
+    bottom0, bottom1 = _window(h[0], 0.20 * s, 0.29 * s, 1), _window(h[16], 0.20 * s, 0.29 * s, 1)
+    focus0, focus1 = _window(h[0], 0.58 * s, 0.70 * s, 1), _window(h[16], 0.58 * s, 0.70 * s, 1)
+    inbound0 = _window(h[0], 0.40 * s, 0.57 * s, 2)
+    print(f"{precision}: bottom {bottom0:.3e} vs {bottom1:.3e}; focus {focus0:.3e} vs {focus1:.3e}; "
+          f"inbound {inbound0:.3e}")
+    assert bottom0 > 5.0 * bottom1
+    assert focus0 > 2.0 * inbound0
+    assert focus0 > 10.0 * focus1
+
+
+@pytest.mark.parametrize("precision,mass_tol", [("fp64", 1e-10), ("fp32mix", 1e-4)])
+def test_chicxulub_like_column_runs(precision, mass_tol):
+    """The paper's verification geometry at its own resolution (462 x 462 cells of 400 m,
+    three layers, 14.4 km dunite projectile, PML 30), 1500 steps: no failure, the crater
+    opens on the axis, and the mass on the grid plus what left through the top, what the
+    clean-up removed and what the strips' damping took out stays the initial mass (FP64:
+    to round-off; FP32-mix: to its FP32 fields' resolution)."""
+    spec = W.chicxulub_like(462)
+    g = salec.Sim(spec, precision=precision)
+    c0 = g.conservation()
+    g.step(1500)
+    sc = g.scalars()
+    assert sc["status"] == 0, sc
+    c1 = g.conservation()
+    acc = c1["mass"] + sc["mass_out"] + sc["mass_discarded"] - sc["mass_pml"]
+    cr = g.crater(spec["z_surface"], 64)
+    print(precision, "t", sc["t"], "mass", c0["mass"], c1["mass"], "accounted", acc, "crater", cr["depth"], cr["diameter"])
+    assert abs(acc / c0["mass"] - 1.0) < mass_tol
+    assert cr["depth"] > 2 * 400.0
