@@ -365,14 +365,15 @@ def _surrogate(args):
 
 
 def _layered(args):
-    """The paper's layered verification geometry (Sect. 4, Tables 1-2) at its own 400 m
-    resolution: 462 x 462 cells, sediment / crust / mantle in hydrostatic equilibrium
-    under Earth gravity with Table 1 strength, a 14.4 km dunite projectile, PML 30.
-    Device-timed steps from the start of the impact in both precisions (the state fits in
-    L2 at this size)."""
+    """The paper's verification run set-up (Sect. 4, Tables 1-2): its grid -- a 462 x 462
+    zone of 400 m cells, 20 extension cells growing by 1.05 to 1061 m on the right, bottom
+    and top, 30 PML cells outside (512 x 532 cells) -- and its target, sediment / crust /
+    mantle in hydrostatic equilibrium under Earth gravity with Table 1 strength, hit by a
+    14.4 km dunite projectile.  Device-timed steps from the start of the impact in both
+    precisions (the state fits in L2 at this size)."""
     import torch
     from paper_2403_04267_gb300 import salec, workloads as W
-    spec = W.chicxulub_like(462)
+    spec = W.chicxulub_stretched()
     cells = spec["grid"]["nr"] * spec["grid"]["nz"]
     out = {"workload": spec["name"], "cells": cells, "steps": args.layered_steps, "l2": "state fits in L2"}
     for prec in ("fp64", "fp32mix"):

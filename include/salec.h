@@ -122,6 +122,17 @@ salec_status salec_create(const salec_grid* grid, int precision, void* dev_state
 /* Set material `id` (0..nmat-1).  Must precede salec_finalize. */
 salec_status salec_set_material(salec_ctx* ctx, int id, const salec_material* mat);
 
+/* Non-uniform cells: column widths dr[nr] and row heights dz[nz] (m, positive, host
+ * arrays read during the call).  Without this call every cell is grid->dx square.  The
+ * paper's grids (Table 2) have a high-resolution zone of equal cells and extension zones
+ * whose cells grow by a constant factor (1.05) up to a maximum spacing; positions are the
+ * running sums of the sizes from the axis and from the bottom.  Cell (i,j) has volume
+ * r_c dr dz per radian, the viscosity and the Courant condition use its smaller side.
+ * Must precede every salec_add_layer / salec_place_projectile (SALEC_EORDER otherwise);
+ * SALEC_EINVAL for a non-positive or non-finite size.  salec_courant_dt_noalloc assumes
+ * uniform cells of grid->dx. */
+salec_status salec_set_spacing(salec_ctx* ctx, const double* dr, const double* dz);
+
 /* Fill the rows between heights zlo < zhi (m; fractional rows allowed) with material
  * `mat` at density rho (rho <= 0: rho0, or discrete hydrostatic equilibrium when gravity
  * > 0 and the material is Tillotson with I0 = 0), specific internal energy I0 and

@@ -88,6 +88,7 @@ def lib():
         L.orc_create.argtypes = [C.POINTER(Grid), C.POINTER(Material)]
         L.orc_destroy.argtypes = [P]
         L.orc_add_layer.argtypes = [P, C.c_int] + [C.c_double] * 5
+        L.orc_set_spacing.argtypes = [P, D, D]
         L.orc_place_projectile.argtypes = [P, C.c_int] + [C.c_double] * 5
         L.orc_finalize.argtypes = [P]
         L.orc_step.argtypes = [P, C.c_int]
@@ -175,6 +176,16 @@ class OracleSim:
         if not self._h:
             raise ValueError("oracle rejected the grid")
         self.nr, self.nz = self.grid["nr"], self.grid["nz"]
+        if self.grid.get("dr") is not None or self.grid.get("dz") is not None:
+            dr = np.ascontiguousarray(self.grid.get("dr", [self.grid["dx"]] * self.nr), dtype=np.float64)
+            dz = np.ascontiguousarray(self.grid.get("dz", [self.grid["dx"]] * self.nz), dtype=np.float64)
+            if dr.shape != (self.nr,) or dz.shape != (self.nz,):
+                raise ValueError("spacing arrays must have nr and nz entries")
+            self._dr, self._dz = dr, dz
+            rc = L.orc_set_spacing(self._h, dr.ctypes.data_as(C.POINTER(C.c_double)),
+                                   dz.ctypes.data_as(C.POINTER(C.c_double)))
+            if rc:
+                raise ValueError(f"oracle rejected the spacing ({rc})")
         for lay in spec.get("layers", []):
             rc = L.orc_add_layer(self._h, lay["mat"], lay["zlo"], lay["zhi"], lay.get("rho", 0.0),
                                  lay.get("I0", 0.0), lay.get("vz", 0.0))
@@ -237,14 +248,14 @@ class OracleSim:
         return out
 
 
-def crater_metrics(h: np.ndarray, dx: float, z_surface: float, npts: int, r_extent: float):
+def crater_metrics(h: np.ndarray, dx: float, z_surface: float, npts: int, r_extent: float, rc=None):
     """Crater read-out from column surface heights h: depth on the axis (z_surface - h[0]);
     diameter = twice the first radius beyond the deepest column where the surface, linearly
     interpolated between column centres, regains z_surface (twice the last centre if it
     never does, 0 if there is no depression); depth profile z_surface - h sampled at
-    r_k = (k + 1/2) r_extent / npts."""
+    r_k = (k + 1/2) r_extent / npts.  Column centres rc: (i + 1/2) dx unless given."""
     nr = h.size
-    rc = (np.arange(nr) + 0.5) * dx
+    rc = (np.arange(nr) + 0.5) * dx if rc is None else np.asarray(rc, dtype=np.float64)
     depth_profile = z_surface - h
     depth = float(depth_profile[0])
     kmin = int(np.argmax(depth_profile))
@@ -253,7 +264,7 @@ def crater_metrics(h: np.ndarray, dx: float, z_surface: float, npts: int, r_exte
         diameter = 2.0 * float(rc[-1])
         for i in range(kmin, nr - 1):
             if h[i] < z_surface <= h[i + 1]:
-                diameter = 2.0 * float(rc[i] + (z_surface - h[i]) / (h[i + 1] - h[i]) * dx)
+                diameter = 2.0 * float(rc[i] + (z_surface - h[i]) / (h[i + 1] - h[i]) * (rc[i + 1] - rc[i]))
                 break
     rk = (np.arange(npts) + 0.5) * r_extent / npts
     prof = np.interp(rk, rc, depth_profile)

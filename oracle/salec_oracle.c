@@ -57,9 +57,12 @@ typedef struct {
     orc_grid g;
     orc_material mat[ORC_MAXMAT];
     int ncell, nvert;
-    /* geometry per column (per radian): radial face area A_R[i] at r_i, vertical face
-       area A_Z[i] and volume V[i] of column i */
-    double *A_R, *A_Z, *V;
+    /* geometry (per radian): column widths dr[i], vertex radii rR[i] (nr+1), centre radii
+       rc[i] = (r_i + r_i+1) / 2 and vertical face areas A_Z[i] = rc dr; row heights dz[j]
+       and vertex heights zv[j] (nz+1).  The radial face at r_i of row j has area
+       rR[i] dz[j]; cell (i,j) has volume A_Z[i] dz[j]. */
+    double *dr, *rR, *rc, *A_Z, *dz, *zv;
+    int has_content;                     /* a layer or projectile is in: the spacing is fixed */
     /* state */
     double *f[ORC_MAXMAT], *rho[ORC_MAXMAT], *I, *srr, *szz, *srz, *D, *pmax;
     double *vr, *vz;
@@ -91,6 +94,12 @@ typedef struct {
 
 #define CID(s, i, j) ((j) * (s)->g.nr + (i))
 #define VID(s, i, j) ((j) * ((s)->g.nr + 1) + (i))
+
+/* radial face at r_i of row j, volume of cell (i,j), and the cell's length scale (its
+   smaller side) for the viscosity and the Courant condition */
+static double face_r(const orc_sim* s, int i, int j) { return s->rR[i] * s->dz[j]; }
+static double vol(const orc_sim* s, int i, int j) { return s->A_Z[i] * s->dz[j]; }
+static double cell_len(const orc_sim* s, int i, int j) { return s->dr[i] < s->dz[j] ? s->dr[i] : s->dz[j]; }
 
 static double* zalloc(size_t n) { return (double*)calloc(n ? n : 1, sizeof(double)); }
 
@@ -226,6 +235,29 @@ static double pml_profile(double c, double width_cells, double dx, double y_cell
     return 1.5 * c / delta * s * s * log(1.0 / R);
 }
 
+/* The same profile with the strip's thickness delta and the distance y in metres (a
+   strip of cells of any heights). */
+static double pml_profile_len(double c, double delta, double y, double R)
+{
+    double s = y / delta;
+    return 1.5 * c / delta * s * s * log(1.0 / R);
+}
+
+/* Vertex positions, centre radii and face areas from the cell sizes, summed outward from
+   the axis and up from the bottom. */
+static void set_geometry(orc_sim* s)
+{
+    int nr = s->g.nr, nz = s->g.nz;
+    s->rR[0] = 0.0;
+    for (int i = 0; i < nr; ++i) s->rR[i + 1] = s->rR[i] + s->dr[i];
+    for (int i = 0; i < nr; ++i) {
+        s->rc[i] = 0.5 * (s->rR[i] + s->rR[i + 1]);
+        s->A_Z[i] = s->rc[i] * s->dr[i];
+    }
+    s->zv[0] = 0.0;
+    for (int j = 0; j < nz; ++j) s->zv[j + 1] = s->zv[j] + s->dz[j];
+}
+
 /* ------------------------------------------------------------------------------------ */
 orc_sim* orc_create(const orc_grid* g, const orc_material* mats)
 {
@@ -236,13 +268,11 @@ orc_sim* orc_create(const orc_grid* g, const orc_material* mats)
     int nr = g->nr, nz = g->nz;
     s->ncell = nr * nz;
     s->nvert = (nr + 1) * (nz + 1);
-    s->A_R = zalloc(nr + 1); s->A_Z = zalloc(nr); s->V = zalloc(nr);
-    for (int i = 0; i <= nr; ++i) s->A_R[i] = ((double)i * g->dx) * g->dx;
-    for (int i = 0; i < nr; ++i) {
-        double rc = ((double)i + 0.5) * g->dx;
-        s->A_Z[i] = rc * g->dx;
-        s->V[i] = rc * g->dx * g->dx;
-    }
+    s->dr = zalloc(nr); s->rR = zalloc(nr + 1); s->rc = zalloc(nr); s->A_Z = zalloc(nr);
+    s->dz = zalloc(nz); s->zv = zalloc(nz + 1);
+    for (int i = 0; i < nr; ++i) s->dr[i] = g->dx;      /* uniform until orc_set_spacing */
+    for (int j = 0; j < nz; ++j) s->dz[j] = g->dx;
+    set_geometry(s);
     size_t nc = s->ncell, nv = s->nvert;
     for (int m = 0; m < ORC_MAXMAT; ++m) {
         s->f[m] = zalloc(nc); s->rho[m] = zalloc(nc);
@@ -275,7 +305,7 @@ orc_sim* orc_create(const orc_grid* g, const orc_material* mats)
 void orc_destroy(orc_sim* s)
 {
     if (!s) return;
-    double** all[] = {&s->A_R, &s->A_Z, &s->V, &s->I, &s->srr, &s->szz, &s->srz, &s->D, &s->pmax,
+    double** all[] = {&s->dr, &s->rR, &s->rc, &s->A_Z, &s->dz, &s->zv, &s->I, &s->srr, &s->szz, &s->srz, &s->D, &s->pmax,
                       &s->vr, &s->vz, &s->phi1_b, &s->phi3_b, &s->psi2_b, &s->phi1_r, &s->phi3_r,
                       &s->psi2_r, &s->phi2r_b, &s->phi2z_b, &s->psi1r_b, &s->psi1z_b, &s->phi2r_r,
                       &s->phi2z_r, &s->psi1r_r, &s->psi1z_r, &s->dB_c, &s->dB_v, &s->dR_c, &s->dR_v, &s->wR_c, &s->wR_v,
@@ -319,20 +349,35 @@ static void contribute(orc_sim* s, int mat, int c, double vol, double rho, doubl
     s->setup_Pz[c] += mass * vz;
 }
 
+/* Non-uniform cells: widths dr[nr] and heights dz[nz] (m, positive), before any layer or
+   projectile.  The paper's grids have a high-resolution zone of equal cells and extension
+   zones whose cells grow geometrically (Table 2: factor 1.05 up to a maximum spacing). */
+int orc_set_spacing(orc_sim* s, const double* dr, const double* dz)
+{
+    if (s->finalized || s->has_content) return 1;
+    for (int i = 0; i < s->g.nr; ++i) if (!(dr[i] > 0.0)) return 2;
+    for (int j = 0; j < s->g.nz; ++j) if (!(dz[j] > 0.0)) return 2;
+    for (int i = 0; i < s->g.nr; ++i) s->dr[i] = dr[i];
+    for (int j = 0; j < s->g.nz; ++j) s->dz[j] = dz[j];
+    set_geometry(s);
+    return 0;
+}
+
 int orc_add_layer(orc_sim* s, int mat, double zlo, double zhi, double rho, double I0, double vz)
 {
     if (s->finalized || mat < 0 || mat >= s->g.nmat || !(zhi > zlo)) return 1;
     const orc_material* m = &s->mat[mat];
     int nr = s->g.nr, nz = s->g.nz;
-    double dx = s->g.dx;
     int hydro = (rho <= 0.0 && s->g.gravity > 0.0 && m->eos == ORC_EOS_TILLOTSON);
     if (hydro && I0 != 0.0) return 1;
+    s->has_content = 1;
     /* overlap fraction of each row */
     double* w = zalloc(nz);
     for (int j = 0; j < nz; ++j) {
-        double z0 = (double)j * dx, z1 = ((double)j + 1.0) * dx;
+        double z0 = s->zv[j], z1 = s->zv[j + 1];
         double lo = zlo > z0 ? zlo : z0, hi = zhi < z1 ? zhi : z1;
-        w[j] = hi > lo ? (hi - lo) / dx : 0.0;
+        /* a row inside the layer is full (z1 - z0 need not round to dz exactly) */
+        w[j] = (zlo <= z0 && zhi >= z1) ? 1.0 : (hi > lo ? (hi - lo) / s->dz[j] : 0.0);
     }
     double* rowrho = zalloc(nz);
     if (!hydro) {
@@ -341,8 +386,9 @@ int orc_add_layer(orc_sim* s, int mat, double zlo, double zhi, double rho, doubl
     } else {
         /* rows must be completely filled or empty; walk down from the top filled row.
            Balance at the vertex between row j (below) and row j+1 (above):
-           P_j - P_{j+1} = (rho_j + rho_{j+1}) g dx / 2, with P_j = A mu + B mu^2 (I = 0). */
-        double Pabove = 0.0, rhoabove = 0.0;
+           P_j - P_{j+1} = g (rho_j dz_j + rho_{j+1} dz_{j+1}) / 2, with P_j = A mu + B mu^2
+           (I = 0).  Wabove = g rho_{j+1} dz_{j+1} / 2, the upper half cell's weight. */
+        double Pabove = 0.0, Wabove = 0.0;
         int top = -1;
         for (int j = nz - 1; j >= 0; --j) if (w[j] > 0.0) { top = j; break; }
         for (int j = 0; j < nz; ++j)
@@ -350,11 +396,11 @@ int orc_add_layer(orc_sim* s, int mat, double zlo, double zhi, double rho, doubl
         /* overburden: the row right above, if an earlier hydrostatic layer filled it */
         if (top >= 0 && top + 1 < nz && s->hyd_R[top + 1] > 0.0) {
             Pabove = s->hyd_P[top + 1];
-            rhoabove = s->hyd_R[top + 1];
+            Wabove = (0.5 * s->dz[top + 1] * s->g.gravity) * s->hyd_R[top + 1];
         }
         for (int j = top; j >= 0 && w[j] > 0.0; --j) {
-            double k = 0.5 * dx * s->g.gravity;
-            double rhs = Pabove + k * rhoabove;
+            double k = 0.5 * s->dz[j] * s->g.gravity;
+            double rhs = Pabove + Wabove;
             double mu = 0.0;
             for (int it = 0; it < 100; ++it) {
                 double r = m->rho0 * (1.0 + mu);
@@ -366,7 +412,7 @@ int orc_add_layer(orc_sim* s, int mat, double zlo, double zhi, double rho, doubl
             }
             rowrho[j] = m->rho0 * (1.0 + mu);
             Pabove = m->A * mu + m->B * mu * mu;
-            rhoabove = rowrho[j];
+            Wabove = k * rowrho[j];
             s->hyd_P[j] = Pabove;
             s->hyd_R[j] = rowrho[j];
         }
@@ -374,7 +420,7 @@ int orc_add_layer(orc_sim* s, int mat, double zlo, double zhi, double rho, doubl
     for (int j = 0; j < nz; ++j) {
         if (w[j] <= 0.0) continue;
         for (int i = 0; i < nr; ++i) {
-            contribute(s, mat, CID(s, i, j), w[j] * s->V[i], rowrho[j], I0, vz);
+            contribute(s, mat, CID(s, i, j), w[j] * vol(s, i, j), rowrho[j], I0, vz);
         }
     }
     free(w); free(rowrho);
@@ -387,14 +433,14 @@ int orc_place_projectile(orc_sim* s, int mat, double radius, double zc, double v
     const orc_material* m = &s->mat[mat];
     double r = rho > 0.0 ? rho : m->rho0;
     int nr = s->g.nr, nz = s->g.nz;
-    double dx = s->g.dx;
+    s->has_content = 1;
     for (int j = 0; j < nz; ++j) {
         for (int i = 0; i < nr; ++i) {
             double inside = 0.0, total = 0.0;
             for (int b = 0; b < 16; ++b) {
                 for (int a = 0; a < 16; ++a) {
-                    double rs = dx * ((double)i + ((double)a + 0.5) / 16.0);
-                    double zs = dx * ((double)j + ((double)b + 0.5) / 16.0);
+                    double rs = s->rR[i] + s->dr[i] * (((double)a + 0.5) / 16.0);
+                    double zs = s->zv[j] + s->dz[j] * (((double)b + 0.5) / 16.0);
                     double dz = zs - zc;
                     total += rs;
                     if (rs * rs + dz * dz < radius * radius) inside += rs;
@@ -411,7 +457,7 @@ int orc_place_projectile(orc_sim* s, int mat, double radius, double zc, double v
             }
             s->setup_E[c] *= keep;
             s->setup_Pz[c] *= keep;
-            contribute(s, mat, c, frac * s->V[i], r, I0, vz);
+            contribute(s, mat, c, frac * vol(s, i, j), r, I0, vz);
         }
     }
     return 0;
@@ -449,7 +495,7 @@ int orc_finalize(orc_sim* s)
             int c = CID(s, i, j);
             double Mtot = 0.0;
             for (int m = 0; m < s->g.nmat; ++m) {
-                double fm = s->setup_V[m][c] / s->V[i];
+                double fm = s->setup_V[m][c] / vol(s, i, j);
                 if (fm < s->g.f_min) fm = 0.0;
                 s->f[m][c] = fm;
                 s->rho[m][c] = fm > 0.0 ? (s->setup_mix[m][c] != 0.0 ? s->setup_M[m][c] / s->setup_V[m][c]
@@ -512,16 +558,19 @@ int orc_finalize(orc_sim* s)
        deviatoric stress a shock leaves in a strong target -- without bound, and the
        resulting force lifts the bottom strip until a cell empties (a batched impact at
        t = 9 s).  Waves with omega >> alpha are absorbed and passed tangentially as before. */
-    s->alpha_b = pb > 0 ? s->g.pml_alpha * c / (pb * s->g.dx) : 0.0;
-    s->alpha_r = pr > 0 ? s->g.pml_alpha * c / (pr * s->g.dx) : 0.0;
+    /* strips of pb rows and pr columns: thickness delta in metres, y measured from the
+       strip's inner edge to the cell centre or vertex */
+    const double delta_b = s->zv[pb], r_in = s->rR[nr - pr], delta_r = s->rR[nr] - r_in;
+    s->alpha_b = pb > 0 ? s->g.pml_alpha * c / delta_b : 0.0;
+    s->alpha_r = pr > 0 ? s->g.pml_alpha * c / delta_r : 0.0;
     for (int j = 0; j < nz; ++j)
-        s->dB_c[j] = j < pb ? pml_profile(c, pb, s->g.dx, (double)pb - (double)j - 0.5, s->g.pml_R) : 0.0;
+        s->dB_c[j] = j < pb ? pml_profile_len(c, delta_b, delta_b - (s->zv[j] + 0.5 * s->dz[j]), s->g.pml_R) : 0.0;
     for (int j = 0; j <= nz; ++j)
-        s->dB_v[j] = j < pb ? pml_profile(c, pb, s->g.dx, (double)pb - (double)j, s->g.pml_R) : 0.0;
+        s->dB_v[j] = j < pb ? pml_profile_len(c, delta_b, delta_b - s->zv[j], s->g.pml_R) : 0.0;
     for (int i = 0; i < nr; ++i)
-        s->dR_c[i] = i >= nr - pr ? pml_profile(c, pr, s->g.dx, (double)i + 0.5 - (double)(nr - pr), s->g.pml_R) : 0.0;
+        s->dR_c[i] = i >= nr - pr ? pml_profile_len(c, delta_r, s->rc[i] - r_in, s->g.pml_R) : 0.0;
     for (int i = 0; i <= nr; ++i)
-        s->dR_v[i] = i > nr - pr ? pml_profile(c, pr, s->g.dx, (double)i - (double)(nr - pr), s->g.pml_R) : 0.0;
+        s->dR_v[i] = i > nr - pr ? pml_profile_len(c, delta_r, s->rR[i] - r_in, s->g.pml_R) : 0.0;
     /* the right strip absorbs waves of the medium: it acts on the rows whose reference
        (far-field) state holds material, not on the void above the target, where the
        reference is empty and damping toward it would remove ejecta (reading of Sect. 3) */
@@ -536,9 +585,10 @@ int orc_finalize(orc_sim* s)
  * Phase 0: EoS, artificial viscosity and the Courant time step.
  *   p_hat = sum_m f_m max(p_m, (1-D) p_t,m w_m)   (void carries no pressure; w_m the
  *   expansion weight)
- *   q = rho_bar (c_Q dx^2 div^2 - c_L dx c div) when div v < 0            (Amsden 1980)
+ *   q = rho_bar (c_Q L^2 div^2 - c_L L c div) when div v < 0            (Amsden 1980)
  *   P = p_hat + Phi q,   Phi = sum_m f_m
- *   dt = min(C0 min_cells dx / (max_vertex |v| + c), growth dt_prev, dt_max)   (Eq. 14)
+ *   dt = min(C0 min_cells L / (max_vertex |v| + c), growth dt_prev, dt_max)   (Eq. 14)
+ * L = min(dr, dz) of the cell (the cell size dx on a uniform grid).
  * Pinned by test_oracle_sod.py (shock capturing) and test_oracle_dt.py (hand-computed
  * dt on a 2x2 grid).
  * ------------------------------------------------------------------------------------ */
@@ -548,14 +598,13 @@ static double cell_div(const orc_sim* s, const double* vr, const double* vz, int
     double uR = 0.5 * (vr[VID(s, i + 1, j)] + vr[VID(s, i + 1, j + 1)]);
     double uB = 0.5 * (vz[VID(s, i, j)] + vz[VID(s, i + 1, j)]);
     double uT = 0.5 * (vz[VID(s, i, j + 1)] + vz[VID(s, i + 1, j + 1)]);
-    double flux = s->A_R[i + 1] * uR - s->A_R[i] * uL + s->A_Z[i] * (uT - uB);
-    return flux / s->V[i];
+    double flux = face_r(s, i + 1, j) * uR - face_r(s, i, j) * uL + s->A_Z[i] * (uT - uB);
+    return flux / vol(s, i, j);
 }
 
 static void phase0_eos_dt(orc_sim* s)
 {
     int nr = s->g.nr, nz = s->g.nz;
-    double dx = s->g.dx;
     double cand_min = INFINITY;
     for (int j = 0; j < nz; ++j) {
         for (int i = 0; i < nr; ++i) {
@@ -565,6 +614,7 @@ static void phase0_eos_dt(orc_sim* s)
             if (!(phi > 0.0)) { s->P[c] = 0.0; s->pbar[c] = 0.0; continue; }
             double cs = sqrt(c2);
             double div = cell_div(s, s->vr, s->vz, i, j);
+            double dx = cell_len(s, i, j);
             double q = 0.0;
             if (div < 0.0) q = rb * (s->g.av_cq * dx * dx * div * div - s->g.av_cl * dx * cs * div);
             s->P[c] = phat + phi * q;
@@ -602,17 +652,17 @@ static void phase0_eos_dt(orc_sim* s)
  * Pinned by test_oracle_rest.py, test_oracle_conservation.py and test_oracle_strength
  * (through the pure-shear driver of the same stress power).
  * ------------------------------------------------------------------------------------ */
-static void corner_forces_dev(const orc_sim* s, int i, double Srr, double Szz, double Srz, double out[4][4])
+static void corner_forces_dev(const orc_sim* s, int i, int j, double Srr, double Szz, double Srz, double out[4][4])
 {
-    double dx = s->g.dx;
-    double hoop = 0.25 * dx * dx;       /* V / (4 r_c) */
+    double hoop = 0.25 * s->dr[i] * s->dz[j];   /* V / (4 r_c) */
     double Stt = -(Srr + Szz);
-    double hz = 0.5 * s->A_Z[i];        /* V / (2 dx) */
+    double hr = 0.5 * s->rc[i] * s->dz[j];      /* V / (2 dr) */
+    double hz = 0.5 * s->A_Z[i];                /* V / (2 dz) */
     /* radial part: V (S_rr e_rr + S_tt e_tt + S_rz dvz/dr) */
-    out[0][0] = hz * Srr - hoop * Stt;   out[0][1] = hz * Srz;
-    out[1][0] = -hz * Srr - hoop * Stt;  out[1][1] = -hz * Srz;
-    out[2][0] = -hz * Srr - hoop * Stt;  out[2][1] = -hz * Srz;
-    out[3][0] = hz * Srr - hoop * Stt;   out[3][1] = hz * Srz;
+    out[0][0] = hr * Srr - hoop * Stt;   out[0][1] = hr * Srz;
+    out[1][0] = -hr * Srr - hoop * Stt;  out[1][1] = -hr * Srz;
+    out[2][0] = -hr * Srr - hoop * Stt;  out[2][1] = -hr * Srz;
+    out[3][0] = hr * Srr - hoop * Stt;   out[3][1] = hr * Srz;
     /* vertical part: V (S_zz e_zz + S_rz dvr/dz) */
     out[0][2] = hz * Srz;   out[0][3] = hz * Szz;
     out[1][2] = hz * Srz;   out[1][3] = hz * Szz;
@@ -624,7 +674,7 @@ static double cell_mass(const orc_sim* s, int c, int i)
 {
     double m = 0.0;
     for (int k = 0; k < s->g.nmat; ++k) m += s->f[k][c] * s->rho[k][c];
-    return m * s->V[i];
+    return m * vol(s, i, c / s->g.nr);
 }
 
 static double cell_phi(const orc_sim* s, int c)
@@ -676,7 +726,7 @@ static void phase1_vertex(orc_sim* s)
                 int c = CID(s, ci, cj);
                 double phi = cell_phi(s, c);
                 double out[4][4];
-                corner_forces_dev(s, ci, phi * s->srr[c], phi * s->szz[c], phi * s->srz[c], out);
+                corner_forces_dev(s, ci, cj, phi * s->srr[c], phi * s->szz[c], phi * s->srz[c], out);
                 int q = corner[k];
                 devr += out[q][0] + out[q][2];
                 devz += out[q][1] + out[q][3];
@@ -688,14 +738,14 @@ static void phase1_vertex(orc_sim* s)
                 Pp[k] = s->P[c] - phi * s->p0[cj];
                 mass += 0.25 * cell_mass(s, c, ci);
             }
-            /* isotropic forces in difference form: radial through the face r_i, vertical
-               through the faces z_j of columns i-1 and i */
-            double AR = s->A_R[i];
+            /* isotropic forces in difference form: radial through the face r_i of rows j-1
+               and j, vertical through the faces z_j of columns i-1 and i */
+            double ARb = j > 0 ? face_r(s, i, j - 1) : 0.0, ARt = j < nz ? face_r(s, i, j) : 0.0;
             double AZl = i > 0 ? s->A_Z[i - 1] : 0.0, AZr = i < nr ? s->A_Z[i] : 0.0;
-            double Fr = 0.5 * AR * (((Pc[0] + Pc[3]) - Pc[1]) - Pc[2]) + devr;
+            double Fr = 0.5 * (ARb * (Pc[0] - Pc[1]) + ARt * (Pc[3] - Pc[2])) + devr;
             double Fz = 0.5 * (AZl * (Pc[0] - Pc[3]) + AZr * (Pc[1] - Pc[2])) + devz;
             if (pml) {
-                Tr_b += 0.5 * AR * (((Pp[0] + Pp[3]) - Pp[1]) - Pp[2]);
+                Tr_b += 0.5 * (ARb * (Pp[0] - Pp[1]) + ARt * (Pp[3] - Pp[2]));
                 Tz_r += 0.5 * (AZl * (Pp[0] - Pp[3]) + AZr * (Pp[1] - Pp[2]));
             }
             s->psi1r_b[v] = s->psi1r_b[v] * (1.0 - s->alpha_b * dt) - dt * s->dB_v[j] * Tr_b;
@@ -778,18 +828,18 @@ void orc_stress_update(double sv[4], const double rates[5], double G, double Y, 
 static void phase2_cell(orc_sim* s)
 {
     int nr = s->g.nr, nz = s->g.nz, nm = s->g.nmat;
-    double dt = s->dt, dx = s->g.dx;
+    double dt = s->dt;
     for (int j = 0; j < nz; ++j) {
         for (int i = 0; i < nr; ++i) {
             int c = CID(s, i, j);
             int va = VID(s, i, j), vb = VID(s, i + 1, j), vc = VID(s, i + 1, j + 1), vd = VID(s, i, j + 1);
             double phi = cell_phi(s, c);
-            double V = s->V[i];
-            double rc = ((double)i + 0.5) * dx;
+            double V = vol(s, i, j);
+            double rc = s->rc[i];
             if (!(phi > 0.0)) {
                 /* empty cell: nothing to update; remap sees zero material */
-                s->VL[c] = V + dt * (s->A_R[i + 1] * 0.5 * (s->vLr[vb] + s->vLr[vc])
-                                     - s->A_R[i] * 0.5 * (s->vLr[va] + s->vLr[vd])
+                s->VL[c] = V + dt * (face_r(s, i + 1, j) * 0.5 * (s->vLr[vb] + s->vLr[vc])
+                                     - face_r(s, i, j) * 0.5 * (s->vLr[va] + s->vLr[vd])
                                      + s->A_Z[i] * (0.5 * (s->vLz[vd] + s->vLz[vc]) - 0.5 * (s->vLz[va] + s->vLz[vb])));
                 for (int m = 0; m < nm; ++m) { s->fL[m][c] = 0.0; s->rhoL[m][c] = 0.0; }
                 s->IL[c] = 0.0; s->srrL[c] = 0.0; s->szzL[c] = 0.0; s->srzL[c] = 0.0; s->DL[c] = 0.0;
@@ -799,14 +849,14 @@ static void phase2_cell(orc_sim* s)
             double uR = 0.5 * (s->vLr[vb] + s->vLr[vc]);
             double uB = 0.5 * (s->vLz[va] + s->vLz[vb]);
             double uT = 0.5 * (s->vLz[vd] + s->vLz[vc]);
-            double err = (uR - uL) / dx;
-            double ezz = (uT - uB) / dx;
+            double err = (uR - uL) / s->dr[i];
+            double ezz = (uT - uB) / s->dz[j];
             double ett = (uR + uL) / (2.0 * rc);
-            double dvr_dz = 0.5 * ((s->vLr[vd] + s->vLr[vc]) - (s->vLr[va] + s->vLr[vb])) / dx;
-            double dvz_dr = 0.5 * ((s->vLz[vb] + s->vLz[vc]) - (s->vLz[va] + s->vLz[vd])) / dx;
+            double dvr_dz = 0.5 * ((s->vLr[vd] + s->vLr[vc]) - (s->vLr[va] + s->vLr[vb])) / s->dz[j];
+            double dvz_dr = 0.5 * ((s->vLz[vb] + s->vLz[vc]) - (s->vLz[va] + s->vLz[vd])) / s->dr[i];
             double erz = 0.5 * (dvr_dz + dvz_dr);
             double omega = 0.5 * (dvr_dz - dvz_dr);
-            double radial_flux = s->A_R[i + 1] * uR - s->A_R[i] * uL;
+            double radial_flux = face_r(s, i + 1, j) * uR - face_r(s, i, j) * uL;
             double vertical_flux = s->A_Z[i] * (uT - uB);
             double dV = dt * (radial_flux + vertical_flux);
             double VL = V + dV;
@@ -915,7 +965,7 @@ static void phase3_remap(orc_sim* s)
         for (int i = 0; i <= nr; ++i) {
             int f = j * (nr + 1) + i;
             double u = 0.5 * (s->vLr[VID(s, i, j)] + s->vLr[VID(s, i, j + 1)]);
-            double dV = dt * s->A_R[i] * u;
+            double dV = dt * face_r(s, i, j) * u;
             if (i == 0 || i == nr) dV = 0.0;
             s->dVR[f] = dV;
             orc_flux fl;
@@ -986,7 +1036,7 @@ static void phase3_remap(orc_sim* s)
        / new carrier amount, which is exact when nothing flows. */
     for (int j = 0; j < nz; ++j) for (int i = 0; i < nr; ++i) {
         int c = CID(s, i, j);
-        double V = s->V[i];
+        double V = vol(s, i, j);
         double VmL[ORC_MAXMAT], MmL[ORC_MAXMAT], rho_new[ORC_MAXMAT];
         double MLtot = 0.0, VLmat = 0.0, dMtot = 0.0, dVtot = 0.0;
         for (int m = 0; m < nm; ++m) {
@@ -1221,7 +1271,7 @@ int orc_step(orc_sim* s, int nsteps)
             for (int j = 0; j < s->g.nz; ++j) for (int i = 0; i < s->g.nr; ++i) {
                 int c = CID(s, i, j);
                 double M = 0.0;
-                for (int m = 0; m < s->g.nmat; ++m) M += s->f[m][c] * s->rho[m][c] * s->V[i];
+                for (int m = 0; m < s->g.nmat; ++m) M += s->f[m][c] * s->rho[m][c] * vol(s, i, j);
                 ie += M * s->IL[c];
             }
             s->ke_lag = ke; s->ie_lag = ie;
@@ -1352,16 +1402,16 @@ double orc_pml_profile(double c, double width, double dx, double y, double R) { 
 void orc_surface_heights(const orc_sim* s, double* h)
 {
     int nr = s->g.nr, nz = s->g.nz;
-    double dx = s->g.dx;
     for (int i = 0; i < nr; ++i) {
         h[i] = 0.0;
         for (int j = nz - 1; j >= 0; --j) {
             double phi = cell_phi(s, CID(s, i, j));
             if (phi >= 0.5) {
-                double zc = ((double)j + 0.5) * dx;
+                double zc = s->zv[j] + 0.5 * s->dz[j];
                 if (j == nz - 1) { h[i] = zc; break; }
                 double up = cell_phi(s, CID(s, i, j + 1));
-                h[i] = zc + (phi - 0.5) / (phi - up) * dx;
+                double zup = s->zv[j + 1] + 0.5 * s->dz[j + 1];
+                h[i] = zc + (phi - 0.5) / (phi - up) * (zup - zc);
                 break;
             }
         }

@@ -31,7 +31,7 @@ const dim3 kDefaultShape(32, 8);
 // fields, PML auxiliaries) comes first so a checkpoint is one contiguous range.
 struct Layout {
     size_t es;   // bytes of one element of the form (8 FP64, 4 mixed); energies are always 8
-    size_t scal, A_R, A_Z, V, invV, inv2rc, p0, rho_ref, I_ref, dB_c, dB_v, dR_c, dR_v;
+    size_t scal, rR, rc, A_Z, invAZ, inv2rc, dr, idr, dz, idz, zc, A_R, V, invV, p0, rho_ref, I_ref, dB_c, dB_v, dR_c, dR_v;
     size_t fr[kMaxMat], I, s01, s2d, pmax, v;
     size_t pb_c, pb_psi2, pb_v, pr_c, pr_psi2, pr_v;
     size_t persist_end;
@@ -56,11 +56,19 @@ Layout make_layout(const salec_grid& g, int precision)
     const size_t d = L.es, d2 = 2 * d, d4 = 4 * d, e8 = sizeof(double);
     size_t cur = 0;
     L.scal = take(cur, sizeof(DevScalars));
-    L.A_R = take(cur, (nr + 1) * d);
+    L.rR = take(cur, (nr + 1) * d);
+    L.rc = take(cur, nr * d);
     L.A_Z = take(cur, nr * d);
+    L.invAZ = take(cur, nr * d);
+    L.inv2rc = take(cur, nr * d);
+    L.dr = take(cur, nr * d);
+    L.idr = take(cur, nr * d);
+    L.dz = take(cur, nz * d);
+    L.idz = take(cur, nz * d);
+    L.zc = take(cur, nz * e8);
+    L.A_R = take(cur, (nr + 1) * d);
     L.V = take(cur, nr * d);
     L.invV = take(cur, nr * d);
-    L.inv2rc = take(cur, nr * d);
     L.p0 = take(cur, nz * d);
     L.rho_ref = take(cur, nz * d);
     L.I_ref = take(cur, nz * e8);
@@ -141,7 +149,13 @@ struct salec_ctx {
     std::vector<double> sI;               // specific energy shared by all contributions
     std::vector<char> sImix;
     std::vector<double> hydP, hydR;       // rows filled by a hydrostatic layer: pressure, density
-    std::vector<double> A_R, A_Z, Vc;
+    // geometry (per radian): column widths dr, vertex radii rR (nr+1), centre radii rc,
+    // vertical face areas A_Z = rc dr; row heights dz, vertex heights zv (nz+1).  Cell
+    // (i,j) has volume A_Z[i] dz[j]; the radial face at r_i of row j area rR[i] dz[j].
+    std::vector<double> dr, rR, rc, A_Z, dz, zv;
+    bool has_content = false;             // a layer or projectile is in: the spacing is fixed
+    bool uniform = true;                  // every cell dx square
+    double vol(int i, int j) const { return A_Z[i] * dz[j]; }
     std::string err;
     // optional per-kernel timing: 7 events per recorded step
     bool timing = false;
@@ -206,9 +220,11 @@ static void fill_params(salec_ctx* ctx, ParamsT<T>& P)
         if (ctx->mats[m].strength == SALEC_STRENGTH_COLLINS) P.any_strength = 1;
     }
     P.nblk_cells = cell_blocks(g.nr, g.nz);
-    P.dx = T(g.dx); P.dx2 = T(g.dx * g.dx); P.cfl = T(g.cfl); P.g = T(g.gravity); P.cq = T(g.av_cq);
+    P.cfl = T(g.cfl); P.g = T(g.gravity); P.cq = T(g.av_cq);
     P.cl = T(g.av_cl); P.f_min = T(g.f_min);
-    P.dxd = g.dx; P.cfld = g.cfl; P.growth = g.dt_growth; P.dt_max = g.dt_max; P.dt_min = g.dt_min;
+    P.uniform = ctx->uniform ? 1 : 0;
+    P.dx = T(g.dx); P.dx2 = T(g.dx * g.dx); P.idx = T(1.0 / g.dx); P.dxd = g.dx;
+    P.cfld = g.cfl; P.growth = g.dt_growth; P.dt_max = g.dt_max; P.dt_min = g.dt_min;
     PtrsT<T>& p = P.p;
     for (int m = 0; m < kMaxMat; ++m) {
         p.fr[m] = m < g.nmat ? at<T2>(ctx, L.fr[m]) : nullptr;
@@ -218,8 +234,10 @@ static void fill_params(salec_ctx* ctx, ParamsT<T>& P)
     p.pmax = at<T>(ctx, L.pmax); p.v = at<T2>(ctx, L.v);
     p.pb_c = at<T2>(ctx, L.pb_c); p.pb_psi2 = at<T>(ctx, L.pb_psi2); p.pb_v = at<T4>(ctx, L.pb_v);
     p.pr_c = at<T2>(ctx, L.pr_c); p.pr_psi2 = at<T>(ctx, L.pr_psi2); p.pr_v = at<T4>(ctx, L.pr_v);
-    p.A_R = at<T>(ctx, L.A_R); p.A_Z = at<T>(ctx, L.A_Z); p.V = at<T>(ctx, L.V);
-    p.invV = at<T>(ctx, L.invV); p.inv2rc = at<T>(ctx, L.inv2rc); p.p0 = at<T>(ctx, L.p0);
+    p.rR = at<T>(ctx, L.rR); p.rc = at<T>(ctx, L.rc); p.A_Z = at<T>(ctx, L.A_Z); p.invAZ = at<T>(ctx, L.invAZ);
+    p.inv2rc = at<T>(ctx, L.inv2rc); p.dr = at<T>(ctx, L.dr); p.idr = at<T>(ctx, L.idr);
+    p.dz = at<T>(ctx, L.dz); p.idz = at<T>(ctx, L.idz); p.zc = at<double>(ctx, L.zc); p.p0 = at<T>(ctx, L.p0);
+    p.A_R = at<T>(ctx, L.A_R); p.V = at<T>(ctx, L.V); p.invV = at<T>(ctx, L.invV);
     p.rho_ref = at<T>(ctx, L.rho_ref); p.I_ref = at<double>(ctx, L.I_ref); p.dB_c = at<T>(ctx, L.dB_c);
     p.dB_v = at<T>(ctx, L.dB_v); p.dR_c = at<T>(ctx, L.dR_c); p.dR_v = at<T>(ctx, L.dR_v);
     p.PM = at<T2>(ctx, L.PM); p.pbphi = at<T2>(ctx, L.pbphi); p.vL = at<T2>(ctx, L.vL);
@@ -231,6 +249,27 @@ static void fill_params(salec_ctx* ctx, ParamsT<T>& P)
 }
 
 static bool mixed(const salec_ctx* ctx) { return ctx->precision == SALEC_FP32MIX; }
+
+// vertex positions, centre radii and vertical face areas from the cell sizes, summed
+// outward from the axis and up from the bottom
+static void set_geometry(salec_ctx* ctx)
+{
+    const int nr = ctx->g.nr, nz = ctx->g.nz;
+    ctx->rR.assign(nr + 1, 0.0);
+    ctx->rc.assign(nr, 0.0);
+    ctx->A_Z.assign(nr, 0.0);
+    ctx->zv.assign(nz + 1, 0.0);
+    for (int i = 0; i < nr; ++i) ctx->rR[i + 1] = ctx->rR[i] + ctx->dr[i];
+    for (int i = 0; i < nr; ++i) {
+        ctx->rc[i] = 0.5 * (ctx->rR[i] + ctx->rR[i + 1]);
+        ctx->A_Z[i] = ctx->rc[i] * ctx->dr[i];
+    }
+    for (int j = 0; j < nz; ++j) ctx->zv[j + 1] = ctx->zv[j] + ctx->dz[j];
+    bool uni = true;
+    for (int i = 0; i < nr; ++i) uni = uni && ctx->dr[i] == ctx->g.dx;
+    for (int j = 0; j < nz; ++j) uni = uni && ctx->dz[j] == ctx->g.dx;
+    ctx->uniform = uni;
+}
 
 extern "C" {
 
@@ -270,16 +309,26 @@ salec_status salec_create(const salec_grid* grid, int precision, void* dev_state
     ctx->sPz.assign(nc, 0.0);
     ctx->hydP.assign(grid->nz, 0.0);
     ctx->hydR.assign(grid->nz, 0.0);
-    const int nr = grid->nr;
-    const double dx = grid->dx;
-    ctx->A_R.resize(nr + 1); ctx->A_Z.resize(nr); ctx->Vc.resize(nr);
-    for (int i = 0; i <= nr; ++i) ctx->A_R[i] = ((double)i * dx) * dx;
-    for (int i = 0; i < nr; ++i) {
-        const double rc = ((double)i + 0.5) * dx;
-        ctx->A_Z[i] = rc * dx;
-        ctx->Vc[i] = rc * dx * dx;
-    }
+    // uniform cells of dx until salec_set_spacing
+    ctx->dr.assign(grid->nr, grid->dx);
+    ctx->dz.assign(grid->nz, grid->dx);
+    set_geometry(ctx);
     *out = ctx;
+    return SALEC_OK;
+}
+
+salec_status salec_set_spacing(salec_ctx* ctx, const double* dr, const double* dz)
+{
+    if (!ctx || !dr || !dz) return SALEC_EINVAL;
+    if (ctx->finalized || ctx->has_content)
+        return fail(ctx, SALEC_EORDER, "set_spacing after a layer, projectile or finalize");
+    for (int i = 0; i < ctx->g.nr; ++i)
+        if (!(dr[i] > 0.0) || !std::isfinite(dr[i])) return fail(ctx, SALEC_EINVAL, "dr[%d] must be positive", i);
+    for (int j = 0; j < ctx->g.nz; ++j)
+        if (!(dz[j] > 0.0) || !std::isfinite(dz[j])) return fail(ctx, SALEC_EINVAL, "dz[%d] must be positive", j);
+    ctx->dr.assign(dr, dr + ctx->g.nr);
+    ctx->dz.assign(dz, dz + ctx->g.nz);
+    set_geometry(ctx);
     return SALEC_OK;
 }
 
@@ -327,48 +376,51 @@ salec_status salec_add_layer(salec_ctx* ctx, int mat, double zlo, double zhi, do
     if (!(zhi > zlo)) return fail(ctx, SALEC_EINVAL, "layer needs zlo < zhi");
     const salec_material& M = ctx->mats[mat];
     const int nr = ctx->g.nr, nz = ctx->g.nz;
-    const double dx = ctx->g.dx, g = ctx->g.gravity;
+    const double g = ctx->g.gravity;
     const bool hydro = rho <= 0.0 && g > 0.0 && M.eos == SALEC_EOS_TILLOTSON;
     if (hydro && I0 != 0.0) return fail(ctx, SALEC_EINVAL, "hydrostatic layer must be cold (I0 = 0)");
+    ctx->has_content = true;
     std::vector<double> w(nz), rrow(nz, rho > 0.0 ? rho : M.rho0);
     for (int j = 0; j < nz; ++j) {
-        const double z0 = (double)j * dx, z1 = ((double)j + 1.0) * dx;
+        const double z0 = ctx->zv[j], z1 = ctx->zv[j + 1];
         const double lo = zlo > z0 ? zlo : z0, hi = zhi < z1 ? zhi : z1;
-        w[j] = hi > lo ? (hi - lo) / dx : 0.0;
+        // a row inside the layer is full (z1 - z0 need not round to dz exactly)
+        w[j] = (zlo <= z0 && zhi >= z1) ? 1.0 : (hi > lo ? (hi - lo) / ctx->dz[j] : 0.0);
     }
     if (hydro) {
         // discrete hydrostatic balance at the vertex between rows j (below) and j+1:
-        // P_j - P_{j+1} = (rho_j + rho_{j+1}) g dx / 2 with the cold curve P = A mu + B mu^2;
-        // per row a quadratic in mu, solved in the cancellation-free form of its root.
+        // P_j - P_{j+1} = g (rho_j dz_j + rho_{j+1} dz_{j+1}) / 2 with the cold curve
+        // P = A mu + B mu^2; per row a quadratic in mu, solved in the cancellation-free form
+        // of its root.  Wup is the upper half cell's weight g rho_{j+1} dz_{j+1} / 2.
         // A layer right below the rows of an earlier hydrostatic layer carries their
         // weight: it starts from the pressure and density of the row above it.
         for (int j = 0; j < nz; ++j)
             if (w[j] > 0.0 && w[j] < 1.0) return fail(ctx, SALEC_EINVAL, "hydrostatic layer must fill whole rows");
-        const double k = 0.5 * dx * g;
-        double Pup = 0.0, rup = 0.0;
+        double Pup = 0.0, Wup = 0.0;
         int j = nz - 1;
         while (j >= 0 && !(w[j] > 0.0)) --j;
         if (j >= 0 && j + 1 < nz && ctx->hydR[j + 1] > 0.0) {
             Pup = ctx->hydP[j + 1];
-            rup = ctx->hydR[j + 1];
+            Wup = (0.5 * ctx->dz[j + 1] * g) * ctx->hydR[j + 1];
         }
         for (; j >= 0 && w[j] > 0.0; --j) {
-            const double rhs = Pup + k * rup;
+            const double k = 0.5 * ctx->dz[j] * g;
+            const double rhs = Pup + Wup;
             const double lin = M.A - k * M.rho0, cst = k * M.rho0 + rhs;
             double mu;
             if (M.B != 0.0) mu = 2.0 * cst / (lin + sqrt(lin * lin + 4.0 * M.B * cst));
             else mu = cst / lin;
             rrow[j] = M.rho0 * (1.0 + mu);
             Pup = M.A * mu + M.B * mu * mu;
-            rup = rrow[j];
+            Wup = k * rrow[j];
             ctx->hydP[j] = Pup;
-            ctx->hydR[j] = rup;
+            ctx->hydR[j] = rrow[j];
         }
     }
     for (int j = 0; j < nz; ++j) {
         if (!(w[j] > 0.0)) continue;
         for (int i = 0; i < nr; ++i) {
-            add_content(ctx, mat, (size_t)j * nr + i, w[j] * ctx->Vc[i], rrow[j], I0, vz);
+            add_content(ctx, mat, (size_t)j * nr + i, w[j] * ctx->vol(i, j), rrow[j], I0, vz);
         }
     }
     return SALEC_OK;
@@ -382,18 +434,18 @@ salec_status salec_place_projectile(salec_ctx* ctx, int mat, double radius, doub
     if (!(radius > 0.0)) return fail(ctx, SALEC_EINVAL, "radius must be positive");
     const double r0 = rho > 0.0 ? rho : ctx->mats[mat].rho0;
     const int nr = ctx->g.nr, nz = ctx->g.nz;
-    const double dx = ctx->g.dx, R2 = radius * radius;
+    const double R2 = radius * radius;
+    ctx->has_content = true;
     // only rows and columns that can touch the sphere
-    const int jlo = (int)floor((zc - radius) / dx) - 1, jhi = (int)ceil((zc + radius) / dx) + 1;
-    const int ihi = (int)ceil(radius / dx) + 1;
-    for (int j = jlo < 0 ? 0 : jlo; j < nz && j <= jhi; ++j) {
-        for (int i = 0; i < nr && i <= ihi; ++i) {
+    for (int j = 0; j < nz; ++j) {
+        if (ctx->zv[j + 1] < zc - radius || ctx->zv[j] > zc + radius) continue;
+        for (int i = 0; i < nr && ctx->rR[i] <= radius; ++i) {
             double wi = 0.0, wt = 0.0;
             for (int b = 0; b < 16; ++b) {
-                const double zs = dx * ((double)j + ((double)b + 0.5) / 16.0);
+                const double zs = ctx->zv[j] + ctx->dz[j] * (((double)b + 0.5) / 16.0);
                 const double dz = zs - zc;
                 for (int a = 0; a < 16; ++a) {
-                    const double rs = dx * ((double)i + ((double)a + 0.5) / 16.0);
+                    const double rs = ctx->rR[i] + ctx->dr[i] * (((double)a + 0.5) / 16.0);
                     wt += rs;
                     if (rs * rs + dz * dz < R2) wi += rs;
                 }
@@ -405,17 +457,19 @@ salec_status salec_place_projectile(salec_ctx* ctx, int mat, double radius, doub
             for (int k = 0; k < ctx->g.nmat; ++k) { ctx->sV[k][c] *= keep; ctx->sM[k][c] *= keep; }
             ctx->sE[c] *= keep;
             ctx->sPz[c] *= keep;
-            add_content(ctx, mat, c, frac * ctx->Vc[i], r0, I0, vz);
+            add_content(ctx, mat, c, frac * ctx->vol(i, j), r0, I0, vz);
         }
     }
     return SALEC_OK;
 }
 
-static double profile(double c, int width, double dx, double y, double R)
+// Eq. 26: d(y) = 3 c / (2 delta) (y / delta)^2 log(1 / R), strip thickness delta and the
+// distance y from its inner edge in metres
+static double profile(double c, double delta, double y, double R)
 {
-    if (width <= 0 || y <= 0.0) return 0.0;
-    const double s = y / (double)width;
-    return 1.5 * c / ((double)width * dx) * s * s * log(1.0 / R);
+    if (!(delta > 0.0) || y <= 0.0) return 0.0;
+    const double s = y / delta;
+    return 1.5 * c / delta * s * s * log(1.0 / R);
 }
 
 salec_status salec_finalize(salec_ctx* ctx)
@@ -446,7 +500,8 @@ salec_status salec_finalize(salec_ctx* ctx)
     // auxiliaries relax at alpha = pml_alpha c / delta of their strip (complex-frequency-
     // shifted stretch 1 + d / (alpha + i omega)), so a static tangential term cannot grow them
     // without bound
-    const double ab = pb > 0 ? g.pml_alpha * c / (pb * g.dx) : 0.0, ar = pr > 0 ? g.pml_alpha * c / (pr * g.dx) : 0.0;
+    const double delta_b = ctx->zv[pb], r_in = ctx->rR[nr - pr], delta_r = ctx->rR[nr] - r_in;
+    const double ab = pb > 0 ? g.pml_alpha * c / delta_b : 0.0, ar = pr > 0 ? g.pml_alpha * c / delta_r : 0.0;
     ctx->Pd.alpha_b = ab; ctx->Pd.alpha_r = ar;
     ctx->Pf.alpha_b = (float)ab; ctx->Pf.alpha_r = (float)ar;
     // cells
@@ -454,10 +509,10 @@ salec_status salec_finalize(salec_ctx* ctx)
     for (int m = 0; m < g.nmat; ++m) fr[m].assign(nc, make_double2(0.0, 0.0));
     std::vector<double> I(nc, 0.0), Mkept(nc, 0.0), Mall(nc, 0.0);
     for (size_t cc = 0; cc < nc; ++cc) {
-        const int i = (int)(cc % nr);
+        const int i = (int)(cc % nr), jj = (int)(cc / nr);
         double mk = 0.0, ma = 0.0;
         for (int m = 0; m < g.nmat; ++m) {
-            double f = ctx->sV[m][cc] / ctx->Vc[i];
+            double f = ctx->sV[m][cc] / ctx->vol(i, jj);
             if (f < g.f_min) f = 0.0;
             ma += ctx->sM[m][cc];
             if (f > 0.0) {
@@ -505,15 +560,28 @@ salec_status salec_finalize(salec_ctx* ctx)
     // PML profiles (Eq. 26)
     std::vector<double> dBc(nz, 0.0), dBv(nz + 1, 0.0), dRc(nr, 0.0), dRv(nr + 1, 0.0);
     for (int j = 0; j < pb; ++j) {
-        dBc[j] = profile(c, pb, g.dx, (double)pb - (double)j - 0.5, g.pml_R);
-        dBv[j] = profile(c, pb, g.dx, (double)(pb - j), g.pml_R);
+        dBc[j] = profile(c, delta_b, delta_b - (ctx->zv[j] + 0.5 * ctx->dz[j]), g.pml_R);
+        dBv[j] = profile(c, delta_b, delta_b - ctx->zv[j], g.pml_R);
     }
-    for (int i = nr - pr; i < nr; ++i) dRc[i] = profile(c, pr, g.dx, (double)i + 0.5 - (double)(nr - pr), g.pml_R);
-    for (int i = nr - pr + 1; i <= nr; ++i) dRv[i] = profile(c, pr, g.dx, (double)(i - (nr - pr)), g.pml_R);
-    std::vector<double> invV(nr), inv2rc(nr);
+    for (int i = nr - pr; i < nr; ++i) dRc[i] = profile(c, delta_r, ctx->rc[i] - r_in, g.pml_R);
+    for (int i = nr - pr + 1; i <= nr; ++i) dRv[i] = profile(c, delta_r, ctx->rR[i] - r_in, g.pml_R);
+    std::vector<double> invAZ(nr), inv2rc(nr), idr(nr), idz(nz), zcen(nz);
+    // the uniform-grid tables (used when every cell is dx square): A_R = r_i dx,
+    // V = r_c dx^2 with r_i = i dx and r_c = (i + 1/2) dx
+    std::vector<double> uAR(nr + 1), uV(nr), uinvV(nr);
+    for (int i = 0; i <= nr; ++i) uAR[i] = ((double)i * g.dx) * g.dx;
     for (int i = 0; i < nr; ++i) {
-        invV[i] = 1.0 / ctx->Vc[i];
-        inv2rc[i] = 1.0 / (2.0 * (((double)i + 0.5) * g.dx));
+        uV[i] = (((double)i + 0.5) * g.dx) * g.dx * g.dx;
+        uinvV[i] = 1.0 / uV[i];
+    }
+    for (int i = 0; i < nr; ++i) {
+        invAZ[i] = 1.0 / ctx->A_Z[i];
+        inv2rc[i] = 1.0 / (2.0 * ctx->rc[i]);
+        idr[i] = 1.0 / ctx->dr[i];
+    }
+    for (int j = 0; j < nz; ++j) {
+        idz[j] = 1.0 / ctx->dz[j];
+        zcen[j] = ctx->zv[j] + 0.5 * ctx->dz[j];
     }
     // scalars
     DevScalars s;
@@ -537,11 +605,19 @@ salec_status salec_finalize(salec_ctx* ctx)
         up(off, f.data(), n * sizeof(float));
     };
     up(L.scal, &s, sizeof(s));
-    upT(L.A_R, ctx->A_R.data(), nr + 1);
+    upT(L.rR, ctx->rR.data(), nr + 1);
+    upT(L.rc, ctx->rc.data(), nr);
     upT(L.A_Z, ctx->A_Z.data(), nr);
-    upT(L.V, ctx->Vc.data(), nr);
-    upT(L.invV, invV.data(), nr);
+    upT(L.invAZ, invAZ.data(), nr);
     upT(L.inv2rc, inv2rc.data(), nr);
+    upT(L.dr, ctx->dr.data(), nr);
+    upT(L.idr, idr.data(), nr);
+    upT(L.dz, ctx->dz.data(), nz);
+    upT(L.idz, idz.data(), nz);
+    up(L.zc, zcen.data(), nz * sizeof(double));
+    upT(L.A_R, uAR.data(), nr + 1);
+    upT(L.V, uV.data(), nr);
+    upT(L.invV, uinvV.data(), nr);
     upT(L.p0, p0.data(), nz);
     upT(L.rho_ref, rref.data(), nz);
     up(L.I_ref, Iref.data(), nz * sizeof(double));
@@ -797,7 +873,7 @@ salec_status salec_crater_profile(salec_ctx* ctx, double z_surface, int npts, do
     if (!ctx || !depth || !diameter || npts < 0 || (npts > 0 && !depth_profile)) return SALEC_EINVAL;
     if (!ctx->finalized) return fail(ctx, SALEC_EORDER, "crater_profile before finalize");
     const int nr = ctx->g.nr;
-    const double dx = ctx->g.dx;
+    const std::vector<double>& rc = ctx->rc;
     std::vector<double> h(nr);
     double* tmp = at<double>(ctx, ctx->L.tmp);
     cudaError_t e = mixed(ctx) ? launch_column_heights<float>(ctx->Pf, tmp, ctx->stream)
@@ -810,24 +886,26 @@ salec_status salec_crater_profile(salec_ctx* ctx, double z_surface, int npts, do
     for (int i = 1; i < nr; ++i) if (z_surface - h[i] > z_surface - h[kmin]) kmin = i;
     double D = 0.0;
     if (z_surface - h[kmin] > 0.0) {
-        D = 2.0 * ((double)nr - 0.5) * dx;
+        D = 2.0 * rc[nr - 1];
         for (int i = kmin; i + 1 < nr; ++i)
             if (h[i] < z_surface && z_surface <= h[i + 1]) {
-                D = 2.0 * (((double)i + 0.5) * dx + (z_surface - h[i]) / (h[i + 1] - h[i]) * dx);
+                D = 2.0 * (rc[i] + (z_surface - h[i]) / (h[i + 1] - h[i]) * (rc[i + 1] - rc[i]));
                 break;
             }
     }
     if (npts > 0) {
-        const double rext = (double)(nr - ctx->g.pml_right) * dx;
+        // the depth profile sampled at r_k = (k + 1/2) r_ext / npts, r_ext the inner edge
+        // of the right strip, linear between column centres
+        const double rext = ctx->rR[nr - ctx->g.pml_right];
+        int i0 = 0;
         for (int k = 0; k < npts; ++k) {
             const double r = ((double)k + 0.5) * rext / npts;
-            double x = r / dx - 0.5;     // fractional column-centre index
             double val;
-            if (x <= 0.0) val = z_surface - h[0];
-            else if (x >= nr - 1) val = z_surface - h[nr - 1];
+            if (r <= rc[0]) val = z_surface - h[0];
+            else if (r >= rc[nr - 1]) val = z_surface - h[nr - 1];
             else {
-                const int i0 = (int)floor(x);
-                const double w = x - i0;
+                while (rc[i0 + 1] < r) ++i0;
+                const double w = (r - rc[i0]) / (rc[i0 + 1] - rc[i0]);
                 val = (1.0 - w) * (z_surface - h[i0]) + w * (z_surface - h[i0 + 1]);
             }
             depth_profile[k] = val;
@@ -959,6 +1037,7 @@ struct salec_batch {
     std::vector<salec_ctx*> runs;
     int precision = 0, nmat = 0;
     bool strength = false;
+    bool uniform = false;       // every run on a uniform grid
     cudaStream_t stream = nullptr;
     char* dev = nullptr;
     size_t bytes = 0;
@@ -1066,6 +1145,8 @@ salec_status salec_batch_create(salec_ctx* const* runs, int nruns, void* dev_buf
     b->precision = runs[0]->precision;
     b->nmat = runs[0]->g.nmat;
     b->strength = runs[0]->Pd.any_strength != 0;
+    b->uniform = true;
+    for (int k = 0; k < nruns; ++k) b->uniform = b->uniform && runs[k]->uniform;
     b->stream = (cudaStream_t)stream;
     b->dev = (char*)dev_buf;
     b->bytes = bytes;
@@ -1096,9 +1177,9 @@ static cudaError_t batch_launch(salec_batch* b, cudaEvent_t* ev)
     for (int k = 0; k < 6; ++k) work[k] = reinterpret_cast<const BatchTile*>(b->dev + b->off_work[k]);
     if (b->precision == SALEC_FP32MIX)
         return launch_batch_step<float>(reinterpret_cast<const ParamsT<float>*>(b->dev + b->off_params), b->nmat,
-                                        b->strength, work, b->ntiles, b->shape, b->stream, ev);
+                                        b->strength, b->uniform, work, b->ntiles, b->shape, b->stream, ev);
     return launch_batch_step<double>(reinterpret_cast<const ParamsT<double>*>(b->dev + b->off_params), b->nmat,
-                                     b->strength, work, b->ntiles, b->shape, b->stream, ev);
+                                     b->strength, b->uniform, work, b->ntiles, b->shape, b->stream, ev);
 }
 
 static salec_status batch_restore_retired(salec_batch* b);

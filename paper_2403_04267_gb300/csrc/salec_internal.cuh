@@ -78,12 +78,22 @@ struct PtrsT {
     T2* pr_c;               // right cells (phi1, phi3), index j*pr + (i - (nr - pr))
     T* pr_psi2;
     T4* pr_v;               // right vertices, index j*pr + (i - (nr - pr + 1)), i > nr - pr
-    // tables
-    const T* A_R;           // nr+1 radial face areas
-    const T* A_Z;           // nr vertical face areas
-    const T* V;             // nr cell volumes
-    const T* invV;          // nr
-    const T* inv2rc;        // nr  1 / (2 r_c)
+    // geometry (per radian): the radial face at r_i of row j has area rR[i] dz[j], the
+    // vertical faces of column i area A_Z[i], cell (i,j) volume A_Z[i] dz[j]
+    const T* rR;            // nr+1 vertex radii r_i
+    const T* rc;            // nr   cell-centre radii
+    const T* A_Z;           // nr   vertical face areas r_c dr
+    const T* invAZ;         // nr   1 / A_Z
+    const T* inv2rc;        // nr   1 / (2 r_c)
+    const T* dr;            // nr   column widths
+    const T* idr;           // nr   1 / dr
+    const T* dz;            // nz   row heights
+    const T* idz;           // nz   1 / dz
+    const double* zc;       // nz   cell-centre heights (read-outs)
+    // the same for a uniform grid of dx cells, one entry per column for every row
+    const T* A_R;           // nr+1 radial face areas r_i dx
+    const T* V;             // nr   cell volumes r_c dx^2
+    const T* invV;          // nr   1 / V
     const T* p0;            // nz reference pressure per row
     const T* rho_ref;       // nz
     const double* I_ref;    // nz
@@ -112,7 +122,9 @@ struct PtrsT {
 template <typename T>
 struct ParamsT {
     int nr, nz, nmat, pr, pb, bc_top, bc_bottom, any_strength, nblk_cells;
-    T dx, dx2, cfl, g, cq, cl, f_min;
+    int uniform;            // every cell dx square: the kernels' uniform-grid form
+    T cfl, g, cq, cl, f_min;
+    T dx, dx2, idx;         // uniform grid: cell size, its square and inverse
     double dxd, cfld, growth, dt_max, dt_min;
     T alpha_b, alpha_r;     // relaxation rates of the bottom / right strips' auxiliaries (1/s)
     MatT<T> mat[kMaxMat];
@@ -280,7 +292,7 @@ __device__ __forceinline__ float max_nonneg(float a, float b)
 // launchers (salec_kernels.cu), instantiated for T = double and T = float
 template <typename T> cudaError_t launch_step(const ParamsT<T>& P, const dim3* blk, cudaStream_t s, cudaEvent_t* ev);
 template <typename T>
-cudaError_t launch_batch_step(const ParamsT<T>* runs_dev, int nmat, bool strength, const BatchTile* const* work,
+cudaError_t launch_batch_step(const ParamsT<T>* runs_dev, int nmat, bool strength, bool uniform, const BatchTile* const* work,
                               const int* ntiles, const dim3* blk, cudaStream_t s, cudaEvent_t* ev);
 template <typename T> cudaError_t launch_batch_poll(const ParamsT<T>* runs_dev, int n, double* out, cudaStream_t s);
 bool kernel_on_vertices(int k);

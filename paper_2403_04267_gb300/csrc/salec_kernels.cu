@@ -54,20 +54,75 @@ __device__ __forceinline__ bool strip_row_v(const PtrsT<T>& p, int j, int nz)
 }
 
 // ---------------------------------------------------------------------------------
+// Cell geometry per radian.  A non-uniform grid (UNI = false) takes a cell's volume and
+// radial faces as a column entry times its row height: V = r_c dr dz, A_R = r_i dz; a
+// uniform grid of dx cells (UNI = true) keeps one entry per column for every row, which
+// spares the FP64 pipe those products.
+// ---------------------------------------------------------------------------------
+template <typename T, bool UNI>
+struct Geo {
+    static __device__ __forceinline__ T vol(const ParamsT<T>& P, int i, int j)
+    {
+        return UNI ? P.p.V[i] : P.p.A_Z[i] * P.p.dz[j];
+    }
+    static __device__ __forceinline__ T ivol(const ParamsT<T>& P, int i, int j)
+    {
+        return UNI ? P.p.invV[i] : P.p.invAZ[i] * P.p.idz[j];
+    }
+    // radial face area at r_i of row j
+    static __device__ __forceinline__ T area_r(const ParamsT<T>& P, int i, int j)
+    {
+        return UNI ? P.p.A_R[i] : P.p.rR[i] * P.p.dz[j];
+    }
+    // net radial volume flux A_R(i+1) uR - A_R(i) uL of cell (i,j)
+    static __device__ __forceinline__ T flux_r(const ParamsT<T>& P, int i, int j, T uL, T uR)
+    {
+        return UNI ? P.p.A_R[i + 1] * uR - P.p.A_R[i] * uL : P.p.dz[j] * (P.p.rR[i + 1] * uR - P.p.rR[i] * uL);
+    }
+    static __device__ __forceinline__ T idr(const ParamsT<T>& P, int i) { return UNI ? P.idx : P.p.idr[i]; }
+    static __device__ __forceinline__ T idz(const ParamsT<T>& P, int j) { return UNI ? P.idx : P.p.idz[j]; }
+    // the cell's length scale L = min(dr, dz) and 1 / L
+    static __device__ __forceinline__ T len(const ParamsT<T>& P, int i, int j)
+    {
+        if (UNI) return P.dx;
+        const T a = P.p.dr[i], b = P.p.dz[j];
+        return a < b ? a : b;
+    }
+    static __device__ __forceinline__ T ilen(const ParamsT<T>& P, int i, int j)
+    {
+        if (UNI) return P.idx;
+        const T a = P.p.idr[i], b = P.p.idz[j];
+        return a > b ? a : b;
+    }
+    // derivatives of the cell's stress power V S:e with respect to its corner velocities:
+    // V / (2 dr) for r-derivatives, V / (4 r_c) for the hoop strain rate
+    static __device__ __forceinline__ T half_v_dr(const ParamsT<T>& P, int i, int j)
+    {
+        return UNI ? T(0.5) * P.p.A_Z[i] : T(0.5) * P.p.rc[i] * P.p.dz[j];
+    }
+    static __device__ __forceinline__ T quarter_v_rc(const ParamsT<T>& P, int i, int j)
+    {
+        return UNI ? T(0.25) * P.dx2 : T(0.25) * P.p.dr[i] * P.p.dz[j];
+    }
+};
+
+// ---------------------------------------------------------------------------------
 // Phase 0: equation of state, artificial viscosity and the Courant time step.
 // ---------------------------------------------------------------------------------
-template <typename T, int NM, bool STR>
+template <typename T, int NM, bool STR, bool UNI>
 __device__ __forceinline__ void body_phase0(const ParamsT<T>& P, int bx, int by, int gx, int gy)
 {
     typedef VT<T> V;
+    typedef Geo<T, UNI> GE;
     const T zero = T(0), one = T(1), half = T(0.5);
     const int i = bx * blockDim.x + threadIdx.x;
     const int j = by * blockDim.y + threadIdx.y;
     const int nr = P.nr;
     const PtrsT<T>& p = P.p;
-    // largest |v| + c of the block; min over cells of dx / (|v| + c) equals dx / max(|v| + c)
-    // exactly, so one division per step suffices.  The max is exact in T, so it is taken in
-    // T and the block's value converted to FP64 once.
+    // largest (|v| + c) / L of the block, L = min(dr, dz) the cell's length scale: the
+    // min over cells of L / (|v| + c) is C0 over its max, one division per step (a
+    // uniform grid takes the max of |v| + c and divides dx by it).  The max is exact in T,
+    // so it is taken in T and the block's value converted to FP64 once.
     T speed = zero;
     if (i < nr && j < P.nz) {
         const int c = j * nr + i;
@@ -97,7 +152,7 @@ __device__ __forceinline__ void body_phase0(const ParamsT<T>& P, int bx, int by,
             const typename V::T2 vc = p.v[(j + 1) * nv + i + 1], vd = p.v[(j + 1) * nv + i];
             const T uL = half * (va.x + vd.x), uR = half * (vb.x + vc.x);
             const T uB = half * (va.y + vb.y), uT = half * (vd.y + vc.y);
-            const T div = (p.A_R[i + 1] * uR - p.A_R[i] * uL + p.A_Z[i] * (uT - uB)) * p.invV[i];
+            const T div = (GE::flux_r(P, i, j, uL, uR) + p.A_Z[i] * (uT - uB)) * GE::ivol(P, i, j);
             const T cs = t_sqrt<T>(c2m);
             // one material: p_bar = p and rho_bar = rho; otherwise divide by Phi once
             const T iphi = NM == 1 ? one : one / phi;
@@ -105,7 +160,8 @@ __device__ __forceinline__ void body_phase0(const ParamsT<T>& P, int bx, int by,
             T q = zero;
             if (neg(div)) {
                 const T rb = NM == 1 ? r1 : mass * iphi;
-                q = rb * (P.cq * P.dx2 * div * div - P.cl * P.dx * cs * div);
+                const T L = GE::len(P, i, j);
+                q = rb * (P.cq * (UNI ? P.dx2 : L * L) * div * div - P.cl * L * cs * div);
             }
             Pc = phat + phi * q;
             const T over = pbar - p.p0[j];
@@ -115,9 +171,10 @@ __device__ __forceinline__ void body_phase0(const ParamsT<T>& P, int bx, int by,
             w = max_nonneg(w, vc.x * vc.x + vc.y * vc.y);
             w = max_nonneg(w, vd.x * vd.x + vd.y * vd.y);
             speed = t_sqrt<T>(w) + cs;
+            if (!UNI) speed = speed * GE::ilen(P, i, j);
             if (is_nan(speed)) atomicOr(&p.scal->status, 2);
         }
-        p.PM[c] = V::mk(Pc, mass * p.V[i]);
+        p.PM[c] = V::mk(Pc, mass * GE::vol(P, i, j));
         p.pbphi[c] = V::mk(pbar, phi);
     }
     // block maximum (on the bit patterns of the non-negative speeds), then the last block
@@ -152,7 +209,7 @@ __device__ __forceinline__ void body_phase0(const ParamsT<T>& P, int bx, int by,
         for (int w = 1; w < nw; ++w) b = max(b, sh[w]);
         DevScalars* s = p.scal;
         double dt = P.growth * s->dt_prev;
-        const double cdt = P.cfld * (P.dxd / __longlong_as_double(b));
+        const double cdt = UNI ? P.cfld * (P.dxd / __longlong_as_double(b)) : P.cfld / __longlong_as_double(b);
         dt = cdt < dt ? cdt : dt;
         dt = P.dt_max < dt ? P.dt_max : dt;
         if (dt < P.dt_min) s->status |= 4;
@@ -168,10 +225,11 @@ __device__ __forceinline__ void body_phase0(const ParamsT<T>& P, int bx, int by,
 // Cells around vertex (i,j): k = 0 (i-1,j-1) corner c, 1 (i,j-1) corner d,
 // 2 (i,j) corner a, 3 (i-1,j) corner b.
 // ---------------------------------------------------------------------------------
-template <typename T, bool STR>
+template <typename T, bool STR, bool UNI>
 __device__ __forceinline__ void body_phase1(const ParamsT<T>& P, int bx, int by, int gx, int gy)
 {
     typedef VT<T> V;
+    typedef Geo<T, UNI> GE;
     const T zero = T(0), one = T(1), half = T(0.5);
     const int i = bx * blockDim.x + threadIdx.x;
     const int j = by * blockDim.y + threadIdx.y;
@@ -180,7 +238,6 @@ __device__ __forceinline__ void body_phase1(const ParamsT<T>& P, int bx, int by,
     const PtrsT<T>& p = P.p;
     const T dt = step_dt<T>(p.scal);
     const int v = j * (nr + 1) + i;
-    const T hoop = T(0.25) * P.dx2;
     T Pc[4] = {zero, zero, zero, zero}, Pp[4] = {zero, zero, zero, zero};
     T devr_rad = zero, devz_rad = zero, devr_ver = zero, devz_ver = zero, mass = zero;
 #pragma unroll
@@ -200,26 +257,34 @@ __device__ __forceinline__ void body_phase1(const ParamsT<T>& P, int bx, int by,
                 const T srz = p.s2d[c].x;
                 const T Srr = phi * s01.x, Szz = phi * s01.y, Srz = phi * srz;
                 const T Stt = -(Srr + Szz);
-                const T hz = half * p.A_Z[ci];
+                // corner-velocity derivatives of the stress power: V / (2 dr), V / (2 dz)
+                // for r- and z-derivatives, V / (4 r_c) for the hoop strain rate
+                const T hr = GE::half_v_dr(P, ci, cj), hz = half * p.A_Z[ci];
+                const T hoop = GE::quarter_v_rc(P, ci, cj);
                 // a (k=2), d (k=1) on the left face; a, b (k=3) at the bottom of the cell
                 const T sr = (k == 2 || k == 1) ? one : -one;
                 const T sz = (k == 2 || k == 3) ? one : -one;
-                devr_rad += sr * hz * Srr - hoop * Stt;
-                devz_rad += sr * hz * Srz;
+                devr_rad += sr * hr * Srr - hoop * Stt;
+                devz_rad += sr * hr * Srz;
                 devr_ver += sz * hz * Srz;
                 devz_ver += sz * hz * Szz;
             }
         }
     }
-    const T AR = p.A_R[i];
+    // radial faces at r_i of rows j-1 (cells 0, 1) and j (cells 3, 2); one area when every
+    // row has the same height
+    const T ARb = UNI ? p.A_R[i] : (j > 0 ? GE::area_r(P, i, j - 1) : zero);
+    const T ARt = UNI ? ARb : (j < nz ? GE::area_r(P, i, j) : zero);
     const T AZl = i > 0 ? p.A_Z[i - 1] : zero, AZr = i < nr ? p.A_Z[i] : zero;
-    const T Fr = half * AR * (((Pc[0] + Pc[3]) - Pc[1]) - Pc[2]) + (devr_rad + devr_ver);
+    const T Fr = (UNI ? half * ARb * (((Pc[0] + Pc[3]) - Pc[1]) - Pc[2])
+                      : half * (ARb * (Pc[0] - Pc[1]) + ARt * (Pc[3] - Pc[2]))) + (devr_rad + devr_ver);
     const T Fz = half * (AZl * (Pc[0] - Pc[3]) + AZr * (Pc[1] - Pc[2])) + (devz_rad + devz_ver);
     T psr = zero, psz = zero;
     if (j < P.pb) {
         const T d = p.dB_v[j];
         typename V::T4 a = p.pb_v[v];
-        const T Tr = half * AR * (((Pp[0] + Pp[3]) - Pp[1]) - Pp[2]) + devr_rad;
+        const T Tr = (UNI ? half * ARb * (((Pp[0] + Pp[3]) - Pp[1]) - Pp[2])
+                          : half * (ARb * (Pp[0] - Pp[1]) + ARt * (Pp[3] - Pp[2]))) + devr_rad;
         const T rl = one - P.alpha_b * dt;     // relaxation of the auxiliaries
         a.z = a.z * rl - dt * d * Tr;
         a.w = a.w * rl - dt * d * devz_rad;
@@ -259,10 +324,11 @@ __device__ __forceinline__ void body_phase1(const ParamsT<T>& P, int bx, int by,
 // ---------------------------------------------------------------------------------
 // Phase 2: Lagrangian cell update from v^L.
 // ---------------------------------------------------------------------------------
-template <typename T, int NM, bool STR>
+template <typename T, int NM, bool STR, bool UNI>
 __device__ __forceinline__ void body_phase2(const ParamsT<T>& P, int bx, int by, int gx, int gy)
 {
     typedef VT<T> V;
+    typedef Geo<T, UNI> GE;
     const T zero = T(0), one = T(1), half = T(0.5), two = T(2);
     const int i = bx * blockDim.x + threadIdx.x;
     const int j = by * blockDim.y + threadIdx.y;
@@ -274,24 +340,23 @@ __device__ __forceinline__ void body_phase2(const ParamsT<T>& P, int bx, int by,
     if (!pos(phi)) {
 #pragma unroll
         for (int m = 0; m < NM; ++m) p.frL[m][c] = V::mk(zero, zero);
-        p.VL[c] = p.V[i];
+        p.VL[c] = GE::vol(P, i, j);
         p.IL[c] = 0.0;
         if (STR) { p.sL01[c] = V::mk(zero, zero); p.sL2d[c] = V::mk(zero, zero); }
         return;
     }
     const T dt = step_dt<T>(p.scal);
-    const T dx = P.dx;
     const int nv = nr + 1;
     const typename V::T2 va = p.vL[j * nv + i], vb = p.vL[j * nv + i + 1];
     const typename V::T2 vc = p.vL[(j + 1) * nv + i + 1], vd = p.vL[(j + 1) * nv + i];
     const T uL = half * (va.x + vd.x), uR = half * (vb.x + vc.x);
     const T uB = half * (va.y + vb.y), uT = half * (vd.y + vc.y);
-    const T idx = one / dx;
-    const T err = (uR - uL) * idx;
-    const T ezz = (uT - uB) * idx;
-    const T Vc = p.V[i];
+    const T idr = GE::idr(P, i), idz = GE::idz(P, j);
+    const T err = (uR - uL) * idr;
+    const T ezz = (uT - uB) * idz;
+    const T Vc = GE::vol(P, i, j);
     const T ett = (uR + uL) * p.inv2rc[i];
-    const T rad_flux = p.A_R[i + 1] * uR - p.A_R[i] * uL;
+    const T rad_flux = GE::flux_r(P, i, j, uL, uR);
     const T ver_flux = p.A_Z[i] * (uT - uB);
     const T dV = dt * (rad_flux + ver_flux);
     const T VLc = Vc + dV;
@@ -302,8 +367,8 @@ __device__ __forceinline__ void body_phase2(const ParamsT<T>& P, int bx, int by,
     if (STR) {
         const typename V::T2 s01 = p.s01[c], s2d = p.s2d[c];
         srr = s01.x; szz = s01.y; srz = s2d.x; D = s2d.y;
-        dvr_dz = half * ((vd.x + vc.x) - (va.x + vb.x)) * idx;
-        dvz_dr = half * ((vb.y + vc.y) - (va.y + vd.y)) * idx;
+        dvr_dz = half * ((vd.x + vc.x) - (va.x + vb.x)) * idz;
+        dvz_dr = half * ((vb.y + vc.y) - (va.y + vd.y)) * idr;
         const T Srr = phi * srr, Szz = phi * szz, Srz = phi * srz, Stt = -(Srr + Szz);
         const T erz = half * (dvr_dz + dvz_dr);
         work = dt * Vc * (Srr * err + Szz * ezz + Stt * ett + two * Srz * erz);
@@ -402,13 +467,13 @@ struct Acc {
 
 // Swept volume of the radial face at r_i of row j, and of the vertical face at z_j of
 // column i, from the Lagrangian velocities (computed identically by both neighbours).
-template <typename T>
+template <typename T, bool UNI>
 __device__ __forceinline__ T radial_dV(const ParamsT<T>& P, int i, int j, T dt)
 {
     if (i == 0 || i == P.nr) return T(0);
     const int nv = P.nr + 1;
     const T u = T(0.5) * (P.p.vL[j * nv + i].x + P.p.vL[(j + 1) * nv + i].x);
-    return dt * P.p.A_R[i] * u;
+    return dt * Geo<T, UNI>::area_r(P, i, j) * u;
 }
 template <typename T>
 __device__ __forceinline__ T vertical_dV(const ParamsT<T>& P, int i, int j, T dt)
@@ -453,7 +518,7 @@ __device__ __forceinline__ void move(const ParamsT<T>& P, int donor, T adV, T sg
     e_out = strip ? T(Id) * mass : T(0);
 }
 
-template <typename T, int NM, bool STR>
+template <typename T, int NM, bool STR, bool UNI>
 __device__ __forceinline__ void body_phase3a(const ParamsT<T>& P, int bx, int by, int gx, int gy)
 {
     typedef VT<T> V;
@@ -480,7 +545,7 @@ __device__ __forceinline__ void body_phase3a(const ParamsT<T>& P, int bx, int by
         T fm, fe;
         // left face r_i: positive dV flows from (i-1,j) into this cell
         {
-            const T dV = radial_dV<T>(P, i, j, dt);
+            const T dV = radial_dV<T, UNI>(P, i, j, dt);
             T sm = zero;
             if (!warp_any(nonzero(dV))) {
             } else if (pos(dV)) { move<T, NM, STR>(P, c - 1, dV, one, ILc, strip, acc, fm, fe); sm = fm; FRm -= fm; FRe -= fe; }
@@ -489,7 +554,7 @@ __device__ __forceinline__ void body_phase3a(const ParamsT<T>& P, int bx, int by
         }
         // right face r_{i+1}
         {
-            const T dV = radial_dV<T>(P, i + 1, j, dt);
+            const T dV = radial_dV<T, UNI>(P, i + 1, j, dt);
             if (!warp_any(nonzero(dV))) {
             } else if (pos(dV)) { move<T, NM, STR>(P, c, dV, -one, ILc, strip, acc, fm, fe); FRm += fm; FRe += fe; }
             else if (neg(dV)) { move<T, NM, STR>(P, c + 1, -dV, one, ILc, strip, acc, fm, fe); FRm -= fm; FRe -= fe; }
@@ -521,7 +586,7 @@ __device__ __forceinline__ void body_phase3a(const ParamsT<T>& P, int bx, int by
         // new state in increment form: q' = q^L + (net q-content flux - q^L net carrier
         // flux) / new carrier amount (exact when nothing flows); the energy change is the
         // inflows' (I_donor - I^L) mass, added in FP64
-        const T Vc = p.V[i];
+        const T Vc = Geo<T, UNI>::vol(P, i, j);
         T Vm[NM], Mm[NM], rn[NM];
         T MLtot = zero, VLmat = zero, dMtot = zero, dVtot = zero;
 #pragma unroll
@@ -811,14 +876,14 @@ __device__ __forceinline__ void body_phase3c(const ParamsT<T>& P, int bx, int by
 // reached their end time are skipped; each run keeps its own dt reduction).
 // ---------------------------------------------------------------------------------
 
-template <typename T, int NM, bool STR>
-__global__ void __launch_bounds__(kMaxThreads) k_phase0(ParamsT<T> P) { body_phase0<T, NM, STR>(P, blockIdx.x, blockIdx.y, gridDim.x, gridDim.y); }
-template <typename T, bool STR>
-__global__ void __launch_bounds__(kMaxThreads) k_phase1(ParamsT<T> P) { body_phase1<T, STR>(P, blockIdx.x, blockIdx.y, gridDim.x, gridDim.y); }
-template <typename T, int NM, bool STR>
-__global__ void __launch_bounds__(kMaxThreads) k_phase2(ParamsT<T> P) { body_phase2<T, NM, STR>(P, blockIdx.x, blockIdx.y, gridDim.x, gridDim.y); }
-template <typename T, int NM, bool STR>
-__global__ void __launch_bounds__(kMaxThreads) k_phase3a(ParamsT<T> P) { body_phase3a<T, NM, STR>(P, blockIdx.x, blockIdx.y, gridDim.x, gridDim.y); }
+template <typename T, int NM, bool STR, bool UNI>
+__global__ void __launch_bounds__(kMaxThreads) k_phase0(ParamsT<T> P) { body_phase0<T, NM, STR, UNI>(P, blockIdx.x, blockIdx.y, gridDim.x, gridDim.y); }
+template <typename T, bool STR, bool UNI>
+__global__ void __launch_bounds__(kMaxThreads) k_phase1(ParamsT<T> P) { body_phase1<T, STR, UNI>(P, blockIdx.x, blockIdx.y, gridDim.x, gridDim.y); }
+template <typename T, int NM, bool STR, bool UNI>
+__global__ void __launch_bounds__(kMaxThreads) k_phase2(ParamsT<T> P) { body_phase2<T, NM, STR, UNI>(P, blockIdx.x, blockIdx.y, gridDim.x, gridDim.y); }
+template <typename T, int NM, bool STR, bool UNI>
+__global__ void __launch_bounds__(kMaxThreads) k_phase3a(ParamsT<T> P) { body_phase3a<T, NM, STR, UNI>(P, blockIdx.x, blockIdx.y, gridDim.x, gridDim.y); }
 template <typename T>
 __global__ void __launch_bounds__(kMaxThreads) k_phase3b(ParamsT<T> P) { body_phase3b<T>(P, blockIdx.x, blockIdx.y, gridDim.x, gridDim.y); }
 template <typename T, int NM>
@@ -826,7 +891,7 @@ __global__ void __launch_bounds__(kMaxThreads) k_phase3c(ParamsT<T> P) { body_ph
 
 // phase 0 decides for the whole step: a run at or past its end time, or one whose status
 // reports a failure (non-positive volume or density, NaN, dt below dt_min), does nothing
-template <typename T, int NM, bool STR>
+template <typename T, int NM, bool STR, bool UNI>
 __global__ void __launch_bounds__(kMaxThreads) kb_phase0(const ParamsT<T>* __restrict__ runs, const BatchTile* __restrict__ work)
 {
     const BatchTile w = work[blockIdx.x];
@@ -836,7 +901,7 @@ __global__ void __launch_bounds__(kMaxThreads) kb_phase0(const ParamsT<T>* __res
         if (w.bx == 0 && w.by == 0 && threadIdx.x == 0 && threadIdx.y == 0) s->active = 0;
         return;
     }
-    body_phase0<T, NM, STR>(P, w.bx, w.by, w.g & 0xffff, w.g >> 16);
+    body_phase0<T, NM, STR, UNI>(P, w.bx, w.by, w.g & 0xffff, w.g >> 16);
 }
 #define SALEC_BATCHED(NAME, CALL)                                                          \
     {                                                                                      \
@@ -845,15 +910,15 @@ __global__ void __launch_bounds__(kMaxThreads) kb_phase0(const ParamsT<T>* __res
         if (P.p.scal->active == 0) return;                                                 \
         CALL(P, w.bx, w.by, w.g & 0xffff, w.g >> 16);                                      \
     }
-template <typename T, bool STR>
+template <typename T, bool STR, bool UNI>
 __global__ void __launch_bounds__(kMaxThreads) kb_phase1(const ParamsT<T>* __restrict__ runs, const BatchTile* __restrict__ work)
-SALEC_BATCHED(phase1, (body_phase1<T, STR>))
-template <typename T, int NM, bool STR>
+SALEC_BATCHED(phase1, (body_phase1<T, STR, UNI>))
+template <typename T, int NM, bool STR, bool UNI>
 __global__ void __launch_bounds__(kMaxThreads) kb_phase2(const ParamsT<T>* __restrict__ runs, const BatchTile* __restrict__ work)
-SALEC_BATCHED(phase2, (body_phase2<T, NM, STR>))
-template <typename T, int NM, bool STR>
+SALEC_BATCHED(phase2, (body_phase2<T, NM, STR, UNI>))
+template <typename T, int NM, bool STR, bool UNI>
 __global__ void __launch_bounds__(kMaxThreads) kb_phase3a(const ParamsT<T>* __restrict__ runs, const BatchTile* __restrict__ work)
-SALEC_BATCHED(phase3a, (body_phase3a<T, NM, STR>))
+SALEC_BATCHED(phase3a, (body_phase3a<T, NM, STR, UNI>))
 template <typename T>
 __global__ void __launch_bounds__(kMaxThreads) kb_phase3b(const ParamsT<T>* __restrict__ runs, const BatchTile* __restrict__ work)
 SALEC_BATCHED(phase3b, (body_phase3b<T>))
@@ -897,7 +962,6 @@ __global__ void k_column_heights(ParamsT<T> P, double* h)
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= P.nr) return;
     const int nr = P.nr, nz = P.nz;
-    const double dx = P.dxd;
     auto phi_at = [&](int j) {
         double f = 0.0;
 #pragma unroll
@@ -909,8 +973,8 @@ __global__ void k_column_heights(ParamsT<T> P, double* h)
     for (int j = nz - 1; j >= 0; --j) {
         const double phi = phi_at(j);
         if (phi >= 0.5) {
-            const double zc = (j + 0.5) * dx;
-            out = (j == nz - 1) ? zc : zc + (phi - 0.5) / (phi - up) * dx;
+            const double zc = P.p.zc[j];
+            out = (j == nz - 1) ? zc : zc + (phi - 0.5) / (phi - up) * (P.p.zc[j + 1] - zc);
             break;
         }
         up = phi;
@@ -934,7 +998,7 @@ __global__ void __launch_bounds__(kMaxThreads) k_conservation(ParamsT<T> P, doub
             const typename V::T2 fr = p.fr[m][cj * nr + ci];
             s += double(fr.x) * double(fr.y);
         }
-        return s * double(p.V[ci]);
+        return s * double(p.A_Z[ci] * p.dz[cj]);
     };
     double mass = 0.0, ie = 0.0, pz = 0.0, ke = 0.0;
     if (i < nr && j < nz) {
@@ -991,18 +1055,18 @@ const char* kernel_name(int k)
 
 // One cycle with per-kernel block shapes; with ev != nullptr an event is recorded before the
 // first kernel and after each kernel (7 events) for per-kernel durations.
-template <typename T, int NM, bool STR>
+template <typename T, int NM, bool STR, bool UNI>
 static cudaError_t step_impl(const ParamsT<T>& P, const dim3* blk, cudaStream_t s, cudaEvent_t* ev)
 {
     const int nr = P.nr, nz = P.nz;
     if (ev) cudaEventRecord(ev[0], s);
-    k_phase0<T, NM, STR><<<grid_of(nr, nz, blk[0]), blk[0], 0, s>>>(P);
+    k_phase0<T, NM, STR, UNI><<<grid_of(nr, nz, blk[0]), blk[0], 0, s>>>(P);
     if (ev) cudaEventRecord(ev[1], s);
-    k_phase1<T, STR><<<grid_of(nr + 1, nz + 1, blk[1]), blk[1], 0, s>>>(P);
+    k_phase1<T, STR, UNI><<<grid_of(nr + 1, nz + 1, blk[1]), blk[1], 0, s>>>(P);
     if (ev) cudaEventRecord(ev[2], s);
-    k_phase2<T, NM, STR><<<grid_of(nr, nz, blk[2]), blk[2], 0, s>>>(P);
+    k_phase2<T, NM, STR, UNI><<<grid_of(nr, nz, blk[2]), blk[2], 0, s>>>(P);
     if (ev) cudaEventRecord(ev[3], s);
-    k_phase3a<T, NM, STR><<<grid_of(nr, nz, blk[3]), blk[3], 0, s>>>(P);
+    k_phase3a<T, NM, STR, UNI><<<grid_of(nr, nz, blk[3]), blk[3], 0, s>>>(P);
     if (ev) cudaEventRecord(ev[4], s);
     k_phase3b<T><<<grid_of(nr + 1, nz + 1, blk[4]), blk[4], 0, s>>>(P);
     if (ev) cudaEventRecord(ev[5], s);
@@ -1015,28 +1079,36 @@ template <typename T>
 cudaError_t launch_step(const ParamsT<T>& P, const dim3* blk, cudaStream_t s, cudaEvent_t* ev)
 {
     const bool st = P.any_strength != 0;
+    if (P.uniform) {
+        switch (P.nmat) {
+        case 1: return st ? step_impl<T, 1, true, true>(P, blk, s, ev) : step_impl<T, 1, false, true>(P, blk, s, ev);
+        case 2: return st ? step_impl<T, 2, true, true>(P, blk, s, ev) : step_impl<T, 2, false, true>(P, blk, s, ev);
+        case 3: return st ? step_impl<T, 3, true, true>(P, blk, s, ev) : step_impl<T, 3, false, true>(P, blk, s, ev);
+        default: return cudaErrorInvalidValue;
+        }
+    }
     switch (P.nmat) {
-    case 1: return st ? step_impl<T, 1, true>(P, blk, s, ev) : step_impl<T, 1, false>(P, blk, s, ev);
-    case 2: return st ? step_impl<T, 2, true>(P, blk, s, ev) : step_impl<T, 2, false>(P, blk, s, ev);
-    case 3: return st ? step_impl<T, 3, true>(P, blk, s, ev) : step_impl<T, 3, false>(P, blk, s, ev);
+    case 1: return st ? step_impl<T, 1, true, false>(P, blk, s, ev) : step_impl<T, 1, false, false>(P, blk, s, ev);
+    case 2: return st ? step_impl<T, 2, true, false>(P, blk, s, ev) : step_impl<T, 2, false, false>(P, blk, s, ev);
+    case 3: return st ? step_impl<T, 3, true, false>(P, blk, s, ev) : step_impl<T, 3, false, false>(P, blk, s, ev);
     default: return cudaErrorInvalidValue;
     }
 }
 
 // One cycle of every run of a batch: work[k] lists the (run, tile) entries of kernel k
 // (ntiles[k] of them) for block shape blk[k].
-template <typename T, int NM, bool STR>
+template <typename T, int NM, bool STR, bool UNI>
 static cudaError_t batch_impl(const ParamsT<T>* runs, const BatchTile* const* work, const int* ntiles,
                               const dim3* blk, cudaStream_t s, cudaEvent_t* ev)
 {
     if (ev) cudaEventRecord(ev[0], s);
-    kb_phase0<T, NM, STR><<<ntiles[0], blk[0], 0, s>>>(runs, work[0]);
+    kb_phase0<T, NM, STR, UNI><<<ntiles[0], blk[0], 0, s>>>(runs, work[0]);
     if (ev) cudaEventRecord(ev[1], s);
-    kb_phase1<T, STR><<<ntiles[1], blk[1], 0, s>>>(runs, work[1]);
+    kb_phase1<T, STR, UNI><<<ntiles[1], blk[1], 0, s>>>(runs, work[1]);
     if (ev) cudaEventRecord(ev[2], s);
-    kb_phase2<T, NM, STR><<<ntiles[2], blk[2], 0, s>>>(runs, work[2]);
+    kb_phase2<T, NM, STR, UNI><<<ntiles[2], blk[2], 0, s>>>(runs, work[2]);
     if (ev) cudaEventRecord(ev[3], s);
-    kb_phase3a<T, NM, STR><<<ntiles[3], blk[3], 0, s>>>(runs, work[3]);
+    kb_phase3a<T, NM, STR, UNI><<<ntiles[3], blk[3], 0, s>>>(runs, work[3]);
     if (ev) cudaEventRecord(ev[4], s);
     kb_phase3b<T><<<ntiles[4], blk[4], 0, s>>>(runs, work[4]);
     if (ev) cudaEventRecord(ev[5], s);
@@ -1046,13 +1118,22 @@ static cudaError_t batch_impl(const ParamsT<T>* runs, const BatchTile* const* wo
 }
 
 template <typename T>
-cudaError_t launch_batch_step(const ParamsT<T>* runs_dev, int nmat, bool strength, const BatchTile* const* work,
+cudaError_t launch_batch_step(const ParamsT<T>* runs_dev, int nmat, bool strength, bool uniform, const BatchTile* const* work,
                               const int* ntiles, const dim3* blk, cudaStream_t s, cudaEvent_t* ev)
 {
+    // every run of the batch on a uniform grid: the uniform form
+    if (uniform) {
+        switch (nmat) {
+        case 1: return strength ? batch_impl<T, 1, true, true>(runs_dev, work, ntiles, blk, s, ev) : batch_impl<T, 1, false, true>(runs_dev, work, ntiles, blk, s, ev);
+        case 2: return strength ? batch_impl<T, 2, true, true>(runs_dev, work, ntiles, blk, s, ev) : batch_impl<T, 2, false, true>(runs_dev, work, ntiles, blk, s, ev);
+        case 3: return strength ? batch_impl<T, 3, true, true>(runs_dev, work, ntiles, blk, s, ev) : batch_impl<T, 3, false, true>(runs_dev, work, ntiles, blk, s, ev);
+        default: return cudaErrorInvalidValue;
+        }
+    }
     switch (nmat) {
-    case 1: return strength ? batch_impl<T, 1, true>(runs_dev, work, ntiles, blk, s, ev) : batch_impl<T, 1, false>(runs_dev, work, ntiles, blk, s, ev);
-    case 2: return strength ? batch_impl<T, 2, true>(runs_dev, work, ntiles, blk, s, ev) : batch_impl<T, 2, false>(runs_dev, work, ntiles, blk, s, ev);
-    case 3: return strength ? batch_impl<T, 3, true>(runs_dev, work, ntiles, blk, s, ev) : batch_impl<T, 3, false>(runs_dev, work, ntiles, blk, s, ev);
+    case 1: return strength ? batch_impl<T, 1, true, false>(runs_dev, work, ntiles, blk, s, ev) : batch_impl<T, 1, false, false>(runs_dev, work, ntiles, blk, s, ev);
+    case 2: return strength ? batch_impl<T, 2, true, false>(runs_dev, work, ntiles, blk, s, ev) : batch_impl<T, 2, false, false>(runs_dev, work, ntiles, blk, s, ev);
+    case 3: return strength ? batch_impl<T, 3, true, false>(runs_dev, work, ntiles, blk, s, ev) : batch_impl<T, 3, false, false>(runs_dev, work, ntiles, blk, s, ev);
     default: return cudaErrorInvalidValue;
     }
 }
@@ -1122,9 +1203,9 @@ template cudaError_t launch_batch_poll<float>(const ParamsT<float>*, int, double
 
 template cudaError_t launch_step<double>(const ParamsT<double>&, const dim3*, cudaStream_t, cudaEvent_t*);
 template cudaError_t launch_step<float>(const ParamsT<float>&, const dim3*, cudaStream_t, cudaEvent_t*);
-template cudaError_t launch_batch_step<double>(const ParamsT<double>*, int, bool, const BatchTile* const*, const int*,
+template cudaError_t launch_batch_step<double>(const ParamsT<double>*, int, bool, bool, const BatchTile* const*, const int*,
                                                const dim3*, cudaStream_t, cudaEvent_t*);
-template cudaError_t launch_batch_step<float>(const ParamsT<float>*, int, bool, const BatchTile* const*, const int*,
+template cudaError_t launch_batch_step<float>(const ParamsT<float>*, int, bool, bool, const BatchTile* const*, const int*,
                                               const dim3*, cudaStream_t, cudaEvent_t*);
 template cudaError_t launch_pressure<double>(const ParamsT<double>&, double*, cudaStream_t);
 template cudaError_t launch_pressure<float>(const ParamsT<float>&, double*, cudaStream_t);

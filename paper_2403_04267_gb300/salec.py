@@ -54,7 +54,7 @@ class salec_material(C.Structure):
 
 
 _lib = None
-EXPORTS = ["salec_state_bytes", "salec_create", "salec_set_material", "salec_add_layer",
+EXPORTS = ["salec_state_bytes", "salec_create", "salec_set_material", "salec_set_spacing", "salec_add_layer",
            "salec_place_projectile", "salec_finalize", "salec_step", "salec_get_scalars",
            "salec_set_time", "salec_get_field", "salec_set_field", "salec_crater_profile",
            "salec_conservation", "salec_checkpoint_bytes", "salec_get_state", "salec_set_state",
@@ -84,6 +84,7 @@ def load(build: bool = True):
         "salec_create": (I, [C.POINTER(salec_grid), I, P, Z, P, C.POINTER(P)]),
         "salec_set_material": (I, [P, I, C.POINTER(salec_material)]),
         "salec_add_layer": (I, [P, I, D, D, D, D, D]),
+        "salec_set_spacing": (I, [P, C.POINTER(C.c_double), C.POINTER(C.c_double)]),
         "salec_place_projectile": (I, [P, I, D, D, D, D, D]),
         "salec_finalize": (I, [P]),
         "salec_step": (I, [P, I]),
@@ -199,6 +200,15 @@ class Sim:
         for k, m in enumerate(spec["materials"]):
             mm = make_material(m)
             self._check(L.salec_set_material(h, k, C.byref(mm)))
+        gd = spec["grid"]
+        if gd.get("dr") is not None or gd.get("dz") is not None:
+            dr = np.ascontiguousarray(gd.get("dr", [gd["dx"]] * self.nr), dtype=np.float64)
+            dz = np.ascontiguousarray(gd.get("dz", [gd["dx"]] * self.nz), dtype=np.float64)
+            if dr.shape != (self.nr,) or dz.shape != (self.nz,):
+                raise ValueError("spacing arrays must have nr and nz entries")
+            self._check(L.salec_set_spacing(h, dr.ctypes.data_as(C.POINTER(C.c_double)),
+                                            dz.ctypes.data_as(C.POINTER(C.c_double))))
+            self.rc = np.cumsum(dr) - 0.5 * dr
         for lay in spec.get("layers", []):
             self._check(L.salec_add_layer(h, int(lay["mat"]), float(lay["zlo"]), float(lay["zhi"]),
                                           float(lay.get("rho", 0.0)), float(lay.get("I0", 0.0)),

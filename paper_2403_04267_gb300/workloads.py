@@ -143,6 +143,90 @@ def chicxulub_like(n: int = 462) -> dict:
     return w
 
 
+def stretched_sizes(n_core: int, dx: float, n_low: int = 0, n_high: int = 0, factor: float = 1.05,
+                    max_dx: float | None = None, pad_low: int = 0, pad_high: int = 0) -> list:
+    """Cell sizes along one axis, low end first: pad_low cells at the largest extension
+    size, n_low cells growing toward the low end, n_core cells of dx, n_high cells growing
+    toward the high end, pad_high cells at the largest size.  Extension cell k (1, 2, ...
+    outward) is dx factor^k, capped at max_dx (Table 2 of the paper: factor 1.05 from
+    400 m up to 1061 m)."""
+    def grow(n):
+        out, s = [], dx
+        for _ in range(n):
+            s = s * factor
+            if max_dx is not None and s > max_dx:
+                s = max_dx
+            out.append(s)
+        return out
+    lo, hi = grow(n_low), grow(n_high)
+    big_lo = lo[-1] if lo else dx
+    big_hi = hi[-1] if hi else dx
+    return [big_lo] * pad_low + lo[::-1] + [dx] * n_core + hi + [big_hi] * pad_high
+
+
+def positions(sizes) -> list:
+    """Vertex positions 0, s0, s0 + s1, ... summed one by one in order, as the library and
+    the oracle sum them (so that a height taken from here lies exactly on a row boundary)."""
+    out = [0.0]
+    for v in sizes:
+        out.append(out[-1] + float(v))
+    return out
+
+
+def stretched_impact(n_core: int, dx: float, n_ext: int, pml: int, target: dict, projectile_mat: dict | None,
+                     radius_cells: float, v_imp: float, surface_from_top: int, gravity: float = 0.0,
+                     factor: float = 1.05, max_dx: float | None = None, **gkw) -> dict:
+    """A half-space impact on the paper's kind of grid: an n_core x n_core zone of dx cells
+    at the axis, extension zones of n_ext growing cells on the right, at the bottom and at
+    the top, and PML strips of `pml` cells of the largest size outside the right and
+    bottom extensions.  The surface lies surface_from_top core rows below the top of the
+    core zone; the projectile sits on the axis, tangent to it."""
+    gkw.setdefault("pml_alpha", 0.1)
+    dr = stretched_sizes(n_core, dx, 0, n_ext, factor, max_dx, 0, pml)
+    dz = stretched_sizes(n_core, dx, n_ext, n_ext, factor, max_dx, pml, 0)
+    zs = positions(dz)[pml + n_ext + n_core - surface_from_top]
+    mats = [target] if projectile_mat is None else [target, projectile_mat]
+    R = radius_cells * dx
+    g = grid(len(dr), len(dz), dx, pml_r=pml, pml_b=pml, gravity=gravity, **gkw)
+    g["dr"], g["dz"] = dr, dz
+    return {
+        "grid": g,
+        "materials": mats,
+        "layers": [dict(mat=0, zlo=0.0, zhi=zs, rho=0.0, I0=0.0, vz=0.0)],
+        "projectile": dict(mat=0 if projectile_mat is None else 1, radius=R, zc=zs + R, vz=-abs(v_imp),
+                           rho=0.0, I0=0.0),
+        "z_surface": zs,
+    }
+
+
+def chicxulub_stretched(n_core: int = 462) -> dict:
+    """The paper's verification grid (Table 2, SALEc-2D+PML): a high-resolution zone of
+    n_core x n_core cells of 400 m, extension zones of 20 cells growing by 1.05 (to
+    1061 m) on the right, bottom and top, PML strips of 30 cells of 1061 m outside the
+    right and bottom extensions (reading: the strips lie beyond the extension zones, which
+    gives the same 231 km radial extent as the 50 extension cells of the runs without
+    PML).  The three-layer target of Sect. 4 with its surface 30 core rows below the top
+    of the zone; a 14.4 km dunite projectile at 12 km/s (the speed is not given)."""
+    dx, ext, pml = 400.0, 20, 30
+    dr = stretched_sizes(n_core, dx, 0, ext, 1.05, 1061.0, 0, pml)
+    dz = stretched_sizes(n_core, dx, ext, ext, 1.05, 1061.0, pml, 0)
+    zv = positions(dz)
+    ks = pml + ext + n_core - 30                 # the surface row boundary
+    zs, z_c, z_m = zv[ks], zv[ks - 7], zv[ks - 82]
+    g = grid(len(dr), len(dz), dx, pml_r=pml, pml_b=pml, gravity=9.81, pml_alpha=0.1)
+    g["dr"], g["dz"] = dr, dz
+    return {
+        "name": f"chicxulub_stretched_{len(dr)}x{len(dz)}",
+        "grid": g,
+        "materials": [calcite(), granite(), dunite()],
+        "layers": [dict(mat=0, zlo=z_c, zhi=zs, rho=0.0, I0=0.0, vz=0.0),
+                   dict(mat=1, zlo=z_m, zhi=z_c, rho=0.0, I0=0.0, vz=0.0),
+                   dict(mat=2, zlo=0.0, zhi=z_m, rho=0.0, I0=0.0, vz=0.0)],
+        "projectile": dict(mat=2, radius=18 * dx, zc=zs + 18 * dx, vz=-12e3, rho=0.0, I0=0.0),
+        "z_surface": zs,
+    }
+
+
 # --- the five configurations -------------------------------------------------------------
 
 def plain_fp64_100() -> dict:

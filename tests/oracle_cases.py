@@ -101,3 +101,24 @@ def axis_anomaly_history(sim, n: int, t_end: float, every: int = 10):
         dp = np.abs(sim.get("p") - p0)[j0:j1]
         out.append((sc["t"], dp[:, :int(0.08 * n)].max(), dp[:, int(0.40 * n):int(0.55 * n)].max()))
     return np.array(out)
+
+
+def stretched_layered_spec(n_core: int = 40, ext: int = 8, pml: int = 8) -> dict:
+    """The three-layer target under Earth gravity on a stretched grid: n_core x n_core
+    cells of 400 m, `ext` extension cells growing by 1.05 on the right, bottom and top,
+    `pml` strip cells of the largest size outside the right and bottom; 3 sediment and 12
+    crust rows below the surface (10 core rows below the top of the zone), mantle below; a
+    dunite sphere of radius 3 cells at 12 km/s."""
+    dx = 400.0
+    dr = W.stretched_sizes(n_core, dx, 0, ext, 1.05, None, 0, pml)
+    dz = W.stretched_sizes(n_core, dx, ext, ext, 1.05, None, pml, 0)
+    zv = W.positions(dz)
+    ks = pml + ext + n_core - 10
+    g = W.grid(len(dr), len(dz), dx, pml_r=pml, pml_b=pml, gravity=9.81, pml_alpha=0.1)
+    g["dr"], g["dz"] = dr, dz
+    return {"grid": g, "materials": [W.calcite(), W.granite(), W.dunite()],
+            "layers": [dict(mat=0, zlo=zv[ks - 3], zhi=zv[ks], rho=0.0, I0=0.0, vz=0.0),
+                       dict(mat=1, zlo=zv[ks - 15], zhi=zv[ks - 3], rho=0.0, I0=0.0, vz=0.0),
+                       dict(mat=2, zlo=0.0, zhi=zv[ks - 15], rho=0.0, I0=0.0, vz=0.0)],
+            "projectile": dict(mat=2, radius=3 * dx, zc=zv[ks] + 3 * dx, vz=-12e3, rho=0.0, I0=0.0),
+            "z_surface": zv[ks]}

@@ -49,9 +49,15 @@ def test_layered_column_matches_oracle_and_stays_at_rest():
     assert np.allclose(g.get("p"), r.get("p"), rtol=1e-12, atol=0.0)
     g.step(200)
     r.step(200)
-    _check(g, r, spec)
-    v = np.hypot(g.get("vr"), g.get("vz")).max()
-    assert v / np.sqrt(130e9 / 3320.0) <= 1e-12
+    # at rest both runs hold round-off motion only (|v| ~ 1e-12 c, I and s from it), so
+    # the comparison is of the state that is not round-off: densities and pressure
+    for name in ("rho0", "rho1", "rho2", "p"):
+        a, b = g.get(name), r.get(name)
+        assert np.max(np.abs(a - b)) <= 1e-12 * np.max(np.abs(b)), name
+    for sim in (g, r):
+        v = np.hypot(sim.get("vr"), sim.get("vz")).max()
+        assert v / np.sqrt(130e9 / 3320.0) <= 1e-12
+        assert sim.scalars()["status"] == 0
 
 
 def test_layered_impact_against_oracle():
