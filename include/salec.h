@@ -154,7 +154,10 @@ salec_status salec_place_projectile(salec_ctx* ctx, int mat, double radius, doub
  * profiles of Eq. 26, reference rows) and copy it to the device. */
 salec_status salec_finalize(salec_ctx* ctx);
 
-/* Enqueue nsteps full cycles on the context's stream (no host synchronisation). */
+/* Enqueue nsteps full cycles on the context's stream (no host synchronisation).  Whole
+ * chunks of 16 steps go out as one CUDA-graph launch each (captured on first use and
+ * again after the block shapes change; plain launches while per-kernel timing is on or
+ * where capture is not possible); the results are those of plain launches. */
 salec_status salec_step(salec_ctx* ctx, int nsteps);
 
 /* Synchronise and read the scalars: out[0] t, out[1] dt of the last step, out[2] step

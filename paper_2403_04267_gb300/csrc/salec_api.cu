@@ -157,6 +157,11 @@ struct salec_ctx {
     bool uniform = true;                  // every cell dx square
     double vol(int i, int j) const { return A_Z[i] * dz[j]; }
     std::string err;
+    // stepping in CUDA-graph replays of kGraphChunk steps (captured once per block-shape
+    // set; false after a capture failed, then plain launches)
+    cudaGraphExec_t graph = nullptr;
+    dim3 graph_shape[6];
+    bool graph_ok = true;
     // optional per-kernel timing: 7 events per recorded step
     bool timing = false;
     std::vector<cudaEvent_t> ev;
@@ -641,10 +646,58 @@ salec_status salec_finalize(salec_ctx* ctx)
     return SALEC_OK;
 }
 
+constexpr int kGraphChunk = 16;
+
+// Capture kGraphChunk steps on a private stream (a graph can then be launched into any
+// stream, the legacy default stream included).  False, with no error left pending, when
+// capture is not possible.
+static bool capture_step_graph(salec_ctx* ctx)
+{
+    if (ctx->graph) { cudaGraphExecDestroy(ctx->graph); ctx->graph = nullptr; }
+    cudaStream_t cs;
+    if (cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) != cudaSuccess) { (void)cudaGetLastError(); return false; }
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+    for (int k = 0; k < kGraphChunk && e == cudaSuccess; ++k)
+        e = mixed(ctx) ? launch_step<float>(ctx->Pf, ctx->shape, cs, nullptr)
+                       : launch_step<double>(ctx->Pd, ctx->shape, cs, nullptr);
+    const cudaError_t e2 = cudaStreamEndCapture(cs, &g);
+    if (e == cudaSuccess) e = e2;
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&ctx->graph, g, 0);
+    if (g) cudaGraphDestroy(g);
+    cudaStreamDestroy(cs);
+    if (e != cudaSuccess) {
+        (void)cudaGetLastError();
+        ctx->graph = nullptr;
+        return false;
+    }
+    for (int k = 0; k < 6; ++k) ctx->graph_shape[k] = ctx->shape[k];
+    return true;
+}
+
+static bool same_shapes(const dim3* a, const dim3* b)
+{
+    for (int k = 0; k < 6; ++k)
+        if (a[k].x != b[k].x || a[k].y != b[k].y) return false;
+    return true;
+}
+
 salec_status salec_step(salec_ctx* ctx, int nsteps)
 {
     if (!ctx || nsteps < 0) return SALEC_EINVAL;
     if (!ctx->finalized) return fail(ctx, SALEC_EORDER, "step before finalize");
+    // whole chunks as graph replays (the kernel arguments are fixed after finalize; the
+    // graph is captured again when the block shapes change)
+    if (!ctx->timing && nsteps >= kGraphChunk && ctx->graph_ok) {
+        if (ctx->graph && !same_shapes(ctx->graph_shape, ctx->shape)) { cudaGraphExecDestroy(ctx->graph); ctx->graph = nullptr; }
+        if (!ctx->graph) ctx->graph_ok = capture_step_graph(ctx);
+        if (ctx->graph) {
+            for (; nsteps >= kGraphChunk; nsteps -= kGraphChunk) {
+                const cudaError_t e = cudaGraphLaunch(ctx->graph, ctx->stream);
+                if (e != cudaSuccess) return cuda_check(ctx, e, "step graph launch");
+            }
+        }
+    }
     const int K = launches_per_step() + 1;
     for (int n = 0; n < nsteps; ++n) {
         cudaEvent_t* evp = nullptr;
@@ -1382,6 +1435,7 @@ const char* salec_last_error(const salec_ctx* ctx)
 void salec_destroy(salec_ctx* ctx)
 {
     if (!ctx) return;
+    if (ctx->graph) cudaGraphExecDestroy(ctx->graph);
     for (cudaEvent_t e : ctx->ev) cudaEventDestroy(e);
     delete ctx;
 }
