@@ -53,6 +53,7 @@ struct DevScalars {
     double t, dt, dt_prev, t_end;   // t_end: a batched run stops stepping once t >= t_end
     double mass_out, mass_discarded, mass_pml, zmom_out;
     unsigned long long nstep;
+    unsigned long long maxbits;   // running max of the blocks' Courant rates (FP64 bit patterns)
     unsigned int counter;   // last-block counter of the dt reduction
     int status;             // bit 1: non-positive volume or density, 2: NaN, 4: dt < dt_min
     int active;             // the run stepped in the current batched step

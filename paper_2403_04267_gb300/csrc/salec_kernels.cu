@@ -177,47 +177,35 @@ __device__ __forceinline__ void body_phase0(const ParamsT<T>& P, int bx, int by,
         p.PM[c] = V::mk(Pc, mass * GE::vol(P, i, j));
         p.pbphi[c] = V::mk(pbar, phi);
     }
-    // block maximum (on the bit patterns of the non-negative speeds), then the last block
-    // to finish reduces the block maxima
-    __shared__ long long sh[kMaxThreads / 32];
-    __shared__ bool last;
+    // block maximum (on the bit patterns of the non-negative speeds) into one running
+    // maximum per run by an atomic max; the last block to finish turns it into dt.  After
+    // the one barrier only thread 0 works, so the other warps leave at once.
+    __shared__ unsigned long long sh[kMaxThreads / 32];
     const int tid = threadIdx.y * blockDim.x + threadIdx.x;
     const int nw = (blockDim.x * blockDim.y) >> 5;
     for (int o = 16; o > 0; o >>= 1) speed = max_nonneg(speed, __shfl_down_sync(0xffffffffu, speed, o));
-    if ((tid & 31) == 0) sh[tid >> 5] = __double_as_longlong(double(speed));
+    if ((tid & 31) == 0) sh[tid >> 5] = (unsigned long long)__double_as_longlong(double(speed));
     __syncthreads();
-    const int nblk = gx * gy;
-    long long* part = reinterpret_cast<long long*>(p.partial);
-    if (tid == 0) {
-        long long b = sh[0];
-        for (int w = 1; w < nw; ++w) b = max(b, sh[w]);
-        part[by * gx + bx] = b;
-        __threadfence();
-        const unsigned prev = atomicAdd(&p.scal->counter, 1u);
-        last = (prev == (unsigned)(nblk - 1));
-    }
-    __syncthreads();
-    if (!last) return;
+    if (tid != 0) return;
+    unsigned long long b = sh[0];
+    for (int w = 1; w < nw; ++w) b = max(b, sh[w]);
+    DevScalars* s = p.scal;
+    atomicMax(&s->maxbits, b);
     __threadfence();
-    long long m = 0;
-    for (int k = tid; k < nblk; k += nw * 32) m = max(m, __ldcg(&part[k]));
-    for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_down_sync(0xffffffffu, m, o));
-    if ((tid & 31) == 0) sh[tid >> 5] = m;
-    __syncthreads();
-    if (tid == 0) {
-        long long b = sh[0];
-        for (int w = 1; w < nw; ++w) b = max(b, sh[w]);
-        DevScalars* s = p.scal;
-        double dt = P.growth * s->dt_prev;
-        const double cdt = UNI ? P.cfld * (P.dxd / __longlong_as_double(b)) : P.cfld / __longlong_as_double(b);
-        dt = cdt < dt ? cdt : dt;
-        dt = P.dt_max < dt ? P.dt_max : dt;
-        if (dt < P.dt_min) s->status |= 4;
-        s->dt = dt;
-        s->dtf = float(dt);
-        s->active = 1;
-        s->counter = 0u;
-    }
+    const unsigned prev = atomicAdd(&s->counter, 1u);
+    if (prev != (unsigned)(gx * gy - 1)) return;
+    // every other block's maximum is in (its atomic preceded its fence and its count)
+    __threadfence();
+    const double mx = __longlong_as_double((long long)atomicExch(&s->maxbits, 0ull));
+    double dt = P.growth * s->dt_prev;
+    const double cdt = UNI ? P.cfld * (P.dxd / mx) : P.cfld / mx;
+    dt = cdt < dt ? cdt : dt;
+    dt = P.dt_max < dt ? P.dt_max : dt;
+    if (dt < P.dt_min) s->status |= 4;
+    s->dt = dt;
+    s->dtf = float(dt);
+    s->active = 1;
+    s->counter = 0u;
 }
 
 // ---------------------------------------------------------------------------------
