@@ -464,202 +464,292 @@ __global__ void __launch_bounds__(kGemmThreads) k_gemm_bf16_tma(const __grid_con
 }
 
 // ---------------------------------------------------------------------------------------
-// The whole network's forward pass in one kernel (inference).  A CTA takes 128 samples;
-// their activations never leave the SM: each layer's epilogue writes gelu(Z) as BF16
-// straight into shared memory in the canonical K-major layout, where it is the next
-// layer's A operand.  The accumulator (128 x 256 FP32) lives in tensor memory.  Weights
-// stream from L2 with TMA, one 64-wide K slice (256 rows x 128 bytes) at a time; the first
-// slice of the next layer is issued as soon as a layer's last MMAs are done, so it lands
-// while the epilogue runs.  Shared memory: activations 64 KB + one weight stage 32 KB, so
-// two CTAs fit on an SM (and 2 x 256 of its 512 TMEM columns), each overlapping its MMA
-// chain with the other's epilogue.  The epilogue is the bulk of the instructions (an erf
-// per element), so it is spread over 16 warps: warp w reads TMEM lanes 32 (w mod 4) ..
-// + 31 (its rows) and column quarter w / 4 (64 columns).
+// Shapes of the whole-network inference kernel below: hidden width 256, outputs padded to
+// 80, an activation tile of 128 x 256 BF16, a weight slice of 256 rows x 64 K.
 // ---------------------------------------------------------------------------------------
 constexpr int kFusedHid = 256;
 constexpr int kFusedOutPad = 80;      // 66 outputs padded to a multiple of 16
-constexpr int kFusedThreads = 512;
 constexpr uint32_t kHBytes = kBM * kFusedHid * 2;          // 65536
 constexpr uint32_t kWStageBytes = kFusedHid * kBK * 2;     // 32768
-
-size_t fused_smem_bytes() { return (size_t)kHBytes + kWStageBytes + 1024; }
-
-struct FusedArgs {
-    int B;                                   // samples
-    const __nv_bfloat16* X;                  // [B][ld_x] BF16 inputs, columns >= 5 zero
-    int ld_x;
-    const __nv_bfloat16* W1;                 // [256][ld_x] BF16, columns >= 5 zero
-    const float* bias[5];
-    float* Y;                                // [B][66]
-    int* err;
-};
 
 // core-matrix offset of (row r, 8-column group kg) in a K-major tile of `rows` rows
 __device__ __forceinline__ uint32_t cm_off(int r, int kg, int rows) { return kg * (rows * 16) + (r >> 3) * 128 + (r & 7) * 16; }
 
-__global__ void __launch_bounds__(kFusedThreads, 2) k_mlp_forward_fused(const __grid_constant__ CUtensorMap mW2,
-                                                                        const __grid_constant__ CUtensorMap mW3,
-                                                                        const __grid_constant__ CUtensorMap mW4,
-                                                                        const __grid_constant__ CUtensorMap mW5,
-                                                                        FusedArgs a)
+// ---------------------------------------------------------------------------------------
+// The inference pass, persistent and warp-specialised: one CTA per SM takes 128-sample
+// tiles two at a time and alternates them, so that the tensor cores work on one tile while
+// the epilogue warps work on the other.  Per tile x (0, 1): an activation buffer H_x (BF16,
+// canonical K-major, 64 KB) and a 256-column accumulator in tensor memory (both tiles: all
+// 512 columns).  Warp 0 streams the weight slices (64-wide K slices, 256 rows x 128 bytes)
+// with TMA into a 2-stage ring, 128-byte swizzled; warp 1 issues the MMAs of job (x, layer)
+// once H_x holds that layer's input and frees each ring stage by tcgen05.commit; warps
+// 2-17 run the epilogue of job (x, layer) when its accumulator is complete: gelu(Z + b) as
+// BF16 back into H_x (the next layer's input), or Y for the output layer followed by the
+// inputs of the tile's successor.  Jobs run in the order (pair, layer, tile) in every role.
+// mbarriers: ring stage full / empty, accumulator x complete, H_x ready (16 epilogue warps).
+// Every wait is bounded; a wait that runs out raises a shared abort flag that ends every
+// role's loop, after which the CTA waits (bounded) for its own copies and MMAs, frees its
+// tensor memory and returns.
+// ---------------------------------------------------------------------------------------
+constexpr int kPPThreads = 18 * 32;
+constexpr uint32_t kW1Bytes = kFusedHid * 16 * 2;          // layer-1 weights, K padded to 16
+constexpr int kPPStages = 2;
+
+size_t pp_smem_bytes() { return 2 * (size_t)kHBytes + kPPStages * (size_t)kWStageBytes + kW1Bytes + 1024; }
+
+// descriptor of a K-major operand in the 128-byte swizzled layout: rows of 128 bytes, 8-row
+// groups 1024 bytes apart (stride-dimension offset), swizzle mode 2 at bits 61-63; the
+// leading-dimension offset is unused for K extents within one 128-byte row
+__device__ __forceinline__ uint64_t sdesc_sw128(uint32_t saddr)
+{
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);
+    d |= (uint64_t)1 << 16;
+    d |= (uint64_t)(1024 >> 4) << 32;
+    d |= (uint64_t)1 << 46;
+    d |= (uint64_t)2 << 61;
+    return d;
+}
+
+// bounded wait of a thread that has nothing else to do: it backs off between polls so
+// that the warps doing arithmetic on its SM sub-partition keep the issue slots
+__device__ __forceinline__ bool mbar_wait_idle(uint64_t* bar, uint32_t parity)
+{
+    const unsigned long long t0 = global_ns();
+    while (!mbar_try_wait(bar, parity)) {
+        if (global_ns() - t0 > kWaitNs) return false;
+        __nanosleep(64);
+    }
+    return true;
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+struct PPArgs {
+    int B, ntiles, npairs;
+    const __nv_bfloat16* X;
+    int ld_x;
+    const __nv_bfloat16* W1;
+    const float* bias[5];
+    float* Y;
+    int* err;
+};
+
+__global__ void __launch_bounds__(kPPThreads, 1) k_mlp_forward_pp(const __grid_constant__ CUtensorMap mW2,
+                                                                 const __grid_constant__ CUtensorMap mW3,
+                                                                 const __grid_constant__ CUtensorMap mW4,
+                                                                 const __grid_constant__ CUtensorMap mW5,
+                                                                 PPArgs a)
 {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     unsigned char* smem = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-    unsigned char* H = smem;                    // activations, 32 column groups of 2048 B
-    unsigned char* Ws = smem + kHBytes;         // one weight stage
+    unsigned char* Hbuf = smem;                                   // H_0, H_1
+    unsigned char* Wring = smem + 2 * kHBytes;                    // 2 stages, 1024-aligned
+    unsigned char* W1s = Wring + kPPStages * kWStageBytes;        // layer-1 weights
     __shared__ __align__(16) float sbias[4 * kFusedHid + kFusedOutPad];
-    __shared__ uint64_t wbar, mbar;
+    __shared__ uint64_t wfull[kPPStages], wempty[kPPStages], accfull[2], hready[2];
     __shared__ uint32_t tmem_holder;
-    __shared__ int ok_flag;
+    __shared__ volatile int abort_flag;
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int m0 = blockIdx.x * kBM;
-    const int quarter = warp & 3;               // TMEM lanes 32 quarter .. + 31 (rows of the tile)
-    const int cq = warp >> 2;                   // column quarter of the epilogue
-    const int r = quarter * 32 + lane;          // this thread's row of the tile
-    const int m = m0 + r;
-    const uint32_t tmem_cols = kFusedHid;
-
+    const int G = gridDim.x;
     if (tid == 0) {
-        mbar_init(&wbar, 1);
-        mbar_init(&mbar, 1);
+        for (int k = 0; k < kPPStages; ++k) { mbar_init(&wfull[k], 1); mbar_init(&wempty[k], 1); }
+        for (int x = 0; x < 2; ++x) { mbar_init(&accfull[x], 1); mbar_init(&hready[x], 16); }
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-        ok_flag = 1;
+        abort_flag = 0;
     }
-    __syncwarp();
-    if (warp == 0) {
+    if (warp == 1) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_holder)),
-                     "r"(tmem_cols)
+                     "r"(512)
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
-    // biases of all layers (zero in the output layer's padding)
-    for (int k = tid; k < 4 * kFusedHid + kFusedOutPad; k += kFusedThreads) {
+    for (int k = tid; k < 4 * kFusedHid + kFusedOutPad; k += kPPThreads) {
         const int l = k / kFusedHid, n = k - l * kFusedHid;
         sbias[k] = l < 4 ? a.bias[l][n] : (n < SALEC_MLP_OUT_N ? a.bias[4][n] : 0.0f);
     }
-    // layer 1 operands by the threads: X rows (8 BF16 = one core-matrix row) and W1 rows,
-    // K padded to 16 with a zero column group
-    if (tid < kBM) {
-        uint4 xv = make_uint4(0u, 0u, 0u, 0u);
-        if (m0 + tid < a.B) xv = *reinterpret_cast<const uint4*>(a.X + (long)(m0 + tid) * a.ld_x);
-        *reinterpret_cast<uint4*>(H + cm_off(tid, 0, kBM)) = xv;
-        *reinterpret_cast<uint4*>(H + cm_off(tid, 1, kBM)) = make_uint4(0u, 0u, 0u, 0u);
-    } else if (tid < kBM + kFusedHid) {
-        const int n = tid - kBM;
-        *reinterpret_cast<uint4*>(Ws + cm_off(n, 0, kFusedHid)) = *reinterpret_cast<const uint4*>(a.W1 + (long)n * a.ld_x);
-        *reinterpret_cast<uint4*>(Ws + cm_off(n, 1, kFusedHid)) = make_uint4(0u, 0u, 0u, 0u);
+    for (int n = tid; n < kFusedHid; n += kPPThreads) {
+        *reinterpret_cast<uint4*>(W1s + cm_off(n, 0, kFusedHid)) = *reinterpret_cast<const uint4*>(a.W1 + (long)n * a.ld_x);
+        *reinterpret_cast<uint4*>(W1s + cm_off(n, 1, kFusedHid)) = make_uint4(0u, 0u, 0u, 0u);
     }
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const uint32_t tmem = tmem_holder;
-    const uint32_t trow = tmem + ((uint32_t)(quarter * 32) << 16);
-    const uint32_t hbase = smem_u32(H), wbase = smem_u32(Ws);
-    uint32_t wphase = 0, mphase = 0;     // completed phases of the two barriers (thread 0's view)
-    bool good = true;
-    bool in_flight = false, mma_pending = false;  // thread 0: a weight load / MMAs not yet waited for
-
-    // thread 0: TMA of K slice kt of layer l's weights into the stage
-    auto load_slice = [&](int l, int kt) {
-        const int N = l == 4 ? kFusedOutPad : kFusedHid;
-        const CUtensorMap* map = l == 1 ? &mW2 : l == 2 ? &mW3 : l == 3 ? &mW4 : &mW5;
-        mbar_expect_tx(&wbar, (uint32_t)N * kBK * 2);
-#pragma unroll
-        for (int kg = 0; kg < kBK / 8; ++kg) tma_load_2d(wbase + kg * (N * 16), map, kt * kBK + 8 * kg, 0, &wbar);
-        in_flight = true;
+    // tile of slot x of the k-th pair of this CTA (-1: none)
+    auto tile_of = [&](int k, int x) {
+        const int t = 2 * (blockIdx.x + k * G) + x;
+        return (blockIdx.x + k * G < a.npairs && t < a.ntiles) ? t : -1;
     };
+    const int npairs_mine = a.npairs > (int)blockIdx.x ? (a.npairs - 1 - (int)blockIdx.x) / G + 1 : 0;
 
-    for (int layer = 0; layer < 5; ++layer) {
-        const int N = layer == 4 ? kFusedOutPad : kFusedHid;
-        const uint32_t idesc = idesc_bf16(kBM, N);
-        const int nslices = layer == 0 ? 1 : kFusedHid / kBK;
-        if (tid == 0) {
-            for (int kt = 0; kt < nslices && good; ++kt) {
-                if (layer > 0) {
-                    // slice 0 was issued at the end of the previous layer; the stage is free
-                    // for the others because the previous slice's MMAs were waited for
-                    if (kt > 0) load_slice(layer, kt);
-                    good = mbar_wait(&wbar, wphase & 1u);
-                    if (!good) break;
-                    in_flight = false;
-                    ++wphase;
-                }
-                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-                const int kks = layer == 0 ? 1 : kBK / 16;
-                for (int kk = 0; kk < kks; ++kk) {
-                    const uint64_t ad = sdesc(hbase + (kt * (kBK / 8) + 2 * kk) * (kBM * 16), kBM * 16, 128);
-                    const uint64_t bd = sdesc(wbase + 2 * kk * (N * 16), N * 16, 128);
-                    mma_bf16(tmem, ad, bd, idesc, (kt > 0 || kk > 0) ? 1u : 0u);
-                }
-                mma_commit(&mbar);
-                mma_pending = true;
-                good = mbar_wait(&mbar, mphase & 1u);
-                if (good) {
-                    mma_pending = false;
-                    ++mphase;
-                }
-            }
-            // every MMA of the layer is done: the next layer's first slice can land while
-            // the epilogue below runs
-            if (good && layer < 4) load_slice(layer + 1, 0);
-            if (!good) ok_flag = 0;
+    if (warp == 0) {
+        // ---- weight producer ----
+        if (lane == 0) {
+            int fills[kPPStages] = {0, 0};
+            int stage = 0;
+            for (int k = 0; k < npairs_mine && !abort_flag; ++k)
+                for (int l = 1; l < 5 && !abort_flag; ++l)
+                    for (int x = 0; x < 2 && !abort_flag; ++x) {
+                        if (tile_of(k, x) < 0) continue;
+                        const int N = l == 4 ? kFusedOutPad : kFusedHid;
+                        const CUtensorMap* map = l == 1 ? &mW2 : l == 2 ? &mW3 : l == 3 ? &mW4 : &mW5;
+                        for (int kt = 0; kt < kFusedHid / kBK; ++kt) {
+                            if (fills[stage] > 0 && !mbar_wait_idle(&wempty[stage], (uint32_t)(fills[stage] - 1) & 1u)) {
+                                abort_flag = 1;
+                                break;
+                            }
+                            mbar_expect_tx(&wfull[stage], (uint32_t)N * 128u);
+                            tma_load_2d(smem_u32(Wring + stage * kWStageBytes), map, kt * kBK, 0, &wfull[stage]);
+                            ++fills[stage];
+                            stage ^= 1;
+                        }
+                    }
+            // the last copies of each stage land before the CTA's memory can go away
+            for (int st = 0; st < kPPStages; ++st)
+                if (fills[st] > 0) (void)mbar_wait(&wfull[st], (uint32_t)(fills[st] - 1) & 1u);
         }
-        __syncthreads();                 // every MMA of the layer is done (or the CTA gave up)
-        if (!ok_flag) break;
-        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        const float* bias = sbias + layer * kFusedHid;
-        if (layer < 4) {
-            // gelu(Z) as BF16 into the activations, in the layout the next layer reads
-            const bool live = m < a.B;
-#pragma unroll 1
-            for (int c0 = cq * 64; c0 < cq * 64 + 64; c0 += 16) {
-                float v[16];
-                tmem_ld16(trow + (uint32_t)c0, v);
-                uint32_t w[8] = {0u, 0u, 0u, 0u, 0u, 0u, 0u, 0u};
-                if (live) {
-                    const float4* b4 = reinterpret_cast<const float4*>(bias + c0);
+    } else if (warp == 1) {
+        // ---- MMA issuer ----
+        if (lane == 0) {
+            int used[kPPStages] = {0, 0}, hwait[2] = {0, 0}, commits[2] = {0, 0};
+            int stage = 0;
+            const uint32_t w1 = smem_u32(W1s);
+            for (int k = 0; k < npairs_mine && !abort_flag; ++k)
+                for (int l = 0; l < 5 && !abort_flag; ++l)
+                    for (int x = 0; x < 2 && !abort_flag; ++x) {
+                        if (tile_of(k, x) < 0) continue;
+                        if (!mbar_wait_idle(&hready[x], (uint32_t)(hwait[x]++) & 1u)) { abort_flag = 1; break; }
+                        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                        const int N = l == 4 ? kFusedOutPad : kFusedHid;
+                        const uint32_t idesc = idesc_bf16(kBM, N);
+                        const uint32_t acc = tmem + (uint32_t)(x * kFusedHid);
+                        const uint32_t hb = smem_u32(Hbuf + x * kHBytes);
+                        if (l == 0) {
+                            mma_bf16(acc, sdesc(hb, kBM * 16, 128), sdesc(w1, kFusedHid * 16, 128), idesc, 0u);
+                        } else {
+                            for (int kt = 0; kt < kFusedHid / kBK; ++kt) {
+                                if (!mbar_wait(&wfull[stage], (uint32_t)(used[stage]++) & 1u)) { abort_flag = 1; break; }
+                                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                                const uint32_t wb = smem_u32(Wring + stage * kWStageBytes);
 #pragma unroll
-                    for (int q = 0; q < 4; ++q) {
-                        const float4 b = b4[q];
-                        const __nv_bfloat162 lo = __floats2bfloat162_rn(gelu_f(v[4 * q] + b.x), gelu_f(v[4 * q + 1] + b.y));
-                        const __nv_bfloat162 hi = __floats2bfloat162_rn(gelu_f(v[4 * q + 2] + b.z), gelu_f(v[4 * q + 3] + b.w));
-                        w[2 * q] = *reinterpret_cast<const uint32_t*>(&lo);
-                        w[2 * q + 1] = *reinterpret_cast<const uint32_t*>(&hi);
+                                for (int kk = 0; kk < kBK / 16; ++kk) {
+                                    const uint64_t ad = sdesc(hb + (kt * (kBK / 8) + 2 * kk) * (kBM * 16), kBM * 16, 128);
+                                    mma_bf16(acc, ad, sdesc_sw128(wb + kk * 32), idesc, (kt > 0 || kk > 0) ? 1u : 0u);
+                                }
+                                mma_commit(&wempty[stage]);
+                                stage ^= 1;
+                            }
+                            if (abort_flag) break;
+                        }
+                        mma_commit(&accfull[x]);
+                        ++commits[x];
+                    }
+            // MMAs still in flight finish before the tensor memory is freed
+            if (abort_flag)
+                for (int x = 0; x < 2; ++x)
+                    if (commits[x] > 0) (void)mbar_wait(&accfull[x], (uint32_t)(commits[x] - 1) & 1u);
+        }
+    } else {
+        // ---- epilogue: warps 2-17; lane quarter q (TMEM lanes 32q..), column quarter cq ----
+        const int q = warp & 3, cq = (warp - 2) >> 2;
+        const int r = q * 32 + lane;                         // row of the tile
+        const uint32_t trow = tmem + ((uint32_t)(q * 32) << 16);
+        int accw[2] = {0, 0};
+        // the warp decides together: an abort seen by any lane ends the warp's loop
+        auto aborted = [&]() { return __any_sync(0xffffffffu, abort_flag != 0); };
+        // inputs of tile t into H_x: X rows (8 BF16 = one core-matrix row), K padded to 16
+        auto stage_inputs = [&](int x, int t) {
+            if (cq == 0) {
+                const int m = t * kBM + r;
+                uint4 xv = make_uint4(0u, 0u, 0u, 0u);
+                if (m < a.B) xv = *reinterpret_cast<const uint4*>(a.X + (long)m * a.ld_x);
+                unsigned char* H = Hbuf + x * kHBytes;
+                *reinterpret_cast<uint4*>(H + cm_off(r, 0, kBM)) = xv;
+                *reinterpret_cast<uint4*>(H + cm_off(r, 1, kBM)) = make_uint4(0u, 0u, 0u, 0u);
+            }
+        };
+        auto release = [&](int x) {
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&hready[x]);
+        };
+        for (int x = 0; x < 2; ++x) {
+            const int t = tile_of(0, x);
+            if (t < 0) continue;
+            stage_inputs(x, t);
+            release(x);
+        }
+        bool stop = aborted();
+        for (int k = 0; k < npairs_mine && !stop; ++k)
+            for (int l = 0; l < 5 && !stop; ++l)
+                for (int x = 0; x < 2 && !(stop = aborted()); ++x) {
+                    const int t = tile_of(k, x);
+                    if (t < 0) continue;
+                    const bool ok = __all_sync(0xffffffffu, mbar_wait(&accfull[x], (uint32_t)(accw[x]++) & 1u));
+                    if (!ok) {
+                        abort_flag = 1;
+                        stop = true;
+                        break;
+                    }
+                    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                    const uint32_t tacc = trow + (uint32_t)(x * kFusedHid);
+                    const int m = t * kBM + r;
+                    const bool live = m < a.B;
+                    const float* bias = sbias + l * kFusedHid;
+                    if (l < 4) {
+                        unsigned char* H = Hbuf + x * kHBytes;
+#pragma unroll 1
+                        for (int c0 = cq * 64; c0 < cq * 64 + 64; c0 += 16) {
+                            float v[16];
+                            tmem_ld16(tacc + (uint32_t)c0, v);
+                            uint32_t w[8] = {0u, 0u, 0u, 0u, 0u, 0u, 0u, 0u};
+                            if (live) {
+                                const float4* b4 = reinterpret_cast<const float4*>(bias + c0);
+#pragma unroll
+                                for (int qq = 0; qq < 4; ++qq) {
+                                    const float4 b = b4[qq];
+                                    const __nv_bfloat162 lo = __floats2bfloat162_rn(gelu_f(v[4 * qq] + b.x), gelu_f(v[4 * qq + 1] + b.y));
+                                    const __nv_bfloat162 hi = __floats2bfloat162_rn(gelu_f(v[4 * qq + 2] + b.z), gelu_f(v[4 * qq + 3] + b.w));
+                                    w[2 * qq] = *reinterpret_cast<const uint32_t*>(&lo);
+                                    w[2 * qq + 1] = *reinterpret_cast<const uint32_t*>(&hi);
+                                }
+                            }
+                            *reinterpret_cast<uint4*>(H + cm_off(r, (c0 >> 3), kBM)) = make_uint4(w[0], w[1], w[2], w[3]);
+                            *reinterpret_cast<uint4*>(H + cm_off(r, (c0 >> 3) + 1, kBM)) = make_uint4(w[4], w[5], w[6], w[7]);
+                        }
+                        release(x);
+                    } else {
+                        for (int c0 = cq * 16; c0 < kFusedOutPad; c0 += 64) {
+                            float v[16];
+                            tmem_ld16(tacc + (uint32_t)c0, v);
+                            if (live) {
+                                float* y = a.Y + (long)m * SALEC_MLP_OUT_N + c0;
+#pragma unroll
+                                for (int j = 0; j < 16; ++j)
+                                    if (c0 + j < SALEC_MLP_OUT_N) y[j] = v[j] + bias[c0 + j];
+                            }
+                        }
+                        // the accumulator is read and H_x is free: the successor's inputs
+                        const int tn = tile_of(k + 1, x);
+                        if (tn >= 0) {
+                            stage_inputs(x, tn);
+                            release(x);
+                        }
                     }
                 }
-                *reinterpret_cast<uint4*>(H + cm_off(r, (c0 >> 3), kBM)) = make_uint4(w[0], w[1], w[2], w[3]);
-                *reinterpret_cast<uint4*>(H + cm_off(r, (c0 >> 3) + 1, kBM)) = make_uint4(w[4], w[5], w[6], w[7]);
-            }
-            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        } else {
-            // 80 padded columns in chunks of 16: chunk cq, and chunk 4 by the first quarter
-            for (int c0 = cq * 16; c0 < kFusedOutPad; c0 += 64) {
-                float v[16];
-                tmem_ld16(trow + (uint32_t)c0, v);
-                if (m < a.B) {
-                    float* y = a.Y + (long)m * SALEC_MLP_OUT_N + c0;
-#pragma unroll
-                    for (int j = 0; j < 16; ++j)
-                        if (c0 + j < SALEC_MLP_OUT_N) y[j] = v[j] + bias[c0 + j];
-                }
-            }
-        }
-        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-        __syncthreads();
-    }
-    if (!ok_flag && tid == 0) {
-        if (a.err) atomicOr(a.err, 4);
-        // a weight load or MMAs still in flight get a bounded chance to finish before the
-        // CTA's memory goes away
-        if (in_flight) (void)mbar_wait(&wbar, wphase & 1u);
-        if (mma_pending) (void)mbar_wait(&mbar, mphase & 1u);
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
-    if (warp == 0) {
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(tmem_cols) : "memory");
+    if (abort_flag && tid == 0 && a.err) atomicOr(a.err, 4);
+    if (warp == 1) {
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512) : "memory");
     }
 }
 
@@ -756,6 +846,21 @@ bool make_map(CUtensorMap* map, const void* base, long rows, long K, long ld, in
 
 size_t tma_smem_bytes(int nt) { return (size_t)kStages * (kBM * kBK * 2 + nt * kBK * 2) + 1024; }
 
+// The same matrix as 64-element (128-byte) x box_rows boxes in the 128-byte swizzled
+// layout (one box is one K slice of box_rows rows).
+bool make_map_sw128(CUtensorMap* map, const void* base, long rows, long K, long ld, int box_rows)
+{
+    EncodeTiledFn fn = encode_tiled();
+    if (!fn || rows < 1 || K < 64 || (reinterpret_cast<uintptr_t>(base) & 15) || ((ld * 2) & 15)) return false;
+    const cuuint64_t dims[2] = {(cuuint64_t)K, (cuuint64_t)rows};
+    const cuuint64_t strides[1] = {(cuuint64_t)(ld * 2)};
+    const cuuint32_t box[2] = {64u, (cuuint32_t)box_rows};
+    const cuuint32_t estr[2] = {1u, 1u};
+    return fn(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), dims, strides, box, estr,
+              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
 }  // namespace
 
 cudaError_t launch_gemm(const GemmArgs& g0, cudaStream_t s)
@@ -812,24 +917,34 @@ cudaError_t launch_mlp_forward_fused(const FusedLaunch& f, cudaStream_t s)
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
     if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
-    CUtensorMap m2, m3, m4, m5;
-    if (!make_map(&m2, f.W[1], kFusedHid, kFusedHid, kFusedHid, kFusedHid) ||
-        !make_map(&m3, f.W[2], kFusedHid, kFusedHid, kFusedHid, kFusedHid) ||
-        !make_map(&m4, f.W[3], kFusedHid, kFusedHid, kFusedHid, kFusedHid) ||
-        !make_map(&m5, f.W[4], SALEC_MLP_OUT_N, kFusedHid, kFusedHid, kFusedOutPad))
-        return cudaErrorNotSupported;
-    static bool attr[64] = {};
-    if (!attr[dev]) {
-        e = cudaFuncSetAttribute(k_mlp_forward_fused, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fused_smem_bytes());
-        if (e != cudaSuccess) return e;
-        attr[dev] = true;
+    {
+        // persistent ping-pong kernel: one CTA per SM, pairs of 128-sample tiles
+        CUtensorMap m2, m3, m4, m5;
+        if (!make_map_sw128(&m2, f.W[1], kFusedHid, kFusedHid, kFusedHid, kFusedHid) ||
+            !make_map_sw128(&m3, f.W[2], kFusedHid, kFusedHid, kFusedHid, kFusedHid) ||
+            !make_map_sw128(&m4, f.W[3], kFusedHid, kFusedHid, kFusedHid, kFusedHid) ||
+            !make_map_sw128(&m5, f.W[4], SALEC_MLP_OUT_N, kFusedHid, kFusedHid, kFusedOutPad))
+            return cudaErrorNotSupported;
+        static bool attr_pp[64] = {};
+        static int nsm[64] = {};
+        if (!attr_pp[dev]) {
+            e = cudaFuncSetAttribute(k_mlp_forward_pp, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pp_smem_bytes());
+            if (e != cudaSuccess) return e;
+            e = cudaDeviceGetAttribute(&nsm[dev], cudaDevAttrMultiProcessorCount, dev);
+            if (e != cudaSuccess) return e;
+            attr_pp[dev] = true;
+        }
+        PPArgs a;
+        a.B = f.B;
+        a.ntiles = (f.B + kBM - 1) / kBM;
+        a.npairs = (a.ntiles + 1) / 2;
+        a.X = f.X; a.ld_x = f.ld_x; a.W1 = f.W[0];
+        for (int l = 0; l < 5; ++l) a.bias[l] = f.bias[l];
+        a.Y = f.Y; a.err = f.err;
+        const int grid = a.npairs < nsm[dev] ? a.npairs : nsm[dev];
+        k_mlp_forward_pp<<<(unsigned)grid, kPPThreads, pp_smem_bytes(), s>>>(m2, m3, m4, m5, a);
+        return cudaGetLastError();
     }
-    FusedArgs a;
-    a.B = f.B; a.X = f.X; a.ld_x = f.ld_x; a.W1 = f.W[0];
-    for (int l = 0; l < 5; ++l) a.bias[l] = f.bias[l];
-    a.Y = f.Y; a.err = f.err;
-    k_mlp_forward_fused<<<(unsigned)((f.B + kBM - 1) / kBM), kFusedThreads, fused_smem_bytes(), s>>>(m2, m3, m4, m5, a);
-    return cudaGetLastError();
 }
 
 cudaError_t launch_colsum(const __nv_bfloat16* G, int M, int N, long ldg, float* out, cudaStream_t s)

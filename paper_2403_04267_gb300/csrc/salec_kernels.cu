@@ -914,6 +914,37 @@ template <typename T, int NM>
 __global__ void __launch_bounds__(kMaxThreads) kb_phase3c(const ParamsT<T>* __restrict__ runs, const BatchTile* __restrict__ work)
 SALEC_BATCHED(phase3c, (body_phase3c<T, NM>))
 
+// The mixed form's remap kernels for one hydrodynamic material (and its vertex remap for
+// any material count, single and batched) are latency-bound (19-34 % of DRAM peak at
+// 62-75 % occupancy): their registers are capped so that a full SM of threads (4 blocks
+// of the largest shape) fits, at the cost of a few bytes of spill.  With more materials
+// or strength the cell remap would spill heavily under such a cap; the FP64 kernels are
+// bound by the FP64 pipe.  Both keep the compiler's own register choice.
+template <>
+__global__ void __launch_bounds__(kMaxThreads, 4) k_phase3a<float, 1, false, true>(ParamsT<float> P)
+{
+    body_phase3a<float, 1, false, true>(P, blockIdx.x, blockIdx.y, gridDim.x, gridDim.y);
+}
+template <>
+__global__ void __launch_bounds__(kMaxThreads, 4) k_phase3a<float, 1, false, false>(ParamsT<float> P)
+{
+    body_phase3a<float, 1, false, false>(P, blockIdx.x, blockIdx.y, gridDim.x, gridDim.y);
+}
+template <>
+__global__ void __launch_bounds__(kMaxThreads, 4) k_phase3b<float>(ParamsT<float> P)
+{
+    body_phase3b<float>(P, blockIdx.x, blockIdx.y, gridDim.x, gridDim.y);
+}
+template <>
+__global__ void __launch_bounds__(kMaxThreads, 4) kb_phase3b<float>(const ParamsT<float>* __restrict__ runs,
+                                                                   const BatchTile* __restrict__ work)
+{
+    const BatchTile w = work[blockIdx.x];
+    const ParamsT<float>& P = runs[w.run];
+    if (P.p.scal->active == 0) return;
+    body_phase3b<float>(P, w.bx, w.by, w.g & 0xffff, w.g >> 16);
+}
+
 // ---------------------------------------------------------------------------------
 // Read-out kernels
 // ---------------------------------------------------------------------------------
