@@ -663,9 +663,18 @@ __device__ __forceinline__ void body_phase3a(const ParamsT<T>& P, int bx, int by
             p.s2d[c] = V::mk(s2, Dm);
         }
     }
-    // tallies: block sums and one atomic per block, only in blocks where some thread has one
-    // (most blocks touch neither the top boundary, the clean-up nor a strip)
-    if (__syncthreads_or(nonzero(t_out) || nonzero(t_disc) || nonzero(t_pml))) {
+    // tallies.  Outflow through the top and the strips' damping happen only in blocks on
+    // the top row or in a strip: those sum over the block with one atomic each, when some
+    // thread has one.  Elsewhere only the rare clean-up tallies, and a warp that has some
+    // adds it by itself, so the block needs no barrier.
+    const int bdx = blockDim.x, bdy = blockDim.y;
+    const bool edge_block = (by + 1) * bdy > P.nz - 1 || by * bdy < P.pb || (bx + 1) * bdx > nr - P.pr;
+    if (!edge_block) {
+        if (__any_sync(0xffffffffu, nonzero(t_disc))) {
+            const double b_disc = warp_sum(t_disc);
+            if ((threadIdx.x & 31) == 0 && b_disc != 0.0) atomicAdd(&p.scal->mass_discarded, b_disc);
+        }
+    } else if (__syncthreads_or(nonzero(t_out) || nonzero(t_disc) || nonzero(t_pml))) {
         __shared__ double sh[kMaxThreads / 32];
         const double b_out = block_sum(t_out, sh);
         const double b_disc = block_sum(t_disc, sh);
@@ -817,7 +826,8 @@ __device__ __forceinline__ void body_phase3b(const ParamsT<T>& P, int bx, int by
         if (is_nan(vr) || is_nan(vz)) atomicOr(&p.scal->status, 2);
         p.v[v] = V::mk(vr, vz);
     }
-    if (__syncthreads_or(nonzero(t_zmom))) {
+    // the z-momentum leaving through the top: only blocks on the top vertex row have any
+    if ((by + 1) * (int)blockDim.y > nz && __syncthreads_or(nonzero(t_zmom))) {
         __shared__ double sh[kMaxThreads / 32];
         const double b = block_sum(t_zmom, sh);
         if (threadIdx.x == 0 && threadIdx.y == 0 && b != 0.0) atomicAdd(&p.scal->zmom_out, b);
