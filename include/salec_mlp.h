@@ -49,8 +49,9 @@ salec_status salec_mlp_set_params(salec_mlp* mlp, const float* theta_host);
 salec_status salec_mlp_get_params(salec_mlp* mlp, float* theta_host);
 
 /* y_dev[b][o] = network(x_dev[b][:]) for b < batch <= batch_max; x_dev is batch x 5 FP32,
- * y_dev batch x 66 FP32, both row-major device arrays.  One kernel runs all five layers on
- * 128-sample tiles with the activations kept on chip. */
+ * y_dev batch x 66 FP32, both row-major device arrays.  One persistent kernel runs all
+ * five layers on 128-sample tiles, two per SM at a time (one on the tensor cores while the
+ * other's epilogue runs), with the activations kept on chip. */
 salec_status salec_mlp_forward(salec_mlp* mlp, const float* x_dev, int batch, float* y_dev);
 
 /* Forward and backward pass against targets t_dev (batch x 66 FP32): the gradient of the
