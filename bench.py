@@ -565,6 +565,9 @@ def main():
                 "peak_kind": "nominal FP64 issue rate 152 SM x 2 DFMA/clk x 2.07 GHz (measured DFMA loop: 1.19)",
                 "achieved": round(ach, 4) if ach else None, "frac": round(ach / FP64_PEAK_TFLOPS, 4) if ach else None,
                 "flops_per_cell": flops, "traffic": _TRAFFIC_PER_CELL.get(dom) and _TRAFFIC_PER_CELL[dom] * cells,
+                "fp64_pipe_busy": _FP64_PIPE_BUSY.get(dom),
+                "note": "flops count 2 per DFMA and 1 per DADD/DMUL; the FP64 pipe issues every FP64 "
+                        "instruction at the DFMA rate, and fp64_pipe_busy (ncu, 2000x2000) is its occupancy",
                 "hbm": roof_hbm["hbm"]}
     else:
         h = roof_hbm["hbm"]
@@ -617,8 +620,11 @@ def main():
 # 4000 x 4000 physics, and DRAM bytes per cell, from ncu on the 2000 x 2000 case
 # (profiles/); refreshed whenever the kernels change.
 _FLOPS_PER_CELL: dict = {"k_phase0": 85.8, "k_phase1": 49.6, "k_phase2": 38.7, "k_phase3a": 75.9, "k_phase3b": 70.4, "k_phase3c": 4.8}
-_TRAFFIC_PER_CELL: dict = {"k_phase0": 58.0, "k_phase1": 72.2, "k_phase2": 75.6, "k_phase3a": 78.4, "k_phase3b": 63.4, "k_phase3c": 22.2}
-_TRAFFIC_PER_CELL_FP32MIX: dict = {"k_phase0": 28.2, "k_phase1": 31.5, "k_phase2": 40.0, "k_phase3a": 41.7, "k_phase3b": 30.0, "k_phase3c": 10.8}
+_TRAFFIC_PER_CELL: dict = {"k_phase0": 57.8, "k_phase1": 72.1, "k_phase2": 75.6, "k_phase3a": 78.3, "k_phase3b": 63.2, "k_phase3c": 22.1}
+_TRAFFIC_PER_CELL_FP32MIX: dict = {"k_phase0": 28.0, "k_phase1": 31.5, "k_phase2": 39.9, "k_phase3a": 41.9, "k_phase3b": 29.6, "k_phase3c": 10.8}
+# fraction of the FP64 pipe's issue slots each FP64-form kernel keeps busy (ncu,
+# sm__pipe_fp64_cycles_active on the 2000 x 2000 case)
+_FP64_PIPE_BUSY: dict = {"k_phase0": 0.846, "k_phase1": 0.862, "k_phase2": 0.859, "k_phase3a": 0.858, "k_phase3b": 0.852, "k_phase3c": 0.791}
 
 if __name__ == "__main__":
     sys.exit(main())
