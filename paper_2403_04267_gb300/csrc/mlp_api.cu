@@ -43,7 +43,7 @@ long n_weights_bf16()
 }
 
 struct Layout {
-    size_t theta, m1, m2, grad, wmap, wbf, X, Z[4], H[4], Y, G[2], loss, err, total;
+    size_t theta, m1, m2, grad, wmap, wbf, X, Z[4], H[4], Y, G[2], part, cpart, loss, err, total;
     Layout(int bmax)
     {
         const long P = n_params(), W = n_weights_bf16();
@@ -57,6 +57,8 @@ struct Layout {
         for (int l = 0; l < 4; ++l) H[l] = take((size_t)bmax * kHid * 2);
         Y = take((size_t)bmax * SALEC_MLP_OUT * 4);
         for (int l = 0; l < 2; ++l) G[l] = take((size_t)bmax * kHid * 2);
+        part = take((size_t)kMaxSplit * kHid * kHid * 4);     // split-K partials of a weight gradient
+        cpart = take((size_t)kColsumChunks * kHid * 4);      // column-sum partials of a bias gradient
         loss = take(8);
         err = take(4);
         total = o;
@@ -77,6 +79,8 @@ struct salec_mlp {
     __nv_bfloat16* H[4] = {};
     float* Y = nullptr;
     __nv_bfloat16* G[2] = {};
+    float* part = nullptr;
+    float* cpart = nullptr;
     double* loss = nullptr;
     int* errflag = nullptr;
     long steps = 0;                       // Adam steps taken
@@ -162,8 +166,9 @@ salec_status backward_impl(salec_mlp* n, int B, float* grad)
         gw.B = Hprev; gw.b_sn = 1; gw.b_sk = ldprev;
         gw.epi = kEpiStore;
         gw.C = grad + n->woff[l]; gw.ldc = ni;
+        gw.part = n->part;
         MLP_CUDA(n, launch_gemm(gw, n->stream), "mlp weight-gradient gemm");
-        MLP_CUDA(n, launch_colsum(G, B, no, kHid, grad + n->boff[l], n->stream), "mlp bias gradient");
+        MLP_CUDA(n, launch_colsum(G, B, no, kHid, grad + n->boff[l], n->cpart, n->stream), "mlp bias gradient");
         if (l == 0) break;
         // dL/dZ_{l-1}[b][i] = (sum_o G[b][o] W_l[o][i]) gelu'(Z_{l-1}[b][i])
         GemmArgs gd = gemm0(B, ni, no, n->errflag);
@@ -223,6 +228,8 @@ salec_status salec_mlp_create(int batch_max, void* dev_buf, size_t bytes, void* 
     }
     n->Y = reinterpret_cast<float*>(b + L.Y);
     for (int l = 0; l < 2; ++l) n->G[l] = reinterpret_cast<__nv_bfloat16*>(b + L.G[l]);
+    n->part = reinterpret_cast<float*>(b + L.part);
+    n->cpart = reinterpret_cast<float*>(b + L.cpart);
     n->loss = reinterpret_cast<double*>(b + L.loss);
     n->errflag = reinterpret_cast<int*>(b + L.err);
     // parameter offsets and the weight -> BF16 block map

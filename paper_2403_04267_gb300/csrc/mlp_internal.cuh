@@ -35,8 +35,13 @@ struct GemmArgs {
     float grad_scale;         // 2 / (B n_out)
     double* loss;             // sum of squared errors (atomic), or null
     int* err;                 // error flag, or null
+    float* part;              // kEpiStore without bias: workspace for split-K partials
+                              // (kMaxSplit x M x N floats), or null for no split
     int nt, tmem_cols;        // set by the launcher
+    int kchunk;               // set by the launcher: K per split (0: no split)
 };
+
+constexpr int kMaxSplit = 16;
 
 constexpr int SALEC_MLP_OUT_N = 66;
 
@@ -57,7 +62,9 @@ struct AdamArgs {
 
 cudaError_t launch_gemm(const GemmArgs& g, cudaStream_t s);
 cudaError_t launch_mlp_forward_fused(const FusedLaunch& f, cudaStream_t s);
-cudaError_t launch_colsum(const __nv_bfloat16* G, int M, int N, long ldg, float* out, cudaStream_t s);
+// column sums out[n] = sum_m G[m][n]; `part` holds kColsumChunks x N floats
+constexpr int kColsumChunks = 64;
+cudaError_t launch_colsum(const __nv_bfloat16* G, int M, int N, long ldg, float* out, float* part, cudaStream_t s);
 cudaError_t launch_inputs_bf16(const float* x, int rows, int cols, int ld, __nv_bfloat16* y, cudaStream_t s);
 cudaError_t launch_adam(float* theta, float* m1, float* m2, const float* grad, long n, const AdamArgs& a,
                         const int* wmap, __nv_bfloat16* wbf, cudaStream_t s);

@@ -306,6 +306,10 @@ __global__ void __launch_bounds__(kGemmThreads) k_gemm_bf16(GemmArgs g)
     const int tid = threadIdx.x, warp = tid >> 5;
     const int m0 = blockIdx.x * kBM, n0 = blockIdx.y * g.nt;
     const int NT = g.nt;
+    // split-K: this CTA sums K range [kb, ke) into its own partial (plain store); a
+    // second kernel adds the partials in a fixed order
+    const int kb = g.kchunk > 0 ? (int)blockIdx.z * g.kchunk : 0;
+    const int ke = g.kchunk > 0 ? min(g.K, kb + g.kchunk) : g.K;
     const uint32_t a_bytes = kBM * kBK * 2, b_bytes = (uint32_t)NT * kBK * 2;
     const uint32_t stage_bytes = a_bytes + b_bytes;
     const uint32_t tmem_cols = g.tmem_cols;
@@ -328,7 +332,7 @@ __global__ void __launch_bounds__(kGemmThreads) k_gemm_bf16(GemmArgs g)
     const uint32_t tmem = tmem_holder;
     const uint32_t idesc = idesc_bf16(kBM, NT);
 
-    const int nk = (g.K + kBK - 1) / kBK;
+    const int nk = (ke - kb + kBK - 1) / kBK;
     bool ok = true;
     int issued = 0;                       // K slices whose MMAs were committed
     for (int kt = 0; kt < nk; ++kt) {
@@ -337,17 +341,17 @@ __global__ void __launch_bounds__(kGemmThreads) k_gemm_bf16(GemmArgs g)
         if (kt >= 2 && !__syncthreads_and(mbar_wait(&bars[s], ((kt - 2) >> 1) & 1))) { ok = false; break; }
         unsigned char* sa = smem + s * stage_bytes;
         unsigned char* sb = sa + a_bytes;
-        const int k0 = kt * kBK;
+        const int k0 = kb + kt * kBK;
         // A: thread tid gathers row tid; core matrix (row group rg, k group kg) at kg*2048 + rg*128
 #pragma unroll
         for (int kg = 0; kg < 8; ++kg) {
-            const uint4 w = gather8(g.A, g.a_sm, g.a_sk, m0 + tid, g.M, k0 + 8 * kg, g.K);
+            const uint4 w = gather8(g.A, g.a_sm, g.a_sk, m0 + tid, g.M, k0 + 8 * kg, ke);
             *reinterpret_cast<uint4*>(sa + kg * (kBM * 16) + (tid >> 3) * 128 + (tid & 7) * 16) = w;
         }
         for (int r = tid; r < NT; r += kGemmThreads) {
 #pragma unroll
             for (int kg = 0; kg < 8; ++kg) {
-                const uint4 w = gather8(g.B, g.b_sn, g.b_sk, n0 + r, g.N, k0 + 8 * kg, g.K);
+                const uint4 w = gather8(g.B, g.b_sn, g.b_sk, n0 + r, g.N, k0 + 8 * kg, ke);
                 *reinterpret_cast<uint4*>(sb + kg * (NT * 16) + (r >> 3) * 128 + (r & 7) * 16) = w;
             }
         }
@@ -379,7 +383,16 @@ __global__ void __launch_bounds__(kGemmThreads) k_gemm_bf16(GemmArgs g)
     }
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
 
-    if (ok) epilogue(g, tmem, m0, n0, NT, nk > 0);
+    if (ok) {
+        if (g.kchunk > 0) {
+            GemmArgs gp = g;
+            gp.C = g.part + (long)blockIdx.z * g.M * g.N;
+            gp.ldc = g.N;
+            epilogue(gp, tmem, m0, n0, NT, nk > 0);
+        } else {
+            epilogue(g, tmem, m0, n0, NT, nk > 0);
+        }
+    }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
     if (warp == 0) {
@@ -800,13 +813,32 @@ __global__ void __launch_bounds__(kPPThreads, 1) k_mlp_forward_pp(const __grid_c
 }
 
 // Column sums of a BF16 matrix (bias gradients): out[n] = sum_m G[m][n].
-__global__ void k_colsum(const __nv_bfloat16* __restrict__ G, int M, int N, long ldg, float* __restrict__ out)
+// Column sums in two passes (many rows, few columns): block (x, y) sums rows y, y + Y, ...
+// of its columns into part[y][n]; the second pass adds the Y partials in order.
+__global__ void k_colsum_part(const __nv_bfloat16* __restrict__ G, int M, int N, long ldg, float* __restrict__ part)
 {
     const int n = blockIdx.x * blockDim.x + threadIdx.x;
     if (n >= N) return;
     float s = 0.0f;
-    for (int m = 0; m < M; ++m) s += __bfloat162float(G[(long)m * ldg + n]);
-    out[n] = s;
+    for (int m = blockIdx.y; m < M; m += gridDim.y) s += __bfloat162float(G[(long)m * ldg + n]);
+    part[(long)blockIdx.y * N + n] = s;
+}
+__global__ void k_sum_parts(const float* __restrict__ part, int nparts, long n, float* __restrict__ out)
+{
+    const long k = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    float s = 0.0f;
+    for (int p = 0; p < nparts; ++p) s += part[(long)p * n + k];
+    out[k] = s;
+}
+// split-K partials [S][M][N] into C (row stride ldc), in split order
+__global__ void k_splitk_reduce(const float* __restrict__ part, int S, int M, int N, float* __restrict__ C, long ldc)
+{
+    const long k = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= (long)M * N) return;
+    float s = 0.0f;
+    for (int p = 0; p < S; ++p) s += part[(long)p * M * N + k];
+    C[(k / N) * ldc + k % N] = s;
 }
 
 // FP32 -> BF16 inputs of the first layer: rows of `cols` values into rows of `ld`, the
@@ -944,6 +976,24 @@ cudaError_t launch_gemm(const GemmArgs& g0, cudaStream_t s)
     while (cols < nt) cols <<= 1;
     g.tmem_cols = cols;
     const size_t smem = gemm_smem_bytes(nt);
+    // few output tiles and a long K (the weight gradients: K = batch): split K over up to
+    // kMaxSplit CTAs per tile, each summing a range of 64-multiples into a partial
+    const int tiles = ((g.M + kBM - 1) / kBM) * ((g.N + nt - 1) / nt);
+    int S = 1;
+    g.kchunk = 0;
+    if (g.epi == kEpiStore && !g.bias && g.part && tiles < 64 && g.K >= 4 * kBK) {
+        S = (g.K + 2 * kBK - 1) / (2 * kBK);                      // at least 2 slices each
+        const int want = (128 + tiles - 1) / tiles;
+        S = S < want ? S : want;
+        S = S < kMaxSplit ? S : kMaxSplit;
+        if (S > 1) {
+            const int slices = (g.K + kBK - 1) / kBK;
+            g.kchunk = (slices + S - 1) / S * kBK;
+            S = (g.K + g.kchunk - 1) / g.kchunk;
+        } else {
+            S = 1;
+        }
+    }
     // the attribute is per device
     static bool attr_set[64] = {};
     if (!attr_set[dev]) {
@@ -951,8 +1001,12 @@ cudaError_t launch_gemm(const GemmArgs& g0, cudaStream_t s)
         if (e != cudaSuccess) return e;
         attr_set[dev] = true;
     }
-    dim3 grid((unsigned)((g.M + kBM - 1) / kBM), (unsigned)((g.N + nt - 1) / nt));
+    dim3 grid((unsigned)((g.M + kBM - 1) / kBM), (unsigned)((g.N + nt - 1) / nt), (unsigned)S);
     k_gemm_bf16<<<grid, kGemmThreads, smem, s>>>(g);
+    e = cudaGetLastError();
+    if (e != cudaSuccess || g.kchunk == 0) return e;
+    const long mn = (long)g.M * g.N;
+    k_splitk_reduce<<<(unsigned)((mn + 255) / 256), 256, 0, s>>>(g.part, S, g.M, g.N, g.C, g.ldc);
     return cudaGetLastError();
 }
 
@@ -993,9 +1047,14 @@ cudaError_t launch_mlp_forward_fused(const FusedLaunch& f, cudaStream_t s)
     }
 }
 
-cudaError_t launch_colsum(const __nv_bfloat16* G, int M, int N, long ldg, float* out, cudaStream_t s)
+cudaError_t launch_colsum(const __nv_bfloat16* G, int M, int N, long ldg, float* out, float* part, cudaStream_t s)
 {
-    k_colsum<<<(N + 127) / 128, 128, 0, s>>>(G, M, N, ldg, out);
+    if (N <= 0) return cudaSuccess;
+    const int Y = M < kColsumChunks ? (M > 0 ? M : 1) : kColsumChunks;
+    k_colsum_part<<<dim3((unsigned)((N + 127) / 128), (unsigned)Y), 128, 0, s>>>(G, M, N, ldg, part);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    k_sum_parts<<<(unsigned)((N + 127) / 128), 128, 0, s>>>(part, Y, N, out);
     return cudaGetLastError();
 }
 
