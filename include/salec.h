@@ -194,14 +194,16 @@ salec_status salec_checkpoint_bytes(salec_ctx* ctx, size_t* bytes);
 salec_status salec_get_state(salec_ctx* ctx, void* host, size_t bytes);
 salec_status salec_set_state(salec_ctx* ctx, const void* host, size_t bytes);
 
-/* Number of kernel launches one step issues (for launch accounting). */
+/* Number of kernel launches one step issues (for launch accounting): the six phases and
+ * the one-thread Courant kernel between phases 0 and 1. */
 int salec_launches_per_step(const salec_ctx* ctx);
 
 /* Per-kernel timing: with timing on, salec_step records a CUDA event before the first
  * and after every kernel of each step on the context's stream; salec_kernel_times
- * synchronises, returns in avg_ms[k] (n >= salec_launches_per_step) the mean duration
- * of kernel k over the steps recorded since timing was switched on or last read, the
- * number of steps in *steps, and restarts the count.  salec_kernel_name(k) names kernel k. */
+ * synchronises, returns in avg_ms[k] (k < 6, n >= 6) the mean duration of phase k over
+ * the steps recorded since timing was switched on or last read (phase 0 includes the
+ * Courant kernel), the number of steps in *steps, and restarts the count.
+ * salec_kernel_name(k) names phase k. */
 salec_status salec_set_kernel_timing(salec_ctx* ctx, int on);
 salec_status salec_kernel_times(salec_ctx* ctx, double* avg_ms, int n, int* steps);
 const char* salec_kernel_name(int k);

@@ -1229,9 +1229,9 @@ static cudaError_t batch_launch(salec_batch* b, cudaEvent_t* ev)
     const BatchTile* work[6];
     for (int k = 0; k < 6; ++k) work[k] = reinterpret_cast<const BatchTile*>(b->dev + b->off_work[k]);
     if (b->precision == SALEC_FP32MIX)
-        return launch_batch_step<float>(reinterpret_cast<const ParamsT<float>*>(b->dev + b->off_params), b->nmat,
+        return launch_batch_step<float>(reinterpret_cast<const ParamsT<float>*>(b->dev + b->off_params), (int)b->runs.size(), b->nmat,
                                         b->strength, b->uniform, work, b->ntiles, b->shape, b->stream, ev);
-    return launch_batch_step<double>(reinterpret_cast<const ParamsT<double>*>(b->dev + b->off_params), b->nmat,
+    return launch_batch_step<double>(reinterpret_cast<const ParamsT<double>*>(b->dev + b->off_params), (int)b->runs.size(), b->nmat,
                                      b->strength, b->uniform, work, b->ntiles, b->shape, b->stream, ev);
 }
 
@@ -1424,7 +1424,7 @@ void salec_batch_destroy(salec_batch* b)
 int salec_launches_per_step(const salec_ctx* ctx)
 {
     (void)ctx;
-    return launches_per_step();
+    return kernels_per_step();
 }
 
 const char* salec_last_error(const salec_ctx* ctx)

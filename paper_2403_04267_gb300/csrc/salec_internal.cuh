@@ -54,7 +54,6 @@ struct DevScalars {
     double mass_out, mass_discarded, mass_pml, zmom_out;
     unsigned long long nstep;
     unsigned long long maxbits;   // running max of the blocks' Courant rates (FP64 bit patterns)
-    unsigned int counter;   // last-block counter of the dt reduction
     int status;             // bit 1: non-positive volume or density, 2: NaN, 4: dt < dt_min
     int active;             // the run stepped in the current batched step
     float dtf;              // dt rounded to FP32 (the mixed form's kernels read it without a conversion)
@@ -293,7 +292,7 @@ __device__ __forceinline__ float max_nonneg(float a, float b)
 // launchers (salec_kernels.cu), instantiated for T = double and T = float
 template <typename T> cudaError_t launch_step(const ParamsT<T>& P, const dim3* blk, cudaStream_t s, cudaEvent_t* ev);
 template <typename T>
-cudaError_t launch_batch_step(const ParamsT<T>* runs_dev, int nmat, bool strength, bool uniform, const BatchTile* const* work,
+cudaError_t launch_batch_step(const ParamsT<T>* runs_dev, int nruns, int nmat, bool strength, bool uniform, const BatchTile* const* work,
                               const int* ntiles, const dim3* blk, cudaStream_t s, cudaEvent_t* ev);
 template <typename T> cudaError_t launch_batch_poll(const ParamsT<T>* runs_dev, int n, double* out, cudaStream_t s);
 bool kernel_on_vertices(int k);
@@ -302,7 +301,8 @@ template <typename T> cudaError_t launch_pressure(const ParamsT<T>& P, double* o
 template <typename T> cudaError_t launch_column_heights(const ParamsT<T>& P, double* heights, cudaStream_t s);
 template <typename T> cudaError_t launch_conservation(const ParamsT<T>& P, double* partial4, int* nblocks, cudaStream_t s);
 const char* kernel_name(int k);
-int launches_per_step();
+int launches_per_step();     // timed phases of a step (the Courant kernel is timed within phase 0)
+int kernels_per_step();      // kernel launches of a step
 const char* noalloc_last_error();
 int cell_blocks(int nr, int nz);
 int vertex_blocks(int nr, int nz);

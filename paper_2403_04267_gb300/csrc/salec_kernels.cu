@@ -178,8 +178,9 @@ __device__ __forceinline__ void body_phase0(const ParamsT<T>& P, int bx, int by,
         p.pbphi[c] = V::mk(pbar, phi);
     }
     // block maximum (on the bit patterns of the non-negative speeds) into one running
-    // maximum per run by an atomic max; the last block to finish turns it into dt.  After
-    // the one barrier only thread 0 works, so the other warps leave at once.
+    // maximum per run by an atomic max that nothing waits for; the Courant kernel that
+    // follows turns it into dt.  After the one barrier only thread 0 works, so the other
+    // warps leave at once and the block right after its atomic.
     __shared__ unsigned long long sh[kMaxThreads / 32];
     const int tid = threadIdx.y * blockDim.x + threadIdx.x;
     const int nw = (blockDim.x * blockDim.y) >> 5;
@@ -189,23 +190,26 @@ __device__ __forceinline__ void body_phase0(const ParamsT<T>& P, int bx, int by,
     if (tid != 0) return;
     unsigned long long b = sh[0];
     for (int w = 1; w < nw; ++w) b = max(b, sh[w]);
-    DevScalars* s = p.scal;
-    atomicMax(&s->maxbits, b);
-    __threadfence();
-    const unsigned prev = atomicAdd(&s->counter, 1u);
-    if (prev != (unsigned)(gx * gy - 1)) return;
-    // every other block's maximum is in (its atomic preceded its fence and its count)
-    __threadfence();
-    const double mx = __longlong_as_double((long long)atomicExch(&s->maxbits, 0ull));
+    atomicMax(&p.scal->maxbits, b);
+}
+
+// Courant step of Eq. 14 from phase 0's running maximum of (|v| + c) / L (of |v| + c on a
+// uniform grid): dt = min(C0 / max, growth dt_prev, dt_max); the maximum is reset for the
+// next step.  One thread per run.
+template <typename T>
+__device__ __forceinline__ void courant_dt(const ParamsT<T>& P)
+{
+    DevScalars* s = P.p.scal;
+    const double mx = __longlong_as_double((long long)s->maxbits);
+    s->maxbits = 0ull;
     double dt = P.growth * s->dt_prev;
-    const double cdt = UNI ? P.cfld * (P.dxd / mx) : P.cfld / mx;
+    const double cdt = P.uniform ? P.cfld * (P.dxd / mx) : P.cfld / mx;
     dt = cdt < dt ? cdt : dt;
     dt = P.dt_max < dt ? P.dt_max : dt;
     if (dt < P.dt_min) s->status |= 4;
     s->dt = dt;
     s->dtf = float(dt);
     s->active = 1;
-    s->counter = 0u;
 }
 
 // ---------------------------------------------------------------------------------
@@ -876,6 +880,11 @@ __device__ __forceinline__ void body_phase3c(const ParamsT<T>& P, int bx, int by
 
 template <typename T, int NM, bool STR, bool UNI>
 __global__ void __launch_bounds__(kMaxThreads) k_phase0(ParamsT<T> P) { body_phase0<T, NM, STR, UNI>(P, blockIdx.x, blockIdx.y, gridDim.x, gridDim.y); }
+template <typename T>
+__global__ void k_courant(ParamsT<T> P)
+{
+    if (threadIdx.x == 0) courant_dt<T>(P);
+}
 template <typename T, bool STR, bool UNI>
 __global__ void __launch_bounds__(kMaxThreads) k_phase1(ParamsT<T> P) { body_phase1<T, STR, UNI>(P, blockIdx.x, blockIdx.y, gridDim.x, gridDim.y); }
 template <typename T, int NM, bool STR, bool UNI>
@@ -894,12 +903,25 @@ __global__ void __launch_bounds__(kMaxThreads) kb_phase0(const ParamsT<T>* __res
 {
     const BatchTile w = work[blockIdx.x];
     const ParamsT<T>& P = runs[w.run];
+    const DevScalars* s = P.p.scal;
+    if (!(s->t < s->t_end) || s->status != 0) return;
+    body_phase0<T, NM, STR, UNI>(P, w.bx, w.by, w.g & 0xffff, w.g >> 16);
+}
+// the Courant step of every run; a run at or past its end time or with a failure status
+// does nothing in this step (active = 0 tells the later kernels)
+template <typename T>
+__global__ void kb_courant(const ParamsT<T>* __restrict__ runs, int nruns)
+{
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= nruns) return;
+    const ParamsT<T>& P = runs[r];
     DevScalars* s = P.p.scal;
     if (!(s->t < s->t_end) || s->status != 0) {
-        if (w.bx == 0 && w.by == 0 && threadIdx.x == 0 && threadIdx.y == 0) s->active = 0;
+        s->active = 0;
+        s->maxbits = 0ull;
         return;
     }
-    body_phase0<T, NM, STR, UNI>(P, w.bx, w.by, w.g & 0xffff, w.g >> 16);
+    courant_dt<T>(P);
 }
 #define SALEC_BATCHED(NAME, CALL)                                                          \
     {                                                                                      \
@@ -1068,6 +1090,7 @@ static dim3 vert_grid(int nr, int nz) { return grid_of(nr + 1, nz + 1, dim3(kBlo
 int cell_blocks(int nr, int nz) { dim3 g = cell_grid(nr, nz); return (int)(g.x * g.y); }
 int vertex_blocks(int nr, int nz) { dim3 g = vert_grid(nr, nz); return (int)(g.x * g.y); }
 int launches_per_step() { return 6; }
+int kernels_per_step() { return 7; }     // the six phases and the Courant kernel
 // kernels 1 (forces) and 4 (momentum remap) run over vertices, the others over cells
 bool kernel_on_vertices(int k) { return k == 1 || k == 4; }
 int tiles_of(int nr, int nz, int k, dim3 blk)
@@ -1090,6 +1113,7 @@ static cudaError_t step_impl(const ParamsT<T>& P, const dim3* blk, cudaStream_t 
     const int nr = P.nr, nz = P.nz;
     if (ev) cudaEventRecord(ev[0], s);
     k_phase0<T, NM, STR, UNI><<<grid_of(nr, nz, blk[0]), blk[0], 0, s>>>(P);
+    k_courant<T><<<1, 32, 0, s>>>(P);
     if (ev) cudaEventRecord(ev[1], s);
     k_phase1<T, STR, UNI><<<grid_of(nr + 1, nz + 1, blk[1]), blk[1], 0, s>>>(P);
     if (ev) cudaEventRecord(ev[2], s);
@@ -1127,11 +1151,12 @@ cudaError_t launch_step(const ParamsT<T>& P, const dim3* blk, cudaStream_t s, cu
 // One cycle of every run of a batch: work[k] lists the (run, tile) entries of kernel k
 // (ntiles[k] of them) for block shape blk[k].
 template <typename T, int NM, bool STR, bool UNI>
-static cudaError_t batch_impl(const ParamsT<T>* runs, const BatchTile* const* work, const int* ntiles,
+static cudaError_t batch_impl(const ParamsT<T>* runs, int nruns, const BatchTile* const* work, const int* ntiles,
                               const dim3* blk, cudaStream_t s, cudaEvent_t* ev)
 {
     if (ev) cudaEventRecord(ev[0], s);
     kb_phase0<T, NM, STR, UNI><<<ntiles[0], blk[0], 0, s>>>(runs, work[0]);
+    kb_courant<T><<<(nruns + 127) / 128, 128, 0, s>>>(runs, nruns);
     if (ev) cudaEventRecord(ev[1], s);
     kb_phase1<T, STR, UNI><<<ntiles[1], blk[1], 0, s>>>(runs, work[1]);
     if (ev) cudaEventRecord(ev[2], s);
@@ -1147,22 +1172,22 @@ static cudaError_t batch_impl(const ParamsT<T>* runs, const BatchTile* const* wo
 }
 
 template <typename T>
-cudaError_t launch_batch_step(const ParamsT<T>* runs_dev, int nmat, bool strength, bool uniform, const BatchTile* const* work,
+cudaError_t launch_batch_step(const ParamsT<T>* runs_dev, int nruns, int nmat, bool strength, bool uniform, const BatchTile* const* work,
                               const int* ntiles, const dim3* blk, cudaStream_t s, cudaEvent_t* ev)
 {
     // every run of the batch on a uniform grid: the uniform form
     if (uniform) {
         switch (nmat) {
-        case 1: return strength ? batch_impl<T, 1, true, true>(runs_dev, work, ntiles, blk, s, ev) : batch_impl<T, 1, false, true>(runs_dev, work, ntiles, blk, s, ev);
-        case 2: return strength ? batch_impl<T, 2, true, true>(runs_dev, work, ntiles, blk, s, ev) : batch_impl<T, 2, false, true>(runs_dev, work, ntiles, blk, s, ev);
-        case 3: return strength ? batch_impl<T, 3, true, true>(runs_dev, work, ntiles, blk, s, ev) : batch_impl<T, 3, false, true>(runs_dev, work, ntiles, blk, s, ev);
+        case 1: return strength ? batch_impl<T, 1, true, true>(runs_dev, nruns, work, ntiles, blk, s, ev) : batch_impl<T, 1, false, true>(runs_dev, nruns, work, ntiles, blk, s, ev);
+        case 2: return strength ? batch_impl<T, 2, true, true>(runs_dev, nruns, work, ntiles, blk, s, ev) : batch_impl<T, 2, false, true>(runs_dev, nruns, work, ntiles, blk, s, ev);
+        case 3: return strength ? batch_impl<T, 3, true, true>(runs_dev, nruns, work, ntiles, blk, s, ev) : batch_impl<T, 3, false, true>(runs_dev, nruns, work, ntiles, blk, s, ev);
         default: return cudaErrorInvalidValue;
         }
     }
     switch (nmat) {
-    case 1: return strength ? batch_impl<T, 1, true, false>(runs_dev, work, ntiles, blk, s, ev) : batch_impl<T, 1, false, false>(runs_dev, work, ntiles, blk, s, ev);
-    case 2: return strength ? batch_impl<T, 2, true, false>(runs_dev, work, ntiles, blk, s, ev) : batch_impl<T, 2, false, false>(runs_dev, work, ntiles, blk, s, ev);
-    case 3: return strength ? batch_impl<T, 3, true, false>(runs_dev, work, ntiles, blk, s, ev) : batch_impl<T, 3, false, false>(runs_dev, work, ntiles, blk, s, ev);
+    case 1: return strength ? batch_impl<T, 1, true, false>(runs_dev, nruns, work, ntiles, blk, s, ev) : batch_impl<T, 1, false, false>(runs_dev, nruns, work, ntiles, blk, s, ev);
+    case 2: return strength ? batch_impl<T, 2, true, false>(runs_dev, nruns, work, ntiles, blk, s, ev) : batch_impl<T, 2, false, false>(runs_dev, nruns, work, ntiles, blk, s, ev);
+    case 3: return strength ? batch_impl<T, 3, true, false>(runs_dev, nruns, work, ntiles, blk, s, ev) : batch_impl<T, 3, false, false>(runs_dev, nruns, work, ntiles, blk, s, ev);
     default: return cudaErrorInvalidValue;
     }
 }
@@ -1232,9 +1257,9 @@ template cudaError_t launch_batch_poll<float>(const ParamsT<float>*, int, double
 
 template cudaError_t launch_step<double>(const ParamsT<double>&, const dim3*, cudaStream_t, cudaEvent_t*);
 template cudaError_t launch_step<float>(const ParamsT<float>&, const dim3*, cudaStream_t, cudaEvent_t*);
-template cudaError_t launch_batch_step<double>(const ParamsT<double>*, int, bool, bool, const BatchTile* const*, const int*,
+template cudaError_t launch_batch_step<double>(const ParamsT<double>*, int, int, bool, bool, const BatchTile* const*, const int*,
                                                const dim3*, cudaStream_t, cudaEvent_t*);
-template cudaError_t launch_batch_step<float>(const ParamsT<float>*, int, bool, bool, const BatchTile* const*, const int*,
+template cudaError_t launch_batch_step<float>(const ParamsT<float>*, int, int, bool, bool, const BatchTile* const*, const int*,
                                               const dim3*, cudaStream_t, cudaEvent_t*);
 template cudaError_t launch_pressure<double>(const ParamsT<double>&, double*, cudaStream_t);
 template cudaError_t launch_pressure<float>(const ParamsT<float>&, double*, cudaStream_t);

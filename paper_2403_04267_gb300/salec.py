@@ -318,7 +318,7 @@ class Sim:
 
     def kernel_times(self) -> tuple[dict, int]:
         """Mean per-kernel duration (ms) over the steps recorded since the last read."""
-        n = self.launches_per_step()
+        n = 6
         out = np.zeros(n)
         steps = C.c_int()
         self._check(load().salec_kernel_times(self._h, out.ctypes.data_as(C.POINTER(C.c_double)), n, C.byref(steps)))
