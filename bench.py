@@ -620,11 +620,11 @@ def main():
 # 4000 x 4000 physics, and DRAM bytes per cell, from ncu on the 2000 x 2000 case
 # (profiles/); refreshed whenever the kernels change.
 _FLOPS_PER_CELL: dict = {"k_phase0": 85.8, "k_phase1": 49.6, "k_phase2": 38.7, "k_phase3a": 75.9, "k_phase3b": 70.4, "k_phase3c": 4.8}
-_TRAFFIC_PER_CELL: dict = {"k_phase0": 57.8, "k_phase1": 72.1, "k_phase2": 75.6, "k_phase3a": 78.3, "k_phase3b": 63.2, "k_phase3c": 22.1}
-_TRAFFIC_PER_CELL_FP32MIX: dict = {"k_phase0": 28.0, "k_phase1": 31.5, "k_phase2": 39.9, "k_phase3a": 41.9, "k_phase3b": 29.6, "k_phase3c": 10.8}
+_TRAFFIC_PER_CELL: dict = {"k_phase0": 57.7, "k_phase1": 72.1, "k_phase2": 75.5, "k_phase3a": 78.3, "k_phase3b": 63.2, "k_phase3c": 22.1}
+_TRAFFIC_PER_CELL_FP32MIX: dict = {"k_phase0": 27.9, "k_phase1": 31.5, "k_phase2": 39.9, "k_phase3a": 42.0, "k_phase3b": 29.6, "k_phase3c": 10.8}
 # fraction of the FP64 pipe's issue slots each FP64-form kernel keeps busy (ncu,
 # sm__pipe_fp64_cycles_active on the 2000 x 2000 case)
-_FP64_PIPE_BUSY: dict = {"k_phase0": 0.846, "k_phase1": 0.862, "k_phase2": 0.859, "k_phase3a": 0.858, "k_phase3b": 0.852, "k_phase3c": 0.791}
+_FP64_PIPE_BUSY: dict = {"k_phase0": 0.854, "k_phase1": 0.862, "k_phase2": 0.859, "k_phase3a": 0.858, "k_phase3b": 0.852, "k_phase3c": 0.791}
 
 if __name__ == "__main__":
     sys.exit(main())
