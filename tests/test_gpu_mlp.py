@@ -108,6 +108,37 @@ def test_forward_inference_batch_sampled_rows():
     assert np.max(np.abs(y[rows] - ref)) < 1e-2 * np.max(np.abs(ref))
 
 
+def test_forward_rows_do_not_depend_on_the_batch():
+    """Samples are independent: a sample's outputs are bitwise the same whether it is
+    computed alone, in a 300-sample batch or in a 5000-sample batch (other tiles, other
+    CTAs, the other slot of a tile pair)."""
+    theta = _net(seed=19)
+    X, _ = _data(5000, seed=10)
+    net = S.MLP(5000)
+    net.set_params(theta)
+    Xd = torch.from_numpy(X).cuda()
+    y_big = net.forward(Xd).cpu().numpy()
+    y_mid = net.forward(Xd[:300].contiguous()).cpu().numpy()
+    y_one = net.forward(Xd[257:258].contiguous()).cpu().numpy()
+    assert np.array_equal(y_big[:300], y_mid)
+    assert np.array_equal(y_big[257:258], y_one)
+
+
+def test_gradient_is_deterministic():
+    """The weight gradients split the batch over CTAs and add the partials in a fixed
+    order, the bias gradients likewise: two evaluations agree bitwise."""
+    theta = _net(seed=14)
+    X, T = _data(3534, seed=8)
+    net = S.MLP(3534)
+    net.set_params(theta)
+    Xd, Td = torch.from_numpy(X).cuda(), torch.from_numpy(T).cuda()
+    l1, g1 = net.gradient(Xd, Td)
+    l2, g2 = net.gradient(Xd, Td)
+    g1, g2 = g1.cpu().numpy(), g2.cpu().numpy()
+    assert np.array_equal(g1, g2)
+    assert np.all(np.isfinite(g1)) and np.any(g1 != 0.0)
+
+
 def test_forward_single_chain():
     """One chain of units (input 0 -> 3 -> 7 -> 1 -> 250 -> output 65) with unit weights:
     output 65 is 2 gelu(gelu(gelu(gelu(x0)))) + 0.5 up to one BF16 rounding per layer and
