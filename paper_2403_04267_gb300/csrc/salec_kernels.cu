@@ -718,6 +718,40 @@ __device__ __forceinline__ T dual_Z(const ParamsT<T>& P, int i, int j)
     return T(0.25) * (dMZ_at(P, i - 1, j) + dMZ_at(P, i - 1, j + 1) + dMZ_at(P, i, j) + dMZ_at(P, i, j + 1));
 }
 
+// What a dual face carries: mass f, momentum f w and kinetic energy f |w|^2 / 2 with the
+// upwind vertex velocity w.
+template <typename T>
+struct DualFace {
+    T f, fr, fz, e;
+};
+// products rounded as written (never fused into a multiply-add with their later use), so
+// that a face computed by either of its vertices, or read from the other, is the same
+__device__ __forceinline__ double mul_rn(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ float mul_rn(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ double add_rn(double a, double b) { return __dadd_rn(a, b); }
+__device__ __forceinline__ float add_rn(float a, float b) { return __fadd_rn(a, b); }
+template <typename T>
+__device__ __forceinline__ DualFace<T> dual_face(T f, typename VT<T>::T2 w)
+{
+    DualFace<T> d;
+    d.f = f;
+    d.fr = mul_rn(f, w.x);
+    d.fz = mul_rn(f, w.y);
+    d.e = mul_rn(mul_rn(T(0.5), f), add_rn(mul_rn(w.x, w.x), mul_rn(w.y, w.y)));
+    return d;
+}
+
+// The FP64 form shares each dual face between its two vertices (its FP64 pipe is the
+// bound, and half the face arithmetic goes); the mixed form, bound by latency, keeps one
+// computation per vertex and face and no barrier.
+template <typename T> struct ShareFaces { static constexpr bool value = false; };
+template <> struct ShareFaces<double> { static constexpr bool value = true; };
+
+// shared memory of phase 3b: the faces to the right and upper neighbours of each thread's
+// vertex, 2 x 4 values per thread (FP64 form)
+template <typename T>
+size_t phase3b_smem(dim3 blk) { return ShareFaces<T>::value ? (size_t)2 * 4 * blk.x * blk.y * sizeof(T) : 0; }
+
 template <typename T>
 __device__ __forceinline__ void body_phase3b(const ParamsT<T>& P, int bx, int by, int gx, int gy)
 {
@@ -728,40 +762,66 @@ __device__ __forceinline__ void body_phase3b(const ParamsT<T>& P, int bx, int by
     const int nr = P.nr, nz = P.nz, nv = nr + 1;
     const PtrsT<T>& p = P.p;
     double t_zmom = 0.0;
-    if (i <= nr && j <= nz) {
-        const int v = j * nv + i;
-        const T dt = step_dt<T>(p.scal);
-        const typename V::T2 vL = p.vL[v];
-        const T m0 = p.mv[v];
-        T m = m0, pr = m0 * vL.x, pz = m0 * vL.y;
-        T kin = half * m0 * (vL.x * vL.x + vL.y * vL.y);
-        T outRr = zero, outRz = zero, inRr = zero, inRz = zero;
-        T outZr = zero, outZz = zero, inZr = zero, inZz = zero;
-        if (i > 0) {   // face to (i-1, j)
-            const T f = dual_R(P, i - 1, j);
-            const typename V::T2 w = pos(f) ? p.vL[v - 1] : vL;
-            inRr = f * w.x; inRz = f * w.y;
-            m += f; kin += half * f * (w.x * w.x + w.y * w.y);
-        }
+    // Each dual face joins two vertices.  Every thread computes the faces to its vertex's
+    // right and upper neighbours and leaves them in shared memory; the faces to its left
+    // and lower neighbours are those neighbours' (recomputed, identically, on the block's
+    // first column and row), so each face is computed once per block.
+    constexpr bool share = ShareFaces<T>::value;
+    const bool valid = i <= nr && j <= nz;
+    const int nt = blockDim.x * blockDim.y, tl = threadIdx.y * blockDim.x + threadIdx.x;
+    extern __shared__ __align__(16) unsigned char smem3b[];
+    T* sR = reinterpret_cast<T*>(smem3b);
+    T* sZ = sR + 4 * nt;
+    const int v = j * nv + i;
+    typename V::T2 vL = V::mk(zero, zero);
+    DualFace<T> oR = {zero, zero, zero, zero}, oZ = {zero, zero, zero, zero};
+    if (valid) {
+        vL = p.vL[v];
         if (i < nr) {  // face to (i+1, j)
             const T f = dual_R(P, i, j);
-            const typename V::T2 w = pos(f) ? vL : p.vL[v + 1];
-            outRr = f * w.x; outRz = f * w.y;
-            m -= f; kin -= half * f * (w.x * w.x + w.y * w.y);
-        }
-        if (j > 0) {   // face to (i, j-1)
-            const T f = dual_Z(P, i, j - 1);
-            const typename V::T2 w = pos(f) ? p.vL[v - nv] : vL;
-            inZr = f * w.x; inZz = f * w.y;
-            m += f; kin += half * f * (w.x * w.x + w.y * w.y);
+            oR = dual_face<T>(f, pos(f) ? vL : p.vL[v + 1]);
         }
         {              // face to (i, j+1), or out through the top
             const T f = dual_Z(P, i, j);
-            const typename V::T2 w = (pos(f) || j == nz) ? vL : p.vL[v + nv];
-            outZr = f * w.x; outZz = f * w.y;
-            m -= f; kin -= half * f * (w.x * w.x + w.y * w.y);
-            if (warp_any(j == nz) && j == nz) t_zmom += double(outZz);
+            oZ = dual_face<T>(f, (pos(f) || j == nz) ? vL : p.vL[v + nv]);
         }
+    }
+    if (share) {
+        sR[tl] = oR.f; sR[nt + tl] = oR.fr; sR[2 * nt + tl] = oR.fz; sR[3 * nt + tl] = oR.e;
+        sZ[tl] = oZ.f; sZ[nt + tl] = oZ.fr; sZ[2 * nt + tl] = oZ.fz; sZ[3 * nt + tl] = oZ.e;
+        __syncthreads();
+    }
+    if (valid) {
+        const T dt = step_dt<T>(p.scal);
+        const T m0 = p.mv[v];
+        T m = m0, pr = m0 * vL.x, pz = m0 * vL.y;
+        T kin = half * m0 * (vL.x * vL.x + vL.y * vL.y);
+        DualFace<T> iR = {zero, zero, zero, zero}, iZ = {zero, zero, zero, zero};
+        if (i > 0) {   // face to (i-1, j)
+            if (share && threadIdx.x > 0) {
+                const int k = tl - 1;
+                iR = DualFace<T>{sR[k], sR[nt + k], sR[2 * nt + k], sR[3 * nt + k]};
+            } else {
+                const T f = dual_R(P, i - 1, j);
+                iR = dual_face<T>(f, pos(f) ? p.vL[v - 1] : vL);
+            }
+        }
+        if (j > 0) {   // face to (i, j-1)
+            if (share && threadIdx.y > 0) {
+                const int k = tl - (int)blockDim.x;
+                iZ = DualFace<T>{sZ[k], sZ[nt + k], sZ[2 * nt + k], sZ[3 * nt + k]};
+            } else {
+                const T f = dual_Z(P, i, j - 1);
+                iZ = dual_face<T>(f, pos(f) ? p.vL[v - nv] : vL);
+            }
+        }
+        m += iR.f; kin += iR.e;
+        m -= oR.f; kin -= oR.e;
+        m += iZ.f; kin += iZ.e;
+        m -= oZ.f; kin -= oZ.e;
+        const T inRr = iR.fr, inRz = iR.fz, outRr = oR.fr, outRz = oR.fz;
+        const T inZr = iZ.fr, inZz = iZ.fz, outZr = oZ.fr, outZz = oZ.fz;
+        if (warp_any(j == nz) && j == nz) t_zmom += double(outZz);
         pr += (inRr - outRr) + (inZr - outZr);
         pz += (inRz - outRz) + (inZz - outZz);
         // a resting vertex (no momentum, no kinetic energy, no flux, no deficit) gets no heat
@@ -1121,7 +1181,7 @@ static cudaError_t step_impl(const ParamsT<T>& P, const dim3* blk, cudaStream_t 
     if (ev) cudaEventRecord(ev[3], s);
     k_phase3a<T, NM, STR, UNI><<<grid_of(nr, nz, blk[3]), blk[3], 0, s>>>(P);
     if (ev) cudaEventRecord(ev[4], s);
-    k_phase3b<T><<<grid_of(nr + 1, nz + 1, blk[4]), blk[4], 0, s>>>(P);
+    k_phase3b<T><<<grid_of(nr + 1, nz + 1, blk[4]), blk[4], phase3b_smem<T>(blk[4]), s>>>(P);
     if (ev) cudaEventRecord(ev[5], s);
     k_phase3c<T, NM><<<grid_of(nr, nz, blk[5]), blk[5], 0, s>>>(P);
     if (ev) cudaEventRecord(ev[6], s);
@@ -1164,7 +1224,7 @@ static cudaError_t batch_impl(const ParamsT<T>* runs, int nruns, const BatchTile
     if (ev) cudaEventRecord(ev[3], s);
     kb_phase3a<T, NM, STR, UNI><<<ntiles[3], blk[3], 0, s>>>(runs, work[3]);
     if (ev) cudaEventRecord(ev[4], s);
-    kb_phase3b<T><<<ntiles[4], blk[4], 0, s>>>(runs, work[4]);
+    kb_phase3b<T><<<ntiles[4], blk[4], phase3b_smem<T>(blk[4]), s>>>(runs, work[4]);
     if (ev) cudaEventRecord(ev[5], s);
     kb_phase3c<T, NM><<<ntiles[5], blk[5], 0, s>>>(runs, work[5]);
     if (ev) cudaEventRecord(ev[6], s);
