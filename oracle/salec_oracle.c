@@ -115,10 +115,13 @@ static double* zalloc(size_t n) { return (double*)calloc(n ? n : 1, sizeof(doubl
 static void tillotson(const orc_material* m, double rho_in, double I_in, double* p_out, double* c2_out)
 {
     double I = I_in > 0.0 ? I_in : 0.0;
-    /* evaluated at no less than 1e-12 rho0 (reading): below it the pressure is ~a rho I,
-       negligible, and c^2 no longer depends on rho; the floor keeps the rho^-2 terms finite
-       in FP32 as well */
-    double rho = rho_in > 1e-12 * m->rho0 ? rho_in : 1e-12 * m->rho0;
+    /* evaluated at no less than rho_f = 1e-12 rho0 (reading): there the form is in its
+       dilute limit, where c^2 no longer depends on rho and the pressure is proportional to
+       it (p = a rho I once the exponential terms vanish), so below rho_f the pressure at
+       rho_f is scaled back by rho / rho_f and c^2 is taken at rho_f; the floor keeps the
+       rho^-2 terms finite in FP32 as well */
+    const double rho_f = 1e-12 * m->rho0;
+    double rho = rho_in > rho_f ? rho_in : rho_f;
     double eta = rho / m->rho0;
     double mu = eta - 1.0;
     double w0 = I / (m->E0 * eta * eta) + 1.0;
@@ -161,6 +164,9 @@ static void tillotson(const orc_material* m, double rho_in, double I_in, double*
             c2 = (we * ce2 + wc * cc2) / den;
         }
     }
+    /* a near-empty cell keeps the dilute gas's pressure, not the one at rho_f: its pressure
+       gradient per unit mass stays ~ a I / dx */
+    if (rho_in < rho_f) p = p * ((rho_in > 0.0 ? rho_in : 0.0) / rho_f);
     double floor2 = 0.01 * m->A / m->rho0;
     if (!(c2 > floor2)) c2 = floor2;
     *p_out = p;

@@ -156,8 +156,10 @@ __host__ __device__ inline void eos_eval(const MatT<T>& m, T rho_in, T I_in, T& 
         c2_out = m.gamma * gm1 * I;
         return;
     }
-    // evaluated at no less than 1e-12 rho0: below it p ~ a rho I is negligible and c^2 no
-    // longer depends on rho, and the rho^-2 terms below stay finite in FP32
+    // evaluated at no less than rho_f = 1e-12 rho0, where the form is in its dilute limit:
+    // c^2 no longer depends on rho and p is proportional to it (p = a rho I once the
+    // exponential terms vanish), so below rho_f the pressure is scaled back by rho / rho_f;
+    // the rho^-2 terms below stay finite in FP32
     const T rho_floor = T(1e-12) * m.rho0;
     const T rho = rho_in > rho_floor ? rho_in : rho_floor;
     // two divisions: 1/rho and 1/w0 (1/(E0 eta^2) = (rho0^2/E0) / rho^2)
@@ -203,6 +205,9 @@ __host__ __device__ inline void eos_eval(const MatT<T>& m, T rho_in, T I_in, T& 
             c2 = we * ce2 + wc * (pc_r + pc * irho2 * pc_I);
         }
     }
+    // a near-empty cell keeps the dilute gas's pressure, not the one at rho_f (whose
+    // gradient per unit of so little mass would accelerate it without bound)
+    if (rho_in < rho_floor) p *= (rho_in > zero ? rho_in : zero) * m.inv_rho0 * T(1e12);
     if (!(c2 > m.c2_floor)) c2 = m.c2_floor;
     p_out = p;
     c2_out = c2;

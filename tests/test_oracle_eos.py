@@ -128,11 +128,22 @@ def test_blend_sound_speed_is_blend_of_branch_sound_speeds(m, eta):
 
 @pytest.mark.parametrize("m", [BAS, IRON])
 def test_density_floor(m):
-    """Reading: the Tillotson form is evaluated at no less than 1e-12 rho0; there p -> a rho I
-    and c^2 -> a (1 + a) I (pinned above), so the floor changes nothing but keeps the
-    rho^-2 terms finite."""
+    """Reading: the Tillotson form is evaluated at no less than rho_f = 1e-12 rho0, where it
+    is in its dilute limit: c^2 -> a (1 + a) I (pinned above) no longer depends on rho, and
+    p -> a rho I is proportional to it, so below rho_f the pressure at rho_f is scaled back
+    by rho / rho_f.  Far below the floor the hot state's pressure is the closed form a rho I
+    (a pressure left at its rho_f value would be 1e8 times that at 1e-20 rho0 and would
+    accelerate a near-empty cell without bound); the cold state keeps its sign (tension,
+    clipped by the caller); an empty cell has none."""
     I = 2 * m["Ecv"]
     lo = O.eos(m, 1e-12 * m["rho0"], I)
-    assert O.eos(m, 1e-20 * m["rho0"], I) == lo
-    assert O.eos(m, 0.0, I) == lo
     assert math.isclose(lo[1], m["a"] * (1 + m["a"]) * I, rel_tol=1e-9)
+    for eta in (1e-13, 1e-16, 1e-20):
+        rho = eta * m["rho0"]
+        p, c2 = O.eos(m, rho, I)
+        assert c2 == lo[1]
+        assert math.isclose(p, m["a"] * rho * I, rel_tol=1e-12)
+    assert O.eos(m, 0.0, I) == (0.0, lo[1])
+    pc_lo, _ = O.eos(m, 1e-12 * m["rho0"], 0.5 * m["Eiv"])
+    pc, _ = O.eos(m, 1e-16 * m["rho0"], 0.5 * m["Eiv"])
+    assert pc_lo < 0.0 and math.isclose(pc, pc_lo * 1e-4, rel_tol=1e-12)
