@@ -207,6 +207,7 @@ static MatT<T> to_mat(const salec_material& s)
     m.G = T(s.strength == SALEC_STRENGTH_COLLINS ? s.G : 0.0);
     m.eps_fb = T(s.eps_fb); m.B_dam = T(s.B_dam); m.p_bd = T(s.p_bd); m.p_t = T(s.p_t);
     m.c2_floor = T(s.eos == SALEC_EOS_TILLOTSON ? 0.01 * s.A / s.rho0 : 0.0);
+    m.rho_f = T(1e-12 * s.rho0); m.inv_rho_f = T(1.0 / (1e-12 * s.rho0));
     return m;
 }
 

@@ -45,6 +45,7 @@ struct MatT {
     int eos, strength;
     T rho0, inv_rho0, rho0sq_E0, A, B, E0, a, b, alpha, beta, Eiv, Ecv, inv_dE, gamma;
     T Yi0, mui, Yim, Yd0, mud, Ydm, inv_Yspan, G, eps_fb, B_dam, p_bd, p_t, c2_floor;
+    T rho_f, inv_rho_f;     // the Tillotson density floor 1e-12 rho0 and its reciprocal
 };
 typedef MatT<double> Mat;
 
@@ -145,6 +146,11 @@ template <> __host__ __device__ inline float t_sqrt<float>(float x) { return sqr
 // before the tension cut-off and c^2 = dp/drho + p/rho^2 dp/dI of the branch (in the
 // blend, the blend of the two branches' values), floored.
 // ---------------------------------------------------------------------------------
+// a < b for b > 0 on the bit patterns: an integer compare (any negative a, and -0, is below)
+__device__ __forceinline__ bool below_bits(double a, double b) { return __double_as_longlong(a) < __double_as_longlong(b); }
+__device__ __forceinline__ bool below_bits(float a, float b) { return __float_as_int(a) < __float_as_int(b); }
+__device__ __forceinline__ bool warp_any(bool p);
+
 template <typename T>
 __host__ __device__ inline void eos_eval(const MatT<T>& m, T rho_in, T I_in, T& p_out, T& c2_out)
 {
@@ -160,8 +166,7 @@ __host__ __device__ inline void eos_eval(const MatT<T>& m, T rho_in, T I_in, T& 
     // c^2 no longer depends on rho and p is proportional to it (p = a rho I once the
     // exponential terms vanish), so below rho_f the pressure is scaled back by rho / rho_f;
     // the rho^-2 terms below stay finite in FP32
-    const T rho_floor = T(1e-12) * m.rho0;
-    const T rho = rho_in > rho_floor ? rho_in : rho_floor;
+    const T rho = rho_in > m.rho_f ? rho_in : m.rho_f;
     // two divisions: 1/rho and 1/w0 (1/(E0 eta^2) = (rho0^2/E0) / rho^2)
     const T irho = one / rho;
     const T mu = (rho - m.rho0) * m.inv_rho0;
@@ -206,8 +211,15 @@ __host__ __device__ inline void eos_eval(const MatT<T>& m, T rho_in, T I_in, T& 
         }
     }
     // a near-empty cell keeps the dilute gas's pressure, not the one at rho_f (whose
-    // gradient per unit of so little mass would accelerate it without bound)
-    if (rho_in < rho_floor) p *= (rho_in > zero ? rho_in : zero) * m.inv_rho0 * T(1e12);
+    // gradient per unit of so little mass would accelerate it without bound); such cells
+    // are rare, so on the GPU the test is an integer compare of the bit patterns (rho_f > 0:
+    // a negative rho_in or -0 compares below it too) behind a warp-uniform branch
+#ifdef __CUDA_ARCH__
+    const bool dilute = below_bits(rho_in, m.rho_f);
+    if (warp_any(dilute) && dilute) p *= (rho_in > zero ? rho_in : zero) * m.inv_rho_f;
+#else
+    if (rho_in < m.rho_f) p *= (rho_in > zero ? rho_in : zero) * m.inv_rho_f;
+#endif
     if (!(c2 > m.c2_floor)) c2 = m.c2_floor;
     p_out = p;
     c2_out = c2;

@@ -186,6 +186,7 @@ extern "C" salec_status salec_courant_dt_noalloc(const salec_grid* grid, const s
             M.inv_dE = (s.Ecv > s.Eiv) ? 1.0 / (s.Ecv - s.Eiv) : 0.0;
             M.gamma = s.gamma;
             M.c2_floor = s.eos == SALEC_EOS_TILLOTSON ? 0.01 * s.A / s.rho0 : 0.0;
+            M.rho_f = 1e-12 * s.rho0; M.inv_rho_f = 1.0 / (1e-12 * s.rho0);
         }
     }
     A.I = I;
