@@ -122,3 +122,13 @@ def stretched_layered_spec(n_core: int = 40, ext: int = 8, pml: int = 8) -> dict
                        dict(mat=2, zlo=0.0, zhi=zv[ks - 15], rho=0.0, I0=0.0, vz=0.0)],
             "projectile": dict(mat=2, radius=3 * dx, zc=zv[ks] + 3 * dx, vz=-12e3, rho=0.0, I0=0.0),
             "z_surface": zv[ks]}
+
+
+def dilute_slab_spec(eta: float, nr: int = 8, nz: int = 48, dx: float = 10.0) -> dict:
+    """A slab of hot basalt vapour (density eta rho0, specific energy 2 E_cv, at rest) in
+    vacuum: rows 20-25 of a column with an open top and no gravity."""
+    bas = W.basalt()
+    g = W.grid(nr, nz, dx, bc_top="outflow")
+    return {"grid": g, "materials": [bas], "projectile": None,
+            "layers": [dict(mat=0, zlo=20 * dx, zhi=26 * dx, rho=eta * bas["rho0"],
+                            I0=2.0 * bas["Ecv"], vz=0.0)]}
