@@ -171,8 +171,8 @@ def job_reduce(vals_max, vals_sum, device="cpu"):
 def _batched(args, rank, ws):
     """Batched impacts of the seeded distribution (rank r takes seeds r, r + ws, ...), FP32-mix,
     each to t_end: one batch, autotuned block shapes, CUDA-graph chunks.  A run whose status
-    reports a failure (a crater or projectile reaching an absorbing strip can drive a cell
-    to negative density) stops where it failed and counts as finished.  runs/hour over the
+    reports a failure (a non-positive volume or density, a NaN, or a step below dt_min) stops
+    where it failed, counts as finished and is listed by cause.  runs/hour over the
     whole job; the plain FP64 solver, one run at a time, on the first few draws that finished
     cleanly gives the reference runs/hour and the crater depth and diameter that the batch
     is checked against (the FP64 GPU solver matches the FP64 oracle to 1e-9 and stands in
@@ -207,14 +207,24 @@ def _batched(args, rank, ws):
     failed = polled[:, 3] != 0
     finished = (polled[:, 0] >= polled[:, 4]) | failed
     cell_updates = float(sum(polled[k, 2] * specs[k]["grid"]["nr"] * specs[k]["grid"]["nz"] for k in range(len(specs))))
-    (tmax,), (nfin, nfail) = job_reduce([wall], [int(finished.sum()), int(failed.sum())], "cuda")
+    st = polled[:, 3].astype(np.int64)
+    iron = np.array([sp["materials"][-1]["rho0"] > 5000.0 for sp in specs])
+    causes = [int(((st & 1) != 0).sum()), int(((st & 2) != 0).sum()), int(((st & 4) != 0).sum()),
+              int((failed & iron).sum()), int((failed & ~iron).sum())]
+    (tmax,), (nfin, nfail, *causes) = job_reduce(
+        [wall], [int(finished.sum()), int(failed.sum())] + causes, "cuda")
     nfin, nfail = int(nfin), int(nfail)
     out = {"runs": args.batch_runs, "t_end_s": args.batch_t_end, "precision": "FP32-mix",
            "runs_finished": nfin, "runs_failed": nfail, "complete": nfin == args.batch_runs,
            "wall_s": round(tmax, 2),
            "runs_per_hour": nfin * 3600.0 / tmax if nfin == args.batch_runs else None,
            "cell_updates_per_s": cell_updates / wall, "batch_steps": int(steps), "cells_per_step": cells,
-           "setup_s": round(setup_s, 1), "block_shapes": shapes, "runs_per_rank": len(specs)}
+           "setup_s": round(setup_s, 1), "block_shapes": shapes, "runs_per_rank": len(specs),
+           "failures": {"volume_or_density": int(causes[0]), "nan": int(causes[1]), "dt_min": int(causes[2]),
+                        "iron_projectile": int(causes[3]), "basalt_projectile": int(causes[4]),
+                        "rank0_first": [{"seed": int(seeds[k]), "n": specs[k]["grid"]["nr"], "status": int(st[k]),
+                                         "t_s": round(float(polled[k, 0]), 3), "steps": int(polled[k, 2])}
+                                        for k in np.where(failed)[0][:16]]}}
     # reference: the plain FP64 solver, one run at a time, on the first draws that finished cleanly
     ok = [k for k in range(len(specs)) if finished[k] and not failed[k]][:args.batch_ref_runs]
     if ok:
