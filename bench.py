@@ -208,9 +208,16 @@ def _batched(args, rank, ws):
     finished = (polled[:, 0] >= polled[:, 4]) | failed
     cell_updates = float(sum(polled[k, 2] * specs[k]["grid"]["nr"] * specs[k]["grid"]["nz"] for k in range(len(specs))))
     st = polled[:, 3].astype(np.int64)
+    # flagged (after the timed region): runs whose crater rim reached the absorbing strip
+    at_pml = 0
+    for k, sp in enumerate(specs):
+        g = sp["grid"]
+        if not failed[k]:
+            c = sims[k].crater(sp["z_surface"], 64)
+            at_pml += int(0.5 * c["diameter"] >= (g["nr"] - g["pml_r"]) * g["dx"])
     iron = np.array([sp["materials"][-1]["rho0"] > 5000.0 for sp in specs])
     causes = [int(((st & 1) != 0).sum()), int(((st & 2) != 0).sum()), int(((st & 4) != 0).sum()),
-              int((failed & iron).sum()), int((failed & ~iron).sum())]
+              int((failed & iron).sum()), int((failed & ~iron).sum()), at_pml]
     (tmax,), (nfin, nfail, *causes) = job_reduce(
         [wall], [int(finished.sum()), int(failed.sum())] + causes, "cuda")
     nfin, nfail = int(nfin), int(nfail)
@@ -220,6 +227,7 @@ def _batched(args, rank, ws):
            "runs_per_hour": nfin * 3600.0 / tmax if nfin == args.batch_runs else None,
            "cell_updates_per_s": cell_updates / wall, "batch_steps": int(steps), "cells_per_step": cells,
            "setup_s": round(setup_s, 1), "block_shapes": shapes, "runs_per_rank": len(specs),
+           "crater_reached_pml": int(causes[5]),
            "failures": {"volume_or_density": int(causes[0]), "nan": int(causes[1]), "dt_min": int(causes[2]),
                         "iron_projectile": int(causes[3]), "basalt_projectile": int(causes[4]),
                         "rank0_first": [{"seed": int(seeds[k]), "n": specs[k]["grid"]["nr"], "status": int(st[k]),
