@@ -168,6 +168,22 @@ def job_reduce(vals_max, vals_sum, device="cpu"):
     return mx.tolist(), sm.tolist()
 
 
+def batch_failures(polled, specs, half_diameters) -> list:
+    """Counts of a batch's outcomes, in the order [non-positive volume or density, NaN, step
+    below dt_min, failed runs with an iron projectile, with a basalt one, runs whose crater
+    rim reached the absorbing strip].  `polled` rows are (t, dt, steps, status, t_end);
+    `half_diameters` holds each run's crater half-width in metres (None for a failed run).
+    A run counts once per status bit it carries."""
+    import numpy as np
+    st = np.asarray(polled)[:, 3].astype(np.int64)
+    failed = st != 0
+    iron = np.array([sp["materials"][-1]["rho0"] > 5000.0 for sp in specs], dtype=bool)
+    at_pml = sum(1 for sp, h in zip(specs, half_diameters)
+                 if h is not None and h >= (sp["grid"]["nr"] - sp["grid"]["pml_r"]) * sp["grid"]["dx"])
+    return [int(((st & 1) != 0).sum()), int(((st & 2) != 0).sum()), int(((st & 4) != 0).sum()),
+            int((failed & iron).sum()), int((failed & ~iron).sum()), int(at_pml)]
+
+
 def _batched(args, rank, ws):
     """Batched impacts of the seeded distribution (rank r takes seeds r, r + ws, ...), FP32-mix,
     each to t_end: one batch, autotuned block shapes, CUDA-graph chunks.  A run whose status
@@ -208,16 +224,10 @@ def _batched(args, rank, ws):
     finished = (polled[:, 0] >= polled[:, 4]) | failed
     cell_updates = float(sum(polled[k, 2] * specs[k]["grid"]["nr"] * specs[k]["grid"]["nz"] for k in range(len(specs))))
     st = polled[:, 3].astype(np.int64)
-    # flagged (after the timed region): runs whose crater rim reached the absorbing strip
-    at_pml = 0
-    for k, sp in enumerate(specs):
-        g = sp["grid"]
-        if not failed[k]:
-            c = sims[k].crater(sp["z_surface"], 64)
-            at_pml += int(0.5 * c["diameter"] >= (g["nr"] - g["pml_r"]) * g["dx"])
-    iron = np.array([sp["materials"][-1]["rho0"] > 5000.0 for sp in specs])
-    causes = [int(((st & 1) != 0).sum()), int(((st & 2) != 0).sum()), int(((st & 4) != 0).sum()),
-              int((failed & iron).sum()), int((failed & ~iron).sum()), at_pml]
+    # read after the timed region: each clean run's crater half-width, for the strip flag
+    half = [None if failed[k] else 0.5 * sims[k].crater(sp["z_surface"], 64)["diameter"]
+            for k, sp in enumerate(specs)]
+    causes = batch_failures(polled, specs, half)
     (tmax,), (nfin, nfail, *causes) = job_reduce(
         [wall], [int(finished.sum()), int(failed.sum())] + causes, "cuda")
     nfin, nfail = int(nfin), int(nfail)

@@ -57,3 +57,26 @@ def test_single_process_is_a_no_op():
     import bench
     assert bench.shard(5, 0, 1) == [0, 1, 2, 3, 4]
     assert bench.job_reduce([3.0], [4, 5]) == ([3.0], [4.0, 5.0])
+
+
+def test_batch_failures_counts_causes():
+    """The batched leg's outcome counts: one count per status bit (1 non-positive volume or
+    density, 2 NaN, 4 step below dt_min), failed runs split by projectile, and clean runs
+    whose crater half-width reaches the absorbing strip (nr - pml_r cells from the axis)."""
+    import numpy as np
+    sys.path.insert(0, ROOT)
+    import bench
+    from paper_2403_04267_gb300 import workloads as W
+
+    def spec(projectile):
+        sp = W.batched_run(W.batched_draw(7), 100)
+        sp["materials"][-1] = W.iron() if projectile == "iron" else W.basalt()
+        return sp
+
+    specs = [spec(p) for p in ("iron", "basalt", "basalt", "iron", "basalt", "basalt")]
+    strip = (specs[0]["grid"]["nr"] - specs[0]["grid"]["pml_r"]) * specs[0]["grid"]["dx"]
+    status = [0, 1, 5, 2, 0, 0]
+    polled = np.array([[20.0, 1e-3, 100, s, 20.0] for s in status])
+    half = [strip, None, None, None, strip - 1.0, strip + 5.0]
+    assert bench.batch_failures(polled, specs, half) == [2, 1, 1, 1, 2, 2]
+    assert bench.batch_failures(np.zeros((0, 5)), [], []) == [0, 0, 0, 0, 0, 0]
