@@ -80,7 +80,10 @@ typedef struct salec_grid {
 } salec_grid;
 
 /* One material: Tillotson (1962) or ideal-gas EoS; optional Collins et al. (2004)
- * strength with scalar damage (Sect. 1 and Table 1 of the paper). */
+ * strength with scalar damage (Sect. 1 and Table 1 of the paper).  The Tillotson form is
+ * evaluated at no less than 1e-12 rho0, its dilute limit: below that density the sound
+ * speed is the value there and the pressure is scaled by rho / (1e-12 rho0), i.e. it stays
+ * a rho I; c^2 is floored at 0.01 A / rho0. */
 typedef struct salec_material {
     int eos;                                        /* SALEC_EOS_* */
     double rho0;                                    /* reference density, kg/m^3 */
