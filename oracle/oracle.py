@@ -24,7 +24,7 @@ _lib = None
 # field codes (same meaning as the C enum in salec_oracle.c)
 FIELDS = {
     "f0": 0, "f1": 1, "f2": 2, "rho0": 3, "rho1": 4, "rho2": 5, "I": 6, "srr": 7, "szz": 8,
-    "srz": 9, "D": 10, "pmax": 11, "vr": 12, "vz": 13, "p": 14,
+    "srz": 9, "D": 10, "pmax": 11, "vr": 12, "vz": 13, "p": 14, "P_total": 15,
     "phi1_b": 20, "phi3_b": 21, "psi2_b": 22, "phi1_r": 23, "phi3_r": 24, "psi2_r": 25,
     "phi2r_b": 30, "phi2z_b": 31, "psi1r_b": 32, "psi1z_b": 33,
     "phi2r_r": 34, "phi2z_r": 35, "psi1r_r": 36, "psi1z_r": 37,
@@ -92,6 +92,7 @@ def lib():
         L.orc_place_projectile.argtypes = [P, C.c_int] + [C.c_double] * 5
         L.orc_finalize.argtypes = [P]
         L.orc_step.argtypes = [P, C.c_int]
+        L.orc_phase0.argtypes = [P]
         L.orc_get_field.argtypes = [P, C.c_int, D, C.c_long]
         L.orc_set_field.argtypes = [P, C.c_int, D, C.c_long]
         L.orc_scalars.argtypes = [P, D]
@@ -209,6 +210,12 @@ class OracleSim:
 
     def step(self, n: int) -> int:
         return lib().orc_step(self._h, int(n))
+
+    def phase0(self) -> int:
+        """Phase 0 alone on the current state (EoS, artificial viscosity, peak
+        over-pressure, Courant step) without advancing; afterwards ``get("P_total")`` is the
+        total isotropic pressure p_hat + Phi q it formed."""
+        return lib().orc_phase0(self._h)
 
     def _shape(self, name):
         return (self.nz + 1, self.nr + 1) if name in VERTEX_FIELDS else (self.nz, self.nr)

@@ -1292,6 +1292,16 @@ int orc_step(orc_sim* s, int nsteps)
     return s->status;
 }
 
+/* Phase 0 alone on the current state (EoS, artificial viscosity, peak over-pressure and the
+ * Courant step), without advancing: the total isotropic pressure P = p_hat + Phi q it forms
+ * is then readable as field F_PTOTAL.  For the artificial-viscosity pins. */
+int orc_phase0(orc_sim* s)
+{
+    if (!s->finalized) return 1;
+    phase0_eos_dt(s);
+    return s->status;
+}
+
 /* ------------------------------------------------------------------------------------
  * Field access.  Cell fields are row-major [j][i] (j = 0 at the bottom), vertex fields
  * [j][i] over (nr+1) x (nz+1).
@@ -1299,7 +1309,7 @@ int orc_step(orc_sim* s, int nsteps)
 enum {
     F_VOLFRAC0 = 0, F_VOLFRAC1 = 1, F_VOLFRAC2 = 2, F_DENS0 = 3, F_DENS1 = 4, F_DENS2 = 5,
     F_IE = 6, F_SRR = 7, F_SZZ = 8, F_SRZ = 9, F_DAMAGE = 10, F_PMAX = 11,
-    F_VR = 12, F_VZ = 13, F_PRESSURE = 14,
+    F_VR = 12, F_VZ = 13, F_PRESSURE = 14, F_PTOTAL = 15,
     F_PHI1_B = 20, F_PHI3_B = 21, F_PSI2_B = 22, F_PHI1_R = 23, F_PHI3_R = 24, F_PSI2_R = 25,
     F_PHI2R_B = 30, F_PHI2Z_B = 31, F_PSI1R_B = 32, F_PSI1Z_B = 33,
     F_PHI2R_R = 34, F_PHI2Z_R = 35, F_PSI1R_R = 36, F_PSI1Z_R = 37
@@ -1313,6 +1323,7 @@ static double* field_ptr(orc_sim* s, int field, int* is_vertex)
     switch (field) {
     case F_IE: return s->I; case F_SRR: return s->srr; case F_SZZ: return s->szz;
     case F_SRZ: return s->srz; case F_DAMAGE: return s->D; case F_PMAX: return s->pmax;
+    case F_PTOTAL: return s->P;
     case F_PHI1_B: return s->phi1_b; case F_PHI3_B: return s->phi3_b; case F_PSI2_B: return s->psi2_b;
     case F_PHI1_R: return s->phi1_r; case F_PHI3_R: return s->phi3_r; case F_PSI2_R: return s->psi2_r;
     default: break;
@@ -1352,7 +1363,7 @@ int orc_set_field(orc_sim* s, int field, const double* in, long n)
 {
     int isv;
     double* p = field_ptr(s, field, &isv);
-    if (!p || field == F_PRESSURE) return 1;
+    if (!p || field == F_PRESSURE || field == F_PTOTAL) return 1;
     if (n != (isv ? s->nvert : s->ncell)) return 1;
     memcpy(p, in, sizeof(double) * (size_t)n);
     return 0;
