@@ -131,6 +131,53 @@ def gated(report):
     return {k: v for k, v in report.items() if not k.startswith("info:")}
 
 
+# the largest bound a sensitivity-relaxed comparison may apply: beyond it the problem's
+# own round-off response would hide a real difference
+RELAXED_CAP = 1e-6
+
+
+def assert_parity(g, r, spec, tol=1e-9, sensitivity=None, status_zero=False):
+    """Every gated quantity of `parity` within tol, the step count and status equal, t and
+    dt within tol.  With `sensitivity` (the oracle against itself after a 1e-15 input
+    perturbation, same steps) a quantity may instead be within 100 times the problem's own
+    response to that perturbation, never more than RELAXED_CAP.  The bound applied to each
+    quantity is printed beside its difference."""
+    rep = parity(g, r, spec)
+    errs = gated(rep)
+
+    def bound_of(k):
+        if sensitivity is None:
+            return tol
+        b = max(tol, 100.0 * sensitivity.get(k, 0.0))
+        assert b <= RELAXED_CAP, f"{k}: the relaxed bound {b:.1e} exceeds {RELAXED_CAP:.0e}"
+        return b
+
+    print({k: f"{v:.1e}" for k, v in rep.items() if k.startswith("info:")})
+    print({k: f"{e:.1e} <= {bound_of(k):.1e}" for k, e in errs.items()})
+    for k, e in errs.items():
+        bound = bound_of(k)
+        assert e <= bound, f"{k}: {e:.3e} > {bound:.1e} (all: { {kk: f'{v:.1e}' for kk, v in rep.items()} })"
+    sg, so = g.scalars(), r.scalars()
+    assert sg["nstep"] == so["nstep"]
+    assert sg["status"] == so["status"]
+    if status_zero:
+        assert so["status"] == 0
+    for k in ("t", "dt"):
+        bound = bound_of(k)
+        print(f"{k}: {abs(sg[k] - so[k]) / max(so[k], 1e-300):.1e} <= {bound:.1e}")
+        assert abs(sg[k] - so[k]) <= bound * max(so[k], 1e-300), k
+    return errs
+
+
+def sensitivity(r, r2, spec):
+    """The oracle's own response (run r2, perturbed at set-up, against r): the gated
+    quantities and the relative t, dt differences."""
+    sens = gated(parity(r2, r, spec))
+    s2, s1 = r2.scalars(), r.scalars()
+    sens.update({k: abs(s2[k] - s1[k]) / s1[k] for k in ("t", "dt")})
+    return sens
+
+
 def perturbed(sim, rel=1e-15, seed=0):
     """Multiply the density, energy and velocity fields of an oracle run by 1 + rel * noise
     (an input perturbation at round-off level, used to measure the problem's own

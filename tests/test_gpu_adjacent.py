@@ -25,16 +25,7 @@ def _cuda():
 
 
 def _check(g, r, spec, tol=TOL, sensitivity=None):
-    rep = U.parity(g, r, spec)
-    print({k: f"{v:.1e}" for k, v in rep.items()})
-    for k, e in U.gated(rep).items():
-        bound = tol if sensitivity is None else max(tol, 100.0 * sensitivity.get(k, 0.0))
-        assert e <= bound, f"{k}: {e:.3e} > {bound:.1e}"
-    sg, so = g.scalars(), r.scalars()
-    assert sg["nstep"] == so["nstep"] and sg["status"] == so["status"] == 0
-    for k in ("t", "dt"):
-        bound = tol if sensitivity is None else max(tol, 100.0 * sensitivity.get(k, 0.0))
-        assert abs(sg[k] - so[k]) <= bound * so[k], k
+    U.assert_parity(g, r, spec, tol=tol, sensitivity=sensitivity, status_zero=True)
 
 
 def test_layered_column_matches_oracle_and_stays_at_rest():
@@ -74,9 +65,7 @@ def test_layered_impact_against_oracle():
     r2.step(1)
     for s in (g, r, r2):
         s.step(59)
-    sens = U.gated(U.parity(r2, r, spec))
-    s2, s1 = r2.scalars(), r.scalars()
-    sens.update({k: abs(s2[k] - s1[k]) / s1[k] for k in ("t", "dt")})
+    sens = U.sensitivity(r, r2, spec)
     _check(g, r, spec, sensitivity=sens)
 
 

@@ -2,7 +2,9 @@
 by element on the same seeded inputs.  Bar: relative max-norm ||a - b||_inf / ||b||_inf
 <= 1e-9 (the FP64 target) for every conserved variable and for every intensive field where
 material is present (see gpu_util.py for the metric and why), after 1 step (every phase at
-once) and after 200 steps; plus exact properties (rest state, determinism, checkpoint)."""
+once) and after 200 steps; plus exact properties (rest state, determinism, checkpoint).
+Ill-conditioned cases (yielding cells) may take 100 x the oracle's own round-off response
+instead, never more than 1e-6; every test prints the bound it applied per quantity."""
 import math
 
 import numpy as np
@@ -37,22 +39,7 @@ def _pair(spec, steps):
 
 
 def _assert_parity(g, r, spec, tol=TOL, sensitivity=None):
-    """Every gated quantity within tol; with `sensitivity` (the oracle against itself after
-    a 1e-15 input perturbation, same steps) a quantity may instead be within 100 times the
-    problem's own response to that perturbation."""
-    rep = U.parity(g, r, spec)
-    errs = U.gated(rep)
-    print({k: f"{v:.1e}" for k, v in rep.items()})
-    for k, e in errs.items():
-        bound = tol if sensitivity is None else max(tol, 100.0 * sensitivity.get(k, 0.0))
-        assert e <= bound, f"{k}: {e:.3e} > {bound:.1e} (all: { {kk: f'{v:.1e}' for kk, v in rep.items()} })"
-    sg, so = g.scalars(), r.scalars()
-    assert sg["nstep"] == so["nstep"]
-    for k in ("t", "dt"):
-        bound = tol if sensitivity is None else max(tol, 100.0 * sensitivity.get(k, 0.0))
-        assert abs(sg[k] - so[k]) <= bound * max(so[k], 1e-300), k
-    assert sg["status"] == so["status"]
-    return errs
+    return U.assert_parity(g, r, spec, tol=tol, sensitivity=sensitivity)
 
 
 def test_initial_state_matches():
@@ -74,10 +61,18 @@ def test_plain_100x100_one_step_and_200_steps():
     assert g.scalars()["nstep"] == 200
 
 
-def test_full_method_800x800_twenty_steps():
+def test_full_method_800x800_twenty_and_200_steps():
+    """The full method (two materials, Collins strength and damage, gravity, PML 40) on the
+    800 x 800 workload: 20 steps, then 200 (about a minute of serial oracle), each within the
+    FP64 bar of 1e-9 (the oracle's own response to a 1e-15 input perturbation is 7e-11
+    after 200 steps)."""
     spec = W.full_fp64_800()
     g, r = _pair(spec, 20)
     _assert_parity(g, r, spec)
+    g.step(180)
+    r.step(180)
+    _assert_parity(g, r, spec)
+    assert g.scalars()["nstep"] == 200
 
 
 @pytest.mark.parametrize("seed,nr,nz,nmat,strength", [
@@ -97,9 +92,7 @@ def test_random_ragged_grids(seed, nr, nz, nmat, strength):
     g.step(59)
     r.step(59)
     r2.step(59)
-    sens = U.gated(U.parity(r2, r, spec))
-    s2, s1 = r2.scalars(), r.scalars()
-    sens.update({k: abs(s2[k] - s1[k]) / s1[k] for k in ("t", "dt")})
+    sens = U.sensitivity(r, r2, spec)
     _assert_parity(g, r, spec, sensitivity=sens)
 
 
@@ -249,7 +242,5 @@ def test_batched_impact_draw_against_oracle():
     r.step(40)
     r2 = U.perturbed(O.OracleSim(spec))
     r2.step(40)
-    sens = U.gated(U.parity(r2, r, spec))
-    s2, s1 = r2.scalars(), r.scalars()
-    sens.update({k: abs(s2[k] - s1[k]) / s1[k] for k in ("t", "dt")})
+    sens = U.sensitivity(r, r2, spec)
     _assert_parity(g, r, spec, sensitivity=sens)
