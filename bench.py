@@ -9,13 +9,14 @@ Courant min-reduction, Lagrangian momentum/energy/strength, PML, donor-cell rema
 momentum remap, heat) over all 16e6 cells.  The state (~1.3 GB) is larger than L2, so no
 flush is needed between steps.
 
-Output: one JSON line (see the contract in the design doc):
+Output: one JSON line:
   value      cell-updates/s, device-timed (CUDA events on the library's stream), state
              resident in HBM; N GPUs run N independent replicas (weak scaling)
   e2e        the same metric through the C ABI with host buffers: the initial state is
              copied from pinned host memory, every step reads its scalars (t, dt, status)
              back, and the final pressure field is copied to the host
-  roofline   the dominant kernel against its bound
+  roofline   the dominant kernel against its bound: the FP64 pipe for the FP64 form,
+             HBM bandwidth for the mixed form
   cpu_baseline  the serial FP64 oracle on the host cores, on a bounded sample
 ``--impl reference`` times the oracle itself (the reference arm of this repository).
 """

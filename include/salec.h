@@ -48,7 +48,7 @@ typedef enum {
 /* Arithmetic of the step.  SALEC_FP64: every field and operation in FP64.
  * SALEC_FP32MIX: fields, stencils and material laws in FP32, while the specific internal
  * energy and its updates, the Courant reduction and the conservation sums are FP64
- * (SURVEY's mixed form; the state buffer is about half the size). */
+ * (the state buffer is about half the size). */
 enum { SALEC_FP64 = 0, SALEC_FP32MIX = 1 };
 
 enum { SALEC_EOS_TILLOTSON = 0, SALEC_EOS_IDEAL_GAS = 1 };
@@ -252,20 +252,25 @@ void salec_batch_destroy(salec_batch* batch);
  * another program's field pointers, the allocator is locked).  The paper has no
  * counterpart; it is the step size salec_step's first kernel computes, evaluated on
  * caller-owned device buffers:
- *   grid    nr, nz, nmat, dx, cfl, dt_growth, dt_max are used
+ *   grid    nr, nz, nmat, dx, cfl, dt_growth, dt_max, dt_min are used
  *   mats    nmat materials (host)
  *   fr[m]   device pointer to nr*nz (f_m, rho_m) pairs of doubles, row-major [j][i]
  *   I       device pointer to nr*nz specific internal energies
  *   D       device pointer to nr*nz damage values, or NULL (not needed for dt)
  *   v       device pointer to (nr+1)*(nz+1) (v_r, v_z) pairs
  *   dt_prev the previous step (growth limit); *dt_out receives the step (host).
- * The call enqueues a memset and one kernel on `stream` and synchronises it.  Its scratch
- * is file-scope device memory of fixed size (65536 blocks of 32 x 8 cells, e.g. 4096 x
- * 4096 cells; larger grids return SALEC_EINVAL) held by every device that loads the
- * library until the process exits.  The first call on a device looks up that memory's
- * address with the device current; make it before any stream capture.  All calls share
- * the scratch: calls that overlap on the GPU (different streams or threads) race.
- * Failures without a context are described by salec_last_error(NULL). */
+ * Cells are taken as uniform squares of grid->dx (a grid given non-uniform sizes with
+ * salec_set_spacing needs salec_step's own step).  The call enqueues a memset and one
+ * kernel on `stream` and synchronises it.  It returns SALEC_EUNSTABLE, leaving *dt_out
+ * alone, where salec_step's status word would report a failure: a NaN vertex speed or
+ * sound speed, or a step below grid->dt_min.  Its scratch is file-scope device memory of
+ * fixed size (65536 blocks of 32 x 8 cells, e.g. 4096 x 4096 cells; larger grids, and
+ * grids of more than 65535 block rows, return SALEC_EINVAL) held by every device that
+ * loads the library until the process exits.  The first call on a device looks up that
+ * memory's address with the device current; make it before any stream capture, and do
+ * not use the call across a device reset.  All calls share the scratch: calls that
+ * overlap on the GPU (different streams or threads) race.  Failures without a context are
+ * described by salec_last_error(NULL). */
 salec_status salec_courant_dt_noalloc(const salec_grid* grid, const salec_material* mats,
                                       const double* const* fr, const double* I, const double* D,
                                       const double* v, double dt_prev, double* dt_out, void* stream);

@@ -191,27 +191,6 @@ template <typename T>
 static T* at(salec_ctx* ctx, size_t off) { return reinterpret_cast<T*>(ctx->base + off); }
 
 template <typename T>
-static MatT<T> to_mat(const salec_material& s)
-{
-    MatT<T> m;
-    memset(&m, 0, sizeof(m));
-    m.eos = s.eos; m.strength = s.strength;
-    m.rho0 = T(s.rho0); m.inv_rho0 = T(1.0 / s.rho0);
-    m.rho0sq_E0 = T(s.eos == SALEC_EOS_TILLOTSON ? s.rho0 * s.rho0 / s.E0 : 0.0);
-    m.A = T(s.A); m.B = T(s.B); m.E0 = T(s.E0); m.a = T(s.a); m.b = T(s.b); m.alpha = T(s.alpha);
-    m.beta = T(s.beta); m.Eiv = T(s.Eiv); m.Ecv = T(s.Ecv);
-    m.inv_dE = T((s.Ecv > s.Eiv) ? 1.0 / (s.Ecv - s.Eiv) : 0.0);
-    m.gamma = T(s.gamma);
-    m.Yi0 = T(s.Yi0); m.mui = T(s.mui); m.Yim = T(s.Yim); m.Yd0 = T(s.Yd0); m.mud = T(s.mud); m.Ydm = T(s.Ydm);
-    m.inv_Yspan = T((s.Yim != s.Yi0) ? 1.0 / (s.Yim - s.Yi0) : 0.0);
-    m.G = T(s.strength == SALEC_STRENGTH_COLLINS ? s.G : 0.0);
-    m.eps_fb = T(s.eps_fb); m.B_dam = T(s.B_dam); m.p_bd = T(s.p_bd); m.p_t = T(s.p_t);
-    m.c2_floor = T(s.eos == SALEC_EOS_TILLOTSON ? 0.01 * s.A / s.rho0 : 0.0);
-    m.rho_f = T(1e-12 * s.rho0); m.inv_rho_f = T(1.0 / (1e-12 * s.rho0));
-    return m;
-}
-
-template <typename T>
 static void fill_params(salec_ctx* ctx, ParamsT<T>& P)
 {
     typedef typename VT<T>::T2 T2;

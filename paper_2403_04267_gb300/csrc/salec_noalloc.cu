@@ -25,7 +25,7 @@ static __device__ __align__(256) double g_noalloc_minima[kNoAllocMaxBlocks];
 
 struct NoAllocControl {
     unsigned int counter;   // blocks finished; must be 0 when a launch starts
-    int pad;
+    int nan;                // a candidate was NaN; must be 0 when a launch starts
     double result;          // the time step of the last call
 };
 static __device__ __align__(256) NoAllocControl g_noalloc_control;
@@ -64,11 +64,14 @@ __global__ void __launch_bounds__(kThreads) k_courant_noalloc(NoAllocArgs A, dou
             const int nv = A.nr + 1;
             const double2 va = A.v[j * nv + i], vb = A.v[j * nv + i + 1];
             const double2 vc = A.v[(j + 1) * nv + i + 1], vd = A.v[(j + 1) * nv + i];
+            // the largest squared vertex speed by its bit pattern, as salec_step's first
+            // kernel takes it: a NaN velocity is carried into the candidate, not dropped
             double w = va.x * va.x + va.y * va.y;
-            w = fmax(w, vb.x * vb.x + vb.y * vb.y);
-            w = fmax(w, vc.x * vc.x + vc.y * vc.y);
-            w = fmax(w, vd.x * vd.x + vd.y * vd.y);
+            w = max_nonneg(w, vb.x * vb.x + vb.y * vb.y);
+            w = max_nonneg(w, vc.x * vc.x + vc.y * vc.y);
+            w = max_nonneg(w, vd.x * vd.x + vd.y * vd.y);
             cand = A.dx / (sqrt(w) + sqrt(c2m));
+            if (is_nan(cand)) atomicOr(&ctl->nan, 1);
         }
     }
     __shared__ double sh[kThreads / 32];
@@ -110,6 +113,8 @@ namespace {
 // Device addresses of the file-scope scratch, looked up once per device with that device
 // current.  In host code the names g_noalloc_minima / g_noalloc_control are host-side
 // stand-ins, not device addresses, so only these looked-up pointers go to the kernel.
+// A device reset (cudaDeviceReset) ends the context they belong to: the call must not be
+// used across one.
 struct DeviceScratch {
     bool ready = false;
     double* minima = nullptr;
@@ -146,6 +151,8 @@ extern "C" salec_status salec_courant_dt_noalloc(const salec_grid* grid, const s
     if (nbx * nby > kNoAllocMaxBlocks)
         return noalloc_fail(SALEC_EINVAL, "courant_dt_noalloc: grid larger than the fixed scratch "
                                           "(at most 65536 blocks of 32 x 8 cells, e.g. 4096 x 4096)");
+    if (nby > 65535)    // the launch's largest grid height
+        return noalloc_fail(SALEC_EINVAL, "courant_dt_noalloc: more than 65535 rows of 8-cell blocks (nz > 524280)");
     if (!mats || !fr || !I || !v || !dt_out)
         return noalloc_fail(SALEC_EINVAL, "courant_dt_noalloc: null argument");
     for (int m = 0; m < grid->nmat; ++m)
@@ -176,33 +183,28 @@ extern "C" salec_status salec_courant_dt_noalloc(const salec_grid* grid, const s
     A.dx = grid->dx; A.cfl = grid->cfl; A.growth = grid->dt_growth; A.dt_max = grid->dt_max; A.dt_prev = dt_prev;
     for (int m = 0; m < kMaxMat; ++m) {
         A.fr[m] = m < grid->nmat ? reinterpret_cast<const double2*>(fr[m]) : nullptr;
-        if (m < grid->nmat) {
-            const salec_material& s = mats[m];
-            Mat& M = A.mat[m];
-            M = Mat();
-            M.eos = s.eos; M.rho0 = s.rho0; M.inv_rho0 = 1.0 / s.rho0;
-            M.rho0sq_E0 = s.eos == SALEC_EOS_TILLOTSON ? s.rho0 * s.rho0 / s.E0 : 0.0; M.A = s.A; M.B = s.B; M.E0 = s.E0;
-            M.a = s.a; M.b = s.b; M.alpha = s.alpha; M.beta = s.beta; M.Eiv = s.Eiv; M.Ecv = s.Ecv;
-            M.inv_dE = (s.Ecv > s.Eiv) ? 1.0 / (s.Ecv - s.Eiv) : 0.0;
-            M.gamma = s.gamma;
-            M.c2_floor = s.eos == SALEC_EOS_TILLOTSON ? 0.01 * s.A / s.rho0 : 0.0;
-            M.rho_f = 1e-12 * s.rho0; M.inv_rho_f = 1.0 / (1e-12 * s.rho0);
-        }
+        A.mat[m] = m < grid->nmat ? to_mat<double>(mats[m]) : Mat();
     }
     A.I = I;
     A.D = D;
     A.v = reinterpret_cast<const double2*>(v);
     cudaStream_t st = static_cast<cudaStream_t>(stream);
-    // the counter must start at zero; the scratch keeps whatever the previous call left
-    e = cudaMemsetAsync(&sc.control->counter, 0, sizeof(unsigned int), st);
+    // the counter and the NaN flag must start at zero; the scratch keeps whatever the
+    // previous call left
+    e = cudaMemsetAsync(sc.control, 0, 2 * sizeof(unsigned int), st);
     if (e != cudaSuccess) return noalloc_fail(SALEC_ECUDA, cudaGetErrorString(e));
     k_courant_noalloc<<<dim3((unsigned)nbx, (unsigned)nby), dim3(kBlockX, kBlockY), 0, st>>>(A, sc.minima, sc.control);
     e = cudaGetLastError();
     if (e != cudaSuccess) return noalloc_fail(SALEC_ECUDA, cudaGetErrorString(e));
-    double out = 0.0;
-    e = cudaMemcpyAsync(&out, &sc.control->result, sizeof(double), cudaMemcpyDeviceToHost, st);
+    NoAllocControl out;
+    e = cudaMemcpyAsync(&out, sc.control, sizeof(NoAllocControl), cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) return noalloc_fail(SALEC_ECUDA, cudaGetErrorString(e));
-    *dt_out = out;
+    // the failures salec_step reports in its status word: a NaN speed (bit 2) and a step
+    // below dt_min (bit 4)
+    if (out.nan) return noalloc_fail(SALEC_EUNSTABLE, "courant_dt_noalloc: NaN in the Courant candidates");
+    if (out.result < grid->dt_min)
+        return noalloc_fail(SALEC_EUNSTABLE, "courant_dt_noalloc: time step below dt_min");
+    *dt_out = out.result;
     return SALEC_OK;
 }

@@ -6,7 +6,9 @@ pointers): it keeps its scratch in fixed file-scope device memory.  Here the fie
 running simulation are copied into plain torch device tensors (standing in for such a
 caller's buffers), the step size is computed from them with no allocation by the
 library, and compared with the step salec_step then takes from the same state, on two
-calls in a row (the scratch is shared and reused).  This file is collected last."""
+calls in a row (the scratch is shared and reused), also on a grid of exactly the largest
+size the scratch holds; a NaN velocity and a step below dt_min are reported as the
+failures salec_step's status word reports.  This file is collected last."""
 import numpy as np
 import pytest
 
@@ -61,3 +63,67 @@ def test_noalloc_rejects_grids_beyond_its_scratch():
         salec.courant_dt_noalloc(spec, [0], 0, 0, 1.0, 0)
     assert ei.value.status == salec.SALEC_EINVAL
     assert "fixed scratch" in str(ei.value)
+
+
+def test_noalloc_at_the_scratch_limit_matches_salec_step():
+    """4096 x 4096 cells: 65536 blocks of 32 x 8, every slot of the fixed scratch in the
+    last block's reduction."""
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    torch.cuda.set_device(0)
+    spec = W.scaled_plain(4096, radius_cells=100)
+    sim = salec.Sim(spec)
+    sim.step(3)
+    dt_prev = sim.scalars()["dt"]
+    fr, I, v = _fields(sim, 1)
+    torch.cuda.synchronize()
+    stream = torch.cuda.current_stream().cuda_stream
+    dt_free = salec.courant_dt_noalloc(spec, [t.data_ptr() for t in fr], I.data_ptr(), v.data_ptr(), dt_prev, stream)
+    sim.step(1)
+    dt_step = sim.scalars()["dt"]
+    assert abs(dt_free - dt_step) <= TOL * dt_step, (dt_free, dt_step)
+
+
+def test_noalloc_reports_nan_and_a_collapsed_step():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    torch.cuda.set_device(0)
+    spec = W.plain_fp64_100()
+    sim = salec.Sim(spec)
+    sim.step(5)
+    dt_prev = sim.scalars()["dt"]
+    fr, I, v = _fields(sim, 1)
+    stream = torch.cuda.current_stream().cuda_stream
+    ptrs = [t.data_ptr() for t in fr]
+    # a step below dt_min
+    tight = dict(spec, grid=dict(spec["grid"], dt_min=1.0))
+    with pytest.raises(salec.SalecError) as ei:
+        salec.courant_dt_noalloc(tight, ptrs, I.data_ptr(), v.data_ptr(), dt_prev, stream)
+    assert ei.value.status == salec.SALEC_EUNSTABLE and "dt_min" in str(ei.value)
+    # a NaN vertex velocity under the projectile: salec_step flags it in its status word
+    # (bit 2), the allocation-free call returns SALEC_EUNSTABLE
+    vr = sim.get("vr")
+    vr[70, 3] = np.nan
+    v[70, 3, 0] = float("nan")
+    torch.cuda.synchronize()
+    with pytest.raises(salec.SalecError) as ei:
+        salec.courant_dt_noalloc(spec, ptrs, I.data_ptr(), v.data_ptr(), dt_prev, stream)
+    assert ei.value.status == salec.SALEC_EUNSTABLE and "NaN" in str(ei.value)
+    sim.set("vr", vr)
+    sim.step(1)
+    assert sim.scalars()["status"] & 2
+    # the next call, on clean fields, succeeds: the flag does not outlive its call
+    fr, I, v = _fields(salec.Sim(spec), 1)
+    torch.cuda.synchronize()
+    assert salec.courant_dt_noalloc(spec, [t.data_ptr() for t in fr], I.data_ptr(), v.data_ptr(), 1.0, stream) > 0.0
+
+
+def test_noalloc_rejects_more_block_rows_than_a_launch_takes():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    spec = W.scaled_plain(100)
+    spec = dict(spec, grid=dict(spec["grid"], nr=32, nz=65536 * 8))
+    with pytest.raises(salec.SalecError) as ei:
+        salec.courant_dt_noalloc(spec, [0], 0, 0, 1.0, 0)
+    assert ei.value.status == salec.SALEC_EINVAL
+    assert "65535" in str(ei.value)
