@@ -163,6 +163,27 @@ salec_status salec_finalize(salec_ctx* ctx);
  * where capture is not possible); the results are those of plain launches. */
 salec_status salec_step(salec_ctx* ctx, int nsteps);
 
+/* How salec_step runs a cycle.
+ *   SALEC_STEP_FUSED   the Courant kernel, then one kernel over tiles of cells that stages
+ *                      each tile with a halo of three cells in shared memory and runs
+ *                      every phase of the cycle (Fig. 1a: EoS and viscosity, corner forces
+ *                      and v^L, energy / strength / volume partition, VOF remap, momentum
+ *                      remap, heat) on it, then the Courant rates of the new state for the
+ *                      next step.  The fields it rewrites are read from one copy and
+ *                      written to a second one inside the state buffer; read-outs bring
+ *                      the current copy back first.  It moves a quarter of the phase
+ *                      form's DRAM bytes per cell, but computes each tile's halo cells again.
+ *   SALEC_STEP_PHASES  six kernels over the whole grid and the Courant kernel, in place
+ *                      (block shapes from salec_set_block_shapes / salec_autotune).  The
+ *                      default of both precisions: on GB300 both forms are bound by
+ *                      instruction issue, and this one issues fewer instructions per cell.
+ * Both forms compute the same cycle with the same arithmetic per cell and vertex;
+ * salec_set_step_form returns SALEC_EINVAL for another value, SALEC_EORDER before
+ * salec_finalize. */
+enum { SALEC_STEP_PHASES = 0, SALEC_STEP_FUSED = 1 };
+salec_status salec_set_step_form(salec_ctx* ctx, int form);
+int salec_get_step_form(const salec_ctx* ctx);
+
 /* Synchronise and read the scalars: out[0] t, out[1] dt of the last step, out[2] step
  * count, out[3] status bits (1 non-positive volume/density, 2 NaN, 4 dt < dt_min),
  * out[4] mass out through the top, out[5] mass removed by clean-up, out[6] mass added by
@@ -197,19 +218,30 @@ salec_status salec_checkpoint_bytes(salec_ctx* ctx, size_t* bytes);
 salec_status salec_get_state(salec_ctx* ctx, void* host, size_t bytes);
 salec_status salec_set_state(salec_ctx* ctx, const void* host, size_t bytes);
 
-/* Number of kernel launches one step issues (for launch accounting): the six phases and
- * the one-thread Courant kernel between phases 0 and 1. */
+/* The caller wrote the first salec_checkpoint_bytes() bytes of the state buffer itself (a
+ * device-to-device copy of an earlier image, say) instead of through salec_set_state: the
+ * current fields are those at the start of the buffer, and the next fused step forms the
+ * Courant maximum of that state again.  SALEC_EORDER before salec_finalize. */
+salec_status salec_state_changed(salec_ctx* ctx);
+
+/* Number of kernel launches one step issues (for launch accounting): in the phase form
+ * the six phases and the one-thread Courant kernel between phases 0 and 1 (7); in the
+ * fused form the Courant kernel and the tile kernel (2; a sequence of fused steps that
+ * follows set-up, a host write or other steps adds one pass of Courant rates first). */
 int salec_launches_per_step(const salec_ctx* ctx);
 
 /* Per-kernel timing: with timing on, salec_step records a CUDA event before the first
- * and after every kernel of each step on the context's stream; salec_kernel_times
- * synchronises, returns in avg_ms[k] (k < 6, n >= 6) the mean duration of phase k over
- * the steps recorded since timing was switched on or last read (phase 0 includes the
- * Courant kernel), the number of steps in *steps, and restarts the count.
- * salec_kernel_name(k) names phase k. */
+ * and after every timed kernel of each step on the context's stream; salec_kernel_times
+ * synchronises, returns in avg_ms[k] (n >= 6; unused entries 0) the mean duration of
+ * kernel k over the steps recorded since timing was switched on or last read, the number
+ * of steps in *steps, and restarts the count.  Phase form: k < 6 are the phases (phase 0
+ * includes the Courant kernel); fused form: k = 0 is the Courant and tile kernels.
+ * salec_step_kernel_name(ctx, k) names entry k of the context's form ("" for an unused
+ * one); salec_kernel_name(k) names phase k of the phase form. */
 salec_status salec_set_kernel_timing(salec_ctx* ctx, int on);
 salec_status salec_kernel_times(salec_ctx* ctx, double* avg_ms, int n, int* steps);
 const char* salec_kernel_name(int k);
+const char* salec_step_kernel_name(const salec_ctx* ctx, int k);
 
 /* End time of a run (default: none).  salec_batch_run stops a run once t >= t_end; a
  * run at or past its end time, or whose status is not 0 (see salec_get_scalars), does

@@ -32,10 +32,15 @@ const dim3 kDefaultShape(32, 8);
 struct Layout {
     size_t es;   // bytes of one element of the form (8 FP64, 4 mixed); energies are always 8
     size_t scal, rR, rc, A_Z, invAZ, inv2rc, dr, idr, dz, idz, zc, A_R, V, invV, p0, rho_ref, I_ref, dB_c, dB_v, dR_c, dR_v;
-    size_t fr[kMaxMat], I, s01, s2d, pmax, v;
+    size_t pmax;
+    // the fields a step rewrites, contiguous from pp_begin to persist_end (the fused form
+    // reads one copy and writes the other: the second copy starts at pp_alt)
+    size_t fr[kMaxMat], I, s01, s2d, v;
     size_t pb_c, pb_psi2, pb_v, pr_c, pr_psi2, pr_v;
-    size_t persist_end;
+    size_t pp_begin, persist_end;
+    size_t pp_alt;
     size_t PM, pbphi, vL, mv, dK, kheat, frL[kMaxMat], VL, IL, sL01, sL2d, dMR, dMZ, partial, tmp;
+    size_t eosc[2];   // the fused form's equation-of-state cache, one per copy of the fields
     size_t total;
 };
 
@@ -76,11 +81,12 @@ Layout make_layout(const salec_grid& g, int precision)
     L.dB_v = take(cur, (nz + 1) * d);
     L.dR_c = take(cur, nr * d);
     L.dR_v = take(cur, (nr + 1) * d);
+    L.pmax = take(cur, nc * d);
+    L.pp_begin = cur;
     for (int m = 0; m < g.nmat; ++m) L.fr[m] = take(cur, nc * d2);
     L.I = take(cur, nc * e8);
     L.s01 = take(cur, nc * d2);
     L.s2d = take(cur, nc * d2);
-    L.pmax = take(cur, nc * d);
     L.v = take(cur, nv * d2);
     L.pb_c = take(cur, nr * pb * d2);
     L.pb_psi2 = take(cur, nr * pb * d);
@@ -89,6 +95,7 @@ Layout make_layout(const salec_grid& g, int precision)
     L.pr_psi2 = take(cur, pr * nz * d);
     L.pr_v = take(cur, pr * (nz + 1) * d4);
     L.persist_end = cur;
+    L.pp_alt = take(cur, L.persist_end - L.pp_begin);
     L.PM = take(cur, nc * d2);
     L.pbphi = take(cur, nc * d2);
     L.vL = take(cur, nv * d2);
@@ -102,6 +109,8 @@ Layout make_layout(const salec_grid& g, int precision)
     L.sL2d = take(cur, nc * d2);
     L.dMR = take(cur, (nr + 1) * nz * d);
     L.dMZ = take(cur, nr * (nz + 1) * d);
+    L.eosc[0] = take(cur, nc * d2);
+    L.eosc[1] = take(cur, nc * d2);
     size_t nb = 0;
     for (int k = 0; k < kNumShapes; ++k) {
         const size_t t = (size_t)tiles_of(g.nr, g.nz, 0, kShapes[k]);
@@ -162,6 +171,17 @@ struct salec_ctx {
     cudaGraphExec_t graph = nullptr;
     dim3 graph_shape[6];
     bool graph_ok = true;
+    // step form: SALEC_STEP_FUSED (Courant kernel + one tile kernel, ping-pong copies of the
+    // rewritten fields) or SALEC_STEP_PHASES (seven launches, in place)
+    int form = SALEC_STEP_PHASES;
+    int parity = 0;                       // 1: the current fields are in the second copy
+    bool rates_valid = false;             // the running Courant maximum holds the current state's rates
+    ParamsT<double> Pd_alt;               // the FP64 / mixed parameters reading the second copy
+    ParamsT<float> Pf_alt;
+    OutPtrsT<double> Od[2];               // where a fused step from copy k writes (the other copy)
+    OutPtrsT<float> Of[2];
+    cudaGraphExec_t fgraph[2] = {nullptr, nullptr};   // fused chunks starting from copy 0 / 1
+    bool fgraph_ok = true;
     // optional per-kernel timing: 7 events per recorded step
     bool timing = false;
     std::vector<cudaEvent_t> ev;
@@ -229,11 +249,64 @@ static void fill_params(salec_ctx* ctx, ParamsT<T>& P)
     p.mv = at<T>(ctx, L.mv); p.dK = at<T>(ctx, L.dK); p.kheat = at<T>(ctx, L.kheat);
     p.VL = at<T>(ctx, L.VL); p.IL = at<double>(ctx, L.IL); p.sL01 = at<T2>(ctx, L.sL01);
     p.sL2d = at<T2>(ctx, L.sL2d); p.dMR = at<T>(ctx, L.dMR); p.dMZ = at<T>(ctx, L.dMZ);
+    p.eosc = at<T2>(ctx, L.eosc[0]);
     p.partial = at<double>(ctx, L.partial);
     p.scal = at<DevScalars>(ctx, L.scal);
 }
 
 static bool mixed(const salec_ctx* ctx) { return ctx->precision == SALEC_FP32MIX; }
+
+// The same parameters with the rewritten fields read from the second copy, and the output
+// pointers of a fused step from copy 0 (writes copy 1) and from copy 1 (writes copy 0).
+template <typename T>
+static void fill_pingpong(salec_ctx* ctx, const ParamsT<T>& P0, ParamsT<T>& P1, OutPtrsT<T>* O)
+{
+    typedef typename VT<T>::T2 T2;
+    typedef typename VT<T>::T4 T4;
+    const Layout& L = ctx->L;
+    const size_t shift = L.pp_alt - L.pp_begin;
+    auto copy_at = [&](int k, size_t off) { return k == 0 ? off : off + shift; };
+    P1 = P0;
+    for (int m = 0; m < kMaxMat; ++m) P1.p.fr[m] = m < ctx->g.nmat ? at<T2>(ctx, copy_at(1, L.fr[m])) : nullptr;
+    P1.p.I = at<double>(ctx, copy_at(1, L.I));
+    P1.p.s01 = at<T2>(ctx, copy_at(1, L.s01)); P1.p.s2d = at<T2>(ctx, copy_at(1, L.s2d));
+    P1.p.v = at<T2>(ctx, copy_at(1, L.v));
+    P1.p.pb_c = at<T2>(ctx, copy_at(1, L.pb_c)); P1.p.pb_psi2 = at<T>(ctx, copy_at(1, L.pb_psi2));
+    P1.p.pb_v = at<T4>(ctx, copy_at(1, L.pb_v));
+    P1.p.pr_c = at<T2>(ctx, copy_at(1, L.pr_c)); P1.p.pr_psi2 = at<T>(ctx, copy_at(1, L.pr_psi2));
+    P1.p.pr_v = at<T4>(ctx, copy_at(1, L.pr_v));
+    P1.p.eosc = at<T2>(ctx, L.eosc[1]);
+    for (int k = 0; k < 2; ++k) {
+        const int w = 1 - k;      // a step from copy k writes copy 1 - k
+        OutPtrsT<T>& o = O[k];
+        memset(&o, 0, sizeof(o));
+        for (int m = 0; m < ctx->g.nmat; ++m) o.fr[m] = at<T2>(ctx, copy_at(w, L.fr[m]));
+        o.I = at<double>(ctx, copy_at(w, L.I));
+        o.s01 = at<T2>(ctx, copy_at(w, L.s01)); o.s2d = at<T2>(ctx, copy_at(w, L.s2d));
+        o.v = at<T2>(ctx, copy_at(w, L.v));
+        o.pb_c = at<T2>(ctx, copy_at(w, L.pb_c)); o.pb_psi2 = at<T>(ctx, copy_at(w, L.pb_psi2));
+        o.pb_v = at<T4>(ctx, copy_at(w, L.pb_v));
+        o.pr_c = at<T2>(ctx, copy_at(w, L.pr_c)); o.pr_psi2 = at<T>(ctx, copy_at(w, L.pr_psi2));
+        o.pr_v = at<T4>(ctx, copy_at(w, L.pr_v));
+        o.eosc = at<T2>(ctx, L.eosc[w]);
+    }
+}
+
+// Bring the current fields (and the equation-of-state cache that goes with them) into the
+// first copy, where every read-out, checkpoint, batch and the phase kernels find them, after
+// an odd number of fused steps: two device copies.
+static cudaError_t canonical(salec_ctx* ctx)
+{
+    if (ctx->parity == 0) return cudaSuccess;
+    const Layout& L = ctx->L;
+    cudaError_t e = cudaMemcpyAsync(ctx->base + L.pp_begin, ctx->base + L.pp_alt, L.persist_end - L.pp_begin,
+                                    cudaMemcpyDeviceToDevice, ctx->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(ctx->base + L.eosc[0], ctx->base + L.eosc[1], L.eosc[1] - L.eosc[0], cudaMemcpyDeviceToDevice,
+                            ctx->stream);
+    if (e == cudaSuccess) ctx->parity = 0;
+    return e;
+}
 
 // vertex positions, centre radii and vertical face areas from the cell sizes, summed
 // outward from the axis and up from the bottom
@@ -622,6 +695,17 @@ salec_status salec_finalize(salec_ctx* ctx)
     ctx->sE.clear(); ctx->sE.shrink_to_fit(); ctx->sPz.clear(); ctx->sPz.shrink_to_fit();
     ctx->sI.clear(); ctx->sI.shrink_to_fit(); ctx->sImix.clear(); ctx->sImix.shrink_to_fit();
     ctx->hydP.clear(); ctx->hydP.shrink_to_fit(); ctx->hydR.clear(); ctx->hydR.shrink_to_fit();
+    fill_pingpong<double>(ctx, ctx->Pd, ctx->Pd_alt, ctx->Od);
+    fill_pingpong<float>(ctx, ctx->Pf, ctx->Pf_alt, ctx->Of);
+    e = mixed(ctx) ? prepare_fused<float>(ctx->Pf) : prepare_fused<double>(ctx->Pd);
+    if (e != cudaSuccess) return cuda_check(ctx, e, "fused step set-up");
+    // the phase kernels by default: on GB300 both forms are bound by instruction issue,
+    // and the fused form's halo cells (computed by every tile that needs them) cost more
+    // than the intermediate traffic it saves (mixed form, 4000 x 4000: 1.05 against 0.89 ms
+    // per step; FP64 9.3 against 7.1 ms)
+    ctx->form = SALEC_STEP_PHASES;
+    ctx->parity = 0;
+    ctx->rates_valid = false;
     ctx->finalized = true;
     return SALEC_OK;
 }
@@ -629,30 +713,48 @@ salec_status salec_finalize(salec_ctx* ctx)
 constexpr int kGraphChunk = 16;
 
 // Capture kGraphChunk steps on a private stream (a graph can then be launched into any
-// stream, the legacy default stream included).  False, with no error left pending, when
-// capture is not possible.
-static bool capture_step_graph(salec_ctx* ctx)
+// stream, the legacy default stream included).  `launch(cs, k)` enqueues step k of the
+// chunk.  nullptr, with no error left pending, when capture is not possible.
+extern "C++" {
+template <typename F>
+static cudaGraphExec_t capture_chunk(F&& launch)
 {
-    if (ctx->graph) { cudaGraphExecDestroy(ctx->graph); ctx->graph = nullptr; }
     cudaStream_t cs;
-    if (cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) != cudaSuccess) { (void)cudaGetLastError(); return false; }
+    if (cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) != cudaSuccess) { (void)cudaGetLastError(); return nullptr; }
     cudaGraph_t g = nullptr;
+    cudaGraphExec_t x = nullptr;
     cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
-    for (int k = 0; k < kGraphChunk && e == cudaSuccess; ++k)
-        e = mixed(ctx) ? launch_step<float>(ctx->Pf, ctx->shape, cs, nullptr)
-                       : launch_step<double>(ctx->Pd, ctx->shape, cs, nullptr);
+    for (int k = 0; k < kGraphChunk && e == cudaSuccess; ++k) e = launch(cs, k);
     const cudaError_t e2 = cudaStreamEndCapture(cs, &g);
     if (e == cudaSuccess) e = e2;
-    if (e == cudaSuccess) e = cudaGraphInstantiate(&ctx->graph, g, 0);
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&x, g, 0);
     if (g) cudaGraphDestroy(g);
     cudaStreamDestroy(cs);
     if (e != cudaSuccess) {
         (void)cudaGetLastError();
-        ctx->graph = nullptr;
-        return false;
+        return nullptr;
     }
+    return x;
+}
+}  // extern "C++"
+
+static bool capture_step_graph(salec_ctx* ctx)
+{
+    if (ctx->graph) { cudaGraphExecDestroy(ctx->graph); ctx->graph = nullptr; }
+    ctx->graph = capture_chunk([&](cudaStream_t cs, int) {
+        return mixed(ctx) ? launch_step<float>(ctx->Pf, ctx->shape, cs, nullptr)
+                          : launch_step<double>(ctx->Pd, ctx->shape, cs, nullptr);
+    });
+    if (!ctx->graph) return false;
     for (int k = 0; k < 6; ++k) ctx->graph_shape[k] = ctx->shape[k];
     return true;
+}
+
+// one fused step from the current copy; the next step reads the other one
+static cudaError_t fused_step(salec_ctx* ctx, int parity, cudaStream_t s, cudaEvent_t* ev)
+{
+    return mixed(ctx) ? launch_step_fused<float>(parity ? ctx->Pf_alt : ctx->Pf, ctx->Of[parity], s, ev)
+                      : launch_step_fused<double>(parity ? ctx->Pd_alt : ctx->Pd, ctx->Od[parity], s, ev);
 }
 
 static bool same_shapes(const dim3* a, const dim3* b)
@@ -662,10 +764,65 @@ static bool same_shapes(const dim3* a, const dim3* b)
     return true;
 }
 
+// events per recorded step: one before the first kernel and one after each timed kernel
+static int timed_kernels(const salec_ctx* ctx) { return ctx->form == SALEC_STEP_FUSED ? 1 : launches_per_step(); }
+
+static salec_status step_fused(salec_ctx* ctx, int nsteps)
+{
+    if (nsteps == 0) return SALEC_OK;
+    // the running Courant maximum must hold the current state's rates: a fused step leaves
+    // them for the next one; anything else (set-up, host writes, phase or batched steps)
+    // needs one pass over the state first
+    if (!ctx->rates_valid) {
+        cudaError_t e = canonical(ctx);
+        if (e == cudaSuccess)
+            e = cudaMemsetAsync(ctx->base + ctx->L.scal + offsetof(DevScalars, maxbits), 0, sizeof(unsigned long long), ctx->stream);
+        if (e == cudaSuccess) e = mixed(ctx) ? launch_courant_rates<float>(ctx->Pf, ctx->stream)
+                                             : launch_courant_rates<double>(ctx->Pd, ctx->stream);
+        if (e != cudaSuccess) return cuda_check(ctx, e, "Courant rates");
+        ctx->rates_valid = true;
+    }
+    if (!ctx->timing && nsteps >= kGraphChunk && ctx->fgraph_ok) {
+        const int p0 = ctx->parity;
+        if (!ctx->fgraph[p0]) {
+            ctx->fgraph[p0] = capture_chunk([&](cudaStream_t cs, int k) { return fused_step(ctx, (p0 + k) & 1, cs, nullptr); });
+            if (!ctx->fgraph[p0]) ctx->fgraph_ok = false;
+        }
+        if (ctx->fgraph[p0]) {
+            // a chunk has an even number of steps: it ends on the copy it started from
+            for (; nsteps >= kGraphChunk; nsteps -= kGraphChunk) {
+                const cudaError_t e = cudaGraphLaunch(ctx->fgraph[p0], ctx->stream);
+                if (e != cudaSuccess) return cuda_check(ctx, e, "fused step graph launch");
+            }
+        }
+    }
+    for (int n = 0; n < nsteps; ++n) {
+        cudaEvent_t* evp = nullptr;
+        if (ctx->timing) {
+            while (ctx->ev_used + 2 > ctx->ev.size()) {
+                cudaEvent_t e0;
+                cudaError_t ce = cudaEventCreate(&e0);
+                if (ce != cudaSuccess) return cuda_check(ctx, ce, "event create");
+                ctx->ev.push_back(e0);
+            }
+            evp = ctx->ev.data() + ctx->ev_used;
+            ctx->ev_used += 2;
+        }
+        const cudaError_t e = fused_step(ctx, ctx->parity, ctx->stream, evp);
+        if (e != cudaSuccess) return cuda_check(ctx, e, "fused step launch");
+        ctx->parity ^= 1;
+    }
+    return SALEC_OK;
+}
+
 salec_status salec_step(salec_ctx* ctx, int nsteps)
 {
     if (!ctx || nsteps < 0) return SALEC_EINVAL;
     if (!ctx->finalized) return fail(ctx, SALEC_EORDER, "step before finalize");
+    if (ctx->form == SALEC_STEP_FUSED) return step_fused(ctx, nsteps);
+    cudaError_t ce = canonical(ctx);
+    if (ce != cudaSuccess) return cuda_check(ctx, ce, "canonical copy");
+    if (nsteps > 0) ctx->rates_valid = false;
     // whole chunks as graph replays (the kernel arguments are fixed after finalize; the
     // graph is captured again when the block shapes change)
     if (!ctx->timing && nsteps >= kGraphChunk && ctx->graph_ok) {
@@ -698,6 +855,21 @@ salec_status salec_step(salec_ctx* ctx, int nsteps)
     return SALEC_OK;
 }
 
+salec_status salec_set_step_form(salec_ctx* ctx, int form)
+{
+    if (!ctx || (form != SALEC_STEP_PHASES && form != SALEC_STEP_FUSED)) return SALEC_EINVAL;
+    if (!ctx->finalized) return fail(ctx, SALEC_EORDER, "set_step_form before finalize");
+    if (form == ctx->form) return SALEC_OK;
+    const cudaError_t e = canonical(ctx);
+    if (e != cudaSuccess) return cuda_check(ctx, e, "canonical copy");
+    ctx->form = form;
+    ctx->rates_valid = false;
+    ctx->ev_used = 0;
+    return SALEC_OK;
+}
+
+int salec_get_step_form(const salec_ctx* ctx) { return ctx ? ctx->form : -1; }
+
 salec_status salec_set_kernel_timing(salec_ctx* ctx, int on)
 {
     if (!ctx) return SALEC_EINVAL;
@@ -708,12 +880,13 @@ salec_status salec_set_kernel_timing(salec_ctx* ctx, int on)
 
 salec_status salec_kernel_times(salec_ctx* ctx, double* avg_ms, int n, int* steps)
 {
-    const int K = launches_per_step();
-    if (!ctx || !avg_ms || !steps || n < K) return SALEC_EINVAL;
+    if (!ctx || !avg_ms || !steps) return SALEC_EINVAL;
+    const int K = timed_kernels(ctx);
+    if (n < K) return SALEC_EINVAL;
     cudaError_t e = cudaStreamSynchronize(ctx->stream);
     if (e != cudaSuccess) return cuda_check(ctx, e, "kernel times");
     const size_t ns = ctx->ev_used / (K + 1);
-    for (int k = 0; k < K; ++k) avg_ms[k] = 0.0;
+    for (int k = 0; k < n; ++k) avg_ms[k] = 0.0;
     for (size_t s = 0; s < ns; ++s)
         for (int k = 0; k < K; ++k) {
             float ms = 0.0f;
@@ -729,6 +902,12 @@ salec_status salec_kernel_times(salec_ctx* ctx, double* avg_ms, int n, int* step
 
 const char* salec_kernel_name(int k)
 {
+    return kernel_name(k);
+}
+
+const char* salec_step_kernel_name(const salec_ctx* ctx, int k)
+{
+    if (ctx && ctx->form == SALEC_STEP_FUSED) return k == 0 ? "k_step_fused" : "";
     return kernel_name(k);
 }
 
@@ -829,10 +1008,21 @@ static long strip_index(const salec_ctx* ctx, const FieldLoc& F, int i, int j)
     }
 }
 
+// the current fields in the first copy before an accessor reads or writes them; a write also
+// invalidates the running Courant maximum
+static salec_status current_fields(salec_ctx* ctx, bool write)
+{
+    const cudaError_t e = canonical(ctx);
+    if (e != cudaSuccess) return cuda_check(ctx, e, "canonical copy");
+    if (write) ctx->rates_valid = false;
+    return SALEC_OK;
+}
+
 salec_status salec_get_field(salec_ctx* ctx, int field, double* host_out, size_t n)
 {
     if (!ctx || !host_out) return SALEC_EINVAL;
     if (!ctx->finalized) return fail(ctx, SALEC_EORDER, "get_field before finalize");
+    if (salec_status st = current_fields(ctx, false)) return st;
     const int nr = ctx->g.nr, nz = ctx->g.nz;
     const size_t nc = (size_t)nr * nz;
     if (field == SALEC_F_PRESSURE) {
@@ -872,6 +1062,7 @@ salec_status salec_set_field(salec_ctx* ctx, int field, const double* host_in, s
     if (!ctx || !host_in) return SALEC_EINVAL;
     if (!ctx->finalized) return fail(ctx, SALEC_EORDER, "set_field before finalize");
     if (field == SALEC_F_PRESSURE) return fail(ctx, SALEC_EINVAL, "pressure is read-only");
+    if (salec_status st = current_fields(ctx, true)) return st;
     const int nr = ctx->g.nr, nz = ctx->g.nz;
     FieldLoc F;
     if (!locate(ctx, field, F)) return fail(ctx, SALEC_EINVAL, "unknown field %d", field);
@@ -905,6 +1096,7 @@ salec_status salec_crater_profile(salec_ctx* ctx, double z_surface, int npts, do
 {
     if (!ctx || !depth || !diameter || npts < 0 || (npts > 0 && !depth_profile)) return SALEC_EINVAL;
     if (!ctx->finalized) return fail(ctx, SALEC_EORDER, "crater_profile before finalize");
+    if (salec_status st = current_fields(ctx, false)) return st;
     const int nr = ctx->g.nr;
     const std::vector<double>& rc = ctx->rc;
     std::vector<double> h(nr);
@@ -954,6 +1146,7 @@ salec_status salec_conservation(salec_ctx* ctx, double out[4])
 {
     if (!ctx || !out) return SALEC_EINVAL;
     if (!ctx->finalized) return fail(ctx, SALEC_EORDER, "conservation before finalize");
+    if (salec_status st = current_fields(ctx, false)) return st;
     double* part = at<double>(ctx, ctx->L.partial);
     int nb = 0;
     cudaError_t e = mixed(ctx) ? launch_conservation<float>(ctx->Pf, part, &nb, ctx->stream)
@@ -981,6 +1174,7 @@ salec_status salec_get_state(salec_ctx* ctx, void* host, size_t bytes)
     if (!ctx || !host) return SALEC_EINVAL;
     if (!ctx->finalized) return fail(ctx, SALEC_EORDER, "get_state before finalize");
     if (bytes != ctx->L.persist_end) return fail(ctx, SALEC_EINVAL, "checkpoint needs %zu bytes", ctx->L.persist_end);
+    if (salec_status st = current_fields(ctx, false)) return st;
     cudaError_t e = cudaMemcpyAsync(host, ctx->base, bytes, cudaMemcpyDeviceToHost, ctx->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
     return cuda_check(ctx, e, "get_state");
@@ -991,9 +1185,19 @@ salec_status salec_set_state(salec_ctx* ctx, const void* host, size_t bytes)
     if (!ctx || !host) return SALEC_EINVAL;
     if (!ctx->finalized) return fail(ctx, SALEC_EORDER, "set_state before finalize");
     if (bytes != ctx->L.persist_end) return fail(ctx, SALEC_EINVAL, "checkpoint needs %zu bytes", ctx->L.persist_end);
+    if (salec_status st = current_fields(ctx, true)) return st;
     cudaError_t e = cudaMemcpyAsync(ctx->base, host, bytes, cudaMemcpyHostToDevice, ctx->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
     return cuda_check(ctx, e, "set_state");
+}
+
+salec_status salec_state_changed(salec_ctx* ctx)
+{
+    if (!ctx) return SALEC_EINVAL;
+    if (!ctx->finalized) return fail(ctx, SALEC_EORDER, "state_changed before finalize");
+    ctx->parity = 0;
+    ctx->rates_valid = false;
+    return SALEC_OK;
 }
 
 salec_status salec_set_end_time(salec_ctx* ctx, double t_end)
@@ -1036,6 +1240,9 @@ salec_status salec_autotune(salec_ctx* ctx, int trial_steps, int* shapes_out)
 {
     if (!ctx || trial_steps < 1) return SALEC_EINVAL;
     if (!ctx->finalized) return fail(ctx, SALEC_EORDER, "autotune before finalize");
+    // the block shapes are those of the phase kernels: tune them in the phase form
+    const int form = ctx->form;
+    if (salec_status st = salec_set_step_form(ctx, SALEC_STEP_PHASES)) return st;
     const int K = launches_per_step();
     double best[6];
     dim3 pick[6];
@@ -1060,7 +1267,7 @@ salec_status salec_autotune(salec_ctx* ctx, int trial_steps, int* shapes_out)
     ctx->timing = was_timing;
     ctx->ev_used = 0;
     if (shapes_out) salec_get_block_shapes(ctx, shapes_out);
-    return SALEC_OK;
+    return salec_set_step_form(ctx, form);
 }
 
 // ---------------------------------------------------------------------------------
@@ -1171,6 +1378,8 @@ salec_status salec_batch_create(salec_ctx* const* runs, int nruns, void* dev_buf
 {
     salec_status st = batch_check(runs, nruns);
     if (st != SALEC_OK || !out) return st != SALEC_OK ? st : SALEC_EINVAL;
+    for (int r = 0; r < nruns; ++r)
+        if ((st = current_fields(runs[r], true)) != SALEC_OK) return st;
     salec_batch* b = new salec_batch();
     const size_t need = batch_layout(runs, nruns, b);
     if (!dev_buf || bytes < need || ((uintptr_t)dev_buf % kAlign) != 0) { delete b; return SALEC_ENOMEM; }
@@ -1217,10 +1426,20 @@ static cudaError_t batch_launch(salec_batch* b, cudaEvent_t* ev)
 
 static salec_status batch_restore_retired(salec_batch* b);
 
+// a run stepped alone in the fused form since the last batched step has its fields in the
+// second copy: bring them back (the batch's kernels work in place on the first)
+static salec_status batch_fields(salec_batch* b)
+{
+    for (salec_ctx* r : b->runs)
+        if (salec_status st = current_fields(r, true)) return bfail(b, st, r->err.c_str());
+    return SALEC_OK;
+}
+
 salec_status salec_batch_step(salec_batch* b, int nsteps)
 {
     if (!b || nsteps < 0) return SALEC_EINVAL;
-    const salec_status st0 = batch_restore_retired(b);
+    salec_status st0 = batch_fields(b);
+    if (st0 == SALEC_OK) st0 = batch_restore_retired(b);
     if (st0 != SALEC_OK) return st0;
     const int K = launches_per_step() + 1;
     for (int n = 0; n < nsteps; ++n) {
@@ -1311,7 +1530,8 @@ salec_status salec_batch_run(salec_batch* b, int chunk, long max_steps, long* st
     if (b->stream == nullptr || b->stream == cudaStreamLegacy || b->stream == cudaStreamPerThread)
         return bfail(b, SALEC_EINVAL, "batch_run captures a CUDA graph and needs a created stream, "
                                       "not a default stream");
-    salec_status st0 = batch_restore_retired(b);
+    salec_status st0 = batch_fields(b);
+    if (st0 == SALEC_OK) st0 = batch_restore_retired(b);
     if (st0 != SALEC_OK) return st0;
     if (b->graph && b->graph_steps != chunk) { cudaGraphExecDestroy(b->graph); b->graph = nullptr; }
     std::vector<double> poll((size_t)5 * n);
@@ -1403,7 +1623,7 @@ void salec_batch_destroy(salec_batch* b)
 
 int salec_launches_per_step(const salec_ctx* ctx)
 {
-    (void)ctx;
+    if (ctx && ctx->form == SALEC_STEP_FUSED) return 2;     // the Courant kernel and the tile kernel
     return kernels_per_step();
 }
 
@@ -1416,6 +1636,8 @@ void salec_destroy(salec_ctx* ctx)
 {
     if (!ctx) return;
     if (ctx->graph) cudaGraphExecDestroy(ctx->graph);
+    for (int k = 0; k < 2; ++k)
+        if (ctx->fgraph[k]) cudaGraphExecDestroy(ctx->fgraph[k]);
     for (cudaEvent_t e : ctx->ev) cudaEventDestroy(e);
     delete ctx;
 }

@@ -1,0 +1,1078 @@
+// salec_fused.cu -- the whole SALE cycle (Fig. 1a of the paper: Lagrangian step, then
+// Eulerian step) in one kernel per step.
+//
+// Each CTA owns a TW x TH tile of cells (and the vertices at their lower-left corners;
+// the last tile of a row or column also owns the vertices on the grid's far edge).  It
+// stages the state of the tile and a halo of H = 3 cells around it in shared memory and
+// runs the phases on regions that shrink by one cell or vertex per dependency:
+//   phase 0  EoS, tension cut-off, artificial viscosity   cells    [-3, T+3)
+//   phase 1  corner forces, PML psi1, v^L                  vertices [-2, T+3)
+//   phase 2  energy, volume partition, strength, psi2      cells    [-2, T+2)
+//   phase 3a donor-cell remap, clean-up, phi1/phi3         cells    [-1, T+1)
+//   phase 3b dual-grid momentum remap, phi2                vertices [ 0, T+1)
+//   phase 3c kinetic-energy deficit as heat                cells    [ 0, T)
+// and then forms, for its own cells, the Courant rate of the new state (Eq. 14): the next
+// step's time step comes from the running maximum over all tiles, which a one-thread
+// kernel turns into dt before the next step starts.  Halo cells are computed by every
+// tile that needs them, from the same inputs with the same arithmetic as the phase
+// kernels, so the tiles agree on them; only the owner writes a result.  Since a tile reads
+// its neighbours' cells, the fields the step rewrites (fractions and densities, energy,
+// stress and damage, velocities, PML auxiliaries) are read from one copy and written to
+// another (ping-pong); the peak over-pressure is read and written by its owner only and
+// stays in place.  Per step the grid's state is read once (plus the halo) and written
+// once; the phase kernels' intermediates (pressures, Lagrangian state, face fluxes,
+// vertex masses) never leave the SM.
+#include <cuda_runtime.h>
+
+#include "salec_device.cuh"
+
+namespace salec {
+
+namespace {
+
+constexpr size_t al16(size_t x) { return (x + 15) / 16 * 16; }
+
+// Shared-memory plan of a tile: arrays that live through the whole cycle, then the inputs
+// and phase-0 results (dead after phase 2), overlaid by the remap's results.
+template <typename T, int NM, bool STR, int TW, int TH>
+struct TileLayout {
+    typedef typename VT<T>::T2 T2;
+    static constexpr int H = 3;
+    static constexpr int CW = TW + 2 * H, CH = TH + 2 * H;   // cell frame
+    static constexpr int VW = CW + 1, VH = CH + 1;           // vertex frame
+    static constexpr int NC = CW * CH, NV = VW * VH;
+    static constexpr bool PBPHI = NM > 1 || STR;              // keep (p_bar, Phi) per cell
+    static constexpr size_t c2 = al16(NC * sizeof(T2)), c1 = al16(NC * sizeof(T)), cd = al16(NC * sizeof(double));
+    static constexpr size_t v2 = al16(NV * sizeof(T2)), v1 = al16(NV * sizeof(T));
+    // whole cycle
+    static constexpr size_t o_vL = 0;
+    static constexpr size_t o_mv = o_vL + v2;
+    static constexpr size_t o_dK = o_mv + v1;
+    static constexpr size_t o_frL = o_dK + v1;
+    static constexpr size_t o_VL = o_frL + NM * c2;
+    static constexpr size_t o_IL = o_VL + c1;
+    static constexpr size_t o_sL = o_IL + cd;
+    static constexpr size_t o_red = o_sL + (STR ? 2 * c2 : 0);
+    static constexpr size_t o_early = o_red + al16(32 * 5 * sizeof(double));
+    // inputs and phase 0
+    static constexpr size_t o_vo = o_early;
+    static constexpr size_t o_fro = o_vo + v2;
+    static constexpr size_t o_Io = o_fro + NM * c2;
+    static constexpr size_t o_PM = o_Io + cd;
+    static constexpr size_t o_pbphi = o_PM + c2;
+    static constexpr size_t o_so = o_pbphi + (PBPHI ? c2 : 0);
+    static constexpr size_t early_end = o_so + (STR ? 2 * c2 : 0);
+    // remap results, over the inputs
+    static constexpr size_t o_dMR = o_early;
+    static constexpr size_t o_dMZ = o_dMR + al16(VW * CH * sizeof(T));
+    static constexpr size_t o_frn = o_dMZ + al16(CW * VH * sizeof(T));
+    static constexpr size_t o_In = o_frn + NM * c2;
+    static constexpr size_t o_kheat = o_In + cd;
+    static constexpr size_t o_vn = o_kheat + v1;
+    static constexpr size_t o_Dn = o_vn + v2;
+    static constexpr size_t late_end = o_Dn + (STR ? c1 : 0);
+    static constexpr size_t bytes = early_end > late_end ? early_end : late_end;
+};
+
+// Tile shape, threads and minimum resident CTAs per SM of an instantiation: the mixed form
+// of one hydrodynamic material takes 32 x 32 cells (two CTAs of 105 KB per SM); the other
+// forms 32 x 16.
+template <typename T, int NM, bool STR>
+struct TileShape {
+    static constexpr bool big = sizeof(T) == 4 && NM == 1 && !STR;
+    static constexpr int TW = 32, TH = big ? 32 : 16, NT = 512;
+    // two CTAs per SM (64 registers a thread) where two plans fit the SM's 228 KB of
+    // shared memory in the mixed form; otherwise one (the FP64 form keeps 128 registers)
+    static constexpr size_t bytes = TileLayout<T, NM, STR, TW, TH>::bytes;
+    static constexpr int MINB = (sizeof(T) == 4 && 2 * (bytes + 1024) <= 228 * 1024) ? 2 : 1;
+};
+
+// What one donor moves through a face: its Lagrangian contents in proportion |dV| / V^L
+// (the phase-3a rule), read from the tile's shared memory.
+template <typename T, int NM, bool STR>
+struct TileDonor {
+    typedef typename VT<T>::T2 T2;
+    const T2* frL[NM];
+    const double* IL;
+    const T2* sL01;
+    const T2* sL2d;
+};
+
+template <typename T, int NM, bool STR>
+__device__ __forceinline__ void move_s(const TileDonor<T, NM, STR>& d, int donor, T adV, T sgn, double Iself, bool strip,
+                                       Acc<T, NM>& acc, T& mass_out, T& e_out)
+{
+    typedef typename VT<T>::T2 T2;
+    T vmat = T(0), mass = T(0);
+#pragma unroll
+    for (int m = 0; m < NM; ++m) {
+        const T2 fl = d.frL[m][donor];
+        const T dv = adV * fl.x;
+        const T dm = fl.y * dv;
+        acc.Vm[m] += sgn * dv;
+        acc.Mm[m] += sgn * dm;
+        vmat += dv;
+        mass += dm;
+    }
+    const double Id = d.IL[donor];
+    if (pos(sgn)) acc.dI += T(Id - Iself) * mass;
+    if (STR) {
+        const T2 a = d.sL01[donor], b = d.sL2d[donor];
+        acc.S[0] += sgn * (a.x * vmat);
+        acc.S[1] += sgn * (a.y * vmat);
+        acc.S[2] += sgn * (b.x * vmat);
+        acc.S[3] += sgn * (b.y * vmat);
+    }
+    mass_out = mass;
+    e_out = strip ? T(Id) * mass : T(0);
+}
+
+// Asynchronous copy of N bytes (4, 8 or 16) from global to shared memory without a round
+// trip through registers (so every load of the frame is in flight at once); with
+// valid == false the destination is zero-filled and nothing is read (src must still be a
+// valid address).  Completed by cp_async_wait() before the barrier that publishes them.
+template <int N>
+__device__ __forceinline__ void cp_async(void* dst, const void* src, bool valid)
+{
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+    const int sz = valid ? N : 0;
+    asm volatile("cp.async.ca.shared.global [%0], [%1], %2, %3;\n" ::"r"(d), "l"(src), "n"(N), "r"(sz) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+
+// store the upper or lower pair of a strip vertex's four auxiliaries (phi2 r, z | psi1 r, z)
+template <typename T4, typename T2>
+__device__ __forceinline__ void store_pair(T4* a, int half, T2 v) { reinterpret_cast<T2*>(a)[half] = v; }
+
+}  // namespace
+
+template <typename T, int NM, bool STR, bool UNI, int TW, int TH, int NT, int MINB>
+__global__ void __launch_bounds__(NT, MINB) k_step_fused(const ParamsT<T> P, const OutPtrsT<T> O)
+{
+    typedef VT<T> V;
+    typedef typename V::T2 T2;
+    typedef typename V::T4 T4;
+    typedef Geo<T, UNI> GE;
+    typedef TileLayout<T, NM, STR, TW, TH> L;
+    constexpr int H = L::H, CW = L::CW, CH = L::CH, VW = L::VW, NC = L::NC, NV = L::NV;
+    constexpr bool PBPHI = L::PBPHI;
+    extern __shared__ __align__(16) unsigned char smem[];
+    T2* s_vL = reinterpret_cast<T2*>(smem + L::o_vL);
+    T* s_mv = reinterpret_cast<T*>(smem + L::o_mv);
+    T* s_dK = reinterpret_cast<T*>(smem + L::o_dK);
+    T2* s_frL[NM];
+    T2* s_fro[NM];
+    T2* s_frn[NM];
+#pragma unroll
+    for (int m = 0; m < NM; ++m) {
+        s_frL[m] = reinterpret_cast<T2*>(smem + L::o_frL + m * L::c2);
+        s_fro[m] = reinterpret_cast<T2*>(smem + L::o_fro + m * L::c2);
+        s_frn[m] = reinterpret_cast<T2*>(smem + L::o_frn + m * L::c2);
+    }
+    T* s_VL = reinterpret_cast<T*>(smem + L::o_VL);
+    double* s_IL = reinterpret_cast<double*>(smem + L::o_IL);
+    T2* s_sL01 = reinterpret_cast<T2*>(smem + L::o_sL);
+    T2* s_sL2d = reinterpret_cast<T2*>(smem + L::o_sL + L::c2);
+    double* s_red = reinterpret_cast<double*>(smem + L::o_red);
+    T2* s_vo = reinterpret_cast<T2*>(smem + L::o_vo);
+    double* s_Io = reinterpret_cast<double*>(smem + L::o_Io);
+    T2* s_PM = reinterpret_cast<T2*>(smem + L::o_PM);
+    T2* s_pbphi = reinterpret_cast<T2*>(smem + L::o_pbphi);
+    T2* s_so01 = reinterpret_cast<T2*>(smem + L::o_so);
+    T2* s_so2d = reinterpret_cast<T2*>(smem + L::o_so + L::c2);
+    T* s_dMR = reinterpret_cast<T*>(smem + L::o_dMR);
+    T* s_dMZ = reinterpret_cast<T*>(smem + L::o_dMZ);
+    double* s_In = reinterpret_cast<double*>(smem + L::o_In);
+    T* s_kheat = reinterpret_cast<T*>(smem + L::o_kheat);
+    T2* s_vn = reinterpret_cast<T2*>(smem + L::o_vn);
+    T* s_Dn = reinterpret_cast<T*>(smem + L::o_Dn);
+
+    const T zero = T(0), one = T(1), half = T(0.5), two = T(2);
+    const PtrsT<T>& p = P.p;
+    const int nr = P.nr, nz = P.nz, nv = nr + 1;
+    const int tid = threadIdx.x;
+    const int ox = blockIdx.x * TW, oy = blockIdx.y * TH;
+    const int x0 = ox - H, y0 = oy - H;            // grid indices of frame position 0
+    const bool last_x = blockIdx.x == gridDim.x - 1, last_y = blockIdx.y == gridDim.y - 1;
+    const T dt = step_dt<T>(p.scal);
+    double t_out = 0.0, t_disc = 0.0, t_pml = 0.0, t_zmom = 0.0;
+
+    // ---- stage the state of the frame (cells and vertices outside the grid read as empty):
+    // asynchronous copies, all in flight together
+    for (int k = tid; k < NV; k += NT) {
+        const int i = x0 + k % VW, j = y0 + k / VW;
+        const bool in = i >= 0 && i <= nr && j >= 0 && j <= nz;
+        cp_async<sizeof(T2)>(&s_vo[k], in ? &p.v[j * nv + i] : p.v, in);
+    }
+    for (int k = tid; k < NC; k += NT) {
+        const int i = x0 + k % CW, j = y0 + k / CW;
+        const bool in = i >= 0 && i < nr && j >= 0 && j < nz;
+        const int c = in ? j * nr + i : 0;
+#pragma unroll
+        for (int m = 0; m < NM; ++m) cp_async<sizeof(T2)>(&s_fro[m][k], &p.fr[m][c], in);
+        cp_async<8>(&s_Io[k], &p.I[c], in);
+        cp_async<sizeof(T2)>(&s_PM[k], &p.eosc[c], in);
+        if (STR) {
+            cp_async<sizeof(T2)>(&s_so01[k], &p.s01[c], in);
+            cp_async<sizeof(T2)>(&s_so2d[k], &p.s2d[c], in);
+        }
+    }
+    cp_async_wait();
+    __syncthreads();
+
+    // ---- phase 0: artificial viscosity and total pressure from the equation of state of
+    // the current state, which the previous step (or the Courant-rate pass) left in the
+    // cache: (p_m, c^2) for one material, (p_hat, max c_m^2) for several; peak over-pressure
+    // (owner)
+    for (int k = tid; k < NC; k += NT) {
+        const int lx = k % CW, ly = k / CW, i = x0 + lx, j = y0 + ly;
+        if (i < 0 || i >= nr || j < 0 || j >= nz) {
+            s_PM[k] = V::mk(zero, zero);
+            if (PBPHI) s_pbphi[k] = V::mk(zero, zero);
+            continue;
+        }
+        const T2 ec = s_PM[k];
+        T phat = zero, phi = zero, mass = zero, r1 = zero;
+#pragma unroll
+        for (int m = 0; m < NM; ++m) {
+            const T2 fr = s_fro[m][k];
+            if (pos(fr.x)) {
+                if (NM == 1) phat += fr.x * ec.x;
+                phi += fr.x;
+                mass += fr.x * fr.y;
+                r1 = fr.y;
+            }
+        }
+        if (NM > 1) phat = ec.x;
+        const T c2m = ec.y, p1 = ec.x;
+        T Pc = zero, pbar = zero;
+        if (pos(phi)) {
+            const T2 va = s_vo[ly * VW + lx], vb = s_vo[ly * VW + lx + 1];
+            const T2 vc = s_vo[(ly + 1) * VW + lx + 1], vd = s_vo[(ly + 1) * VW + lx];
+            const T uL = half * (va.x + vd.x), uR = half * (vb.x + vc.x);
+            const T uB = half * (va.y + vb.y), uT = half * (vd.y + vc.y);
+            const T div = (GE::flux_r(P, i, j, uL, uR) + p.A_Z[i] * (uT - uB)) * GE::ivol(P, i, j);
+            const T cs = t_sqrt<T>(c2m);
+            const T iphi = NM == 1 ? one : one / phi;
+            pbar = NM == 1 ? p1 : phat * iphi;
+            T q = zero;
+            if (neg(div)) {
+                const T rb = NM == 1 ? r1 : mass * iphi;
+                const T Lc = GE::len(P, i, j);
+                q = rb * (P.cq * (UNI ? P.dx2 : Lc * Lc) * div * div - P.cl * Lc * cs * div);
+            }
+            Pc = phat + phi * q;
+            if (i >= ox && i < ox + TW && j >= oy && j < oy + TH) {
+                const int c = j * nr + i;
+                const T over = pbar - p.p0[j];
+                if (over > p.pmax[c]) p.pmax[c] = over;
+            }
+        }
+        s_PM[k] = V::mk(Pc, mass * GE::vol(P, i, j));
+        if (PBPHI) s_pbphi[k] = V::mk(pbar, phi);
+    }
+    __syncthreads();
+
+    // ---- phase 1: corner forces, gravity, PML psi1, Lagrangian velocity, BCs
+    constexpr int R1 = CW - 1;
+    for (int k = tid; k < R1 * (CH - 1); k += NT) {
+        const int lx = 1 + k % R1, ly = 1 + k / R1, i = x0 + lx, j = y0 + ly;
+        const int kv = ly * VW + lx;
+        if (i < 0 || i > nr || j < 0 || j > nz) {
+            s_vL[kv] = V::mk(zero, zero);
+            s_mv[kv] = zero;
+            s_dK[kv] = zero;
+            continue;
+        }
+        const bool own = i >= ox && (i < ox + TW || (last_x && i <= nr)) && j >= oy && (j < oy + TH || (last_y && j <= nz));
+        const int v = j * nv + i;
+        T Pc[4] = {zero, zero, zero, zero}, Pp[4] = {zero, zero, zero, zero};
+        T devr_rad = zero, devz_rad = zero, devr_ver = zero, devz_ver = zero, mass = zero;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int ci = (q == 0 || q == 3) ? i - 1 : i;
+            const int cj = (q < 2) ? j - 1 : j;
+            if (ci < 0 || ci >= nr || cj < 0 || cj >= nz) continue;
+            const int kc = (cj - y0) * CW + (ci - x0);
+            const T2 pm = s_PM[kc];
+            Pc[q] = pm.x;
+            mass += T(0.25) * pm.y;
+            if (STR || P.pr > 0 || P.pb > 0) {
+                T phi;
+                if (PBPHI) {
+                    phi = s_pbphi[kc].y;
+                } else {
+                    const T f = s_fro[0][kc].x;
+                    phi = pos(f) ? f : zero;
+                }
+                Pp[q] = pm.x - phi * p.p0[cj];
+                if (STR) {
+                    const T2 s01 = s_so01[kc];
+                    const T srz = s_so2d[kc].x;
+                    const T Srr = phi * s01.x, Szz = phi * s01.y, Srz = phi * srz;
+                    const T Stt = -(Srr + Szz);
+                    const T hr = GE::half_v_dr(P, ci, cj), hz = half * p.A_Z[ci];
+                    const T hoop = GE::quarter_v_rc(P, ci, cj);
+                    const T sr = (q == 2 || q == 1) ? one : -one;
+                    const T sz = (q == 2 || q == 3) ? one : -one;
+                    devr_rad += sr * hr * Srr - hoop * Stt;
+                    devz_rad += sr * hr * Srz;
+                    devr_ver += sz * hz * Srz;
+                    devz_ver += sz * hz * Szz;
+                }
+            }
+        }
+        const T ARb = UNI ? p.A_R[i] : (j > 0 ? GE::area_r(P, i, j - 1) : zero);
+        const T ARt = UNI ? ARb : (j < nz ? GE::area_r(P, i, j) : zero);
+        const T AZl = i > 0 ? p.A_Z[i - 1] : zero, AZr = i < nr ? p.A_Z[i] : zero;
+        const T Fr = (UNI ? half * ARb * (((Pc[0] + Pc[3]) - Pc[1]) - Pc[2])
+                          : half * (ARb * (Pc[0] - Pc[1]) + ARt * (Pc[3] - Pc[2]))) + (devr_rad + devr_ver);
+        const T Fz = half * (AZl * (Pc[0] - Pc[3]) + AZr * (Pc[1] - Pc[2])) + (devz_rad + devz_ver);
+        T psr = zero, psz = zero;
+        if (j < P.pb) {
+            const T d = p.dB_v[j];
+            T4 a = p.pb_v[v];
+            const T Tr = (UNI ? half * ARb * (((Pp[0] + Pp[3]) - Pp[1]) - Pp[2])
+                              : half * (ARb * (Pp[0] - Pp[1]) + ARt * (Pp[3] - Pp[2]))) + devr_rad;
+            const T rl = one - P.alpha_b * dt;
+            a.z = a.z * rl - dt * d * Tr;
+            a.w = a.w * rl - dt * d * devz_rad;
+            if (own) store_pair(&O.pb_v[v], 1, V::mk(a.z, a.w));
+            psr += a.z; psz += a.w;
+        }
+        if (i > nr - P.pr) {
+            const int kk = j * P.pr + (i - (nr - P.pr + 1));
+            const T d = strip_row_v(p, j, nz) ? p.dR_v[i] : zero;
+            T4 a = p.pr_v[kk];
+            const T Tz = half * (AZl * (Pp[0] - Pp[3]) + AZr * (Pp[1] - Pp[2])) + devz_ver;
+            const T rl = one - P.alpha_r * dt;
+            a.z = a.z * rl - dt * d * devr_ver;
+            a.w = a.w * rl - dt * d * Tz;
+            if (own) store_pair(&O.pr_v[kk], 1, V::mk(a.z, a.w));
+            psr += a.z; psz += a.w;
+        }
+        const T2 vo = s_vo[kv];
+        T vr = zero, vz = zero;
+        if (pos(mass)) {
+            // no net force and no gravity: v^L = v (the same value the update would give,
+            // up to the sign of a zero) without the reciprocal
+            const T fr_ = Fr - psr, fz_ = Fz - psz;
+            const bool acc = nonzero(fr_) || nonzero(fz_) || nonzero(P.g);
+            if (warp_any(acc) && acc) {
+                const T im = one / mass;
+                vr = vo.x + dt * (fr_ * im);
+                vz = vo.y + dt * (fz_ * im - P.g);
+            } else {
+                vr = vo.x;
+                vz = vo.y;
+            }
+        }
+        if (i == 0 || i == nr) vr = zero;
+        if (j == 0) {
+            vz = zero;
+            if (P.bc_bottom == SALEC_BOTTOM_NOSLIP) vr = zero;
+        }
+        if (j == nz && P.bc_top == SALEC_TOP_WALL) vz = zero;
+        s_vL[kv] = V::mk(vr, vz);
+        s_mv[kv] = mass;
+        const T dvr = vr - vo.x, dvz = vz - vo.y;
+        s_dK[kv] = half * mass * (dvr * dvr + dvz * dvz);
+    }
+    __syncthreads();
+
+    // ---- phase 2: Lagrangian cell update from v^L
+    constexpr int R2 = CW - 2;
+    for (int k = tid; k < R2 * (CH - 2); k += NT) {
+        const int lx = 1 + k % R2, ly = 1 + k / R2, i = x0 + lx, j = y0 + ly;
+        const int kc = ly * CW + lx;
+        if (i < 0 || i >= nr || j < 0 || j >= nz) continue;
+        const int c = j * nr + i;
+        const bool own = i >= ox && i < ox + TW && j >= oy && j < oy + TH;
+        T phi;
+        if (PBPHI) {
+            phi = s_pbphi[kc].y;
+        } else {
+            const T f = s_fro[0][kc].x;
+            phi = pos(f) ? f : zero;
+        }
+        if (!pos(phi)) {
+#pragma unroll
+            for (int m = 0; m < NM; ++m) s_frL[m][kc] = V::mk(zero, zero);
+            s_VL[kc] = GE::vol(P, i, j);
+            s_IL[kc] = 0.0;
+            if (STR) { s_sL01[kc] = V::mk(zero, zero); s_sL2d[kc] = V::mk(zero, zero); }
+            // an empty cell's psi2 is carried over unchanged
+            if (own && j < P.pb) O.pb_psi2[c] = p.pb_psi2[c];
+            if (own && i >= nr - P.pr) {
+                const int kk = j * P.pr + (i - (nr - P.pr));
+                O.pr_psi2[kk] = p.pr_psi2[kk];
+            }
+            continue;
+        }
+        const T2 va = s_vL[ly * VW + lx], vb = s_vL[ly * VW + lx + 1];
+        const T2 vc = s_vL[(ly + 1) * VW + lx + 1], vd = s_vL[(ly + 1) * VW + lx];
+        const T uL = half * (va.x + vd.x), uR = half * (vb.x + vc.x);
+        const T uB = half * (va.y + vb.y), uT = half * (vd.y + vc.y);
+        const T idr = GE::idr(P, i), idz = GE::idz(P, j);
+        const T err = (uR - uL) * idr;
+        const T ezz = (uT - uB) * idz;
+        const T Vc = GE::vol(P, i, j);
+        const T ett = (uR + uL) * p.inv2rc[i];
+        const T rad_flux = GE::flux_r(P, i, j, uL, uR);
+        const T ver_flux = p.A_Z[i] * (uT - uB);
+        const T dV = dt * (rad_flux + ver_flux);
+        const T VLc = Vc + dV;
+        const T2 pm = s_PM[kc];
+        const T Pc = pm.x, M = pm.y;
+        T work = zero, Pi_rad = -Pc * rad_flux, Pi_ver = -Pc * ver_flux;
+        T dvr_dz = zero, dvz_dr = zero, srr = zero, szz = zero, srz = zero, D = zero;
+        if (STR) {
+            const T2 s01 = s_so01[kc], s2d = s_so2d[kc];
+            srr = s01.x; szz = s01.y; srz = s2d.x; D = s2d.y;
+            dvr_dz = half * ((vd.x + vc.x) - (va.x + vb.x)) * idz;
+            dvz_dr = half * ((vb.y + vc.y) - (va.y + vd.y)) * idr;
+            const T Srr = phi * srr, Szz = phi * szz, Srz = phi * srz, Stt = -(Srr + Szz);
+            const T erz = half * (dvr_dz + dvz_dr);
+            work = dt * Vc * (Srr * err + Szz * ezz + Stt * ett + two * Srz * erz);
+            Pi_rad += Vc * (Srr * err + Stt * ett + Srz * dvz_dr);
+            Pi_ver += Vc * (Szz * ezz + Srz * dvr_dz);
+        }
+        T psi2 = zero;
+        if (j < P.pb) {
+            T a = p.pb_psi2[c];
+            a = a * (one - P.alpha_b * dt) - dt * p.dB_c[j] * Pi_rad;
+            if (own) O.pb_psi2[c] = a;
+            psi2 += a;
+        }
+        if (i >= nr - P.pr) {
+            const int kk = j * P.pr + (i - (nr - P.pr));
+            T a = p.pr_psi2[kk];
+            a = a * (one - P.alpha_r * dt) - dt * (strip_row_c(p, j) ? p.dR_c[i] : zero) * Pi_ver;
+            if (own) O.pr_psi2[kk] = a;
+            psi2 += a;
+        }
+        const T dE = -Pc * dV + work - dt * psi2;
+        const double Ic = s_Io[kc];
+        const bool add_dE = pos(M) && nonzero(dE);
+        double ILnew = Ic;
+        if (warp_any(add_dE) && add_dE) ILnew = Ic + double(dE / M);
+        s_IL[kc] = ILnew;
+        s_VL[kc] = VLc;
+        const T dVmat = phi * dV;
+        bool bad = false;
+        T G = zero, Y = zero, iepsf = zero;
+#pragma unroll
+        for (int m = 0; m < NM; ++m) {
+            const T2 fr = s_fro[m][kc];
+            if (pos(fr.x)) {
+                const T Vm = fr.x * Vc;
+                const T VmL = NM == 1 ? Vm + dVmat : Vm + fr.x / phi * dVmat;
+                bad |= !pos(VmL);
+                // unchanged volume: V_m / V_m^L is exactly 1 (no division)
+                s_frL[m][kc] = V::mk(VmL / VLc, warp_any(nonzero(dV)) ? fr.y * (Vm / VmL) : fr.y);
+                if (STR && P.mat[m].strength == SALEC_STRENGTH_COLLINS) {
+                    const MatT<T>& mm = P.mat[m];
+                    const T pb = s_pbphi[kc].x;
+                    G += fr.x * mm.G;
+                    Y += fr.x * yield_eval<T>(mm, pb, D, T(Ic), fr.y);
+                    T ef = mm.B_dam * (pb - mm.p_bd);
+                    ef = ef < mm.eps_fb ? mm.eps_fb : ef;
+                    iepsf += fr.x / ef;
+                }
+            } else {
+                s_frL[m][kc] = V::mk(zero, zero);
+            }
+        }
+        if (bad) atomicOr(&p.scal->status, 1);
+        if (STR) {
+            const T iphi = one / phi;
+            G *= iphi; Y *= iphi; iepsf *= iphi;
+            if (pos(G)) {
+                const T omega = half * (dvr_dz - dvz_dr);
+                const T erz = half * (dvr_dz + dvz_dr);
+                const T tr3 = (err + ezz + ett) * (one / T(3));
+                const T G2 = two * G;
+                T nrr = srr + dt * (G2 * (err - tr3) + two * omega * srz);
+                T nzz = szz + dt * (G2 * (ezz - tr3) - two * omega * srz);
+                T nrz = srz + dt * (G2 * erz + omega * (szz - srr));
+                const T ntt = -(nrr + nzz);
+                const T J2 = half * (nrr * nrr + nzz * nzz + ntt * ntt) + nrz * nrz;
+                if (J2 > Y * Y) {
+                    const T sq = t_sqrt<T>(J2);
+                    const T kq = Y / sq;
+                    nrr *= kq; nzz *= kq; nrz *= kq;
+                    D += (sq - Y) / (T(1.7320508075688772) * G) * iepsf;
+                    D = D > one ? one : D;
+                }
+                srr = nrr; szz = nzz; srz = nrz;
+            } else {
+                srr = zero; szz = zero; srz = zero;
+            }
+            s_sL01[kc] = V::mk(srr, szz);
+            s_sL2d[kc] = V::mk(srz, D);
+        }
+    }
+    __syncthreads();
+
+    // ---- phase 3a: donor-cell remap of the cells; face mass fluxes into shared memory
+    {
+        TileDonor<T, NM, STR> dn;
+#pragma unroll
+        for (int m = 0; m < NM; ++m) dn.frL[m] = s_frL[m];
+        dn.IL = s_IL;
+        dn.sL01 = s_sL01;
+        dn.sL2d = s_sL2d;
+        constexpr int R3 = CW - 4;
+        for (int k = tid; k < R3 * (CH - 4); k += NT) {
+            const int lx = 2 + k % R3, ly = 2 + k / R3, i = x0 + lx, j = y0 + ly;
+            if (i < 0 || i >= nr || j < 0 || j >= nz) continue;
+            const int kc = ly * CW + lx, c = j * nr + i;
+            const bool own = i >= ox && i < ox + TW && j >= oy && j < oy + TH;
+            Acc<T, NM> acc;
+            const T VLc = s_VL[kc];
+            const double ILc = s_IL[kc];
+#pragma unroll
+            for (int m = 0; m < NM; ++m) { acc.Vm[m] = zero; acc.Mm[m] = zero; }
+            acc.dI = zero;
+            acc.S[0] = acc.S[1] = acc.S[2] = acc.S[3] = zero;
+            const bool strip = j < P.pb || i >= nr - P.pr;
+            T FRm = zero, FRe = zero, FZm = zero, FZe = zero;
+            T fm, fe;
+            // left face r_i: positive dV flows from (i-1,j) into this cell
+            {
+                T dV = zero;
+                if (i != 0 && i != nr) {
+                    const T u = T(0.5) * (s_vL[ly * VW + lx].x + s_vL[(ly + 1) * VW + lx].x);
+                    dV = dt * GE::area_r(P, i, j) * u;
+                }
+                T sm = zero;
+                if (!warp_any(nonzero(dV))) {
+                } else if (pos(dV)) { move_s<T, NM, STR>(dn, kc - 1, dV, one, ILc, strip, acc, fm, fe); sm = fm; FRm -= fm; FRe -= fe; }
+                else if (neg(dV)) { move_s<T, NM, STR>(dn, kc, -dV, -one, ILc, strip, acc, fm, fe); sm = -fm; FRm += fm; FRe += fe; }
+                s_dMR[ly * VW + lx] = sm;
+            }
+            // right face r_{i+1}
+            {
+                T dV = zero;
+                if (i + 1 != nr) {
+                    const T u = T(0.5) * (s_vL[ly * VW + lx + 1].x + s_vL[(ly + 1) * VW + lx + 1].x);
+                    dV = dt * GE::area_r(P, i + 1, j) * u;
+                }
+                T sm = zero;
+                if (!warp_any(nonzero(dV))) {
+                } else if (pos(dV)) { move_s<T, NM, STR>(dn, kc, dV, -one, ILc, strip, acc, fm, fe); FRm += fm; FRe += fe; sm = fm; }
+                else if (neg(dV)) { move_s<T, NM, STR>(dn, kc + 1, -dV, one, ILc, strip, acc, fm, fe); FRm -= fm; FRe -= fe; sm = -fm; }
+                // the region's last column also records its right faces (the vertex remap
+                // reads them); the grid's right wall carries nothing
+                if (i == nr - 1) s_dMR[ly * VW + lx + 1] = zero;
+                else if (lx == CW - 3) s_dMR[ly * VW + lx + 1] = sm;
+            }
+            // bottom face z_j
+            {
+                T dV = zero;
+                if (j != 0 && !(j == nz && P.bc_top == SALEC_TOP_WALL)) {
+                    const T u = T(0.5) * (s_vL[ly * VW + lx].y + s_vL[ly * VW + lx + 1].y);
+                    dV = dt * p.A_Z[i] * u;
+                }
+                T sm = zero;
+                if (!warp_any(nonzero(dV))) {
+                } else if (pos(dV)) { move_s<T, NM, STR>(dn, kc - CW, dV, one, ILc, strip, acc, fm, fe); sm = fm; FZm -= fm; FZe -= fe; }
+                else if (neg(dV)) { move_s<T, NM, STR>(dn, kc, -dV, -one, ILc, strip, acc, fm, fe); sm = -fm; FZm += fm; FZe += fe; }
+                s_dMZ[ly * CW + lx] = sm;
+            }
+            // top face z_{j+1}: above the domain only outflow (inflow is void)
+            {
+                T dV = zero;
+                if (!(j + 1 == nz && P.bc_top == SALEC_TOP_WALL)) {
+                    const T u = T(0.5) * (s_vL[(ly + 1) * VW + lx].y + s_vL[(ly + 1) * VW + lx + 1].y);
+                    dV = dt * p.A_Z[i] * u;
+                }
+                T sm = zero;
+                if (!warp_any(nonzero(dV))) {
+                } else if (pos(dV)) {
+                    move_s<T, NM, STR>(dn, kc, dV, -one, ILc, strip, acc, fm, fe);
+                    FZm += fm; FZe += fe; sm = fm;
+                    if (j == nz - 1 && own) t_out += double(fm);
+                } else if (neg(dV) && j + 1 < nz) {
+                    move_s<T, NM, STR>(dn, kc + CW, -dV, one, ILc, strip, acc, fm, fe); FZm -= fm; FZe -= fe; sm = -fm;
+                }
+                // the region's last row also records its top faces; the top of the grid
+                // records the outflow
+                if (j == nz - 1 || ly == CH - 3) s_dMZ[(ly + 1) * CW + lx] = sm;
+            }
+            // new state in increment form (as the phase kernels)
+            const T Vc = GE::vol(P, i, j);
+            T Vm[NM], Mm[NM], rn[NM];
+            T MLtot = zero, VLmat = zero, dMtot = zero, dVtot = zero;
+#pragma unroll
+            for (int m = 0; m < NM; ++m) {
+                const T2 fl = s_frL[m][kc];
+                const T VmL = fl.x * VLc;
+                const T MmL = fl.y * VmL;
+                MLtot += MmL; VLmat += VmL;
+                dMtot += acc.Mm[m]; dVtot += acc.Vm[m];
+                Vm[m] = VmL + acc.Vm[m];
+                Mm[m] = MmL + acc.Mm[m];
+                // nothing moved: the increment (0 - rho^L 0) / V_m is zero (no division)
+                const bool moved = nonzero(acc.Mm[m]) || nonzero(acc.Vm[m]);
+                rn[m] = !pos(Vm[m]) ? zero : (warp_any(moved) && moved) ? fl.y + (acc.Mm[m] - fl.y * acc.Vm[m]) / Vm[m] : fl.y;
+            }
+            const T Mtot = MLtot + dMtot, Vtot = VLmat + dVtot;
+            double Ic = pos(Mtot) ? ILc : 0.0;
+            const bool add_dI = pos(Mtot) && nonzero(acc.dI);
+            if (warp_any(add_dI) && add_dI) Ic = ILc + double(acc.dI / Mtot);
+            T s0 = zero, s1 = zero, s2 = zero, Dm = zero;
+            if (STR && pos(Vtot)) {
+                const T iv = one / Vtot;
+                const T2 a = s_sL01[kc], b = s_sL2d[kc];
+                s0 = a.x + (acc.S[0] - a.x * dVtot) * iv;
+                s1 = a.y + (acc.S[1] - a.y * dVtot) * iv;
+                s2 = b.x + (acc.S[2] - b.x * dVtot) * iv;
+                Dm = b.y + (acc.S[3] - b.y * dVtot) * iv;
+            }
+            T Mkeep = zero, Vkeep = zero, fnew[NM];
+#pragma unroll
+            for (int m = 0; m < NM; ++m) {
+                fnew[m] = Vm[m] / Vc;
+                if (fnew[m] < P.f_min) {
+                    const bool tally = own && nonzero(Mm[m]);
+                    if (warp_any(tally) && tally) t_disc += double(Mm[m]);
+                    Vm[m] = zero;
+                    Mm[m] = zero;
+                    rn[m] = zero;
+                }
+                Mkeep += Mm[m];
+                Vkeep += Vm[m];
+            }
+            if (!pos(Mkeep)) { Ic = 0.0; s0 = s1 = s2 = Dm = zero; }
+            T kappa = one;
+            const bool inB = j < P.pb, inR = i >= nr - P.pr;
+            if (inB || inR) {
+                T dsum = zero, phi1 = zero, phi3 = zero;
+                if (inB) {
+                    const T d = p.dB_c[j];
+                    T2 a = p.pb_c[c];
+                    const T rl = one - P.alpha_b * dt;
+                    a.x = a.x * rl + d * FRm;
+                    a.y = a.y * rl + d * FRe;
+                    if (own) O.pb_c[c] = a;
+                    dsum += d; phi1 += a.x; phi3 += a.y;
+                }
+                if (inR) {
+                    const int kk = j * P.pr + (i - (nr - P.pr));
+                    const T d = strip_row_c(p, j) ? p.dR_c[i] : zero;
+                    T2 a = p.pr_c[kk];
+                    const T rl = one - P.alpha_r * dt;
+                    a.x = a.x * rl + d * FZm;
+                    a.y = a.y * rl + d * FZe;
+                    if (own) O.pr_c[kk] = a;
+                    dsum += d; phi1 += a.x; phi3 += a.y;
+                }
+                if (pos(Mkeep) && pos(dsum)) {
+                    const T Mref = Vkeep * p.rho_ref[j];
+                    const T dM = -dt * (dsum * (Mkeep - Mref) + phi1);
+                    const double dEp = -double(dt) * (double(dsum) * (double(Mkeep) * Ic - double(Mref) * p.I_ref[j]) + double(phi3));
+                    const T Mnew = Mkeep + dM;
+                    if (!pos(Mnew)) atomicOr(&p.scal->status, 1);
+                    if (own) t_pml += double(dM);
+                    kappa = one + dM / Mkeep;
+                    Ic = Ic + (dEp - Ic * double(dM)) / double(Mnew);
+                }
+            }
+#pragma unroll
+            for (int m = 0; m < NM; ++m) {
+                const T2 f = pos(Vm[m]) ? V::mk(fnew[m], kappa * rn[m]) : V::mk(zero, zero);
+                s_frn[m][kc] = f;
+                if (own) O.fr[m][c] = f;
+            }
+            s_In[kc] = Ic;
+            if (is_nan(Ic)) atomicOr(&p.scal->status, 2);
+            if (STR && own) {
+                O.s01[c] = V::mk(s0, s1);
+                O.s2d[c] = V::mk(s2, Dm);
+                s_Dn[kc] = Dm;
+            }
+        }
+    }
+    __syncthreads();
+
+    // ---- phase 3b: momentum remap on the dual grid, PML phi2, heat per vertex
+    {
+        // face mass fluxes from shared memory; faces outside the grid carry nothing
+        auto dMR_s = [&](int fx, int fy, int jj) -> T { return (jj < 0 || jj >= nz) ? zero : s_dMR[fy * VW + fx]; };
+        auto dMZ_s = [&](int fx, int fy, int ii) -> T { return (ii < 0 || ii >= nr) ? zero : s_dMZ[fy * CW + fx]; };
+        // dual mass flux between vertices (lx,ly) and (lx+1,ly), grid (i,j)
+        auto dual_R_s = [&](int lx, int ly, int j) -> T {
+            return T(0.25) * (dMR_s(lx, ly - 1, j - 1) + dMR_s(lx + 1, ly - 1, j - 1) + dMR_s(lx, ly, j) + dMR_s(lx + 1, ly, j));
+        };
+        // between (lx,ly) and (lx,ly+1); j == nz: out through the top
+        auto dual_Z_s = [&](int lx, int ly, int i, int j) -> T {
+            if (j == nz) return T(0.5) * (dMZ_s(lx - 1, ly, i - 1) + dMZ_s(lx, ly, i));
+            return T(0.25) * (dMZ_s(lx - 1, ly, i - 1) + dMZ_s(lx - 1, ly + 1, i - 1) + dMZ_s(lx, ly, i) + dMZ_s(lx, ly + 1, i));
+        };
+        constexpr int RB = TW + 1;
+        for (int k = tid; k < RB * (TH + 1); k += NT) {
+            const int lx = H + k % RB, ly = H + k / RB, i = x0 + lx, j = y0 + ly;
+            if (i > nr || j > nz) continue;
+            const int kv = ly * VW + lx, v = j * nv + i;
+            const bool own = (i < ox + TW || last_x) && (j < oy + TH || last_y);
+            const T2 vL = s_vL[kv];
+            DualFace<T> oR = {zero, zero, zero, zero}, oZ = {zero, zero, zero, zero};
+            DualFace<T> iR = {zero, zero, zero, zero}, iZ = {zero, zero, zero, zero};
+            if (i < nr) {
+                const T f = dual_R_s(lx, ly, j);
+                oR = dual_face<T>(f, pos(f) ? vL : s_vL[kv + 1]);
+            }
+            {
+                const T f = dual_Z_s(lx, ly, i, j);
+                oZ = dual_face<T>(f, (pos(f) || j == nz) ? vL : s_vL[kv + VW]);
+            }
+            if (i > 0) {
+                const T f = dual_R_s(lx - 1, ly, j);
+                iR = dual_face<T>(f, pos(f) ? s_vL[kv - 1] : vL);
+            }
+            if (j > 0) {
+                const T f = dual_Z_s(lx, ly - 1, i, j - 1);
+                iZ = dual_face<T>(f, pos(f) ? s_vL[kv - VW] : vL);
+            }
+            const T m0 = s_mv[kv];
+            T m = m0, pr = m0 * vL.x, pz = m0 * vL.y;
+            T kin = half * m0 * (vL.x * vL.x + vL.y * vL.y);
+            m += iR.f; kin += iR.e;
+            m -= oR.f; kin -= oR.e;
+            m += iZ.f; kin += iZ.e;
+            m -= oZ.f; kin -= oZ.e;
+            const T inRr = iR.fr, inRz = iR.fz, outRr = oR.fr, outRz = oR.fz;
+            const T inZr = iZ.fr, inZz = iZ.fz, outZr = oZ.fr, outZz = oZ.fz;
+            const bool top = own && j == nz;
+            if (warp_any(top) && top) t_zmom += double(outZz);
+            pr += (inRr - outRr) + (inZr - outZr);
+            pz += (inRz - outRz) + (inZz - outZz);
+            const T dKv = s_dK[kv];
+            const bool quiet = !nonzero(pr) && !nonzero(pz) && !nonzero(kin) && !nonzero(dKv);
+            T kheat = zero, im = zero;
+            bool have_im = false;
+            if (pos(m) && warp_any(!quiet) && !quiet) {
+                im = one / m;
+                have_im = true;
+                const T dKr = kin - half * (pr * pr + pz * pz) * im;
+                kheat = (dKv + dKr) * im;
+            }
+            s_kheat[kv] = kheat;
+            T dsum = zero, a2r = zero, a2z = zero;
+            if (j < P.pb) {
+                const T d = p.dB_v[j];
+                T4 a = p.pb_v[v];
+                const T rl = one - P.alpha_b * dt;
+                a.x = a.x * rl + d * (outRr - inRr);
+                a.y = a.y * rl + d * (outRz - inRz);
+                if (own) store_pair(&O.pb_v[v], 0, V::mk(a.x, a.y));
+                dsum += d; a2r += a.x; a2z += a.y;
+            }
+            if (i > nr - P.pr) {
+                const int kk = j * P.pr + (i - (nr - P.pr + 1));
+                const T d = strip_row_v(p, j, nz) ? p.dR_v[i] : zero;
+                T4 a = p.pr_v[kk];
+                const T rl = one - P.alpha_r * dt;
+                a.x = a.x * rl + d * (outZr - inZr);
+                a.y = a.y * rl + d * (outZz - inZz);
+                if (own) store_pair(&O.pr_v[kk], 0, V::mk(a.x, a.y));
+                dsum += d; a2r += a.x; a2z += a.y;
+            }
+            if (j < P.pb || i > nr - P.pr) {
+                pr = pr - dt * (dsum * pr + a2r);
+                pz = pz - dt * (dsum * pz + a2z);
+            }
+            T vr = zero, vz = zero;
+            const bool moving = nonzero(pr) || nonzero(pz);
+            if (pos(m) && warp_any(moving) && moving) {
+                // no material in any adjacent cell after the clean-up: no momentum
+                bool occupied = false;
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    const int ci = (q == 0 || q == 3) ? i - 1 : i;
+                    const int cj = (q < 2) ? j - 1 : j;
+                    if (ci < 0 || ci >= nr || cj < 0 || cj >= nz) continue;
+                    const int kc = (cj - y0) * CW + (ci - x0);
+#pragma unroll
+                    for (int mm = 0; mm < NM; ++mm) occupied |= pos(s_frn[mm][kc].x);
+                }
+                if (occupied) {
+                    if (!have_im) im = one / m;
+                    vr = pr * im;
+                    vz = pz * im;
+                }
+            }
+            if (i == 0 || i == nr) vr = zero;
+            if (j == 0) {
+                vz = zero;
+                if (P.bc_bottom == SALEC_BOTTOM_NOSLIP) vr = zero;
+            }
+            if (j == nz && P.bc_top == SALEC_TOP_WALL) vz = zero;
+            if (is_nan(vr) || is_nan(vz)) atomicOr(&p.scal->status, 2);
+            const T2 vnew = V::mk(vr, vz);
+            s_vn[kv] = vnew;
+            if (own) O.v[v] = vnew;
+        }
+    }
+    __syncthreads();
+
+    // ---- phase 3c: heat to the own cells; the Courant rate of the new state (Eq. 14)
+    T speed_max = zero;
+    for (int k = tid; k < TW * TH; k += NT) {
+        const int lx = H + k % TW, ly = H + k / TW, i = x0 + lx, j = y0 + ly;
+        if (i >= nr || j >= nz) continue;
+        const int kc = ly * CW + lx, c = j * nr + i;
+        T M = zero;
+#pragma unroll
+        for (int m = 0; m < NM; ++m) {
+            const T2 fr = s_frn[m][kc];
+            M += fr.x * fr.y;
+        }
+        double Ic = s_In[kc];
+        const int ka = ly * VW + lx;
+        if (pos(M)) {
+            const T add = T(0.25) * (s_kheat[ka] + s_kheat[ka + 1] + s_kheat[ka + VW + 1] + s_kheat[ka + VW]);
+            if (warp_any(nonzero(add)) && nonzero(add)) Ic += double(add);
+        }
+        O.I[c] = Ic;
+        // the equation of state of the new state, as phase 0 of the next step would form it
+        // (into the cache it reads), and the rate (|v| + c) / L for the next step's dt.  A
+        // cell whose fractions, densities, energy and damage are bitwise those of the
+        // current state keeps its cached values (same inputs, same results).
+        T phi = zero;
+        T2 ec;
+        const T D = STR ? s_Dn[kc] : zero;
+        bool same = __double_as_longlong(Ic) == __double_as_longlong(p.I[c]);
+#pragma unroll
+        for (int m = 0; m < NM; ++m) {
+            const T2 fn = s_frn[m][kc], fo = p.fr[m][c];
+            same = same && fn.x == fo.x && fn.y == fo.y;
+            if (pos(fn.x)) phi += fn.x;
+        }
+        if (STR) same = same && D == p.s2d[c].y;
+        if (!warp_any(!same)) {
+            ec = p.eosc[c];
+        } else {
+            T c2m = zero, phat = zero, p1 = zero;
+            const T In = T(Ic);
+#pragma unroll
+            for (int m = 0; m < NM; ++m) {
+                const T2 fr = s_frn[m][kc];
+                if (pos(fr.x)) {
+                    T pm, c2;
+                    eos_eval<T>(P.mat[m], fr.y, In, pm, c2);
+                    const T pmin = (one - D) * P.mat[m].p_t * expansion_weight(P.mat[m], fr.y);
+                    pm = pm < pmin ? pmin : pm;
+                    phat += fr.x * pm;
+                    c2m = max_nonneg(c2m, c2);
+                    p1 = pm;
+                }
+            }
+            ec = V::mk(NM == 1 ? p1 : phat, c2m);
+        }
+        O.eosc[c] = ec;
+        const T c2m = ec.y;
+        if (pos(phi)) {
+            const T2 va = s_vn[ka], vb = s_vn[ka + 1], vc = s_vn[ka + VW + 1], vd = s_vn[ka + VW];
+            T w = va.x * va.x + va.y * va.y;
+            w = max_nonneg(w, vb.x * vb.x + vb.y * vb.y);
+            w = max_nonneg(w, vc.x * vc.x + vc.y * vc.y);
+            w = max_nonneg(w, vd.x * vd.x + vd.y * vd.y);
+            T speed = t_sqrt<T>(w) + t_sqrt<T>(c2m);
+            if (!UNI) speed = speed * GE::ilen(P, i, j);
+            if (is_nan(speed)) atomicOr(&p.scal->status, 2);
+            speed_max = max_nonneg(speed_max, speed);
+        }
+    }
+
+    // ---- reductions.  The tallies (FP64) are rare (top row, strips, clean-up): a warp that
+    // holds one sums it and adds it with one atomic per tally, so no other warp issues FP64
+    // work for them.  The Courant maximum of every block goes through warp 0.
+    {
+        const int lane = tid & 31, w = tid >> 5;
+        const bool any_tally = nonzero(t_out) || nonzero(t_disc) || nonzero(t_pml) || nonzero(t_zmom);
+        if (__any_sync(0xffffffffu, any_tally)) {
+            double sv[4] = {t_out, t_disc, t_pml, t_zmom};
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+                for (int q = 0; q < 4; ++q) sv[q] += __shfl_down_sync(0xffffffffu, sv[q], o);
+            if (lane == 0) {
+                DevScalars* s = p.scal;
+                if (sv[0] != 0.0) atomicAdd(&s->mass_out, sv[0]);
+                if (sv[1] != 0.0) atomicAdd(&s->mass_discarded, sv[1]);
+                if (sv[2] != 0.0) atomicAdd(&s->mass_pml, sv[2]);
+                if (sv[3] != 0.0) atomicAdd(&s->zmom_out, sv[3]);
+            }
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) speed_max = max_nonneg(speed_max, __shfl_down_sync(0xffffffffu, speed_max, o));
+        unsigned long long* s_bits = reinterpret_cast<unsigned long long*>(s_red);
+        if (lane == 0) s_bits[w] = (unsigned long long)__double_as_longlong(double(speed_max));
+        __syncthreads();
+        if (w == 0) {
+            unsigned long long b = lane < NT / 32 ? s_bits[lane] : 0ull;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) b = max(b, __shfl_down_sync(0xffffffffu, b, o));
+            if (lane == 0) {
+                DevScalars* s = p.scal;
+                atomicMax(&s->maxbits, b);
+                if (blockIdx.x == 0 && blockIdx.y == 0) {
+                    s->t += s->dt;
+                    s->dt_prev = s->dt;
+                    s->nstep += 1ull;
+                }
+            }
+        }
+    }
+}
+
+// The equation of state of the current state into the cache and its Courant rates into the
+// running maximum (the first step of a sequence of fused steps, or after the host changed
+// the state): the phase-0 arithmetic of both.
+template <typename T, int NM, bool STR, bool UNI>
+__global__ void __launch_bounds__(kThreads) k_courant_rates(const ParamsT<T> P)
+{
+    typedef VT<T> V;
+    typedef typename V::T2 T2;
+    typedef Geo<T, UNI> GE;
+    const T zero = T(0);
+    const int i = blockIdx.x * kBlockX + threadIdx.x;
+    const int j = blockIdx.y * kBlockY + threadIdx.y;
+    const PtrsT<T>& p = P.p;
+    const int nr = P.nr;
+    T speed = zero;
+    if (i < nr && j < P.nz) {
+        const int c = j * nr + i;
+        T phi = zero, c2m = zero, phat = zero, p1 = zero;
+        const T Ic = T(p.I[c]);
+        const T D = STR ? p.s2d[c].y : zero;
+#pragma unroll
+        for (int m = 0; m < NM; ++m) {
+            const T2 fr = p.fr[m][c];
+            if (pos(fr.x)) {
+                T pm, c2;
+                eos_eval<T>(P.mat[m], fr.y, Ic, pm, c2);
+                const T pmin = (T(1) - D) * P.mat[m].p_t * expansion_weight(P.mat[m], fr.y);
+                pm = pm < pmin ? pmin : pm;
+                phat += fr.x * pm;
+                phi += fr.x;
+                c2m = max_nonneg(c2m, c2);
+                p1 = pm;
+            }
+        }
+        p.eosc[c] = V::mk(NM == 1 ? p1 : phat, c2m);
+        if (pos(phi)) {
+            const int nv = nr + 1;
+            const T2 va = p.v[j * nv + i], vb = p.v[j * nv + i + 1];
+            const T2 vc = p.v[(j + 1) * nv + i + 1], vd = p.v[(j + 1) * nv + i];
+            T w = va.x * va.x + va.y * va.y;
+            w = max_nonneg(w, vb.x * vb.x + vb.y * vb.y);
+            w = max_nonneg(w, vc.x * vc.x + vc.y * vc.y);
+            w = max_nonneg(w, vd.x * vd.x + vd.y * vd.y);
+            speed = t_sqrt<T>(w) + t_sqrt<T>(c2m);
+            if (!UNI) speed = speed * GE::ilen(P, i, j);
+            if (is_nan(speed)) atomicOr(&p.scal->status, 2);
+        }
+    }
+    __shared__ unsigned long long sh[kThreads / 32];
+    const int tid = threadIdx.y * kBlockX + threadIdx.x;
+    for (int o = 16; o > 0; o >>= 1) speed = max_nonneg(speed, __shfl_down_sync(0xffffffffu, speed, o));
+    if ((tid & 31) == 0) sh[tid >> 5] = (unsigned long long)__double_as_longlong(double(speed));
+    __syncthreads();
+    if (tid != 0) return;
+    unsigned long long b = sh[0];
+    for (int w = 1; w < kThreads / 32; ++w) b = max(b, sh[w]);
+    atomicMax(&p.scal->maxbits, b);
+}
+
+namespace {
+
+template <typename T, int NM, bool STR, bool UNI>
+struct Fused {
+    typedef TileShape<T, NM, STR> S;
+    typedef TileLayout<T, NM, STR, S::TW, S::TH> L;
+    static void* fn() { return reinterpret_cast<void*>(k_step_fused<T, NM, STR, UNI, S::TW, S::TH, S::NT, S::MINB>); }
+    static cudaError_t prepare()
+    {
+        return cudaFuncSetAttribute(k_step_fused<T, NM, STR, UNI, S::TW, S::TH, S::NT, S::MINB>,
+                                    cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L::bytes);
+    }
+    static cudaError_t launch(const ParamsT<T>& P, const OutPtrsT<T>& O, cudaStream_t s)
+    {
+        const dim3 g((P.nr + S::TW - 1) / S::TW, (P.nz + S::TH - 1) / S::TH);
+        k_step_fused<T, NM, STR, UNI, S::TW, S::TH, S::NT, S::MINB><<<g, S::NT, L::bytes, s>>>(P, O);
+        return cudaGetLastError();
+    }
+    static cudaError_t rates(const ParamsT<T>& P, cudaStream_t s)
+    {
+        const dim3 g((P.nr + kBlockX - 1) / kBlockX, (P.nz + kBlockY - 1) / kBlockY);
+        k_courant_rates<T, NM, STR, UNI><<<g, dim3(kBlockX, kBlockY), 0, s>>>(P);
+        return cudaGetLastError();
+    }
+};
+
+// dispatch on the material count, strength and grid form of a run
+template <typename T, template <typename, int, bool, bool> class F, typename Fn>
+cudaError_t dispatch(const ParamsT<T>& P, Fn&& fn)
+{
+    const bool st = P.any_strength != 0, un = P.uniform != 0;
+#define SALEC_FUSED_CASE(NM_)                                                                        \
+    case NM_:                                                                                         \
+        if (un) return st ? fn(F<T, NM_, true, true>()) : fn(F<T, NM_, false, true>());               \
+        return st ? fn(F<T, NM_, true, false>()) : fn(F<T, NM_, false, false>());
+    switch (P.nmat) {
+        SALEC_FUSED_CASE(1)
+        SALEC_FUSED_CASE(2)
+        SALEC_FUSED_CASE(3)
+    default: return cudaErrorInvalidValue;
+    }
+#undef SALEC_FUSED_CASE
+}
+
+}  // namespace
+
+template <typename T>
+cudaError_t prepare_fused(const ParamsT<T>& P)
+{
+    return dispatch<T, Fused>(P, [](auto f) { return decltype(f)::prepare(); });
+}
+
+template <typename T>
+size_t fused_smem_bytes(const ParamsT<T>& P)
+{
+    size_t b = 0;
+    dispatch<T, Fused>(P, [&](auto f) { b = decltype(f)::L::bytes; return cudaSuccess; });
+    return b;
+}
+
+template <typename T>
+cudaError_t launch_courant_rates(const ParamsT<T>& P, cudaStream_t s)
+{
+    return dispatch<T, Fused>(P, [&](auto f) { return decltype(f)::rates(P, s); });
+}
+
+// One fused cycle: the Courant kernel (dt from the running maximum of the rates), then the
+// tile kernel.  With ev: an event before and after (2 events).
+template <typename T>
+cudaError_t launch_step_fused(const ParamsT<T>& P, const OutPtrsT<T>& O, cudaStream_t s, cudaEvent_t* ev)
+{
+    if (ev) cudaEventRecord(ev[0], s);
+    cudaError_t e = launch_courant<T>(P, s);
+    if (e != cudaSuccess) return e;
+    e = dispatch<T, Fused>(P, [&](auto f) { return decltype(f)::launch(P, O, s); });
+    if (ev) cudaEventRecord(ev[1], s);
+    return e;
+}
+
+template cudaError_t prepare_fused<double>(const ParamsT<double>&);
+template cudaError_t prepare_fused<float>(const ParamsT<float>&);
+template size_t fused_smem_bytes<double>(const ParamsT<double>&);
+template size_t fused_smem_bytes<float>(const ParamsT<float>&);
+template cudaError_t launch_courant_rates<double>(const ParamsT<double>&, cudaStream_t);
+template cudaError_t launch_courant_rates<float>(const ParamsT<float>&, cudaStream_t);
+template cudaError_t launch_step_fused<double>(const ParamsT<double>&, const OutPtrsT<double>&, cudaStream_t, cudaEvent_t*);
+template cudaError_t launch_step_fused<float>(const ParamsT<float>&, const OutPtrsT<float>&, cudaStream_t, cudaEvent_t*);
+
+}  // namespace salec

@@ -117,8 +117,31 @@ struct PtrsT {
     T2* sL2d;               // Lagrangian (s_rz, D)
     T* dMR;                 // signed mass flux through radial faces, (nr+1) x nz
     T* dMZ;                 // signed mass flux through vertical faces, nr x (nz+1)
+    T2* eosc;               // fused form: each cell's equation of state at the current state,
+                            // (p_m after the tension cut-off, c^2) for one material,
+                            // (p_hat = sum f_m p_m, max c_m^2) for several
     double* partial;        // per-block reduction partials
     DevScalars* scal;
+};
+
+// Where a fused step writes the fields it rewrites (the other copy of the ping-pong pair;
+// the kernel reads the current copy through ParamsT::p).
+template <typename T>
+struct OutPtrsT {
+    typedef typename VT<T>::T2 T2;
+    typedef typename VT<T>::T4 T4;
+    T2* fr[kMaxMat];
+    double* I;
+    T2* s01;
+    T2* s2d;
+    T2* v;
+    T2* pb_c;
+    T* pb_psi2;
+    T4* pb_v;
+    T2* pr_c;
+    T* pr_psi2;
+    T4* pr_v;
+    T2* eosc;
 };
 
 template <typename T>
@@ -335,6 +358,13 @@ template <typename T>
 cudaError_t launch_batch_step(const ParamsT<T>* runs_dev, int nruns, int nmat, bool strength, bool uniform, const BatchTile* const* work,
                               const int* ntiles, const dim3* blk, cudaStream_t s, cudaEvent_t* ev);
 template <typename T> cudaError_t launch_batch_poll(const ParamsT<T>* runs_dev, int n, double* out, cudaStream_t s);
+template <typename T> cudaError_t launch_courant(const ParamsT<T>& P, cudaStream_t s);
+// fused form (salec_fused.cu): one tile kernel per step after the Courant kernel
+template <typename T> cudaError_t prepare_fused(const ParamsT<T>& P);
+template <typename T> size_t fused_smem_bytes(const ParamsT<T>& P);
+template <typename T> cudaError_t launch_courant_rates(const ParamsT<T>& P, cudaStream_t s);
+template <typename T>
+cudaError_t launch_step_fused(const ParamsT<T>& P, const OutPtrsT<T>& O, cudaStream_t s, cudaEvent_t* ev);
 bool kernel_on_vertices(int k);
 int tiles_of(int nr, int nz, int k, dim3 blk);
 template <typename T> cudaError_t launch_pressure(const ParamsT<T>& P, double* out, cudaStream_t s);

@@ -16,95 +16,9 @@
 // FP32 form issues no FP64 arithmetic except in the energy update and the reductions.
 #include <cuda_runtime.h>
 
-#include "salec_internal.cuh"
+#include "salec_device.cuh"
 
 namespace salec {
-
-__device__ __forceinline__ double warp_sum(double v)
-{
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-    return v;
-}
-
-// block-wide sum, result valid in thread 0 (blocks are whole warps, at most kMaxThreads)
-__device__ double block_sum(double v, double* sh)
-{
-    const int tid = threadIdx.y * blockDim.x + threadIdx.x;
-    const int nw = (blockDim.x * blockDim.y) >> 5;
-    v = warp_sum(v);
-    __syncthreads();
-    if ((tid & 31) == 0) sh[tid >> 5] = v;
-    __syncthreads();
-    double s = 0.0;
-    if (tid == 0)
-        for (int w = 0; w < nw; ++w) s += sh[w];
-    return s;
-}
-
-// The right absorbing strip acts on the rows whose reference (far-field) state holds
-// material: the medium whose waves it absorbs.  Above the target the reference is void and
-// damping toward it would remove ejecta, so there it does nothing (cells: row j; vertices:
-// either adjacent cell row).
-template <typename T>
-__device__ __forceinline__ bool strip_row_c(const PtrsT<T>& p, int j) { return pos(p.rho_ref[j]); }
-template <typename T>
-__device__ __forceinline__ bool strip_row_v(const PtrsT<T>& p, int j, int nz)
-{
-    return (j > 0 && pos(p.rho_ref[j - 1])) || (j < nz && pos(p.rho_ref[j]));
-}
-
-// ---------------------------------------------------------------------------------
-// Cell geometry per radian.  A non-uniform grid (UNI = false) takes a cell's volume and
-// radial faces as a column entry times its row height: V = r_c dr dz, A_R = r_i dz; a
-// uniform grid of dx cells (UNI = true) keeps one entry per column for every row, which
-// spares the FP64 pipe those products.
-// ---------------------------------------------------------------------------------
-template <typename T, bool UNI>
-struct Geo {
-    static __device__ __forceinline__ T vol(const ParamsT<T>& P, int i, int j)
-    {
-        return UNI ? P.p.V[i] : P.p.A_Z[i] * P.p.dz[j];
-    }
-    static __device__ __forceinline__ T ivol(const ParamsT<T>& P, int i, int j)
-    {
-        return UNI ? P.p.invV[i] : P.p.invAZ[i] * P.p.idz[j];
-    }
-    // radial face area at r_i of row j
-    static __device__ __forceinline__ T area_r(const ParamsT<T>& P, int i, int j)
-    {
-        return UNI ? P.p.A_R[i] : P.p.rR[i] * P.p.dz[j];
-    }
-    // net radial volume flux A_R(i+1) uR - A_R(i) uL of cell (i,j)
-    static __device__ __forceinline__ T flux_r(const ParamsT<T>& P, int i, int j, T uL, T uR)
-    {
-        return UNI ? P.p.A_R[i + 1] * uR - P.p.A_R[i] * uL : P.p.dz[j] * (P.p.rR[i + 1] * uR - P.p.rR[i] * uL);
-    }
-    static __device__ __forceinline__ T idr(const ParamsT<T>& P, int i) { return UNI ? P.idx : P.p.idr[i]; }
-    static __device__ __forceinline__ T idz(const ParamsT<T>& P, int j) { return UNI ? P.idx : P.p.idz[j]; }
-    // the cell's length scale L = min(dr, dz) and 1 / L
-    static __device__ __forceinline__ T len(const ParamsT<T>& P, int i, int j)
-    {
-        if (UNI) return P.dx;
-        const T a = P.p.dr[i], b = P.p.dz[j];
-        return a < b ? a : b;
-    }
-    static __device__ __forceinline__ T ilen(const ParamsT<T>& P, int i, int j)
-    {
-        if (UNI) return P.idx;
-        const T a = P.p.idr[i], b = P.p.idz[j];
-        return a > b ? a : b;
-    }
-    // derivatives of the cell's stress power V S:e with respect to its corner velocities:
-    // V / (2 dr) for r-derivatives, V / (4 r_c) for the hoop strain rate
-    static __device__ __forceinline__ T half_v_dr(const ParamsT<T>& P, int i, int j)
-    {
-        return UNI ? T(0.5) * P.p.A_Z[i] : T(0.5) * P.p.rc[i] * P.p.dz[j];
-    }
-    static __device__ __forceinline__ T quarter_v_rc(const ParamsT<T>& P, int i, int j)
-    {
-        return UNI ? T(0.25) * P.dx2 : T(0.25) * P.p.dr[i] * P.p.dz[j];
-    }
-};
 
 // ---------------------------------------------------------------------------------
 // Phase 0: equation of state, artificial viscosity and the Courant time step.
@@ -297,9 +211,18 @@ __device__ __forceinline__ void body_phase1(const ParamsT<T>& P, int bx, int by,
     const typename V::T2 vn = p.v[v];
     T vr = zero, vz = zero;
     if (pos(mass)) {
-        const T im = one / mass;
-        vr = vn.x + dt * ((Fr - psr) * im);
-        vz = vn.y + dt * ((Fz - psz) * im - P.g);
+        // no net force and no gravity: v^L = v (the update's own value, up to the sign of a
+        // zero) without the reciprocal, which is a long FP64-pipe sequence in the FP64 form
+        const T fr_ = Fr - psr, fz_ = Fz - psz;
+        const bool acc = nonzero(fr_) || nonzero(fz_) || nonzero(P.g);
+        if (warp_any(acc) && acc) {
+            const T im = one / mass;
+            vr = vn.x + dt * (fr_ * im);
+            vz = vn.y + dt * (fz_ * im - P.g);
+        } else {
+            vr = vn.x;
+            vz = vn.y;
+        }
     }
     if (i == 0 || i == nr) vr = zero;
     if (j == 0) {
@@ -404,7 +327,8 @@ __device__ __forceinline__ void body_phase2(const ParamsT<T>& P, int bx, int by,
             // one material: f_m / Phi = 1; true divisions keep a resting cell exact
             const T VmL = NM == 1 ? Vm + dVmat : Vm + fr.x / phi * dVmat;
             bad |= !pos(VmL);
-            p.frL[m][c] = V::mk(VmL / VLc, fr.y * (Vm / VmL));
+            // unchanged volume: V_m / V_m^L is exactly 1 (no division)
+            p.frL[m][c] = V::mk(VmL / VLc, warp_any(nonzero(dV)) ? fr.y * (Vm / VmL) : fr.y);
             if (STR && P.mat[m].strength == SALEC_STRENGTH_COLLINS) {
                 const MatT<T>& mm = P.mat[m];
                 const T pb = p.pbphi[c].x;
@@ -451,11 +375,6 @@ __device__ __forceinline__ void body_phase2(const ParamsT<T>& P, int bx, int by,
 // ---------------------------------------------------------------------------------
 // Phase 3a: donor-cell remap of the cells.
 // ---------------------------------------------------------------------------------
-template <typename T, int NM>
-struct Acc {
-    T Vm[NM], Mm[NM], S[4];
-    T dI;        // sum over inflows of (I_donor - I^L) * mass (the remap's energy change)
-};
 
 // Swept volume of the radial face at r_i of row j, and of the vertical face at z_j of
 // column i, from the Lagrangian velocities (computed identically by both neighbours).
@@ -590,7 +509,9 @@ __device__ __forceinline__ void body_phase3a(const ParamsT<T>& P, int bx, int by
             dMtot += acc.Mm[m]; dVtot += acc.Vm[m];
             Vm[m] = VmL + acc.Vm[m];
             Mm[m] = MmL + acc.Mm[m];
-            rn[m] = pos(Vm[m]) ? fl.y + (acc.Mm[m] - fl.y * acc.Vm[m]) / Vm[m] : zero;
+            // nothing moved: the increment (0 - rho^L 0) / V_m is zero (no division)
+            const bool moved = nonzero(acc.Mm[m]) || nonzero(acc.Vm[m]);
+            rn[m] = !pos(Vm[m]) ? zero : (warp_any(moved) && moved) ? fl.y + (acc.Mm[m] - fl.y * acc.Vm[m]) / Vm[m] : fl.y;
         }
         const T Mtot = MLtot + dMtot, Vtot = VLmat + dVtot;
         double Ic = pos(Mtot) ? ILc : 0.0;
@@ -716,29 +637,6 @@ __device__ __forceinline__ T dual_Z(const ParamsT<T>& P, int i, int j)
 {
     if (j == P.nz) return T(0.5) * (dMZ_at(P, i - 1, j) + dMZ_at(P, i, j));
     return T(0.25) * (dMZ_at(P, i - 1, j) + dMZ_at(P, i - 1, j + 1) + dMZ_at(P, i, j) + dMZ_at(P, i, j + 1));
-}
-
-// What a dual face carries: mass f, momentum f w and kinetic energy f |w|^2 / 2 with the
-// upwind vertex velocity w.
-template <typename T>
-struct DualFace {
-    T f, fr, fz, e;
-};
-// products rounded as written (never fused into a multiply-add with their later use), so
-// that a face computed by either of its vertices, or read from the other, is the same
-__device__ __forceinline__ double mul_rn(double a, double b) { return __dmul_rn(a, b); }
-__device__ __forceinline__ float mul_rn(float a, float b) { return __fmul_rn(a, b); }
-__device__ __forceinline__ double add_rn(double a, double b) { return __dadd_rn(a, b); }
-__device__ __forceinline__ float add_rn(float a, float b) { return __fadd_rn(a, b); }
-template <typename T>
-__device__ __forceinline__ DualFace<T> dual_face(T f, typename VT<T>::T2 w)
-{
-    DualFace<T> d;
-    d.f = f;
-    d.fr = mul_rn(f, w.x);
-    d.fz = mul_rn(f, w.y);
-    d.e = mul_rn(mul_rn(T(0.5), f), add_rn(mul_rn(w.x, w.x), mul_rn(w.y, w.y)));
-    return d;
 }
 
 // The FP64 form shares each dual face between its two vertices (its FP64 pipe is the
@@ -945,6 +843,15 @@ __global__ void k_courant(ParamsT<T> P)
 {
     if (threadIdx.x == 0) courant_dt<T>(P);
 }
+
+template <typename T>
+cudaError_t launch_courant(const ParamsT<T>& P, cudaStream_t s)
+{
+    k_courant<T><<<1, 32, 0, s>>>(P);
+    return cudaGetLastError();
+}
+template cudaError_t launch_courant<double>(const ParamsT<double>&, cudaStream_t);
+template cudaError_t launch_courant<float>(const ParamsT<float>&, cudaStream_t);
 template <typename T, bool STR, bool UNI>
 __global__ void __launch_bounds__(kMaxThreads) k_phase1(ParamsT<T> P) { body_phase1<T, STR, UNI>(P, blockIdx.x, blockIdx.y, gridDim.x, gridDim.y); }
 template <typename T, int NM, bool STR, bool UNI>

@@ -16,6 +16,7 @@ from . import build as _build
 SALEC_OK, SALEC_EINVAL, SALEC_ENOMEM, SALEC_ECUDA, SALEC_EORDER, SALEC_EUNSTABLE = range(6)
 SALEC_FP64 = 0
 SALEC_FP32MIX = 1
+SALEC_STEP_PHASES, SALEC_STEP_FUSED = 0, 1
 PRECISIONS = {"fp64": SALEC_FP64, "fp32mix": SALEC_FP32MIX}
 _STATUS = {0: "SALEC_OK", 1: "SALEC_EINVAL", 2: "SALEC_ENOMEM", 3: "SALEC_ECUDA", 4: "SALEC_EORDER",
            5: "SALEC_EUNSTABLE"}
@@ -57,9 +58,10 @@ _lib = None
 EXPORTS = ["salec_state_bytes", "salec_create", "salec_set_material", "salec_set_spacing", "salec_add_layer",
            "salec_place_projectile", "salec_finalize", "salec_step", "salec_get_scalars",
            "salec_set_time", "salec_get_field", "salec_set_field", "salec_crater_profile",
-           "salec_conservation", "salec_checkpoint_bytes", "salec_get_state", "salec_set_state",
+           "salec_conservation", "salec_checkpoint_bytes", "salec_get_state", "salec_set_state", "salec_state_changed",
            "salec_launches_per_step", "salec_set_kernel_timing", "salec_kernel_times",
-           "salec_kernel_name", "salec_courant_dt_noalloc", "salec_last_error", "salec_destroy",
+           "salec_kernel_name", "salec_step_kernel_name", "salec_set_step_form", "salec_get_step_form",
+           "salec_courant_dt_noalloc", "salec_last_error", "salec_destroy",
            "salec_set_end_time", "salec_set_block_shapes", "salec_get_block_shapes", "salec_autotune",
            "salec_batch_bytes", "salec_batch_create", "salec_batch_step", "salec_batch_run", "salec_batch_poll",
            "salec_batch_autotune", "salec_batch_last_error", "salec_batch_destroy",
@@ -97,10 +99,14 @@ def load(build: bool = True):
         "salec_checkpoint_bytes": (I, [P, C.POINTER(C.c_size_t)]),
         "salec_get_state": (I, [P, P, Z]),
         "salec_set_state": (I, [P, P, Z]),
+        "salec_state_changed": (I, [P]),
         "salec_launches_per_step": (I, [P]),
         "salec_set_kernel_timing": (I, [P, I]),
         "salec_kernel_times": (I, [P, PD, I, C.POINTER(C.c_int)]),
         "salec_kernel_name": (C.c_char_p, [I]),
+        "salec_step_kernel_name": (C.c_char_p, [P, I]),
+        "salec_set_step_form": (I, [P, I]),
+        "salec_get_step_form": (I, [P]),
         "salec_courant_dt_noalloc": (I, [C.POINTER(salec_grid), C.POINTER(salec_material), C.POINTER(C.c_void_p),
                                          P, P, P, D, PD, P]),
         "salec_last_error": (C.c_char_p, [P]),
@@ -293,6 +299,11 @@ class Sim:
         b = np.ascontiguousarray(buf, dtype=np.uint8)
         self._check(load().salec_set_state(self._h, C.c_void_p(b.ctypes.data), b.size))
 
+    def state_changed(self) -> None:
+        """Declare that the checkpoint range of ``state`` was written directly (a device
+        copy of an earlier image): the next step starts from it."""
+        self._check(load().salec_state_changed(self._h))
+
     def launches_per_step(self) -> int:
         return load().salec_launches_per_step(self._h)
 
@@ -322,7 +333,18 @@ class Sim:
         out = np.zeros(n)
         steps = C.c_int()
         self._check(load().salec_kernel_times(self._h, out.ctypes.data_as(C.POINTER(C.c_double)), n, C.byref(steps)))
-        return {load().salec_kernel_name(k).decode(): float(out[k]) for k in range(n)}, steps.value
+        names = [load().salec_step_kernel_name(self._h, k).decode() for k in range(n)]
+        return {nm: float(out[k]) for k, nm in enumerate(names) if nm}, steps.value
+
+    @property
+    def step_form(self) -> str:
+        """"fused" (one tile kernel per step after the Courant kernel) or "phases" (six
+        whole-grid kernels and the Courant kernel)."""
+        return {SALEC_STEP_PHASES: "phases", SALEC_STEP_FUSED: "fused"}[load().salec_get_step_form(self._h)]
+
+    @step_form.setter
+    def step_form(self, form: str) -> None:
+        self._check(load().salec_set_step_form(self._h, {"phases": SALEC_STEP_PHASES, "fused": SALEC_STEP_FUSED}[form]))
 
 
 def courant_dt_noalloc(spec: dict, fr_ptrs, I_ptr: int, v_ptr: int, dt_prev: float, stream_ptr: int,

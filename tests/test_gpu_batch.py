@@ -44,6 +44,13 @@ def _specs(n_runs, seed0=100):
 TOL = {"fp64": 1e-12, "fp32mix": 1e-5}
 
 
+def _alone(spec, precision):
+    """A run stepped by itself with the phase kernels, whose per-cell code the batch runs."""
+    s = salec.Sim(spec, precision=precision)
+    s.step_form = "phases"
+    return s
+
+
 def _same(a, b, precision):
     sa, sb = a.scalars(), b.scalars()
     bad = []
@@ -62,7 +69,7 @@ def _same(a, b, precision):
 @pytest.mark.parametrize("precision", ["fp64", "fp32mix"])
 def test_batch_equals_runs_alone(precision):
     specs = _specs(5)
-    alone = [salec.Sim(s, precision=precision) for s in specs]
+    alone = [_alone(s, precision) for s in specs]
     for s in alone:
         s.step(30)
     runs = [salec.Sim(s, precision=precision) for s in specs]
@@ -75,9 +82,9 @@ def test_batch_equals_runs_alone(precision):
 def test_end_times_graph_replay_and_autotune():
     specs = _specs(4, seed0=200)
     runs = [salec.Sim(s, precision="fp32mix") for s in specs]
-    ref = [salec.Sim(s, precision="fp32mix") for s in specs]
+    ref = [_alone(s, "fp32mix") for s in specs]
     # end times reached after different step counts
-    probe = [salec.Sim(s, precision="fp32mix") for s in specs]
+    probe = [_alone(s, "fp32mix") for s in specs]
     t_end = []
     for k, p in enumerate(probe):
         p.step(20 + 7 * k)
@@ -121,7 +128,7 @@ def test_finished_runs_leave_and_rejoin_the_batch():
     the same run stepped alone."""
     specs = _specs(3, seed0=300)
     runs = [salec.Sim(s, precision="fp32mix") for s in specs]
-    probe = salec.Sim(specs[0], precision="fp32mix")
+    probe = _alone(specs[0], "fp32mix")
     probe.step(12)
     t12 = probe.scalars()["t"]
     probe.step(10)
