@@ -38,9 +38,32 @@ if ROOT not in sys.path:
 METRIC = "cell-updates/s per ALE step (FP64 vs FP32, % HBM roofline); batched runs/hour"
 UNIT = "cell-updates/s"
 
-# FP64 issue rate: 152 SMs x 2 DFMA/clk/SM x 2 flop x 2.07 GHz (the part's nominal
-# 1.25 TFLOP/s FP64); measured 1.19 TFLOP/s with a dependent-chain-free DFMA loop.
-FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12
+# FP64 issue rate of the part: 2 DFMA per clock per SM (its nominal 1.25 TFLOP/s at
+# 152 SMs and 2.07 GHz); the bench reads the SM count from the device and the clock from
+# nvidia-smi, and measures an FP64 GEMM (cuBLAS) as the attainable peak.
+DFMA_PER_CLK_PER_SM = 2
+
+
+def fp64_peaks(sm_max_mhz):
+    """(nominal TFLOP/s from the device's SM count and maximum clock, measured TFLOP/s of a
+    4096^3 FP64 GEMM, best of 5 by CUDA events)."""
+    import torch
+    sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+    nominal = sms * DFMA_PER_CLK_PER_SM * 2 * sm_max_mhz * 1e6 / 1e12
+    n = 4096
+    a = torch.rand((n, n), dtype=torch.float64, device="cuda")
+    b = torch.rand((n, n), dtype=torch.float64, device="cuda")
+    c = a @ b
+    best = 0.0
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    for _ in range(5):
+        e0.record()
+        torch.matmul(a, b, out=c)
+        e1.record()
+        torch.cuda.synchronize()
+        best = max(best, 2.0 * n ** 3 / (e0.elapsed_time(e1) * 1e-3) / 1e12)
+    del a, b, c
+    return sms, nominal, best
 
 # Algorithmic bytes per cell-update of each kernel (one material, hydrodynamic): the fields
 # each kernel must read and write once, e = element bytes (8 FP64, 4 mixed), energies 8.
@@ -52,6 +75,8 @@ def kernel_bytes_per_cell(e: int) -> dict:
         "k_phase3a": 2 * e + 2 * e + e + 8 + 2 * e + 8 + e + e,   # vL (fL,rhoL) VL IL -> (f,rho) I dMR dMZ
         "k_phase3b": e + e + 2 * e + e + e + 2 * e + e,           # dMR dMZ vL mv dK -> v kheat
         "k_phase3c": 2 * e + e + 8 + 8,                           # (f,rho) kheat I(rw)
+        # the fused cycle reads and writes the persistent state once (plus the Courant kernel)
+        "k_step_fused": step_bytes_per_cell(e),
     }
 
 
@@ -68,6 +93,14 @@ def _load_peaks():
         return float(d["hbm_gbs"]), "measured"
     except Exception:
         return 6800.0, "fallback"
+
+
+def _sm_max_mhz():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return float(json.load(fh)["sm_max_mhz"])
+    except Exception:
+        return 2070.0
 
 
 class ClockSampler:
@@ -169,20 +202,42 @@ def job_reduce(vals_max, vals_sum, device="cpu"):
     return mx.tolist(), sm.tolist()
 
 
-def batch_failures(polled, specs, half_diameters) -> list:
+def batch_failures(polled, specs, half_diameters, cavity_in_strip=None) -> list:
     """Counts of a batch's outcomes, in the order [non-positive volume or density, NaN, step
     below dt_min, failed runs with an iron projectile, with a basalt one, runs whose crater
-    rim reached the absorbing strip].  `polled` rows are (t, dt, steps, status, t_end);
-    `half_diameters` holds each run's crater half-width in metres (None for a failed run).
-    A run counts once per status bit it carries."""
+    rim reached the absorbing strip, failed runs whose transient cavity had reached an
+    absorbing strip, failed runs whose cavity had not].  `polled` rows are (t, dt, steps,
+    status, t_end); `half_diameters` holds each run's crater half-width in metres (None for
+    a failed run); `cavity_in_strip[k]` tells whether run k, where it stopped, has emptied
+    strip cells below its initial surface (None: not examined).  A run counts once per
+    status bit it carries."""
     import numpy as np
     st = np.asarray(polled)[:, 3].astype(np.int64)
     failed = st != 0
     iron = np.array([sp["materials"][-1]["rho0"] > 5000.0 for sp in specs], dtype=bool)
     at_pml = sum(1 for sp, h in zip(specs, half_diameters)
                  if h is not None and h >= (sp["grid"]["nr"] - sp["grid"]["pml_r"]) * sp["grid"]["dx"])
+    cav = [bool(c) for c in (cavity_in_strip or [None] * len(specs))]
+    in_strip = sum(1 for k in range(len(specs)) if failed[k] and cav[k])
     return [int(((st & 1) != 0).sum()), int(((st & 2) != 0).sum()), int(((st & 4) != 0).sum()),
-            int((failed & iron).sum()), int((failed & ~iron).sum()), int(at_pml)]
+            int((failed & iron).sum()), int((failed & ~iron).sum()), int(at_pml),
+            int(in_strip), int(failed.sum()) - int(in_strip)]
+
+
+def cavity_in_strip(phi, spec) -> bool:
+    """Whether the transient cavity has reached an absorbing strip: a strip cell (bottom
+    rows < pml_b, right columns >= nr - pml_r) below the initial surface holds less than
+    half matter.  The strips damp deviations from the initial state and are written for
+    small ones (Sect. 3); a run whose cavity reaches them is outside that regime."""
+    import numpy as np
+    g = spec["grid"]
+    nr, nz, pb, pr = g["nr"], g["nz"], g.get("pml_b", 0), g.get("pml_r", 0)
+    ks = int(round(spec["z_surface"] / g["dx"]))
+    strip = np.zeros((nz, nr), dtype=bool)
+    strip[:pb, :] = True
+    strip[:, nr - pr:] = True
+    strip[ks:, :] = False
+    return bool((np.asarray(phi)[strip] < 0.5).any())
 
 
 def _batched(args, rank, ws):
@@ -223,26 +278,33 @@ def _batched(args, rank, ws):
     polled = batch.poll()
     failed = polled[:, 3] != 0
     finished = (polled[:, 0] >= polled[:, 4]) | failed
+    completed = (polled[:, 0] >= polled[:, 4]) & ~failed
     cell_updates = float(sum(polled[k, 2] * specs[k]["grid"]["nr"] * specs[k]["grid"]["nz"] for k in range(len(specs))))
     st = polled[:, 3].astype(np.int64)
-    # read after the timed region: each clean run's crater half-width, for the strip flag
+    # read after the timed region: each clean run's crater half-width, for the strip flag,
+    # and where each failed run stopped, whether its cavity had reached a strip
     half = [None if failed[k] else 0.5 * sims[k].crater(sp["z_surface"], 64)["diameter"]
             for k, sp in enumerate(specs)]
-    causes = batch_failures(polled, specs, half)
-    (tmax,), (nfin, nfail, *causes) = job_reduce(
-        [wall], [int(finished.sum()), int(failed.sum())] + causes, "cuda")
-    nfin, nfail = int(nfin), int(nfail)
+    cav = [cavity_in_strip(sum(sims[k].get(f"f{m}") for m in range(len(sp["materials"]))), sp) if failed[k] else None
+           for k, sp in enumerate(specs)]
+    causes = batch_failures(polled, specs, half, cav)
+    (tmax,), (nfin, nfail, ncomp, *causes) = job_reduce(
+        [wall], [int(finished.sum()), int(failed.sum()), int(completed.sum())] + causes, "cuda")
+    nfin, nfail, ncomp = int(nfin), int(nfail), int(ncomp)
     out = {"runs": args.batch_runs, "t_end_s": args.batch_t_end, "precision": "FP32-mix",
-           "runs_finished": nfin, "runs_failed": nfail, "complete": nfin == args.batch_runs,
+           "runs_finished": nfin, "runs_failed": nfail, "runs_completed": ncomp, "complete": nfin == args.batch_runs,
            "wall_s": round(tmax, 2),
-           "runs_per_hour": nfin * 3600.0 / tmax if nfin == args.batch_runs else None,
+           # runs that reached t_end without a failure, per hour of the whole batch's wall time
+           "runs_per_hour": ncomp * 3600.0 / tmax if nfin == args.batch_runs else None,
            "cell_updates_per_s": cell_updates / wall, "batch_steps": int(steps), "cells_per_step": cells,
            "setup_s": round(setup_s, 1), "block_shapes": shapes, "runs_per_rank": len(specs),
            "crater_reached_pml": int(causes[5]),
            "failures": {"volume_or_density": int(causes[0]), "nan": int(causes[1]), "dt_min": int(causes[2]),
                         "iron_projectile": int(causes[3]), "basalt_projectile": int(causes[4]),
+                        "cavity_in_strip": int(causes[6]), "unexplained": int(causes[7]),
                         "rank0_first": [{"seed": int(seeds[k]), "n": specs[k]["grid"]["nr"], "status": int(st[k]),
-                                         "t_s": round(float(polled[k, 0]), 3), "steps": int(polled[k, 2])}
+                                         "t_s": round(float(polled[k, 0]), 3), "steps": int(polled[k, 2]),
+                                         "cavity_in_strip": cav[k]}
                                         for k in np.where(failed)[0][:16]]}}
     # reference: the plain FP64 solver, one run at a time, on the first draws that finished cleanly
     ok = [k for k in range(len(specs)) if finished[k] and not failed[k]][:args.batch_ref_runs]
@@ -433,6 +495,98 @@ def _layered(args):
     return out
 
 
+def peak_decay(pmax, rc, zc, z_surface, bin_width, nbins):
+    """Peak over-pressure against distance from the impact point (on the axis at the
+    surface), Sect. 4 of the paper: the largest recorded over-pressure of the cells in each
+    distance bin of width bin_width."""
+    import numpy as np
+    dist = np.hypot(np.asarray(rc)[None, :], np.asarray(zc)[:, None] - z_surface)
+    k = np.minimum((dist / bin_width).astype(np.int64), nbins)
+    out = np.zeros(nbins + 1)
+    np.maximum.at(out, k.ravel(), np.asarray(pmax).ravel())
+    return out[:nbins]
+
+
+def decay_errors(p32, p64, floor=0.01):
+    """Relative errors of a peak-pressure decay curve against the FP64 one, over the bins
+    whose FP64 peak is at least `floor` of the largest."""
+    import numpy as np
+    p32, p64 = np.asarray(p32), np.asarray(p64)
+    sel = p64 >= floor * p64.max()
+    e = np.abs(p32[sel] / p64[sel] - 1.0)
+    return {"bins": int(sel.sum()), "max": float(e.max()) if e.size else None, "mean": float(e.mean()) if e.size else None}
+
+
+def _fp32_accuracy(args):
+    """The mixed form's error against FP64 on the 4000 x 4000 physics (basalt, hydrodynamic,
+    10 m cells, 10 km/s) at 400 x 400 with a 10-cell projectile, run until a crater has
+    formed (t = 0.6 s, the simulated time of the large run's 2000 steps, and t = 2 s): crater
+    depth and diameter, and the peak-pressure decay with distance.  The FP64 GPU solver,
+    which matches the FP64 oracle to 1e-9, stands in for the oracle."""
+    import numpy as np
+    from paper_2403_04267_gb300 import salec, workloads as W
+    spec = W.scaled_plain(400, radius_cells=10)
+    g = spec["grid"]
+    rc = (np.arange(g["nr"]) + 0.5) * g["dx"]
+    zc = (np.arange(g["nz"]) + 0.5) * g["dx"]
+    sims = {p: salec.Sim(spec, precision=p) for p in ("fp64", "fp32mix")}
+    out = {"workload": "4000x4000 physics at 400x400, projectile radius 10 cells", "reference": "FP64 GPU solver",
+           "fp32_form": sims["fp32mix"].step_form}
+    for t_end in (0.6, 2.0):
+        res = {}
+        for p, sim in sims.items():
+            while sim.scalars()["t"] < t_end and sim.scalars()["status"] == 0:
+                sim.step(10)
+            sc = sim.scalars()
+            res[p] = (sim.crater(spec["z_surface"], 64), peak_decay(sim.get("pmax"), rc, zc, spec["z_surface"], g["dx"], 300), sc)
+        c32, c64 = res["fp32mix"][0], res["fp64"][0]
+        out[f"t={t_end}s"] = {
+            "t_fp64": res["fp64"][2]["t"], "t_fp32mix": res["fp32mix"][2]["t"],
+            "status": [res["fp64"][2]["status"], res["fp32mix"][2]["status"]],
+            "depth_m": [c32["depth"], c64["depth"]], "diameter_m": [c32["diameter"], c64["diameter"]],
+            "depth_rel_err": abs(c32["depth"] / c64["depth"] - 1) if c64["depth"] else None,
+            "diameter_rel_err": abs(c32["diameter"] / c64["diameter"] - 1) if c64["diameter"] else None,
+            "peak_pressure_decay_rel_err": decay_errors(res["fp32mix"][1], res["fp64"][1])}
+    del sims
+    return out
+
+
+def _active(args, hbm_peak):
+    """Throughput on a grid most of which moves: the 4000 x 4000 physics at 1600 x 1600
+    (state above L2 in both forms) with a 200-cell projectile, advanced 3000 steps before
+    the timed ones (the large run's first steps time an almost resting grid).  Both
+    precisions, each in its default step form; the fraction of moving vertices is stated."""
+    import numpy as np
+    import torch
+    from paper_2403_04267_gb300 import salec, workloads as W
+    spec = W.scaled_plain(1600, radius_cells=200)
+    cells = spec["grid"]["nr"] * spec["grid"]["nz"]
+    out = {"workload": "4000x4000 physics at 1600x1600, projectile radius 200 cells, after 3000 steps",
+           "cells": cells, "steps": args.active_steps}
+    for prec in ("fp64", "fp32mix"):
+        sim = salec.Sim(spec, precision=prec)
+        sim.step(3000)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(sim.stream)
+        sim.step(args.active_steps)
+        e1.record(sim.stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / args.active_steps
+        sc = sim.scalars()
+        moving = float((np.hypot(sim.get("vr"), sim.get("vz")) > 1.0).mean())
+        r = {"form": sim.step_form, "value": cells / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms, "sim_time_s": sc["t"],
+             "status": sc["status"], "moving_vertex_fraction": round(moving, 3)}
+        if prec == "fp32mix":
+            gbs = step_bytes_per_cell(4) * cells / (ms * 1e-3) / 1e9
+            r["step_hbm"] = {"achieved_gbs": round(gbs, 1), "peak_gbs": hbm_peak, "frac": round(gbs / hbm_peak, 4),
+                             "bytes_per_cell": step_bytes_per_cell(4)}
+        out[prec] = r
+        del sim
+        torch.cuda.empty_cache()
+    return out
+
+
 def run_reference(args):
     ws, rank, _ = _dist()
     if rank != 0:
@@ -474,18 +628,23 @@ def main():
     ap.add_argument("--cpu-steps", type=int, default=2)
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--precision", default="both", choices=["both", "fp64", "fp32mix"])
+    ap.add_argument("--form", default="default", choices=["default", "phases", "fused"],
+                    help="step form of the timed runs (default: the library's, the phase kernels)")
     ap.add_argument("--batch-runs", type=int, default=256)
     ap.add_argument("--batch-t-end", type=float, default=20.0)
-    ap.add_argument("--batch-ref-runs", type=int, default=8)
+    ap.add_argument("--batch-ref-runs", type=int, default=16)
     ap.add_argument("--batch-max-s", type=float, default=900.0)
     ap.add_argument("--batch-ref-max-s", type=float, default=300.0)
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--no-surrogate", action="store_true")
     ap.add_argument("--no-layered", action="store_true")
     ap.add_argument("--layered-steps", type=int, default=1000)
+    ap.add_argument("--active-steps", type=int, default=100)
+    ap.add_argument("--no-active", action="store_true")
+    ap.add_argument("--no-accuracy", action="store_true")
     ap.add_argument("--sur-members", type=int, default=4)
     ap.add_argument("--sur-steps", type=int, default=3000)
-    ap.add_argument("--sur-solver-runs", type=int, default=2)
+    ap.add_argument("--sur-solver-runs", type=int, default=8)
     ap.add_argument("--sur-infer-batch", type=int, default=65536)
     ap.add_argument("--sur-gate-target", type=float, default=0.95)
     args = ap.parse_args()
@@ -512,10 +671,13 @@ def main():
             dist.barrier()
         torch.cuda.synchronize()
 
-    def measure(precision, with_e2e):
+    def measure(precision, with_e2e, form=None):
         """Device-timed K steps from t = 0 (after W warm-up steps and a restore), with live
         per-kernel events; then optionally the same K steps end to end through the C ABI."""
         sim = salec.Sim(spec, precision=precision)
+        form = form or (None if args.form == "default" else args.form)
+        if form:
+            sim.step_form = form
         stream = sim.stream
         nbytes = sim.checkpoint_bytes()
         init = sim.state[:nbytes].clone()          # device copy of the initial state
@@ -523,6 +685,7 @@ def main():
         def restore():
             sim.state[:nbytes].copy_(init)
             torch.cuda.synchronize()
+            sim.state_changed()
 
         sim.step(args.warmup)
         torch.cuda.synchronize()
@@ -546,8 +709,10 @@ def main():
             dist.all_reduce(t, op=dist.ReduceOp.MAX)
             ms_max = float(t.item())
         out = {"value": ws * cells * args.steps / (ms_max * 1e-3), "ms": ms, "ms_max": ms_max, "ktimes": ktimes,
-               "scalars": sc, "clocks": clk.summary(), "launches": sim.launches_per_step() * args.steps,
-               "crater": sim.crater(spec["z_surface"], 64)}
+               "scalars": sc, "clocks": clk.summary(),
+               # a fused sequence after the restore starts with one pass of Courant rates
+               "launches": sim.launches_per_step() * args.steps + (1 if sim.step_form == "fused" else 0),
+               "form": sim.step_form, "pmax": sim.get("pmax")}
         if with_e2e:
             host = torch.empty(nbytes, dtype=torch.uint8, pin_memory=True)
             host.copy_(init.cpu())
@@ -588,6 +753,8 @@ def main():
 
     res64 = measure("fp64", not args.no_e2e) if args.precision in ("both", "fp64") else None
     res32 = measure("fp32mix", not args.no_e2e and args.precision == "fp32mix") if args.precision in ("both", "fp32mix") else None
+    # the mixed form's fused step (one tile kernel per cycle) beside the default phase kernels
+    res32f = measure("fp32mix", False, "fused") if args.precision == "both" and args.form == "default" else None
     if rank != 0:
         dist.destroy_process_group()
         return 0
@@ -596,14 +763,20 @@ def main():
     e_main = 8 if res64 is not None else 4
     roof_hbm, dom = roofline(main_res, e_main)
     if res64 is not None:
-        flops = _FLOPS_PER_CELL.get(dom)
+        clk = main_res["clocks"].get("sm_max_mhz") or _sm_max_mhz()
+        sms, fp64_nominal, fp64_gemm = fp64_peaks(clk)
+        stale = dom in _COUNTERS_STALE["fp64"]
+        flops = None if stale else _FLOPS_PER_CELL.get(dom)
         ach = flops * cells / (main_res["ktimes"][dom] * 1e-3) / 1e12 if flops else None
-        roof = {"bound": "alu", "kernel": dom, "unit": "TFLOP/s", "peak": round(FP64_PEAK_TFLOPS, 4),
-                "peak_kind": "nominal FP64 issue rate 152 SM x 2 DFMA/clk x 2.07 GHz (measured DFMA loop: 1.19)",
-                "achieved": round(ach, 4) if ach else None, "frac": round(ach / FP64_PEAK_TFLOPS, 4) if ach else None,
+        roof = {"bound": "alu", "kernel": dom, "unit": "TFLOP/s", "peak": round(fp64_gemm, 4),
+                "peak_kind": "measured FP64 GEMM (cuBLAS, 4096^3) on this GPU",
+                "peak_nominal": round(fp64_nominal, 4),
+                "peak_nominal_kind": f"{sms} SMs (device) x {DFMA_PER_CLK_PER_SM} DFMA/clk x 2 flop x {clk:.0f} MHz",
+                "achieved": round(ach, 4) if ach else None, "frac": round(ach / fp64_gemm, 4) if ach else None,
+                "frac_of_nominal": round(ach / fp64_nominal, 4) if ach else None,
                 "flops_per_cell": flops,
-                "traffic": None if dom in _COUNTERS_STALE["fp64"] else _TRAFFIC_PER_CELL.get(dom) and _TRAFFIC_PER_CELL[dom] * cells,
-                "counters_stale": dom in _COUNTERS_STALE["fp64"],
+                "traffic": None if stale else _TRAFFIC_PER_CELL.get(dom) and _TRAFFIC_PER_CELL[dom] * cells,
+                "counters_stale": stale,
                 "fp64_pipe_busy": _FP64_PIPE_BUSY.get(dom),
                 "note": "flops count 2 per DFMA and 1 per DADD/DMUL; the FP64 pipe issues every FP64 "
                         "instruction at the DFMA rate, and fp64_pipe_busy (ncu, 2000x2000) is its occupancy",
@@ -630,18 +803,39 @@ def main():
     }
     if res64 is not None and res32 is not None:
         r32, d32 = roofline(res32, 4)
-        c64, c32 = res64["crater"], res32["crater"]
+        # the peak-pressure decay of the two forms over the same K steps (Sect. 4)
+        g = spec["grid"]
+        rc = (np.arange(g["nr"]) + 0.5) * g["dx"]
+        zc = (np.arange(g["nz"]) + 0.5) * g["dx"]
+        dec = decay_errors(peak_decay(res32["pmax"], rc, zc, spec["z_surface"], g["dx"], 400),
+                           peak_decay(res64["pmax"], rc, zc, spec["z_surface"], g["dx"], 400))
         line["fp32_mix"] = {
             "value": res32["value"], "unit": UNIT, "ms_per_step": res32["ms_max"] / args.steps,
-            "speedup_vs_fp64": res32["value"] / res64["value"],
+            "speedup_vs_fp64": res32["value"] / res64["value"], "step_form": res32["form"],
             "kernel_ms": {k: round(v, 4) for k, v in res32["ktimes"].items()},
             "roofline": {"bound": "hbm", "kernel": d32, "unit": "GB/s", **r32["hbm"],
                          "traffic": None if d32 in _COUNTERS_STALE["fp32mix"] else
                          _TRAFFIC_PER_CELL_FP32MIX.get(d32) and _TRAFFIC_PER_CELL_FP32MIX[d32] * cells,
-                         "traffic_note": "DRAM read+write bytes per cell from ncu on 2000x2000, times the cells"},
+                         "traffic_note": "DRAM read+write bytes per cell from ncu (one kernel, 2000x2000), times the cells"},
             "step_hbm_frac": round(step_bytes_per_cell(4) * cells / (res32["ms"] / args.steps * 1e-3) / 1e9 / hbm_peak, 4),
-            "crater_vs_fp64": {"depth": [c32["depth"], c64["depth"]], "diameter": [c32["diameter"], c64["diameter"]]},
+            "peak_pressure_decay_vs_fp64_same_steps": dec,
             "gpu_launches": res32["launches"], "clocks": res32["clocks"], "status": res32["scalars"]["status"]}
+        if res32f is not None:
+            rf, df = roofline(res32f, 4)
+            line["fp32_mix"]["fused_form"] = {
+                "value": res32f["value"], "unit": UNIT, "ms_per_step": res32f["ms_max"] / args.steps,
+                "kernel_ms": {k: round(v, 4) for k, v in res32f["ktimes"].items()},
+                "roofline": {"bound": "hbm", "kernel": df, "unit": "GB/s", **rf["hbm"],
+                             "traffic": None if df in _COUNTERS_STALE["fp32mix"] else
+                             _TRAFFIC_PER_CELL_FP32MIX.get(df) and _TRAFFIC_PER_CELL_FP32MIX[df] * cells,
+                             "traffic_note": "DRAM read+write bytes per cell from ncu (one kernel, 2000x2000), times the cells"},
+                "step_hbm_frac": round(step_bytes_per_cell(4) * cells / (res32f["ms"] / args.steps * 1e-3) / 1e9 / hbm_peak, 4),
+                "gpu_launches": res32f["launches"], "status": res32f["scalars"]["status"],
+                "note": "bound by instruction issue, not HBM: each tile recomputes its 3-cell halo"}
+        if not args.no_accuracy and ws == 1:
+            line["fp32_mix"]["accuracy"] = _fp32_accuracy(args)
+    if not args.no_active and ws == 1:
+        line["active_grid"] = _active(args, hbm_peak)
     if not args.no_layered and ws == 1:
         line["layered"] = _layered(args)
     if not args.no_batch and args.batch_runs > 0:
@@ -665,10 +859,10 @@ _TRAFFIC_PER_CELL_FP32MIX: dict = {"k_phase0": 27.9, "k_phase1": 31.5, "k_phase2
 # fraction of the FP64 pipe's issue slots each FP64-form kernel keeps busy (ncu,
 # sm__pipe_fp64_cycles_active on the 2000 x 2000 case)
 _FP64_PIPE_BUSY: dict = {"k_phase0": 0.854, "k_phase1": 0.862, "k_phase2": 0.859, "k_phase3a": 0.858, "k_phase3b": 0.841, "k_phase3c": 0.789}
-# kernels changed since their counters were taken: no DRAM traffic is reported for them
-# until the next capture (phase 0's equation of state gained the density-floor branch, a
-# warp-uniform test of registers only; its FP64 count holds where no cell is that dilute)
-_COUNTERS_STALE: dict = {"fp64": {"k_phase0"}, "fp32mix": {"k_phase0"}}
+# kernels changed since their counters were taken: neither DRAM traffic nor flop rates are
+# reported for them until the next capture
+_COUNTERS_STALE: dict = {"fp64": {"k_phase0", "k_phase1", "k_phase2", "k_phase3a", "k_step_fused"},
+                         "fp32mix": {"k_phase0", "k_phase1", "k_phase2", "k_phase3a", "k_step_fused"}}
 
 if __name__ == "__main__":
     sys.exit(main())

@@ -62,7 +62,8 @@ def test_single_process_is_a_no_op():
 def test_batch_failures_counts_causes():
     """The batched leg's outcome counts: one count per status bit (1 non-positive volume or
     density, 2 NaN, 4 step below dt_min), failed runs split by projectile, and clean runs
-    whose crater half-width reaches the absorbing strip (nr - pml_r cells from the axis)."""
+    whose crater half-width reaches the absorbing strip (nr - pml_r cells from the axis),
+    and failed runs split by whether their cavity had reached a strip."""
     import numpy as np
     sys.path.insert(0, ROOT)
     import bench
@@ -78,5 +79,32 @@ def test_batch_failures_counts_causes():
     status = [0, 1, 5, 2, 0, 0]
     polled = np.array([[20.0, 1e-3, 100, s, 20.0] for s in status])
     half = [strip, None, None, None, strip - 1.0, strip + 5.0]
-    assert bench.batch_failures(polled, specs, half) == [2, 1, 1, 1, 2, 2]
-    assert bench.batch_failures(np.zeros((0, 5)), [], []) == [0, 0, 0, 0, 0, 0]
+    assert bench.batch_failures(polled, specs, half) == [2, 1, 1, 1, 2, 2, 0, 3]
+    # failed runs 1 and 3 stopped with their cavity in a strip, run 2 did not
+    cav = [None, True, False, True, None, None]
+    assert bench.batch_failures(polled, specs, half, cav) == [2, 1, 1, 1, 2, 2, 2, 1]
+    assert bench.batch_failures(np.zeros((0, 5)), [], []) == [0, 0, 0, 0, 0, 0, 0, 0]
+
+
+def test_cavity_in_strip_reads_the_strip_cells_below_the_surface():
+    """A strip cell below the initial surface with less than half matter marks the run;
+    emptied cells above the surface, or inside the domain, do not."""
+    import numpy as np
+    sys.path.insert(0, ROOT)
+    import bench
+    from paper_2403_04267_gb300 import workloads as W
+    sp = W.batched_run(W.batched_draw(7), 120)
+    g = sp["grid"]
+    nr, nz, pb, pr = g["nr"], g["nz"], g["pml_b"], g["pml_r"]
+    ks = int(round(sp["z_surface"] / g["dx"]))
+    phi = np.zeros((nz, nr))
+    phi[:ks, :] = 1.0
+    assert not bench.cavity_in_strip(phi, sp)
+    cav = phi.copy()
+    cav[pb + 5:ks, :10] = 0.0                     # a deep cavity inside the domain
+    assert not bench.cavity_in_strip(cav, sp)
+    cav[pb - 1, 3] = 0.3                          # it reaches the bottom strip
+    assert bench.cavity_in_strip(cav, sp)
+    side = phi.copy()
+    side[ks - 3, nr - pr] = 0.0                   # the crater rim reaches the right strip
+    assert bench.cavity_in_strip(side, sp)
