@@ -887,7 +887,8 @@ static void phase2_cell(orc_sim* s)
                 if (!(fm > 0.0)) { s->fL[m][c] = 0.0; s->rhoL[m][c] = 0.0; continue; }
                 double Vm = fm * V;
                 double VmL = Vm + (fm / phi) * dVmat;
-                if (!(VmL > 0.0)) s->status |= 1;
+                /* status: a present material with a non-positive Lagrangian volume or density */
+                if (!(VmL > 0.0) || !(s->rho[m][c] > 0.0)) s->status |= 1;
                 s->rhoL[m][c] = s->rho[m][c] * (Vm / VmL);
                 s->fL[m][c] = VmL / VL;
             }

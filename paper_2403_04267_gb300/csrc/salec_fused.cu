@@ -467,7 +467,7 @@ __global__ void __launch_bounds__(NT, MINB) k_step_fused(const ParamsT<T> P, con
             if (pos(fr.x)) {
                 const T Vm = fr.x * Vc;
                 const T VmL = NM == 1 ? Vm + dVmat : Vm + fr.x / phi * dVmat;
-                bad |= !pos(VmL);
+                bad |= !pos(VmL) || !pos(fr.y);     // non-positive Lagrangian volume or density
                 // unchanged volume: V_m / V_m^L is exactly 1 (no division)
                 s_frL[m][kc] = V::mk(VmL / VLc, warp_any(nonzero(dV)) ? fr.y * (Vm / VmL) : fr.y);
                 if (STR && P.mat[m].strength == SALEC_STRENGTH_COLLINS) {

@@ -326,7 +326,7 @@ __device__ __forceinline__ void body_phase2(const ParamsT<T>& P, int bx, int by,
             const T Vm = fr.x * Vc;
             // one material: f_m / Phi = 1; true divisions keep a resting cell exact
             const T VmL = NM == 1 ? Vm + dVmat : Vm + fr.x / phi * dVmat;
-            bad |= !pos(VmL);
+            bad |= !pos(VmL) || !pos(fr.y);     // non-positive Lagrangian volume or density
             // unchanged volume: V_m / V_m^L is exactly 1 (no division)
             p.frL[m][c] = V::mk(VmL / VLc, warp_any(nonzero(dV)) ? fr.y * (Vm / VmL) : fr.y);
             if (STR && P.mat[m].strength == SALEC_STRENGTH_COLLINS) {
