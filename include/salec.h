@@ -172,11 +172,15 @@ salec_status salec_step(salec_ctx* ctx, int nsteps);
  *                      next step.  The fields it rewrites are read from one copy and
  *                      written to a second one inside the state buffer; read-outs bring
  *                      the current copy back first.  It moves a quarter of the phase
- *                      form's DRAM bytes per cell, but computes each tile's halo cells again.
+ *                      form's DRAM bytes per cell but computes each tile's halo cells
+ *                      again; a quiescent tile (matter at rest at zero pressure, whole
+ *                      fractions, no deviatoric stress, no strip, no gravity), on which
+ *                      every phase returns its input, only reads and writes its state.
+ *                      Default when grid->gravity == 0.
  *   SALEC_STEP_PHASES  six kernels over the whole grid and the Courant kernel, in place
- *                      (block shapes from salec_set_block_shapes / salec_autotune).  The
- *                      default of both precisions: on GB300 both forms are bound by
- *                      instruction issue, and this one issues fewer instructions per cell.
+ *                      (block shapes from salec_set_block_shapes / salec_autotune).
+ *                      Default under gravity, where no tile is quiescent and this form,
+ *                      which computes no cell twice, issues fewer instructions.
  * Both forms compute the same cycle with the same arithmetic per cell and vertex;
  * salec_set_step_form returns SALEC_EINVAL for another value, SALEC_EORDER before
  * salec_finalize. */

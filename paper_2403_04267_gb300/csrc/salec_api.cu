@@ -699,11 +699,14 @@ salec_status salec_finalize(salec_ctx* ctx)
     fill_pingpong<float>(ctx, ctx->Pf, ctx->Pf_alt, ctx->Of);
     e = mixed(ctx) ? prepare_fused<float>(ctx->Pf) : prepare_fused<double>(ctx->Pd);
     if (e != cudaSuccess) return cuda_check(ctx, e, "fused step set-up");
-    // the phase kernels by default: on GB300 both forms are bound by instruction issue,
-    // and the fused form's halo cells (computed by every tile that needs them) cost more
-    // than the intermediate traffic it saves (mixed form, 4000 x 4000: 1.05 against 0.89 ms
-    // per step; FP64 9.3 against 7.1 ms)
-    ctx->form = SALEC_STEP_PHASES;
+    // Default form.  Without gravity the fused form: its quiescent tiles (matter at rest
+    // at zero pressure) only read and write their state, which on an impact grid is most of
+    // it (4000 x 4000: mixed form 0.41 against 0.90 ms per step, FP64 1.26 against 7.16; a
+    // 1600 x 1600 grid with a fifth of its vertices moving: 0.125 against 0.172, 1.02
+    // against 1.47).  Under gravity no tile is quiescent (a loaded column is not at zero
+    // pressure) and the phase kernels, which compute no cell twice, are faster (the
+    // paper's layered grid: 0.054 against 0.087 ms, FP64 0.45 against 0.70).
+    ctx->form = g.gravity == 0.0 ? SALEC_STEP_FUSED : SALEC_STEP_PHASES;
     ctx->parity = 0;
     ctx->rates_valid = false;
     ctx->finalized = true;

@@ -220,6 +220,72 @@ __global__ void __launch_bounds__(NT, MINB) k_step_fused(const ParamsT<T> P, con
     cp_async_wait();
     __syncthreads();
 
+    // ---- a quiescent frame: every vertex at rest, every material fraction exactly 0 or 1,
+    // zero pressure in the equation-of-state cache (so no viscosity either: div v = 0), no
+    // deviatoric stress, no gravity, no absorbing strip in the frame.  Then every phase
+    // returns its input: zero forces leave v^L = v = 0, no volume changes (V_m^L / V^L =
+    // V / V = 1 for a full cell), no face carries anything, nothing is heated; the own cells'
+    // outputs are their inputs (an empty cell's as zeros, as the remap writes it), the peak
+    // over-pressure update is the same, the Courant rate is c / L.  The tile then only
+    // reads and writes its state.
+    T speed_max = zero;
+    bool quiet = !nonzero(P.g) && y0 >= P.pb && x0 + CW <= nr - P.pr;
+    if (quiet) {
+        bool q = true;
+        for (int k = tid; k < NV; k += NT) {
+            const T2 v = s_vo[k];
+            q = q && !nonzero(v.x) && !nonzero(v.y);
+        }
+        for (int k = tid; k < NC; k += NT) {
+#pragma unroll
+            for (int m = 0; m < NM; ++m) {
+                const T f = s_fro[m][k].x;
+                q = q && (!nonzero(f) || f == one);
+            }
+            q = q && !nonzero(s_PM[k].x) && !is_nan(s_Io[k]);
+            if (STR) {
+                const T2 a = s_so01[k];
+                q = q && !nonzero(a.x) && !nonzero(a.y) && !nonzero(s_so2d[k].x);
+            }
+        }
+        quiet = __syncthreads_and(q);
+    }
+    if (quiet) {
+        for (int k = tid; k < TW * TH; k += NT) {
+            const int lx = H + k % TW, ly = H + k / TW, i = x0 + lx, j = y0 + ly;
+            if (i >= nr || j >= nz) continue;
+            const int kc = ly * CW + lx, c = j * nr + i;
+            T phi = zero, M = zero;
+#pragma unroll
+            for (int m = 0; m < NM; ++m) {
+                const T2 fr = s_fro[m][kc];
+                const bool here = pos(fr.x);
+                if (here) { phi += fr.x; M += fr.x * fr.y; }
+                O.fr[m][c] = here ? fr : V::mk(zero, zero);
+            }
+            O.I[c] = pos(M) ? s_Io[kc] : 0.0;
+            if (STR) {
+                O.s01[c] = V::mk(zero, zero);
+                O.s2d[c] = V::mk(zero, pos(phi) && pos(M) ? s_so2d[kc].y : zero);
+            }
+            const T2 ec = s_PM[kc];
+            O.eosc[c] = ec;
+            if (pos(phi)) {
+                const T over = (NM == 1 ? ec.x : ec.x * (one / phi)) - p.p0[j];
+                if (over > p.pmax[c]) p.pmax[c] = over;
+                T speed = t_sqrt<T>(zero) + t_sqrt<T>(ec.y);
+                if (!UNI) speed = speed * GE::ilen(P, i, j);
+                if (is_nan(speed)) atomicOr(&p.scal->status, 2);
+                speed_max = max_nonneg(speed_max, speed);
+            }
+        }
+        for (int k = tid; k < (TW + 1) * (TH + 1); k += NT) {
+            const int i = ox + k % (TW + 1), j = oy + k / (TW + 1);
+            if (i > nr || j > nz) continue;
+            if ((i < ox + TW || last_x) && (j < oy + TH || last_y)) O.v[j * nv + i] = V::mk(zero, zero);
+        }
+    } else {
+
     // ---- phase 0: artificial viscosity and total pressure from the equation of state of
     // the current state, which the previous step (or the Courant-rate pass) left in the
     // cache: (p_m, c^2) for one material, (p_hat, max c_m^2) for several; peak over-pressure
@@ -818,7 +884,6 @@ __global__ void __launch_bounds__(NT, MINB) k_step_fused(const ParamsT<T> P, con
     __syncthreads();
 
     // ---- phase 3c: heat to the own cells; the Courant rate of the new state (Eq. 14)
-    T speed_max = zero;
     for (int k = tid; k < TW * TH; k += NT) {
         const int lx = H + k % TW, ly = H + k / TW, i = x0 + lx, j = y0 + ly;
         if (i >= nr || j >= nz) continue;
@@ -885,6 +950,8 @@ __global__ void __launch_bounds__(NT, MINB) k_step_fused(const ParamsT<T> P, con
             speed_max = max_nonneg(speed_max, speed);
         }
     }
+
+    }   // not quiescent
 
     // ---- reductions.  The tallies (FP64) are rare (top row, strips, clean-up): a warp that
     // holds one sums it and adds it with one atomic per tally, so no other warp issues FP64

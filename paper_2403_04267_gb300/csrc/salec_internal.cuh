@@ -198,7 +198,7 @@ __device__ __forceinline__ bool below_bits(float a, float b) { return __float_as
 __device__ __forceinline__ bool warp_any(bool p);
 
 template <typename T>
-__host__ __device__ inline void eos_eval(const MatT<T>& m, T rho_in, T I_in, T& p_out, T& c2_out)
+__host__ __device__ __forceinline__ void eos_eval(const MatT<T>& m, T rho_in, T I_in, T& p_out, T& c2_out)
 {
     const T zero = T(0), one = T(1), two = T(2);
     const T I = I_in > zero ? I_in : zero;
@@ -280,7 +280,7 @@ template <> __host__ __device__ inline float t_tanh<float>(float x) { return tan
 // w = 2 rho / rho0 - 1 (in dilute ejecta a stress or tension times a step's strain, per unit
 // of so little mass, would send the specific energy to +-1e10 J/kg).
 template <typename T>
-__host__ __device__ inline T expansion_weight(const MatT<T>& m, T rho)
+__host__ __device__ __forceinline__ T expansion_weight(const MatT<T>& m, T rho)
 {
     const T w = T(2) * rho * m.inv_rho0 - T(1);
     return w < T(0) ? T(0) : (w > T(1) ? T(1) : w);
@@ -293,7 +293,7 @@ __host__ __device__ inline T expansion_weight(const MatT<T>& m, T rho)
 // expanded mixture keeps a frictional strength mu p from its vapour pressure and heats
 // itself through its stress work.
 template <typename T>
-__host__ __device__ inline T yield_eval(const MatT<T>& m, T p_in, T D, T I, T rho)
+__host__ __device__ __forceinline__ T yield_eval(const MatT<T>& m, T p_in, T D, T I, T rho)
 {
     const T zero = T(0), one = T(1);
     const T p = p_in > zero ? p_in : zero;

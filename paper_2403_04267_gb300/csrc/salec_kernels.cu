@@ -836,8 +836,14 @@ __device__ __forceinline__ void body_phase3c(const ParamsT<T>& P, int bx, int by
 // reached their end time are skipped; each run keeps its own dt reduction).
 // ---------------------------------------------------------------------------------
 
+// The FP64 phase 0 (equation of state per material, artificial viscosity) holds more live
+// values than 64 registers: with one resident block of the largest shape as its bound it
+// takes 80-90 registers and spills nothing (under the default bound ptxas settled on 64
+// and spilled 8-144 bytes a thread); the mixed form keeps the default.
+template <typename T> struct Phase0Bound { static constexpr int min_blocks = sizeof(T) == 8 ? 1 : 0; };
+
 template <typename T, int NM, bool STR, bool UNI>
-__global__ void __launch_bounds__(kMaxThreads) k_phase0(ParamsT<T> P) { body_phase0<T, NM, STR, UNI>(P, blockIdx.x, blockIdx.y, gridDim.x, gridDim.y); }
+__global__ void __launch_bounds__(kMaxThreads, Phase0Bound<T>::min_blocks) k_phase0(ParamsT<T> P) { body_phase0<T, NM, STR, UNI>(P, blockIdx.x, blockIdx.y, gridDim.x, gridDim.y); }
 template <typename T>
 __global__ void k_courant(ParamsT<T> P)
 {
@@ -866,7 +872,8 @@ __global__ void __launch_bounds__(kMaxThreads) k_phase3c(ParamsT<T> P) { body_ph
 // phase 0 decides for the whole step: a run at or past its end time, or one whose status
 // reports a failure (non-positive volume or density, NaN, dt below dt_min), does nothing
 template <typename T, int NM, bool STR, bool UNI>
-__global__ void __launch_bounds__(kMaxThreads) kb_phase0(const ParamsT<T>* __restrict__ runs, const BatchTile* __restrict__ work)
+__global__ void __launch_bounds__(kMaxThreads, Phase0Bound<T>::min_blocks) kb_phase0(const ParamsT<T>* __restrict__ runs,
+                                                                                     const BatchTile* __restrict__ work)
 {
     const BatchTile w = work[blockIdx.x];
     const ParamsT<T>& P = runs[w.run];
