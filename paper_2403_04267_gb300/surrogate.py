@@ -244,10 +244,28 @@ def train(X, T, steps: int = 4000, lr: float = 2e-3, seed: int = 0, batch_max: i
     return net
 
 
-# weights of the outputs in the squared-error loss: transient depth and diameter, the two
-# numbers a cratering study reads, count 16x a profile point (targets scaled by 4)
+# What the network regresses: the 64-point profile in units of DEPTH_SCALE metres, and the
+# logarithms of the transient depth and the diameter (the two numbers a cratering study reads;
+# a squared error in their logarithm is a squared relative error, the measure the surrogate is
+# judged by).  Their weight in the squared-error loss: 10 (a 1 % error costs what a 10 m error
+# at every profile point costs together).
 OUT_WEIGHT = np.ones(N_OUT, dtype=np.float32)
-OUT_WEIGHT[N_PROFILE:] = 4.0
+OUT_WEIGHT[N_PROFILE:] = 10.0
+LOG_FLOOR = 1e-3             # smallest depth or diameter (DEPTH_SCALE units) taken as its log
+
+
+def to_network(T) -> np.ndarray:
+    """Targets (outputs of `targets`) in the network's weighted output space."""
+    Tn = np.array(T, dtype=np.float64, copy=True)
+    Tn[:, N_PROFILE:] = np.log(np.maximum(Tn[:, N_PROFILE:], LOG_FLOOR))
+    return (Tn * OUT_WEIGHT).astype(np.float32)
+
+
+def from_network(Y) -> np.ndarray:
+    """Inverse of to_network: network outputs back to the units of `targets`."""
+    Y = np.asarray(Y, dtype=np.float64) / OUT_WEIGHT
+    Y[..., N_PROFILE:] = np.exp(Y[..., N_PROFILE:])
+    return Y
 
 
 class Ensemble:
@@ -256,17 +274,19 @@ class Ensemble:
     prediction is trusted or the draw goes to the solver."""
 
     def __init__(self, X, T, members: int = 4, steps: int = 4000, lr: float = 2e-3, log=None):
-        Tw = np.asarray(T, dtype=np.float32) * OUT_WEIGHT
+        Tw = to_network(T)
         self.nets = [train(X, Tw, steps=steps, lr=lr, seed=1000 + k, log=log) for k in range(members)]
 
     def predict(self, X):
-        """(mean outputs, relative spread of transient depth, of diameter) for inputs X."""
+        """(mean outputs, relative spread of transient depth, of diameter) for inputs X: the
+        members' mean in the units of `targets`, and the largest relative departure of a
+        member from it."""
         import torch
         Xd = torch.from_numpy(np.ascontiguousarray(X, dtype=np.float32)).cuda()
         outs = [net.forward(Xd) for net in self.nets]
         for net in self.nets:
             net.stream.synchronize()
-        ys = np.stack([y.cpu().numpy().astype(np.float64) / OUT_WEIGHT for y in outs])
+        ys = np.stack([from_network(y.cpu().numpy()) for y in outs])
         mean = ys.mean(axis=0)
         sd = np.max(np.abs(ys - mean), axis=0)
         rel_d = sd[:, N_PROFILE] / np.maximum(np.abs(mean[:, N_PROFILE]), 1e-9)
