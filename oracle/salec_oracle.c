@@ -631,7 +631,7 @@ static void phase0_eos_dt(orc_sim* s)
             int vv[4] = {VID(s, i, j), VID(s, i + 1, j), VID(s, i + 1, j + 1), VID(s, i, j + 1)};
             for (int k = 0; k < 4; ++k) {
                 double u2 = s->vr[vv[k]] * s->vr[vv[k]] + s->vz[vv[k]] * s->vz[vv[k]];
-                if (u2 > w) w = u2;
+                if (!(u2 <= w)) w = u2;     /* the larger speed; a NaN speed is kept (failure) */
             }
             double cand = dx / (sqrt(w) + cs);
             if (cand != cand) s->status |= 2;
