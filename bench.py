@@ -77,6 +77,9 @@ def kernel_bytes_per_cell(e: int) -> dict:
         "k_phase3c": 2 * e + e + 8 + 8,                           # (f,rho) kheat I(rw)
         # the fused cycle reads and writes the persistent state once (plus the Courant kernel)
         "k_step_fused": step_bytes_per_cell(e),
+        # a tile at rest: (f, rho), I and the EoS cache (p, c^2) read and written, vertices
+        # written (at rest): the same count as the state's
+        "k_rest_tiles": 2 * (2 * e + 8 + 2 * e) + 2 * e,
     }
 
 
@@ -577,6 +580,9 @@ def _active(args, hbm_peak):
         moving = float((np.hypot(sim.get("vr"), sim.get("vz")) > 1.0).mean())
         r = {"form": sim.step_form, "value": cells / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms, "sim_time_s": sc["t"],
              "status": sc["status"], "moving_vertex_fraction": round(moving, 3)}
+        if sim.step_form == "fused":
+            q, t = sim.fused_queue()
+            r["tiles_queued_last_step"] = [q, t]
         if prec == "fp32mix":
             gbs = step_bytes_per_cell(4) * cells / (ms * 1e-3) / 1e9
             r["step_hbm"] = {"achieved_gbs": round(gbs, 1), "peak_gbs": hbm_peak, "frac": round(gbs / hbm_peak, 4),
@@ -703,6 +709,18 @@ def main():
         ktimes, _ = sim.kernel_times()
         sim.set_kernel_timing(False)
         sc = sim.scalars()
+        queue = None
+        if sim.step_form == "fused":
+            # the same K steps again, untimed, one call each: how many tiles each step ran
+            # through the whole cycle (the others the rest-tile kernel copied)
+            restore()
+            qs = []
+            for _ in range(args.steps):
+                sim.step(1)
+                qs.append(sim.fused_queue()[0])
+            tiles = sim.fused_queue()[1]
+            queue = {"tiles": tiles, "queued_mean": float(np.mean(qs)), "queued_first": qs[0], "queued_last": qs[-1],
+                     "note": "the first step after the restore queues every tile (no tile is yet known to be at rest)"}
         ms_max = ms
         if ws > 1:
             t = torch.tensor([ms], device="cuda", dtype=torch.float64)
@@ -712,7 +730,7 @@ def main():
                "scalars": sc, "clocks": clk.summary(),
                # a fused sequence after the restore starts with one pass of Courant rates
                "launches": sim.launches_per_step() * args.steps + (1 if sim.step_form == "fused" else 0),
-               "form": sim.step_form, "pmax": sim.get("pmax")}
+               "form": sim.step_form, "pmax": sim.get("pmax"), "queue": queue}
         if with_e2e:
             host = torch.empty(nbytes, dtype=torch.uint8, pin_memory=True)
             host.copy_(init.cpu())
@@ -742,13 +760,22 @@ def main():
 
     hbm_peak, peak_kind = _load_peaks()
 
-    def roofline(res, e):
+    def roofline(res, e, dom=None):
         kt = res["ktimes"]
-        dom = max(kt, key=kt.get)
+        dom = dom or max(kt, key=kt.get)
         kb = kernel_bytes_per_cell(e)
-        gbs = kb[dom] * cells / (kt[dom] * 1e-3) / 1e9
+        # cells one launch processes: every cell for a phase kernel; in the fused form the
+        # cells of the tiles at rest (rest-tile kernel) or of the queued tiles (tile kernel),
+        # averaged over the K steps
+        units = float(cells)
+        q = res.get("queue")
+        if q:
+            qf = q["queued_mean"] / q["tiles"]
+            units = cells * (1.0 - qf if dom == "k_rest_tiles" else qf)
+        gbs = kb[dom] * units / (kt[dom] * 1e-3) / 1e9
         roof = {"kernel": dom, "hbm": {"achieved_gbs": round(gbs, 1), "peak_gbs": hbm_peak, "peak_kind": peak_kind,
-                                       "frac": round(gbs / hbm_peak, 4), "bytes_per_cell": kb[dom]}}
+                                       "frac": round(gbs / hbm_peak, 4), "bytes_per_cell": kb[dom],
+                                       "cells_per_launch": round(units)}}
         return roof, dom
 
     res64 = measure("fp64", not args.no_e2e) if args.precision in ("both", "fp64") else None
@@ -765,42 +792,61 @@ def main():
 
     main_res = res64 if res64 is not None else res32
     e_main = 8 if res64 is not None else 4
+    prec_main = "fp64" if res64 is not None else "fp32mix"
     roof_hbm, dom = roofline(main_res, e_main)
+
+    def hbm_roof(r, d, prec):
+        h = r["hbm"]
+        tr, trk = _traffic(d, prec, args)
+        return {"bound": "hbm", "kernel": d, "unit": "GB/s", "achieved": h["achieved_gbs"], "peak": hbm_peak,
+                "frac": h["frac"], "peak_kind": peak_kind, "bytes_per_cell": h["bytes_per_cell"],
+                "cells_per_launch": h["cells_per_launch"], "traffic": tr, "traffic_kind": trk}
+
     fp64_alu = None
     if res64 is not None:
         clk = main_res["clocks"].get("sm_max_mhz") or _sm_max_mhz()
         sms, fp64_nominal, fp64_gemm = fp64_peaks(clk)
-        stale = dom in _COUNTERS_STALE["fp64"]
-        flops = None if stale else _FLOPS_PER_CELL.get(dom)
-        ach = flops * cells / (main_res["ktimes"][dom] * 1e-3) / 1e12 if flops else None
-        roof = {"bound": "alu", "kernel": dom, "unit": "TFLOP/s", "peak": round(fp64_gemm, 4),
-                "peak_kind": "measured FP64 GEMM (cuBLAS, 4096^3) on this GPU",
-                "peak_nominal": round(fp64_nominal, 4),
-                "peak_nominal_kind": f"{sms} SMs (device) x {DFMA_PER_CLK_PER_SM} DFMA/clk x 2 flop x {clk:.0f} MHz",
-                "achieved": round(ach, 4) if ach else None, "frac": round(ach / fp64_gemm, 4) if ach else None,
-                "frac_of_nominal": round(ach / fp64_nominal, 4) if ach else None,
-                "flops_per_cell": flops,
-                "traffic": None if stale else _TRAFFIC_PER_CELL.get(dom) and _TRAFFIC_PER_CELL[dom] * cells,
-                "counters_stale": stale,
-                "fp64_pipe_busy": _FP64_PIPE_BUSY.get(dom),
-                "note": "flops count 2 per DFMA and 1 per DADD/DMUL; the FP64 pipe issues every FP64 "
-                        "instruction at the DFMA rate, and fp64_pipe_busy (ncu, 2000x2000) is its occupancy",
-                "hbm": roof_hbm["hbm"]}
-        if dom == "k_step_fused":
-            # the tile kernel: most tiles of the grid only read and write their state, so the
-            # bound it is held to is HBM (the state's algorithmic bytes); the FP64-pipe figures
-            # stay beside it
-            fp64_alu = roof
-            h = roof_hbm["hbm"]
-            stale32 = dom in _COUNTERS_STALE["fp64"]
-            roof = {"bound": "hbm", "kernel": dom, "unit": "GB/s", "achieved": h["achieved_gbs"], "peak": hbm_peak,
-                    "frac": h["frac"], "peak_kind": peak_kind, "bytes_per_cell": h["bytes_per_cell"],
-                    "traffic": None if stale32 else _TRAFFIC_PER_CELL.get(dom) and _TRAFFIC_PER_CELL[dom] * cells,
-                    "counters_stale": stale32}
+
+        def alu_roof(d):
+            kt = main_res["ktimes"][d]
+            if d in _FUSED_FULL_SIZE.get("fp64", {}):
+                full = _FUSED_FULL_SIZE["fp64"][d] if (args.workload, args.steps) == _FULL_SIZE_CASE else {}
+                flops = full.get("flops")
+                ach = flops / (kt * 1e-3) / 1e12 if flops else None
+                per = {"flops_per_launch": flops, "flops_kind": "ncu FP64 instruction counts of the same 20 launches "
+                       "(large_4000 from t = 0), mean per launch" if flops else "not captured for this workload / K"}
+            else:
+                stale = d in _COUNTERS_STALE["fp64"]
+                flops = None if stale else _FLOPS_PER_CELL.get(d)
+                ach = flops * cells / (kt * 1e-3) / 1e12 if flops else None
+                per = {"flops_per_cell": flops, "counters_stale": stale}
+            tr, trk = _traffic(d, "fp64", args)
+            return {"bound": "alu", "kernel": d, "unit": "TFLOP/s", "peak": round(fp64_gemm, 4),
+                    "peak_kind": "measured FP64 GEMM (cuBLAS, 4096^3) on this GPU",
+                    "peak_nominal": round(fp64_nominal, 4),
+                    "peak_nominal_kind": f"{sms} SMs (device) x {DFMA_PER_CLK_PER_SM} DFMA/clk x 2 flop x {clk:.0f} MHz",
+                    "achieved": round(ach, 4) if ach else None, "frac": round(ach / fp64_gemm, 4) if ach else None,
+                    "frac_of_nominal": round(ach / fp64_nominal, 4) if ach else None, **per,
+                    "traffic": tr, "traffic_kind": trk, "fp64_pipe_busy": _FP64_PIPE_BUSY.get(d),
+                    "note": "flops count 2 per DFMA and 1 per DADD/DMUL; the FP64 pipe issues every FP64 "
+                            "instruction at the DFMA rate, and fp64_pipe_busy (ncu, 2000x2000) is its occupancy"}
+
+        if dom == "k_rest_tiles":
+            # the tiles at rest dominate: a copy of the state, held to HBM
+            roof = hbm_roof(roof_hbm, dom, "fp64")
+            if "k_step_fused" in main_res["ktimes"]:
+                fp64_alu = alu_roof("k_step_fused")
+        else:
+            roof = alu_roof(dom)
+            roof["hbm"] = roof_hbm["hbm"]
+        if "k_rest_tiles" in main_res["ktimes"] and dom != "k_rest_tiles":
+            rr, _ = roofline(main_res, e_main, "k_rest_tiles")
+            line_rest = hbm_roof(rr, "k_rest_tiles", "fp64")
+        else:
+            line_rest = None
     else:
-        h = roof_hbm["hbm"]
-        roof = {"bound": "hbm", "kernel": dom, "unit": "GB/s", "achieved": h["achieved_gbs"], "peak": hbm_peak,
-                "frac": h["frac"], "traffic": None, "peak_kind": peak_kind}
+        roof = hbm_roof(roof_hbm, dom, "fp32mix")
+        line_rest = None
     ms = main_res["ms"]
     sc = main_res["scalars"]
     line = {
@@ -819,6 +865,10 @@ def main():
     }
     if fp64_alu is not None:
         line["roofline_fp64_pipe"] = fp64_alu
+    if line_rest is not None:
+        line["roofline_rest_tiles"] = line_rest
+    if main_res.get("queue"):
+        line["fused_queue"] = main_res["queue"]
     if res64o is not None:
         line["other_form"] = {"form": res64o["form"], "value": res64o["value"], "unit": UNIT,
                               "ms_per_step": res64o["ms_max"] / args.steps,
@@ -836,10 +886,7 @@ def main():
             "value": res32["value"], "unit": UNIT, "ms_per_step": res32["ms_max"] / args.steps,
             "speedup_vs_fp64": res32["value"] / res64["value"], "step_form": res32["form"],
             "kernel_ms": {k: round(v, 4) for k, v in res32["ktimes"].items()},
-            "roofline": {"bound": "hbm", "kernel": d32, "unit": "GB/s", **r32["hbm"],
-                         "traffic": None if d32 in _COUNTERS_STALE["fp32mix"] else
-                         _TRAFFIC_PER_CELL_FP32MIX.get(d32) and _TRAFFIC_PER_CELL_FP32MIX[d32] * cells,
-                         "traffic_note": "DRAM read+write bytes per cell from ncu (one kernel, 2000x2000), times the cells"},
+            "roofline": hbm_roof(r32, d32, "fp32mix"), "fused_queue": res32.get("queue"),
             "step_hbm_frac": round(step_bytes_per_cell(4) * cells / (res32["ms"] / args.steps * 1e-3) / 1e9 / hbm_peak, 4),
             "peak_pressure_decay_vs_fp64_same_steps": dec,
             "gpu_launches": res32["launches"], "clocks": res32["clocks"], "status": res32["scalars"]["status"]}
@@ -848,10 +895,7 @@ def main():
             line["fp32_mix"]["other_form"] = {"form": res32f["form"],
                 "value": res32f["value"], "unit": UNIT, "ms_per_step": res32f["ms_max"] / args.steps,
                 "kernel_ms": {k: round(v, 4) for k, v in res32f["ktimes"].items()},
-                "roofline": {"bound": "hbm", "kernel": df, "unit": "GB/s", **rf["hbm"],
-                             "traffic": None if df in _COUNTERS_STALE["fp32mix"] else
-                             _TRAFFIC_PER_CELL_FP32MIX.get(df) and _TRAFFIC_PER_CELL_FP32MIX[df] * cells,
-                             "traffic_note": "DRAM read+write bytes per cell from ncu (one kernel, 2000x2000), times the cells"},
+                "roofline": hbm_roof(rf, df, "fp32mix"),
                 "step_hbm_frac": round(step_bytes_per_cell(4) * cells / (res32f["ms"] / args.steps * 1e-3) / 1e9 / hbm_peak, 4),
                 "gpu_launches": res32f["launches"], "status": res32f["scalars"]["status"]}
         if not args.no_accuracy and ws == 1:
@@ -872,19 +916,45 @@ def main():
     return 0
 
 
-# FP64 operations per cell (2 DFMA + DADD + DMUL) issued by each FP64-form kernel on the
-# 4000 x 4000 physics, and DRAM bytes per cell, from ncu on the 2000 x 2000 case
-# (profiles/); refreshed whenever the kernels change.
-_FLOPS_PER_CELL: dict = {"k_phase0": 85.8, "k_phase1": 49.6, "k_phase2": 38.7, "k_phase3a": 75.9, "k_phase3b": 50.1, "k_phase3c": 4.8}
-_TRAFFIC_PER_CELL: dict = {"k_phase0": 57.8, "k_phase1": 72.1, "k_phase2": 75.6, "k_phase3a": 78.3, "k_phase3b": 63.1, "k_phase3c": 22.1}
-_TRAFFIC_PER_CELL_FP32MIX: dict = {"k_phase0": 27.9, "k_phase1": 31.5, "k_phase2": 40.0, "k_phase3a": 41.9, "k_phase3b": 29.7, "k_phase3c": 10.8}
+# FP64 operations per cell (2 DFMA + DADD + DMUL) issued by each phase kernel of the FP64
+# form, and DRAM bytes per cell of each phase kernel, from ncu (one kernel, one launch: the
+# first timed step of the 4000 x 4000 physics at 2000 x 2000, radius 50 cells; profiles/).
+_FLOPS_PER_CELL: dict = {"k_phase0": 85.1, "k_phase1": 37.7, "k_phase2": 27.4, "k_phase3a": 51.4, "k_phase3b": 50.1, "k_phase3c": 4.8}
+_TRAFFIC_PER_CELL: dict = {"k_phase0": 57.7, "k_phase1": 72.2, "k_phase2": 75.3, "k_phase3a": 78.5, "k_phase3b": 62.8, "k_phase3c": 22.1}
+_TRAFFIC_PER_CELL_FP32MIX: dict = {"k_phase0": 27.7, "k_phase1": 30.8, "k_phase2": 40.1, "k_phase3a": 42.3, "k_phase3b": 29.6, "k_phase3c": 10.8}
 # fraction of the FP64 pipe's issue slots each FP64-form kernel keeps busy (ncu,
-# sm__pipe_fp64_cycles_active on the 2000 x 2000 case)
-_FP64_PIPE_BUSY: dict = {"k_phase0": 0.854, "k_phase1": 0.862, "k_phase2": 0.859, "k_phase3a": 0.858, "k_phase3b": 0.841, "k_phase3c": 0.789}
+# sm__pipe_fp64_cycles_active, 2000 x 2000, the fused kernels at the second timed step)
+_FP64_PIPE_BUSY: dict = {"k_phase0": 0.847, "k_phase1": 0.847, "k_phase2": 0.845, "k_phase3a": 0.847, "k_phase3b": 0.841,
+                         "k_phase3c": 0.783, "k_step_fused": 0.735, "k_rest_tiles": 0.180}
+# The fused form's two kernels on the headline workload (4000 x 4000, K = 20 timed steps from
+# t = 0): DRAM read + write bytes and FP64 operations per launch, the mean over the 20 launches
+# of the timed region from one-pass ncu captures of the same command (profiles/).  The rest
+# flags make these launches depend on the step sequence, so they hold for that case only.
+_FULL_SIZE_CASE = ("large_4000", 20)
+_FUSED_FULL_SIZE: dict = {
+    "fp64": {"k_rest_tiles": {"traffic": 1.3585e9}, "k_step_fused": {"traffic": 1.3462e8, "flops": 1.2507e8}},
+    "fp32mix": {"k_rest_tiles": {"traffic": 7.6605e8}, "k_step_fused": {"traffic": 7.9006e7}},
+}
 # kernels changed since their counters were taken: neither DRAM traffic nor flop rates are
 # reported for them until the next capture
-_COUNTERS_STALE: dict = {"fp64": {"k_phase0", "k_phase1", "k_phase2", "k_phase3a", "k_step_fused"},
-                         "fp32mix": {"k_phase0", "k_phase1", "k_phase2", "k_phase3a", "k_step_fused"}}
+_COUNTERS_STALE: dict = {"fp64": set(), "fp32mix": set()}
+
+
+def _traffic(kernel: str, prec: str, args):
+    """DRAM bytes per launch of a kernel from ncu, and what they were measured on; None
+    where no capture applies."""
+    if kernel in _COUNTERS_STALE[prec]:
+        return None, "counters stale"
+    if kernel in _FUSED_FULL_SIZE[prec]:
+        if (args.workload, args.steps) != _FULL_SIZE_CASE:
+            return None, "not captured for this workload / K"
+        return _FUSED_FULL_SIZE[prec][kernel]["traffic"], "ncu, the same 20 launches, mean per launch"
+    table = _TRAFFIC_PER_CELL if prec == "fp64" else _TRAFFIC_PER_CELL_FP32MIX
+    if kernel not in table:
+        return None, "no capture"
+    g = _workload(args.workload)["grid"]
+    return table[kernel] * g["nr"] * g["nz"], "ncu bytes per cell (one launch, 2000x2000) x the cells"
+
 
 if __name__ == "__main__":
     sys.exit(main())

@@ -176,7 +176,11 @@ salec_status salec_step(salec_ctx* ctx, int nsteps);
  *                      again; a quiescent tile (matter at rest at zero pressure, whole
  *                      fractions, no deviatoric stress, no strip, no gravity), on which
  *                      every phase returns its input, only reads and writes its state.
- *                      Default when grid->gravity == 0.
+ *                      A tile found quiescent in the step before, with its eight
+ *                      neighbours, is at rest: a streaming kernel before the tile kernel
+ *                      copies it without a halo and queues the other tiles, which the
+ *                      tile kernel (one CTA per resident slot of the device) takes from
+ *                      the queue.  Default when grid->gravity == 0.
  *   SALEC_STEP_PHASES  six kernels over the whole grid and the Courant kernel, in place
  *                      (block shapes from salec_set_block_shapes / salec_autotune).
  *                      Default under gravity, where no tile is quiescent and this form,
@@ -230,16 +234,23 @@ salec_status salec_state_changed(salec_ctx* ctx);
 
 /* Number of kernel launches one step issues (for launch accounting): in the phase form
  * the six phases and the one-thread Courant kernel between phases 0 and 1 (7); in the
- * fused form the Courant kernel and the tile kernel (2; a sequence of fused steps that
- * follows set-up, a host write or other steps adds one pass of Courant rates first). */
+ * fused form the Courant kernel, the rest-tile kernel and the tile kernel (3; a sequence of
+ * fused steps that follows set-up, a host write or other steps adds one pass of Courant
+ * rates first). */
 int salec_launches_per_step(const salec_ctx* ctx);
+
+/* Fused form: *queued = the tiles the last fused step ran through the whole cycle (the
+ * others it copied as at rest), *tiles = the tiles of the grid.  Synchronises.  Both 0
+ * before the first fused step after a state change; SALEC_EORDER before salec_finalize. */
+salec_status salec_fused_queue(salec_ctx* ctx, int* queued, int* tiles);
 
 /* Per-kernel timing: with timing on, salec_step records a CUDA event before the first
  * and after every timed kernel of each step on the context's stream; salec_kernel_times
  * synchronises, returns in avg_ms[k] (n >= 6; unused entries 0) the mean duration of
  * kernel k over the steps recorded since timing was switched on or last read, the number
  * of steps in *steps, and restarts the count.  Phase form: k < 6 are the phases (phase 0
- * includes the Courant kernel); fused form: k = 0 is the Courant and tile kernels.
+ * includes the Courant kernel); fused form: k = 0 the Courant and rest-tile kernels,
+ * k = 1 the tile kernel.
  * salec_step_kernel_name(ctx, k) names entry k of the context's form ("" for an unused
  * one); salec_kernel_name(k) names phase k of the phase form. */
 salec_status salec_set_kernel_timing(salec_ctx* ctx, int on);

@@ -41,6 +41,10 @@ struct Layout {
     size_t pp_alt;
     size_t PM, pbphi, vL, mv, dK, kheat, frL[kMaxMat], VL, IL, sL01, sL2d, dMR, dMZ, partial, tmp;
     size_t eosc[2];   // the fused form's equation-of-state cache, one per copy of the fields
+    size_t rest[2];   // the fused form's rest flags of the tiles, one per copy
+    size_t work;      // two TileWork queues (one per copy the step reads)
+    size_t list;      // the queued tiles
+    size_t ntiles;    // bound on the fused form's tile count
     size_t total;
 };
 
@@ -111,6 +115,11 @@ Layout make_layout(const salec_grid& g, int precision)
     L.dMZ = take(cur, nr * (nz + 1) * d);
     L.eosc[0] = take(cur, nc * d2);
     L.eosc[1] = take(cur, nc * d2);
+    L.ntiles = (size_t)((nr + kFusedTileW - 1) / kFusedTileW) * ((nz + kFusedTileMinH - 1) / kFusedTileMinH);
+    L.rest[0] = take(cur, L.ntiles);
+    L.rest[1] = take(cur, L.ntiles);
+    L.work = take(cur, 2 * sizeof(TileWork));
+    L.list = take(cur, L.ntiles * sizeof(int));
     size_t nb = 0;
     for (int k = 0; k < kNumShapes; ++k) {
         const size_t t = (size_t)tiles_of(g.nr, g.nz, 0, kShapes[k]);
@@ -289,12 +298,19 @@ static void fill_pingpong(salec_ctx* ctx, const ParamsT<T>& P0, ParamsT<T>& P1, 
         o.pr_c = at<T2>(ctx, copy_at(w, L.pr_c)); o.pr_psi2 = at<T>(ctx, copy_at(w, L.pr_psi2));
         o.pr_v = at<T4>(ctx, copy_at(w, L.pr_v));
         o.eosc = at<T2>(ctx, L.eosc[w]);
+        o.rest_in = at<unsigned char>(ctx, L.rest[k]);
+        o.rest_out = at<unsigned char>(ctx, L.rest[w]);
+        o.work = at<TileWork>(ctx, L.work) + k;
+        o.work_next = at<TileWork>(ctx, L.work) + w;
+        o.list = at<int>(ctx, L.list);
     }
 }
 
-// Bring the current fields (and the equation-of-state cache that goes with them) into the
-// first copy, where every read-out, checkpoint, batch and the phase kernels find them, after
-// an odd number of fused steps: two device copies.
+// Bring the current fields (and the equation-of-state cache and the rest flags that go with
+// them) into the first copy, where every read-out, checkpoint, batch and the phase kernels
+// find them, after an odd number of fused steps: three device copies; the queue the step
+// that wrote the second copy used moves to the second copy's place (salec_fused_queue reads
+// it there) and the first copy's is emptied for the next step.
 static cudaError_t canonical(salec_ctx* ctx)
 {
     if (ctx->parity == 0) return cudaSuccess;
@@ -304,6 +320,12 @@ static cudaError_t canonical(salec_ctx* ctx)
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(ctx->base + L.eosc[0], ctx->base + L.eosc[1], L.eosc[1] - L.eosc[0], cudaMemcpyDeviceToDevice,
                             ctx->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(ctx->base + L.rest[0], ctx->base + L.rest[1], L.ntiles, cudaMemcpyDeviceToDevice, ctx->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(ctx->base + L.work + sizeof(TileWork), ctx->base + L.work, sizeof(TileWork),
+                            cudaMemcpyDeviceToDevice, ctx->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(ctx->base + L.work, 0, sizeof(TileWork), ctx->stream);
     if (e == cudaSuccess) ctx->parity = 0;
     return e;
 }
@@ -697,8 +719,10 @@ salec_status salec_finalize(salec_ctx* ctx)
     ctx->hydP.clear(); ctx->hydP.shrink_to_fit(); ctx->hydR.clear(); ctx->hydR.shrink_to_fit();
     fill_pingpong<double>(ctx, ctx->Pd, ctx->Pd_alt, ctx->Od);
     fill_pingpong<float>(ctx, ctx->Pf, ctx->Pf_alt, ctx->Of);
-    e = mixed(ctx) ? prepare_fused<float>(ctx->Pf) : prepare_fused<double>(ctx->Pd);
+    int ctas = 0;
+    e = mixed(ctx) ? prepare_fused<float>(ctx->Pf, &ctas) : prepare_fused<double>(ctx->Pd, &ctas);
     if (e != cudaSuccess) return cuda_check(ctx, e, "fused step set-up");
+    for (int k = 0; k < 2; ++k) ctx->Od[k].ctas = ctx->Of[k].ctas = ctas;
     // Default form.  Without gravity the fused form: its quiescent tiles (matter at rest
     // at zero pressure) only read and write their state, which on an impact grid is most of
     // it (4000 x 4000: mixed form 0.41 against 0.90 ms per step, FP64 1.26 against 7.16; a
@@ -768,7 +792,7 @@ static bool same_shapes(const dim3* a, const dim3* b)
 }
 
 // events per recorded step: one before the first kernel and one after each timed kernel
-static int timed_kernels(const salec_ctx* ctx) { return ctx->form == SALEC_STEP_FUSED ? 1 : launches_per_step(); }
+static int timed_kernels(const salec_ctx* ctx) { return ctx->form == SALEC_STEP_FUSED ? 2 : launches_per_step(); }
 
 static salec_status step_fused(salec_ctx* ctx, int nsteps)
 {
@@ -776,10 +800,13 @@ static salec_status step_fused(salec_ctx* ctx, int nsteps)
     // the running Courant maximum must hold the current state's rates: a fused step leaves
     // them for the next one; anything else (set-up, host writes, phase or batched steps)
     // needs one pass over the state first
+    // and no tile counts as at rest until a step has found it quiescent
     if (!ctx->rates_valid) {
+        const Layout& L = ctx->L;
         cudaError_t e = canonical(ctx);
         if (e == cudaSuccess)
-            e = cudaMemsetAsync(ctx->base + ctx->L.scal + offsetof(DevScalars, maxbits), 0, sizeof(unsigned long long), ctx->stream);
+            e = cudaMemsetAsync(ctx->base + L.scal + offsetof(DevScalars, maxbits), 0, sizeof(unsigned long long), ctx->stream);
+        if (e == cudaSuccess) e = cudaMemsetAsync(ctx->base + L.rest[0], 0, L.work + 2 * sizeof(TileWork) - L.rest[0], ctx->stream);
         if (e == cudaSuccess) e = mixed(ctx) ? launch_courant_rates<float>(ctx->Pf, ctx->stream)
                                              : launch_courant_rates<double>(ctx->Pd, ctx->stream);
         if (e != cudaSuccess) return cuda_check(ctx, e, "Courant rates");
@@ -802,14 +829,14 @@ static salec_status step_fused(salec_ctx* ctx, int nsteps)
     for (int n = 0; n < nsteps; ++n) {
         cudaEvent_t* evp = nullptr;
         if (ctx->timing) {
-            while (ctx->ev_used + 2 > ctx->ev.size()) {
+            while (ctx->ev_used + 3 > ctx->ev.size()) {
                 cudaEvent_t e0;
                 cudaError_t ce = cudaEventCreate(&e0);
                 if (ce != cudaSuccess) return cuda_check(ctx, ce, "event create");
                 ctx->ev.push_back(e0);
             }
             evp = ctx->ev.data() + ctx->ev_used;
-            ctx->ev_used += 2;
+            ctx->ev_used += 3;
         }
         const cudaError_t e = fused_step(ctx, ctx->parity, ctx->stream, evp);
         if (e != cudaSuccess) return cuda_check(ctx, e, "fused step launch");
@@ -910,7 +937,7 @@ const char* salec_kernel_name(int k)
 
 const char* salec_step_kernel_name(const salec_ctx* ctx, int k)
 {
-    if (ctx && ctx->form == SALEC_STEP_FUSED) return k == 0 ? "k_step_fused" : "";
+    if (ctx && ctx->form == SALEC_STEP_FUSED) return k == 0 ? "k_rest_tiles" : k == 1 ? "k_step_fused" : "";
     return kernel_name(k);
 }
 
@@ -1626,8 +1653,26 @@ void salec_batch_destroy(salec_batch* b)
 
 int salec_launches_per_step(const salec_ctx* ctx)
 {
-    if (ctx && ctx->form == SALEC_STEP_FUSED) return 2;     // the Courant kernel and the tile kernel
+    if (ctx && ctx->form == SALEC_STEP_FUSED) return 3;     // the Courant, rest-tile and tile kernels
     return kernels_per_step();
+}
+
+salec_status salec_fused_queue(salec_ctx* ctx, int* queued, int* tiles)
+{
+    if (!ctx || !queued || !tiles) return SALEC_EINVAL;
+    if (!ctx->finalized) return fail(ctx, SALEC_EORDER, "fused_queue before finalize");
+    *queued = *tiles = 0;
+    if (!ctx->rates_valid) return SALEC_OK;
+    // the step that wrote the current copy used the other copy's queue
+    TileWork w;
+    cudaError_t e = cudaMemcpyAsync(&w, ctx->base + ctx->L.work + (1 - ctx->parity) * sizeof(TileWork), sizeof(w),
+                                    cudaMemcpyDeviceToHost, ctx->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+    if (e != cudaSuccess) return cuda_check(ctx, e, "fused queue");
+    if (w.next == 0) return SALEC_OK;      // no fused step since the queues were emptied
+    *queued = w.count;
+    *tiles = mixed(ctx) ? fused_tiles<float>(ctx->Pf) : fused_tiles<double>(ctx->Pd);
+    return SALEC_OK;
 }
 
 const char* salec_last_error(const salec_ctx* ctx)

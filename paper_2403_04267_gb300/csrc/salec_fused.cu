@@ -191,11 +191,27 @@ __global__ void __launch_bounds__(NT, MINB) k_step_fused(const ParamsT<T> P, con
     const PtrsT<T>& p = P.p;
     const int nr = P.nr, nz = P.nz, nv = nr + 1;
     const int tid = threadIdx.x;
-    const int ox = blockIdx.x * TW, oy = blockIdx.y * TH;
-    const int x0 = ox - H, y0 = oy - H;            // grid indices of frame position 0
-    const bool last_x = blockIdx.x == gridDim.x - 1, last_y = blockIdx.y == gridDim.y - 1;
+    const int nbx = (nr + TW - 1) / TW, nby = (nz + TH - 1) / TH;
     const T dt = step_dt<T>(p.scal);
     double t_out = 0.0, t_disc = 0.0, t_pml = 0.0, t_zmom = 0.0;
+    T speed_max = zero;
+    // The CTA takes tiles from the queue the rest-tile kernel filled (complete: that kernel
+    // ran before this one) until it is empty; the tallies and the Courant maximum collect
+    // over all of them.
+    __shared__ int s_tile;
+    const int queued = min(O.work->count, nbx * nby);
+    for (;;) {
+    if (tid == 0) {
+        const int t = atomicAdd(&O.work->next, 1);
+        s_tile = t < queued ? O.list[t] : -1;
+    }
+    __syncthreads();        // also: every thread is done with the previous tile's shared memory
+    const int tile = s_tile;
+    if (tile < 0) break;
+    const int bx = tile % nbx, by = tile / nbx;
+    const int ox = bx * TW, oy = by * TH;
+    const int x0 = ox - H, y0 = oy - H;            // grid indices of frame position 0
+    const bool last_x = bx == nbx - 1, last_y = by == nby - 1;
 
     // ---- stage the state of the frame (cells and vertices outside the grid read as empty):
     // asynchronous copies, all in flight together
@@ -228,7 +244,6 @@ __global__ void __launch_bounds__(NT, MINB) k_step_fused(const ParamsT<T> P, con
     // outputs are their inputs (an empty cell's as zeros, as the remap writes it), the peak
     // over-pressure update is the same, the Courant rate is c / L.  The tile then only
     // reads and writes its state.
-    T speed_max = zero;
     bool quiet = !nonzero(P.g) && y0 >= P.pb && x0 + CW <= nr - P.pr;
     if (quiet) {
         bool q = true;
@@ -952,6 +967,8 @@ __global__ void __launch_bounds__(NT, MINB) k_step_fused(const ParamsT<T> P, con
     }
 
     }   // not quiescent
+    if (tid == 0) O.rest_out[tile] = quiet ? 1 : 0;
+    }   // tiles
 
     // ---- reductions.  The tallies (FP64) are rare (top row, strips, clean-up): a warp that
     // holds one sums it and adds it with one atomic per tally, so no other warp issues FP64
@@ -985,13 +1002,129 @@ __global__ void __launch_bounds__(NT, MINB) k_step_fused(const ParamsT<T> P, con
             if (lane == 0) {
                 DevScalars* s = p.scal;
                 atomicMax(&s->maxbits, b);
-                if (blockIdx.x == 0 && blockIdx.y == 0) {
+                if (blockIdx.x == 0) {
                     s->t += s->dt;
                     s->dt_prev = s->dt;
                     s->nstep += 1ull;
                 }
             }
         }
+    }
+}
+
+// ---- tiles at rest.  A tile that the step before took through the quiescent path, and
+// whose eight neighbours it took through it too, has an unchanged frame that still passes
+// every test of that path; and its fields already are what that path writes (an absent
+// material as zeros, no deviatoric stress, vertices at rest, an empty cell's energy zero).
+// So its outputs are its inputs bit for bit, its peak over-pressure stays (the same
+// pressure against the same reference as in the step before), and its Courant rate is
+// that of its fastest sound speed: one square root of the largest c^2 of its cells on a
+// uniform grid (the rounded square root is monotonic).  This kernel copies those tiles,
+// one warp per tile with the loads of several rows in flight, and queues every other tile
+// for the tile kernel.
+constexpr int kRestThreads = 256;
+
+template <typename T, int NM, bool STR, bool UNI, int TW, int TH>
+__global__ void __launch_bounds__(kRestThreads) k_rest_tiles(const ParamsT<T> P, const OutPtrsT<T> O)
+{
+    typedef VT<T> V;
+    typedef typename V::T2 T2;
+    typedef Geo<T, UNI> GE;
+    static_assert(TW == 32, "one lane per column of a tile");
+    constexpr int R = NM == 1 ? 4 : 2;            // rows whose loads are in flight together
+    const PtrsT<T>& p = P.p;
+    const T zero = T(0);
+    const int nr = P.nr, nz = P.nz, nv = nr + 1;
+    const int nbx = (nr + TW - 1) / TW, nby = (nz + TH - 1) / TH;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int tile = blockIdx.x * (kRestThreads / 32) + w;
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        O.work_next->count = 0;
+        O.work_next->next = 0;
+    }
+    T c2max = zero, speed_max = zero;
+    bool bad = false;
+    if (tile < nbx * nby) {
+        const int bx = tile % nbx, by = tile / nbx;
+        bool rest = true;
+        if (lane < 9) {
+            const int tx = bx + lane % 3 - 1, ty = by + lane / 3 - 1;
+            if (tx >= 0 && tx < nbx && ty >= 0 && ty < nby) rest = O.rest_in[ty * nbx + tx] != 0;
+        }
+        rest = __all_sync(0xffffffffu, rest);
+        if (!rest) {
+            if (lane == 0) {
+                const int q = atomicAdd(&O.work->count, 1);
+                if (q < nbx * nby) O.list[q] = tile;       // each tile is queued once a step
+            }
+        } else {
+            if (lane == 0) O.rest_out[tile] = 1;
+            const int i = bx * TW + lane, jb = by * TH, je = min(jb + TH, nz);
+            if (i < nr) {
+                for (int j0 = jb; j0 < je; j0 += R) {
+                    T2 fr[R][NM], ec[R], sd[R];
+                    double Ic[R];
+#pragma unroll
+                    for (int r = 0; r < R; ++r) {
+                        if (j0 + r >= je) break;
+                        const int c = (j0 + r) * nr + i;
+#pragma unroll
+                        for (int m = 0; m < NM; ++m) fr[r][m] = p.fr[m][c];
+                        Ic[r] = p.I[c];
+                        ec[r] = p.eosc[c];
+                        if (STR) sd[r] = p.s2d[c];
+                    }
+#pragma unroll
+                    for (int r = 0; r < R; ++r) {
+                        if (j0 + r >= je) break;
+                        const int j = j0 + r, c = j * nr + i;
+                        bool here = false;
+#pragma unroll
+                        for (int m = 0; m < NM; ++m) {
+                            O.fr[m][c] = fr[r][m];
+                            here = here || pos(fr[r][m].x);
+                        }
+                        O.I[c] = Ic[r];
+                        O.eosc[c] = ec[r];
+                        if (STR) {
+                            O.s01[c] = V::mk(zero, zero);
+                            O.s2d[c] = sd[r];
+                        }
+                        if (here) {
+                            const T c2 = ec[r].y;
+                            if (!UNI || is_nan(c2) || neg(c2)) {
+                                // the quiescent path's own arithmetic, cell by cell
+                                T speed = t_sqrt<T>(zero) + t_sqrt<T>(c2);
+                                if (!UNI) speed = speed * GE::ilen(P, i, j);
+                                bad = bad || is_nan(speed);
+                                speed_max = max_nonneg(speed_max, speed);
+                            } else {
+                                c2max = max_nonneg(c2max, c2);
+                            }
+                        }
+                    }
+                }
+            }
+            // the tile's vertices (with the grid's far edges on the last tiles) at rest
+            const int jv = by == nby - 1 ? nz + 1 : jb + TH;
+            const bool edge = lane == 0 && bx == nbx - 1 && bx * TW + TW == nr;
+            for (int j = jb; j < jv; ++j) {
+                if (i <= nr) O.v[j * nv + i] = V::mk(zero, zero);
+                if (edge) O.v[j * nv + nr] = V::mk(zero, zero);
+            }
+        }
+    }
+    if (UNI) speed_max = max_nonneg(speed_max, t_sqrt<T>(zero) + t_sqrt<T>(c2max));
+    if (__any_sync(0xffffffffu, bad) && lane == 0) atomicOr(&p.scal->status, 2);
+    __shared__ unsigned long long sh[kRestThreads / 32];
+    unsigned long long b = (unsigned long long)__double_as_longlong(double(speed_max));
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) b = max(b, __shfl_down_sync(0xffffffffu, b, o));
+    if (lane == 0) sh[w] = b;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int k = 1; k < kRestThreads / 32; ++k) b = max(b, sh[k]);
+        if (b != 0ull) atomicMax(&p.scal->maxbits, b);
     }
 }
 
@@ -1060,16 +1193,31 @@ template <typename T, int NM, bool STR, bool UNI>
 struct Fused {
     typedef TileShape<T, NM, STR> S;
     typedef TileLayout<T, NM, STR, S::TW, S::TH> L;
+    static_assert(S::TW == kFusedTileW && S::TH >= kFusedTileMinH, "tile count bound");
     static void* fn() { return reinterpret_cast<void*>(k_step_fused<T, NM, STR, UNI, S::TW, S::TH, S::NT, S::MINB>); }
-    static cudaError_t prepare()
+    static int tiles(const ParamsT<T>& P) { return ((P.nr + S::TW - 1) / S::TW) * ((P.nz + S::TH - 1) / S::TH); }
+    // the persistent grid: as many CTAs as the device holds at once
+    static cudaError_t prepare(int* ctas)
     {
-        return cudaFuncSetAttribute(k_step_fused<T, NM, STR, UNI, S::TW, S::TH, S::NT, S::MINB>,
-                                    cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L::bytes);
+        auto k = k_step_fused<T, NM, STR, UNI, S::TW, S::TH, S::NT, S::MINB>;
+        cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L::bytes);
+        int dev = 0, sms = 0, per_sm = 0;
+        if (e == cudaSuccess) e = cudaGetDevice(&dev);
+        if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, S::NT, L::bytes);
+        if (e == cudaSuccess && per_sm < 1) e = cudaErrorInvalidConfiguration;
+        if (e == cudaSuccess) *ctas = sms * per_sm;
+        return e;
+    }
+    static cudaError_t rest(const ParamsT<T>& P, const OutPtrsT<T>& O, cudaStream_t s)
+    {
+        constexpr int wpb = kRestThreads / 32;
+        k_rest_tiles<T, NM, STR, UNI, S::TW, S::TH><<<(tiles(P) + wpb - 1) / wpb, kRestThreads, 0, s>>>(P, O);
+        return cudaGetLastError();
     }
     static cudaError_t launch(const ParamsT<T>& P, const OutPtrsT<T>& O, cudaStream_t s)
     {
-        const dim3 g((P.nr + S::TW - 1) / S::TW, (P.nz + S::TH - 1) / S::TH);
-        k_step_fused<T, NM, STR, UNI, S::TW, S::TH, S::NT, S::MINB><<<g, S::NT, L::bytes, s>>>(P, O);
+        k_step_fused<T, NM, STR, UNI, S::TW, S::TH, S::NT, S::MINB><<<O.ctas, S::NT, L::bytes, s>>>(P, O);
         return cudaGetLastError();
     }
     static cudaError_t rates(const ParamsT<T>& P, cudaStream_t s)
@@ -1101,9 +1249,9 @@ cudaError_t dispatch(const ParamsT<T>& P, Fn&& fn)
 }  // namespace
 
 template <typename T>
-cudaError_t prepare_fused(const ParamsT<T>& P)
+cudaError_t prepare_fused(const ParamsT<T>& P, int* ctas)
 {
-    return dispatch<T, Fused>(P, [](auto f) { return decltype(f)::prepare(); });
+    return dispatch<T, Fused>(P, [&](auto f) { return decltype(f)::prepare(ctas); });
 }
 
 template <typename T>
@@ -1115,26 +1263,39 @@ size_t fused_smem_bytes(const ParamsT<T>& P)
 }
 
 template <typename T>
+int fused_tiles(const ParamsT<T>& P)
+{
+    int n = 0;
+    dispatch<T, Fused>(P, [&](auto f) { n = decltype(f)::tiles(P); return cudaSuccess; });
+    return n;
+}
+
+template <typename T>
 cudaError_t launch_courant_rates(const ParamsT<T>& P, cudaStream_t s)
 {
     return dispatch<T, Fused>(P, [&](auto f) { return decltype(f)::rates(P, s); });
 }
 
-// One fused cycle: the Courant kernel (dt from the running maximum of the rates), then the
-// tile kernel.  With ev: an event before and after (2 events).
+// One fused cycle: the Courant kernel (dt from the running maximum of the rates), the
+// rest-tile kernel (copies the tiles at rest, queues the others), the persistent tile
+// kernel.  With ev: an event before, one after the rest-tile kernel and one at the end.
 template <typename T>
 cudaError_t launch_step_fused(const ParamsT<T>& P, const OutPtrsT<T>& O, cudaStream_t s, cudaEvent_t* ev)
 {
     if (ev) cudaEventRecord(ev[0], s);
     cudaError_t e = launch_courant<T>(P, s);
+    if (e == cudaSuccess) e = dispatch<T, Fused>(P, [&](auto f) { return decltype(f)::rest(P, O, s); });
     if (e != cudaSuccess) return e;
-    e = dispatch<T, Fused>(P, [&](auto f) { return decltype(f)::launch(P, O, s); });
     if (ev) cudaEventRecord(ev[1], s);
+    e = dispatch<T, Fused>(P, [&](auto f) { return decltype(f)::launch(P, O, s); });
+    if (ev) cudaEventRecord(ev[2], s);
     return e;
 }
 
-template cudaError_t prepare_fused<double>(const ParamsT<double>&);
-template cudaError_t prepare_fused<float>(const ParamsT<float>&);
+template cudaError_t prepare_fused<double>(const ParamsT<double>&, int*);
+template cudaError_t prepare_fused<float>(const ParamsT<float>&, int*);
+template int fused_tiles<double>(const ParamsT<double>&);
+template int fused_tiles<float>(const ParamsT<float>&);
 template size_t fused_smem_bytes<double>(const ParamsT<double>&);
 template size_t fused_smem_bytes<float>(const ParamsT<float>&);
 template cudaError_t launch_courant_rates<double>(const ParamsT<double>&, cudaStream_t);

@@ -50,6 +50,13 @@ struct MatT {
 };
 typedef MatT<double> Mat;
 
+// The fused step's queue of tiles that need the whole cycle: filled by the rest-tile
+// kernel (count), drained by the persistent tile kernel (next).
+struct TileWork {
+    int count;
+    int next;
+};
+
 // Scalars of a run, resident on the device.
 struct DevScalars {
     double t, dt, dt_prev, t_end;   // t_end: a batched run stops stepping once t >= t_end
@@ -142,6 +149,16 @@ struct OutPtrsT {
     T* pr_psi2;
     T4* pr_v;
     T2* eosc;
+    // tiles at rest: rest_in[t] = 1 when the step that wrote the copy read here took tile t
+    // through the quiescent path (its outputs are then its inputs); this step writes
+    // rest_out.  work counts and hands out the tiles this step runs through the whole
+    // cycle (list: their indices); work_next is zeroed for the next step.
+    const unsigned char* rest_in;
+    unsigned char* rest_out;
+    TileWork* work;
+    TileWork* work_next;
+    int* list;
+    int ctas;               // CTAs of the persistent tile kernel (all the device holds at once)
 };
 
 template <typename T>
@@ -359,9 +376,13 @@ cudaError_t launch_batch_step(const ParamsT<T>* runs_dev, int nruns, int nmat, b
                               const int* ntiles, const dim3* blk, cudaStream_t s, cudaEvent_t* ev);
 template <typename T> cudaError_t launch_batch_poll(const ParamsT<T>* runs_dev, int n, double* out, cudaStream_t s);
 template <typename T> cudaError_t launch_courant(const ParamsT<T>& P, cudaStream_t s);
-// fused form (salec_fused.cu): one tile kernel per step after the Courant kernel
-template <typename T> cudaError_t prepare_fused(const ParamsT<T>& P);
+// fused form (salec_fused.cu): after the Courant kernel, the rest-tile kernel and the
+// persistent tile kernel.  kFusedTileW x kFusedTileMinH bounds the tile count of every
+// instantiation (the rest flags and the work list are sized by it).
+constexpr int kFusedTileW = 32, kFusedTileMinH = 16;
+template <typename T> cudaError_t prepare_fused(const ParamsT<T>& P, int* ctas);
 template <typename T> size_t fused_smem_bytes(const ParamsT<T>& P);
+template <typename T> int fused_tiles(const ParamsT<T>& P);
 template <typename T> cudaError_t launch_courant_rates(const ParamsT<T>& P, cudaStream_t s);
 template <typename T>
 cudaError_t launch_step_fused(const ParamsT<T>& P, const OutPtrsT<T>& O, cudaStream_t s, cudaEvent_t* ev);

@@ -61,6 +61,7 @@ EXPORTS = ["salec_state_bytes", "salec_create", "salec_set_material", "salec_set
            "salec_conservation", "salec_checkpoint_bytes", "salec_get_state", "salec_set_state", "salec_state_changed",
            "salec_launches_per_step", "salec_set_kernel_timing", "salec_kernel_times",
            "salec_kernel_name", "salec_step_kernel_name", "salec_set_step_form", "salec_get_step_form",
+           "salec_fused_queue",
            "salec_courant_dt_noalloc", "salec_last_error", "salec_destroy",
            "salec_set_end_time", "salec_set_block_shapes", "salec_get_block_shapes", "salec_autotune",
            "salec_batch_bytes", "salec_batch_create", "salec_batch_step", "salec_batch_run", "salec_batch_poll",
@@ -105,6 +106,7 @@ def load(build: bool = True):
         "salec_kernel_times": (I, [P, PD, I, C.POINTER(C.c_int)]),
         "salec_kernel_name": (C.c_char_p, [I]),
         "salec_step_kernel_name": (C.c_char_p, [P, I]),
+        "salec_fused_queue": (I, [P, C.POINTER(C.c_int), C.POINTER(C.c_int)]),
         "salec_set_step_form": (I, [P, I]),
         "salec_get_step_form": (I, [P]),
         "salec_courant_dt_noalloc": (I, [C.POINTER(salec_grid), C.POINTER(salec_material), C.POINTER(C.c_void_p),
@@ -335,6 +337,13 @@ class Sim:
         self._check(load().salec_kernel_times(self._h, out.ctypes.data_as(C.POINTER(C.c_double)), n, C.byref(steps)))
         names = [load().salec_step_kernel_name(self._h, k).decode() for k in range(n)]
         return {nm: float(out[k]) for k, nm in enumerate(names) if nm}, steps.value
+
+    def fused_queue(self) -> tuple[int, int]:
+        """(tiles the last fused step ran through the whole cycle, tiles of the grid); the
+        others it copied as at rest.  (0, 0) before a fused step."""
+        q, t = C.c_int(), C.c_int()
+        self._check(load().salec_fused_queue(self._h, C.byref(q), C.byref(t)))
+        return q.value, t.value
 
     @property
     def step_form(self) -> str:

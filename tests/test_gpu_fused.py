@@ -38,7 +38,7 @@ def _cuda():
 def _fused(spec, precision="fp64"):
     g = salec.Sim(spec, precision=precision)
     g.step_form = "fused"
-    assert g.step_form == "fused" and g.launches_per_step() == 2
+    assert g.step_form == "fused" and g.launches_per_step() == 3
     return g
 
 
@@ -181,6 +181,32 @@ def test_fused_matches_phase_kernels(precision, tol1, tol30):
         mass = b.conservation()["mass"]
         for k in ("mass_out", "mass_pml", "mass_discarded"):
             assert abs(sa[k] - sb[k]) <= tol30 * 1e-3 * mass, k
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32mix"])
+@pytest.mark.parametrize("n", [200, 203])
+def test_rest_tiles_copy_what_the_quiescent_path_writes(precision, n):
+    """A tile found quiescent in the step before, with its eight neighbours, is copied by
+    the rest-tile kernel instead of going through the tile kernel.  Against the same steps
+    taken with the rest flags cleared before each one (every tile then goes through the
+    tile kernel's own quiescence test and path; a field written back from the host clears
+    them): bitwise the same fields, time, dt and tallies, on a grid the tiles divide and on
+    a ragged one."""
+    spec = W.scaled_plain(n, radius_cells=5)
+    a = _fused(spec, precision)
+    a.step(70)
+    queued, tiles = a.fused_queue()
+    print(f"{precision} {n}x{n}: {queued} of {tiles} tiles through the whole cycle after 70 steps")
+    assert 0 < queued < tiles
+    b = _fused(spec, precision)
+    for _ in range(70):
+        b.set("vz", b.get("vz"))
+        b.step(1)
+        assert b.fused_queue() == (tiles, tiles)
+    _assert_equal(a, b, spec)
+    sa, sb = a.scalars(), b.scalars()
+    for k in ("mass_out", "mass_pml", "mass_discarded", "zmom_out"):
+        assert sa[k] == sb[k], k
 
 
 @pytest.mark.parametrize("precision", ["fp64", "fp32mix"])
