@@ -67,6 +67,18 @@ salec_status salec_mlp_gradient(salec_mlp* mlp, const float* x_dev, const float*
 salec_status salec_mlp_train_step(salec_mlp* mlp, const float* x_dev, const float* t_dev, int batch, float lr,
                                   float beta1, float beta2, float eps, double* sse_dev);
 
+/* `steps` training steps as above, step k (0-based) with learning rate lr_dev[k] (`steps`
+ * FP32 values on the device, read as each step begins), in one call: the inputs are
+ * converted once, and after the first step whole chunks of 25 steps go out as CUDA-graph
+ * replays into the context's stream (the graph is captured again when t_dev, lr_dev, batch
+ * or a hyper-parameter changes).  The Adam step count continues from the context's; the
+ * arithmetic of every step is that of salec_mlp_train_step, with the bias corrections
+ * formed on the device.  Contexts on different streams train concurrently.  If sse_dev is
+ * not NULL the last step's sum of squared errors is copied there.  SALEC_EINVAL for a
+ * negative step count, a null pointer or a bad hyper-parameter.  Asynchronous. */
+salec_status salec_mlp_train(salec_mlp* mlp, const float* x_dev, const float* t_dev, int batch, int steps,
+                             const float* lr_dev, float beta1, float beta2, float eps, double* sse_dev);
+
 /* Synchronises and reports whether a tensor-core wait ran out of time since creation. */
 salec_status salec_mlp_check(salec_mlp* mlp);
 

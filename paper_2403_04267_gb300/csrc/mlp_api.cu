@@ -43,7 +43,7 @@ long n_weights_bf16()
 }
 
 struct Layout {
-    size_t theta, m1, m2, grad, wmap, wbf, X, Z[4], H[4], Y, G[2], part, cpart, loss, err, total;
+    size_t theta, m1, m2, grad, wmap, wbf, X, Z[4], H[4], Y, G[2], part, cpart, loss, err, ts, total;
     Layout(int bmax)
     {
         const long P = n_params(), W = n_weights_bf16();
@@ -61,6 +61,7 @@ struct Layout {
         cpart = take((size_t)kColsumChunks * kHid * 4);      // column-sum partials of a bias gradient
         loss = take(8);
         err = take(4);
+        ts = take(sizeof(TrainState));
         total = o;
     }
 };
@@ -83,7 +84,19 @@ struct salec_mlp {
     float* cpart = nullptr;
     double* loss = nullptr;
     int* errflag = nullptr;
+    TrainState* ts = nullptr;
     long steps = 0;                       // Adam steps taken
+    // salec_mlp_train: a CUDA graph of kTrainChunk steps, for the arguments it was captured with
+    cudaGraphExec_t tgraph = nullptr;
+    const float* tg_t = nullptr;
+    const float* tg_lr = nullptr;
+    int tg_batch = 0;
+    float tg_beta1 = 0.0f, tg_beta2 = 0.0f, tg_eps = 0.0f;
+    bool tg_ok = true;                    // false after a capture failed: plain launches
+    ~salec_mlp()
+    {
+        if (tgraph) cudaGraphExecDestroy(tgraph);
+    }
     long woff[kLayers], boff[kLayers];    // offsets of W_l and b_l in theta
     long wbf_off[kLayers];                // offset of W_l in the BF16 weight block
 };
@@ -190,6 +203,61 @@ salec_status check_batch(salec_mlp* n, int B)
     return SALEC_OK;
 }
 
+constexpr int kTrainChunk = 25;
+
+// One step of a multi-step call: its learning rate and bias corrections from the device
+// state, then the gradient and the Adam update (the inputs are already in X).
+salec_status train_one(salec_mlp* n, int B, const float* t_dev, const float* lr_dev, float beta1, float beta2,
+                       float eps)
+{
+    MLP_CUDA(n, launch_train_begin(n->ts, lr_dev, beta1, beta2, n->loss, n->stream), "mlp train step");
+    salec_status st = forward_impl(n, B, n->Y, SALEC_MLP_OUT, t_dev, true);
+    if (st != SALEC_OK) return st;
+    st = backward_impl(n, B, n->grad);
+    if (st != SALEC_OK) return st;
+    AdamArgs a;
+    a.lr = 0.0f; a.c1 = 0.0f; a.c2 = 0.0f;
+    a.beta1 = beta1; a.beta2 = beta2; a.eps = eps; a.ts = n->ts;
+    MLP_CUDA(n, launch_adam(n->theta, n->m1, n->m2, n->grad, n_params(), a, n->wmap, n->wbf, n->stream), "mlp adam");
+    return SALEC_OK;
+}
+
+// Capture kTrainChunk steps on a private stream (the graph can then be launched into any
+// stream); false, with no error left pending, when capture is not possible.
+bool capture_train(salec_mlp* n, int B, const float* t_dev, const float* lr_dev, float beta1, float beta2, float eps)
+{
+    if (n->tgraph) {
+        cudaGraphExecDestroy(n->tgraph);
+        n->tgraph = nullptr;
+    }
+    cudaStream_t cs;
+    if (cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) != cudaSuccess) {
+        (void)cudaGetLastError();
+        return false;
+    }
+    cudaStream_t keep = n->stream;
+    n->stream = cs;
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+    salec_status st = SALEC_OK;
+    for (int k = 0; k < kTrainChunk && e == cudaSuccess && st == SALEC_OK; ++k)
+        st = train_one(n, B, t_dev, lr_dev, beta1, beta2, eps);
+    const cudaError_t e2 = cudaStreamEndCapture(cs, &g);
+    n->stream = keep;
+    if (e == cudaSuccess) e = e2;
+    if (e == cudaSuccess && st == SALEC_OK) e = cudaGraphInstantiate(&n->tgraph, g, 0);
+    if (g) cudaGraphDestroy(g);
+    cudaStreamDestroy(cs);
+    if (e != cudaSuccess || st != SALEC_OK) {
+        (void)cudaGetLastError();
+        n->tgraph = nullptr;
+        return false;
+    }
+    n->tg_t = t_dev; n->tg_lr = lr_dev; n->tg_batch = B;
+    n->tg_beta1 = beta1; n->tg_beta2 = beta2; n->tg_eps = eps;
+    return true;
+}
+
 }  // namespace
 
 extern "C" {
@@ -232,6 +300,7 @@ salec_status salec_mlp_create(int batch_max, void* dev_buf, size_t bytes, void* 
     n->cpart = reinterpret_cast<float*>(b + L.cpart);
     n->loss = reinterpret_cast<double*>(b + L.loss);
     n->errflag = reinterpret_cast<int*>(b + L.err);
+    n->ts = reinterpret_cast<TrainState*>(b + L.ts);
     // parameter offsets and the weight -> BF16 block map
     const long P = n_params();
     std::vector<int> wmap(P, -1);
@@ -335,10 +404,47 @@ salec_status salec_mlp_train_step(salec_mlp* n, const float* x_dev, const float*
     if (st != SALEC_OK) return st;
     n->steps += 1;
     AdamArgs a;
-    a.lr = lr; a.beta1 = beta1; a.beta2 = beta2; a.eps = eps;
+    a.lr = lr; a.beta1 = beta1; a.beta2 = beta2; a.eps = eps; a.ts = nullptr;
     a.c1 = (float)(1.0 / (1.0 - std::pow((double)beta1, (double)n->steps)));
     a.c2 = (float)(1.0 / (1.0 - std::pow((double)beta2, (double)n->steps)));
     MLP_CUDA(n, launch_adam(n->theta, n->m1, n->m2, n->grad, n_params(), a, n->wmap, n->wbf, n->stream), "mlp adam");
+    if (sse_dev) MLP_CUDA(n, cudaMemcpyAsync(sse_dev, n->loss, 8, cudaMemcpyDeviceToDevice, n->stream), "mlp loss copy");
+    return SALEC_OK;
+}
+
+salec_status salec_mlp_train(salec_mlp* n, const float* x_dev, const float* t_dev, int batch, int steps,
+                             const float* lr_dev, float beta1, float beta2, float eps, double* sse_dev)
+{
+    salec_status st = check_batch(n, batch);
+    if (st != SALEC_OK) return st;
+    if (steps < 0) return fail(n, SALEC_EINVAL, "negative step count");
+    if (steps == 0) return SALEC_OK;
+    if (!x_dev || !t_dev || !lr_dev) return fail(n, SALEC_EINVAL, "null pointer");
+    if (!(beta1 >= 0.0f && beta1 < 1.0f) || !(beta2 >= 0.0f && beta2 < 1.0f) || !(eps > 0.0f))
+        return fail(n, SALEC_EINVAL, "bad Adam hyper-parameters");
+    if (n->steps + (long)steps > 0x7fffffffL) return fail(n, SALEC_EINVAL, "step count overflow");
+    MLP_CUDA(n, launch_inputs_bf16(x_dev, batch, SALEC_MLP_IN, kInLd, n->X, n->stream), "mlp input");
+    MLP_CUDA(n, launch_train_reset(n->ts, (int)n->steps, n->stream), "mlp train reset");
+    // the first step with plain launches (it also sets the kernels' attributes), then whole
+    // chunks as graph replays, then the rest
+    st = train_one(n, batch, t_dev, lr_dev, beta1, beta2, eps);
+    if (st != SALEC_OK) return st;
+    int done = 1;
+    const int chunks = (steps - 1) / kTrainChunk;
+    if (chunks > 0 && n->tg_ok) {
+        const bool same = n->tgraph && n->tg_t == t_dev && n->tg_lr == lr_dev && n->tg_batch == batch &&
+                          n->tg_beta1 == beta1 && n->tg_beta2 == beta2 && n->tg_eps == eps;
+        if (!same && !capture_train(n, batch, t_dev, lr_dev, beta1, beta2, eps)) n->tg_ok = false;
+        if (n->tgraph && n->tg_ok) {
+            for (int c = 0; c < chunks; ++c) MLP_CUDA(n, cudaGraphLaunch(n->tgraph, n->stream), "mlp train graph");
+            done += chunks * kTrainChunk;
+        }
+    }
+    for (; done < steps; ++done) {
+        st = train_one(n, batch, t_dev, lr_dev, beta1, beta2, eps);
+        if (st != SALEC_OK) return st;
+    }
+    n->steps += steps;
     if (sse_dev) MLP_CUDA(n, cudaMemcpyAsync(sse_dev, n->loss, 8, cudaMemcpyDeviceToDevice, n->stream), "mlp loss copy");
     return SALEC_OK;
 }

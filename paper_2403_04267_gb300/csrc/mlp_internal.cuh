@@ -56,8 +56,16 @@ struct FusedLaunch {
     int* err;
 };
 
+// Device state of a multi-step training call: k = steps of the call begun so far, t0 = Adam
+// steps before the call; the step's learning rate and bias corrections, formed once per step.
+struct TrainState {
+    int k, t0;
+    float lr, c1, c2;
+};
+
 struct AdamArgs {
     float lr, beta1, beta2, eps, c1, c2;   // c1 = 1 / (1 - beta1^t), c2 = 1 / (1 - beta2^t)
+    const TrainState* ts;                  // not null: lr, c1, c2 from here instead
 };
 
 cudaError_t launch_gemm(const GemmArgs& g, cudaStream_t s);
@@ -68,6 +76,12 @@ cudaError_t launch_colsum(const __nv_bfloat16* G, int M, int N, long ldg, float*
 cudaError_t launch_inputs_bf16(const float* x, int rows, int cols, int ld, __nv_bfloat16* y, cudaStream_t s);
 cudaError_t launch_adam(float* theta, float* m1, float* m2, const float* grad, long n, const AdamArgs& a,
                         const int* wmap, __nv_bfloat16* wbf, cudaStream_t s);
+// one thread: ts->k = 0, ts->t0 = t0
+cudaError_t launch_train_reset(TrainState* ts, int t0, cudaStream_t s);
+// one thread, first kernel of a step: k += 1, lr = lr_dev[k - 1], the bias corrections of
+// Adam step t0 + k, loss = 0
+cudaError_t launch_train_begin(TrainState* ts, const float* lr_dev, float beta1, float beta2, double* loss,
+                               cudaStream_t s);
 cudaError_t launch_refresh_bf16(const float* theta, long n, const int* wmap, __nv_bfloat16* wbf, cudaStream_t s);
 size_t gemm_smem_bytes(int nt);
 

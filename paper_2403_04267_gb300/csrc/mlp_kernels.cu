@@ -860,15 +860,40 @@ __global__ void k_adam(float* __restrict__ theta, float* __restrict__ m1, float*
 {
     const long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
+    float lr = a.lr, c1 = a.c1, c2 = a.c2;
+    if (a.ts) {
+        lr = a.ts->lr;
+        c1 = a.ts->c1;
+        c2 = a.ts->c2;
+    }
     const float g = grad[i];
     const float mi = a.beta1 * m1[i] + (1.0f - a.beta1) * g;
     const float vi = a.beta2 * m2[i] + (1.0f - a.beta2) * g * g;
     m1[i] = mi;
     m2[i] = vi;
-    const float th = theta[i] - a.lr * (mi * a.c1) / (sqrtf(vi * a.c2) + a.eps);
+    const float th = theta[i] - lr * (mi * c1) / (sqrtf(vi * c2) + a.eps);
     theta[i] = th;
     const int w = wmap[i];
     if (w >= 0) wbf[w] = __float2bfloat16_rn(th);
+}
+
+__global__ void k_train_reset(TrainState* ts, int t0)
+{
+    ts->k = 0;
+    ts->t0 = t0;
+}
+
+// The step's learning rate and Adam bias corrections (the same double-precision formula the
+// single-step call evaluates on the host), and the loss accumulator zeroed.
+__global__ void k_train_begin(TrainState* ts, const float* __restrict__ lr_dev, float beta1, float beta2, double* loss)
+{
+    const int k = ts->k + 1;
+    const double t = (double)(ts->t0 + k);
+    ts->k = k;
+    ts->lr = lr_dev[k - 1];
+    ts->c1 = (float)(1.0 / (1.0 - pow((double)beta1, t)));
+    ts->c2 = (float)(1.0 / (1.0 - pow((double)beta2, t)));
+    *loss = 0.0;
 }
 
 // BF16 copy of the weights from the FP32 parameters.
@@ -1070,6 +1095,18 @@ cudaError_t launch_adam(float* theta, float* m1, float* m2, const float* grad, l
                         const int* wmap, __nv_bfloat16* wbf, cudaStream_t s)
 {
     k_adam<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(theta, m1, m2, grad, n, a, wmap, wbf);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_train_reset(TrainState* ts, int t0, cudaStream_t s)
+{
+    k_train_reset<<<1, 1, 0, s>>>(ts, t0);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_train_begin(TrainState* ts, const float* lr_dev, float beta1, float beta2, double* loss, cudaStream_t s)
+{
+    k_train_begin<<<1, 1, 0, s>>>(ts, lr_dev, beta1, beta2, loss);
     return cudaGetLastError();
 }
 

@@ -96,6 +96,17 @@ class MLP:
                                                 int(x.shape[0]), float(lr), float(beta1), float(beta2),
                                                 float(eps), ptr))
 
+    def train(self, x, t, lr, beta1: float = 0.9, beta2: float = 0.999, eps: float = 1e-8, sse=None) -> None:
+        """len(lr) training steps, step k with learning rate lr[k] (an FP32 device tensor), in
+        one call (CUDA-graph replays on this network's stream; asynchronous)."""
+        import torch
+        x, t = self._dev(x, N_IN), self._dev(t, N_OUT)
+        assert isinstance(lr, torch.Tensor) and lr.is_cuda and lr.dtype == torch.float32 and lr.is_contiguous()
+        ptr = C.c_void_p(sse.data_ptr()) if sse is not None else None
+        self._check(load().salec_mlp_train(self._h, C.c_void_p(x.data_ptr()), C.c_void_p(t.data_ptr()),
+                                           int(x.shape[0]), int(lr.numel()), C.c_void_p(lr.data_ptr()),
+                                           float(beta1), float(beta2), float(eps), ptr))
+
     def check(self) -> None:
         self._check(load().salec_mlp_check(self._h))
 
@@ -226,21 +237,31 @@ def generate(seeds, n: int = 400, group: int = 1024, log=None, partial=None, **k
     return out
 
 
-def train(X, T, steps: int = 4000, lr: float = 2e-3, seed: int = 0, batch_max: int = 4096, log=None) -> "MLP":
-    """Full-batch Adam on (X, T) with a cosine learning-rate decay; returns the network."""
+def cosine_lr(steps: int, lr: float) -> np.ndarray:
+    """Learning rates of a cosine decay from lr over `steps` steps (FP32)."""
+    return np.array([lr * 0.5 * (1.0 + math.cos(math.pi * s / steps)) for s in range(steps)], dtype=np.float32)
+
+
+def train(X, T, steps: int = 4000, lr: float = 2e-3, seed: int = 0, batch_max: int = 4096, log=None,
+          stream=None) -> "MLP":
+    """Full-batch Adam on (X, T) with a cosine learning-rate decay; returns the network.  The
+    steps go out as one multi-step call (pieces of 1000 with `log`, to report the loss), on
+    `stream` if given; asynchronous unless `log` is given."""
     import torch
     from . import workloads as W
-    net = MLP(max(batch_max, len(X)))
+    net = MLP(max(batch_max, len(X)), stream=stream)
     net.set_params(W.mlp_init(seed).astype(np.float32))
     Xd = torch.from_numpy(np.ascontiguousarray(X, dtype=np.float32)).cuda()
     Td = torch.from_numpy(np.ascontiguousarray(T, dtype=np.float32)).cuda()
-    for s in range(steps):
-        a = lr * 0.5 * (1.0 + math.cos(math.pi * s / steps))
-        net.train_step(Xd, Td, a)
-        if log and (s % 1000 == 0 or s == steps - 1):
+    L = torch.from_numpy(cosine_lr(steps, lr)).cuda()
+    torch.cuda.current_stream().synchronize()        # the inputs, before another stream reads them
+    net.keep = (Xd, Td, L)                           # alive until the network's stream is done
+    piece = 1000 if log else steps
+    for s0 in range(0, steps, piece):
+        net.train(Xd, Td, L[s0:s0 + piece])
+        if log:
             loss, _ = net.gradient(Xd, Td)
-            log(f"  step {s}: loss {loss:.3e}")
-    net.check()
+            log(f"  step {min(s0 + piece, steps) - 1}: loss {loss:.3e}")
     return net
 
 
@@ -274,8 +295,14 @@ class Ensemble:
     prediction is trusted or the draw goes to the solver."""
 
     def __init__(self, X, T, members: int = 4, steps: int = 4000, lr: float = 2e-3, log=None):
+        import torch
         Tw = to_network(T)
-        self.nets = [train(X, Tw, steps=steps, lr=lr, seed=1000 + k, log=log) for k in range(members)]
+        # each member on its own stream: the members' small GEMMs run concurrently
+        self.streams = [torch.cuda.Stream() for _ in range(members)]
+        self.nets = [train(X, Tw, steps=steps, lr=lr, seed=1000 + k, log=log, stream=self.streams[k])
+                     for k in range(members)]
+        for net in self.nets:
+            net.check()
 
     def predict(self, X):
         """(mean outputs, relative spread of transient depth, of diameter) for inputs X: the

@@ -217,3 +217,55 @@ def test_training_reduces_loss():
     l1, _ = net.gradient(Xd, Td)
     net.check()
     assert l1 < 0.1 * l0, (l0, l1)
+
+
+def test_multi_step_training_matches_single_steps():
+    """salec_mlp_train: 60 steps as one call (one plain step, two 25-step graph replays, nine
+    plain steps), learning rates from a device table, against 60 single-step calls with
+    the same rates: the same arithmetic per step, the bias corrections formed on the device
+    instead of the host (both in double precision)."""
+    X, T = _data(700, seed=5)
+    Xd, Td = torch.from_numpy(X).cuda(), torch.from_numpy(T).cuda()
+    lr = S.cosine_lr(60, 2e-3)
+    a = S.MLP(700)
+    a.set_params(W.mlp_init(4).astype(np.float32))
+    for k in range(60):
+        a.train_step(Xd, Td, float(lr[k]))
+    b = S.MLP(700)
+    b.set_params(W.mlp_init(4).astype(np.float32))
+    b.train(Xd, Td, torch.from_numpy(lr).cuda())
+    pa, pb = a.get_params(), b.get_params()
+    d = float(np.max(np.abs(pa - pb)) / np.max(np.abs(pa)))
+    print("multi-step vs single steps: max parameter difference", d)
+    assert d <= 1e-6
+    # a second call continues the Adam step count
+    b.train(Xd, Td, torch.from_numpy(lr[:30]).cuda())
+    for k in range(30):
+        a.train_step(Xd, Td, float(lr[k]))
+    assert float(np.max(np.abs(a.get_params() - b.get_params())) / np.max(np.abs(pa))) <= 1e-6
+
+
+def test_networks_on_separate_streams_train_as_alone():
+    """Two networks trained at the same time on two streams end with the parameters each
+    has when trained alone, bit for bit."""
+    X, T = _data(900, seed=8)
+    Xd, Td = torch.from_numpy(X).cuda(), torch.from_numpy(T).cuda()
+    L = torch.from_numpy(S.cosine_lr(80, 2e-3)).cuda()
+    alone = []
+    for seed in (1, 2):
+        n = S.MLP(900)
+        n.set_params(W.mlp_init(seed).astype(np.float32))
+        n.train(Xd, Td, L)
+        alone.append(n.get_params())
+    streams = [torch.cuda.Stream(), torch.cuda.Stream()]
+    nets = []
+    for seed, st in zip((1, 2), streams):
+        n = S.MLP(900, stream=st)
+        n.set_params(W.mlp_init(seed).astype(np.float32))
+        nets.append(n)
+    torch.cuda.synchronize()
+    for n in nets:
+        n.train(Xd, Td, L)
+    for n, ref in zip(nets, alone):
+        n.check()
+        assert np.array_equal(n.get_params(), ref)
