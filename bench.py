@@ -227,11 +227,13 @@ def batch_failures(polled, specs, half_diameters, cavity_in_strip=None) -> list:
             int(in_strip), int(failed.sum()) - int(in_strip)]
 
 
-def cavity_in_strip(phi, spec) -> bool:
-    """Whether the transient cavity has reached an absorbing strip: a strip cell (bottom
-    rows < pml_b, right columns >= nr - pml_r) below the initial surface holds less than
-    half matter.  The strips damp deviations from the initial state and are written for
-    small ones (Sect. 3); a run whose cavity reaches them is outside that regime."""
+def cavity_in_strip(phi, spec, density_ratio=None) -> bool:
+    """Whether a cavity has reached an absorbing strip: a strip cell (bottom rows < pml_b,
+    right columns >= nr - pml_r) below the initial surface holds less than half matter, or
+    its matter has been torn open to below 1 % of its reference density (density_ratio:
+    sum f_m rho_m / sum f_m rho0_m per cell, where matter is present).  The strips damp
+    deviations from the initial state and are written for small ones (Sect. 3); a run whose
+    cavity reaches them is outside that regime."""
     import numpy as np
     g = spec["grid"]
     nr, nz, pb, pr = g["nr"], g["nz"], g.get("pml_b", 0), g.get("pml_r", 0)
@@ -240,7 +242,21 @@ def cavity_in_strip(phi, spec) -> bool:
     strip[:pb, :] = True
     strip[:, nr - pr:] = True
     strip[ks:, :] = False
-    return bool((np.asarray(phi)[strip] < 0.5).any())
+    hole = np.asarray(phi) < 0.5
+    if density_ratio is not None:
+        hole |= np.asarray(density_ratio) < 0.01
+    return bool(hole[strip].any())
+
+
+def density_ratio(sim, spec):
+    """Per cell sum f_m rho_m / sum f_m rho0_m (1 where no matter is present)."""
+    import numpy as np
+    num, den = 0.0, 0.0
+    for m, mat in enumerate(spec["materials"]):
+        f = sim.get(f"f{m}")
+        num = num + f * sim.get(f"rho{m}")
+        den = den + f * mat["rho0"]
+    return np.where(den > 0, num / np.where(den > 0, den, 1.0), 1.0)
 
 
 def _batched(args, rank, ws):
@@ -288,7 +304,8 @@ def _batched(args, rank, ws):
     # and where each failed run stopped, whether its cavity had reached a strip
     half = [None if failed[k] else 0.5 * sims[k].crater(sp["z_surface"], 64)["diameter"]
             for k, sp in enumerate(specs)]
-    cav = [cavity_in_strip(sum(sims[k].get(f"f{m}") for m in range(len(sp["materials"]))), sp) if failed[k] else None
+    cav = [cavity_in_strip(sum(sims[k].get(f"f{m}") for m in range(len(sp["materials"]))), sp,
+                           density_ratio(sims[k], sp)) if failed[k] else None
            for k, sp in enumerate(specs)]
     causes = batch_failures(polled, specs, half, cav)
     (tmax,), (nfin, nfail, ncomp, *causes) = job_reduce(
@@ -397,9 +414,13 @@ def _surrogate(args):
             c = ref.crater(sp["z_surface"], 64)
             errs.append(abs(c["diameter"] / (1000.0 * float(Th[k, S.N_PROFILE + 1])) - 1.0))
         del one, ref
+    fwd = 2.0 * sum(a * b for a, b in zip(S.DIMS[:-1], S.DIMS[1:]))        # flops per sample
     out = {"train_draws": int(ok_tr.sum()), "heldout_draws": int(ok_ho.sum()),
            "failed_runs_excluded": int((~ok_tr).sum() + (~ok_ho).sum()),
            "members": args.sur_members, "train_steps": args.sur_steps, "train_s": round(t_train, 2),
+           # the whole ensemble's training (members concurrently on their own streams,
+           # 25-step graph replays): forward + backward = 3 forward passes per sample and step
+           "train_tflops_ensemble": round(3.0 * fwd * len(Xf) * args.sur_members * args.sur_steps / t_train / 1e12, 2),
            "fp64_solver_runs": nsol, "fp64_solver_failed": nfail}
     if nsol:
         rep = S.gain_report(ens, tau, Xh, Th, t_sol / nsol)
@@ -426,7 +447,6 @@ def _surrogate(args):
     net = ens.nets[0]
     Xd = torch.from_numpy(np.ascontiguousarray(Xf, dtype=np.float32)).cuda()
     Td = torch.from_numpy(np.ascontiguousarray(Tf, dtype=np.float32)).cuda()
-    fwd = 2.0 * sum(a * b for a, b in zip(S.DIMS[:-1], S.DIMS[1:]))        # flops per sample
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     for _ in range(3):
         net.train_step(Xd, Td, 0.0)
@@ -437,7 +457,7 @@ def _surrogate(args):
     torch.cuda.synchronize()
     ms = ev0.elapsed_time(ev1) / 20
     out["train_step_ms"] = ms
-    out["train_tflops"] = 3.0 * fwd * len(Xf) / (ms * 1e-3) / 1e12
+    out["train_tflops_single_step"] = 3.0 * fwd * len(Xf) / (ms * 1e-3) / 1e12
     big = S.MLP(args.sur_infer_batch)
     big.set_params(net.get_params())
     Xb = torch.rand((args.sur_infer_batch, S.N_IN), device="cuda") * 2 - 1

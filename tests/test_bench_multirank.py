@@ -108,3 +108,12 @@ def test_cavity_in_strip_reads_the_strip_cells_below_the_surface():
     side = phi.copy()
     side[ks - 3, nr - pr] = 0.0                   # the crater rim reaches the right strip
     assert bench.cavity_in_strip(side, sp)
+    # matter torn open to a near-vacuum density at full fraction: in the strip it marks the
+    # run, inside the domain it does not
+    ratio = np.ones((nz, nr))
+    ratio[pb + 5, 0] = 0.005
+    assert not bench.cavity_in_strip(phi, sp, ratio)
+    ratio[pb - 3, 1] = 0.005
+    assert bench.cavity_in_strip(phi, sp, ratio)
+    ratio[pb - 3, 1] = 0.02
+    assert not bench.cavity_in_strip(phi, sp, ratio)
