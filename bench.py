@@ -3,8 +3,8 @@
 
 Workload (default): the 4000 x 4000 single-run configuration (10 m cells, basalt
 Tillotson half-space, hydrodynamic, projectile radius 100 cells at 10 km/s, PML 16 right
-and bottom, no gravity), FP64, K steps from t = 0 (default K = 2000, the configuration's
-run length).  One "step" is one full cycle of the hot path (EoS + artificial viscosity +
+and bottom, no gravity), FP64: W warm-up steps from t = 0, then K timed steps that continue
+the run (default K = 2000, the configuration's run length).  One "step" is one full cycle of the hot path (EoS + artificial viscosity +
 Courant min-reduction, Lagrangian momentum/energy/strength, PML, donor-cell remap,
 momentum remap, heat) over all 16e6 cells.  The state (~1.3 GB) is larger than L2, so no
 flush is needed between steps.
@@ -363,6 +363,53 @@ def _batched(args, rank, ws):
     return out
 
 
+def _batch_modes(args):
+    """The two batched launch forms on the same runs: graph replays of six kernels and a
+    Courant kernel per step (the default), against one persistent cooperative launch per
+    chunk with grid-wide barriers between the phases.  Each form steps fresh copies of the
+    runs from t = 0, after one untimed chunk, with its own autotuned block shapes; ms per
+    batched step over the timed chunks, by CUDA events on the batch stream.  Two cases: the
+    batched workload's full draw (every run active, large work per phase) and 16 runs of
+    200 x 200 cells (little work per phase: launch and barrier costs show)."""
+    import torch
+    from paper_2403_04267_gb300 import salec, workloads as W
+    out = {}
+    cases = [("full_draw", args.batch_runs, None), ("small_16x200", 16, 200)]
+    for name, nruns, n in cases:
+        specs = []
+        for sd in range(nruns):
+            d = W.batched_draw(sd)
+            if n:
+                d["n"] = n
+            specs.append(W.batched_run(d))
+        res = {"runs": nruns, "cells_per_step": sum(sp["grid"]["nr"] * sp["grid"]["nz"] for sp in specs)}
+        chunk, chunks = 25, 8 if n is None else 40
+        for mode in ("graph", "persistent"):
+            sims = [salec.Sim(sp, precision="fp32mix") for sp in specs]
+            b = salec.Batch(sims)
+            if mode == "persistent":
+                b.persistent = True
+            shapes = b.autotune(trial_steps=2)
+            b.run(chunk=chunk, max_steps=chunk)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            e0.record(b.stream)
+            for _ in range(chunks):
+                b.run(chunk=chunk, max_steps=chunk)
+            e1.record(b.stream)
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1) / (chunk * chunks)
+            res[mode] = {"ms_per_step": round(ms, 4), "block_shapes": shapes[:1] if mode == "persistent" else shapes,
+                         "launches_per_step": 7 if mode == "graph" else round(1.0 / chunk, 3)}
+            del b, sims
+            torch.cuda.empty_cache()
+        res["persistent_over_graph"] = round(res["persistent"]["ms_per_step"] / res["graph"]["ms_per_step"], 3)
+        out[name] = res
+    out["note"] = ("ms per batched step (every active run advances one step), FP32-mix, strength, two materials, "
+                   "gravity; each chunk ends with a poll of the runs' scalars in both forms")
+    return out
+
+
 def _surrogate(args):
     """The crater surrogate: an ensemble of MLPs trained on the GPU by the library's own
     tcgen05 kernels on the batched solver's 400 x 400 runs (4096 training draws, 256
@@ -448,12 +495,13 @@ def _surrogate(args):
     Xd = torch.from_numpy(np.ascontiguousarray(Xf, dtype=np.float32)).cuda()
     Td = torch.from_numpy(np.ascontiguousarray(Tf, dtype=np.float32)).cuda()
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()                 # the inputs, before the network's stream reads them
     for _ in range(3):
         net.train_step(Xd, Td, 0.0)
-    ev0.record()
+    ev0.record(net.stream)                   # the events on the stream the steps run on
     for _ in range(20):
         net.train_step(Xd, Td, 0.0)
-    ev1.record()
+    ev1.record(net.stream)
     torch.cuda.synchronize()
     ms = ev0.elapsed_time(ev1) / 20
     out["train_step_ms"] = ms
@@ -698,8 +746,9 @@ def main():
         torch.cuda.synchronize()
 
     def measure(precision, with_e2e, form=None):
-        """Device-timed K steps from t = 0 (after W warm-up steps and a restore), with live
-        per-kernel events; then optionally the same K steps end to end through the C ABI."""
+        """Device-timed K steps that continue the run after its W warm-up steps (steps W + 1
+        to W + K of the workload), with live per-kernel events; then optionally K steps from
+        t = 0 end to end through the C ABI (initial state copied from the host)."""
         sim = salec.Sim(spec, precision=precision)
         form = form or (None if args.form == "default" else args.form)
         if form:
@@ -715,7 +764,7 @@ def main():
 
         sim.step(args.warmup)
         torch.cuda.synchronize()
-        restore()
+        snap = sim.get_state() if sim.step_form == "fused" else None    # host copy of the timed steps' start
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         sim.set_kernel_timing(True)
@@ -733,14 +782,15 @@ def main():
         if sim.step_form == "fused":
             # the same K steps again, untimed, one call each: how many tiles each step ran
             # through the whole cycle (the others the rest-tile kernel copied)
-            restore()
+            sim.set_state(snap)
             qs = []
             for _ in range(args.steps):
                 sim.step(1)
                 qs.append(sim.fused_queue()[0])
             tiles = sim.fused_queue()[1]
             queue = {"tiles": tiles, "queued_mean": float(np.mean(qs)), "queued_first": qs[0], "queued_last": qs[-1],
-                     "note": "the first step after the restore queues every tile (no tile is yet known to be at rest)"}
+                     "note": "steps W + 1 .. W + K; the replay restarts from a host copy, so its first step "
+                             "follows a Courant-rate pass"}
         ms_max = ms
         if ws > 1:
             t = torch.tensor([ms], device="cuda", dtype=torch.float64)
@@ -748,8 +798,7 @@ def main():
             ms_max = float(t.item())
         out = {"value": ws * cells * args.steps / (ms_max * 1e-3), "ms": ms, "ms_max": ms_max, "ktimes": ktimes,
                "scalars": sc, "clocks": clk.summary(),
-               # a fused sequence after the restore starts with one pass of Courant rates
-               "launches": sim.launches_per_step() * args.steps + (1 if sim.step_form == "fused" else 0),
+               "launches": sim.launches_per_step() * args.steps,
                "form": sim.step_form, "pmax": sim.get("pmax"), "queue": queue}
         if with_e2e:
             host = torch.empty(nbytes, dtype=torch.uint8, pin_memory=True)
@@ -829,12 +878,12 @@ def main():
 
         def alu_roof(d):
             kt = main_res["ktimes"][d]
-            if d in _FUSED_FULL_SIZE.get("fp64", {}):
-                full = _FUSED_FULL_SIZE["fp64"][d] if (args.workload, args.steps) == _FULL_SIZE_CASE else {}
+            if d in _FUSED_FULL_SIZE.get("fp64", {}) and d not in _COUNTERS_STALE["fp64"]:
+                full = _FUSED_FULL_SIZE["fp64"][d] if (args.workload, args.steps, args.warmup) == _FULL_SIZE_CASE else {}
                 flops = full.get("flops")
                 ach = flops / (kt * 1e-3) / 1e12 if flops else None
                 per = {"flops_per_launch": flops, "flops_kind": "ncu FP64 instruction counts of the same 20 launches "
-                       "(large_4000 from t = 0), mean per launch" if flops else "not captured for this workload / K"}
+                       "(large_4000, after 5 warm-up steps), mean per launch" if flops else "not captured for this workload / K / W"}
             else:
                 stale = d in _COUNTERS_STALE["fp64"]
                 flops = None if stale else _FLOPS_PER_CELL.get(d)
@@ -926,6 +975,8 @@ def main():
         line["layered"] = _layered(args)
     if not args.no_batch and args.batch_runs > 0:
         line["batched"] = _batched(args, rank, ws)
+        if ws == 1:
+            line["batched"]["launch_forms"] = _batch_modes(args)
     if not args.no_surrogate and ws == 1:
         line["surrogate"] = _surrogate(args)
     if ws == 1 and not args.no_cpu:
@@ -946,14 +997,15 @@ _TRAFFIC_PER_CELL_FP32MIX: dict = {"k_phase0": 27.7, "k_phase1": 30.8, "k_phase2
 # sm__pipe_fp64_cycles_active, 2000 x 2000, the fused kernels at the second timed step)
 _FP64_PIPE_BUSY: dict = {"k_phase0": 0.847, "k_phase1": 0.847, "k_phase2": 0.845, "k_phase3a": 0.847, "k_phase3b": 0.841,
                          "k_phase3c": 0.783, "k_step_fused": 0.735, "k_rest_tiles": 0.180}
-# The fused form's two kernels on the headline workload (4000 x 4000, K = 20 timed steps from
-# t = 0): DRAM read + write bytes and FP64 operations per launch, the mean over the 20 launches
-# of the timed region from one-pass ncu captures of the same command (profiles/).  The rest
-# flags make these launches depend on the step sequence, so they hold for that case only.
-_FULL_SIZE_CASE = ("large_4000", 20)
+# The fused form's two kernels on the headline workload (4000 x 4000, K = 20 timed steps after
+# W = 5 warm-up steps): DRAM read + write bytes and FP64 operations per launch, the mean over
+# the 20 launches of the timed region from one-pass ncu captures of the same command
+# (profiles/).  The rest flags make these launches depend on the step sequence, so they hold
+# for that case only.
+_FULL_SIZE_CASE = ("large_4000", 20, 5)
 _FUSED_FULL_SIZE: dict = {
-    "fp64": {"k_rest_tiles": {"traffic": 1.3585e9}, "k_step_fused": {"traffic": 1.3462e8, "flops": 1.2507e8}},
-    "fp32mix": {"k_rest_tiles": {"traffic": 7.6605e8}, "k_step_fused": {"traffic": 7.9006e7}},
+    "fp64": {"k_rest_tiles": {"traffic": 1.4301e9}, "k_step_fused": {"traffic": 4.2005e7, "flops": 1.14608e8}},
+    "fp32mix": {"k_rest_tiles": {"traffic": 8.0675e8}, "k_step_fused": {"traffic": 2.6107e7}},
 }
 # kernels changed since their counters were taken: neither DRAM traffic nor flop rates are
 # reported for them until the next capture
@@ -966,7 +1018,7 @@ def _traffic(kernel: str, prec: str, args):
     if kernel in _COUNTERS_STALE[prec]:
         return None, "counters stale"
     if kernel in _FUSED_FULL_SIZE[prec]:
-        if (args.workload, args.steps) != _FULL_SIZE_CASE:
+        if (args.workload, args.steps, args.warmup) != _FULL_SIZE_CASE:
             return None, "not captured for this workload / K"
         return _FUSED_FULL_SIZE[prec][kernel]["traffic"], "ncu, the same 20 launches, mean per launch"
     table = _TRAFFIC_PER_CELL if prec == "fp64" else _TRAFFIC_PER_CELL_FP32MIX

@@ -41,8 +41,10 @@ typedef enum {
     SALEC_ENOMEM = 2,      /* the state buffer is too small or misaligned */
     SALEC_ECUDA = 3,       /* a CUDA call failed (message in salec_last_error) */
     SALEC_EORDER = 4,      /* call made before/after the stage it belongs to */
-    SALEC_EUNSTABLE = 5    /* the device status word reports a non-positive volume or
+    SALEC_EUNSTABLE = 5,   /* the device status word reports a non-positive volume or
                               density, a NaN, or dt below dt_min (see salec_get_scalars) */
+    SALEC_ETIMEOUT = 6     /* a bounded device wait ran out (the persistent batch's grid
+                              barrier); the runs' states are partly advanced */
 } salec_status;
 
 /* Arithmetic of the step.  SALEC_FP64: every field and operation in FP64.
@@ -192,6 +194,15 @@ enum { SALEC_STEP_PHASES = 0, SALEC_STEP_FUSED = 1 };
 salec_status salec_set_step_form(salec_ctx* ctx, int form);
 int salec_get_step_form(const salec_ctx* ctx);
 
+/* Fused form: copy the tiles at rest (on != 0, the default) or send every tile through
+ * the tile kernel (on = 0).  A tile is at rest when it and its eight neighbours passed
+ * the tile kernel's quiescence test in the step before (or, for the first fused step
+ * after set-up, a host write or other steps, when the Courant-rate pass over that state
+ * found them quiescent with fields already in the form the quiescent path writes); the
+ * copy returns bit for bit what the tile kernel would, so this switch changes no result,
+ * only the work done (for checking that).  SALEC_EINVAL for a null context. */
+salec_status salec_set_rest_copy(salec_ctx* ctx, int on);
+
 /* Synchronise and read the scalars: out[0] t, out[1] dt of the last step, out[2] step
  * count, out[3] status bits (1 non-positive volume/density, 2 NaN, 4 dt < dt_min),
  * out[4] mass out through the top, out[5] mass removed by clean-up, out[6] mass added by
@@ -291,6 +302,29 @@ salec_status salec_batch_step(salec_batch* batch, int nsteps);
 salec_status salec_batch_run(salec_batch* batch, int chunk, long max_steps, long* steps_done, int* runs_done);
 salec_status salec_batch_poll(salec_batch* batch, double* out);
 salec_status salec_batch_autotune(salec_batch* batch, int trial_steps, int* shapes_out);
+
+/* Persistent mode (on != 0; off is the default): each salec_batch_step call, and each
+ * chunk of salec_batch_run (captured in its CUDA graph with the clearing of the barrier
+ * word, or launched directly where the device refuses to capture it), is ONE cooperative
+ * launch of a grid that the device holds at once.  Its blocks loop over the steps and, in
+ * each, over the (run, tile) entries of every phase, with a grid-wide barrier between the
+ * phases and a pass of per-run Courant steps after phase 0: the same code per cell and
+ * vertex as the six launches per step, so the fields are bitwise those of the default
+ * mode.  Every phase takes one block shape of at most 256 threads (the first kernel's,
+ * else 32 x 4; salec_batch_autotune then picks one shape for all six).  Every barrier wait
+ * is bounded (2 s); a wait that ran out ends the launch and the next salec_batch_poll or
+ * salec_batch_run returns SALEC_ETIMEOUT.  SALEC_ECUDA when the kernel cannot be made
+ * resident. */
+salec_status salec_batch_set_persistent(salec_batch* batch, int on);
+
+/* Failure detection, for testing it: the next salec_batch_step call (persistent mode)
+ * starts its launch with the barrier's arrival counter far above the grid size, so no
+ * block completes the first barrier (after phase 0 of the first step, which changes no
+ * persistent field but the peak over-pressure, with the same values a repeat writes).
+ * Every block's wait there runs out after 2 s and the launch ends; that step call's poll
+ * returns SALEC_ETIMEOUT, and later steps continue from the unchanged state.  SALEC_EINVAL
+ * outside persistent mode. */
+salec_status salec_batch_expire_next_barrier(salec_batch* batch);
 const char* salec_batch_last_error(const salec_batch* batch);
 void salec_batch_destroy(salec_batch* batch);
 

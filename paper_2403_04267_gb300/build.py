@@ -15,7 +15,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libsalec.so")
-SOURCES = ["salec_kernels.cu", "salec_fused.cu", "salec_api.cu", "salec_noalloc.cu", "mlp_kernels.cu", "mlp_api.cu"]
+SOURCES = ["salec_kernels.cu", "salec_persist.cu", "salec_fused.cu", "salec_api.cu", "salec_noalloc.cu", "mlp_kernels.cu",
+           "mlp_api.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -191,6 +191,7 @@ struct salec_ctx {
     OutPtrsT<float> Of[2];
     cudaGraphExec_t fgraph[2] = {nullptr, nullptr};   // fused chunks starting from copy 0 / 1
     bool fgraph_ok = true;
+    bool rest_copy = true;                // tiles at rest copied (salec_set_rest_copy)
     // optional per-kernel timing: 7 events per recorded step
     bool timing = false;
     std::vector<cudaEvent_t> ev;
@@ -777,9 +778,15 @@ static bool capture_step_graph(salec_ctx* ctx)
     return true;
 }
 
-// one fused step from the current copy; the next step reads the other one
+// one fused step from the current copy; the next step reads the other one.  With the copy
+// of tiles at rest switched off, the step's rest flags are cleared first: every tile then
+// goes through the tile kernel.
 static cudaError_t fused_step(salec_ctx* ctx, int parity, cudaStream_t s, cudaEvent_t* ev)
 {
+    if (!ctx->rest_copy) {
+        const cudaError_t e = cudaMemsetAsync(ctx->base + ctx->L.rest[parity], 0, ctx->L.ntiles, s);
+        if (e != cudaSuccess) return e;
+    }
     return mixed(ctx) ? launch_step_fused<float>(parity ? ctx->Pf_alt : ctx->Pf, ctx->Of[parity], s, ev)
                       : launch_step_fused<double>(parity ? ctx->Pd_alt : ctx->Pd, ctx->Od[parity], s, ev);
 }
@@ -799,16 +806,18 @@ static salec_status step_fused(salec_ctx* ctx, int nsteps)
     if (nsteps == 0) return SALEC_OK;
     // the running Courant maximum must hold the current state's rates: a fused step leaves
     // them for the next one; anything else (set-up, host writes, phase or batched steps)
-    // needs one pass over the state first
-    // and no tile counts as at rest until a step has found it quiescent
+    // needs one pass over the state first, which also flags the tiles that the quiescent
+    // path would return unchanged (the first step copies those whose neighbours are flagged)
     if (!ctx->rates_valid) {
         const Layout& L = ctx->L;
         cudaError_t e = canonical(ctx);
         if (e == cudaSuccess)
             e = cudaMemsetAsync(ctx->base + L.scal + offsetof(DevScalars, maxbits), 0, sizeof(unsigned long long), ctx->stream);
         if (e == cudaSuccess) e = cudaMemsetAsync(ctx->base + L.rest[0], 0, L.work + 2 * sizeof(TileWork) - L.rest[0], ctx->stream);
-        if (e == cudaSuccess) e = mixed(ctx) ? launch_courant_rates<float>(ctx->Pf, ctx->stream)
-                                             : launch_courant_rates<double>(ctx->Pd, ctx->stream);
+        if (e == cudaSuccess && ctx->rest_copy) e = cudaMemsetAsync(ctx->base + L.rest[0], 1, L.ntiles, ctx->stream);
+        unsigned char* rest0 = ctx->rest_copy ? at<unsigned char>(ctx, L.rest[0]) : nullptr;
+        if (e == cudaSuccess) e = mixed(ctx) ? launch_courant_rates<float>(ctx->Pf, rest0, ctx->stream)
+                                             : launch_courant_rates<double>(ctx->Pd, rest0, ctx->stream);
         if (e != cudaSuccess) return cuda_check(ctx, e, "Courant rates");
         ctx->rates_valid = true;
     }
@@ -899,6 +908,16 @@ salec_status salec_set_step_form(salec_ctx* ctx, int form)
 }
 
 int salec_get_step_form(const salec_ctx* ctx) { return ctx ? ctx->form : -1; }
+
+salec_status salec_set_rest_copy(salec_ctx* ctx, int on)
+{
+    if (!ctx) return SALEC_EINVAL;
+    if ((on != 0) == ctx->rest_copy) return SALEC_OK;
+    ctx->rest_copy = on != 0;
+    for (int k = 0; k < 2; ++k)
+        if (ctx->fgraph[k]) { cudaGraphExecDestroy(ctx->fgraph[k]); ctx->fgraph[k] = nullptr; }
+    return SALEC_OK;
+}
 
 salec_status salec_set_kernel_timing(salec_ctx* ctx, int on)
 {
@@ -1321,6 +1340,12 @@ struct salec_batch {
     std::vector<cudaEvent_t> ev;
     size_t ev_used = 0;
     std::string err;
+    // persistent mode (salec_batch_set_persistent): one cooperative launch per chunk
+    bool persistent = false;
+    int pctas = 0;                  // resident blocks of the persistent kernel
+    bool pgraph = true;             // its launch is captured in the chunk graph (false: capture refused)
+    size_t off_sync = 0;            // its grid barrier
+    bool expire_next = false;       // salec_batch_expire_next_barrier
 };
 
 static salec_status bfail(salec_batch* b, salec_status st, const char* msg)
@@ -1337,6 +1362,7 @@ static size_t batch_layout(salec_ctx* const* runs, int n, salec_batch* b)
     const size_t psize = runs[0]->precision == SALEC_FP32MIX ? sizeof(ParamsT<float>) : sizeof(ParamsT<double>);
     const size_t op = take(cur, psize * (size_t)n);
     const size_t opoll = take(cur, sizeof(double) * 5 * (size_t)n);
+    const size_t osync = take(cur, sizeof(GridSync));
     size_t ow[6];
     for (int k = 0; k < 6; ++k) {
         size_t cap = 0;
@@ -1353,6 +1379,7 @@ static size_t batch_layout(salec_ctx* const* runs, int n, salec_batch* b)
     if (b) {
         b->off_params = op;
         b->off_poll = opoll;
+        b->off_sync = osync;
         for (int k = 0; k < 6; ++k) b->off_work[k] = ow[k];
     }
     return cur;
@@ -1454,6 +1481,36 @@ static cudaError_t batch_launch(salec_batch* b, cudaEvent_t* ev)
                                      b->strength, b->uniform, work, b->ntiles, b->shape, b->stream, ev);
 }
 
+// Persistent mode: `steps` steps of every run in one cooperative launch (the cell work list
+// of kernel 0 and the vertex list of kernel 1; every kernel has the same block shape).
+static cudaError_t batch_launch_persistent(salec_batch* b, int steps, bool expire = false)
+{
+    const BatchTile* cells = reinterpret_cast<const BatchTile*>(b->dev + b->off_work[0]);
+    const BatchTile* verts = reinterpret_cast<const BatchTile*>(b->dev + b->off_work[1]);
+    GridSync* gs = reinterpret_cast<GridSync*>(b->dev + b->off_sync);
+    const int n = (int)b->runs.size();
+    if (b->precision == SALEC_FP32MIX)
+        return launch_batch_persistent<float>(reinterpret_cast<const ParamsT<float>*>(b->dev + b->off_params), n, b->nmat,
+                                              b->strength, b->uniform, cells, b->ntiles[0], verts, b->ntiles[1], b->shape[0],
+                                              b->pctas, steps, gs, expire, b->stream);
+    return launch_batch_persistent<double>(reinterpret_cast<const ParamsT<double>*>(b->dev + b->off_params), n, b->nmat,
+                                           b->strength, b->uniform, cells, b->ntiles[0], verts, b->ntiles[1], b->shape[0],
+                                           b->pctas, steps, gs, expire, b->stream);
+}
+
+// the resident grid of the persistent kernel for the current block shape
+static salec_status batch_prepare_persistent(salec_batch* b)
+{
+    const cudaError_t e = b->precision == SALEC_FP32MIX
+                              ? prepare_batch_persistent<float>(b->nmat, b->strength, b->uniform, b->shape[0], &b->pctas)
+                              : prepare_batch_persistent<double>(b->nmat, b->strength, b->uniform, b->shape[0], &b->pctas);
+    if (e != cudaSuccess) {
+        (void)cudaGetLastError();
+        return bfail(b, SALEC_ECUDA, cudaGetErrorString(e));
+    }
+    return SALEC_OK;
+}
+
 static salec_status batch_restore_retired(salec_batch* b);
 
 // a run stepped alone in the fused form since the last batched step has its fields in the
@@ -1471,6 +1528,26 @@ salec_status salec_batch_step(salec_batch* b, int nsteps)
     salec_status st0 = batch_fields(b);
     if (st0 == SALEC_OK) st0 = batch_restore_retired(b);
     if (st0 != SALEC_OK) return st0;
+    if (b->persistent) {
+        // one launch for the n steps; with timing on, an event before and one after it
+        if (nsteps == 0) return SALEC_OK;
+        cudaEvent_t* evp = nullptr;
+        if (b->timing) {
+            while (b->ev_used + 2 > b->ev.size()) {
+                cudaEvent_t e0;
+                if (cudaEventCreate(&e0) != cudaSuccess) return bfail(b, SALEC_ECUDA, "event create");
+                b->ev.push_back(e0);
+            }
+            evp = b->ev.data() + b->ev_used;
+            b->ev_used += 2;
+            cudaEventRecord(evp[0], b->stream);
+        }
+        const cudaError_t e = batch_launch_persistent(b, nsteps, b->expire_next);
+        b->expire_next = false;
+        if (e != cudaSuccess) return bfail(b, SALEC_ECUDA, cudaGetErrorString(e));
+        if (evp) cudaEventRecord(evp[1], b->stream);
+        return SALEC_OK;
+    }
     const int K = launches_per_step() + 1;
     for (int n = 0; n < nsteps; ++n) {
         cudaEvent_t* evp = nullptr;
@@ -1499,8 +1576,17 @@ salec_status salec_batch_poll(salec_batch* b, double* out)
                         ? launch_batch_poll<float>(reinterpret_cast<const ParamsT<float>*>(b->dev + b->off_params), n, d, b->stream)
                         : launch_batch_poll<double>(reinterpret_cast<const ParamsT<double>*>(b->dev + b->off_params), n, d, b->stream);
     if (e == cudaSuccess) e = cudaMemcpyAsync(out, d, sizeof(double) * 5 * n, cudaMemcpyDeviceToHost, b->stream);
+    GridSync gs = {0, 0, 0, 0};
+    if (e == cudaSuccess && b->persistent)
+        e = cudaMemcpyAsync(&gs, b->dev + b->off_sync, sizeof(gs), cudaMemcpyDeviceToHost, b->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
     if (e != cudaSuccess) return bfail(b, SALEC_ECUDA, cudaGetErrorString(e));
+    if (gs.err) {
+        char msg[160];
+        snprintf(msg, sizeof msg, "persistent batch: a grid-barrier wait ran out (step %d of the launch, barrier %d)",
+                 (gs.where - 1) / 8, (gs.where - 1) % 8);
+        return bfail(b, SALEC_ETIMEOUT, msg);
+    }
     return SALEC_OK;
 }
 
@@ -1513,7 +1599,10 @@ static salec_status batch_capture(salec_batch* b, int chunk)
         (void)cudaGetLastError();   // do not leave the error for a later, unrelated check
         return bfail(b, SALEC_ECUDA, cudaGetErrorString(e));
     }
-    for (int k = 0; k < chunk && e == cudaSuccess; ++k) e = batch_launch(b, nullptr);
+    if (b->persistent)
+        e = batch_launch_persistent(b, chunk);
+    else
+        for (int k = 0; k < chunk && e == cudaSuccess; ++k) e = batch_launch(b, nullptr);
     const cudaError_t e2 = cudaStreamEndCapture(b->stream, &g);
     if (e != cudaSuccess || e2 != cudaSuccess) {
         if (g) cudaGraphDestroy(g);
@@ -1568,12 +1657,22 @@ salec_status salec_batch_run(salec_batch* b, int chunk, long max_steps, long* st
     long done_steps = 0;
     int done = 0;
     while (done_steps < max_steps) {
-        if (!b->graph) {
-            const salec_status st = batch_capture(b, chunk);
-            if (st != SALEC_OK) return st;
+        if (b->persistent && !b->pgraph) {
+            // the cooperative launch could not be captured: launch it directly
+            const cudaError_t e = batch_launch_persistent(b, chunk);
+            if (e != cudaSuccess) return bfail(b, SALEC_ECUDA, cudaGetErrorString(e));
+        } else {
+            if (!b->graph) {
+                const salec_status st = batch_capture(b, chunk);
+                if (st != SALEC_OK && b->persistent) {
+                    b->pgraph = false;
+                    continue;
+                }
+                if (st != SALEC_OK) return st;
+            }
+            const cudaError_t e = cudaGraphLaunch(b->graph, b->stream);
+            if (e != cudaSuccess) return bfail(b, SALEC_ECUDA, cudaGetErrorString(e));
         }
-        const cudaError_t e = cudaGraphLaunch(b->graph, b->stream);
-        if (e != cudaSuccess) return bfail(b, SALEC_ECUDA, cudaGetErrorString(e));
         done_steps += chunk;
         const salec_status st = salec_batch_poll(b, poll.data());
         if (st != SALEC_OK) return st;
@@ -1603,9 +1702,65 @@ salec_status salec_batch_run(salec_batch* b, int chunk, long max_steps, long* st
     return SALEC_OK;
 }
 
+// Persistent mode: one block shape for every phase, chosen by the time of trial_steps
+// steps in one launch.
+static salec_status batch_autotune_persistent(salec_batch* b, int trial_steps, int* shapes_out)
+{
+    double best = 1e300;
+    dim3 pick = b->shape[0];
+    for (int c = 0; c < kNumShapes; ++c) {
+        if (kShapes[c].x * kShapes[c].y > (unsigned)kPersistMaxThreads) continue;
+        for (int k = 0; k < 6; ++k) b->shape[k] = kShapes[c];
+        salec_status st = batch_prepare_persistent(b);
+        if (st == SALEC_OK) st = batch_build_work(b);
+        b->timing = false;
+        if (st == SALEC_OK) st = salec_batch_step(b, 1);
+        b->timing = true;
+        b->ev_used = 0;
+        if (st == SALEC_OK) st = salec_batch_step(b, trial_steps);
+        b->timing = false;
+        if (st != SALEC_OK) return st;
+        if (cudaStreamSynchronize(b->stream) != cudaSuccess) return bfail(b, SALEC_ECUDA, "sync");
+        float ms = 0.0f;
+        cudaEventElapsedTime(&ms, b->ev[0], b->ev[1]);
+        b->ev_used = 0;
+        if (ms < best) { best = ms; pick = kShapes[c]; }
+    }
+    for (int k = 0; k < 6; ++k) b->shape[k] = pick;
+    salec_status st = batch_prepare_persistent(b);
+    if (st == SALEC_OK) st = batch_build_work(b);
+    if (shapes_out)
+        for (int k = 0; k < 6; ++k) { shapes_out[2 * k] = (int)pick.x; shapes_out[2 * k + 1] = (int)pick.y; }
+    return st;
+}
+
+salec_status salec_batch_expire_next_barrier(salec_batch* b)
+{
+    if (!b || !b->persistent) return SALEC_EINVAL;
+    b->expire_next = true;
+    return SALEC_OK;
+}
+
+salec_status salec_batch_set_persistent(salec_batch* b, int on)
+{
+    if (!b) return SALEC_EINVAL;
+    b->persistent = on != 0;
+    if (b->persistent) {
+        // every phase takes the block shape of the first kernel (at most kPersistMaxThreads)
+        dim3 blk = b->shape[0];
+        if (blk.x * blk.y > (unsigned)kPersistMaxThreads) blk = dim3(32, 4);
+        for (int k = 0; k < 6; ++k) b->shape[k] = blk;
+        b->pgraph = true;
+        const salec_status st = batch_prepare_persistent(b);
+        if (st != SALEC_OK) { b->persistent = false; return st; }
+    }
+    return batch_build_work(b);
+}
+
 salec_status salec_batch_autotune(salec_batch* b, int trial_steps, int* shapes_out)
 {
     if (!b || trial_steps < 1) return SALEC_EINVAL;
+    if (b->persistent) return batch_autotune_persistent(b, trial_steps, shapes_out);
     const int K = launches_per_step();
     double best[6];
     dim3 pick[6];

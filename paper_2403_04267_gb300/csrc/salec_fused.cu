@@ -1130,10 +1130,18 @@ __global__ void __launch_bounds__(kRestThreads) k_rest_tiles(const ParamsT<T> P,
 
 // The equation of state of the current state into the cache and its Courant rates into the
 // running maximum (the first step of a sequence of fused steps, or after the host changed
-// the state): the phase-0 arithmetic of both.
-template <typename T, int NM, bool STR, bool UNI>
-__global__ void __launch_bounds__(kThreads) k_courant_rates(const ParamsT<T> P)
+// the state): the phase-0 arithmetic of both.  With rest (set to 1 for every tile before
+// the launch) it also clears the rest flag of every tile that the quiescent path would not
+// return bit for bit: one whose frame lies in a strip or under gravity, or one with a cell
+// or vertex that fails the quiescence test, or whose fields differ from what that path
+// writes (an absent material or an empty cell's energy not +0, deviatoric stress or a
+// damage that the path zeroes, a peak over-pressure the path would raise).  A tile whose
+// eight neighbours keep their flags too then has a quiescent frame and outputs equal to its
+// inputs, so the first fused step copies it instead of queueing it.
+template <typename T, int NM, bool STR, bool UNI, int TW, int TH>
+__global__ void __launch_bounds__(kThreads) k_courant_rates(const ParamsT<T> P, unsigned char* __restrict__ rest)
 {
+    static_assert(TW == kBlockX && TH % kBlockY == 0, "a block of the pass lies in one tile");
     typedef VT<T> V;
     typedef typename V::T2 T2;
     typedef Geo<T, UNI> GE;
@@ -1143,6 +1151,7 @@ __global__ void __launch_bounds__(kThreads) k_courant_rates(const ParamsT<T> P)
     const PtrsT<T>& p = P.p;
     const int nr = P.nr;
     T speed = zero;
+    bool q = true;          // cells outside the grid read as empty: quiescent
     if (i < nr && j < P.nz) {
         const int c = j * nr + i;
         T phi = zero, c2m = zero, phat = zero, p1 = zero;
@@ -1162,11 +1171,12 @@ __global__ void __launch_bounds__(kThreads) k_courant_rates(const ParamsT<T> P)
                 p1 = pm;
             }
         }
-        p.eosc[c] = V::mk(NM == 1 ? p1 : phat, c2m);
+        const T ecx = NM == 1 ? p1 : phat;
+        p.eosc[c] = V::mk(ecx, c2m);
+        const int nv = nr + 1;
+        const T2 va = p.v[j * nv + i], vb = p.v[j * nv + i + 1];
+        const T2 vc = p.v[(j + 1) * nv + i + 1], vd = p.v[(j + 1) * nv + i];
         if (pos(phi)) {
-            const int nv = nr + 1;
-            const T2 va = p.v[j * nv + i], vb = p.v[j * nv + i + 1];
-            const T2 vc = p.v[(j + 1) * nv + i + 1], vd = p.v[(j + 1) * nv + i];
             T w = va.x * va.x + va.y * va.y;
             w = max_nonneg(w, vb.x * vb.x + vb.y * vb.y);
             w = max_nonneg(w, vc.x * vc.x + vc.y * vc.y);
@@ -1175,6 +1185,37 @@ __global__ void __launch_bounds__(kThreads) k_courant_rates(const ParamsT<T> P)
             if (!UNI) speed = speed * GE::ilen(P, i, j);
             if (is_nan(speed)) atomicOr(&p.scal->status, 2);
         }
+        if (rest) {
+            // the quiescence test of the tile kernel on this cell and its corners, and its
+            // outputs equal to its inputs
+            q = !nonzero(va.x) && !nonzero(va.y) && !nonzero(vb.x) && !nonzero(vb.y) &&
+                !nonzero(vc.x) && !nonzero(vc.y) && !nonzero(vd.x) && !nonzero(vd.y) &&
+                !nonzero(ecx) && !is_nan(Ic);
+            T M = zero;
+#pragma unroll
+            for (int m = 0; m < NM; ++m) {
+                const T2 fr = p.fr[m][c];
+                if (pos(fr.x)) M += fr.x * fr.y;
+                q = q && (fr.x == T(1) || (is_pzero(fr.x) && is_pzero(fr.y)));
+            }
+            if (!pos(M)) q = q && is_pzero(p.I[c]);
+            if (STR) {
+                const T2 a = p.s01[c], b = p.s2d[c];
+                q = q && !nonzero(a.x) && !nonzero(a.y) && is_pzero(b.x) && ((pos(phi) && pos(M)) || is_pzero(b.y));
+            }
+            if (pos(phi)) {
+                const T over = (NM == 1 ? ecx : ecx * (T(1) / phi)) - p.p0[j];
+                q = q && !(over > p.pmax[c]);
+            }
+        }
+    }
+    if (rest) {
+        // the frame of the tile: outside the strips, no gravity
+        const int bx = blockIdx.x * kBlockX / TW, by = blockIdx.y * kBlockY / TH;
+        const int x0 = bx * TW - 3, y0 = by * TH - 3;
+        const bool frame = !nonzero(P.g) && y0 >= P.pb && x0 + TW + 6 <= nr - P.pr;
+        if (!__syncthreads_and(q && frame) && threadIdx.x == 0 && threadIdx.y == 0)
+            rest[by * ((nr + TW - 1) / TW) + bx] = 0;
     }
     __shared__ unsigned long long sh[kThreads / 32];
     const int tid = threadIdx.y * kBlockX + threadIdx.x;
@@ -1220,10 +1261,10 @@ struct Fused {
         k_step_fused<T, NM, STR, UNI, S::TW, S::TH, S::NT, S::MINB><<<O.ctas, S::NT, L::bytes, s>>>(P, O);
         return cudaGetLastError();
     }
-    static cudaError_t rates(const ParamsT<T>& P, cudaStream_t s)
+    static cudaError_t rates(const ParamsT<T>& P, unsigned char* rest, cudaStream_t s)
     {
         const dim3 g((P.nr + kBlockX - 1) / kBlockX, (P.nz + kBlockY - 1) / kBlockY);
-        k_courant_rates<T, NM, STR, UNI><<<g, dim3(kBlockX, kBlockY), 0, s>>>(P);
+        k_courant_rates<T, NM, STR, UNI, S::TW, S::TH><<<g, dim3(kBlockX, kBlockY), 0, s>>>(P, rest);
         return cudaGetLastError();
     }
 };
@@ -1271,9 +1312,9 @@ int fused_tiles(const ParamsT<T>& P)
 }
 
 template <typename T>
-cudaError_t launch_courant_rates(const ParamsT<T>& P, cudaStream_t s)
+cudaError_t launch_courant_rates(const ParamsT<T>& P, unsigned char* rest, cudaStream_t s)
 {
-    return dispatch<T, Fused>(P, [&](auto f) { return decltype(f)::rates(P, s); });
+    return dispatch<T, Fused>(P, [&](auto f) { return decltype(f)::rates(P, rest, s); });
 }
 
 // One fused cycle: the Courant kernel (dt from the running maximum of the rates), the
@@ -1298,8 +1339,8 @@ template int fused_tiles<double>(const ParamsT<double>&);
 template int fused_tiles<float>(const ParamsT<float>&);
 template size_t fused_smem_bytes<double>(const ParamsT<double>&);
 template size_t fused_smem_bytes<float>(const ParamsT<float>&);
-template cudaError_t launch_courant_rates<double>(const ParamsT<double>&, cudaStream_t);
-template cudaError_t launch_courant_rates<float>(const ParamsT<float>&, cudaStream_t);
+template cudaError_t launch_courant_rates<double>(const ParamsT<double>&, unsigned char*, cudaStream_t);
+template cudaError_t launch_courant_rates<float>(const ParamsT<float>&, unsigned char*, cudaStream_t);
 template cudaError_t launch_step_fused<double>(const ParamsT<double>&, const OutPtrsT<double>&, cudaStream_t, cudaEvent_t*);
 template cudaError_t launch_step_fused<float>(const ParamsT<float>&, const OutPtrsT<float>&, cudaStream_t, cudaEvent_t*);
 

@@ -27,6 +27,11 @@ constexpr int kMaxThreads = 512;      // largest block shape any kernel is launc
 // (g & 0xffff) x (g >> 16)
 struct BatchTile { int run, bx, by, g; };
 
+// Grid-wide barrier of the persistent batched kernel: arrival counter, generation, error
+// word (a wait ran out) and where it ran out (8 x step + barrier index + 1).
+struct GridSync { unsigned arrive, gen; int err, where; };
+constexpr int kPersistMaxThreads = 256;     // largest block of the persistent batched kernel
+
 // vector types of an element type
 template <typename T> struct VT;
 template <> struct VT<double> {
@@ -349,6 +354,8 @@ __device__ __forceinline__ bool is_nan(double x)
 __device__ __forceinline__ bool is_nan(float x) { return (__float_as_int(x) & 0x7fffffff) > 0x7f800000; }
 // x != 0 (either sign of zero counts as zero) on the bit pattern
 __device__ __forceinline__ bool nonzero(double x) { return (__double_as_longlong(x) << 1) != 0; }
+__device__ __forceinline__ bool is_pzero(double x) { return __double_as_longlong(x) == 0; }
+__device__ __forceinline__ bool is_pzero(float x) { return __float_as_int(x) == 0; }
 __device__ __forceinline__ bool nonzero(float x) { return (__float_as_int(x) << 1) != 0; }
 // Any active lane of the warp: a warp-uniform branch condition.  Guarding FP64 work with it
 // keeps the compiler from turning a rarely taken branch into predicated instructions that
@@ -375,6 +382,12 @@ template <typename T>
 cudaError_t launch_batch_step(const ParamsT<T>* runs_dev, int nruns, int nmat, bool strength, bool uniform, const BatchTile* const* work,
                               const int* ntiles, const dim3* blk, cudaStream_t s, cudaEvent_t* ev);
 template <typename T> cudaError_t launch_batch_poll(const ParamsT<T>* runs_dev, int n, double* out, cudaStream_t s);
+template <typename T>
+cudaError_t prepare_batch_persistent(int nmat, bool strength, bool uniform, dim3 blk, int* ctas);
+template <typename T>
+cudaError_t launch_batch_persistent(const ParamsT<T>* runs, int nruns, int nmat, bool strength, bool uniform,
+                                    const BatchTile* cells, int ncells, const BatchTile* verts, int nverts, dim3 blk,
+                                    int ctas, int steps, GridSync* gs, bool expire, cudaStream_t s);
 template <typename T> cudaError_t launch_courant(const ParamsT<T>& P, cudaStream_t s);
 // fused form (salec_fused.cu): after the Courant kernel, the rest-tile kernel and the
 // persistent tile kernel.  kFusedTileW x kFusedTileMinH bounds the tile count of every
@@ -383,7 +396,7 @@ constexpr int kFusedTileW = 32, kFusedTileMinH = 16;
 template <typename T> cudaError_t prepare_fused(const ParamsT<T>& P, int* ctas);
 template <typename T> size_t fused_smem_bytes(const ParamsT<T>& P);
 template <typename T> int fused_tiles(const ParamsT<T>& P);
-template <typename T> cudaError_t launch_courant_rates(const ParamsT<T>& P, cudaStream_t s);
+template <typename T> cudaError_t launch_courant_rates(const ParamsT<T>& P, unsigned char* rest, cudaStream_t s);
 template <typename T>
 cudaError_t launch_step_fused(const ParamsT<T>& P, const OutPtrsT<T>& O, cudaStream_t s, cudaEvent_t* ev);
 bool kernel_on_vertices(int k);

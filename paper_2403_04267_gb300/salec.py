@@ -13,13 +13,13 @@ import numpy as np
 
 from . import build as _build
 
-SALEC_OK, SALEC_EINVAL, SALEC_ENOMEM, SALEC_ECUDA, SALEC_EORDER, SALEC_EUNSTABLE = range(6)
+SALEC_OK, SALEC_EINVAL, SALEC_ENOMEM, SALEC_ECUDA, SALEC_EORDER, SALEC_EUNSTABLE, SALEC_ETIMEOUT = range(7)
 SALEC_FP64 = 0
 SALEC_FP32MIX = 1
 SALEC_STEP_PHASES, SALEC_STEP_FUSED = 0, 1
 PRECISIONS = {"fp64": SALEC_FP64, "fp32mix": SALEC_FP32MIX}
 _STATUS = {0: "SALEC_OK", 1: "SALEC_EINVAL", 2: "SALEC_ENOMEM", 3: "SALEC_ECUDA", 4: "SALEC_EORDER",
-           5: "SALEC_EUNSTABLE"}
+           5: "SALEC_EUNSTABLE", 6: "SALEC_ETIMEOUT"}
 
 FIELDS = {
     "f0": 0, "f1": 1, "f2": 2, "rho0": 3, "rho1": 4, "rho2": 5, "I": 6, "srr": 7, "szz": 8,
@@ -61,11 +61,12 @@ EXPORTS = ["salec_state_bytes", "salec_create", "salec_set_material", "salec_set
            "salec_conservation", "salec_checkpoint_bytes", "salec_get_state", "salec_set_state", "salec_state_changed",
            "salec_launches_per_step", "salec_set_kernel_timing", "salec_kernel_times",
            "salec_kernel_name", "salec_step_kernel_name", "salec_set_step_form", "salec_get_step_form",
-           "salec_fused_queue",
+           "salec_fused_queue", "salec_set_rest_copy",
            "salec_courant_dt_noalloc", "salec_last_error", "salec_destroy",
            "salec_set_end_time", "salec_set_block_shapes", "salec_get_block_shapes", "salec_autotune",
            "salec_batch_bytes", "salec_batch_create", "salec_batch_step", "salec_batch_run", "salec_batch_poll",
-           "salec_batch_autotune", "salec_batch_last_error", "salec_batch_destroy",
+           "salec_batch_autotune", "salec_batch_set_persistent", "salec_batch_expire_next_barrier",
+           "salec_batch_last_error", "salec_batch_destroy",
            "salec_mlp_n_params", "salec_mlp_bytes", "salec_mlp_create", "salec_mlp_set_params",
            "salec_mlp_get_params", "salec_mlp_forward", "salec_mlp_gradient", "salec_mlp_train_step",
            "salec_mlp_train",
@@ -109,6 +110,7 @@ def load(build: bool = True):
         "salec_step_kernel_name": (C.c_char_p, [P, I]),
         "salec_fused_queue": (I, [P, C.POINTER(C.c_int), C.POINTER(C.c_int)]),
         "salec_set_step_form": (I, [P, I]),
+        "salec_set_rest_copy": (I, [P, I]),
         "salec_get_step_form": (I, [P]),
         "salec_courant_dt_noalloc": (I, [C.POINTER(salec_grid), C.POINTER(salec_material), C.POINTER(C.c_void_p),
                                          P, P, P, D, PD, P]),
@@ -123,6 +125,8 @@ def load(build: bool = True):
         "salec_batch_run": (I, [P, I, C.c_long, C.POINTER(C.c_long), C.POINTER(C.c_int)]),
         "salec_batch_poll": (I, [P, PD]),
         "salec_batch_autotune": (I, [P, I, C.POINTER(C.c_int)]),
+        "salec_batch_set_persistent": (I, [P, I]),
+        "salec_batch_expire_next_barrier": (I, [P]),
         "salec_batch_last_error": (C.c_char_p, [P]),
         "salec_batch_destroy": (None, [P]),
         "salec_destroy": (None, [P]),
@@ -347,6 +351,11 @@ class Sim:
         self._check(load().salec_fused_queue(self._h, C.byref(q), C.byref(t)))
         return q.value, t.value
 
+    def set_rest_copy(self, on: bool) -> None:
+        """Fused form: copy tiles at rest (default) or run every tile through the tile
+        kernel; the results are the same bit for bit."""
+        self._check(load().salec_set_rest_copy(self._h, 1 if on else 0))
+
     @property
     def step_form(self) -> str:
         """"fused" (one tile kernel per step after the Courant kernel) or "phases" (six
@@ -415,9 +424,28 @@ class Batch:
 
     def step(self, n: int) -> None:
         """n batched steps; returns after they finished (the runs' fields are then safe to
-        read on any stream)."""
+        read on any stream).  In persistent mode a grid-barrier wait that ran out raises
+        SalecError (SALEC_ETIMEOUT)."""
         self._check(load().salec_batch_step(self._h, int(n)))
         self.stream.synchronize()
+        if self.persistent:
+            self.poll()
+
+    @property
+    def persistent(self) -> bool:
+        """Persistent mode: one cooperative launch per step call or run chunk (grid-wide
+        barriers between the phases) instead of six launches and a Courant kernel per step."""
+        return getattr(self, "_persistent", False)
+
+    @persistent.setter
+    def persistent(self, on: bool) -> None:
+        self._check(load().salec_batch_set_persistent(self._h, 1 if on else 0))
+        self._persistent = bool(on)
+
+    def expire_next_barrier(self) -> None:
+        """Failure-detection test: the next persistent step call's first grid barrier never
+        completes, its waits run out (2 s) and step() raises SalecError (SALEC_ETIMEOUT)."""
+        self._check(load().salec_batch_expire_next_barrier(self._h))
 
     def run(self, chunk: int = 50, max_steps: int = 10 ** 9):
         steps, done = C.c_long(), C.c_int()

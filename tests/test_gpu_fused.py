@@ -187,20 +187,29 @@ def test_fused_matches_phase_kernels(precision, tol1, tol30):
 @pytest.mark.parametrize("n", [200, 203])
 def test_rest_tiles_copy_what_the_quiescent_path_writes(precision, n):
     """A tile found quiescent in the step before, with its eight neighbours, is copied by
-    the rest-tile kernel instead of going through the tile kernel.  Against the same steps
-    taken with the rest flags cleared before each one (every tile then goes through the
-    tile kernel's own quiescence test and path; a field written back from the host clears
-    them): bitwise the same fields, time, dt and tallies, on a grid the tiles divide and on
-    a ragged one."""
+    the rest-tile kernel instead of going through the tile kernel; so is one that the
+    Courant-rate pass before the first step (and again after a host write) found quiescent
+    with its fields in the quiescent path's form.  Against the same steps taken with the
+    copy switched off (every tile then goes through the tile kernel's own quiescence test
+    and path): bitwise the same fields, time, dt and tallies, on a grid the tiles divide and
+    on a ragged one."""
     spec = W.scaled_plain(n, radius_cells=5)
     a = _fused(spec, precision)
-    a.step(70)
-    queued, tiles = a.fused_queue()
+    a.step(1)
+    q1, tiles = a.fused_queue()
+    print(f"{precision} {n}x{n}: {q1} of {tiles} tiles through the whole cycle in the first step")
+    assert 0 < q1 < tiles
+    a.step(33)
+    a.set("vz", a.get("vz"))       # a host write: the rate pass flags the tiles again
+    a.step(1)
+    assert 0 < a.fused_queue()[0] < tiles
+    a.step(35)
+    queued = a.fused_queue()[0]
     print(f"{precision} {n}x{n}: {queued} of {tiles} tiles through the whole cycle after 70 steps")
     assert 0 < queued < tiles
     b = _fused(spec, precision)
+    b.set_rest_copy(False)
     for _ in range(70):
-        b.set("vz", b.get("vz"))
         b.step(1)
         assert b.fused_queue() == (tiles, tiles)
     _assert_equal(a, b, spec)
