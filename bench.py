@@ -717,10 +717,10 @@ def main():
     ap.add_argument("--no-active", action="store_true")
     ap.add_argument("--no-accuracy", action="store_true")
     ap.add_argument("--sur-members", type=int, default=8)
-    ap.add_argument("--sur-steps", type=int, default=6000)
+    ap.add_argument("--sur-steps", type=int, default=12000)
     ap.add_argument("--sur-solver-runs", type=int, default=8)
     ap.add_argument("--sur-infer-batch", type=int, default=65536)
-    ap.add_argument("--sur-gate-target", type=float, default=0.95)
+    ap.add_argument("--sur-gate-target", type=float, default=0.97)
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     if args.impl == "reference":

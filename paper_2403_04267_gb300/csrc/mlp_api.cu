@@ -25,6 +25,14 @@ constexpr int kInLd = 8;
 
 // BF16 row stride of W_l
 int w_ld(int l) { return l == 0 ? kInLd : kDims[l]; }
+// BF16 row stride of W_l^T (n_in rows of n_out values, padded to 16-byte rows); layer 0
+// needs none (no activation gradient below the first layer)
+int wt_ld(int l) { return (kDims[l + 1] + 7) / 8 * 8; }
+// rows of the transposed activation buffers: the layer's units, one row of ones (the bias
+// gradients are the weight gradients of that row), padded
+constexpr int kHidT = kHid + 16;
+constexpr int kInT = 16;
+long ld_t(int bmax) { return ((long)bmax + 7) / 8 * 8; }
 
 size_t align_up(size_t x) { return (x + 255) & ~size_t(255); }
 
@@ -42,23 +50,39 @@ long n_weights_bf16()
     return n;
 }
 
+long n_weights_bf16_t()
+{
+    long n = 0;
+    for (int l = 1; l < kLayers; ++l) n += (long)kDims[l] * wt_ld(l);
+    return n;
+}
+
+// The backward pass reads its operands K-major (K = the batch for the weight gradients, K =
+// a layer's outputs for the activation gradients), so the TMA-fed GEMM serves it too: the
+// forward epilogues also write the activations transposed (HT, XT), the backward epilogues
+// the gradients transposed (GT), and the BF16 weights are kept transposed as well (wbfT).
 struct Layout {
-    size_t theta, m1, m2, grad, wmap, wbf, X, Z[4], H[4], Y, G[2], part, cpart, loss, err, ts, total;
+    size_t theta, m1, m2, grad, wmap, wbf, wmapT, wbfT, X, XT, Z[4], H[4], HT[4], Y, G[2], GT[2], part, loss, err,
+        ts, total;
     Layout(int bmax)
     {
-        const long P = n_params(), W = n_weights_bf16();
+        const long P = n_params(), W = n_weights_bf16(), WT = n_weights_bf16_t(), ldT = ld_t(bmax);
         size_t o = 0;
         auto take = [&](size_t bytes) { size_t r = o; o = align_up(o + bytes); return r; };
         theta = take(P * 4); m1 = take(P * 4); m2 = take(P * 4); grad = take(P * 4);
         wmap = take(P * 4);
         wbf = take(W * 2);
+        wmapT = take(P * 4);
+        wbfT = take(WT * 2);
         X = take((size_t)bmax * kInLd * 2);
+        XT = take((size_t)kInT * ldT * 2);
         for (int l = 0; l < 4; ++l) Z[l] = take((size_t)bmax * kHid * 4);
         for (int l = 0; l < 4; ++l) H[l] = take((size_t)bmax * kHid * 2);
+        for (int l = 0; l < 4; ++l) HT[l] = take((size_t)kHidT * ldT * 2);
         Y = take((size_t)bmax * SALEC_MLP_OUT * 4);
         for (int l = 0; l < 2; ++l) G[l] = take((size_t)bmax * kHid * 2);
-        part = take((size_t)kMaxSplit * kHid * kHid * 4);     // split-K partials of a weight gradient
-        cpart = take((size_t)kColsumChunks * kHid * 4);      // column-sum partials of a bias gradient
+        for (int l = 0; l < 2; ++l) GT[l] = take((size_t)kHid * ldT * 2);
+        part = take((size_t)kMaxSplit * kHid * (kHid + 1) * 4);   // split-K partials of a weight gradient
         loss = take(8);
         err = take(4);
         ts = take(sizeof(TrainState));
@@ -75,13 +99,18 @@ struct salec_mlp {
     float *theta = nullptr, *m1 = nullptr, *m2 = nullptr, *grad = nullptr;
     int* wmap = nullptr;
     __nv_bfloat16* wbf = nullptr;
+    int* wmapT = nullptr;
+    __nv_bfloat16* wbfT = nullptr;
     __nv_bfloat16* X = nullptr;
+    __nv_bfloat16* XT = nullptr;
     float* Z[4] = {};
     __nv_bfloat16* H[4] = {};
+    __nv_bfloat16* HT[4] = {};
     float* Y = nullptr;
     __nv_bfloat16* G[2] = {};
+    __nv_bfloat16* GT[2] = {};
+    long ldT = 0;                         // row stride of the transposed buffers (batch_max, padded)
     float* part = nullptr;
-    float* cpart = nullptr;
     double* loss = nullptr;
     int* errflag = nullptr;
     TrainState* ts = nullptr;
@@ -99,6 +128,7 @@ struct salec_mlp {
     }
     long woff[kLayers], boff[kLayers];    // offsets of W_l and b_l in theta
     long wbf_off[kLayers];                // offset of W_l in the BF16 weight block
+    long wbfT_off[kLayers];               // offset of W_l^T in the transposed block (l >= 1)
 };
 
 namespace {
@@ -146,11 +176,13 @@ salec_status forward_impl(salec_mlp* n, int B, float* y, long ldy, const float* 
             g.epi = kEpiBiasGelu;
             g.C = keep_z ? n->Z[l] : nullptr; g.ldc = kHid;
             g.Hout = n->H[l]; g.ldh = kHid;
+            if (keep_z) { g.HoutT = n->HT[l]; g.ldhT = n->ldT; }
         } else if (with_loss) {
             g.epi = kEpiOutLoss;
             g.C = y; g.ldc = ldy;
             g.Tin = t; g.ldt = SALEC_MLP_OUT;
             g.Hout = n->G[0]; g.ldh = kHid;
+            g.HoutT = n->GT[0]; g.ldhT = n->ldT;
             g.grad_scale = 2.0f / ((float)B * (float)SALEC_MLP_OUT);
             g.loss = n->loss;
         } else {
@@ -164,32 +196,33 @@ salec_status forward_impl(salec_mlp* n, int B, float* y, long ldy, const float* 
     return SALEC_OK;
 }
 
-// backward pass from G[0] = dL/dY (BF16): weight and bias gradients into grad
+// backward pass from G[0] = dL/dY (BF16, and GT[0] its transpose): weight and bias
+// gradients into grad.  Every operand is read K-major, so every GEMM is TMA-fed.
 salec_status backward_impl(salec_mlp* n, int B, float* grad)
 {
     int cur = 0;
     for (int l = kLayers - 1; l >= 0; --l) {
         const int ni = kDims[l], no = kDims[l + 1];
-        const __nv_bfloat16* G = n->G[cur];
-        const __nv_bfloat16* Hprev = l > 0 ? n->H[l - 1] : n->X;
-        const long ldprev = l > 0 ? kHid : kInLd;
-        // dW_l[o][i] = sum_b G[b][o] Hprev[b][i]
-        GemmArgs gw = gemm0(no, ni, B, n->errflag);
-        gw.A = G; gw.a_sm = 1; gw.a_sk = kHid;
-        gw.B = Hprev; gw.b_sn = 1; gw.b_sk = ldprev;
+        // dW_l[o][i] = sum_b G[b][o] Hprev[b][i] and db_l[o] = sum_b G[b][o], as one product
+        // of G^T (no x B) with [Hprev | 1]^T ((ni + 1) x B): the row of ones after the
+        // transposed activations gives the bias gradient in the last column
+        GemmArgs gw = gemm0(no, ni + 1, B, n->errflag);
+        gw.A = n->GT[cur]; gw.a_sm = n->ldT; gw.a_sk = 1;
+        gw.B = l > 0 ? n->HT[l - 1] : n->XT; gw.b_sn = n->ldT; gw.b_sk = 1;
         gw.epi = kEpiStore;
         gw.C = grad + n->woff[l]; gw.ldc = ni;
+        gw.Cb = grad + n->boff[l];
         gw.part = n->part;
         MLP_CUDA(n, launch_gemm(gw, n->stream), "mlp weight-gradient gemm");
-        MLP_CUDA(n, launch_colsum(G, B, no, kHid, grad + n->boff[l], n->cpart, n->stream), "mlp bias gradient");
         if (l == 0) break;
-        // dL/dZ_{l-1}[b][i] = (sum_o G[b][o] W_l[o][i]) gelu'(Z_{l-1}[b][i])
+        // dL/dZ_{l-1}[b][i] = (sum_o G[b][o] W_l[o][i]) gelu'(Z_{l-1}[b][i]), W_l^T K-major
         GemmArgs gd = gemm0(B, ni, no, n->errflag);
-        gd.A = G; gd.a_sm = kHid; gd.a_sk = 1;
-        gd.B = n->wbf + n->wbf_off[l]; gd.b_sn = 1; gd.b_sk = w_ld(l);
+        gd.A = n->G[cur]; gd.a_sm = kHid; gd.a_sk = 1;
+        gd.B = n->wbfT + n->wbfT_off[l]; gd.b_sn = wt_ld(l); gd.b_sk = 1;
         gd.epi = kEpiGeluBwd;
         gd.Zin = n->Z[l - 1]; gd.ldz = kHid;
         gd.Hout = n->G[cur ^ 1]; gd.ldh = kHid;
+        gd.HoutT = n->GT[cur ^ 1]; gd.ldhT = n->ldT;
         MLP_CUDA(n, launch_gemm(gd, n->stream), "mlp activation-gradient gemm");
         cur ^= 1;
     }
@@ -218,7 +251,7 @@ salec_status train_one(salec_mlp* n, int B, const float* t_dev, const float* lr_
     AdamArgs a;
     a.lr = 0.0f; a.c1 = 0.0f; a.c2 = 0.0f;
     a.beta1 = beta1; a.beta2 = beta2; a.eps = eps; a.ts = n->ts;
-    MLP_CUDA(n, launch_adam(n->theta, n->m1, n->m2, n->grad, n_params(), a, n->wmap, n->wbf, n->stream), "mlp adam");
+    MLP_CUDA(n, launch_adam(n->theta, n->m1, n->m2, n->grad, n_params(), a, n->wmap, n->wbf, n->stream, n->wmapT, n->wbfT), "mlp adam");
     return SALEC_OK;
 }
 
@@ -289,35 +322,56 @@ salec_status salec_mlp_create(int batch_max, void* dev_buf, size_t bytes, void* 
     n->grad = reinterpret_cast<float*>(b + L.grad);
     n->wmap = reinterpret_cast<int*>(b + L.wmap);
     n->wbf = reinterpret_cast<__nv_bfloat16*>(b + L.wbf);
+    n->wmapT = reinterpret_cast<int*>(b + L.wmapT);
+    n->wbfT = reinterpret_cast<__nv_bfloat16*>(b + L.wbfT);
     n->X = reinterpret_cast<__nv_bfloat16*>(b + L.X);
+    n->XT = reinterpret_cast<__nv_bfloat16*>(b + L.XT);
+    n->ldT = ld_t(batch_max);
     for (int l = 0; l < 4; ++l) {
         n->Z[l] = reinterpret_cast<float*>(b + L.Z[l]);
         n->H[l] = reinterpret_cast<__nv_bfloat16*>(b + L.H[l]);
+        n->HT[l] = reinterpret_cast<__nv_bfloat16*>(b + L.HT[l]);
     }
     n->Y = reinterpret_cast<float*>(b + L.Y);
-    for (int l = 0; l < 2; ++l) n->G[l] = reinterpret_cast<__nv_bfloat16*>(b + L.G[l]);
+    for (int l = 0; l < 2; ++l) {
+        n->G[l] = reinterpret_cast<__nv_bfloat16*>(b + L.G[l]);
+        n->GT[l] = reinterpret_cast<__nv_bfloat16*>(b + L.GT[l]);
+    }
     n->part = reinterpret_cast<float*>(b + L.part);
-    n->cpart = reinterpret_cast<float*>(b + L.cpart);
     n->loss = reinterpret_cast<double*>(b + L.loss);
     n->errflag = reinterpret_cast<int*>(b + L.err);
     n->ts = reinterpret_cast<TrainState*>(b + L.ts);
     // parameter offsets and the weight -> BF16 block map
     const long P = n_params();
-    std::vector<int> wmap(P, -1);
-    long o = 0, w = 0;
+    std::vector<int> wmap(P, -1), wmapT(P, -1);
+    long o = 0, w = 0, wt = 0;
     for (int l = 0; l < kLayers; ++l) {
         const int ni = kDims[l], no = kDims[l + 1], ld = w_ld(l);
         n->woff[l] = o;
         n->wbf_off[l] = w;
+        n->wbfT_off[l] = l > 0 ? wt : -1;
         for (int r = 0; r < no; ++r)
-            for (int c = 0; c < ni; ++c) wmap[o + (long)r * ni + c] = (int)(w + (long)r * ld + c);
+            for (int c = 0; c < ni; ++c) {
+                wmap[o + (long)r * ni + c] = (int)(w + (long)r * ld + c);
+                if (l > 0) wmapT[o + (long)r * ni + c] = (int)(wt + (long)c * wt_ld(l) + r);
+            }
         o += (long)no * ni;
         w += (long)no * ld;
+        if (l > 0) wt += (long)ni * wt_ld(l);
         n->boff[l] = o;
         o += no;
     }
+    // the rows of ones under the transposed activations (BF16 1.0 = 0x3f80): columns past
+    // the batch lie outside the tensor map and read as zero
+    std::vector<uint16_t> ones((size_t)n->ldT, 0x3f80u);
     cudaError_t e = cudaMemsetAsync(dev_buf, 0, L.total, n->stream);
     if (e == cudaSuccess) e = cudaMemcpyAsync(n->wmap, wmap.data(), P * sizeof(int), cudaMemcpyHostToDevice, n->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(n->wmapT, wmapT.data(), P * sizeof(int), cudaMemcpyHostToDevice, n->stream);
+    for (int l = 0; l < 4 && e == cudaSuccess; ++l)
+        e = cudaMemcpyAsync(n->HT[l] + (long)kHid * n->ldT, ones.data(), ones.size() * 2, cudaMemcpyHostToDevice, n->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(n->XT + (long)SALEC_MLP_IN * n->ldT, ones.data(), ones.size() * 2, cudaMemcpyHostToDevice,
+                            n->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(n->stream);
     if (e != cudaSuccess) {
         delete n;
@@ -334,7 +388,7 @@ salec_status salec_mlp_set_params(salec_mlp* n, const float* theta_host)
     MLP_CUDA(n, cudaMemcpyAsync(n->theta, theta_host, P * 4, cudaMemcpyHostToDevice, n->stream), "set_params copy");
     MLP_CUDA(n, cudaMemsetAsync(n->m1, 0, P * 4, n->stream), "set_params reset");
     MLP_CUDA(n, cudaMemsetAsync(n->m2, 0, P * 4, n->stream), "set_params reset");
-    MLP_CUDA(n, launch_refresh_bf16(n->theta, P, n->wmap, n->wbf, n->stream), "set_params bf16 copy");
+    MLP_CUDA(n, launch_refresh_bf16(n->theta, P, n->wmap, n->wbf, n->stream, n->wmapT, n->wbfT), "set_params bf16 copy");
     MLP_CUDA(n, cudaStreamSynchronize(n->stream), "set_params sync");
     n->steps = 0;
     return SALEC_OK;
@@ -373,7 +427,7 @@ salec_status salec_mlp_gradient(salec_mlp* n, const float* x_dev, const float* t
     if (!x_dev || !t_dev) return fail(n, SALEC_EINVAL, "null pointer");
     float* grad = grad_dev ? grad_dev : n->grad;
     MLP_CUDA(n, cudaMemsetAsync(n->loss, 0, 8, n->stream), "mlp loss reset");
-    MLP_CUDA(n, launch_inputs_bf16(x_dev, batch, SALEC_MLP_IN, kInLd, n->X, n->stream), "mlp input");
+    MLP_CUDA(n, launch_inputs_bf16(x_dev, batch, SALEC_MLP_IN, kInLd, n->X, n->stream, n->XT, n->ldT), "mlp input");
     st = forward_impl(n, batch, n->Y, SALEC_MLP_OUT, t_dev, true);
     if (st != SALEC_OK) return st;
     st = backward_impl(n, batch, grad);
@@ -397,7 +451,7 @@ salec_status salec_mlp_train_step(salec_mlp* n, const float* x_dev, const float*
     if (!(lr >= 0.0f) || !(beta1 >= 0.0f && beta1 < 1.0f) || !(beta2 >= 0.0f && beta2 < 1.0f) || !(eps > 0.0f))
         return fail(n, SALEC_EINVAL, "bad Adam hyper-parameters");
     MLP_CUDA(n, cudaMemsetAsync(n->loss, 0, 8, n->stream), "mlp loss reset");
-    MLP_CUDA(n, launch_inputs_bf16(x_dev, batch, SALEC_MLP_IN, kInLd, n->X, n->stream), "mlp input");
+    MLP_CUDA(n, launch_inputs_bf16(x_dev, batch, SALEC_MLP_IN, kInLd, n->X, n->stream, n->XT, n->ldT), "mlp input");
     st = forward_impl(n, batch, n->Y, SALEC_MLP_OUT, t_dev, true);
     if (st != SALEC_OK) return st;
     st = backward_impl(n, batch, n->grad);
@@ -407,7 +461,7 @@ salec_status salec_mlp_train_step(salec_mlp* n, const float* x_dev, const float*
     a.lr = lr; a.beta1 = beta1; a.beta2 = beta2; a.eps = eps; a.ts = nullptr;
     a.c1 = (float)(1.0 / (1.0 - std::pow((double)beta1, (double)n->steps)));
     a.c2 = (float)(1.0 / (1.0 - std::pow((double)beta2, (double)n->steps)));
-    MLP_CUDA(n, launch_adam(n->theta, n->m1, n->m2, n->grad, n_params(), a, n->wmap, n->wbf, n->stream), "mlp adam");
+    MLP_CUDA(n, launch_adam(n->theta, n->m1, n->m2, n->grad, n_params(), a, n->wmap, n->wbf, n->stream, n->wmapT, n->wbfT), "mlp adam");
     if (sse_dev) MLP_CUDA(n, cudaMemcpyAsync(sse_dev, n->loss, 8, cudaMemcpyDeviceToDevice, n->stream), "mlp loss copy");
     return SALEC_OK;
 }
@@ -423,7 +477,7 @@ salec_status salec_mlp_train(salec_mlp* n, const float* x_dev, const float* t_de
     if (!(beta1 >= 0.0f && beta1 < 1.0f) || !(beta2 >= 0.0f && beta2 < 1.0f) || !(eps > 0.0f))
         return fail(n, SALEC_EINVAL, "bad Adam hyper-parameters");
     if (n->steps + (long)steps > 0x7fffffffL) return fail(n, SALEC_EINVAL, "step count overflow");
-    MLP_CUDA(n, launch_inputs_bf16(x_dev, batch, SALEC_MLP_IN, kInLd, n->X, n->stream), "mlp input");
+    MLP_CUDA(n, launch_inputs_bf16(x_dev, batch, SALEC_MLP_IN, kInLd, n->X, n->stream, n->XT, n->ldT), "mlp input");
     MLP_CUDA(n, launch_train_reset(n->ts, (int)n->steps, n->stream), "mlp train reset");
     // the first step with plain launches (it also sets the kernels' attributes), then whole
     // chunks as graph replays, then the rest

@@ -28,6 +28,8 @@ struct GemmArgs {
     const float* bias;        // [N] or null
     __nv_bfloat16* Hout;      // BF16 output, row stride ldh
     long ldh;
+    __nv_bfloat16* HoutT;     // the same BF16 output transposed (HoutT[n * ldhT + m]), or null
+    long ldhT;
     const float* Zin;         // saved pre-activations, row stride ldz
     long ldz;
     const float* Tin;         // targets, row stride ldt
@@ -37,8 +39,11 @@ struct GemmArgs {
     int* err;                 // error flag, or null
     float* part;              // kEpiStore without bias: workspace for split-K partials
                               // (kMaxSplit x M x N floats), or null for no split
+    float* Cb;                // with part: column N - 1 of C goes to Cb[m] instead (a bias
+                              // gradient summed against a row of ones), C keeps columns < N - 1
     int nt, tmem_cols;        // set by the launcher
     int kchunk;               // set by the launcher: K per split (0: no split)
+    int stages;               // set by the launcher: shared-memory stages of the TMA-fed kernel
 };
 
 constexpr int kMaxSplit = 16;
@@ -70,19 +75,21 @@ struct AdamArgs {
 
 cudaError_t launch_gemm(const GemmArgs& g, cudaStream_t s);
 cudaError_t launch_mlp_forward_fused(const FusedLaunch& f, cudaStream_t s);
-// column sums out[n] = sum_m G[m][n]; `part` holds kColsumChunks x N floats
-constexpr int kColsumChunks = 64;
-cudaError_t launch_colsum(const __nv_bfloat16* G, int M, int N, long ldg, float* out, float* part, cudaStream_t s);
-cudaError_t launch_inputs_bf16(const float* x, int rows, int cols, int ld, __nv_bfloat16* y, cudaStream_t s);
+cudaError_t launch_inputs_bf16(const float* x, int rows, int cols, int ld, __nv_bfloat16* y, cudaStream_t s,
+                               __nv_bfloat16* yT = nullptr, long ldT = 0);
+// wmapT / wbfT (optional): a second BF16 copy of every weight at wmapT[i] (the transposed
+// weights of the backward pass)
 cudaError_t launch_adam(float* theta, float* m1, float* m2, const float* grad, long n, const AdamArgs& a,
-                        const int* wmap, __nv_bfloat16* wbf, cudaStream_t s);
+                        const int* wmap, __nv_bfloat16* wbf, cudaStream_t s, const int* wmapT = nullptr,
+                        __nv_bfloat16* wbfT = nullptr);
 // one thread: ts->k = 0, ts->t0 = t0
 cudaError_t launch_train_reset(TrainState* ts, int t0, cudaStream_t s);
 // one thread, first kernel of a step: k += 1, lr = lr_dev[k - 1], the bias corrections of
 // Adam step t0 + k, loss = 0
 cudaError_t launch_train_begin(TrainState* ts, const float* lr_dev, float beta1, float beta2, double* loss,
                                cudaStream_t s);
-cudaError_t launch_refresh_bf16(const float* theta, long n, const int* wmap, __nv_bfloat16* wbf, cudaStream_t s);
+cudaError_t launch_refresh_bf16(const float* theta, long n, const int* wmap, __nv_bfloat16* wbf, cudaStream_t s,
+                                const int* wmapT = nullptr, __nv_bfloat16* wbfT = nullptr);
 size_t gemm_smem_bytes(int nt);
 
 }  // namespace mlp

@@ -232,7 +232,7 @@ __device__ __forceinline__ void epilogue(const GemmArgs& g, uint32_t tmem, int m
     const int m = m0 + warp * 32 + lane;
     const uint32_t trow = tmem + ((uint32_t)(warp * 32) << 16);
     double lsum = 0.0;
-    const bool vec_c = ((g.ldc * 4) & 15) == 0 && ((reinterpret_cast<uintptr_t>(g.C) & 15) == 0);
+    const bool vec_c = !g.Cb && ((g.ldc * 4) & 15) == 0 && ((reinterpret_cast<uintptr_t>(g.C) & 15) == 0);
     const bool vec_h = ((g.ldh * 2) & 15) == 0 && ((reinterpret_cast<uintptr_t>(g.Hout) & 15) == 0);
     const bool has_c = g.epi != kEpiGeluBwd && g.C != nullptr;
     const bool has_h = g.epi != kEpiStore;
@@ -276,7 +276,12 @@ __device__ __forceinline__ void epilogue(const GemmArgs& g, uint32_t tmem, int m
 #pragma unroll
             for (int q = 0; q < 4; ++q) dst[q] = make_float4(x[4 * q], x[4 * q + 1], x[4 * q + 2], x[4 * q + 3]);
         } else if (has_c) {
-            for (int j = 0; j < 16 && nb + j < g.N; ++j) g.C[(long)m * g.ldc + nb + j] = x[j];
+            for (int j = 0; j < 16 && nb + j < g.N; ++j) {
+                if (g.Cb && nb + j == g.N - 1)
+                    g.Cb[m] = x[j];          // the column of the row of ones: a bias gradient
+                else
+                    g.C[(long)m * g.ldc + nb + j] = x[j];
+            }
         }
         if (full && has_h && vec_h) {
             union { uint4 u[2]; __nv_bfloat16 b[16]; } pk;
@@ -287,6 +292,12 @@ __device__ __forceinline__ void epilogue(const GemmArgs& g, uint32_t tmem, int m
             dst[1] = pk.u[1];
         } else if (has_h) {
             for (int j = 0; j < 16 && nb + j < g.N; ++j) g.Hout[(long)m * g.ldh + nb + j] = __float2bfloat16_rn(h[j]);
+        }
+        // the transposed copy: for each column, the warp's 32 rows are 64 contiguous bytes
+        if (has_h && g.HoutT) {
+#pragma unroll
+            for (int j = 0; j < 16; ++j)
+                if (full || nb + j < g.N) g.HoutT[(long)(nb + j) * g.ldhT + m] = __float2bfloat16_rn(h[j]);
         }
     }
     if (g.epi == kEpiOutLoss && g.loss) {
@@ -388,6 +399,7 @@ __global__ void __launch_bounds__(kGemmThreads) k_gemm_bf16(GemmArgs g)
             GemmArgs gp = g;
             gp.C = g.part + (long)blockIdx.z * g.M * g.N;
             gp.ldc = g.N;
+            gp.Cb = nullptr;
             epilogue(gp, tmem, m0, n0, NT, nk > 0);
         } else {
             epilogue(g, tmem, m0, n0, NT, nk > 0);
@@ -441,7 +453,12 @@ __global__ void __launch_bounds__(kGemmThreads) k_gemm_bf16_tma(const __grid_con
     const uint32_t a_bytes = kBM * kBK * 2, b_bytes = (uint32_t)NT * kBK * 2;
     const uint32_t stage_bytes = a_bytes + b_bytes;
     const uint32_t tmem_cols = g.tmem_cols;
-    const int nk = (g.K + kBK - 1) / kBK;
+    // split-K: this CTA sums K range [kb, ke) (whole 64-wide slices: kchunk is a multiple of
+    // kBK) into its own partial; a second kernel adds the partials in a fixed order
+    const int kb = g.kchunk > 0 ? (int)blockIdx.z * g.kchunk : 0;
+    const int ke = g.kchunk > 0 ? min(g.K, kb + g.kchunk) : g.K;
+    const int nk = (ke - kb + kBK - 1) / kBK;
+    const int ns = g.stages;              // ring stages in use (1..kStages), set by the launcher
 
     if (tid == 0) {
         for (int i = 0; i < kStages; ++i) { mbar_init(&full[i], 1); mbar_init(&empty[i], 1); }
@@ -466,10 +483,10 @@ __global__ void __launch_bounds__(kGemmThreads) k_gemm_bf16_tma(const __grid_con
         const uint32_t idesc = idesc_bf16(kBM, NT);
         const uint32_t base = smem_u32(smem);
         auto load_slice = [&](int kt) {
-            const int st = kt % kStages;
+            const int st = kt % ns;
             const uint32_t sa = base + st * stage_bytes, sb = sa + a_bytes;
             mbar_expect_tx(&full[st], stage_bytes);
-            const int k0 = kt * kBK;
+            const int k0 = kb + kt * kBK;
 #pragma unroll
             for (int kg = 0; kg < kBK / 8; ++kg) {
                 tma_load_2d(sa + kg * (kBM * 16), &mapA, k0 + 8 * kg, m0, &full[st]);
@@ -478,11 +495,11 @@ __global__ void __launch_bounds__(kGemmThreads) k_gemm_bf16_tma(const __grid_con
         };
         bool good = true;
         int committed = 0;              // slices whose MMAs were committed
-        const int pre = nk < kStages ? nk : kStages;
+        const int pre = nk < ns ? nk : ns;
         for (int kt = 0; kt < pre; ++kt) load_slice(kt);
         for (int kt = 0; kt < nk && good; ++kt) {
-            const int st = kt % kStages;
-            const uint32_t par = (uint32_t)(kt / kStages) & 1u;
+            const int st = kt % ns;
+            const uint32_t par = (uint32_t)(kt / ns) & 1u;
             if (!mbar_wait(&full[st], par)) { good = false; break; }
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
             const uint32_t a0 = base + st * stage_bytes, b0 = a0 + a_bytes;
@@ -494,25 +511,35 @@ __global__ void __launch_bounds__(kGemmThreads) k_gemm_bf16_tma(const __grid_con
             }
             mma_commit(&empty[st]);
             committed = kt + 1;
-            if (kt + kStages < nk) {
+            if (kt + ns < nk) {
                 // the stage is refilled once its MMAs have read it
                 if (!mbar_wait(&empty[st], par)) { good = false; break; }
-                load_slice(kt + kStages);
+                load_slice(kt + ns);
             }
         }
         // the last commit covers every MMA; wait for it (bounded)
         if (good && committed > 0)
-            good = mbar_wait(&empty[(committed - 1) % kStages], (uint32_t)((committed - 1) / kStages) & 1u);
+            good = mbar_wait(&empty[(committed - 1) % ns], (uint32_t)((committed - 1) / ns) & 1u);
         if (!good) {
             if (g.err) atomicOr(g.err, 2);
             // bounded chance for copies and MMAs still in flight to finish
-            for (int i = 0; i < kStages; ++i) (void)mbar_wait(&empty[i], 0);
+            for (int i = 0; i < ns; ++i) (void)mbar_wait(&empty[i], 0);
             ok_flag = 0;
         }
     }
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    if (ok_flag) epilogue(g, tmem, m0, n0, NT, nk > 0);
+    if (ok_flag) {
+        if (g.kchunk > 0) {
+            GemmArgs gp = g;
+            gp.C = g.part + (long)blockIdx.z * g.M * g.N;
+            gp.ldc = g.N;
+            gp.Cb = nullptr;
+            epilogue(gp, tmem, m0, n0, NT, nk > 0);
+        } else {
+            epilogue(g, tmem, m0, n0, NT, nk > 0);
+        }
+    }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
     if (warp == 0) {
@@ -815,48 +842,42 @@ __global__ void __launch_bounds__(kPPThreads, 1) k_mlp_forward_pp(const __grid_c
 // Column sums of a BF16 matrix (bias gradients): out[n] = sum_m G[m][n].
 // Column sums in two passes (many rows, few columns): block (x, y) sums rows y, y + Y, ...
 // of its columns into part[y][n]; the second pass adds the Y partials in order.
-__global__ void k_colsum_part(const __nv_bfloat16* __restrict__ G, int M, int N, long ldg, float* __restrict__ part)
-{
-    const int n = blockIdx.x * blockDim.x + threadIdx.x;
-    if (n >= N) return;
-    float s = 0.0f;
-    for (int m = blockIdx.y; m < M; m += gridDim.y) s += __bfloat162float(G[(long)m * ldg + n]);
-    part[(long)blockIdx.y * N + n] = s;
-}
-__global__ void k_sum_parts(const float* __restrict__ part, int nparts, long n, float* __restrict__ out)
-{
-    const long k = (long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (k >= n) return;
-    float s = 0.0f;
-    for (int p = 0; p < nparts; ++p) s += part[(long)p * n + k];
-    out[k] = s;
-}
-// split-K partials [S][M][N] into C (row stride ldc), in split order
-__global__ void k_splitk_reduce(const float* __restrict__ part, int S, int M, int N, float* __restrict__ C, long ldc)
+// split-K partials [S][M][N] into C (row stride ldc), in split order; with Cb, column N - 1
+// goes to Cb[m] and C holds the other columns
+__global__ void k_splitk_reduce(const float* __restrict__ part, int S, int M, int N, float* __restrict__ C, long ldc,
+                                float* __restrict__ Cb)
 {
     const long k = (long)blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= (long)M * N) return;
     float s = 0.0f;
     for (int p = 0; p < S; ++p) s += part[(long)p * M * N + k];
-    C[(k / N) * ldc + k % N] = s;
+    const long m = k / N;
+    const int n = (int)(k - m * N);
+    if (Cb && n == N - 1)
+        Cb[m] = s;
+    else
+        C[m * ldc + n] = s;
 }
 
 // FP32 -> BF16 inputs of the first layer: rows of `cols` values into rows of `ld`, the
 // padding zero.
-__global__ void k_inputs_bf16(const float* __restrict__ x, int rows, int cols, int ld, __nv_bfloat16* __restrict__ y)
+__global__ void k_inputs_bf16(const float* __restrict__ x, int rows, int cols, int ld, __nv_bfloat16* __restrict__ y,
+                              __nv_bfloat16* __restrict__ yT, long ldT)
 {
     const long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= (long)rows * ld) return;
     const long r = i / ld;
     const int c = (int)(i - r * ld);
-    y[i] = __float2bfloat16_rn(c < cols ? x[r * cols + c] : 0.0f);
+    const __nv_bfloat16 v = __float2bfloat16_rn(c < cols ? x[r * cols + c] : 0.0f);
+    y[i] = v;
+    if (yT && c < cols) yT[(long)c * ldT + r] = v;
 }
 
 // Adam on the FP32 master parameters; refreshes the BF16 copy of every weight.  wmap[i] is
 // the index of parameter i in the BF16 weight block, or -1 for a bias.
 __global__ void k_adam(float* __restrict__ theta, float* __restrict__ m1, float* __restrict__ m2,
                        const float* __restrict__ grad, long n, AdamArgs a, const int* __restrict__ wmap,
-                       __nv_bfloat16* __restrict__ wbf)
+                       __nv_bfloat16* __restrict__ wbf, const int* __restrict__ wmapT, __nv_bfloat16* __restrict__ wbfT)
 {
     const long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
@@ -875,6 +896,10 @@ __global__ void k_adam(float* __restrict__ theta, float* __restrict__ m1, float*
     theta[i] = th;
     const int w = wmap[i];
     if (w >= 0) wbf[w] = __float2bfloat16_rn(th);
+    if (wmapT) {
+        const int wt = wmapT[i];
+        if (wt >= 0) wbfT[wt] = __float2bfloat16_rn(th);
+    }
 }
 
 __global__ void k_train_reset(TrainState* ts, int t0)
@@ -898,12 +923,17 @@ __global__ void k_train_begin(TrainState* ts, const float* __restrict__ lr_dev, 
 
 // BF16 copy of the weights from the FP32 parameters.
 __global__ void k_refresh_bf16(const float* __restrict__ theta, long n, const int* __restrict__ wmap,
-                               __nv_bfloat16* __restrict__ wbf)
+                               __nv_bfloat16* __restrict__ wbf, const int* __restrict__ wmapT,
+                               __nv_bfloat16* __restrict__ wbfT)
 {
     const long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     const int w = wmap[i];
     if (w >= 0) wbf[w] = __float2bfloat16_rn(theta[i]);
+    if (wmapT) {
+        const int wt = wmapT[i];
+        if (wt >= 0) wbfT[wt] = __float2bfloat16_rn(theta[i]);
+    }
 }
 
 size_t gemm_smem_bytes(int nt) { return 2 * (size_t)(kBM * kBK * 2 + nt * kBK * 2) + 1024; }
@@ -947,7 +977,7 @@ bool make_map(CUtensorMap* map, const void* base, long rows, long K, long ld, in
               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
-size_t tma_smem_bytes(int nt) { return (size_t)kStages * (kBM * kBK * 2 + nt * kBK * 2) + 1024; }
+size_t tma_smem_bytes(int nt, int stages = kStages) { return (size_t)stages * (kBM * kBK * 2 + nt * kBK * 2) + 1024; }
 
 // The same matrix as 64-element (128-byte) x box_rows boxes in the 128-byte swizzled
 // layout (one box is one K slice of box_rows rows).
@@ -976,7 +1006,41 @@ cudaError_t launch_gemm(const GemmArgs& g0, cudaStream_t s)
     if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
     // both operands K-major with 16-byte rows: the TMA-fed kernel
     if (g.K > 0 && g.a_sk == 1 && g.b_sk == 1) {
-        const int nt = ((g.N < kMaxNT_TMA ? g.N : kMaxNT_TMA) + 15) / 16 * 16;
+        static int sm_count[64] = {};
+        if (!sm_count[dev]) {
+            e = cudaDeviceGetAttribute(&sm_count[dev], cudaDevAttrMultiProcessorCount, dev);
+            if (e != cudaSuccess) return e;
+        }
+        const int sms = sm_count[dev];
+        const int mt = (g.M + kBM - 1) / kBM;
+        auto round16 = [](int x) { return (x + 15) / 16 * 16; };
+        auto tiles_n = [&](int w) { return (g.N + w - 1) / w; };
+        // a long K over few output tiles (the weight gradients, K = batch): wide tiles and K
+        // split over up to kMaxSplit CTAs per tile, each storing a partial
+        int ntn = tiles_n(kMaxNT_TMA);
+        int nt = round16((g.N + ntn - 1) / ntn);
+        int S = 1;
+        g.kchunk = 0;
+        if (g.epi == kEpiStore && !g.bias && g.part && g.K >= 4 * kBK && mt * ntn < sms / 2) {
+            const int slices = (g.K + kBK - 1) / kBK;
+            S = (sms + mt * ntn - 1) / (mt * ntn);
+            S = S < kMaxSplit ? S : kMaxSplit;
+            S = S < (slices + 1) / 2 ? S : (slices + 1) / 2;          // at least 2 slices each
+            if (S > 1) {
+                g.kchunk = (slices + S - 1) / S * kBK;
+                S = (g.K + g.kchunk - 1) / g.kchunk;
+            } else {
+                S = 1;
+            }
+        } else {
+            // otherwise narrower tiles (down to 32 columns) until the tiles fill the SMs:
+            // the epilogue of a tile is the longest part of a CTA, and it shrinks with it
+            while (mt * tiles_n(nt) < sms && nt > 32) {
+                ntn *= 2;
+                const int w = round16((g.N + ntn - 1) / ntn);
+                nt = w > 32 ? w : 32;
+            }
+        }
         CUtensorMap ma, mb;
         if (make_map(&ma, g.A, g.M, g.K, g.a_sm, kBM) && make_map(&mb, g.B, g.N, g.K, g.b_sn, nt)) {
             static bool attr_tma[64] = {};
@@ -990,10 +1054,18 @@ cudaError_t launch_gemm(const GemmArgs& g0, cudaStream_t s)
             int cols = 32;
             while (cols < nt) cols <<= 1;
             g.tmem_cols = cols;
-            dim3 grid((unsigned)((g.M + kBM - 1) / kBM), (unsigned)((g.N + nt - 1) / nt));
-            k_gemm_bf16_tma<<<grid, kGemmThreads, tma_smem_bytes(nt), s>>>(ma, mb, g);
+            // narrow tiles keep two stages in flight: 41 KB of shared memory, five CTAs per
+            // SM, so that concurrent GEMMs (ensemble members on their own streams) overlap
+            g.stages = nt <= 64 ? 2 : kStages;
+            dim3 grid((unsigned)mt, (unsigned)tiles_n(nt), (unsigned)S);
+            k_gemm_bf16_tma<<<grid, kGemmThreads, tma_smem_bytes(nt, g.stages), s>>>(ma, mb, g);
+            e = cudaGetLastError();
+            if (e != cudaSuccess || g.kchunk == 0) return e;
+            const long mn = (long)g.M * g.N;
+            k_splitk_reduce<<<(unsigned)((mn + 255) / 256), 256, 0, s>>>(g.part, S, g.M, g.N, g.C, g.ldc, g.Cb);
             return cudaGetLastError();
         }
+        g.kchunk = 0;
     }
     const int nt = ((g.N < kMaxNT ? g.N : kMaxNT) + 15) / 16 * 16;
     g.nt = nt;
@@ -1031,7 +1103,7 @@ cudaError_t launch_gemm(const GemmArgs& g0, cudaStream_t s)
     e = cudaGetLastError();
     if (e != cudaSuccess || g.kchunk == 0) return e;
     const long mn = (long)g.M * g.N;
-    k_splitk_reduce<<<(unsigned)((mn + 255) / 256), 256, 0, s>>>(g.part, S, g.M, g.N, g.C, g.ldc);
+    k_splitk_reduce<<<(unsigned)((mn + 255) / 256), 256, 0, s>>>(g.part, S, g.M, g.N, g.C, g.ldc, g.Cb);
     return cudaGetLastError();
 }
 
@@ -1072,29 +1144,19 @@ cudaError_t launch_mlp_forward_fused(const FusedLaunch& f, cudaStream_t s)
     }
 }
 
-cudaError_t launch_colsum(const __nv_bfloat16* G, int M, int N, long ldg, float* out, float* part, cudaStream_t s)
-{
-    if (N <= 0) return cudaSuccess;
-    const int Y = M < kColsumChunks ? (M > 0 ? M : 1) : kColsumChunks;
-    k_colsum_part<<<dim3((unsigned)((N + 127) / 128), (unsigned)Y), 128, 0, s>>>(G, M, N, ldg, part);
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
-    k_sum_parts<<<(unsigned)((N + 127) / 128), 128, 0, s>>>(part, Y, N, out);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_inputs_bf16(const float* x, int rows, int cols, int ld, __nv_bfloat16* y, cudaStream_t s)
+cudaError_t launch_inputs_bf16(const float* x, int rows, int cols, int ld, __nv_bfloat16* y, cudaStream_t s,
+                               __nv_bfloat16* yT, long ldT)
 {
     const long n = (long)rows * ld;
     if (n <= 0) return cudaSuccess;
-    k_inputs_bf16<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(x, rows, cols, ld, y);
+    k_inputs_bf16<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(x, rows, cols, ld, y, yT, ldT);
     return cudaGetLastError();
 }
 
 cudaError_t launch_adam(float* theta, float* m1, float* m2, const float* grad, long n, const AdamArgs& a,
-                        const int* wmap, __nv_bfloat16* wbf, cudaStream_t s)
+                        const int* wmap, __nv_bfloat16* wbf, cudaStream_t s, const int* wmapT, __nv_bfloat16* wbfT)
 {
-    k_adam<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(theta, m1, m2, grad, n, a, wmap, wbf);
+    k_adam<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(theta, m1, m2, grad, n, a, wmap, wbf, wmapT, wbfT);
     return cudaGetLastError();
 }
 
@@ -1110,9 +1172,10 @@ cudaError_t launch_train_begin(TrainState* ts, const float* lr_dev, float beta1,
     return cudaGetLastError();
 }
 
-cudaError_t launch_refresh_bf16(const float* theta, long n, const int* wmap, __nv_bfloat16* wbf, cudaStream_t s)
+cudaError_t launch_refresh_bf16(const float* theta, long n, const int* wmap, __nv_bfloat16* wbf, cudaStream_t s,
+                                const int* wmapT, __nv_bfloat16* wbfT)
 {
-    k_refresh_bf16<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(theta, n, wmap, wbf);
+    k_refresh_bf16<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(theta, n, wmap, wbf, wmapT, wbfT);
     return cudaGetLastError();
 }
 
