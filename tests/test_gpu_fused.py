@@ -191,8 +191,8 @@ def test_rest_tiles_copy_what_the_quiescent_path_writes(precision, n):
     Courant-rate pass before the first step (and again after a host write) found quiescent
     with its fields in the quiescent path's form.  Against the same steps taken with the
     copy switched off (every tile then goes through the tile kernel's own quiescence test
-    and path): bitwise the same fields, time, dt and tallies, on a grid the tiles divide and
-    on a ragged one."""
+    and path): bitwise the same fields, time and dt, the tallies to rounding, on a grid the
+    tiles divide and on a ragged one."""
     spec = W.scaled_plain(n, radius_cells=5)
     a = _fused(spec, precision)
     a.step(1)
@@ -213,9 +213,11 @@ def test_rest_tiles_copy_what_the_quiescent_path_writes(precision, n):
         b.step(1)
         assert b.fused_queue() == (tiles, tiles)
     _assert_equal(a, b, spec)
+    # the tallies are sums of the CTAs' atomic additions, in the order the CTAs take their
+    # tiles from the queue: equal to rounding
     sa, sb = a.scalars(), b.scalars()
     for k in ("mass_out", "mass_pml", "mass_discarded", "zmom_out"):
-        assert sa[k] == sb[k], k
+        assert abs(sa[k] - sb[k]) <= 1e-12 * abs(sb[k]), k
 
 
 @pytest.mark.parametrize("precision", ["fp64", "fp32mix"])
