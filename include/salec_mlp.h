@@ -79,6 +79,26 @@ salec_status salec_mlp_train_step(salec_mlp* mlp, const float* x_dev, const floa
 salec_status salec_mlp_train(salec_mlp* mlp, const float* x_dev, const float* t_dev, int batch, int steps,
                              const float* lr_dev, float beta1, float beta2, float eps, double* sse_dev);
 
+/* Ensemble training: n (1..8) distinct networks trained together on the same inputs,
+ * targets and learning-rate table, each step's GEMMs, Adam update and bookkeeping issued
+ * as ONE launch for all members (a member index per CTA), each member with the same plan
+ * and arithmetic as salec_mlp_train gives it alone, so the results are those of n separate
+ * salec_mlp_train calls.  The group holds pointers to the member contexts (which must
+ * outlive it) and works on `stream` (the members' own streams are not used by group
+ * calls).  salec_mlp_train_group: `steps` steps, step k with learning rate lr_dev[k]; the
+ * first step with plain launches, then chunks of 25 steps as CUDA-graph replays (captured
+ * again when t_dev, lr_dev, batch or a hyper-parameter changes); every member's Adam step
+ * count advances by `steps`.  SALEC_EINVAL for n outside 1..8, a repeated or null member,
+ * a batch above a member's batch_max, a negative step count, a null pointer or a bad
+ * hyper-parameter.  Asynchronous; salec_mlp_check on each member reports a tensor-core
+ * wait that ran out. */
+typedef struct salec_mlp_group salec_mlp_group;
+salec_status salec_mlp_group_create(salec_mlp* const* nets, int n, void* stream, salec_mlp_group** out);
+salec_status salec_mlp_train_group(salec_mlp_group* group, const float* x_dev, const float* t_dev, int batch,
+                                   int steps, const float* lr_dev, float beta1, float beta2, float eps);
+const char* salec_mlp_group_last_error(const salec_mlp_group* group);
+void salec_mlp_group_destroy(salec_mlp_group* group);
+
 /* Synchronises and reports whether a tensor-core wait ran out of time since creation. */
 salec_status salec_mlp_check(salec_mlp* mlp);
 

@@ -158,72 +158,85 @@ GemmArgs gemm0(int M, int N, int K, int* err)
     return g;
 }
 
-// forward pass on X (already BF16): Z_l, H_l for the hidden layers; the output layer with
-// the epilogue `out_epi` (plain store into y, or the fused loss gradient against t)
+// Forward layer l on X (already BF16): Z_l, H_l (and H_l^T) for the hidden layers; the
+// output layer with the plain store into y, or (with the targets t) the fused loss gradient.
+// The pre-activations and the transposed copies are kept only for a backward pass.
+GemmArgs fwd_gemm(salec_mlp* n, int l, int B, float* y, long ldy, const float* t, bool with_loss)
+{
+    const bool keep_z = with_loss;
+    const int ni = kDims[l], no = kDims[l + 1];
+    GemmArgs g = gemm0(B, no, ni, n->errflag);
+    g.A = l == 0 ? n->X : n->H[l - 1]; g.a_sm = l == 0 ? kInLd : kHid; g.a_sk = 1;
+    g.B = n->wbf + n->wbf_off[l]; g.b_sn = w_ld(l); g.b_sk = 1;
+    g.bias = n->theta + n->boff[l];
+    if (l + 1 < kLayers) {
+        g.epi = kEpiBiasGelu;
+        g.C = keep_z ? n->Z[l] : nullptr; g.ldc = kHid;
+        g.Hout = n->H[l]; g.ldh = kHid;
+        if (keep_z) { g.HoutT = n->HT[l]; g.ldhT = n->ldT; }
+    } else if (with_loss) {
+        g.epi = kEpiOutLoss;
+        g.C = y; g.ldc = ldy;
+        g.Tin = t; g.ldt = SALEC_MLP_OUT;
+        g.Hout = n->G[0]; g.ldh = kHid;
+        g.HoutT = n->GT[0]; g.ldhT = n->ldT;
+        g.grad_scale = 2.0f / ((float)B * (float)SALEC_MLP_OUT);
+        g.loss = n->loss;
+    } else {
+        g.epi = kEpiStore;
+        g.C = y; g.ldc = ldy;
+    }
+    return g;
+}
+
+// Backward, layer l, from G[cur] = dL/dZ_l (BF16, GT[cur] its transpose).
+// dW_l[o][i] = sum_b G[b][o] Hprev[b][i] and db_l[o] = sum_b G[b][o], as one product of
+// G^T (no x B) with [Hprev | 1]^T ((ni + 1) x B): the row of ones after the transposed
+// activations gives the bias gradient in the last column.
+GemmArgs dw_gemm(salec_mlp* n, int l, int B, int cur, float* grad)
+{
+    const int ni = kDims[l], no = kDims[l + 1];
+    GemmArgs g = gemm0(no, ni + 1, B, n->errflag);
+    g.A = n->GT[cur]; g.a_sm = n->ldT; g.a_sk = 1;
+    g.B = l > 0 ? n->HT[l - 1] : n->XT; g.b_sn = n->ldT; g.b_sk = 1;
+    g.epi = kEpiStore;
+    g.C = grad + n->woff[l]; g.ldc = ni;
+    g.Cb = grad + n->boff[l];
+    g.part = n->part;
+    return g;
+}
+
+// dL/dZ_{l-1}[b][i] = (sum_o G[b][o] W_l[o][i]) gelu'(Z_{l-1}[b][i]) into G[cur ^ 1] and its
+// transpose, W_l^T K-major (l >= 1).
+GemmArgs dh_gemm(salec_mlp* n, int l, int B, int cur)
+{
+    const int ni = kDims[l], no = kDims[l + 1];
+    GemmArgs g = gemm0(B, ni, no, n->errflag);
+    g.A = n->G[cur]; g.a_sm = kHid; g.a_sk = 1;
+    g.B = n->wbfT + n->wbfT_off[l]; g.b_sn = wt_ld(l); g.b_sk = 1;
+    g.epi = kEpiGeluBwd;
+    g.Zin = n->Z[l - 1]; g.ldz = kHid;
+    g.Hout = n->G[cur ^ 1]; g.ldh = kHid;
+    g.HoutT = n->GT[cur ^ 1]; g.ldhT = n->ldT;
+    return g;
+}
+
 salec_status forward_impl(salec_mlp* n, int B, float* y, long ldy, const float* t, bool with_loss)
 {
-    // the pre-activations Z are kept only for a backward pass
-    const bool keep_z = with_loss;
-    const __nv_bfloat16* Hin = n->X;
-    long ldin = kInLd;
-    for (int l = 0; l < kLayers; ++l) {
-        const int ni = kDims[l], no = kDims[l + 1];
-        GemmArgs g = gemm0(B, no, ni, n->errflag);
-        g.A = Hin; g.a_sm = ldin; g.a_sk = 1;
-        g.B = n->wbf + n->wbf_off[l]; g.b_sn = w_ld(l); g.b_sk = 1;
-        g.bias = n->theta + n->boff[l];
-        if (l + 1 < kLayers) {
-            g.epi = kEpiBiasGelu;
-            g.C = keep_z ? n->Z[l] : nullptr; g.ldc = kHid;
-            g.Hout = n->H[l]; g.ldh = kHid;
-            if (keep_z) { g.HoutT = n->HT[l]; g.ldhT = n->ldT; }
-        } else if (with_loss) {
-            g.epi = kEpiOutLoss;
-            g.C = y; g.ldc = ldy;
-            g.Tin = t; g.ldt = SALEC_MLP_OUT;
-            g.Hout = n->G[0]; g.ldh = kHid;
-            g.HoutT = n->GT[0]; g.ldhT = n->ldT;
-            g.grad_scale = 2.0f / ((float)B * (float)SALEC_MLP_OUT);
-            g.loss = n->loss;
-        } else {
-            g.epi = kEpiStore;
-            g.C = y; g.ldc = ldy;
-        }
-        MLP_CUDA(n, launch_gemm(g, n->stream), "mlp forward gemm");
-        Hin = n->H[l < 4 ? l : 3];
-        ldin = kHid;
-    }
+    for (int l = 0; l < kLayers; ++l)
+        MLP_CUDA(n, launch_gemm(fwd_gemm(n, l, B, y, ldy, t, with_loss), n->stream), "mlp forward gemm");
     return SALEC_OK;
 }
 
-// backward pass from G[0] = dL/dY (BF16, and GT[0] its transpose): weight and bias
-// gradients into grad.  Every operand is read K-major, so every GEMM is TMA-fed.
+// backward pass from G[0] = dL/dY: weight and bias gradients into grad.  Every operand is
+// read K-major, so every GEMM is TMA-fed.
 salec_status backward_impl(salec_mlp* n, int B, float* grad)
 {
     int cur = 0;
     for (int l = kLayers - 1; l >= 0; --l) {
-        const int ni = kDims[l], no = kDims[l + 1];
-        // dW_l[o][i] = sum_b G[b][o] Hprev[b][i] and db_l[o] = sum_b G[b][o], as one product
-        // of G^T (no x B) with [Hprev | 1]^T ((ni + 1) x B): the row of ones after the
-        // transposed activations gives the bias gradient in the last column
-        GemmArgs gw = gemm0(no, ni + 1, B, n->errflag);
-        gw.A = n->GT[cur]; gw.a_sm = n->ldT; gw.a_sk = 1;
-        gw.B = l > 0 ? n->HT[l - 1] : n->XT; gw.b_sn = n->ldT; gw.b_sk = 1;
-        gw.epi = kEpiStore;
-        gw.C = grad + n->woff[l]; gw.ldc = ni;
-        gw.Cb = grad + n->boff[l];
-        gw.part = n->part;
-        MLP_CUDA(n, launch_gemm(gw, n->stream), "mlp weight-gradient gemm");
+        MLP_CUDA(n, launch_gemm(dw_gemm(n, l, B, cur, grad), n->stream), "mlp weight-gradient gemm");
         if (l == 0) break;
-        // dL/dZ_{l-1}[b][i] = (sum_o G[b][o] W_l[o][i]) gelu'(Z_{l-1}[b][i]), W_l^T K-major
-        GemmArgs gd = gemm0(B, ni, no, n->errflag);
-        gd.A = n->G[cur]; gd.a_sm = kHid; gd.a_sk = 1;
-        gd.B = n->wbfT + n->wbfT_off[l]; gd.b_sn = wt_ld(l); gd.b_sk = 1;
-        gd.epi = kEpiGeluBwd;
-        gd.Zin = n->Z[l - 1]; gd.ldz = kHid;
-        gd.Hout = n->G[cur ^ 1]; gd.ldh = kHid;
-        gd.HoutT = n->GT[cur ^ 1]; gd.ldhT = n->ldT;
-        MLP_CUDA(n, launch_gemm(gd, n->stream), "mlp activation-gradient gemm");
+        MLP_CUDA(n, launch_gemm(dh_gemm(n, l, B, cur), n->stream), "mlp activation-gradient gemm");
         cur ^= 1;
     }
     return SALEC_OK;
@@ -288,6 +301,107 @@ bool capture_train(salec_mlp* n, int B, const float* t_dev, const float* lr_dev,
     }
     n->tg_t = t_dev; n->tg_lr = lr_dev; n->tg_batch = B;
     n->tg_beta1 = beta1; n->tg_beta2 = beta2; n->tg_eps = eps;
+    return true;
+}
+
+}  // namespace
+
+// Ensemble members trained together (salec_mlp_train_group): the member contexts and the
+// CUDA graph of kTrainChunk steps captured for the arguments of the last call.
+struct salec_mlp_group {
+    std::vector<salec_mlp*> nets;
+    cudaStream_t stream = nullptr;
+    std::string err;
+    cudaGraphExec_t tgraph = nullptr;
+    const float* tg_t = nullptr;
+    const float* tg_lr = nullptr;
+    int tg_batch = 0;
+    float tg_beta1 = 0.0f, tg_beta2 = 0.0f, tg_eps = 0.0f;
+    bool tg_ok = true;
+    ~salec_mlp_group()
+    {
+        if (tgraph) cudaGraphExecDestroy(tgraph);
+    }
+};
+
+namespace {
+
+salec_status gfail(salec_mlp_group* g, salec_status st, const std::string& msg)
+{
+    if (g) g->err = msg;
+    return st;
+}
+
+#define GROUP_CUDA(g, call, where)                                                                                \
+    do {                                                                                                          \
+        cudaError_t e_ = (call);                                                                                  \
+        if (e_ != cudaSuccess) return gfail((g), SALEC_ECUDA, std::string(where) + ": " + cudaGetErrorString(e_)); \
+    } while (0)
+
+// One training step of every member: the step's start, the forward pass, the backward pass
+// and Adam, each GEMM one launch for all members (the inputs are already in each X, X^T).
+salec_status group_train_one(salec_mlp_group* G, cudaStream_t s, int B, const float* t_dev, const float* lr_dev,
+                             float beta1, float beta2, float eps)
+{
+    const int n = (int)G->nets.size();
+    GemmArgs args[kMaxGroup];
+    BeginGroup bg;
+    for (int k = 0; k < n; ++k) { bg.ts[k] = G->nets[k]->ts; bg.loss[k] = G->nets[k]->loss; }
+    GROUP_CUDA(G, launch_train_begin_group(bg, n, lr_dev, beta1, beta2, s), "group train step");
+    for (int l = 0; l < kLayers; ++l) {
+        for (int k = 0; k < n; ++k) args[k] = fwd_gemm(G->nets[k], l, B, G->nets[k]->Y, SALEC_MLP_OUT, t_dev, true);
+        GROUP_CUDA(G, launch_gemm_group(args, n, s), "group forward gemm");
+    }
+    int cur = 0;
+    for (int l = kLayers - 1; l >= 0; --l) {
+        for (int k = 0; k < n; ++k) args[k] = dw_gemm(G->nets[k], l, B, cur, G->nets[k]->grad);
+        GROUP_CUDA(G, launch_gemm_group(args, n, s), "group weight-gradient gemm");
+        if (l == 0) break;
+        for (int k = 0; k < n; ++k) args[k] = dh_gemm(G->nets[k], l, B, cur);
+        GROUP_CUDA(G, launch_gemm_group(args, n, s), "group activation-gradient gemm");
+        cur ^= 1;
+    }
+    AdamGroup ag;
+    for (int k = 0; k < n; ++k) {
+        salec_mlp* m = G->nets[k];
+        ag.theta[k] = m->theta; ag.m1[k] = m->m1; ag.m2[k] = m->m2; ag.grad[k] = m->grad;
+        ag.wbf[k] = m->wbf; ag.wbfT[k] = m->wbfT; ag.ts[k] = m->ts;
+    }
+    GROUP_CUDA(G, launch_adam_group(ag, n, n_params(), beta1, beta2, eps, G->nets[0]->wmap, G->nets[0]->wmapT, s),
+               "group adam");
+    return SALEC_OK;
+}
+
+// Capture kTrainChunk group steps on a private stream; false, with no error left pending,
+// when capture is not possible.
+bool capture_group(salec_mlp_group* G, int B, const float* t_dev, const float* lr_dev, float beta1, float beta2, float eps)
+{
+    if (G->tgraph) {
+        cudaGraphExecDestroy(G->tgraph);
+        G->tgraph = nullptr;
+    }
+    cudaStream_t cs;
+    if (cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) != cudaSuccess) {
+        (void)cudaGetLastError();
+        return false;
+    }
+    cudaGraph_t gr = nullptr;
+    cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+    salec_status st = SALEC_OK;
+    for (int k = 0; k < kTrainChunk && e == cudaSuccess && st == SALEC_OK; ++k)
+        st = group_train_one(G, cs, B, t_dev, lr_dev, beta1, beta2, eps);
+    const cudaError_t e2 = cudaStreamEndCapture(cs, &gr);
+    if (e == cudaSuccess) e = e2;
+    if (e == cudaSuccess && st == SALEC_OK) e = cudaGraphInstantiate(&G->tgraph, gr, 0);
+    if (gr) cudaGraphDestroy(gr);
+    cudaStreamDestroy(cs);
+    if (e != cudaSuccess || st != SALEC_OK) {
+        (void)cudaGetLastError();
+        G->tgraph = nullptr;
+        return false;
+    }
+    G->tg_t = t_dev; G->tg_lr = lr_dev; G->tg_batch = B;
+    G->tg_beta1 = beta1; G->tg_beta2 = beta2; G->tg_eps = eps;
     return true;
 }
 
@@ -526,6 +640,68 @@ salec_status salec_gemm_bf16(int M, int N, int K, const void* A, long a_sm, long
     if (launch_gemm(g, static_cast<cudaStream_t>(stream)) != cudaSuccess) return SALEC_ECUDA;
     return SALEC_OK;
 }
+
+salec_status salec_mlp_group_create(salec_mlp* const* nets, int n, void* stream, salec_mlp_group** out)
+{
+    if (!out || !nets || n < 1 || n > kMaxGroup) return SALEC_EINVAL;
+    *out = nullptr;
+    for (int k = 0; k < n; ++k) {
+        if (!nets[k]) return SALEC_EINVAL;
+        for (int j = 0; j < k; ++j)
+            if (nets[j] == nets[k]) return SALEC_EINVAL;
+    }
+    salec_mlp_group* g = new (std::nothrow) salec_mlp_group();
+    if (!g) return SALEC_ENOMEM;
+    g->nets.assign(nets, nets + n);
+    g->stream = static_cast<cudaStream_t>(stream);
+    *out = g;
+    return SALEC_OK;
+}
+
+salec_status salec_mlp_train_group(salec_mlp_group* G, const float* x_dev, const float* t_dev, int batch, int steps,
+                                   const float* lr_dev, float beta1, float beta2, float eps)
+{
+    if (!G) return SALEC_EINVAL;
+    if (steps < 0) return gfail(G, SALEC_EINVAL, "negative step count");
+    if (steps == 0) return SALEC_OK;
+    if (!x_dev || !t_dev || !lr_dev) return gfail(G, SALEC_EINVAL, "null pointer");
+    if (!(beta1 >= 0.0f && beta1 < 1.0f) || !(beta2 >= 0.0f && beta2 < 1.0f) || !(eps > 0.0f))
+        return gfail(G, SALEC_EINVAL, "bad Adam hyper-parameters");
+    for (salec_mlp* m : G->nets) {
+        if (batch < 1 || batch > m->bmax) return gfail(G, SALEC_EINVAL, "batch outside 1..batch_max of a member");
+        if (m->steps + (long)steps > 0x7fffffffL) return gfail(G, SALEC_EINVAL, "step count overflow");
+    }
+    cudaStream_t s = G->stream;
+    for (salec_mlp* m : G->nets) {
+        GROUP_CUDA(G, launch_inputs_bf16(x_dev, batch, SALEC_MLP_IN, kInLd, m->X, s, m->XT, m->ldT), "group input");
+        GROUP_CUDA(G, launch_train_reset(m->ts, (int)m->steps, s), "group train reset");
+    }
+    // the first step with plain launches (it also sets the kernels' attributes), then whole
+    // chunks as graph replays, then the rest
+    salec_status st = group_train_one(G, s, batch, t_dev, lr_dev, beta1, beta2, eps);
+    if (st != SALEC_OK) return st;
+    int done = 1;
+    const int chunks = (steps - 1) / kTrainChunk;
+    if (chunks > 0 && G->tg_ok) {
+        const bool same = G->tgraph && G->tg_t == t_dev && G->tg_lr == lr_dev && G->tg_batch == batch &&
+                          G->tg_beta1 == beta1 && G->tg_beta2 == beta2 && G->tg_eps == eps;
+        if (!same && !capture_group(G, batch, t_dev, lr_dev, beta1, beta2, eps)) G->tg_ok = false;
+        if (G->tgraph && G->tg_ok) {
+            for (int c = 0; c < chunks; ++c) GROUP_CUDA(G, cudaGraphLaunch(G->tgraph, s), "group train graph");
+            done += chunks * kTrainChunk;
+        }
+    }
+    for (; done < steps; ++done) {
+        st = group_train_one(G, s, batch, t_dev, lr_dev, beta1, beta2, eps);
+        if (st != SALEC_OK) return st;
+    }
+    for (salec_mlp* m : G->nets) m->steps += steps;
+    return SALEC_OK;
+}
+
+const char* salec_mlp_group_last_error(const salec_mlp_group* g) { return g ? g->err.c_str() : "null group"; }
+
+void salec_mlp_group_destroy(salec_mlp_group* g) { delete g; }
 
 const char* salec_mlp_last_error(const salec_mlp* n) { return n ? n->err.c_str() : ""; }
 

@@ -47,6 +47,7 @@ struct GemmArgs {
 };
 
 constexpr int kMaxSplit = 16;
+constexpr int kMaxGroup = 8;      // ensemble members one group launch takes
 
 constexpr int SALEC_MLP_OUT_N = 66;
 
@@ -91,6 +92,28 @@ cudaError_t launch_train_begin(TrainState* ts, const float* lr_dev, float beta1,
 cudaError_t launch_refresh_bf16(const float* theta, long n, const int* wmap, __nv_bfloat16* wbf, cudaStream_t s,
                                 const int* wmapT = nullptr, __nv_bfloat16* wbfT = nullptr);
 size_t gemm_smem_bytes(int nt);
+
+// An ensemble's members advanced together: each GEMM of a step is one launch for every
+// member (n <= kMaxGroup, the same shapes, each member's own buffers), with the same plan
+// and arithmetic per member as launch_gemm; likewise the Adam update and the step's start.
+cudaError_t launch_gemm_group(const GemmArgs* g, int n, cudaStream_t s);
+struct AdamGroup {
+    float* theta[kMaxGroup];
+    float* m1[kMaxGroup];
+    float* m2[kMaxGroup];
+    const float* grad[kMaxGroup];
+    __nv_bfloat16* wbf[kMaxGroup];
+    __nv_bfloat16* wbfT[kMaxGroup];
+    const TrainState* ts[kMaxGroup];
+};
+cudaError_t launch_adam_group(const AdamGroup& a, int n, long np, float beta1, float beta2, float eps, const int* wmap,
+                              const int* wmapT, cudaStream_t s);
+struct BeginGroup {
+    TrainState* ts[kMaxGroup];
+    double* loss[kMaxGroup];
+};
+cudaError_t launch_train_begin_group(const BeginGroup& b, int n, const float* lr_dev, float beta1, float beta2,
+                                     cudaStream_t s);
 
 }  // namespace mlp
 }  // namespace salec

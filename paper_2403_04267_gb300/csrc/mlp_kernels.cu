@@ -425,6 +425,14 @@ __global__ void __launch_bounds__(kGemmThreads) k_gemm_bf16(GemmArgs g)
 constexpr int kStages = 4;
 constexpr int kMaxNT_TMA = 256;
 
+// One GEMM for each member of an ensemble, launched together: the members' tensor maps and
+// arguments (the same shapes and plan, their own buffers).
+struct GroupGemm {
+    CUtensorMap ma[kMaxGroup], mb[kMaxGroup];
+    GemmArgs g[kMaxGroup];
+    int n, S;
+};
+
 __device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes)
 {
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
@@ -438,9 +446,13 @@ __device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map
         : "memory");
 }
 
-__global__ void __launch_bounds__(kGemmThreads) k_gemm_bf16_tma(const __grid_constant__ CUtensorMap mapA,
-                                                                const __grid_constant__ CUtensorMap mapB, GemmArgs g)
+// The body of the TMA-fed GEMM for one CTA: its tile (blockIdx.x, blockIdx.y) of the product
+// that g describes, K split `zsplit` of it.
+__device__ __forceinline__ void gemm_tma_body(const CUtensorMap* mapA_p, const CUtensorMap* mapB_p, const GemmArgs& g,
+                                              int zsplit)
 {
+    const CUtensorMap& mapA = *mapA_p;
+    const CUtensorMap& mapB = *mapB_p;
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     unsigned char* smem = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
     __shared__ uint64_t full[kStages], empty[kStages];
@@ -455,7 +467,7 @@ __global__ void __launch_bounds__(kGemmThreads) k_gemm_bf16_tma(const __grid_con
     const uint32_t tmem_cols = g.tmem_cols;
     // split-K: this CTA sums K range [kb, ke) (whole 64-wide slices: kchunk is a multiple of
     // kBK) into its own partial; a second kernel adds the partials in a fixed order
-    const int kb = g.kchunk > 0 ? (int)blockIdx.z * g.kchunk : 0;
+    const int kb = g.kchunk > 0 ? zsplit * g.kchunk : 0;
     const int ke = g.kchunk > 0 ? min(g.K, kb + g.kchunk) : g.K;
     const int nk = (ke - kb + kBK - 1) / kBK;
     const int ns = g.stages;              // ring stages in use (1..kStages), set by the launcher
@@ -532,7 +544,7 @@ __global__ void __launch_bounds__(kGemmThreads) k_gemm_bf16_tma(const __grid_con
     if (ok_flag) {
         if (g.kchunk > 0) {
             GemmArgs gp = g;
-            gp.C = g.part + (long)blockIdx.z * g.M * g.N;
+            gp.C = g.part + (long)zsplit * g.M * g.N;
             gp.ldc = g.N;
             gp.Cb = nullptr;
             epilogue(gp, tmem, m0, n0, NT, nk > 0);
@@ -545,6 +557,19 @@ __global__ void __launch_bounds__(kGemmThreads) k_gemm_bf16_tma(const __grid_con
     if (warp == 0) {
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(tmem_cols) : "memory");
     }
+}
+
+__global__ void __launch_bounds__(kGemmThreads) k_gemm_bf16_tma(const __grid_constant__ CUtensorMap mapA,
+                                                                const __grid_constant__ CUtensorMap mapB, GemmArgs g)
+{
+    gemm_tma_body(&mapA, &mapB, g, (int)blockIdx.z);
+}
+
+// The same GEMM for the members of an ensemble, one launch: blockIdx.z = member x S + split.
+__global__ void __launch_bounds__(kGemmThreads) k_gemm_bf16_tma_group(const __grid_constant__ GroupGemm G)
+{
+    const int member = (int)blockIdx.z / G.S, split = (int)blockIdx.z - member * G.S;
+    gemm_tma_body(&G.ma[member], &G.mb[member], G.g[member], split);
 }
 
 // ---------------------------------------------------------------------------------------
@@ -859,6 +884,30 @@ __global__ void k_splitk_reduce(const float* __restrict__ part, int S, int M, in
         C[m * ldc + n] = s;
 }
 
+// The split-K reduction of a group's GEMMs: blockIdx.y = member.
+struct GroupReduce {
+    const float* part[kMaxGroup];
+    float* C[kMaxGroup];
+    float* Cb[kMaxGroup];
+    long ldc;
+    int S, M, N;
+};
+__global__ void k_splitk_reduce_group(const __grid_constant__ GroupReduce R)
+{
+    const int g = blockIdx.y;
+    const long k = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= (long)R.M * R.N) return;
+    const float* part = R.part[g];
+    float s = 0.0f;
+    for (int p = 0; p < R.S; ++p) s += part[(long)p * R.M * R.N + k];
+    const long m = k / R.N;
+    const int n = (int)(k - m * R.N);
+    if (R.Cb[g] && n == R.N - 1)
+        R.Cb[g][m] = s;
+    else
+        R.C[g][m * R.ldc + n] = s;
+}
+
 // FP32 -> BF16 inputs of the first layer: rows of `cols` values into rows of `ld`, the
 // padding zero.
 __global__ void k_inputs_bf16(const float* __restrict__ x, int rows, int cols, int ld, __nv_bfloat16* __restrict__ y,
@@ -919,6 +968,46 @@ __global__ void k_train_begin(TrainState* ts, const float* __restrict__ lr_dev, 
     ts->c1 = (float)(1.0 / (1.0 - pow((double)beta1, t)));
     ts->c2 = (float)(1.0 / (1.0 - pow((double)beta2, t)));
     *loss = 0.0;
+}
+
+// Adam for the members of a group (blockIdx.y = member): the arithmetic of k_adam.
+__global__ void k_adam_group(const __grid_constant__ AdamGroup A, long n, float beta1, float beta2, float eps,
+                             const int* __restrict__ wmap, const int* __restrict__ wmapT)
+{
+    const int g = blockIdx.y;
+    const long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const TrainState* ts = A.ts[g];
+    const float lr = ts->lr, c1 = ts->c1, c2 = ts->c2;
+    float* m1 = A.m1[g];
+    float* m2 = A.m2[g];
+    const float gr = A.grad[g][i];
+    const float mi = beta1 * m1[i] + (1.0f - beta1) * gr;
+    const float vi = beta2 * m2[i] + (1.0f - beta2) * gr * gr;
+    m1[i] = mi;
+    m2[i] = vi;
+    const float th = A.theta[g][i] - lr * (mi * c1) / (sqrtf(vi * c2) + eps);
+    A.theta[g][i] = th;
+    const int w = wmap[i];
+    if (w >= 0) A.wbf[g][w] = __float2bfloat16_rn(th);
+    const int wt = wmapT[i];
+    if (wt >= 0) A.wbfT[g][wt] = __float2bfloat16_rn(th);
+}
+
+// k_train_begin for every member of a group (thread = member).
+__global__ void k_train_begin_group(const __grid_constant__ BeginGroup B, int n, const float* __restrict__ lr_dev,
+                                    float beta1, float beta2)
+{
+    const int g = threadIdx.x;
+    if (g >= n) return;
+    TrainState* ts = B.ts[g];
+    const int k = ts->k + 1;
+    const double t = (double)(ts->t0 + k);
+    ts->k = k;
+    ts->lr = lr_dev[k - 1];
+    ts->c1 = (float)(1.0 / (1.0 - pow((double)beta1, t)));
+    ts->c2 = (float)(1.0 / (1.0 - pow((double)beta2, t)));
+    *B.loss[g] = 0.0;
 }
 
 // BF16 copy of the weights from the FP32 parameters.
@@ -996,6 +1085,73 @@ bool make_map_sw128(CUtensorMap* map, const void* base, long rows, long K, long 
 
 }  // namespace
 
+// SM count and the TMA kernels' shared-memory attribute, per device (set once)
+cudaError_t tma_device_setup(int dev, int* sms)
+{
+    static int sm_count[64] = {};
+    static bool attr_tma[64] = {};
+    cudaError_t e = cudaSuccess;
+    if (!sm_count[dev]) {
+        e = cudaDeviceGetAttribute(&sm_count[dev], cudaDevAttrMultiProcessorCount, dev);
+        if (e != cudaSuccess) return e;
+    }
+    if (!attr_tma[dev]) {
+        e = cudaFuncSetAttribute(k_gemm_bf16_tma, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tma_smem_bytes(kMaxNT_TMA));
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(k_gemm_bf16_tma_group, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)tma_smem_bytes(kMaxNT_TMA));
+        if (e != cudaSuccess) return e;
+        attr_tma[dev] = true;
+    }
+    *sms = sm_count[dev];
+    return cudaSuccess;
+}
+
+// The TMA-fed kernel's plan for one product: tile width, K split, ring stages, tensor-memory
+// columns (into g), and the grid (mt row tiles, ntl column tiles, S splits).
+void plan_tma(GemmArgs& g, int sms, int* mt_out, int* ntl_out, int* S_out)
+{
+    const int mt = (g.M + kBM - 1) / kBM;
+    auto round16 = [](int x) { return (x + 15) / 16 * 16; };
+    auto tiles_n = [&](int w) { return (g.N + w - 1) / w; };
+    // a long K over few output tiles (the weight gradients, K = batch): wide tiles and K
+    // split over up to kMaxSplit CTAs per tile, each storing a partial
+    int ntn = tiles_n(kMaxNT_TMA);
+    int nt = round16((g.N + ntn - 1) / ntn);
+    int S = 1;
+    g.kchunk = 0;
+    if (g.epi == kEpiStore && !g.bias && g.part && g.K >= 4 * kBK && mt * ntn < sms / 2) {
+        const int slices = (g.K + kBK - 1) / kBK;
+        S = (sms + mt * ntn - 1) / (mt * ntn);
+        S = S < kMaxSplit ? S : kMaxSplit;
+        S = S < (slices + 1) / 2 ? S : (slices + 1) / 2;          // at least 2 slices each
+        if (S > 1) {
+            g.kchunk = (slices + S - 1) / S * kBK;
+            S = (g.K + g.kchunk - 1) / g.kchunk;
+        } else {
+            S = 1;
+        }
+    } else {
+        // otherwise narrower tiles (down to 32 columns) until the tiles fill the SMs:
+        // the epilogue of a tile is the longest part of a CTA, and it shrinks with it
+        while (mt * tiles_n(nt) < sms && nt > 32) {
+            ntn *= 2;
+            const int w = round16((g.N + ntn - 1) / ntn);
+            nt = w > 32 ? w : 32;
+        }
+    }
+    g.nt = nt;
+    int cols = 32;
+    while (cols < nt) cols <<= 1;
+    g.tmem_cols = cols;
+    // narrow tiles keep two stages in flight: 41 KB of shared memory, five CTAs per SM, so
+    // that concurrent GEMMs (ensemble members) overlap
+    g.stages = nt <= 64 ? 2 : kStages;
+    *mt_out = mt;
+    *ntl_out = tiles_n(nt);
+    *S_out = S;
+}
+
 cudaError_t launch_gemm(const GemmArgs& g0, cudaStream_t s)
 {
     GemmArgs g = g0;
@@ -1006,59 +1162,14 @@ cudaError_t launch_gemm(const GemmArgs& g0, cudaStream_t s)
     if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
     // both operands K-major with 16-byte rows: the TMA-fed kernel
     if (g.K > 0 && g.a_sk == 1 && g.b_sk == 1) {
-        static int sm_count[64] = {};
-        if (!sm_count[dev]) {
-            e = cudaDeviceGetAttribute(&sm_count[dev], cudaDevAttrMultiProcessorCount, dev);
-            if (e != cudaSuccess) return e;
-        }
-        const int sms = sm_count[dev];
-        const int mt = (g.M + kBM - 1) / kBM;
-        auto round16 = [](int x) { return (x + 15) / 16 * 16; };
-        auto tiles_n = [&](int w) { return (g.N + w - 1) / w; };
-        // a long K over few output tiles (the weight gradients, K = batch): wide tiles and K
-        // split over up to kMaxSplit CTAs per tile, each storing a partial
-        int ntn = tiles_n(kMaxNT_TMA);
-        int nt = round16((g.N + ntn - 1) / ntn);
-        int S = 1;
-        g.kchunk = 0;
-        if (g.epi == kEpiStore && !g.bias && g.part && g.K >= 4 * kBK && mt * ntn < sms / 2) {
-            const int slices = (g.K + kBK - 1) / kBK;
-            S = (sms + mt * ntn - 1) / (mt * ntn);
-            S = S < kMaxSplit ? S : kMaxSplit;
-            S = S < (slices + 1) / 2 ? S : (slices + 1) / 2;          // at least 2 slices each
-            if (S > 1) {
-                g.kchunk = (slices + S - 1) / S * kBK;
-                S = (g.K + g.kchunk - 1) / g.kchunk;
-            } else {
-                S = 1;
-            }
-        } else {
-            // otherwise narrower tiles (down to 32 columns) until the tiles fill the SMs:
-            // the epilogue of a tile is the longest part of a CTA, and it shrinks with it
-            while (mt * tiles_n(nt) < sms && nt > 32) {
-                ntn *= 2;
-                const int w = round16((g.N + ntn - 1) / ntn);
-                nt = w > 32 ? w : 32;
-            }
-        }
+        int sms = 0, mt = 0, ntl = 0, S = 1;
+        e = tma_device_setup(dev, &sms);
+        if (e != cudaSuccess) return e;
+        plan_tma(g, sms, &mt, &ntl, &S);
         CUtensorMap ma, mb;
-        if (make_map(&ma, g.A, g.M, g.K, g.a_sm, kBM) && make_map(&mb, g.B, g.N, g.K, g.b_sn, nt)) {
-            static bool attr_tma[64] = {};
-            if (!attr_tma[dev]) {
-                e = cudaFuncSetAttribute(k_gemm_bf16_tma, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)tma_smem_bytes(kMaxNT_TMA));
-                if (e != cudaSuccess) return e;
-                attr_tma[dev] = true;
-            }
-            g.nt = nt;
-            int cols = 32;
-            while (cols < nt) cols <<= 1;
-            g.tmem_cols = cols;
-            // narrow tiles keep two stages in flight: 41 KB of shared memory, five CTAs per
-            // SM, so that concurrent GEMMs (ensemble members on their own streams) overlap
-            g.stages = nt <= 64 ? 2 : kStages;
-            dim3 grid((unsigned)mt, (unsigned)tiles_n(nt), (unsigned)S);
-            k_gemm_bf16_tma<<<grid, kGemmThreads, tma_smem_bytes(nt, g.stages), s>>>(ma, mb, g);
+        if (make_map(&ma, g.A, g.M, g.K, g.a_sm, kBM) && make_map(&mb, g.B, g.N, g.K, g.b_sn, g.nt)) {
+            dim3 grid((unsigned)mt, (unsigned)ntl, (unsigned)S);
+            k_gemm_bf16_tma<<<grid, kGemmThreads, tma_smem_bytes(g.nt, g.stages), s>>>(ma, mb, g);
             e = cudaGetLastError();
             if (e != cudaSuccess || g.kchunk == 0) return e;
             const long mn = (long)g.M * g.N;
@@ -1104,6 +1215,57 @@ cudaError_t launch_gemm(const GemmArgs& g0, cudaStream_t s)
     if (e != cudaSuccess || g.kchunk == 0) return e;
     const long mn = (long)g.M * g.N;
     k_splitk_reduce<<<(unsigned)((mn + 255) / 256), 256, 0, s>>>(g.part, S, g.M, g.N, g.C, g.ldc, g.Cb);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_gemm_group(const GemmArgs* g0, int n, cudaStream_t s)
+{
+    if (n < 1 || n > kMaxGroup) return cudaErrorInvalidValue;
+    const GemmArgs& a = g0[0];
+    if (a.M <= 0 || a.N <= 0) return cudaSuccess;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+    bool tma = a.K > 0 && a.a_sk == 1 && a.b_sk == 1;
+    GroupGemm G;
+    int mt = 0, ntl = 0, S = 1;
+    if (tma) {
+        int sms = 0;
+        e = tma_device_setup(dev, &sms);
+        if (e != cudaSuccess) return e;
+        for (int k = 0; k < n && tma; ++k) {
+            G.g[k] = g0[k];
+            plan_tma(G.g[k], sms, &mt, &ntl, &S);      // the same plan as a member launched alone
+            tma = make_map(&G.ma[k], G.g[k].A, G.g[k].M, G.g[k].K, G.g[k].a_sm, kBM) &&
+                  make_map(&G.mb[k], G.g[k].B, G.g[k].N, G.g[k].K, G.g[k].b_sn, G.g[k].nt);
+        }
+    }
+    if (!tma) {
+        // operands the TMA cannot address: each member on its own
+        for (int k = 0; k < n; ++k)
+            if ((e = launch_gemm(g0[k], s)) != cudaSuccess) return e;
+        return cudaSuccess;
+    }
+    G.n = n;
+    G.S = S;
+    const GemmArgs& p = G.g[0];
+    dim3 grid((unsigned)mt, (unsigned)ntl, (unsigned)(S * n));
+    k_gemm_bf16_tma_group<<<grid, kGemmThreads, tma_smem_bytes(p.nt, p.stages), s>>>(G);
+    e = cudaGetLastError();
+    if (e != cudaSuccess || p.kchunk == 0) return e;
+    GroupReduce R;
+    for (int k = 0; k < n; ++k) {
+        R.part[k] = G.g[k].part;
+        R.C[k] = G.g[k].C;
+        R.Cb[k] = G.g[k].Cb;
+    }
+    R.ldc = p.ldc;
+    R.S = S;
+    R.M = p.M;
+    R.N = p.N;
+    const long mn = (long)p.M * p.N;
+    k_splitk_reduce_group<<<dim3((unsigned)((mn + 255) / 256), (unsigned)n), 256, 0, s>>>(R);
     return cudaGetLastError();
 }
 
@@ -1169,6 +1331,22 @@ cudaError_t launch_train_reset(TrainState* ts, int t0, cudaStream_t s)
 cudaError_t launch_train_begin(TrainState* ts, const float* lr_dev, float beta1, float beta2, double* loss, cudaStream_t s)
 {
     k_train_begin<<<1, 1, 0, s>>>(ts, lr_dev, beta1, beta2, loss);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_adam_group(const AdamGroup& a, int n, long np, float beta1, float beta2, float eps, const int* wmap,
+                              const int* wmapT, cudaStream_t s)
+{
+    if (n < 1 || n > kMaxGroup) return cudaErrorInvalidValue;
+    k_adam_group<<<dim3((unsigned)((np + 255) / 256), (unsigned)n), 256, 0, s>>>(a, np, beta1, beta2, eps, wmap, wmapT);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_train_begin_group(const BeginGroup& b, int n, const float* lr_dev, float beta1, float beta2,
+                                     cudaStream_t s)
+{
+    if (n < 1 || n > kMaxGroup) return cudaErrorInvalidValue;
+    k_train_begin_group<<<1, 32, 0, s>>>(b, n, lr_dev, beta1, beta2);
     return cudaGetLastError();
 }
 

@@ -69,7 +69,8 @@ EXPORTS = ["salec_state_bytes", "salec_create", "salec_set_material", "salec_set
            "salec_batch_last_error", "salec_batch_destroy",
            "salec_mlp_n_params", "salec_mlp_bytes", "salec_mlp_create", "salec_mlp_set_params",
            "salec_mlp_get_params", "salec_mlp_forward", "salec_mlp_gradient", "salec_mlp_train_step",
-           "salec_mlp_train",
+           "salec_mlp_train", "salec_mlp_group_create", "salec_mlp_train_group", "salec_mlp_group_last_error",
+           "salec_mlp_group_destroy",
            "salec_mlp_check", "salec_gemm_bf16", "salec_mlp_last_error", "salec_mlp_destroy"]
 
 
@@ -139,6 +140,10 @@ def load(build: bool = True):
         "salec_mlp_gradient": (I, [P, P, P, I, P, PD]),
         "salec_mlp_train_step": (I, [P, P, P, I, C.c_float, C.c_float, C.c_float, C.c_float, P]),
         "salec_mlp_train": (I, [P, P, P, I, I, P, C.c_float, C.c_float, C.c_float, P]),
+        "salec_mlp_group_create": (I, [C.POINTER(P), I, P, C.POINTER(P)]),
+        "salec_mlp_train_group": (I, [P, P, P, I, I, P, C.c_float, C.c_float, C.c_float]),
+        "salec_mlp_group_last_error": (C.c_char_p, [P]),
+        "salec_mlp_group_destroy": (None, [P]),
         "salec_mlp_check": (I, [P]),
         "salec_gemm_bf16": (I, [I, I, I, P, C.c_long, C.c_long, P, C.c_long, C.c_long, P, C.c_long, P]),
         "salec_mlp_last_error": (C.c_char_p, [P]),

@@ -111,6 +111,44 @@ class MLP:
         self._check(load().salec_mlp_check(self._h))
 
 
+class Group:
+    """Networks (at most 8) trained together on the same data: each step's GEMMs, Adam update
+    and bookkeeping are one launch for all of them, with each member's arithmetic that of
+    MLP.train alone (salec_mlp_train_group)."""
+
+    MAX = 8
+
+    def __init__(self, nets, stream=None):
+        import torch
+        assert 1 <= len(nets) <= self.MAX
+        self.nets = list(nets)
+        self.stream = stream if stream is not None else torch.cuda.current_stream(nets[0].device)
+        arr = (C.c_void_p * len(self.nets))(*[n._h for n in self.nets])
+        h = C.c_void_p()
+        st = load().salec_mlp_group_create(arr, len(self.nets), C.c_void_p(self.stream.cuda_stream), C.byref(h))
+        if st != SALEC_OK:
+            raise SalecError(st, "salec_mlp_group_create failed")
+        self._h = h
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h:
+            load().salec_mlp_group_destroy(h)
+            self._h = None
+
+    def train(self, x, t, lr, beta1: float = 0.9, beta2: float = 0.999, eps: float = 1e-8) -> None:
+        """len(lr) steps of every member, step k with learning rate lr[k] (an FP32 device
+        tensor), on the group's stream (asynchronous)."""
+        import torch
+        x, t = MLP._dev(x, N_IN), MLP._dev(t, N_OUT)
+        assert isinstance(lr, torch.Tensor) and lr.is_cuda and lr.dtype == torch.float32 and lr.is_contiguous()
+        st = load().salec_mlp_train_group(self._h, C.c_void_p(x.data_ptr()), C.c_void_p(t.data_ptr()),
+                                          int(x.shape[0]), int(lr.numel()), C.c_void_p(lr.data_ptr()),
+                                          float(beta1), float(beta2), float(eps))
+        if st != SALEC_OK:
+            raise SalecError(st, load().salec_mlp_group_last_error(self._h).decode())
+
+
 def gemm_bf16(M, N, K, A, a_strides, B, b_strides, C_out, ldc, stream=None) -> None:
     """C_out[m*ldc + n] = sum_k A[m*a_sm + k*a_sk] B[n*b_sn + k*b_sk] on the tensor cores
     (A, B: BF16 device tensors; C_out: FP32 device tensor; strides in elements)."""
@@ -294,13 +332,35 @@ class Ensemble:
     the prediction; their spread in transient depth and diameter decides whether a
     prediction is trusted or the draw goes to the solver."""
 
-    def __init__(self, X, T, members: int = 4, steps: int = 4000, lr: float = 2e-3, log=None):
+    def __init__(self, X, T, members: int = 4, steps: int = 4000, lr: float = 2e-3, log=None, group: int = 2):
         import torch
+        from . import workloads as W
         Tw = to_network(T)
-        # each member on its own stream: the members' small GEMMs run concurrently
-        self.streams = [torch.cuda.Stream() for _ in range(members)]
-        self.nets = [train(X, Tw, steps=steps, lr=lr, seed=1000 + k, log=log, stream=self.streams[k])
-                     for k in range(members)]
+        if group > 0 and log is None:
+            # `group` members a group (at most 8), every step of a group one set of launches;
+            # groups on their own streams
+            Xd = torch.from_numpy(np.ascontiguousarray(X, dtype=np.float32)).cuda()
+            Td = torch.from_numpy(np.ascontiguousarray(Tw, dtype=np.float32)).cuda()
+            L = torch.from_numpy(cosine_lr(steps, lr)).cuda()
+            self.streams, self.nets, self.groups = [], [], []
+            gs = min(group, Group.MAX)
+            for g0 in range(0, members, gs):
+                s = torch.cuda.Stream()
+                nets = [MLP(max(4096, len(X)), stream=s) for _ in range(g0, min(members, g0 + gs))]
+                for k, net in enumerate(nets):
+                    net.set_params(W.mlp_init(1000 + g0 + k).astype(np.float32))
+                self.streams.append(s)
+                self.nets += nets
+                self.groups.append(Group(nets, stream=s))
+            torch.cuda.current_stream().synchronize()       # the inputs, before the groups read them
+            self.keep = (Xd, Td, L)
+            for grp in self.groups:
+                grp.train(Xd, Td, L)
+        else:
+            # each member on its own stream: the members' small GEMMs run concurrently
+            self.streams = [torch.cuda.Stream() for _ in range(members)]
+            self.nets = [train(X, Tw, steps=steps, lr=lr, seed=1000 + k, log=log, stream=self.streams[k])
+                         for k in range(members)]
         for net in self.nets:
             net.check()
 

@@ -269,3 +269,38 @@ def test_networks_on_separate_streams_train_as_alone():
     for n, ref in zip(nets, alone):
         n.check()
         assert np.array_equal(n.get_params(), ref)
+
+
+@pytest.mark.parametrize("members, batch", [(3, 900), (8, 200)])
+def test_group_training_matches_members_trained_alone(members, batch):
+    """salec_mlp_train_group: the members' GEMMs, Adam updates and step starts launched once
+    for the whole group (80 steps: one plain step, three 25-step graph replays, four plain
+    steps), with each member's plan and arithmetic as when trained alone: the same
+    parameters bit for bit.  Batch 900 splits the weight gradients' K over CTAs (a
+    deterministic partial sum per split), batch 200 does not."""
+    X, T = _data(batch, seed=9)
+    Xd, Td = torch.from_numpy(X).cuda(), torch.from_numpy(T).cuda()
+    L = torch.from_numpy(S.cosine_lr(80, 2e-3)).cuda()
+    alone = []
+    for seed in range(members):
+        n = S.MLP(batch)
+        n.set_params(W.mlp_init(20 + seed).astype(np.float32))
+        n.train(Xd, Td, L)
+        alone.append(n.get_params())
+    st = torch.cuda.Stream()
+    nets = [S.MLP(batch, stream=st) for _ in range(members)]
+    for seed, n in enumerate(nets):
+        n.set_params(W.mlp_init(20 + seed).astype(np.float32))
+    torch.cuda.synchronize()
+    g = S.Group(nets, stream=st)
+    g.train(Xd, Td, L)
+    for n, ref in zip(nets, alone):
+        n.check()
+        assert np.array_equal(n.get_params(), ref)
+    # a second call continues every member's Adam step count
+    g.train(Xd, Td, L[:30])
+    solo = S.MLP(batch)
+    solo.set_params(W.mlp_init(20).astype(np.float32))
+    solo.train(Xd, Td, L)
+    solo.train(Xd, Td, L[:30])
+    assert np.array_equal(nets[0].get_params(), solo.get_params())
