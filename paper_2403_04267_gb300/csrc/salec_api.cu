@@ -1825,7 +1825,7 @@ salec_status salec_fused_queue(salec_ctx* ctx, int* queued, int* tiles)
     if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
     if (e != cudaSuccess) return cuda_check(ctx, e, "fused queue");
     if (w.next == 0) return SALEC_OK;      // no fused step since the queues were emptied
-    *queued = w.count;
+    *queued = w.count + w.back;
     *tiles = mixed(ctx) ? fused_tiles<float>(ctx->Pf) : fused_tiles<double>(ctx->Pd);
     return SALEC_OK;
 }

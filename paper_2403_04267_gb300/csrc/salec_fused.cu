@@ -196,14 +196,14 @@ __global__ void __launch_bounds__(NT, MINB) k_step_fused(const ParamsT<T> P, con
     double t_out = 0.0, t_disc = 0.0, t_pml = 0.0, t_zmom = 0.0;
     T speed_max = zero;
     // The CTA takes tiles from the queue the rest-tile kernel filled (complete: that kernel
-    // ran before this one) until it is empty; the tallies and the Courant maximum collect
-    // over all of them.
+    // ran before this one) until it is empty, the front of the list first, then the back
+    // from its end; the tallies and the Courant maximum collect over all of them.
     __shared__ int s_tile;
-    const int queued = min(O.work->count, nbx * nby);
+    const int nfront = min(O.work->count, nbx * nby), queued = min(nfront + O.work->back, nbx * nby);
     for (;;) {
     if (tid == 0) {
         const int t = atomicAdd(&O.work->next, 1);
-        s_tile = t < queued ? O.list[t] : -1;
+        s_tile = t < nfront ? O.list[t] : t < queued ? O.list[nbx * nby - 1 - (t - nfront)] : -1;
     }
     __syncthreads();        // also: every thread is done with the previous tile's shared memory
     const int tile = s_tile;
@@ -1041,6 +1041,7 @@ __global__ void __launch_bounds__(kRestThreads) k_rest_tiles(const ParamsT<T> P,
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         O.work_next->count = 0;
         O.work_next->next = 0;
+        O.work_next->back = 0;
     }
     T c2max = zero, speed_max = zero;
     bool bad = false;
@@ -1053,9 +1054,18 @@ __global__ void __launch_bounds__(kRestThreads) k_rest_tiles(const ParamsT<T> P,
         }
         rest = __all_sync(0xffffffffu, rest);
         if (!rest) {
+            // each tile is queued once a step: one that took the whole cycle in the step
+            // before at the front, one queued only for a neighbour (most of these take the
+            // quiescent path again) at the back, so that the long cycles start first and
+            // the short ones fill the end of the kernel
             if (lane == 0) {
-                const int q = atomicAdd(&O.work->count, 1);
-                if (q < nbx * nby) O.list[q] = tile;       // each tile is queued once a step
+                if (O.rest_in[tile] == 0) {
+                    const int q = atomicAdd(&O.work->count, 1);
+                    if (q < nbx * nby) O.list[q] = tile;
+                } else {
+                    const int q = atomicAdd(&O.work->back, 1);
+                    if (q < nbx * nby) O.list[nbx * nby - 1 - q] = tile;
+                }
             }
         } else {
             if (lane == 0) O.rest_out[tile] = 1;

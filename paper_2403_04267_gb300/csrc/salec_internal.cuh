@@ -58,8 +58,10 @@ typedef MatT<double> Mat;
 // The fused step's queue of tiles that need the whole cycle: filled by the rest-tile
 // kernel (count), drained by the persistent tile kernel (next).
 struct TileWork {
-    int count;
-    int next;
+    int count;      // queued tiles at the front of the list: tiles that took the whole cycle
+                    // in the step before (their cycles are the longest)
+    int next;       // queued tiles handed out
+    int back;       // queued tiles at the back of the list: tiles queued for a neighbour
 };
 
 // Scalars of a run, resident on the device.
