@@ -465,8 +465,9 @@ def _surrogate(args):
     out = {"train_draws": int(ok_tr.sum()), "heldout_draws": int(ok_ho.sum()),
            "failed_runs_excluded": int((~ok_tr).sum() + (~ok_ho).sum()),
            "members": args.sur_members, "train_steps": args.sur_steps, "train_s": round(t_train, 2),
-           # the whole ensemble's training (members concurrently on their own streams,
-           # 25-step graph replays): forward + backward = 3 forward passes per sample and step
+           # the whole ensemble's training (groups of two members, each group's step one set of
+           # launches, groups on their own streams, 25-step graph replays; wall time including
+           # set-up): forward + backward = 3 forward passes per sample and step
            "train_tflops_ensemble": round(3.0 * fwd * len(Xf) * args.sur_members * args.sur_steps / t_train / 1e12, 2),
            "fp64_solver_runs": nsol, "fp64_solver_failed": nfail}
     if nsol:

@@ -50,3 +50,21 @@ def test_state_bytes_and_argument_checks():
 def test_graft_build_entry():
     import __graft_entry__ as ge
     ge.build()
+
+
+def test_host_checks_of_the_batch_modes_and_the_ensemble_group():
+    """The entry points added for the persistent batch, the rest-tile switch and the
+    ensemble group refuse null or out-of-range arguments on the host, before any CUDA call."""
+    L = salec.load()
+    assert L.salec_batch_set_persistent(None, 1) == salec.SALEC_EINVAL
+    assert L.salec_batch_expire_next_barrier(None) == salec.SALEC_EINVAL
+    assert L.salec_set_rest_copy(None, 0) == salec.SALEC_EINVAL
+    h = C.c_void_p()
+    assert L.salec_mlp_group_create(None, 2, None, C.byref(h)) == salec.SALEC_EINVAL
+    one = (C.c_void_p * 1)(None)
+    assert L.salec_mlp_group_create(one, 1, None, C.byref(h)) == salec.SALEC_EINVAL      # a null member
+    fake = (C.c_void_p * 9)(*[C.c_void_p(16 * (k + 1)) for k in range(9)])
+    assert L.salec_mlp_group_create(fake, 9, None, C.byref(h)) == salec.SALEC_EINVAL     # more than 8
+    rep = (C.c_void_p * 2)(C.c_void_p(16), C.c_void_p(16))
+    assert L.salec_mlp_group_create(rep, 2, None, C.byref(h)) == salec.SALEC_EINVAL      # a repeated member
+    assert L.salec_mlp_train_group(None, None, None, 1, 1, None, 0.9, 0.999, 1e-8) == salec.SALEC_EINVAL
