@@ -11,6 +11,7 @@
 
 #include "../../include/salec_mlp.h"
 #include "mlp_internal.cuh"
+#include "salec_trace.h"
 
 using namespace salec::mlp;
 
@@ -518,6 +519,7 @@ salec_status salec_mlp_get_params(salec_mlp* n, float* theta_host)
 
 salec_status salec_mlp_forward(salec_mlp* n, const float* x_dev, int batch, float* y_dev)
 {
+    salec::HostRange range("salec_mlp_forward");
     salec_status st = check_batch(n, batch);
     if (st != SALEC_OK) return st;
     if (!x_dev || !y_dev) return fail(n, SALEC_EINVAL, "null pointer");
@@ -536,6 +538,7 @@ salec_status salec_mlp_forward(salec_mlp* n, const float* x_dev, int batch, floa
 salec_status salec_mlp_gradient(salec_mlp* n, const float* x_dev, const float* t_dev, int batch, float* grad_dev,
                                 double* loss_host)
 {
+    salec::HostRange range("salec_mlp_gradient");
     salec_status st = check_batch(n, batch);
     if (st != SALEC_OK) return st;
     if (!x_dev || !t_dev) return fail(n, SALEC_EINVAL, "null pointer");
@@ -559,6 +562,7 @@ salec_status salec_mlp_gradient(salec_mlp* n, const float* x_dev, const float* t
 salec_status salec_mlp_train_step(salec_mlp* n, const float* x_dev, const float* t_dev, int batch, float lr,
                                   float beta1, float beta2, float eps, double* sse_dev)
 {
+    salec::HostRange range("salec_mlp_train_step");
     salec_status st = check_batch(n, batch);
     if (st != SALEC_OK) return st;
     if (!x_dev || !t_dev) return fail(n, SALEC_EINVAL, "null pointer");
@@ -583,6 +587,7 @@ salec_status salec_mlp_train_step(salec_mlp* n, const float* x_dev, const float*
 salec_status salec_mlp_train(salec_mlp* n, const float* x_dev, const float* t_dev, int batch, int steps,
                              const float* lr_dev, float beta1, float beta2, float eps, double* sse_dev)
 {
+    salec::HostRange range("salec_mlp_train");
     salec_status st = check_batch(n, batch);
     if (st != SALEC_OK) return st;
     if (steps < 0) return fail(n, SALEC_EINVAL, "negative step count");
@@ -661,6 +666,7 @@ salec_status salec_mlp_group_create(salec_mlp* const* nets, int n, void* stream,
 salec_status salec_mlp_train_group(salec_mlp_group* G, const float* x_dev, const float* t_dev, int batch, int steps,
                                    const float* lr_dev, float beta1, float beta2, float eps)
 {
+    salec::HostRange range("salec_mlp_train_group");
     if (!G) return SALEC_EINVAL;
     if (steps < 0) return gfail(G, SALEC_EINVAL, "negative step count");
     if (steps == 0) return SALEC_OK;

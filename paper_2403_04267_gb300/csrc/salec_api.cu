@@ -13,6 +13,7 @@
 #include <vector>
 
 #include "salec_internal.cuh"
+#include "salec_trace.h"
 
 using namespace salec;
 
@@ -856,6 +857,7 @@ static salec_status step_fused(salec_ctx* ctx, int nsteps)
 
 salec_status salec_step(salec_ctx* ctx, int nsteps)
 {
+    HostRange range("salec_step");
     if (!ctx || nsteps < 0) return SALEC_EINVAL;
     if (!ctx->finalized) return fail(ctx, SALEC_EORDER, "step before finalize");
     if (ctx->form == SALEC_STEP_FUSED) return step_fused(ctx, nsteps);
@@ -1287,6 +1289,7 @@ salec_status salec_get_block_shapes(const salec_ctx* ctx, int* shapes)
 // change any field (only the summation order of the diagnostic tallies).
 salec_status salec_autotune(salec_ctx* ctx, int trial_steps, int* shapes_out)
 {
+    HostRange range("salec_autotune");
     if (!ctx || trial_steps < 1) return SALEC_EINVAL;
     if (!ctx->finalized) return fail(ctx, SALEC_EORDER, "autotune before finalize");
     // the block shapes are those of the phase kernels: tune them in the phase form
@@ -1524,6 +1527,7 @@ static salec_status batch_fields(salec_batch* b)
 
 salec_status salec_batch_step(salec_batch* b, int nsteps)
 {
+    HostRange range("salec_batch_step");
     if (!b || nsteps < 0) return SALEC_EINVAL;
     salec_status st0 = batch_fields(b);
     if (st0 == SALEC_OK) st0 = batch_restore_retired(b);
@@ -1644,6 +1648,7 @@ static salec_status batch_restore_retired(salec_batch* b)
 // eighth of the blocks they are left out of the work lists and the graph is captured again.
 salec_status salec_batch_run(salec_batch* b, int chunk, long max_steps, long* steps_done, int* runs_done)
 {
+    HostRange range("salec_batch_run");
     if (!b || chunk < 1 || max_steps < 0) return SALEC_EINVAL;
     const int n = (int)b->runs.size();
     if (b->stream == nullptr || b->stream == cudaStreamLegacy || b->stream == cudaStreamPerThread)
@@ -1759,6 +1764,7 @@ salec_status salec_batch_set_persistent(salec_batch* b, int on)
 
 salec_status salec_batch_autotune(salec_batch* b, int trial_steps, int* shapes_out)
 {
+    HostRange range("salec_batch_autotune");
     if (!b || trial_steps < 1) return SALEC_EINVAL;
     if (b->persistent) return batch_autotune_persistent(b, trial_steps, shapes_out);
     const int K = launches_per_step();
