@@ -372,6 +372,38 @@ class Sim:
         self._check(load().salec_set_step_form(self._h, {"phases": SALEC_STEP_PHASES, "fused": SALEC_STEP_FUSED}[form]))
 
 
+def run_logged(sim, steps: int, every: int, path: str, z_surface: float | None = None) -> list:
+    """Advance `sim` by `steps` steps in calls of `every` steps; after each call append one
+    JSON line to `path` (and to the returned list): the step count, time, the last dt and the
+    status word, the conservation sums (mass, z-momentum, kinetic and internal energy), the
+    tallies (mass out through the top, removed by clean-up, added by the strips' damping,
+    z-momentum out), the largest peak over-pressure, and with `z_surface` the crater depth
+    and diameter.  The dt history and the crater's growth of a run, as a log.  A run whose
+    status reports a failure stops logging after the line that shows it."""
+    import json
+    every = max(int(every), 1)
+    out = []
+    done = 0
+    with open(path, "a") as fh:
+        while done < steps:
+            n = min(every, steps - done)
+            sim.step(n)
+            done += n
+            sc = sim.scalars()
+            rec = {"step": int(sc["nstep"]), "t": float(sc["t"]), "dt": float(sc["dt"]), "status": int(sc["status"]),
+                   "tallies": {k: float(sc[k]) for k in ("mass_out", "mass_discarded", "mass_pml", "zmom_out")},
+                   "sums": {k: float(v) for k, v in sim.conservation().items()},
+                   "pmax": float(np.max(sim.get("pmax")))}
+            if z_surface is not None:
+                cr = sim.crater(z_surface, 64)
+                rec["crater"] = {"depth": float(cr["depth"]), "diameter": float(cr["diameter"])}
+            fh.write(json.dumps(rec) + "\n")
+            out.append(rec)
+            if rec["status"] != 0:
+                break
+    return out
+
+
 def courant_dt_noalloc(spec: dict, fr_ptrs, I_ptr: int, v_ptr: int, dt_prev: float, stream_ptr: int,
                        D_ptr: int | None = None) -> float:
     """Courant time step of a state held in caller device buffers, with no allocation
