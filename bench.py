@@ -80,7 +80,13 @@ def kernel_bytes_per_cell(e: int) -> dict:
         # a tile at rest: (f, rho), I and the EoS cache (p, c^2) read and written, vertices
         # written (at rest): the same count as the state's
         "k_rest_tiles": 2 * (2 * e + 8 + 2 * e) + 2 * e,
+        # the same tiles moved by the copy kernel that runs beside the tile kernel
+        "k_rest_copy": 2 * (2 * e + 8 + 2 * e) + 2 * e,
     }
+
+
+# the fused form's kernels that copy the tiles at rest (before the tile kernel, or beside it)
+REST_KERNELS = ("k_rest_tiles", "k_rest_copy")
 
 
 # persistent state read once and written once per step (one material, hydrodynamic):
@@ -735,6 +741,9 @@ def main():
     ap.add_argument("--precision", default="both", choices=["both", "fp64", "fp32mix"])
     ap.add_argument("--form", default="default", choices=["default", "phases", "fused"],
                     help="step form of the timed runs (default: the library's choice)")
+    ap.add_argument("--rest-copy", type=int, default=None, choices=[0, 1, 2],
+                    help="fused form: how the tiles at rest are copied (salec_set_rest_copy; "
+                         "default: the library's choice)")
     ap.add_argument("--batch-runs", type=int, default=256)
     ap.add_argument("--batch-t-end", type=float, default=20.0)
     ap.add_argument("--batch-ref-runs", type=int, default=16)
@@ -789,6 +798,8 @@ def main():
         form = form or (None if args.form == "default" else args.form)
         if form:
             sim.step_form = form
+        if args.rest_copy is not None:
+            sim.set_rest_copy(args.rest_copy)
         stream = sim.stream
         nbytes = sim.checkpoint_bytes()
         init = sim.state[:nbytes].clone()          # device copy of the initial state
@@ -876,7 +887,7 @@ def main():
         q = res.get("queue")
         if q:
             qf = q["queued_mean"] / q["tiles"]
-            units = cells * (1.0 - qf if dom == "k_rest_tiles" else qf)
+            units = cells * (1.0 - qf if dom in REST_KERNELS else qf)
         gbs = kb[dom] * units / (kt[dom] * 1e-3) / 1e9
         roof = {"kernel": dom, "hbm": {"achieved_gbs": round(gbs, 1), "peak_gbs": hbm_peak, "peak_kind": peak_kind,
                                        "frac": round(gbs / hbm_peak, 4), "bytes_per_cell": kb[dom],
@@ -914,7 +925,8 @@ def main():
 
         def alu_roof(d):
             kt = main_res["ktimes"][d]
-            if d in _FUSED_FULL_SIZE.get("fp64", {}) and d not in _COUNTERS_STALE["fp64"]:
+            if d in _FUSED_FULL_SIZE.get("fp64", {}) and d not in _COUNTERS_STALE["fp64"] and \
+                    _FUSED_FULL_SIZE["fp64"][d].get("flops"):
                 full = _FUSED_FULL_SIZE["fp64"][d] if (args.workload, args.steps, args.warmup) == _FULL_SIZE_CASE else {}
                 flops = full.get("flops")
                 ach = flops / (kt * 1e-3) / 1e12 if flops else None
@@ -925,7 +937,7 @@ def main():
                 flops = None if stale else _FLOPS_PER_CELL.get(d)
                 ach = flops * cells / (kt * 1e-3) / 1e12 if flops else None
                 per = {"flops_per_cell": flops, "counters_stale": stale}
-            tr, trk = _traffic(d, "fp64", args)
+            tr, trk = _traffic(d, "fp64", args, "k_rest_copy" in main_res["ktimes"])
             return {"bound": "alu", "kernel": d, "unit": "TFLOP/s", "peak": round(fp64_gemm, 4),
                     "peak_kind": "measured FP64 GEMM (cuBLAS, 4096^3) on this GPU",
                     "peak_nominal": round(fp64_nominal, 4),
@@ -936,7 +948,8 @@ def main():
                     "note": "flops count 2 per DFMA and 1 per DADD/DMUL; the FP64 pipe issues every FP64 "
                             "instruction at the DFMA rate, and fp64_pipe_busy (ncu, 2000x2000) is its occupancy"}
 
-        if dom == "k_rest_tiles":
+        rest_k = next((k for k in REST_KERNELS if k in main_res["ktimes"]), None)
+        if dom in REST_KERNELS:
             # the tiles at rest dominate: a copy of the state, held to HBM
             roof = hbm_roof(roof_hbm, dom, "fp64")
             if "k_step_fused" in main_res["ktimes"]:
@@ -944,9 +957,9 @@ def main():
         else:
             roof = alu_roof(dom)
             roof["hbm"] = roof_hbm["hbm"]
-        if "k_rest_tiles" in main_res["ktimes"] and dom != "k_rest_tiles":
-            rr, _ = roofline(main_res, e_main, "k_rest_tiles")
-            line_rest = hbm_roof(rr, "k_rest_tiles", "fp64")
+        if rest_k is not None and dom != rest_k:
+            rr, _ = roofline(main_res, e_main, rest_k)
+            line_rest = hbm_roof(rr, rest_k, "fp64")
         else:
             line_rest = None
     else:
@@ -1046,13 +1059,19 @@ _FUSED_FULL_SIZE: dict = {
 # kernels changed since their counters were taken: neither DRAM traffic nor flop rates are
 # reported for them until the next capture
 _COUNTERS_STALE: dict = {"fp64": set(), "fp32mix": set()}
+# Beside the copy kernel (salec_set_rest_copy mode 2) the FP64 tile kernel is another
+# instantiation (120 registers, the same arithmetic) sharing the SMs with the copies: its
+# FP64 operation count carries over, the DRAM traffic of the capture above does not.
 
 
-def _traffic(kernel: str, prec: str, args):
+def _traffic(kernel: str, prec: str, args, beside: bool = False):
     """DRAM bytes per launch of a kernel from ncu, and what they were measured on; None
-    where no capture applies."""
+    where no capture applies (beside: the step copied its tiles at rest beside the tile
+    kernel)."""
     if kernel in _COUNTERS_STALE[prec]:
         return None, "counters stale"
+    if beside and kernel == "k_step_fused":
+        return None, "runs beside the copy kernel: not captured"
     if kernel in _FUSED_FULL_SIZE[prec]:
         if (args.workload, args.steps, args.warmup) != _FULL_SIZE_CASE:
             return None, "not captured for this workload / K"

@@ -42,7 +42,8 @@ typedef enum {
     SALEC_ECUDA = 3,       /* a CUDA call failed (message in salec_last_error) */
     SALEC_EORDER = 4,      /* call made before/after the stage it belongs to */
     SALEC_EUNSTABLE = 5,   /* the device status word reports a non-positive volume or
-                              density, a NaN, or dt below dt_min (see salec_get_scalars) */
+                              density, a NaN, dt below dt_min, or a copy of the tiles at
+                              rest that did not complete (see salec_get_scalars) */
     SALEC_ETIMEOUT = 6     /* a bounded device wait ran out (the persistent batch's grid
                               barrier); the runs' states are partly advanced */
 } salec_status;
@@ -179,10 +180,11 @@ salec_status salec_step(salec_ctx* ctx, int nsteps);
  *                      fractions, no deviatoric stress, no strip, no gravity), on which
  *                      every phase returns its input, only reads and writes its state.
  *                      A tile found quiescent in the step before, with its eight
- *                      neighbours, is at rest: a streaming kernel before the tile kernel
- *                      copies it without a halo and queues the other tiles, which the
- *                      tile kernel (one CTA per resident slot of the device) takes from
- *                      the queue.  Default when grid->gravity == 0.
+ *                      neighbours, is at rest: it is copied without a halo (by a
+ *                      streaming kernel before the tile kernel, or by a copy kernel
+ *                      beside it: salec_set_rest_copy), and the other tiles are queued
+ *                      for the tile kernel (one CTA per resident slot of the device).
+ *                      Default when grid->gravity == 0.
  *   SALEC_STEP_PHASES  six kernels over the whole grid and the Courant kernel, in place
  *                      (block shapes from salec_set_block_shapes / salec_autotune).
  *                      Default under gravity, where no tile is quiescent and this form,
@@ -194,17 +196,25 @@ enum { SALEC_STEP_PHASES = 0, SALEC_STEP_FUSED = 1 };
 salec_status salec_set_step_form(salec_ctx* ctx, int form);
 int salec_get_step_form(const salec_ctx* ctx);
 
-/* Fused form: copy the tiles at rest (on != 0, the default) or send every tile through
- * the tile kernel (on = 0).  A tile is at rest when it and its eight neighbours passed
+/* Fused form, tiles at rest.  A tile is at rest when it and its eight neighbours passed
  * the tile kernel's quiescence test in the step before (or, for the first fused step
  * after set-up, a host write or other steps, when the Courant-rate pass over that state
- * found them quiescent with fields already in the form the quiescent path writes); the
- * copy returns bit for bit what the tile kernel would, so this switch changes no result,
- * only the work done (for checking that).  SALEC_EINVAL for a null context. */
-salec_status salec_set_rest_copy(salec_ctx* ctx, int on);
+ * found them quiescent with fields already in the form the quiescent path writes).
+ *   mode 0  every tile goes through the tile kernel;
+ *   mode 1  (default) a streaming kernel copies the tiles at rest and queues the others
+ *           before the tile kernel starts;
+ *   mode 2  a scan kernel queues the tiles, and a copy kernel of one warp per SM
+ *           on a second stream of the context moves the tiles at rest with bulk tensor
+ *           copies while the tile kernel runs on the same SMs.  Available in the FP64 form
+ *           for a uniform grid of one hydrodynamic material with nr even, where a CTA of
+ *           each kernel fit on one SM together; elsewhere mode 2 runs as mode 1.
+ * The copy returns bit for bit what the tile kernel would, so the mode changes no result,
+ * only the work done and its order.  SALEC_EINVAL for a null context or another mode. */
+salec_status salec_set_rest_copy(salec_ctx* ctx, int mode);
 
 /* Synchronise and read the scalars: out[0] t, out[1] dt of the last step, out[2] step
- * count, out[3] status bits (1 non-positive volume/density, 2 NaN, 4 dt < dt_min),
+ * count, out[3] status bits (1 non-positive volume/density, 2 NaN, 4 dt < dt_min, 8 the
+ * copy of the tiles at rest beside the tile kernel did not complete: a wait ran out),
  * out[4] mass out through the top, out[5] mass removed by clean-up, out[6] mass added by
  * the PML damping, out[7] z-momentum out through the top.  Returns SALEC_EUNSTABLE
  * (with out written) when status != 0. */
@@ -245,9 +255,10 @@ salec_status salec_state_changed(salec_ctx* ctx);
 
 /* Number of kernel launches one step issues (for launch accounting): in the phase form
  * the six phases and the one-thread Courant kernel between phases 0 and 1 (7); in the
- * fused form the Courant kernel, the rest-tile kernel and the tile kernel (3; a sequence of
- * fused steps that follows set-up, a host write or other steps adds one pass of Courant
- * rates first). */
+ * fused form the Courant kernel, the rest-tile kernel and the tile kernel (3), or, with the
+ * tiles at rest copied beside the tile kernel, the Courant, scan, copy and tile kernels
+ * (4); a sequence of fused steps that follows set-up, a host write or other steps adds one
+ * pass of Courant rates first. */
 int salec_launches_per_step(const salec_ctx* ctx);
 
 /* Fused form: *queued = the tiles the last fused step ran through the whole cycle (the
@@ -261,7 +272,9 @@ salec_status salec_fused_queue(salec_ctx* ctx, int* queued, int* tiles);
  * kernel k over the steps recorded since timing was switched on or last read, the number
  * of steps in *steps, and restarts the count.  Phase form: k < 6 are the phases (phase 0
  * includes the Courant kernel); fused form: k = 0 the Courant and rest-tile kernels,
- * k = 1 the tile kernel.
+ * k = 1 the tile kernel; with the copy beside the tile kernel, k = 0 from before the
+ * Courant kernel to the end of the copy kernel (second stream), k = 1 the tile kernel
+ * alone (the two overlap).
  * salec_step_kernel_name(ctx, k) names entry k of the context's form ("" for an unused
  * one); salec_kernel_name(k) names phase k of the phase form. */
 salec_status salec_set_kernel_timing(salec_ctx* ctx, int on);

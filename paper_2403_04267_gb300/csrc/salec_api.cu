@@ -193,6 +193,10 @@ struct salec_ctx {
     cudaGraphExec_t fgraph[2] = {nullptr, nullptr};   // fused chunks starting from copy 0 / 1
     bool fgraph_ok = true;
     bool rest_copy = true;                // tiles at rest copied (salec_set_rest_copy)
+    bool copy_beside = false;             // ... by the copy kernel beside the tile kernel, where available
+    RestCopy* rcopy = nullptr;            // its maps and launch shape for steps from copy 0 / 1 (FP64 form)
+    cudaStream_t s2 = nullptr;            // its stream, and the events that fork it off and join it back
+    cudaEvent_t fork = nullptr, join = nullptr;
     // optional per-kernel timing: 7 events per recorded step
     bool timing = false;
     std::vector<cudaEvent_t> ev;
@@ -554,6 +558,56 @@ static double profile(double c, double delta, double y, double R)
     return 1.5 * c / delta * s * s * log(1.0 / R);
 }
 
+// The FP64 form's copy of the tiles at rest beside the tile kernel: maps, stream and events,
+// where the grid and the device allow it (otherwise the rest-tile kernel copies them).
+static void release_beside(salec_ctx* ctx)
+{
+    delete[] ctx->rcopy;
+    ctx->rcopy = nullptr;
+    if (ctx->fork) cudaEventDestroy(ctx->fork);
+    if (ctx->join) cudaEventDestroy(ctx->join);
+    if (ctx->s2) cudaStreamDestroy(ctx->s2);
+    ctx->fork = ctx->join = nullptr;
+    ctx->s2 = nullptr;
+}
+
+static void prepare_beside(salec_ctx* ctx)
+{
+    release_beside(ctx);
+    RestCopy* rc = new (std::nothrow) RestCopy[2];
+    if (!rc) return;
+    if (!prepare_rest_copy(ctx->Pd, ctx->Od[0], &rc[0]) || !prepare_rest_copy(ctx->Pd_alt, ctx->Od[1], &rc[1])) {
+        delete[] rc;
+        return;
+    }
+    if (cudaStreamCreateWithFlags(&ctx->s2, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&ctx->fork, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&ctx->join, cudaEventDisableTiming) != cudaSuccess) {
+        (void)cudaGetLastError();
+        delete[] rc;
+        release_beside(ctx);
+        return;
+    }
+    ctx->rcopy = rc;
+}
+
+// a fused step copies its tiles at rest beside the tile kernel
+static bool beside(const salec_ctx* ctx) { return ctx->rest_copy && ctx->copy_beside && ctx->rcopy && !mixed(ctx); }
+
+// events one recorded step takes, and the pair that brackets timed kernel k
+static int events_per_step(const salec_ctx* ctx)
+{
+    if (ctx->form != SALEC_STEP_FUSED) return launches_per_step() + 1;
+    return beside(ctx) ? 4 : 3;
+}
+
+static void kernel_events(const salec_ctx* ctx, int k, int* a, int* b)
+{
+    const bool two = ctx->form == SALEC_STEP_FUSED && beside(ctx);
+    *a = two ? 2 * k : k;
+    *b = *a + 1;
+}
+
 salec_status salec_finalize(salec_ctx* ctx)
 {
     if (!ctx) return SALEC_EINVAL;
@@ -725,6 +779,7 @@ salec_status salec_finalize(salec_ctx* ctx)
     e = mixed(ctx) ? prepare_fused<float>(ctx->Pf, &ctas) : prepare_fused<double>(ctx->Pd, &ctas);
     if (e != cudaSuccess) return cuda_check(ctx, e, "fused step set-up");
     for (int k = 0; k < 2; ++k) ctx->Od[k].ctas = ctx->Of[k].ctas = ctas;
+    if (!mixed(ctx)) prepare_beside(ctx);
     // Default form.  Without gravity the fused form: its quiescent tiles (matter at rest
     // at zero pressure) only read and write their state, which on an impact grid is most of
     // it (4000 x 4000: mixed form 0.41 against 0.90 ms per step, FP64 1.26 against 7.16; a
@@ -788,6 +843,9 @@ static cudaError_t fused_step(salec_ctx* ctx, int parity, cudaStream_t s, cudaEv
         const cudaError_t e = cudaMemsetAsync(ctx->base + ctx->L.rest[parity], 0, ctx->L.ntiles, s);
         if (e != cudaSuccess) return e;
     }
+    if (beside(ctx))
+        return launch_step_fused_beside(parity ? ctx->Pd_alt : ctx->Pd, ctx->Od[parity], ctx->rcopy[parity], s, ctx->s2,
+                                        ctx->fork, ctx->join, ev);
     return mixed(ctx) ? launch_step_fused<float>(parity ? ctx->Pf_alt : ctx->Pf, ctx->Of[parity], s, ev)
                       : launch_step_fused<double>(parity ? ctx->Pd_alt : ctx->Pd, ctx->Od[parity], s, ev);
 }
@@ -839,14 +897,15 @@ static salec_status step_fused(salec_ctx* ctx, int nsteps)
     for (int n = 0; n < nsteps; ++n) {
         cudaEvent_t* evp = nullptr;
         if (ctx->timing) {
-            while (ctx->ev_used + 3 > ctx->ev.size()) {
+            const size_t E = (size_t)events_per_step(ctx);
+            while (ctx->ev_used + E > ctx->ev.size()) {
                 cudaEvent_t e0;
                 cudaError_t ce = cudaEventCreate(&e0);
                 if (ce != cudaSuccess) return cuda_check(ctx, ce, "event create");
                 ctx->ev.push_back(e0);
             }
             evp = ctx->ev.data() + ctx->ev_used;
-            ctx->ev_used += 3;
+            ctx->ev_used += E;
         }
         const cudaError_t e = fused_step(ctx, ctx->parity, ctx->stream, evp);
         if (e != cudaSuccess) return cuda_check(ctx, e, "fused step launch");
@@ -911,11 +970,14 @@ salec_status salec_set_step_form(salec_ctx* ctx, int form)
 
 int salec_get_step_form(const salec_ctx* ctx) { return ctx ? ctx->form : -1; }
 
-salec_status salec_set_rest_copy(salec_ctx* ctx, int on)
+salec_status salec_set_rest_copy(salec_ctx* ctx, int mode)
 {
-    if (!ctx) return SALEC_EINVAL;
-    if ((on != 0) == ctx->rest_copy) return SALEC_OK;
-    ctx->rest_copy = on != 0;
+    if (!ctx || mode < 0 || mode > 2) return SALEC_EINVAL;
+    const bool on = mode != 0, by = mode == 2;
+    if (on == ctx->rest_copy && by == ctx->copy_beside) return SALEC_OK;
+    ctx->rest_copy = on;
+    ctx->copy_beside = by;
+    ctx->ev_used = 0;
     for (int k = 0; k < 2; ++k)
         if (ctx->fgraph[k]) { cudaGraphExecDestroy(ctx->fgraph[k]); ctx->fgraph[k] = nullptr; }
     return SALEC_OK;
@@ -936,12 +998,15 @@ salec_status salec_kernel_times(salec_ctx* ctx, double* avg_ms, int n, int* step
     if (n < K) return SALEC_EINVAL;
     cudaError_t e = cudaStreamSynchronize(ctx->stream);
     if (e != cudaSuccess) return cuda_check(ctx, e, "kernel times");
-    const size_t ns = ctx->ev_used / (K + 1);
+    const size_t E = (size_t)events_per_step(ctx);
+    const size_t ns = ctx->ev_used / E;
     for (int k = 0; k < n; ++k) avg_ms[k] = 0.0;
     for (size_t s = 0; s < ns; ++s)
         for (int k = 0; k < K; ++k) {
             float ms = 0.0f;
-            e = cudaEventElapsedTime(&ms, ctx->ev[s * (K + 1) + k], ctx->ev[s * (K + 1) + k + 1]);
+            int a = 0, b = 0;
+            kernel_events(ctx, k, &a, &b);
+            e = cudaEventElapsedTime(&ms, ctx->ev[s * E + a], ctx->ev[s * E + b]);
             if (e != cudaSuccess) return cuda_check(ctx, e, "event elapsed");
             avg_ms[k] += ms;
         }
@@ -958,7 +1023,8 @@ const char* salec_kernel_name(int k)
 
 const char* salec_step_kernel_name(const salec_ctx* ctx, int k)
 {
-    if (ctx && ctx->form == SALEC_STEP_FUSED) return k == 0 ? "k_rest_tiles" : k == 1 ? "k_step_fused" : "";
+    if (ctx && ctx->form == SALEC_STEP_FUSED)
+        return k == 0 ? (beside(ctx) ? "k_rest_copy" : "k_rest_tiles") : k == 1 ? "k_step_fused" : "";
     return kernel_name(k);
 }
 
@@ -1814,7 +1880,9 @@ void salec_batch_destroy(salec_batch* b)
 
 int salec_launches_per_step(const salec_ctx* ctx)
 {
-    if (ctx && ctx->form == SALEC_STEP_FUSED) return 3;     // the Courant, rest-tile and tile kernels
+    // the Courant, rest-tile and tile kernels; beside the tile kernel: the Courant, scan,
+    // copy and tile kernels
+    if (ctx && ctx->form == SALEC_STEP_FUSED) return beside(ctx) ? 4 : 3;
     return kernels_per_step();
 }
 
@@ -1848,6 +1916,7 @@ void salec_destroy(salec_ctx* ctx)
     for (int k = 0; k < 2; ++k)
         if (ctx->fgraph[k]) cudaGraphExecDestroy(ctx->fgraph[k]);
     for (cudaEvent_t e : ctx->ev) cudaEventDestroy(e);
+    release_beside(ctx);
     delete ctx;
 }
 

@@ -25,6 +25,7 @@
 #include <cuda_runtime.h>
 
 #include "salec_device.cuh"
+#include "salec_tma.cuh"
 
 namespace salec {
 
@@ -146,8 +147,18 @@ __device__ __forceinline__ void store_pair(T4* a, int half, T2 v) { reinterpret_
 
 }  // namespace
 
-template <typename T, int NM, bool STR, bool UNI, int TW, int TH, int NT, int MINB>
-__global__ void __launch_bounds__(NT, MINB) k_step_fused(const ParamsT<T> P, const OutPtrsT<T> O)
+// Registers a thread of the tile kernel may take: what its occupancy leaves (65536 per SM),
+// or REGS where that is set (the instantiation that runs beside the copy kernel keeps 120
+// of its 128, so that its 16 warps leave room on the SM for the copy warp).
+template <int NT, int MINB, int REGS>
+struct TileRegs {
+    static constexpr int all = 65536 / (NT * MINB);
+    static constexpr int value = REGS ? REGS : (all > 255 ? 255 : all);
+};
+
+template <typename T, int NM, bool STR, bool UNI, int TW, int TH, int NT, int MINB, int REGS = 0>
+__global__ void __launch_bounds__(NT, MINB) __maxnreg__((TileRegs<NT, MINB, REGS>::value))
+    k_step_fused(const ParamsT<T> P, const OutPtrsT<T> O)
 {
     typedef VT<T> V;
     typedef typename V::T2 T2;
@@ -1042,6 +1053,7 @@ __global__ void __launch_bounds__(kRestThreads) k_rest_tiles(const ParamsT<T> P,
         O.work_next->count = 0;
         O.work_next->next = 0;
         O.work_next->back = 0;
+        O.work_next->copy_next = 0;
     }
     T c2max = zero, speed_max = zero;
     bool bad = false;
@@ -1136,6 +1148,222 @@ __global__ void __launch_bounds__(kRestThreads) k_rest_tiles(const ParamsT<T> P,
         for (int k = 1; k < kRestThreads / 32; ++k) b = max(b, sh[k]);
         if (b != 0ull) atomicMax(&p.scal->maxbits, b);
     }
+}
+
+// ---- Tiles at rest copied beside the tile kernel (FP64 form) -----------------------------
+// The rest-tile kernel above streams the tiles at rest before the tile kernel starts; the
+// tile kernel then keeps the FP64 pipes busy with DRAM idle.  Here the two overlap: a scan
+// kernel only queues the tiles (and flags the tiles at rest), and a copy kernel of one
+// warp per SM, on a second stream, moves the tiles at rest with bulk tensor copies
+// (global -> shared -> global, no registers in between) while the tile kernel computes on
+// the same SMs.  Its CTA takes more than half of an SM's shared memory, so no SM holds two
+// of them, and little enough that one fits beside a tile-kernel CTA.
+
+constexpr int kCopyStages = 5;          // tiles whose loads a copy CTA keeps in flight
+
+struct RestCopyArgs {
+    int nr, nz;
+    const unsigned char* rest_in;
+    TileWork* work;         // copy_next: groups of 32 tiles handed out
+    DevScalars* scal;
+    double2* v;             // vertices of the copy written (the grid's last row and column)
+};
+
+// A tile is at rest when it and its eight neighbours (those inside the grid) took the
+// quiescent path in the step that wrote the copy read here.
+__device__ __forceinline__ bool tile_at_rest(const unsigned char* __restrict__ rest_in, int tile, int nbx, int nby)
+{
+    const int bx = tile % nbx, by = tile / nbx;
+    int rest = 1;
+#pragma unroll
+    for (int dy = -1; dy <= 1; ++dy)
+#pragma unroll
+        for (int dx = -1; dx <= 1; ++dx) {
+            const int tx = bx + dx, ty = by + dy;
+            if (tx >= 0 && tx < nbx && ty >= 0 && ty < nby) rest &= rest_in[ty * nbx + tx] != 0;
+        }
+    return rest != 0;
+}
+
+// One thread per tile: a tile at rest gets its flag for the next step (the copy kernel
+// moves its fields); every other tile is queued for the tile kernel, as the rest-tile
+// kernel queues it (front: took the whole cycle in the step before; back: queued for a
+// neighbour).  Empties the next step's queue.
+template <int TW, int TH>
+__global__ void __launch_bounds__(kThreads) k_rest_scan(const int nr, const int nz, const OutPtrsT<double> O)
+{
+    const int nbx = (nr + TW - 1) / TW, nby = (nz + TH - 1) / TH, ntiles = nbx * nby;
+    const int tile = blockIdx.x * blockDim.x + threadIdx.x;
+    if (tile == 0) {
+        O.work_next->count = 0;
+        O.work_next->next = 0;
+        O.work_next->back = 0;
+        O.work_next->copy_next = 0;
+    }
+    if (tile >= ntiles) return;
+    if (tile_at_rest(O.rest_in, tile, nbx, nby)) {
+        O.rest_out[tile] = 1;
+    } else if (O.rest_in[tile] == 0) {
+        const int q = atomicAdd(&O.work->count, 1);
+        if (q < ntiles) O.list[q] = tile;
+    } else {
+        const int q = atomicAdd(&O.work->back, 1);
+        if (q < ntiles) O.list[ntiles - 1 - q] = tile;
+    }
+}
+
+// The copy: one warp per CTA.  Lane 0 issues the bulk copies; the warp takes groups of 32
+// tiles from a counter, tests them (one lane a tile) and copies those at rest through a
+// ring of kCopyStages shared-memory stages: the (f, rho) of each material, the EoS cache
+// and the energy of a tile in, the same out to the copy written, plus zeros for the
+// tile's vertices.  Between the load and the store the warp forms the tile's Courant
+// rates as the rest-tile kernel does (the largest c^2 of its cells with matter; NaN or
+// negative c^2 cell by cell), for the running maximum that sets the next step's dt.
+// Stage layout: (f, rho) of material m at m * FR, the EoS cache at NM * FR, I at
+// (NM + 1) * FR.  The maps index: src/dst[m] (f, rho), [NM] I, [NM + 1] the EoS cache.
+// A wait that runs out (2 s) sets status bit 8 and ends the copy.
+template <int NM, int TW, int TH>
+__global__ void __launch_bounds__(32, 1) k_rest_copy(const __grid_constant__ RestCopy rc, const RestCopyArgs A)
+{
+    constexpr int FR = TW * TH * 16, FI = TW * TH * 8;
+    constexpr int STAGE = (NM + 1) * FR + FI;
+    constexpr int S = kCopyStages;
+    extern __shared__ __align__(128) unsigned char copy_smem[];
+    __shared__ __align__(8) uint64_t full[S];
+    // the stages on a 128-byte boundary (the launch asks for 128 bytes more than they take)
+    unsigned char* smem = copy_smem + ((128u - (tma::smem_u32(copy_smem) & 127u)) & 127u);
+    unsigned char* zeros = smem + S * STAGE;          // TW x TH vertices of (0, 0)
+    const int lane = threadIdx.x;
+    const int nr = A.nr, nz = A.nz, nv = nr + 1;
+    const int nbx = (nr + TW - 1) / TW, nby = (nz + TH - 1) / TH, ntiles = nbx * nby;
+    const int ngroups = (ntiles + 31) / 32;
+    for (int k = lane; k < TW * TH; k += 32) reinterpret_cast<double2*>(zeros)[k] = make_double2(0.0, 0.0);
+    if (lane == 0) {
+        for (int s = 0; s < S; ++s) tma::mbar_init(&full[s], 1);
+        tma::fence_mbar_init();
+    }
+    tma::fence_async_smem();        // the zeros, for the tensor stores
+    __syncwarp();
+
+    // the warp's tiles at rest, in the order it takes them (warp-uniform)
+    int grp = 0;
+    unsigned mask = 0u;
+    bool more = true;
+    auto next_tile = [&]() -> int {
+        while (mask == 0u && more) {
+            int g = 0;
+            if (lane == 0) g = atomicAdd(&A.work->copy_next, 1);
+            g = __shfl_sync(0xffffffffu, g, 0);
+            if (g >= ngroups) {
+                more = false;
+                break;
+            }
+            grp = g;
+            const int t = g * 32 + lane;
+            mask = __ballot_sync(0xffffffffu, t < ntiles && tile_at_rest(A.rest_in, t, nbx, nby));
+        }
+        if (mask == 0u) return -1;
+        const int b = __ffs(mask) - 1;
+        mask &= mask - 1u;
+        return grp * 32 + b;
+    };
+    auto load = [&](int s, int tile) {     // lane 0
+        unsigned char* st = smem + s * STAGE;
+        const int x2 = 2 * TW * (tile % nbx), x1 = TW * (tile % nbx), y = TH * (tile / nbx);
+        tma::mbar_expect_tx(&full[s], STAGE);
+#pragma unroll
+        for (int m = 0; m < NM; ++m) tma::load_2d(st + m * FR, &rc.src[m], x2, y, &full[s]);
+        tma::load_2d(st + NM * FR, &rc.src[NM + 1], x2, y, &full[s]);
+        tma::load_2d(st + (NM + 1) * FR, &rc.src[NM], x1, y, &full[s]);
+    };
+
+    int ring[S];
+#pragma unroll
+    for (int s = 0; s < S; ++s) {
+        ring[s] = next_tile();
+        if (lane == 0 && ring[s] >= 0) load(s, ring[s]);
+    }
+    double c2max = 0.0, speed_max = 0.0;
+    bool bad = false, failed = false;
+    int n = 0;
+    for (;; ++n) {
+        const int s = n % S;
+        const int tile = ring[s];
+        if (tile < 0) break;
+        if (!__all_sync(0xffffffffu, tma::mbar_wait(&full[s], (n / S) & 1))) {
+            failed = true;
+            break;
+        }
+        const unsigned char* st = smem + s * STAGE;
+        const double2* ec = reinterpret_cast<const double2*>(st + NM * FR);
+#pragma unroll 4
+        for (int r = 0; r < TH; ++r) {
+            const int k = r * TW + lane;
+            bool here = false;
+#pragma unroll
+            for (int m = 0; m < NM; ++m) here = here || pos(reinterpret_cast<const double2*>(st + m * FR)[k].x);
+            if (here) {
+                const double c2 = ec[k].y;
+                if (is_nan(c2) || neg(c2)) {
+                    const double speed = t_sqrt<double>(0.0) + t_sqrt<double>(c2);
+                    bad = bad || is_nan(speed);
+                    speed_max = max_nonneg(speed_max, speed);
+                } else {
+                    c2max = max_nonneg(c2max, c2);
+                }
+            }
+        }
+        __syncwarp();
+        const int bx = tile % nbx, by = tile / nbx;
+        if (lane == 0) {
+            const int x2 = 2 * TW * bx, x1 = TW * bx, y = TH * by;
+#pragma unroll
+            for (int m = 0; m < NM; ++m) tma::store_2d(&rc.dst[m], x2, y, st + m * FR);
+            tma::store_2d(&rc.dst[NM + 1], x2, y, st + NM * FR);
+            tma::store_2d(&rc.dst[NM], x1, y, st + (NM + 1) * FR);
+            tma::store_2d(&rc.v, x2, y, zeros);
+            tma::bulk_commit();
+        }
+        // the vertex box covers columns TW bx .. TW bx + TW - 1 and rows TH by .. TH by + TH - 1
+        // (clipped to the grid); where the grid's last vertex row or column falls just
+        // outside it, plain stores
+        const int jb = TH * by, i = TW * bx + lane;
+        if (by == nby - 1 && jb + TH == nz && i <= nr) A.v[nz * nv + i] = make_double2(0.0, 0.0);
+        if (bx == nbx - 1 && TW * bx + TW == nr) {
+            const int jv = by == nby - 1 ? nz + 1 : jb + TH;
+            for (int j = jb + lane; j < jv; j += 32) A.v[j * nv + nr] = make_double2(0.0, 0.0);
+        }
+        // refill the stage of the tile before, once its stores have read it
+        if (n > 0) {
+            const int ps = (n - 1) % S;
+            if (lane == 0) tma::bulk_wait_read<1>();
+            __syncwarp();
+            const int t2 = next_tile();
+            ring[ps] = t2;
+            if (lane == 0 && t2 >= 0) {
+                tma::fence_async_smem();
+                load(ps, t2);
+            }
+        }
+    }
+    if (lane == 0) {
+        tma::bulk_wait_all();
+        if (failed) {
+            // the loads still in flight land before the CTA's shared memory is released
+            const int pending = n == 0 ? S : S - 1;
+            for (int d = 0; d < pending; ++d) {
+                const int q = (n + d) % S;
+                if (ring[q] >= 0) (void)tma::mbar_wait(&full[q], ((n + d) / S) & 1);
+            }
+            atomicOr(&A.scal->status, 8);
+        }
+    }
+    speed_max = max_nonneg(speed_max, t_sqrt<double>(0.0) + t_sqrt<double>(c2max));
+    if (__any_sync(0xffffffffu, bad) && lane == 0) atomicOr(&A.scal->status, 2);
+    unsigned long long b = (unsigned long long)__double_as_longlong(speed_max);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) b = max(b, __shfl_down_sync(0xffffffffu, b, o));
+    if (lane == 0 && b != 0ull) atomicMax(&A.scal->maxbits, b);
 }
 
 // The equation of state of the current state into the cache and its Courant rates into the
@@ -1341,6 +1569,142 @@ cudaError_t launch_step_fused(const ParamsT<T>& P, const OutPtrsT<T>& O, cudaStr
     e = dispatch<T, Fused>(P, [&](auto f) { return decltype(f)::launch(P, O, s); });
     if (ev) cudaEventRecord(ev[2], s);
     return e;
+}
+
+// ---- host side of the copy beside the tile kernel -----------------------------------------
+
+TmaEncodeTiledFn tma_encode_tiled()
+{
+    static TmaEncodeTiledFn fn = nullptr;
+    static bool tried = false;
+    if (!tried) {
+        tried = true;
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<TmaEncodeTiledFn>(p);
+        else
+            (void)cudaGetLastError();
+    }
+    return fn;
+}
+
+namespace {
+
+// the one instantiation whose tile-kernel CTA leaves room for a copy CTA on its SM (120
+// registers a thread, 110 KB of shared memory): FP64, one hydrodynamic material, uniform grid
+typedef Fused<double, 1, false, true> Beside;
+constexpr int kBesideTW = Beside::S::TW, kBesideTH = Beside::S::TH, kBesideRegs = 120;
+constexpr int kCopyStageBytes = 2 * kBesideTW * kBesideTH * 16 + kBesideTW * kBesideTH * 8;
+constexpr int kCopySmemNeed = kCopyStages * kCopyStageBytes + kBesideTW * kBesideTH * 16 + 128;
+
+// 2-D FP64 map: rows of `width` doubles `pitch` bytes apart, boxes of box_w x box_h
+bool map_2d(CUtensorMap* map, const void* base, long width, long rows, long pitch, int box_w, int box_h)
+{
+    const TmaEncodeTiledFn fn = tma_encode_tiled();
+    if (!fn || !base || (reinterpret_cast<uintptr_t>(base) & 15) || (pitch & 15) || width < 1 || rows < 1) return false;
+    const cuuint64_t dims[2] = {(cuuint64_t)width, (cuuint64_t)rows};
+    const cuuint64_t strides[1] = {(cuuint64_t)pitch};
+    const cuuint32_t box[2] = {(cuuint32_t)box_w, (cuuint32_t)box_h};
+    const cuuint32_t estr[2] = {1u, 1u};
+    return fn(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 2, const_cast<void*>(base), dims, strides, box, estr,
+              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+}  // namespace
+
+bool prepare_rest_copy(const ParamsT<double>& P, const OutPtrsT<double>& O, RestCopy* rc)
+{
+    if (!rc || P.nmat != 1 || P.any_strength || !P.uniform || (P.nr & 1)) return false;
+    auto tile_k = k_step_fused<double, 1, false, true, kBesideTW, kBesideTH, Beside::S::NT, Beside::S::MINB, kBesideRegs>;
+    auto copy_k = k_rest_copy<1, kBesideTW, kBesideTH>;
+    auto scan_k = k_rest_scan<kBesideTW, kBesideTH>;
+    cudaFuncAttributes ft, fc;
+    int dev = 0, sms = 0, smem_sm = 0, regs_sm = 0, optin = 0, reserved = 0;
+    bool ok = cudaFuncGetAttributes(&ft, tile_k) == cudaSuccess && cudaFuncGetAttributes(&fc, copy_k) == cudaSuccess &&
+              cudaGetDevice(&dev) == cudaSuccess &&
+              cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess &&
+              cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev) == cudaSuccess &&
+              cudaDeviceGetAttribute(&regs_sm, cudaDevAttrMaxRegistersPerMultiprocessor, dev) == cudaSuccess &&
+              cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) == cudaSuccess &&
+              cudaDeviceGetAttribute(&reserved, cudaDevAttrReservedSharedMemoryPerBlock, dev) == cudaSuccess;
+    if (!ok) {
+        (void)cudaGetLastError();
+        return false;
+    }
+    // registers are given out per warp in units of 256 (8 a thread)
+    const int tile_regs = (ft.numRegs + 7) / 8 * 8 * Beside::S::NT;
+    const int copy_regs = (fc.numRegs + 7) / 8 * 8 * 32;
+    if (tile_regs + copy_regs > regs_sm) return false;
+    const int tile_smem = (int)Beside::L::bytes + (int)ft.sharedSizeBytes + reserved;
+    // more than half of the SM: no SM takes two copy CTAs (which would leave no room there
+    // for a tile CTA)
+    int dyn = smem_sm / 2 - reserved - (int)fc.sharedSizeBytes + 128;
+    dyn = ((dyn > kCopySmemNeed ? dyn : kCopySmemNeed) + 127) / 128 * 128;
+    if (dyn > optin || tile_smem + dyn + (int)fc.sharedSizeBytes + reserved > smem_sm) return false;
+    // the largest shared-memory share of the SM for all three kernels: an SM whose L1 /
+    // shared split suits one of them alone would hold a second kernel's CTA back until it
+    // drains
+    int per_sm = 0, per_sm_tile = 0;
+    const int maxshared = (int)cudaSharedmemCarveoutMaxShared;
+    if (cudaFuncSetAttribute(copy_k, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn) != cudaSuccess ||
+        cudaFuncSetAttribute(tile_k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Beside::L::bytes) != cudaSuccess ||
+        cudaFuncSetAttribute(copy_k, cudaFuncAttributePreferredSharedMemoryCarveout, maxshared) != cudaSuccess ||
+        cudaFuncSetAttribute(tile_k, cudaFuncAttributePreferredSharedMemoryCarveout, maxshared) != cudaSuccess ||
+        cudaFuncSetAttribute(scan_k, cudaFuncAttributePreferredSharedMemoryCarveout, maxshared) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, copy_k, 32, dyn) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_tile, tile_k, Beside::S::NT, Beside::L::bytes) != cudaSuccess) {
+        (void)cudaGetLastError();
+        return false;
+    }
+    if (per_sm != 1 || per_sm_tile != 1) return false;
+    const long nr = P.nr, nz = P.nz;
+    ok = map_2d(&rc->src[0], P.p.fr[0], 2 * nr, nz, 16 * nr, 2 * kBesideTW, kBesideTH) &&
+         map_2d(&rc->src[1], P.p.I, nr, nz, 8 * nr, kBesideTW, kBesideTH) &&
+         map_2d(&rc->src[2], P.p.eosc, 2 * nr, nz, 16 * nr, 2 * kBesideTW, kBesideTH) &&
+         map_2d(&rc->dst[0], O.fr[0], 2 * nr, nz, 16 * nr, 2 * kBesideTW, kBesideTH) &&
+         map_2d(&rc->dst[1], O.I, nr, nz, 8 * nr, kBesideTW, kBesideTH) &&
+         map_2d(&rc->dst[2], O.eosc, 2 * nr, nz, 16 * nr, 2 * kBesideTW, kBesideTH) &&
+         map_2d(&rc->v, O.v, 2 * (nr + 1), nz + 1, 16 * (nr + 1), 2 * kBesideTW, kBesideTH);
+    if (!ok) return false;
+    rc->ctas = sms;
+    rc->smem = dyn;
+    return true;
+}
+
+cudaError_t launch_step_fused_beside(const ParamsT<double>& P, const OutPtrsT<double>& O, const RestCopy& rc,
+                                     cudaStream_t s, cudaStream_t s2, cudaEvent_t fork, cudaEvent_t join,
+                                     cudaEvent_t* ev)
+{
+    if (ev) cudaEventRecord(ev[0], s);
+    cudaError_t e = launch_courant<double>(P, s);
+    if (e == cudaSuccess) e = cudaEventRecord(fork, s);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(s2, fork, 0);
+    if (e != cudaSuccess) return e;
+    RestCopyArgs A;
+    A.nr = P.nr; A.nz = P.nz; A.rest_in = O.rest_in; A.work = O.work; A.scal = P.p.scal; A.v = O.v;
+    k_rest_copy<1, kBesideTW, kBesideTH><<<rc.ctas, 32, rc.smem, s2>>>(rc, A);
+    e = cudaGetLastError();
+    if (ev) cudaEventRecord(ev[1], s2);
+    // the second stream joins back whatever happened, so that a capture stays well formed
+    const cudaError_t ej = cudaEventRecord(join, s2);
+    if (e == cudaSuccess) e = ej;
+    if (e == cudaSuccess) {
+        const int nt = Beside::tiles(P);
+        k_rest_scan<kBesideTW, kBesideTH><<<(nt + kThreads - 1) / kThreads, kThreads, 0, s>>>(P.nr, P.nz, O);
+        e = cudaGetLastError();
+    }
+    if (ev) cudaEventRecord(ev[2], s);
+    if (e == cudaSuccess) {
+        k_step_fused<double, 1, false, true, kBesideTW, kBesideTH, Beside::S::NT, Beside::S::MINB, kBesideRegs>
+            <<<O.ctas, Beside::S::NT, Beside::L::bytes, s>>>(P, O);
+        e = cudaGetLastError();
+    }
+    if (ev) cudaEventRecord(ev[3], s);
+    const cudaError_t ew = cudaStreamWaitEvent(s, join, 0);
+    return e == cudaSuccess ? ew : e;
 }
 
 template cudaError_t prepare_fused<double>(const ParamsT<double>&, int*);

@@ -9,6 +9,7 @@
 //               conservation sums stay FP64.
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 #include <string.h>
@@ -62,6 +63,7 @@ struct TileWork {
                     // in the step before (their cycles are the longest)
     int next;       // queued tiles handed out
     int back;       // queued tiles at the back of the list: tiles queued for a neighbour
+    int copy_next;  // groups of 32 tiles handed to the copy kernel that runs beside the tile kernel
 };
 
 // Scalars of a run, resident on the device.
@@ -401,6 +403,29 @@ template <typename T> int fused_tiles(const ParamsT<T>& P);
 template <typename T> cudaError_t launch_courant_rates(const ParamsT<T>& P, unsigned char* rest, cudaStream_t s);
 template <typename T>
 cudaError_t launch_step_fused(const ParamsT<T>& P, const OutPtrsT<T>& O, cudaStream_t s, cudaEvent_t* ev);
+// The FP64 form's tiles at rest copied beside the tile kernel: a scan kernel queues the
+// tiles (as the rest-tile kernel does) and a copy kernel of one warp per SM, on a second
+// stream, moves the tiles at rest with bulk tensor copies while the tile kernel runs.  It
+// needs a tile-kernel CTA and a copy CTA to fit on one SM together (registers and shared
+// memory), even nr (the energy's rows then start on 16-byte boundaries) and a uniform
+// grid of one hydrodynamic material.  The maps and the launch shape of one direction
+// (read copy -> written copy):
+constexpr int kCopyFields = kMaxMat + 2;
+struct RestCopy {
+    CUtensorMap src[kCopyFields];   // (f, rho) of each material, I, the EoS cache of the copy read
+    CUtensorMap dst[kCopyFields];   // the same fields of the copy written
+    CUtensorMap v;                  // the vertices of the copy written
+    int ctas;                       // one per SM
+    int smem;                       // dynamic shared memory of a copy CTA
+};
+// false (no error pending) where the form is not available for this grid and device
+bool prepare_rest_copy(const ParamsT<double>& P, const OutPtrsT<double>& O, RestCopy* rc);
+// one step: the Courant kernel on s; then the copy kernel on s2 beside the scan and tile
+// kernels on s; s waits for s2 at the end.  With ev: events before the Courant kernel (s),
+// after the copy kernel (s2), after the scan kernel (s), after the tile kernel (s).
+cudaError_t launch_step_fused_beside(const ParamsT<double>& P, const OutPtrsT<double>& O, const RestCopy& rc,
+                                     cudaStream_t s, cudaStream_t s2, cudaEvent_t fork, cudaEvent_t join,
+                                     cudaEvent_t* ev);
 bool kernel_on_vertices(int k);
 int tiles_of(int nr, int nz, int k, dim3 blk);
 template <typename T> cudaError_t launch_pressure(const ParamsT<T>& P, double* out, cudaStream_t s);

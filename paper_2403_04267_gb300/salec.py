@@ -356,10 +356,13 @@ class Sim:
         self._check(load().salec_fused_queue(self._h, C.byref(q), C.byref(t)))
         return q.value, t.value
 
-    def set_rest_copy(self, on: bool) -> None:
-        """Fused form: copy tiles at rest (default) or run every tile through the tile
-        kernel; the results are the same bit for bit."""
-        self._check(load().salec_set_rest_copy(self._h, 1 if on else 0))
+    def set_rest_copy(self, mode) -> None:
+        """Fused form, tiles at rest: 0 (or False) run every tile through the tile kernel;
+        1 (or True, the default) copy them with the rest-tile kernel before the tile kernel;
+        2 copy them beside the tile kernel where the form allows it, else as 1.  The results
+        are the same bit for bit."""
+        m = 1 if mode is True else 0 if mode is False else int(mode)
+        self._check(load().salec_set_rest_copy(self._h, m))
 
     @property
     def step_form(self) -> str:

@@ -16,6 +16,8 @@ def test_algorithmic_bytes_per_cell():
     # written, its vertex written
     assert kb8["k_rest_tiles"] == 96 and kb4["k_rest_tiles"] == 56
     assert kb8["k_step_fused"] == 96 and kb4["k_step_fused"] == 56
+    # the copy beside the tile kernel moves the same tiles
+    assert all(kb8[k] == 96 for k in bench.REST_KERNELS)
 
 
 def test_peak_decay_bins_by_distance_from_the_impact_point():
@@ -68,3 +70,14 @@ def test_ncu_counters_only_for_the_workload_they_were_taken_on():
     finally:
         bench._COUNTERS_STALE.clear()
         bench._COUNTERS_STALE.update(saved)
+
+
+def test_tile_kernel_traffic_withheld_beside_the_copy_kernel():
+    """With the tiles at rest copied beside the tile kernel, the FP64 tile kernel is another
+    instantiation sharing its SMs with the copies: the DRAM traffic of the capture is not
+    reported for it, its FP64 operation count (same arithmetic) is."""
+    args = types.SimpleNamespace(workload="large_4000", steps=20, warmup=5)
+    assert bench._traffic("k_step_fused", "fp64", args)[0] is not None
+    assert bench._traffic("k_step_fused", "fp64", args, beside=True)[0] is None
+    assert bench._FUSED_FULL_SIZE["fp64"]["k_step_fused"]["flops"] > 0
+    assert bench._traffic("k_rest_copy", "fp64", args)[0] is None

@@ -220,6 +220,59 @@ def test_rest_tiles_copy_what_the_quiescent_path_writes(precision, n):
         assert abs(sa[k] - sb[k]) <= 1e-12 * abs(sb[k]), k
 
 
+@pytest.mark.parametrize("nr,nz,pml", [(200, 200, 16), (256, 192, 0), (202, 160, 16), (230, 176, 0)])
+def test_rest_copy_beside_the_tile_kernel_matches_the_rest_tile_kernel(nr, nz, pml):
+    """FP64, one hydrodynamic material, nr even: the copy kernel that runs beside the tile
+    kernel (bulk tensor copies of the tiles at rest, on a second stream) against the
+    rest-tile kernel that runs before the tile kernel, and against no copy at all: bitwise
+    the same fields, time and dt after 60 steps (a graph chunk included), the tallies to
+    rounding.  The 32 x 16 tiles divide the grid in neither direction, in both (without
+    absorbing strips, so the last tile column is at rest too: the grid's last vertex row and
+    column fall just outside the copied vertex boxes), in z only, and in r only."""
+    spec = W.impact(nr, nz, 10.0, W.basalt(), None, 4, 10e3, int(0.7 * nz), pml, pml_alpha=0.0)
+    runs = {}
+    for mode in (2, 1, 0):
+        g = _fused(spec)
+        g.set_rest_copy(mode)
+        assert g.launches_per_step() == (4 if mode == 2 else 3)
+        g.step(1)
+        q, tiles = g.fused_queue()
+        assert (0 < q < tiles) if mode else q == tiles
+        g.set_kernel_timing(True)
+        g.step(2)
+        names = set(g.kernel_times()[0])
+        g.set_kernel_timing(False)
+        assert names == ({"k_rest_copy", "k_step_fused"} if mode == 2 else {"k_rest_tiles", "k_step_fused"})
+        g.step(57)
+        runs[mode] = g
+    print(f"{nr}x{nz} pml {pml}: {runs[2].fused_queue()} queued / tiles after 60 steps")
+    for mode in (1, 0):
+        _assert_equal(runs[2], runs[mode], spec)
+        sa, sb = runs[2].scalars(), runs[mode].scalars()
+        for k in ("mass_out", "mass_pml", "mass_discarded", "zmom_out"):
+            assert abs(sa[k] - sb[k]) <= 1e-12 * abs(sb[k]), k
+    with pytest.raises(salec.SalecError):
+        runs[2].set_rest_copy(3)
+
+
+def test_rest_copy_beside_falls_back_where_the_form_does_not_allow_it():
+    """Odd nr (the energy's rows would not start on 16-byte boundaries), the mixed form and
+    two materials: the tiles at rest are copied by the rest-tile kernel, with the same
+    results as no copy."""
+    cases = [(W.impact(201, 160, 10.0, W.basalt(), None, 4, 10e3, 112, 0, pml_alpha=0.0), "fp64"),
+             (W.impact(200, 160, 10.0, W.basalt(), None, 4, 10e3, 112, 0, pml_alpha=0.0), "fp32mix"),
+             (W.impact(200, 160, 10.0, W.basalt(), W.iron(), 4, 10e3, 112, 0, pml_alpha=0.0), "fp64")]
+    for spec, precision in cases:
+        a, b = _fused(spec, precision), _fused(spec, precision)
+        a.set_rest_copy(2)
+        b.set_rest_copy(0)
+        assert a.launches_per_step() == 3
+        a.step(40)
+        b.step(40)
+        assert 0 < a.fused_queue()[0] < a.fused_queue()[1]
+        _assert_equal(a, b, spec)
+
+
 @pytest.mark.parametrize("precision", ["fp64", "fp32mix"])
 def test_fused_rest_states_are_exact(precision):
     spec = OC.gas_box_spec(37, 29)
