@@ -26,6 +26,7 @@
 #include <stdint.h>
 
 #include "mlp_internal.cuh"
+#include "salec_tma.cuh"
 
 namespace salec {
 namespace mlp {
@@ -1029,33 +1030,14 @@ size_t gemm_smem_bytes(int nt) { return 2 * (size_t)(kBM * kBK * 2 + nt * kBK * 
 
 namespace {
 
-typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
-                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
-                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
-
-// cuTensorMapEncodeTiled from the driver, looked up once
-EncodeTiledFn encode_tiled()
-{
-    static EncodeTiledFn fn = nullptr;
-    static bool tried = false;
-    if (!tried) {
-        tried = true;
-        void* p = nullptr;
-        cudaDriverEntryPointQueryResult q;
-        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
-            q == cudaDriverEntryPointSuccess)
-            fn = reinterpret_cast<EncodeTiledFn>(p);
-        else
-            (void)cudaGetLastError();
-    }
-    return fn;
-}
+// cuTensorMapEncodeTiled from the driver (looked up once, shared with the solver's copy kernel)
+TmaEncodeTiledFn encode_tiled() { return tma_encode_tiled(); }
 
 // 2-D map of a row-major BF16 matrix [rows][K] with row stride ld elements; boxes of 8
 // elements (16 bytes) x box_rows rows.  False when TMA cannot address it (alignment).
 bool make_map(CUtensorMap* map, const void* base, long rows, long K, long ld, int box_rows)
 {
-    EncodeTiledFn fn = encode_tiled();
+    const TmaEncodeTiledFn fn = encode_tiled();
     if (!fn || rows < 1 || K < 1 || (reinterpret_cast<uintptr_t>(base) & 15) || ((ld * 2) & 15)) return false;
     const cuuint64_t dims[2] = {(cuuint64_t)K, (cuuint64_t)rows};
     const cuuint64_t strides[1] = {(cuuint64_t)(ld * 2)};
@@ -1072,7 +1054,7 @@ size_t tma_smem_bytes(int nt, int stages = kStages) { return (size_t)stages * (k
 // layout (one box is one K slice of box_rows rows).
 bool make_map_sw128(CUtensorMap* map, const void* base, long rows, long K, long ld, int box_rows)
 {
-    EncodeTiledFn fn = encode_tiled();
+    const TmaEncodeTiledFn fn = encode_tiled();
     if (!fn || rows < 1 || K < 64 || (reinterpret_cast<uintptr_t>(base) & 15) || ((ld * 2) & 15)) return false;
     const cuuint64_t dims[2] = {(cuuint64_t)K, (cuuint64_t)rows};
     const cuuint64_t strides[1] = {(cuuint64_t)(ld * 2)};
