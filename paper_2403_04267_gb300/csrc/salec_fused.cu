@@ -1221,9 +1221,11 @@ __global__ void __launch_bounds__(kThreads) k_rest_scan(const int nr, const int 
 // negative c^2 cell by cell), for the running maximum that sets the next step's dt.
 // Stage layout: (f, rho) of material m at m * FR, the EoS cache at NM * FR, I at
 // (NM + 1) * FR.  The maps index: src/dst[m] (f, rho), [NM] I, [NM + 1] the EoS cache.
-// A wait that runs out (2 s) sets status bit 8 and ends the copy.
+// A wait that runs out (2 s) sets status bit 8 and ends the copy.  32 registers a thread:
+// the warp then fits into the quarter of the register file that the tile CTA's four warps
+// in each SM sub-partition leave (4 x 120 x 32 of 16 384).
 template <int NM, int TW, int TH>
-__global__ void __launch_bounds__(32, 1) k_rest_copy(const __grid_constant__ RestCopy rc, const RestCopyArgs A)
+__global__ void __maxnreg__(32) k_rest_copy(const __grid_constant__ RestCopy rc, const RestCopyArgs A)
 {
     constexpr int FR = TW * TH * 16, FI = TW * TH * 8;
     constexpr int STAGE = (NM + 1) * FR + FI;
@@ -1634,10 +1636,14 @@ bool prepare_rest_copy(const ParamsT<double>& P, const OutPtrsT<double>& O, Rest
         (void)cudaGetLastError();
         return false;
     }
-    // registers are given out per warp in units of 256 (8 a thread)
-    const int tile_regs = (ft.numRegs + 7) / 8 * 8 * Beside::S::NT;
+    // registers are given out per warp in units of 256 (8 a thread), each warp's from the
+    // quarter of the register file of its SM sub-partition (four a SM); the tile CTA's
+    // warps spread evenly over the four, and the copy warp must fit beside them in one
+    constexpr int kQuarters = 4;
+    const int tile_warps = (Beside::S::NT / 32 + kQuarters - 1) / kQuarters;
+    const int tile_regs = tile_warps * ((ft.numRegs + 7) / 8 * 8 * 32);
     const int copy_regs = (fc.numRegs + 7) / 8 * 8 * 32;
-    if (tile_regs + copy_regs > regs_sm) return false;
+    if (tile_regs + copy_regs > regs_sm / kQuarters) return false;
     const int tile_smem = (int)Beside::L::bytes + (int)ft.sharedSizeBytes + reserved;
     // more than half of the SM: no SM takes two copy CTAs (which would leave no room there
     // for a tile CTA)
